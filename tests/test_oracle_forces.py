@@ -1,0 +1,148 @@
+"""Pins of the oracle's conserved totals, EOS and Marangoni force
+(Sec. 2.3-2.4)."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import workloads as W
+
+
+def test_compensated_total_is_correctly_rounded():
+    rng = np.random.default_rng(2)
+    g = W.Grid(W.AXI, 37, 23, 1, 0.013)
+    x = rng.standard_normal(g.shape) * 10.0 ** rng.uniform(-8, 8, g.shape)
+    V = oracle.cell_volumes(g)
+    exact = math.fsum((V * x).ravel())
+    assert abs(oracle.total(g, x) - exact) <= 2 * abs(exact) * 2.2e-16 + 1e-300
+
+
+def _band(n=64, R=0.25):
+    g = W.Grid(W.PLANAR, n, n, 1, 1.0 / n)
+    Cf = W.circle_vof(n, n, g.h, 0.5, 0.5, R)
+    _, phi, delta = oracle.phase_field_build(g, Cf, 48, 0.5 * g.h, 0.75 * g.h)
+    return g, Cf, phi, delta
+
+
+def test_gamma_recovery_and_eos_special_values():
+    g, Cf, phi, delta = _band(32)
+    p = W.Params(eps=0.75 * g.h, gamma_inf=2.0, sigma0=3.0, E=0.4)
+    G0 = 0.6
+    gam, sig = oracle.eos(g, p, G0 * delta, phi)
+    inband = delta >= 1e-3 / p.eps
+    np.testing.assert_allclose(gam[inband], G0, rtol=1e-14)
+    assert np.all(gam[~inband] == 0.0) and np.all(sig[~inband] == p.sigma0)
+    # clean interface -> sigma0 for every EOS
+    for e in (W.EOS_LANGMUIR, W.EOS_LINEAR, W.EOS_TANH):
+        p.eos = e
+        _, s0 = oracle.eos(g, p, 0.0 * delta, phi)
+        assert np.all(s0 == p.sigma0)
+    # Langmuir: sigma vanishes at Gamma = Gamma_inf (1 - exp(-1/E))
+    p.eos = W.EOS_LANGMUIR
+    Gz = p.gamma_inf * (1 - math.exp(-1 / p.E))
+    _, sz = oracle.eos(g, p, Gz * delta, phi)
+    assert np.abs(sz[inband]).max() < 1e-13
+    # low-concentration limit: Langmuir and tanh share the linear slope
+    # -sigma0 E / Gamma_inf (Sec. 2.3)
+    dG = 1e-6
+    for e in (W.EOS_LANGMUIR, W.EOS_TANH, W.EOS_LINEAR):
+        p.eos = e
+        _, s = oracle.eos(g, p, dG * delta, phi)
+        slope = (s[inband] - p.sigma0) / dG
+        np.testing.assert_allclose(slope, -p.sigma0 * p.E / p.gamma_inf, rtol=1e-5)
+
+
+def test_plic_area_closed_forms():
+    # interface normal to an axis: unit area for any fraction
+    for C in (0.1, 0.5, 0.93):
+        assert abs(oracle.plic_area(2, [1.0, 0.0], C) - 1.0) < 1e-12
+        assert abs(oracle.plic_area(3, [0.0, 0.0, -2.0], C) - 1.0) < 1e-12
+    # 2D diagonal through the centre: length sqrt(2)
+    assert abs(oracle.plic_area(2, [1.0, 1.0], 0.5) - math.sqrt(2)) < 1e-12
+    # 3D diagonal through the centre: regular hexagon of area 3 sqrt(3)/4
+    assert abs(oracle.plic_area(3, [1.0, 1.0, 1.0], 0.5) - 3 * math.sqrt(3) / 4) < 1e-12
+    # 3D corner triangle: alpha = 1/4 with m = (1,1,1)/3 cuts a triangle of
+    # side sqrt(2)*0.75 -> area sqrt(3)/4 * (0.75 sqrt 2)^2, volume (0.75^3)/6
+    C = 0.75 ** 3 / 6
+    assert abs(oracle.plic_area(3, [1.0, 1.0, 1.0], C) -
+               math.sqrt(3) / 4 * 2 * 0.75 ** 2) < 1e-12
+
+
+def test_plic_volume_matches_brute_force():
+    rng = np.random.default_rng(9)
+    k = 60
+    s = (np.arange(k) + 0.5) / k
+    X, Y, Z = np.meshgrid(s, s, s, indexing="ij")
+    for _ in range(5):
+        m = rng.uniform(-1, 1, 3)
+        mp = np.abs(m) / np.abs(m).sum()
+        a = rng.uniform(0.1, 0.9)
+        inside = (mp[0] * X + mp[1] * Y + mp[2] * Z <= a).mean()
+        assert abs(oracle.plic_volume(3, m, a) - inside) < 4e-3
+
+
+def test_plic_delta_integrates_to_perimeter():
+    for n in (32, 64):
+        g = W.Grid(W.PLANAR, n, n, 1, 1.0 / n)
+        R = 0.3
+        Cf = W.circle_vof(n, n, g.h, 0.5, 0.5, R)
+        p = W.Params(eps=0.75 * g.h)
+        _, phi, delta = oracle.phase_field_build(g, Cf, 24, 0.5 * g.h, p.eps)
+        # uniform tension gradient along x: the force is delta_m (I - nn) e_x
+        # so sum_c V delta_m = perimeter is read from a linear EOS trick:
+        sig, force = oracle.marangoni(g, p, 0 * delta, phi, Cf, dm_mode=1)
+        # uniform Gamma -> no Marangoni force
+        assert np.abs(force).max() == 0.0
+    # perimeter from the PLIC segment lengths: with the exact (radial)
+    # normal the polygon length converges to 2 pi R; with Youngs normals
+    # (first-order) it stays within about 1.5 %
+    n, R = 128, 0.3
+    g = W.Grid(W.PLANAR, n, n, 1, 1.0 / n)
+    Cf = W.circle_vof(n, n, g.h, 0.5, 0.5, R)
+    x = (np.arange(n) + 0.5) * g.h - 0.5
+    P = np.pad(Cf[0], 1, mode="edge")
+    w = np.array([1.0, 2.0, 1.0])
+    tot_exact = tot_youngs = 0.0
+    for j in range(n):
+        for i in range(n):
+            c = Cf[0, j, i]
+            if 0 < c < 1:
+                tot_exact += oracle.plic_area(2, [x[i], x[j]], c) * g.h
+                blk = P[j:j + 3, i:i + 3]
+                mx = -((blk[:, 2] - blk[:, 0]) * w).sum()
+                my = -((blk[2, :] - blk[0, :]) * w).sum()
+                tot_youngs += oracle.plic_area(2, [mx, my], c) * g.h
+    assert abs(tot_exact - 2 * math.pi * R) < 1e-3 * 2 * math.pi * R
+    assert abs(tot_youngs - 2 * math.pi * R) < 2e-2 * 2 * math.pi * R
+
+
+def test_marangoni_force_is_tangential_and_matches_surface_gradient():
+    """Linear EOS with Gamma = 1 + 0.2 cos(theta) on a circle: F_Ma is
+    tangential (n . F = 0) and F/delta_m -> grad_s sigma
+    = -sigma0 E/Gamma_inf dGamma/ds = 0.2 sigma0 E sin(theta)/(R Gamma_inf) e_theta."""
+    errs = []
+    for n in (64, 128):
+        g, Cf, phi, delta = _band(n)
+        R = 0.25
+        x = (np.arange(n) + 0.5) * g.h - 0.5
+        th = np.arctan2(x[:, None], x[None, :])[None]
+        Gam = 1.0 + 0.2 * np.cos(th)
+        p = W.Params(eps=0.75 * g.h, eos=W.EOS_LINEAR, sigma0=1.0, E=0.3, gamma_inf=1.0)
+        sig, force = oracle.marangoni(g, p, Gam * delta, phi, Cf, dm_mode=1)
+        nrm = oracle.normals(g, phi)
+        ndotf = nrm[0] * force[0] + nrm[1] * force[1]
+        assert np.abs(ndotf).max() < 1e-12 * np.abs(force).max()
+        # compare in interface cells, away from the band edge
+        sel = (Cf > 0.05) & (Cf < 0.95)
+        dm = np.hypot(force[0], force[1])
+        ft = -force[0] * np.sin(th) + force[1] * np.cos(th)
+        # delta_m from the force magnitude direction-free: project and divide
+        # by the PLIC delta that the oracle used
+        tot_force = (ft * g.h ** 2)[sel].sum()
+        expect_density = (0.2 * p.sigma0 * p.E / (R * p.gamma_inf)) * np.sin(th)
+        # integrate sin(theta) * F_t over the band: -> int over the circle of
+        # 0.2 E/R sin^2 ds = 0.2 E pi
+        num = (ft * np.sin(th) * g.h ** 2).sum()
+        errs.append(abs(num - 0.2 * p.E * math.pi) / (0.2 * p.E * math.pi))
+    assert errs[-1] < 0.05 and errs[-1] <= errs[0] + 1e-3, errs
