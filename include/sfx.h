@@ -1,0 +1,185 @@
+/*
+ * libsfx: GB300 (sm_103a) library for the per-time-step coupled soluble-
+ * surfactant update of the hybrid VoF / phase-field method
+ * (arxiv 2605.27534) on uniform Cartesian blocks: 2D planar, axisymmetric
+ * and 3D.
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ * Layout.  Cell arrays hold nx*ny*nz values, x fastest: (k*ny + j)*nx + i.
+ *   2D planar and axisymmetric grids have nz = 1; in the axisymmetric case x
+ *   is the radius r (axis at r = 0) and y the axial coordinate z.
+ *   Face-normal velocities: ux (nz, ny, nx+1), uy (nz, ny+1, nx),
+ *   uz (nz+1, ny, nx) (3D only), x fastest.
+ * Memory.  Every field pointer is a DEVICE pointer owned by the caller (e.g.
+ *   a torch tensor), contiguous, of the element type named in each call.  The
+ *   library owns only the opaque context and the scratch inside it (the
+ *   multigrid pyramid and work arrays), allocated by sfx_ctx_create and freed
+ *   by sfx_ctx_destroy.
+ * Streams.  `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *   stream).  Work is enqueued on it in order.  Calls that report statistics
+ *   or iterate to a tolerance synchronise with that stream before returning.
+ * Errors.  Every call returns an sfx_status; nothing is thrown across the
+ *   ABI.  sfx_status_string() names a status.  On SFX_ERR_ARG nothing was
+ *   enqueued.  On SFX_ERR_NOT_CONVERGED the fields hold the last iterate and
+ *   the stats are filled.  SFX_ERR_CUDA carries the CUDA error that
+ *   sfx_last_cuda_error() returns.
+ * Precision.  A context is created for SFX_F64 (every array double) or
+ *   SFX_F32 (transported state f, F and totals in double; phase field,
+ *   velocities and smoothing in float, with the residual and the
+ *   iterative-refinement correction evaluated in double-float arithmetic).
+ */
+#ifndef SFX_H
+#define SFX_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  SFX_OK = 0,
+  SFX_ERR_ARG = 1,            /* null pointer, bad size or option */
+  SFX_ERR_NOT_CONVERGED = 2,  /* tolerance not reached in max_cycles */
+  SFX_ERR_NONFINITE = 3,      /* NaN or Inf met in a residual */
+  SFX_ERR_TIMEOUT = 4,        /* a bounded device-side wait gave up */
+  SFX_ERR_CUDA = 5,           /* a CUDA runtime call failed */
+  SFX_ERR_WORKSPACE = 6       /* grid larger than the context was made for */
+} sfx_status;
+
+typedef enum { SFX_PLANAR2D = 0, SFX_AXISYM = 1, SFX_CART3D = 2 } sfx_geom;
+typedef enum { SFX_F64 = 0, SFX_F32 = 1 } sfx_precision;
+typedef enum { SFX_EOS_LANGMUIR = 0, SFX_EOS_LINEAR = 1, SFX_EOS_TANH = 2 } sfx_eos;
+
+/* Uniform block (Sec. 3.2; App. A for 3D, App. B for axisymmetric). */
+typedef struct {
+  int geom;           /* sfx_geom */
+  int nx, ny, nz;     /* cells; nz = 1 unless SFX_CART3D */
+  double h;           /* cell size, > 0 */
+} sfx_grid;
+
+/* Physical parameters of Sec. 2.3-2.6 and App. C. */
+typedef struct {
+  double ka, kd;      /* adsorption rate r_a, desorption rate r_d, >= 0 */
+  double gamma_inf;   /* saturation concentration Gamma_inf, > 0 */
+  double Df, DF;      /* interfacial and bulk diffusivity, >= 0 */
+  double eps;         /* phase-field width epsilon, > 0 (paper: 0.75 h) */
+  double eta;         /* small constant in F/(phi + eta) (Sec. 2.6), >= 0 */
+  double sigma0, E;   /* clean surface tension, Gibbs elasticity */
+  int eos;            /* sfx_eos */
+  int literal_upwind; /* 0: drift upwinded on its transport velocity -B;
+                         1: face value as printed in Sec. 3.2 (for study) */
+  double bc_F, bc_f;  /* inflow values used by the advection at walls */
+} sfx_params;
+
+/* Implicit solve controls (App. C Picard iteration, multigrid V-cycles). */
+typedef struct {
+  double tol;         /* stop when both relative nonlinear residuals
+                         |b - L(a)|_inf / |b|_inf <= tol */
+  int max_cycles;     /* cap on Picard iterations (each: nu V-cycles per field) */
+  int nu1, nu2;       /* red-black Gauss-Seidel sweeps before / after the
+                         coarse-grid correction */
+  int mg_levels;      /* levels in the V-cycle (1 = smoother only; 0 = auto) */
+  int vcycles;        /* V-cycles per field per Picard iteration (>= 1) */
+  int check_every;    /* Picard iterations between residual checks (>= 1) */
+  int coarse_sweeps;  /* Gauss-Seidel sweeps on the coarsest level */
+} sfx_solve_opts;
+
+typedef struct {
+  int picard;         /* Picard iterations taken */
+  int vcycles;        /* V-cycles taken (both fields) */
+  double res_f, res_F;/* final relative nonlinear residuals */
+  double mass_f, mass_F; /* sum V f and sum V F after the step (FP64,
+                            compensated) */
+  int converged;
+} sfx_step_stats;
+
+typedef struct sfx_ctx sfx_ctx;
+
+/* Library version and error text. */
+const char* sfx_version(void);
+const char* sfx_status_string(sfx_status s);
+const char* sfx_last_cuda_error(void);
+
+/* Context for one grid shape and precision: allocates the multigrid
+   pyramid and work arrays on the current CUDA device (cudaMalloc).
+   Returns SFX_ERR_ARG for a bad grid, SFX_ERR_CUDA if allocation fails. */
+sfx_status sfx_ctx_create(const sfx_grid* grid, int precision, sfx_ctx** out);
+void sfx_ctx_destroy(sfx_ctx* ctx);
+/* Fill opts with the defaults used when a call gets opts = NULL. */
+void sfx_default_opts(sfx_solve_opts* opts);
+
+/* a1 + a2.  Phase field from the VoF fraction (Sec. 2.5):
+   chi0 = 2h(C - 1/2), `iters` Jacobi steps of the Hamilton-Jacobi
+   redistancing d chi/d tau + sign(chi0)(|grad chi| - 1) = 0 (first-order
+   Godunov with the Russo-Smereka sub-cell fix) at pseudo-time step dtau,
+   then phi = (1 - tanh(chi/(2 eps)))/2 and delta = phi (1 - phi)/eps.
+   C, chi: double.  phi, delta: the context precision (double or float).
+   delta may be NULL. */
+sfx_status sfx_phase_field_build(sfx_ctx* ctx, const double* C, double* chi,
+                                 void* phi, void* delta, int iters,
+                                 double dtau, double eps, void* stream);
+
+/* a3.  Explicit BCG advection xi* = xi - dt div(u xi) (Sec. 3.1) of one
+   double field with face velocities u (context precision); bc_in is the
+   value carried in through inflow walls.  xi_out must not alias xi. */
+sfx_status sfx_advect(sfx_ctx* ctx, const void* ux, const void* uy,
+                      const void* uz, double dt, const double* xi,
+                      double bc_in, double* xi_out, void* stream);
+
+/* a5.  Solve the generalised elliptic problem of Sec. 3.1
+   div(alpha grad a + beta a) + lambda a = b with alpha = -D and beta = -B
+   (B given on faces: Bx (nz,ny,nx+1), By (nz,ny+1,nx), Bz (nz+1,ny,nx) or
+   NULL in 2D; wall faces are ignored) by multigrid V-cycles until
+   |b - L(a)|_inf <= tol |b|_inf.  All arrays double (SFX_F64 contexts).
+   a holds the initial guess and receives the solution. */
+sfx_status sfx_mg_solve(sfx_ctx* ctx, double D, const double* Bx,
+                        const double* By, const double* Bz, int literal_upwind,
+                        const double* lambda, const double* b, double* a,
+                        const sfx_solve_opts* opts, int* cycles_out,
+                        double* res_out, void* stream);
+
+/* a2 + a3 + a4 + a5 + a6.  One coupled surfactant step (Sec. 3.1 splitting;
+   App. C source): explicit BCG advection of f and F when ux != NULL, then
+   the fully implicit f/F system of App. C solved by Picard iteration, each
+   half a multigrid solve of the Sec. 3.1 operator with the drifts
+   B_f = -Df 2(0.5 - phi)/eps n and B_F = -DF (1 - phi)/eps n,
+   n = grad phi/|grad phi|.  f and F (double) are updated in place; phi and
+   the velocities are in the context precision.  stats may be NULL. */
+sfx_status sfx_surfactant_step(sfx_ctx* ctx, const sfx_params* params,
+                               const void* phi, const void* ux,
+                               const void* uy, const void* uz, double* f,
+                               double* F, double dt,
+                               const sfx_solve_opts* opts,
+                               sfx_step_stats* stats, void* stream);
+
+/* a6.  Compensated totals sum V x of `n_fields` double fields (out[i],
+   host memory).  Volumes: h^2 (planar), h^3 (3D), pi (r+^2 - r-^2) h
+   (axisymmetric).  Deterministic: fixed reduction order. */
+sfx_status sfx_totals(sfx_ctx* ctx, const double* const* fields, int n_fields,
+                      double* out, void* stream);
+
+/* a7 + a8.  EOS and Marangoni force (Sec. 2.3-2.4):
+   Gamma = f/delta_phi where delta_phi >= 1e-3/eps (else 0); sigma(Gamma)
+   by params->eos, evaluated in double; force = delta_m (I - n n) grad sigma
+   with centred grad sigma, n from phi, and delta_m the PLIC interface area
+   per cell volume (dm_mode 1; Youngs normal) or |grad C| (dm_mode 0).
+   f, C, sigma, force: double; phi: context precision.  force holds
+   ndim arrays of N cells, component-major. */
+sfx_status sfx_marangoni_force(sfx_ctx* ctx, const sfx_params* params,
+                               const double* f, const void* phi,
+                               const double* C, int dm_mode, double* sigma,
+                               double* force, void* stream);
+
+/* a9.  Time step of Sec. 3.3: safety * min(h/(umax + D/eps),
+   h^2/(2 N_d D)), with umax the largest |face velocity| (reduced on the
+   device from ux, uy, uz in the context precision).  Host result. */
+sfx_status sfx_cfl_dt(sfx_ctx* ctx, const void* ux, const void* uy,
+                      const void* uz, double D, double eps, double safety,
+                      double* dt_out, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SFX_H */

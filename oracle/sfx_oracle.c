@@ -341,9 +341,9 @@ int orc_elliptic_solve(const orc_grid* g, double D, const double* Bx,
         }
     ++sweeps;
     res = rel_residual(g, D, Bx, By, Bz, literal_upwind, lambda, b, a);
-    /* stop at the round-off floor: no progress over 4 sweeps */
-    if (res < 0.5 * best) { best = res; stall = 0; }
-    else if (++stall >= 4) break;
+    /* stop at the round-off floor: 50 sweeps without a 0.1 % improvement */
+    if (res < best * (1.0 - 1e-3)) { best = res; stall = 0; }
+    else if (++stall >= 50) break;
   }
   if (rel_res) *rel_res = res;
   return res <= tol ? sweeps : -sweeps;
@@ -624,56 +624,67 @@ void orc_eos(const orc_grid* g, const orc_params* p, const double* f,
   }
 }
 
-/* volume of the unit cube below m.x = alpha, m >= 0 with sum m = 1
-   (Scardovelli & Zaleski 2000), dimension reduced when components vanish */
-static double hpos(double x) { return x > 0 ? x : 0; }
+/* Volume of the unit cube below the plane m.x = a, for m >= 0 with
+   sum m = 1 (Scardovelli & Zaleski 2000), and its derivative in a.  The
+   cubic of that paper is evaluated region by region in expanded form, so
+   components near zero lose no precision (the region whose width equals a
+   tiny component is simply empty).  By symmetry V(a) = 1 - V(1 - a), so
+   only a <= 1/2 is evaluated directly.  m is sorted ascending here. */
+static void sort_asc(double* m, int n) {
+  for (int i = 1; i < n; ++i)
+    for (int j = i; j > 0 && m[j] < m[j - 1]; --j) {
+      double t = m[j]; m[j] = m[j - 1]; m[j - 1] = t;
+    }
+}
 
-static void plic_reduce(int dim, const double* m, double* mm, int* dd) {
-  int n = 0;
-  for (int d = 0; d < dim; ++d)
-    if (m[d] > 1e-10) mm[n++] = m[d];
-  *dd = n;
+/* value (want_derivative = 0) or derivative (1) for a <= 1/2 */
+static double plic_half(int dim, const double* m, double a, int want_derivative) {
+  if (a <= 0.0) return 0.0;
+  if (dim == 2) {
+    double m1 = m[0], m2 = m[1];           /* m1 <= m2, m1 + m2 = 1 */
+    if (a < m1)                            /* corner triangle */
+      return want_derivative ? a / (m1 * m2) : a * a / (2.0 * m1 * m2);
+    return want_derivative ? 1.0 / m2 : (a - 0.5 * m1) / m2; /* trapezoid */
+  }
+  double m1 = m[0], m2 = m[1], m3 = m[2];  /* ascending, sum 1 */
+  double v, dv;
+  if (a < m1) {                            /* corner tetrahedron */
+    v = a * a * a / (6.0 * m1 * m2 * m3);
+    dv = a * a / (2.0 * m1 * m2 * m3);
+  } else if (a < m2) {                     /* wedge along the m1 axis */
+    v = (a * a - a * m1 + m1 * m1 / 3.0) / (2.0 * m2 * m3);
+    dv = (2.0 * a - m1) / (2.0 * m2 * m3);
+  } else if (a < m3 && a < m1 + m2) {      /* two corners cut */
+    double u = a - m2;
+    v = (3.0 * a * a - 3.0 * a * m1 + m1 * m1) / (6.0 * m2 * m3) -
+        u * u * u / (6.0 * m1 * m2 * m3);
+    dv = (2.0 * a - m1) / (2.0 * m2 * m3) - u * u / (2.0 * m1 * m2 * m3);
+  } else if (m3 >= m1 + m2) {              /* plane spans the m3 direction */
+    v = (a - 0.5 * (m1 + m2)) / m3;
+    dv = 1.0 / m3;
+  } else {                                 /* m3 <= a < m1 + m2 */
+    double u = a - m2, w = a - m3;
+    v = (3.0 * a * a - 3.0 * a * m1 + m1 * m1) / (6.0 * m2 * m3) -
+        (u * u * u + w * w * w) / (6.0 * m1 * m2 * m3);
+    dv = (2.0 * a - m1) / (2.0 * m2 * m3) - (u * u + w * w) / (2.0 * m1 * m2 * m3);
+  }
+  return want_derivative ? dv : v;
 }
 
 static double plic_vol_pos(int dim, const double* m, double a) {
-  double mm[3];
-  int n;
-  plic_reduce(dim, m, mm, &n);
-  if (a <= 0) return 0.0;
-  double s = 0;
-  for (int d = 0; d < n; ++d) s += mm[d];
-  if (a >= s) return 1.0;
-  if (n == 1) return a / mm[0];
-  if (n == 2)
-    return (a * a - hpos(a - mm[0]) * hpos(a - mm[0]) -
-            hpos(a - mm[1]) * hpos(a - mm[1]) +
-            hpos(a - s) * hpos(a - s)) / (2.0 * mm[0] * mm[1]);
-  double v = a * a * a;
-  for (int d = 0; d < 3; ++d) v -= pow(hpos(a - mm[d]), 3);
-  v += pow(hpos(a - mm[0] - mm[1]), 3) + pow(hpos(a - mm[0] - mm[2]), 3) +
-       pow(hpos(a - mm[1] - mm[2]), 3);
-  v -= pow(hpos(a - s), 3);
-  return v / (6.0 * mm[0] * mm[1] * mm[2]);
+  double ms[3] = {m[0], m[1], dim == 3 ? m[2] : 0.0};
+  sort_asc(ms, dim);
+  if (a <= 0.0) return 0.0;
+  if (a >= 1.0) return 1.0;
+  if (a <= 0.5) return plic_half(dim, ms, a, 0);
+  return 1.0 - plic_half(dim, ms, 1.0 - a, 0);
 }
 
-/* derivative of the volume with respect to alpha */
 static double plic_dvol_pos(int dim, const double* m, double a) {
-  double mm[3];
-  int n;
-  plic_reduce(dim, m, mm, &n);
-  double s = 0;
-  for (int d = 0; d < n; ++d) s += mm[d];
-  if (a <= 0 || a >= s) return 0.0;
-  if (n == 1) return 1.0 / mm[0];
-  if (n == 2)
-    return (a - hpos(a - mm[0]) - hpos(a - mm[1]) + hpos(a - s)) /
-           (mm[0] * mm[1]);
-  double v = a * a;
-  for (int d = 0; d < 3; ++d) v -= hpos(a - mm[d]) * hpos(a - mm[d]);
-  v += pow(hpos(a - mm[0] - mm[1]), 2) + pow(hpos(a - mm[0] - mm[2]), 2) +
-       pow(hpos(a - mm[1] - mm[2]), 2);
-  v -= hpos(a - s) * hpos(a - s);
-  return v / (2.0 * mm[0] * mm[1] * mm[2]);
+  double ms[3] = {m[0], m[1], dim == 3 ? m[2] : 0.0};
+  sort_asc(ms, dim);
+  if (a <= 0.0 || a >= 1.0) return 0.0;
+  return plic_half(dim, ms, a <= 0.5 ? a : 1.0 - a, 1);
 }
 
 static void plic_normalise(int dim, const double* m, double* mp, double* l2) {

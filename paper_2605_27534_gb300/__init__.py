@@ -1,0 +1,152 @@
+"""GB300 (sm_103a) library for the coupled soluble-surfactant step of the hybrid
+VoF / phase-field method (arxiv 2605.27534).
+
+This module is a thin binding: it marshals torch CUDA tensors (device
+pointers) and the current torch stream into the C-ABI of libsfx
+(include/sfx.h).  Every step of the method runs in the library's CUDA
+kernels; nothing here computes on the CPU, and nothing falls back when the
+library is missing.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import dataclasses
+from typing import Optional, Sequence
+
+from . import _lib
+from ._lib import (SFX_AXISYM, SFX_CART3D, SFX_F32, SFX_F64, SFX_OK, SFX_ERR_NOT_CONVERGED,
+                   SFX_PLANAR2D, Grid, Params, SolveOpts, StepStats)
+
+__all__ = ["SfxError", "Context", "lib", "default_opts", "SFX_PLANAR2D", "SFX_AXISYM",
+           "SFX_CART3D", "SFX_F64", "SFX_F32"]
+
+
+class SfxError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        L = lib()
+        msg = L.sfx_status_string(status).decode()
+        if status == _lib.SFX_ERR_CUDA:
+            msg += " (%s)" % L.sfx_last_cuda_error().decode()
+        super().__init__("%s: %s" % (where, msg))
+        self.status = status
+
+
+def lib():
+    return _lib.load()
+
+
+def _check(st: int, where: str, allow=()):
+    if st != SFX_OK and st not in allow:
+        raise SfxError(st, where)
+    return st
+
+
+def default_opts(**kw) -> SolveOpts:
+    o = SolveOpts()
+    lib().sfx_default_opts(C.byref(o))
+    for k, v in kw.items():
+        setattr(o, k, v)
+    return o
+
+
+def _ptr(t) -> Optional[int]:
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError("libsfx takes CUDA tensors (device pointers)")
+    if not t.is_contiguous():
+        raise ValueError("libsfx takes contiguous tensors")
+    return t.data_ptr()
+
+
+def _stream():
+    import torch
+    return torch.cuda.current_stream().cuda_stream
+
+
+def params_struct(p) -> Params:
+    """Params from any object with the fields of sfx_params."""
+    return Params(p.ka, p.kd, p.gamma_inf, p.Df, p.DF, p.eps, p.eta, p.sigma0, p.E, int(p.eos),
+                  int(p.literal_upwind), p.bc_F, p.bc_f)
+
+
+class Context:
+    """One grid shape and precision (owns the multigrid pyramid and scratch)."""
+
+    def __init__(self, geom: int, nx: int, ny: int, nz: int, h: float, precision: int = SFX_F64):
+        self.grid = Grid(int(geom), int(nx), int(ny), int(nz), float(h))
+        self.precision = int(precision)
+        h_ = C.c_void_p()
+        _check(lib().sfx_ctx_create(C.byref(self.grid), self.precision, C.byref(h_)),
+               "sfx_ctx_create")
+        self._h = h_
+
+    @classmethod
+    def for_grid(cls, g, precision=SFX_F64):
+        return cls(g.geom, g.nx, g.ny, g.nz, g.h, precision)
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self):
+        if self._h:
+            lib().sfx_ctx_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ------------------------------------------------------------ calls
+    def sfx_phase_field_build(self, Cf, chi, phi, delta=None, iters=24, dtau=None, eps=None):
+        dtau = dtau if dtau is not None else 0.5 * self.grid.h
+        _check(lib().sfx_phase_field_build(self._h, _ptr(Cf), _ptr(chi), _ptr(phi), _ptr(delta),
+                                           int(iters), float(dtau), float(eps), _stream()),
+               "sfx_phase_field_build")
+
+    def sfx_advect(self, ux, uy, uz, dt, xi, bc_in, xi_out):
+        _check(lib().sfx_advect(self._h, _ptr(ux), _ptr(uy), _ptr(uz), float(dt), _ptr(xi),
+                                float(bc_in), _ptr(xi_out), _stream()), "sfx_advect")
+
+    def sfx_mg_solve(self, D, Bx, By, Bz, lam, b, a, opts=None, literal_upwind=0):
+        o = opts if opts is not None else default_opts()
+        cyc, res = C.c_int(0), C.c_double(0)
+        st = lib().sfx_mg_solve(self._h, float(D), _ptr(Bx), _ptr(By), _ptr(Bz),
+                                int(literal_upwind), _ptr(lam), _ptr(b), _ptr(a), C.byref(o),
+                                C.byref(cyc), C.byref(res), _stream())
+        _check(st, "sfx_mg_solve", allow=(SFX_ERR_NOT_CONVERGED,))
+        return cyc.value, res.value, st == SFX_OK
+
+    def sfx_surfactant_step(self, params, phi, f, F, dt, ux=None, uy=None, uz=None, opts=None,
+                            stats=True, allow_not_converged=False):
+        o = opts if opts is not None else default_opts()
+        st_ = StepStats()
+        ps = params if isinstance(params, Params) else params_struct(params)
+        st = lib().sfx_surfactant_step(self._h, C.byref(ps), _ptr(phi), _ptr(ux), _ptr(uy),
+                                       _ptr(uz), _ptr(f), _ptr(F), float(dt), C.byref(o),
+                                       C.byref(st_) if stats else None, _stream())
+        _check(st, "sfx_surfactant_step",
+               allow=(SFX_ERR_NOT_CONVERGED,) if allow_not_converged else ())
+        return st_
+
+    def sfx_totals(self, fields: Sequence):
+        n = len(fields)
+        arr = (C.c_void_p * n)(*[_ptr(t) for t in fields])
+        out = (C.c_double * n)()
+        _check(lib().sfx_totals(self._h, arr, n, out, _stream()), "sfx_totals")
+        return [out[i] for i in range(n)]
+
+    def sfx_marangoni_force(self, params, f, phi, Cf, sigma, force, dm_mode=1):
+        ps = params if isinstance(params, Params) else params_struct(params)
+        _check(lib().sfx_marangoni_force(self._h, C.byref(ps), _ptr(f), _ptr(phi), _ptr(Cf),
+                                         int(dm_mode), _ptr(sigma), _ptr(force), _stream()),
+               "sfx_marangoni_force")
+
+    def sfx_cfl_dt(self, ux, uy, uz, D, eps, safety=1.0):
+        out = C.c_double(0)
+        _check(lib().sfx_cfl_dt(self._h, _ptr(ux), _ptr(uy), _ptr(uz), float(D), float(eps),
+                                float(safety), C.byref(out), _stream()), "sfx_cfl_dt")
+        return out.value

@@ -1,0 +1,94 @@
+"""ctypes declarations of the libsfx C-ABI (include/sfx.h).
+
+Loading fails loudly when the library has not been built: there is no CPU
+or Python fallback for any call.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+PKG = os.path.dirname(os.path.abspath(__file__))
+SO_PATH = os.path.join(PKG, "libsfx.so")
+
+SFX_OK, SFX_ERR_ARG, SFX_ERR_NOT_CONVERGED, SFX_ERR_NONFINITE, SFX_ERR_TIMEOUT, \
+    SFX_ERR_CUDA, SFX_ERR_WORKSPACE = range(7)
+SFX_PLANAR2D, SFX_AXISYM, SFX_CART3D = 0, 1, 2
+SFX_F64, SFX_F32 = 0, 1
+
+#: every entry point declared in include/sfx.h
+EXPORTS = [
+    "sfx_version", "sfx_status_string", "sfx_last_cuda_error", "sfx_ctx_create",
+    "sfx_ctx_destroy", "sfx_default_opts", "sfx_phase_field_build", "sfx_advect",
+    "sfx_mg_solve", "sfx_surfactant_step", "sfx_totals", "sfx_marangoni_force", "sfx_cfl_dt",
+]
+
+
+class Grid(C.Structure):
+    _fields_ = [("geom", C.c_int), ("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int),
+                ("h", C.c_double)]
+
+
+class Params(C.Structure):
+    _fields_ = [("ka", C.c_double), ("kd", C.c_double), ("gamma_inf", C.c_double),
+                ("Df", C.c_double), ("DF", C.c_double), ("eps", C.c_double),
+                ("eta", C.c_double), ("sigma0", C.c_double), ("E", C.c_double),
+                ("eos", C.c_int), ("literal_upwind", C.c_int), ("bc_F", C.c_double),
+                ("bc_f", C.c_double)]
+
+
+class SolveOpts(C.Structure):
+    _fields_ = [("tol", C.c_double), ("max_cycles", C.c_int), ("nu1", C.c_int),
+                ("nu2", C.c_int), ("mg_levels", C.c_int), ("vcycles", C.c_int),
+                ("check_every", C.c_int), ("coarse_sweeps", C.c_int)]
+
+
+class StepStats(C.Structure):
+    _fields_ = [("picard", C.c_int), ("vcycles", C.c_int), ("res_f", C.c_double),
+                ("res_F", C.c_double), ("mass_f", C.c_double), ("mass_F", C.c_double),
+                ("converged", C.c_int)]
+
+
+_lib = None
+vp, dp = C.c_void_p, C.c_double
+
+
+def load(path: str = SO_PATH):
+    """Load libsfx.so (raises OSError if it is missing or unloadable)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise OSError("libsfx.so not built (%s): run __graft_entry__.build() or "
+                      "python paper_2605_27534_gb300/build.py" % path)
+    L = C.CDLL(path)
+    L.sfx_version.restype = C.c_char_p
+    L.sfx_version.argtypes = []
+    L.sfx_status_string.restype = C.c_char_p
+    L.sfx_status_string.argtypes = [C.c_int]
+    L.sfx_last_cuda_error.restype = C.c_char_p
+    L.sfx_last_cuda_error.argtypes = []
+    L.sfx_ctx_create.restype = C.c_int
+    L.sfx_ctx_create.argtypes = [C.POINTER(Grid), C.c_int, C.POINTER(vp)]
+    L.sfx_ctx_destroy.restype = None
+    L.sfx_ctx_destroy.argtypes = [vp]
+    L.sfx_default_opts.restype = None
+    L.sfx_default_opts.argtypes = [C.POINTER(SolveOpts)]
+    L.sfx_phase_field_build.restype = C.c_int
+    L.sfx_phase_field_build.argtypes = [vp, vp, vp, vp, vp, C.c_int, dp, dp, vp]
+    L.sfx_advect.restype = C.c_int
+    L.sfx_advect.argtypes = [vp, vp, vp, vp, dp, vp, dp, vp, vp]
+    L.sfx_mg_solve.restype = C.c_int
+    L.sfx_mg_solve.argtypes = [vp, dp, vp, vp, vp, C.c_int, vp, vp, vp, C.POINTER(SolveOpts),
+                               C.POINTER(C.c_int), C.POINTER(C.c_double), vp]
+    L.sfx_surfactant_step.restype = C.c_int
+    L.sfx_surfactant_step.argtypes = [vp, C.POINTER(Params), vp, vp, vp, vp, vp, vp, dp,
+                                      C.POINTER(SolveOpts), C.POINTER(StepStats), vp]
+    L.sfx_totals.restype = C.c_int
+    L.sfx_totals.argtypes = [vp, C.POINTER(C.c_void_p), C.c_int, C.POINTER(C.c_double), vp]
+    L.sfx_marangoni_force.restype = C.c_int
+    L.sfx_marangoni_force.argtypes = [vp, C.POINTER(Params), vp, vp, vp, C.c_int, vp, vp, vp]
+    L.sfx_cfl_dt.restype = C.c_int
+    L.sfx_cfl_dt.argtypes = [vp, vp, vp, vp, dp, dp, dp, C.POINTER(C.c_double), vp]
+    _lib = L
+    return L

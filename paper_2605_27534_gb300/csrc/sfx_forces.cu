@@ -1,0 +1,273 @@
+// Conserved totals (compensated, deterministic), the surface-tension EOS of
+// Sec. 2.3 and the Marangoni force of Sec. 2.4.
+#include <cmath>
+#include <cstring>
+
+#include "sfx_internal.h"
+
+namespace sfx {
+namespace {
+
+constexpr int kTotThreads = 256;
+
+// Per-block compensated partial sums of V x for field `fi`.
+__global__ void k_total_partials(Level L, const double* __restrict__ x, int fi,
+                                 double* __restrict__ partials) {
+  const size_t n = L.ncell();
+  double s = 0.0, cc = 0.0;
+  for (size_t c = blockIdx.x * (size_t)blockDim.x + threadIdx.x; c < n;
+       c += (size_t)gridDim.x * blockDim.x) {
+    double v = cell_volume(L, (int)(c % L.nx)) * x[c];
+    double t, e;
+    two_sum(s, v, t, e);
+    s = t;
+    cc += e;
+  }
+  warp_sum_comp(s, cc);
+  __shared__ double ss[kTotThreads / 32], sc[kTotThreads / 32];
+  int w = threadIdx.x >> 5;
+  if ((threadIdx.x & 31) == 0) { ss[w] = s; sc[w] = cc; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double a = ss[0], b = sc[0];
+    for (int q = 1; q < kTotThreads / 32; ++q) {
+      double t, e;
+      two_sum(a, ss[q], t, e);
+      a = t;
+      b += sc[q] + e;
+    }
+    size_t o = 2 * ((size_t)fi * gridDim.x + blockIdx.x);
+    partials[o] = a;
+    partials[o + 1] = b;
+  }
+}
+
+// One block per field: fixed-order combination of the block partials.
+__global__ void k_total_final(const double* __restrict__ partials, int nblk,
+                              double* __restrict__ out) {
+  const int fi = blockIdx.x;
+  double s = 0.0, cc = 0.0;
+  for (int q = threadIdx.x; q < nblk; q += blockDim.x) {
+    size_t o = 2 * ((size_t)fi * nblk + q);
+    double t, e;
+    two_sum(s, partials[o], t, e);
+    s = t;
+    cc += partials[o + 1] + e;
+  }
+  warp_sum_comp(s, cc);
+  __shared__ double ss[kTotThreads / 32], sc[kTotThreads / 32];
+  int w = threadIdx.x >> 5;
+  if ((threadIdx.x & 31) == 0) { ss[w] = s; sc[w] = cc; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double a = ss[0], b = sc[0];
+    for (int q = 1; q < kTotThreads / 32; ++q) {
+      double t, e;
+      two_sum(a, ss[q], t, e);
+      a = t;
+      b += sc[q] + e;
+    }
+    out[fi] = a + b;
+  }
+}
+
+struct EosArgs {
+  double ginf, eps, sigma0, E;
+  int eos;
+};
+
+// Gamma = f/delta_phi where delta_phi >= 1e-3/eps, else 0; sigma in double.
+template <typename P>
+__global__ void k_eos(size_t n, EosArgs q, const double* __restrict__ f,
+                      const P* __restrict__ phi, double* __restrict__ sigma) {
+  for (size_t c = blockIdx.x * (size_t)blockDim.x + threadIdx.x; c < n;
+       c += (size_t)gridDim.x * blockDim.x) {
+    double p = (double)phi[c];
+    double del = p * (1.0 - p) / q.eps;
+    double G = del >= 1e-3 / q.eps ? f[c] / del : 0.0;
+    double x = G / q.ginf;
+    double s;
+    if (q.eos == SFX_EOS_LANGMUIR) {
+      x = fmin(x, 1.0 - 1e-12);          // stay below saturation
+      s = q.sigma0 * (1.0 + q.E * log1p(-x));
+    } else if (q.eos == SFX_EOS_LINEAR) {
+      s = q.sigma0 * (1.0 - q.E * x);
+    } else {
+      s = q.sigma0 * (1.0 - tanh(q.E * x));
+    }
+    sigma[c] = s;
+  }
+}
+
+// ------------------------------------------------------------- PLIC area
+// Fraction of the unit cube below the plane m.x = a (m >= 0, sum m = 1;
+// Scardovelli & Zaleski 2000) and its slope dV/da.  The cubic is expanded
+// per region so that near-zero components cost no precision; V(a) =
+// 1 - V(1 - a) folds a into [0, 1/2].  `q` holds the components in
+// ascending order (q[0] = 0 in 2D).
+struct VolSlope {
+  double v, dv;
+};
+
+__device__ VolSlope plic_lower_half(const double* q, bool three_d, double a) {
+  VolSlope r{0.0, 0.0};
+  if (a <= 0.0) return r;
+  if (!three_d) {
+    const double lo = q[1], hi = q[2];
+    if (a < lo) {
+      r.v = 0.5 * a * a / (lo * hi);
+      r.dv = a / (lo * hi);
+    } else {
+      r.v = (a - 0.5 * lo) / hi;
+      r.dv = 1.0 / hi;
+    }
+    return r;
+  }
+  const double p = q[0], s = q[1], t = q[2];
+  const double inv_st = 1.0 / (s * t);
+  if (a < p) {
+    r.v = a * a * a * inv_st / (6.0 * p);
+    r.dv = 0.5 * a * a * inv_st / p;
+  } else if (a < s) {
+    r.v = 0.5 * (a * (a - p) + p * p / 3.0) * inv_st;
+    r.dv = (a - 0.5 * p) * inv_st;
+  } else if (t >= p + s) {
+    if (a < p + s) {
+      double u = a - s;
+      r.v = (a * a - a * p + p * p / 3.0) * 0.5 * inv_st - u * u * u * inv_st / (6.0 * p);
+      r.dv = (a - 0.5 * p) * inv_st - 0.5 * u * u * inv_st / p;
+    } else {
+      r.v = (a - 0.5 * (p + s)) / t;
+      r.dv = 1.0 / t;
+    }
+  } else {
+    double u = a - s, w = fmax(a - t, 0.0);
+    r.v = (a * a - a * p + p * p / 3.0) * 0.5 * inv_st - (u * u * u + w * w * w) * inv_st / (6.0 * p);
+    r.dv = (a - 0.5 * p) * inv_st - 0.5 * (u * u + w * w) * inv_st / p;
+  }
+  return r;
+}
+
+__device__ VolSlope plic_volume(const double* q, bool three_d, double a) {
+  if (a <= 0.0) return VolSlope{0.0, 0.0};
+  if (a >= 1.0) return VolSlope{1.0, 0.0};
+  if (a <= 0.5) return plic_lower_half(q, three_d, a);
+  VolSlope r = plic_lower_half(q, three_d, 1.0 - a);
+  r.v = 1.0 - r.v;
+  return r;
+}
+
+// Interface area inside the unit cell holding fraction C with normal m.
+__device__ double plic_unit_area(int nd, const double* mraw, double C) {
+  if (!(C > 0.0 && C < 1.0)) return 0.0;
+  double s = 0.0, q2 = 0.0;
+  for (int d = 0; d < nd; ++d) { s += fabs(mraw[d]); q2 += mraw[d] * mraw[d]; }
+  if (s == 0.0) return 0.0;
+  double q[3] = {0.0, fabs(mraw[0]) / s, fabs(mraw[1]) / s};
+  if (nd == 3) q[0] = fabs(mraw[2]) / s;
+  // ascending order
+  if (q[0] > q[1]) { double t = q[0]; q[0] = q[1]; q[1] = t; }
+  if (q[1] > q[2]) { double t = q[1]; q[1] = q[2]; q[2] = t; }
+  if (q[0] > q[1]) { double t = q[0]; q[0] = q[1]; q[1] = t; }
+  const bool three_d = nd == 3;
+  double lo = 0.0, hi = 1.0;
+  for (int it = 0; it < 64; ++it) {
+    double mid = 0.5 * (lo + hi);
+    if (plic_volume(q, three_d, mid).v < C) lo = mid;
+    else hi = mid;
+  }
+  return (sqrt(q2) / s) * plic_volume(q, three_d, 0.5 * (lo + hi)).dv;
+}
+
+template <typename P>
+__global__ void k_force(Level L, const P* __restrict__ phi, const double* __restrict__ C,
+                        const double* __restrict__ sigma, int dm_mode,
+                        double* __restrict__ force) {
+  const size_t n = L.ncell();
+  const int nd = L.ndim();
+  const double inv2h = 0.5 / L.h;
+  for (size_t c = blockIdx.x * (size_t)blockDim.x + threadIdx.x; c < n;
+       c += (size_t)gridDim.x * blockDim.x) {
+    int idx[3] = {(int)(c % L.nx), (int)((c / L.nx) % L.ny), (int)(c / ((size_t)L.nx * L.ny))};
+    double gs[3] = {0, 0, 0}, nn[3] = {0, 0, 0}, ndg = 0.0;
+    for (int d = 0; d < nd; ++d) {
+      int pp[3] = {idx[0], idx[1], idx[2]}, pm[3] = {idx[0], idx[1], idx[2]};
+      pp[d] = min(pp[d] + 1, L.extent(d) - 1);
+      pm[d] = max(pm[d] - 1, 0);
+      gs[d] = (sigma[cidx(L, pp[0], pp[1], pp[2])] - sigma[cidx(L, pm[0], pm[1], pm[2])]) * inv2h;
+      nn[d] = normal_comp(L, phi, idx[0], idx[1], idx[2], d);
+      ndg += nn[d] * gs[d];
+    }
+    double dm;
+    if (dm_mode == 0) {
+      double q = 0.0;
+      for (int d = 0; d < nd; ++d) {
+        int pp[3] = {idx[0], idx[1], idx[2]}, pm[3] = {idx[0], idx[1], idx[2]};
+        pp[d] = min(pp[d] + 1, L.extent(d) - 1);
+        pm[d] = max(pm[d] - 1, 0);
+        double g = (C[cidx(L, pp[0], pp[1], pp[2])] - C[cidx(L, pm[0], pm[1], pm[2])]) * inv2h;
+        q += g * g;
+      }
+      dm = sqrt(q);
+    } else {
+      double Cc = C[c];
+      if (Cc > 0.0 && Cc < 1.0) {
+        // Youngs normal: minus the (1,2,1)-weighted gradient of C
+        double m[3] = {0, 0, 0};
+        int kr = nd == 3 ? 1 : 0;
+        for (int dk = -kr; dk <= kr; ++dk)
+          for (int dj = -1; dj <= 1; ++dj)
+            for (int di = -1; di <= 1; ++di) {
+              int a = min(max(idx[0] + di, 0), L.nx - 1);
+              int b = min(max(idx[1] + dj, 0), L.ny - 1);
+              int e = min(max(idx[2] + dk, 0), L.nz - 1);
+              double w = (di == 0 ? 2.0 : 1.0) * (dj == 0 ? 2.0 : 1.0) *
+                         (nd == 3 ? (dk == 0 ? 2.0 : 1.0) : 1.0);
+              double v = C[cidx(L, a, b, e)];
+              m[0] -= w * di * v;
+              m[1] -= w * dj * v;
+              m[2] -= w * dk * v;
+            }
+        dm = plic_unit_area(nd, m, Cc) / L.h;
+      } else {
+        dm = 0.0;
+      }
+    }
+    for (int d = 0; d < nd; ++d) force[(size_t)d * n + c] = dm * (gs[d] - nn[d] * ndg);
+  }
+}
+
+}  // namespace
+
+sfx_status totals(sfx_ctx* c, const double* const* fields, int nf, double* out, cudaStream_t s) {
+  const Level& L = c->lev[0].lv;
+  const int nblk = c->n_partial_blocks;
+  for (int i = 0; i < nf; ++i)
+    k_total_partials<<<nblk, kTotThreads, 0, s>>>(L, fields[i], i, c->partials);
+  k_total_final<<<nf, kTotThreads, 0, s>>>(c->partials, nblk, c->d_sums);
+  SFX_LAUNCH_CHECK();
+  SFX_CUDA(cudaMemcpyAsync(c->h_sums, c->d_sums, nf * sizeof(double), cudaMemcpyDeviceToHost, s));
+  SFX_CUDA(cudaStreamSynchronize(s));
+  memcpy(out, c->h_sums, nf * sizeof(double));
+  return SFX_OK;
+}
+
+sfx_status marangoni(sfx_ctx* c, const sfx_params* p, const double* f, const void* phi,
+                     const double* C, int dm_mode, double* sigma, double* force,
+                     cudaStream_t s) {
+  const Level& L = c->lev[0].lv;
+  const size_t n = L.ncell();
+  EosArgs q{p->gamma_inf, p->eps, p->sigma0, p->E, p->eos};
+  const int nb = blocks_for(n, 256);
+  if (c->prec == SFX_F64) {
+    k_eos<double><<<nb, 256, 0, s>>>(n, q, f, (const double*)phi, sigma);
+    k_force<double><<<nb, 256, 0, s>>>(L, (const double*)phi, C, sigma, dm_mode, force);
+  } else {
+    k_eos<float><<<nb, 256, 0, s>>>(n, q, f, (const float*)phi, sigma);
+    k_force<float><<<nb, 256, 0, s>>>(L, (const float*)phi, C, sigma, dm_mode, force);
+  }
+  SFX_LAUNCH_CHECK();
+  return SFX_OK;
+}
+
+}  // namespace sfx

@@ -1,0 +1,90 @@
+// Private host-side declarations of libsfx: the context and the launchers
+// each translation unit provides.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <string>
+#include <vector>
+
+#include "sfx.h"
+#include "sfx_common.cuh"
+
+namespace sfx {
+
+// Device arrays of one multigrid level.  Level 0 (the fine grid) works on
+// the caller's field; its coefficient arrays live here too.
+struct LevelData {
+  Level lv;
+  double* a = nullptr;      // correction (coarse levels only)
+  double* b = nullptr;      // right-hand side
+  double* lam = nullptr;    // lambda (cell)
+  double* B[2][3] = {};     // drift faces for the f (0) and F (1) problems
+  double* Bg[3] = {};       // drift faces of a generic sfx_mg_solve call
+};
+
+struct sfx_ctx_impl;
+
+}  // namespace sfx
+
+struct sfx_ctx {
+  sfx_grid grid;
+  int prec = SFX_F64;
+  std::vector<sfx::LevelData> lev;   // lev[0] = fine
+  // fine-level scratch
+  double* fstar = nullptr;
+  double* Fstar = nullptr;
+  double* chi0 = nullptr;
+  double* chi_tmp = nullptr;
+  double* sigma_tmp = nullptr;
+  // reductions
+  double* partials = nullptr;        // block partial sums (s, c) pairs
+  int n_partial_blocks = 0;
+  unsigned long long* d_norms = nullptr;  // 8 slots (device)
+  unsigned long long* h_norms = nullptr;  // pinned mirror
+  double* d_sums = nullptr;          // compensated totals (device)
+  double* h_sums = nullptr;          // pinned mirror
+  int* d_flag = nullptr;
+  std::vector<void*> allocations;
+};
+
+namespace sfx {
+
+// cuda error bookkeeping (sfx_api.cu)
+sfx_status cuda_fail(cudaError_t e);
+#define SFX_CUDA(call)                                   \
+  do {                                                   \
+    cudaError_t e_ = (call);                             \
+    if (e_ != cudaSuccess) return ::sfx::cuda_fail(e_);  \
+  } while (0)
+#define SFX_LAUNCH_CHECK() SFX_CUDA(cudaGetLastError())
+
+// sfx_phase.cu
+sfx_status phase_field_build(sfx_ctx* c, const double* C, double* chi, void* phi, void* delta,
+                             int iters, double dtau, double eps, cudaStream_t s);
+// sfx_advect.cu
+sfx_status advect(sfx_ctx* c, const void* ux, const void* uy, const void* uz, double dt,
+                  const double* xi, double bc_in, double* out, cudaStream_t s);
+sfx_status cfl_umax(sfx_ctx* c, const void* ux, const void* uy, const void* uz, double* umax,
+                    cudaStream_t s);
+// sfx_solver.cu
+sfx_status mg_solve(sfx_ctx* c, double D, const double* Bx, const double* By, const double* Bz,
+                    int literal, const double* lam, const double* b, double* a,
+                    const sfx_solve_opts* o, int* cycles, double* res, cudaStream_t s);
+sfx_status surfactant_step(sfx_ctx* c, const sfx_params* p, const void* phi, const void* ux,
+                           const void* uy, const void* uz, double* f, double* F, double dt,
+                           const sfx_solve_opts* o, sfx_step_stats* st, cudaStream_t s);
+// sfx_forces.cu
+sfx_status totals(sfx_ctx* c, const double* const* fields, int n, double* out, cudaStream_t s);
+sfx_status marangoni(sfx_ctx* c, const sfx_params* p, const double* f, const void* phi,
+                     const double* C, int dm_mode, double* sigma, double* force,
+                     cudaStream_t s);
+
+inline int blocks_for(size_t n, int threads) {
+  size_t b = (n + threads - 1) / threads;
+  if (b > 152 * 64) b = 152 * 64;
+  if (b < 1) b = 1;
+  return (int)b;
+}
+
+}  // namespace sfx

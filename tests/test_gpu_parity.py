@@ -1,0 +1,315 @@
+"""GPU (libsfx, C-ABI) against the FP64 CPU oracle on the same seeded
+inputs.  FP64 contexts must agree to 1e-12 normwise relative
+(||x_gpu - x_oracle||_inf / ||x_oracle||_inf) when both sides converge to
+tol = 1e-13; FP32 contexts to 1e-5 with totals conserved to 1e-10."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import workloads as W
+from gpu_util import dev, host, rel_err
+
+pytestmark = pytest.mark.gpu
+
+PARITY = 1e-12
+TOL = 1e-13
+
+
+@pytest.fixture(scope="module")
+def sfx():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    import paper_2605_27534_gb300 as m
+    m.lib()
+    return m
+
+
+def _ctx(sfx, g, prec=0):
+    return sfx.Context.for_grid(g, prec)
+
+
+def _planar_circle(nx, ny, R=0.25):
+    h = 1.0 / max(nx, ny)
+    g = W.Grid(W.PLANAR, nx, ny, 1, h)
+    return g, W.circle_vof(nx, ny, h, 0.5 * nx * h, 0.5 * ny * h, R * min(nx, ny) * h)
+
+
+def _axi_sphere(nr, nz, R=0.2):
+    h = 1.0 / nr
+    g = W.Grid(W.AXI, nr, nz, 1, h)
+    return g, W.ring_vof(nr, nz, h, 0.5 * nz * h, R)
+
+
+def _sphere(nx, ny, nz, R=0.3):
+    h = 1.0 / max(nx, ny, nz)
+    g = W.Grid(W.CART3D, nx, ny, nz, h)
+    assert nx == ny == nz or True
+    Cf = np.zeros((nz, ny, nx))
+    n = max(nx, ny, nz)
+    full = W.sphere_vof(n, h, (0.5, 0.5, 0.5), R)
+    Cf[:] = full[:nz, :ny, :nx]
+    return g, Cf
+
+
+GEOMS = {
+    "planar": lambda: _planar_circle(70, 52),
+    "axi": lambda: _axi_sphere(40, 80),
+    "3d": lambda: _sphere(24, 20, 28, 0.3),
+}
+
+
+@pytest.mark.parametrize("geom", list(GEOMS))
+def test_phase_field_build_parity(sfx, geom):
+    import torch
+    g, Cf = GEOMS[geom]()
+    eps, dtau = 0.75 * g.h, (g.h / 3 if g.geom == W.CART3D else 0.5 * g.h)
+    chi_o, phi_o, del_o = oracle.phase_field_build(g, Cf, 24, dtau, eps)
+    ctx = _ctx(sfx, g)
+    Cd = dev(Cf)
+    chi = torch.empty_like(Cd)
+    phi = torch.empty_like(Cd)
+    dl = torch.empty_like(Cd)
+    ctx.sfx_phase_field_build(Cd, chi, phi, dl, iters=24, dtau=dtau, eps=eps)
+    assert rel_err(host(chi), chi_o) < PARITY
+    assert rel_err(host(phi), phi_o) < PARITY
+    assert rel_err(host(dl), del_o) < PARITY
+    # FP32 carrier: phi stored in float
+    ctx32 = _ctx(sfx, g, 1)
+    phi32 = torch.empty(Cd.shape, dtype=torch.float32, device="cuda")
+    ctx32.sfx_phase_field_build(Cd, chi, phi32, None, iters=24, dtau=dtau, eps=eps)
+    assert rel_err(host(phi32), phi_o) < 1e-6
+
+
+def _random_problem(g, seed, scale=2.0):
+    rng = np.random.default_rng(seed)
+    nz, ny, nx = g.shape
+    Bx = np.zeros((nz, ny, nx + 1))
+    By = np.zeros((nz, ny + 1, nx))
+    Bz = np.zeros((nz + 1, ny, nx)) if g.ndim == 3 else None
+    Bx[..., 1:-1] = rng.uniform(-scale, scale, Bx[..., 1:-1].shape)
+    By[:, 1:-1, :] = rng.uniform(-scale, scale, By[:, 1:-1, :].shape)
+    if Bz is not None:
+        Bz[1:-1] = rng.uniform(-scale, scale, Bz[1:-1].shape)
+    lam = rng.uniform(50.0, 100.0, g.shape)
+    b = rng.uniform(-1.0, 1.0, g.shape)
+    return Bx, By, Bz, lam, b
+
+
+@pytest.mark.parametrize("shape,geom", [((1, 48, 64), W.PLANAR), ((1, 64, 32), W.AXI),
+                                        ((24, 16, 16), W.CART3D), ((1, 29, 37), W.PLANAR),
+                                        ((1, 1, 1), W.PLANAR), ((2, 2, 2), W.CART3D)])
+def test_mg_solve_parity(sfx, shape, geom):
+    import torch
+    nz, ny, nx = shape
+    g = W.Grid(geom, nx, ny, nz, 1.0 / max(shape))
+    D = 0.05
+    Bx, By, Bz, lam, b = _random_problem(g, 3)
+    a_o, s, _ = oracle.elliptic_solve(g, D, Bx, By, Bz, lam, b, tol=1e-15)
+    assert s > 0
+    ctx = _ctx(sfx, g)
+    a = torch.zeros(shape, dtype=torch.float64, device="cuda")
+    opts = sfx.default_opts(tol=TOL, max_cycles=100)
+    cyc, res, ok = ctx.sfx_mg_solve(D, dev(Bx), dev(By), None if Bz is None else dev(Bz),
+                                    dev(lam), dev(b), a, opts)
+    assert ok and res <= TOL
+    assert rel_err(host(a), a_o) < PARITY
+
+
+@pytest.mark.parametrize("case", ["vortex", "hr3d", "hraxi", "uniform3d"])
+def test_advection_parity(sfx, case):
+    import torch
+    rng = np.random.default_rng(1)
+    if case == "vortex":
+        n = 48
+        g = W.Grid(W.PLANAR, n, n, 1, 1.0 / n)
+        ux, uy = W.single_vortex_faces(n, g.h, 0.3, 4.0)
+        uz, dt = None, 0.4 * g.h
+        xi = W.circle_vof(n, n, g.h, 0.5, 0.75, 0.15)
+    elif case == "hr3d":
+        n = 20
+        g = W.Grid(W.CART3D, n, n, n, 1.0 / n)
+        ux, uy, uz = W.hr_faces_3d(n, g.h, (0.5, 0.5, 0.5), 0.2)
+        dt = 0.3 * g.h
+        xi = rng.uniform(0, 1, g.shape)
+    elif case == "hraxi":
+        g = W.Grid(W.AXI, 24, 48, 1, 1.0 / 24)
+        ux, uy = W.hr_faces_axi(24, 48, g.h, 1.0, 0.2)
+        uz, dt = None, 0.3 * g.h
+        xi = rng.uniform(0, 1, g.shape)
+    else:
+        g = W.Grid(W.CART3D, 12, 10, 14, 0.1)
+        ux, uy, uz = W.uniform_faces(g, (0.3, -0.2, 0.45))
+        dt = 0.1
+        xi = rng.uniform(0, 1, g.shape)
+    ref = oracle.advect_bcg(g, ux, uy, uz, dt, xi, 0.4)
+    ctx = _ctx(sfx, g)
+    out = torch.empty(g.shape, dtype=torch.float64, device="cuda")
+    ctx.sfx_advect(dev(ux), dev(uy), None if uz is None else dev(uz), dt, dev(xi), 0.4, out)
+    assert rel_err(host(out), ref) < 1e-14
+
+
+def _step_case(name):
+    if name == "adsorption2d":
+        c = W.case_adsorption_2d(n=48, steps=5, tol=TOL)
+        return c, None, None, None
+    if name == "vortex2d":
+        c = W.case_vortex_2d(n=48, soluble=True)
+        c.steps = 3
+        return c, c.ux, c.uy, None
+    if name == "hr3d":
+        c = W.case_hr_3d(n=24, steps=2)
+        return c, c.ux, c.uy, c.uz
+    if name == "axi":
+        c = W.case_axi(32, 64, Bi=1.0, Da=10.0, steps=3)
+        return c, c.ux, c.uy, None
+    raise KeyError(name)
+
+
+@pytest.mark.parametrize("name", ["adsorption2d", "vortex2d", "hr3d", "axi"])
+def test_surfactant_step_parity_fp64(sfx, name):
+    import torch
+    c, ux, uy, uz = _step_case(name)
+    g, p = c.grid, c.params
+    _, phi, delta = oracle.phase_field_build(g, c.C, c.redist_iters, c.dtau, p.eps)
+    f0 = c.gamma0 * delta if c.gamma0 is not None else np.zeros(g.shape)
+    f_o, F_o = f0.copy(), c.F0.copy()
+    for _ in range(c.steps):
+        f_o, F_o, st = oracle.surfactant_step(g, p, phi, f_o, F_o, c.dt, TOL / 10, ux, uy, uz)
+        assert st.converged
+    ctx = _ctx(sfx, g)
+    f, F = dev(f0), dev(c.F0)
+    phid = dev(phi)
+    u = [None if v is None else dev(v) for v in (ux, uy, uz)]
+    opts = sfx.default_opts(tol=TOL, max_cycles=200)
+    M0 = sum(ctx.sfx_totals([f, F]))
+    for _ in range(c.steps):
+        stt = ctx.sfx_surfactant_step(p, phid, f, F, c.dt, *u, opts=opts)
+        assert stt.converged and stt.res_f <= TOL and stt.res_F <= TOL
+    scale = max(np.abs(F_o).max(), np.abs(f_o).max())
+    assert np.abs(host(F) - F_o).max() / scale < PARITY
+    assert np.abs(host(f) - f_o).max() / scale < PARITY
+    if ux is None:   # closed box: total surfactant is invariant
+        M1 = stt.mass_f + stt.mass_F
+        assert abs(M1 - M0) < 1e-12 * abs(M0)
+
+
+def test_surfactant_step_fp32_context(sfx):
+    """float carrier and velocities, double state: within the FP32 target."""
+    import torch
+    c, ux, uy, uz = _step_case("adsorption2d")
+    g, p = c.grid, c.params
+    _, phi, delta = oracle.phase_field_build(g, c.C, c.redist_iters, c.dtau, p.eps)
+    f_o, F_o = np.zeros(g.shape), c.F0.copy()
+    for _ in range(c.steps):
+        f_o, F_o, st = oracle.surfactant_step(g, p, phi, f_o, F_o, c.dt, 1e-14)
+    ctx = _ctx(sfx, g, 1)
+    f, F = dev(np.zeros(g.shape)), dev(c.F0)
+    phid = dev(phi, torch.float32)
+    opts = sfx.default_opts(tol=1e-12)
+    M0 = sum(ctx.sfx_totals([f, F]))
+    for _ in range(c.steps):
+        stt = ctx.sfx_surfactant_step(p, phid, f, F, c.dt, opts=opts)
+        assert stt.converged
+    assert rel_err(host(F), F_o) < 1e-5
+    assert rel_err(host(f), f_o) < 1e-5
+    assert abs(stt.mass_f + stt.mass_F - M0) < 1e-10 * abs(M0)
+
+
+def test_totals_match_exact_sum(sfx):
+    rng = np.random.default_rng(8)
+    g = W.Grid(W.AXI, 333, 77, 1, 0.003)
+    x = rng.standard_normal(g.shape) * 10.0 ** rng.uniform(-6, 6, g.shape)
+    y = rng.uniform(0, 1, g.shape)
+    ctx = _ctx(sfx, g)
+    got = ctx.sfx_totals([dev(x), dev(y)])
+    V = oracle.cell_volumes(g)
+    for val, arr in zip(got, (x, y)):
+        exact = math.fsum((V * arr).ravel())
+        assert abs(val - exact) <= 4e-16 * np.abs(V * arr).sum()
+    # deterministic: same bits on a second call
+    assert ctx.sfx_totals([dev(x), dev(y)]) == got
+
+
+@pytest.mark.parametrize("geom", list(GEOMS))
+@pytest.mark.parametrize("dm_mode", [0, 1])
+def test_marangoni_parity(sfx, geom, dm_mode):
+    import torch
+    g, Cf = GEOMS[geom]()
+    p = W.Params(eps=0.75 * g.h, sigma0=1.0, E=0.3, gamma_inf=1.0)
+    _, phi, delta = oracle.phase_field_build(g, Cf, 24, 0.5 * g.h, p.eps)
+    rng = np.random.default_rng(4)
+    Gam = rng.uniform(0.1, 0.9, g.shape)
+    f = Gam * delta
+    ctx = _ctx(sfx, g)
+    for eos in (W.EOS_LANGMUIR, W.EOS_LINEAR, W.EOS_TANH):
+        p.eos = eos
+        sig_o, force_o = oracle.marangoni(g, p, f, phi, Cf, dm_mode)
+        sig = torch.empty(g.shape, dtype=torch.float64, device="cuda")
+        force = torch.empty((g.ndim,) + g.shape, dtype=torch.float64, device="cuda")
+        ctx.sfx_marangoni_force(p, dev(f), dev(phi), dev(Cf), sig, force, dm_mode)
+        assert rel_err(host(sig), sig_o) < PARITY
+        assert rel_err(host(force), force_o) < 1e-11
+
+
+def test_cfl_dt_matches_oracle(sfx):
+    c = W.case_hr_3d(n=16, steps=1)
+    ctx = _ctx(sfx, c.grid)
+    dt = ctx.sfx_cfl_dt(dev(c.ux), dev(c.uy), dev(c.uz), 0.025, c.params.eps, 0.5)
+    umax = max(np.abs(c.ux).max(), np.abs(c.uy).max(), np.abs(c.uz).max())
+    assert dt == pytest.approx(oracle.cfl_dt(3, c.grid.h, umax, 0.025, c.params.eps, 0.5),
+                               rel=1e-15)
+
+
+# ----------------------------------------------------------------- edges
+def test_degenerate_single_cell_reduces_to_kinetics(sfx):
+    """One cell: no faces, so App. C reduces to the pointwise kinetic system."""
+    g = W.Grid(W.PLANAR, 1, 1, 1, 0.1)
+    p = W.Params(ka=2.0, kd=0.5, gamma_inf=1.0, Df=0.1, DF=0.1, eps=0.075)
+    phi = np.full(g.shape, 0.4)
+    f0, F0 = np.full(g.shape, 0.3), np.full(g.shape, 0.8)
+    f_o, F_o, _ = oracle.surfactant_step(g, p, phi, f0, F0, 0.01, 1e-15)
+    ctx = _ctx(sfx, g)
+    f, F = dev(f0), dev(F0)
+    ctx.sfx_surfactant_step(p, dev(phi), f, F, 0.01, opts=sfx.default_opts(tol=1e-14))
+    assert rel_err(host(f), f_o) < 1e-13 and rel_err(host(F), F_o) < 1e-13
+
+
+def test_nonfinite_input_is_reported(sfx):
+    c, *_ = _step_case("adsorption2d")
+    g, p = c.grid, c.params
+    _, phi, _ = oracle.phase_field_build(g, c.C, 12, c.dtau, p.eps)
+    F0 = c.F0.copy()
+    F0[0, 10, 10] = np.nan
+    ctx = _ctx(sfx, g)
+    with pytest.raises(sfx.SfxError, match="non-finite"):
+        ctx.sfx_surfactant_step(p, dev(phi), dev(np.zeros(g.shape)), dev(F0), c.dt)
+
+
+def test_not_converged_is_reported_with_stats(sfx):
+    c, *_ = _step_case("adsorption2d")
+    g, p = c.grid, c.params
+    _, phi, _ = oracle.phase_field_build(g, c.C, 12, c.dtau, p.eps)
+    ctx = _ctx(sfx, g)
+    st = ctx.sfx_surfactant_step(p, dev(phi), dev(np.zeros(g.shape)), dev(c.F0), c.dt,
+                                 opts=sfx.default_opts(tol=1e-15, max_cycles=1),
+                                 allow_not_converged=True)
+    assert st.converged == 0 and st.picard == 1 and st.res_f > 1e-15
+
+
+def test_invalid_arguments_rejected(sfx):
+    import torch
+    g = W.Grid(W.PLANAR, 8, 8, 1, 0.1)
+    ctx = _ctx(sfx, g)
+    f = torch.zeros(g.shape, dtype=torch.float64, device="cuda")
+    p = W.Params(eps=0.075)
+    with pytest.raises(sfx.SfxError, match="invalid argument"):
+        ctx.sfx_surfactant_step(p, f, f, f, 0.1)          # f aliases F
+    with pytest.raises(sfx.SfxError, match="invalid argument"):
+        ctx.sfx_surfactant_step(p, f, f.clone(), f.clone(), -1.0)
+    bad = W.Params(eps=0.0)
+    with pytest.raises(sfx.SfxError, match="invalid argument"):
+        ctx.sfx_surfactant_step(bad, f, f.clone(), f.clone(), 0.1)
+    with pytest.raises(sfx.SfxError, match="invalid argument"):
+        sfx.Context(W.PLANAR, 8, 8, 2, 0.1)               # nz > 1 in 2D

@@ -146,3 +146,16 @@ def test_marangoni_force_is_tangential_and_matches_surface_gradient():
         num = (ft * np.sin(th) * g.h ** 2).sum()
         errs.append(abs(num - 0.2 * p.E * math.pi) / (0.2 * p.E * math.pi))
     assert errs[-1] < 0.05 and errs[-1] <= errs[0] + 1e-3, errs
+
+
+def test_plic_area_keeps_precision_for_tiny_normal_components():
+    """A vanishing component reduces the cube to the square: the area must
+    approach the 2D value smoothly, without the cancellation of the raw
+    cubic (which loses about eps/m of relative precision)."""
+    for C in (0.02, 0.3, 0.5, 0.77, 0.99):
+        a2 = oracle.plic_area(2, [0.3, 0.7], C)
+        for tiny in (1e-6, 1e-9, 1e-13, 0.0):
+            a3 = oracle.plic_area(3, [tiny, 0.3, 0.7], C)
+            assert abs(a3 - a2) < 5 * tiny + 1e-13, (C, tiny, a3, a2)
+        a1 = oracle.plic_area(2, [1e-12, 1.0], C)
+        assert abs(a1 - 1.0) < 1e-11
