@@ -1,0 +1,343 @@
+#!/usr/bin/env python
+"""Throughput of the coupled surfactant step (cell-updates/s) on GB300.
+
+Default workload: 3D bubble-like transport, 256^3 unit cube, sphere R = 0.125,
+prescribed Hadamard-Rybczynski Stokes flow (viscosity ratio 0.01, unit
+far-field velocity), F = 1 and Gamma = 0 initially, Bi = Da = 1, Langmuir EOS
+sigma0 = 1, E = 0.2, dt = 5e-5.  One step = BCG advection of f and F, the
+App. C implicit source system solved to tolerance (Picard + multigrid),
+compensated totals, EOS and Marangoni force.  The phase field is built once
+(the interface is static in this workload).
+
+Arms:
+  (default)          libsfx on cuda:LOCAL_RANK, one independent replica per
+                     rank (weak scaling); prints one JSON line on rank 0.
+  --impl reference   the FP64 CPU oracle on the host cores, each step a
+                     bounded 64^3 sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads as W  # noqa: E402
+
+METRIC = "cell-updates/s of coupled surfactant step (FP32/batched vs FP64), % HBM roofline"
+UNIT = "cell-updates/s"
+SAMPLE_N = 64          # oracle sample: centred 64^3 block of the same grid
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="sfx", choices=["sfx", "reference"])
+    ap.add_argument("--precision", default="f64", choices=["f64", "f32"])
+    ap.add_argument("--n", type=int, default=256)
+    ap.add_argument("--tol", type=float, default=1e-10)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--oracle-steps", type=int, default=3)
+    return ap.parse_args()
+
+
+# ------------------------------------------------------------------ helpers
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return json.load(fh), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+def algorithmic_bytes(kind, grid, wbytes):
+    """Unique global bytes one launch of `kind` must move on the fine grid
+    (reads + writes; every array counted once per launch).  N = cells,
+    d = dimensions; drift faces are double, phi has `wbytes` bytes.
+      smooth_fine (one colour): a (N, neighbours) + b, lambda (N/2 each)
+        + d face arrays + write a (N/2)            = 8 (2.5 + d) N
+    """
+    N = grid.ncell
+    d = grid.ndim
+    if kind == "smooth_fine":
+        return 8.0 * (2.5 + d) * N
+    if kind == "advect":
+        return 8.0 * 2 * N + wbytes * d * N
+    return None
+
+
+class ClockSampler:
+    """nvidia-smi samples during the timed region (clocks, throttle reasons)."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join("/tmp", "sfx_clocks_%d.csv" % os.getpid())
+
+    def start(self):
+        try:
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.fh, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.fh.close()
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as fh:
+            for line in fh:
+                p = [x.strip() for x in line.split(",")]
+                if len(p) < 9:
+                    continue
+                try:
+                    sm.append(float(p[1]))
+                    mx = max(mx, float(p[2]))
+                except ValueError:
+                    continue
+                for nm, v in zip(names, p[5:9]):
+                    if v.lower() in ("active", "0x1", "1"):
+                        reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def sample_block(case, n_s=SAMPLE_N):
+    """Centred n_s^3 block of a 3D case: same cells, h, dt and flow."""
+    n = case.grid.nx
+    a = (n - n_s) // 2
+    s = slice(a, a + n_s)
+    s1 = slice(a, a + n_s + 1)
+    g = W.Grid(W.CART3D, n_s, n_s, n_s, case.grid.h)
+    return (g, np.ascontiguousarray(case.C[s, s, s]),
+            np.ascontiguousarray(case.ux[s, s, s1]), np.ascontiguousarray(case.uy[s, s1, s]),
+            np.ascontiguousarray(case.uz[s1, s, s]))
+
+
+def oracle_rate(case, steps, tol):
+    """The FP64 CPU oracle, as it stands, on a bounded sample (single thread)."""
+    import oracle
+    g, Cs, ux, uy, uz = sample_block(case)
+    p = case.params
+    _, phi, _ = oracle.phase_field_build(g, Cs, case.redist_iters, case.dtau, p.eps)
+    f, F = np.zeros(g.shape), np.ones(g.shape)
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        f, F, st = oracle.surfactant_step(g, p, phi, f, F, case.dt, tol, ux, uy, uz)
+        oracle.marangoni(g, p, f, phi, Cs, 1)
+    dt = time.perf_counter() - t0
+    return g.ncell * steps / dt, dt, g
+
+
+# ------------------------------------------------------------------ arms
+def run_reference(a, case, rank):
+    if rank != 0:
+        return
+    import oracle
+    g, Cs, ux, uy, uz = sample_block(case)
+    p = case.params
+    _, phi, _ = oracle.phase_field_build(g, Cs, case.redist_iters, case.dtau, p.eps)
+    f, F = np.zeros(g.shape), np.ones(g.shape)
+    times = []
+    for s in range(a.warmup + a.steps):
+        t0 = time.perf_counter()
+        f, F, st = oracle.surfactant_step(g, p, phi, f, F, case.dt, a.tol, ux, uy, uz)
+        oracle.marangoni(g, p, f, phi, Cs, 1)
+        if s >= a.warmup:
+            times.append(time.perf_counter() - t0)
+    tot = sum(times)
+    value = g.ncell * a.steps / tot
+    sample = "centred %d^3 block of the %d^3 workload (same h, dt, flow), 1 thread" % (
+        SAMPLE_N, case.grid.nx)
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": a.gpus,
+        "steps": a.steps, "warmup": a.warmup, "ms_per_step": 1e3 * tot / a.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": case.name + " (oracle sample)", "sample": sample,
+                   "tol": a.tol},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+def run_gpu(a, case, rank, world, local_rank):
+    import torch
+    import paper_2605_27534_gb300 as sfx
+
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    g, p = case.grid, case.params
+    prec = sfx.SFX_F32 if a.precision == "f32" else sfx.SFX_F64
+    wdt = torch.float32 if prec == sfx.SFX_F32 else torch.float64
+    wbytes = 4 if prec == sfx.SFX_F32 else 8
+    ctx = sfx.Context.for_grid(g, prec)
+    Cd = torch.from_numpy(case.C).to(dev)
+    chi = torch.empty_like(Cd)
+    phi = torch.empty(g.shape, dtype=wdt, device=dev)
+    ctx.sfx_phase_field_build(Cd, chi, phi, None, iters=case.redist_iters, dtau=case.dtau,
+                              eps=p.eps)
+    ux, uy, uz = (torch.from_numpy(u).to(dev, wdt) for u in (case.ux, case.uy, case.uz))
+    f = torch.zeros(g.shape, dtype=torch.float64, device=dev)
+    F = torch.ones(g.shape, dtype=torch.float64, device=dev)
+    sigma = torch.empty_like(f)
+    force = torch.empty((3,) + g.shape, dtype=torch.float64, device=dev)
+    opts = sfx.default_opts(tol=a.tol, max_cycles=200)
+    stats = []
+
+    def step():
+        st = ctx.sfx_surfactant_step(p, phi, f, F, case.dt, ux, uy, uz, opts=opts)
+        ctx.sfx_marangoni_force(p, f, phi, Cd, sigma, force, dm_mode=1)
+        stats.append((st.picard, st.vcycles, st.res_f, st.res_F, st.mass_f, st.mass_F))
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(a.warmup):
+        step()
+    stream = torch.cuda.current_stream()
+    clk = ClockSampler(local_rank)
+    ctx.sfx_profile(True)
+    barrier()
+    clk.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(a.steps):
+        step()
+    e1.record(stream)
+    barrier()
+    clocks = clk.stop()
+    ctx.sfx_profile(False)
+    ms = e0.elapsed_time(e1)
+    prof = ctx.sfx_profile_read()
+    ms_max = ms
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_max = float(t.item())
+    cells = g.ncell * a.steps * world
+    value = cells / (ms_max * 1e-3)
+
+    # ---- end to end through the C-ABI with host buffers (pinned)
+    e2e = None
+    if not a.no_e2e:
+        fh = torch.zeros(g.shape, dtype=torch.float64).pin_memory()
+        Fh = torch.ones(g.shape, dtype=torch.float64).pin_memory()
+        barrier()
+        s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s0.record(stream)
+        for _ in range(a.steps):
+            f.copy_(fh, non_blocking=True)
+            F.copy_(Fh, non_blocking=True)
+            step()
+            fh.copy_(f, non_blocking=True)
+            Fh.copy_(F, non_blocking=True)
+        s1.record(stream)
+        barrier()
+        ms_e = s0.elapsed_time(s1)
+        if world > 1:
+            import torch.distributed as dist
+            t = torch.tensor([ms_e], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms_e = float(t.item())
+        nb = 2 * g.ncell * 8
+        e2e = {"value": cells / (ms_e * 1e-3), "unit": UNIT, "h2d_bytes_per_step": nb,
+               "d2h_bytes_per_step": nb}
+
+    if rank != 0:
+        return
+    # ---- roofline of the dominant kernel kind
+    peaks, peak_src = measured_peaks()
+    top = max(prof.items(), key=lambda kv: kv[1][1])
+    kind, (nl, tot_ms, nt) = top
+    roof = None
+    ab = algorithmic_bytes(kind, g, wbytes)
+    if ab is not None and nt > 0:
+        avg_s = tot_ms * 1e-3 / nt
+        achieved = ab / avg_s / 1e9
+        roof = {"bound": "hbm", "kernel": kind, "achieved": achieved, "peak": peaks["hbm_gbs"],
+                "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"], "traffic": None,
+                "algorithmic_bytes_per_launch": ab, "avg_launch_ms": avg_s * 1e3,
+                "peak_source": "%s (MEASURED_PEAKS.json hbm_gbs)" % peak_src}
+    launches = int(sum(v[0] for v in prof.values()))
+    breakdown = {k: {"launches": v[0], "ms": round(v[1], 3)} for k, v in prof.items() if v[0]}
+    cpu = None
+    if not a.no_cpu:
+        rate, secs, gs = oracle_rate(case, a.oracle_steps, a.tol)
+        cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": "%d step(s) on the centred %d^3 block of the %d^3 workload "
+                         "(same h, dt, flow): %.1f s" % (a.oracle_steps, SAMPLE_N, g.nx, secs)}
+    pic = [s[0] for s in stats[-a.steps:]]
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
+        "warmup": a.warmup, "ms_per_step": ms_max / a.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": a.precision, "data": "synthetic",
+        "config": {"workload": "%s: 3D %d^3 HR Stokes flow, sphere R=0.125, Bi=Da=1, "
+                               "dt=%g, tol=%g" % (case.name, g.nx, case.dt, a.tol),
+                   "cells": g.ncell, "precision": a.precision,
+                   "l2": "inputs larger than L2 (state + coefficients %.2f GB)" % (
+                       g.ncell * 8 * 20 / 1e9),
+                   "parallelism": "replicas%d" % world,
+                   "picard_per_step": statistics.mean(pic) if pic else None},
+        "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+        "clocks": clocks, "kernels": breakdown,
+    }
+    print(json.dumps(line))
+
+
+def main():
+    a = parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    case = W.case_hr_3d(n=a.n, steps=a.steps, tol=a.tol)
+    if a.impl == "reference":
+        if world > 1 and rank != 0:
+            return
+        run_reference(a, case, rank)
+        return
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local_rank)
+        dist.init_process_group("nccl")
+    run_gpu(a, case, rank, world, local_rank)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

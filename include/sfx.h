@@ -179,6 +179,32 @@ sfx_status sfx_cfl_dt(sfx_ctx* ctx, const void* ux, const void* uy,
                       const void* uz, double D, double eps, double safety,
                       double* dt_out, void* stream);
 
+/* Instrumentation (not part of the method).  Kernel kinds: */
+typedef enum {
+  SFX_K_SMOOTH_FINE = 0,  /* red-black Gauss-Seidel colour sweep, fine level */
+  SFX_K_SMOOTH_COARSE,    /* colour sweeps and the coarsest-level solve */
+  SFX_K_RESTRICT,         /* residual restriction */
+  SFX_K_PROLONG,          /* prolongation and correction */
+  SFX_K_SETUP,            /* App. C coefficients, drift faces, restrictions */
+  SFX_K_RESIDUAL,         /* residual norms (convergence checks) */
+  SFX_K_ADVECT,           /* BCG advection */
+  SFX_K_TOTALS,           /* compensated totals */
+  SFX_K_FORCES,           /* EOS and Marangoni force */
+  SFX_K_PHASE,            /* redistancing and phase field */
+  SFX_K_OTHER,
+  SFX_K_COUNT
+} sfx_kernel_kind;
+
+/* on != 0: reset the per-kind launch counters and start bracketing every
+   kernel launch of this context with CUDA events recorded on the launching
+   stream (at most 8192 launches are timed per run); on = 0: stop. */
+sfx_status sfx_profile(sfx_ctx* ctx, int on);
+/* Launches of `kind` since the last sfx_profile(ctx, 1), the summed
+   event-timed duration in ms and how many launches were timed.  Waits for
+   the recorded events.  Any output pointer may be NULL. */
+sfx_status sfx_profile_read(sfx_ctx* ctx, int kind, long long* launches,
+                            double* total_ms, long long* timed);
+
 #ifdef __cplusplus
 }
 #endif

@@ -145,6 +145,19 @@ class Context:
                                          int(dm_mode), _ptr(sigma), _ptr(force), _stream()),
                "sfx_marangoni_force")
 
+    def sfx_profile(self, on: bool):
+        _check(lib().sfx_profile(self._h, 1 if on else 0), "sfx_profile")
+
+    def sfx_profile_read(self):
+        """{kind: (launches, total_ms, timed_launches)} since sfx_profile(True)."""
+        out = {}
+        for k, name in enumerate(_lib.KERNEL_KINDS):
+            n, ms, nt = C.c_longlong(0), C.c_double(0), C.c_longlong(0)
+            _check(lib().sfx_profile_read(self._h, k, C.byref(n), C.byref(ms), C.byref(nt)),
+                   "sfx_profile_read")
+            out[name] = (n.value, ms.value, nt.value)
+        return out
+
     def sfx_cfl_dt(self, ux, uy, uz, D, eps, safety=1.0):
         out = C.c_double(0)
         _check(lib().sfx_cfl_dt(self._h, _ptr(ux), _ptr(uy), _ptr(uz), float(D), float(eps),

@@ -21,7 +21,10 @@ EXPORTS = [
     "sfx_version", "sfx_status_string", "sfx_last_cuda_error", "sfx_ctx_create",
     "sfx_ctx_destroy", "sfx_default_opts", "sfx_phase_field_build", "sfx_advect",
     "sfx_mg_solve", "sfx_surfactant_step", "sfx_totals", "sfx_marangoni_force", "sfx_cfl_dt",
+    "sfx_profile", "sfx_profile_read",
 ]
+KERNEL_KINDS = ["smooth_fine", "smooth_coarse", "restrict", "prolong", "setup", "residual",
+                "advect", "totals", "forces", "phase", "other"]
 
 
 class Grid(C.Structure):
@@ -90,5 +93,10 @@ def load(path: str = SO_PATH):
     L.sfx_marangoni_force.argtypes = [vp, C.POINTER(Params), vp, vp, vp, C.c_int, vp, vp, vp]
     L.sfx_cfl_dt.restype = C.c_int
     L.sfx_cfl_dt.argtypes = [vp, vp, vp, vp, dp, dp, dp, C.POINTER(C.c_double), vp]
+    L.sfx_profile.restype = C.c_int
+    L.sfx_profile.argtypes = [vp, C.c_int]
+    L.sfx_profile_read.restype = C.c_int
+    L.sfx_profile_read.argtypes = [vp, C.c_int, C.POINTER(C.c_longlong), C.POINTER(C.c_double),
+                                   C.POINTER(C.c_longlong)]
     _lib = L
     return L

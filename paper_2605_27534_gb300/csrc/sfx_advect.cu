@@ -110,10 +110,10 @@ sfx_status advect(sfx_ctx* c, const void* ux, const void* uy, const void* uz, do
   const int nb = blocks_for(L.ncell(), 256);
   if (c->prec == SFX_F64) {
     Vel<double> v{{(const double*)ux, (const double*)uy, (const double*)uz}};
-    k_advect<double><<<nb, 256, 0, s>>>(L, v, dt, xi, bc_in, out);
+    SFX_KERNEL(c, K_ADVECT, k_advect<double>, nb, 256, s, L, v, dt, xi, bc_in, out);
   } else {
     Vel<float> v{{(const float*)ux, (const float*)uy, (const float*)uz}};
-    k_advect<float><<<nb, 256, 0, s>>>(L, v, dt, xi, bc_in, out);
+    SFX_KERNEL(c, K_ADVECT, k_advect<float>, nb, 256, s, L, v, dt, xi, bc_in, out);
   }
   SFX_LAUNCH_CHECK();
   return SFX_OK;
@@ -127,9 +127,9 @@ sfx_status cfl_umax(sfx_ctx* c, const void* ux, const void* uy, const void* uz, 
   for (int d = 0; d < L.ndim(); ++d) {
     size_t n = L.nface(d);
     if (c->prec == SFX_F64)
-      k_umax<double><<<blocks_for(n, 256), 256, 0, s>>>(n, (const double*)u[d], c->d_norms);
+      SFX_KERNEL(c, K_OTHER, k_umax<double>, blocks_for(n, 256), 256, s, n, (const double*)u[d], c->d_norms);
     else
-      k_umax<float><<<blocks_for(n, 256), 256, 0, s>>>(n, (const float*)u[d], c->d_norms);
+      SFX_KERNEL(c, K_OTHER, k_umax<float>, blocks_for(n, 256), 256, s, n, (const float*)u[d], c->d_norms);
   }
   SFX_LAUNCH_CHECK();
   SFX_CUDA(cudaMemcpyAsync(c->h_norms, c->d_norms, sizeof(unsigned long long),

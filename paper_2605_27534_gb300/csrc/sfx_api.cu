@@ -15,6 +15,29 @@ sfx_status cuda_fail(cudaError_t e) {
   return SFX_ERR_CUDA;
 }
 
+void prof_before(sfx_ctx* c, int kind, cudaStream_t s) {
+  Prof& P = c->prof;
+  P.launches[kind]++;
+  if (!P.on || P.used >= 8192) return;
+  if (P.ev.size() < 2 * (P.used + 1)) {
+    cudaEvent_t a, b;
+    if (cudaEventCreate(&a) != cudaSuccess) return;
+    if (cudaEventCreate(&b) != cudaSuccess) { cudaEventDestroy(a); return; }
+    P.ev.push_back(a);
+    P.ev.push_back(b);
+  }
+  cudaEventRecord(P.ev[2 * P.used], s);
+}
+
+void prof_after(sfx_ctx* c, int kind, cudaStream_t s) {
+  Prof& P = c->prof;
+  if (!P.on || P.used >= 8192 || P.ev.size() < 2 * (P.used + 1)) return;
+  cudaEventRecord(P.ev[2 * P.used + 1], s);
+  if (P.kind.size() <= P.used) P.kind.push_back(kind);
+  else P.kind[P.used] = kind;
+  P.used++;
+}
+
 namespace {
 
 template <typename T>
@@ -121,6 +144,7 @@ void sfx_default_opts(sfx_solve_opts* o) {
 
 void sfx_ctx_destroy(sfx_ctx* c) {
   if (!c) return;
+  for (cudaEvent_t e : c->prof.ev) cudaEventDestroy(e);
   for (void* p : c->allocations) cudaFree(p);
   if (c->h_norms) cudaFreeHost(c->h_norms);
   if (c->h_sums) cudaFreeHost(c->h_sums);
@@ -229,6 +253,36 @@ sfx_status sfx_cfl_dt(sfx_ctx* c, const void* ux, const void* uy, const void* uz
   double dconv = h / (umax + D / eps);
   double ddiff = h * h / (2.0 * nd * D);
   *dt_out = safety * (dconv < ddiff ? dconv : ddiff);
+  return SFX_OK;
+}
+
+sfx_status sfx_profile(sfx_ctx* c, int on) {
+  if (!c) return SFX_ERR_ARG;
+  if (on) {
+    for (int k = 0; k < K_COUNT; ++k) c->prof.launches[k] = 0;
+    c->prof.used = 0;
+  }
+  c->prof.on = on != 0;
+  return SFX_OK;
+}
+
+sfx_status sfx_profile_read(sfx_ctx* c, int kind, long long* launches, double* total_ms,
+                            long long* timed) {
+  if (!c || kind < 0 || kind >= K_COUNT) return SFX_ERR_ARG;
+  Prof& P = c->prof;
+  if (launches) *launches = P.launches[kind];
+  double ms = 0.0;
+  long long nt = 0;
+  for (size_t q = 0; q < P.used; ++q) {
+    if (P.kind[q] != kind) continue;
+    SFX_CUDA(cudaEventSynchronize(P.ev[2 * q + 1]));
+    float e = 0.f;
+    SFX_CUDA(cudaEventElapsedTime(&e, P.ev[2 * q], P.ev[2 * q + 1]));
+    ms += e;
+    ++nt;
+  }
+  if (total_ms) *total_ms = ms;
+  if (timed) *timed = nt;
   return SFX_OK;
 }
 

@@ -243,8 +243,8 @@ sfx_status totals(sfx_ctx* c, const double* const* fields, int nf, double* out, 
   const Level& L = c->lev[0].lv;
   const int nblk = c->n_partial_blocks;
   for (int i = 0; i < nf; ++i)
-    k_total_partials<<<nblk, kTotThreads, 0, s>>>(L, fields[i], i, c->partials);
-  k_total_final<<<nf, kTotThreads, 0, s>>>(c->partials, nblk, c->d_sums);
+    SFX_KERNEL(c, K_TOTALS, k_total_partials, nblk, kTotThreads, s, L, fields[i], i, c->partials);
+  SFX_KERNEL(c, K_TOTALS, k_total_final, nf, kTotThreads, s, c->partials, nblk, c->d_sums);
   SFX_LAUNCH_CHECK();
   SFX_CUDA(cudaMemcpyAsync(c->h_sums, c->d_sums, nf * sizeof(double), cudaMemcpyDeviceToHost, s));
   SFX_CUDA(cudaStreamSynchronize(s));
@@ -260,11 +260,11 @@ sfx_status marangoni(sfx_ctx* c, const sfx_params* p, const double* f, const voi
   EosArgs q{p->gamma_inf, p->eps, p->sigma0, p->E, p->eos};
   const int nb = blocks_for(n, 256);
   if (c->prec == SFX_F64) {
-    k_eos<double><<<nb, 256, 0, s>>>(n, q, f, (const double*)phi, sigma);
-    k_force<double><<<nb, 256, 0, s>>>(L, (const double*)phi, C, sigma, dm_mode, force);
+    SFX_KERNEL(c, K_FORCES, k_eos<double>, nb, 256, s, n, q, f, (const double*)phi, sigma);
+    SFX_KERNEL(c, K_FORCES, k_force<double>, nb, 256, s, L, (const double*)phi, C, sigma, dm_mode, force);
   } else {
-    k_eos<float><<<nb, 256, 0, s>>>(n, q, f, (const float*)phi, sigma);
-    k_force<float><<<nb, 256, 0, s>>>(L, (const float*)phi, C, sigma, dm_mode, force);
+    SFX_KERNEL(c, K_FORCES, k_eos<float>, nb, 256, s, n, q, f, (const float*)phi, sigma);
+    SFX_KERNEL(c, K_FORCES, k_force<float>, nb, 256, s, L, (const float*)phi, C, sigma, dm_mode, force);
   }
   SFX_LAUNCH_CHECK();
   return SFX_OK;

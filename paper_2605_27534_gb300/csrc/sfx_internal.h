@@ -23,7 +23,20 @@ struct LevelData {
   double* Bg[3] = {};       // drift faces of a generic sfx_mg_solve call
 };
 
-struct sfx_ctx_impl;
+// Kernel kinds counted (and, when profiling is on, timed with CUDA events
+// on the launching stream) per context; values match sfx_kernel_kind.
+enum Kind {
+  K_SMOOTH_FINE = 0, K_SMOOTH_COARSE, K_RESTRICT, K_PROLONG, K_SETUP, K_RESIDUAL, K_ADVECT,
+  K_TOTALS, K_FORCES, K_PHASE, K_OTHER, K_COUNT
+};
+
+struct Prof {
+  bool on = false;
+  long long launches[K_COUNT] = {};
+  std::vector<cudaEvent_t> ev;   // event pairs (start, end)
+  std::vector<int> kind;         // kind of each recorded pair
+  size_t used = 0;
+};
 
 }  // namespace sfx
 
@@ -46,6 +59,7 @@ struct sfx_ctx {
   double* h_sums = nullptr;          // pinned mirror
   int* d_flag = nullptr;
   std::vector<void*> allocations;
+  sfx::Prof prof;
 };
 
 namespace sfx {
@@ -58,6 +72,16 @@ sfx_status cuda_fail(cudaError_t e);
     if (e_ != cudaSuccess) return ::sfx::cuda_fail(e_);  \
   } while (0)
 #define SFX_LAUNCH_CHECK() SFX_CUDA(cudaGetLastError())
+
+// instrumentation around each kernel launch (sfx_api.cu)
+void prof_before(sfx_ctx* c, int kind, cudaStream_t s);
+void prof_after(sfx_ctx* c, int kind, cudaStream_t s);
+#define SFX_KERNEL(c, kind, kern, grid, block, s, ...) \
+  do {                                                 \
+    ::sfx::prof_before(c, kind, s);                    \
+    kern<<<grid, block, 0, s>>>(__VA_ARGS__);          \
+    ::sfx::prof_after(c, kind, s);                     \
+  } while (0)
 
 // sfx_phase.cu
 sfx_status phase_field_build(sfx_ctx* c, const double* C, double* chi, void* phi, void* delta,

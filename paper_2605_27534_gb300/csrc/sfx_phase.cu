@@ -92,12 +92,12 @@ sfx_status phase_field_build(sfx_ctx* c, const double* C, double* chi, void* phi
   const Level& L = c->lev[0].lv;
   const size_t n = L.ncell();
   const int nb = blocks_for(n, 256);
-  k_chi0<<<nb, 256, 0, s>>>(n, L.h, C, c->chi0, chi);
+  SFX_KERNEL(c, K_PHASE, k_chi0, nb, 256, s, n, L.h, C, c->chi0, chi);
   SFX_LAUNCH_CHECK();
   double* a = chi;
   double* b = c->chi_tmp;
   for (int it = 0; it < iters; ++it) {
-    k_redistance_step<<<nb, 256, 0, s>>>(L, dtau, c->chi0, a, b);
+    SFX_KERNEL(c, K_PHASE, k_redistance_step, nb, 256, s, L, dtau, c->chi0, a, b);
     double* t = a;
     a = b;
     b = t;
@@ -106,9 +106,9 @@ sfx_status phase_field_build(sfx_ctx* c, const double* C, double* chi, void* phi
   if (a != chi)
     SFX_CUDA(cudaMemcpyAsync(chi, a, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
   if (c->prec == SFX_F64)
-    k_phi_delta<double><<<nb, 256, 0, s>>>(n, eps, chi, (double*)phi, (double*)delta);
+    SFX_KERNEL(c, K_PHASE, k_phi_delta<double>, nb, 256, s, n, eps, chi, (double*)phi, (double*)delta);
   else
-    k_phi_delta<float><<<nb, 256, 0, s>>>(n, eps, chi, (float*)phi, (float*)delta);
+    SFX_KERNEL(c, K_PHASE, k_phi_delta<float>, nb, 256, s, n, eps, chi, (float*)phi, (float*)delta);
   SFX_LAUNCH_CHECK();
   return SFX_OK;
 }

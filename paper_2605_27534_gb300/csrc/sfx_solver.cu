@@ -359,43 +359,44 @@ Op op_at(const Hier& H, int l) {
   return o;
 }
 
-sfx_status smooth(const Level& L, const Op& op, const double* b, double* a, int sweeps,
-                  cudaStream_t s) {
+sfx_status smooth(sfx_ctx* c, int kind, const Level& L, const Op& op, const double* b, double* a,
+                  int sweeps, cudaStream_t s) {
   dim3 blk(128), grd((unsigned)(((L.nx + 1) / 2 + 127) / 128), (unsigned)L.ny, (unsigned)L.nz);
   for (int it = 0; it < sweeps; ++it)
     for (int color = 0; color < 2; ++color)
-      k_rbgs<<<grd, blk, 0, s>>>(L, op, b, a, color);
+      SFX_KERNEL(c, kind, k_rbgs, grd, blk, s, L, op, b, a, color);
   SFX_LAUNCH_CHECK();
   return SFX_OK;
 }
 
-sfx_status coarse_solve(const Level& L, const Op& op, const double* b, double* a, int sweeps,
-                        cudaStream_t s) {
+sfx_status coarse_solve(sfx_ctx* c, const Level& L, const Op& op, const double* b, double* a,
+                        int sweeps, cudaStream_t s) {
   if (L.ncell() <= 8192) {
-    k_coarse_solve<<<1, 1024, 0, s>>>(L, op, b, a, sweeps);
+    SFX_KERNEL(c, K_SMOOTH_COARSE, k_coarse_solve, 1, 1024, s, L, op, b, a, sweeps);
     SFX_LAUNCH_CHECK();
     return SFX_OK;
   }
-  return smooth(L, op, b, a, sweeps, s);
+  return smooth(c, K_SMOOTH_COARSE, L, op, b, a, sweeps, s);
 }
 
 sfx_status vcycle(sfx_ctx* c, const Hier& H, int l, double* a, const double* b,
                   const sfx_solve_opts* o, cudaStream_t s) {
   const Level& L = c->lev[l].lv;
   Op op = op_at(H, l);
-  if (l == H.nlev - 1) return coarse_solve(L, op, b, a, o->coarse_sweeps, s);
-  sfx_status st = smooth(L, op, b, a, o->nu1, s);
+  if (l == H.nlev - 1) return coarse_solve(c, L, op, b, a, o->coarse_sweeps, s);
+  const int kind = l == 0 ? K_SMOOTH_FINE : K_SMOOTH_COARSE;
+  sfx_status st = smooth(c, kind, L, op, b, a, o->nu1, s);
   if (st != SFX_OK) return st;
   LevelData& C = c->lev[l + 1];
   const Level& Lc = C.lv;
-  k_resid_restrict<<<blocks_for(Lc.ncell(), 256), 256, 0, s>>>(L, Lc, op, b, a, C.b);
-  k_zero<<<blocks_for(Lc.ncell(), 256), 256, 0, s>>>(Lc.ncell(), C.a);
+  SFX_KERNEL(c, K_RESTRICT, k_resid_restrict, blocks_for(Lc.ncell(), 256), 256, s, L, Lc, op, b, a, C.b);
+  SFX_KERNEL(c, K_OTHER, k_zero, blocks_for(Lc.ncell(), 256), 256, s, Lc.ncell(), C.a);
   SFX_LAUNCH_CHECK();
   st = vcycle(c, H, l + 1, C.a, C.b, o, s);
   if (st != SFX_OK) return st;
-  k_prolong_add<<<blocks_for(L.ncell(), 256), 256, 0, s>>>(Lc, L, C.a, a);
+  SFX_KERNEL(c, K_PROLONG, k_prolong_add, blocks_for(L.ncell(), 256), 256, s, Lc, L, C.a, a);
   SFX_LAUNCH_CHECK();
-  return smooth(L, op, b, a, o->nu2, s);
+  return smooth(c, kind, L, op, b, a, o->nu2, s);
 }
 
 int levels_to_use(sfx_ctx* c, const sfx_solve_opts* o) {
@@ -408,7 +409,7 @@ sfx_status restrict_lambda(sfx_ctx* c, int nlev, cudaStream_t s) {
   for (int l = 1; l < nlev; ++l) {
     const Level& Lf = c->lev[l - 1].lv;
     const Level& Lc = c->lev[l].lv;
-    k_restrict_cells<<<blocks_for(Lc.ncell(), 256), 256, 0, s>>>(Lf, Lc, c->lev[l - 1].lam,
+    SFX_KERNEL(c, K_SETUP, k_restrict_cells, blocks_for(Lc.ncell(), 256), 256, s, Lf, Lc, c->lev[l - 1].lam,
                                                                  c->lev[l].lam);
   }
   SFX_LAUNCH_CHECK();
@@ -449,12 +450,12 @@ sfx_status step_impl(sfx_ctx* c, const sfx_params* p, const P* phi, const void* 
   const int nd = L.ndim();
   // drift faces of both problems at every level (phi is fixed over the step)
   for (int d = 0; d < nd; ++d)
-    k_drift_faces<P><<<blocks_for(L.nface(d), 256), 256, 0, s>>>(
+    SFX_KERNEL(c, K_SETUP, k_drift_faces<P>, blocks_for(L.nface(d), 256), 256, s, 
         L, d, phi, p->Df, p->DF, p->eps, c->lev[0].B[0][d], c->lev[0].B[1][d]);
   for (int l = 1; l < nlev; ++l)
     for (int fld = 0; fld < 2; ++fld)
       for (int d = 0; d < nd; ++d)
-        k_restrict_faces<<<blocks_for(c->lev[l].lv.nface(d), 256), 256, 0, s>>>(
+        SFX_KERNEL(c, K_SETUP, k_restrict_faces, blocks_for(c->lev[l].lv.nface(d), 256), 256, s, 
             c->lev[l - 1].lv, c->lev[l].lv, d, c->lev[l - 1].B[fld][d], c->lev[l].B[fld][d]);
   SFX_LAUNCH_CHECK();
   // a3: explicit advection, then start the implicit solve from (f*, F*)
@@ -489,7 +490,7 @@ sfx_status step_impl(sfx_ctx* c, const sfx_params* p, const P* phi, const void* 
   double nrm[4] = {0, 0, 0, 0};
   const int nb = blocks_for(n, 256);
   for (it = 1; it <= o->max_cycles; ++it) {
-    k_setup_f<P><<<nb, 256, 0, s>>>(n, q, phi, F, c->fstar, lam0, b0);
+    SFX_KERNEL(c, K_SETUP, k_setup_f<P>, nb, 256, s, n, q, phi, F, c->fstar, lam0, b0);
     SFX_LAUNCH_CHECK();
     sfx_status st = restrict_lambda(c, nlev, s);
     if (st != SFX_OK) return st;
@@ -498,7 +499,7 @@ sfx_status step_impl(sfx_ctx* c, const sfx_params* p, const P* phi, const void* 
       if (st != SFX_OK) return st;
       ++cycles;
     }
-    k_setup_F<P><<<nb, 256, 0, s>>>(n, q, phi, f, c->Fstar, lam0, b0);
+    SFX_KERNEL(c, K_SETUP, k_setup_F<P>, nb, 256, s, n, q, phi, f, c->Fstar, lam0, b0);
     SFX_LAUNCH_CHECK();
     st = restrict_lambda(c, nlev, s);
     if (st != SFX_OK) return st;
@@ -510,7 +511,7 @@ sfx_status step_impl(sfx_ctx* c, const sfx_params* p, const P* phi, const void* 
     if (it % o->check_every == 0 || it == o->max_cycles) {
       st = clear_norms(c, s);
       if (st != SFX_OK) return st;
-      k_coupled_resid<P><<<blocks_for(n, 256), 256, 0, s>>>(L, q, op_at(Hf, 0), op_at(HF, 0), phi,
+      SFX_KERNEL(c, K_RESIDUAL, k_coupled_resid<P>, blocks_for(n, 256), 256, s, L, q, op_at(Hf, 0), op_at(HF, 0), phi,
                                                             f, F, c->fstar, c->Fstar, c->d_norms,
                                                             c->d_flag);
       SFX_LAUNCH_CHECK();
@@ -569,12 +570,12 @@ sfx_status mg_solve(sfx_ctx* c, double D, const double* Bx, const double* By, co
   for (int l = 1; l < nlev; ++l) {
     const Level& Lf = c->lev[l - 1].lv;
     const Level& Lc = c->lev[l].lv;
-    k_restrict_cells<<<blocks_for(Lc.ncell(), 256), 256, 0, s>>>(Lf, Lc, H.lam[l - 1],
+    SFX_KERNEL(c, K_SETUP, k_restrict_cells, blocks_for(Lc.ncell(), 256), 256, s, Lf, Lc, H.lam[l - 1],
                                                                  c->lev[l].lam);
     H.lam[l] = c->lev[l].lam;
     for (int d = 0; d < 3; ++d) {
       if (H.B[l - 1][d] == nullptr) { H.B[l][d] = nullptr; continue; }
-      k_restrict_faces<<<blocks_for(Lc.nface(d), 256), 256, 0, s>>>(Lf, Lc, d, H.B[l - 1][d],
+      SFX_KERNEL(c, K_SETUP, k_restrict_faces, blocks_for(Lc.nface(d), 256), 256, s, Lf, Lc, d, H.B[l - 1][d],
                                                                     c->lev[l].Bg[d]);
       H.B[l][d] = c->lev[l].Bg[d];
     }
@@ -588,7 +589,7 @@ sfx_status mg_solve(sfx_ctx* c, double D, const double* Bx, const double* By, co
     if (cyc % o->check_every == 0 || cyc == o->max_cycles) {
       sfx_status st = clear_norms(c, s);
       if (st != SFX_OK) return st;
-      k_resid_norm<<<blocks_for(L.ncell(), 256), 256, 0, s>>>(L, op_at(H, 0), b, a, c->d_norms, 0,
+      SFX_KERNEL(c, K_RESIDUAL, k_resid_norm, blocks_for(L.ncell(), 256), 256, s, L, op_at(H, 0), b, a, c->d_norms, 0,
                                                               c->d_flag);
       SFX_LAUNCH_CHECK();
       bool bad = false;

@@ -376,7 +376,7 @@ def case_hr_3d(n=256, Bi=1.0, Da=1.0, steps=2000, tol=1e-10):
                bc_f=0.0)
     umax = max(np.abs(ux).max(), np.abs(uy).max(), np.abs(uz).max())
     # dt fixed per resolution, within the Sec. 3.3 bound (checked by a test)
-    dt = HR3D_DT.get(n, 0.05 * h)
+    dt = HR3D_DT.get(n, 3.2 * h * h)
     return Case("hr3d_%d" % n, g, p, C, np.ones_like(C), np.zeros_like(C), ux,
                 uy, uz, dt=dt, steps=steps, tol=tol,
                 extra=dict(Bi=Bi, Da=Da, umax=umax))
