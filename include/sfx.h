@@ -160,6 +160,32 @@ sfx_status sfx_surfactant_step(sfx_ctx* ctx, const sfx_params* params,
 sfx_status sfx_totals(sfx_ctx* ctx, const double* const* fields, int n_fields,
                       double* out, void* stream);
 
+/* Largest n_fields that sfx_totals_noalloc accepts. */
+#define SFX_NOALLOC_MAX_FIELDS 8
+
+/* The totals of sfx_totals (same reduction order, same result) without a
+   context and without allocating.  For callers that may not allocate device
+   memory: programs whose device memory belongs to another allocator, and
+   code that must avoid the device-wide synchronisation of cudaMalloc and
+   cudaFree.  The paper has no counterpart; this is a service of the
+   library.
+   Scratch: a fixed file-scope device array of 2 x SFX_NOALLOC_MAX_FIELDS x
+   608 + SFX_NOALLOC_MAX_FIELDS doubles (about 78 KB) that every GPU which
+   loads the library keeps until the process exits.  The first call on a
+   device looks up the array's device address (cudaGetSymbolAddress) with
+   that device current; make that first call before any stream capture.
+   Every call shares the array and leaves its contents behind; each call
+   writes every slot before reading it.  Calls whose GPU work overlaps (for
+   instance on two unordered streams) race on the array.
+   grid: host pointer, as for sfx_ctx_create.  fields: host array of
+   n_fields device pointers to double cell arrays.  out: host array of
+   n_fields doubles, written after the call synchronises with `stream`.
+   Returns SFX_ERR_WORKSPACE when n_fields > SFX_NOALLOC_MAX_FIELDS,
+   SFX_ERR_ARG for a bad grid or null pointer, SFX_ERR_CUDA on a CUDA
+   failure.  Calls no cudaMalloc, cudaFree or allocating library routine. */
+sfx_status sfx_totals_noalloc(const sfx_grid* grid, const double* const* fields,
+                              int n_fields, double* out, void* stream);
+
 /* a7 + a8.  EOS and Marangoni force (Sec. 2.3-2.4):
    Gamma = f/delta_phi where delta_phi >= 1e-3/eps (else 0); sigma(Gamma)
    by params->eos, evaluated in double; force = delta_m (I - n n) grad sigma
