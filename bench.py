@@ -63,17 +63,20 @@ def measured_peaks():
 
 def algorithmic_bytes(kind, grid, wbytes):
     """Unique global bytes one launch of `kind` must move on the fine grid
-    (reads + writes; every array counted once per launch).  N = cells,
-    d = dimensions; drift faces are double, phi has `wbytes` bytes.
-      smooth_fine (one colour): a (N, neighbours) + b, lambda (N/2 each)
-        + d face arrays + write a (N/2)            = 8 (2.5 + d) N
-    """
+    (reads + writes; arrays touched by half the cells count half).  N cells,
+    d dimensions, 8-byte state (double or double-float pair).
+    FP64 colour sweep (k_rbgs): a (all N, as neighbours) + b, lambda (N/2
+      each) + d double face arrays + write a (N/2)       = 8 (2.5 + d) N
+    FP32 colour sweep (k_nlgs32): a (all N) + a*, other field (N/2 each,
+      8 B) + phi (N/2, 4 B) + d float face arrays + write a (N/2)
+                                                         = (22 + 4 d) N
+    Advection of one field: state in/out 16 N + d velocity arrays."""
     N = grid.ncell
     d = grid.ndim
     if kind == "smooth_fine":
-        return 8.0 * (2.5 + d) * N
+        return (8.0 * (2.5 + d) if wbytes == 8 else 22.0 + 4.0 * d) * N
     if kind == "advect":
-        return 8.0 * 2 * N + wbytes * d * N
+        return 16.0 * N + wbytes * d * N
     return None
 
 
@@ -206,16 +209,21 @@ def run_gpu(a, case, rank, world, local_rank):
     ctx.sfx_phase_field_build(Cd, chi, phi, None, iters=case.redist_iters, dtau=case.dtau,
                               eps=p.eps)
     ux, uy, uz = (torch.from_numpy(u).to(dev, wdt) for u in (case.ux, case.uy, case.uz))
-    f = torch.zeros(g.shape, dtype=torch.float64, device=dev)
-    F = torch.ones(g.shape, dtype=torch.float64, device=dev)
-    sigma = torch.empty_like(f)
-    force = torch.empty((3,) + g.shape, dtype=torch.float64, device=dev)
+    f64 = prec == sfx.SFX_F64
+    zeros = torch.zeros(g.shape, dtype=torch.float64, device=dev)
+    ones = torch.ones(g.shape, dtype=torch.float64, device=dev)
+    # state: double (FP64 context) or double-float pairs (FP32 context)
+    f = zeros.clone() if f64 else ctx.sfx_df_pack(zeros)
+    F = ones.clone() if f64 else ctx.sfx_df_pack(ones)
+    Cw = Cd if f64 else Cd.to(torch.float32)
+    sigma = torch.empty(g.shape, dtype=wdt, device=dev)
+    force = torch.empty((3,) + g.shape, dtype=wdt, device=dev)
     opts = sfx.default_opts(tol=a.tol, max_cycles=200)
     stats = []
 
     def step():
         st = ctx.sfx_surfactant_step(p, phi, f, F, case.dt, ux, uy, uz, opts=opts)
-        ctx.sfx_marangoni_force(p, f, phi, Cd, sigma, force, dm_mode=1)
+        ctx.sfx_marangoni_force(p, f, phi, Cw, sigma, force, dm_mode=1)
         stats.append((st.picard, st.vcycles, st.res_f, st.res_F, st.mass_f, st.mass_F))
 
     def barrier():
@@ -253,8 +261,8 @@ def run_gpu(a, case, rank, world, local_rank):
     # ---- end to end through the C-ABI with host buffers (pinned)
     e2e = None
     if not a.no_e2e:
-        fh = torch.zeros(g.shape, dtype=torch.float64).pin_memory()
-        Fh = torch.ones(g.shape, dtype=torch.float64).pin_memory()
+        fh = f.detach().cpu().pin_memory()
+        Fh = F.detach().cpu().pin_memory()
         barrier()
         s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         s0.record(stream)

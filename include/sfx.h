@@ -24,10 +24,17 @@
  *   enqueued.  On SFX_ERR_NOT_CONVERGED the fields hold the last iterate and
  *   the stats are filled.  SFX_ERR_CUDA carries the CUDA error that
  *   sfx_last_cuda_error() returns.
- * Precision.  A context is created for SFX_F64 (every array double) or
- *   SFX_F32 (transported state f, F and totals in double; phase field,
- *   velocities and smoothing in float, with the residual and the
- *   iterative-refinement correction evaluated in double-float arithmetic).
+ * Precision.  A context is created for SFX_F64 or SFX_F32.
+ *   SFX_F64: every field is double.
+ *   SFX_F32: the transported state (f, F and the advected xi) is stored as
+ *   double-float pairs: two floats per cell, hi then lo, value hi + lo
+ *   (about 48 significant bits; sfx_df_pack/sfx_df_unpack convert from/to
+ *   double).  The phase field (folded, see sfx_phi_fold), velocities, VoF
+ *   fraction, sigma and force are float.  Kernels use FP32 arithmetic only: residuals are formed from
+ *   pair differences and applied as pair additions, so the totals keep
+ *   ~1e-14 relative precision while the FP32 coefficients put the solution
+ *   within ~1e-7 of the FP64 operator's.  Totals are reduced in FP64 across
+ *   threads.
  */
 #ifndef SFX_H
 #define SFX_H
@@ -115,18 +122,19 @@ void sfx_default_opts(sfx_solve_opts* opts);
    redistancing d chi/d tau + sign(chi0)(|grad chi| - 1) = 0 (first-order
    Godunov with the Russo-Smereka sub-cell fix) at pseudo-time step dtau,
    then phi = (1 - tanh(chi/(2 eps)))/2 and delta = phi (1 - phi)/eps.
-   C, chi: double.  phi, delta: the context precision (double or float).
-   delta may be NULL. */
+   C, chi: double.  phi, delta: the context precision (double or float;
+   SFX_F32 writes phi folded, see sfx_phi_fold).  delta may be NULL. */
 sfx_status sfx_phase_field_build(sfx_ctx* ctx, const double* C, double* chi,
                                  void* phi, void* delta, int iters,
                                  double dtau, double eps, void* stream);
 
 /* a3.  Explicit BCG advection xi* = xi - dt div(u xi) (Sec. 3.1) of one
-   double field with face velocities u (context precision); bc_in is the
-   value carried in through inflow walls.  xi_out must not alias xi. */
+   state field (double, or double-float pairs in SFX_F32 contexts) with face
+   velocities u (context precision); bc_in is the value carried in through
+   inflow walls.  xi_out must not alias xi. */
 sfx_status sfx_advect(sfx_ctx* ctx, const void* ux, const void* uy,
-                      const void* uz, double dt, const double* xi,
-                      double bc_in, double* xi_out, void* stream);
+                      const void* uz, double dt, const void* xi,
+                      double bc_in, void* xi_out, void* stream);
 
 /* a5.  Solve the generalised elliptic problem of Sec. 3.1
    div(alpha grad a + beta a) + lambda a = b with alpha = -D and beta = -B
@@ -145,19 +153,25 @@ sfx_status sfx_mg_solve(sfx_ctx* ctx, double D, const double* Bx,
    the fully implicit f/F system of App. C solved by Picard iteration, each
    half a multigrid solve of the Sec. 3.1 operator with the drifts
    B_f = -Df 2(0.5 - phi)/eps n and B_F = -DF (1 - phi)/eps n,
-   n = grad phi/|grad phi|.  f and F (double) are updated in place; phi and
-   the velocities are in the context precision.  stats may be NULL. */
+   n = grad phi/|grad phi|.  f and F (state layout of the context) are
+   updated in place; phi and the velocities are in the context precision.
+   SFX_F32 contexts relax the same system by nonlinear red-black
+   Gauss-Seidel sweeps on the pair state (nu1 + nu2 sweeps per field per
+   Picard iteration; the residual bound is each cell's residual just before
+   its update).  stats may be NULL. */
 sfx_status sfx_surfactant_step(sfx_ctx* ctx, const sfx_params* params,
                                const void* phi, const void* ux,
-                               const void* uy, const void* uz, double* f,
-                               double* F, double dt,
+                               const void* uy, const void* uz, void* f,
+                               void* F, double dt,
                                const sfx_solve_opts* opts,
                                sfx_step_stats* stats, void* stream);
 
-/* a6.  Compensated totals sum V x of `n_fields` double fields (out[i],
-   host memory).  Volumes: h^2 (planar), h^3 (3D), pi (r+^2 - r-^2) h
-   (axisymmetric).  Deterministic: fixed reduction order. */
-sfx_status sfx_totals(sfx_ctx* ctx, const double* const* fields, int n_fields,
+/* a6.  Compensated totals sum V x of `n_fields` <= 8 state fields (double,
+   or double-float pairs in SFX_F32 contexts; `fields` is a host array of
+   device pointers) into out[i] (host memory).  Volumes: h^2 (planar), h^3
+   (3D), pi (r+^2 - r-^2) h (axisymmetric).  Deterministic: fixed reduction
+   order. */
+sfx_status sfx_totals(sfx_ctx* ctx, const void* const* fields, int n_fields,
                       double* out, void* stream);
 
 /* Largest n_fields that sfx_totals_noalloc accepts. */
@@ -191,12 +205,14 @@ sfx_status sfx_totals_noalloc(const sfx_grid* grid, const double* const* fields,
    by params->eos, evaluated in double; force = delta_m (I - n n) grad sigma
    with centred grad sigma, n from phi, and delta_m the PLIC interface area
    per cell volume (dm_mode 1; Youngs normal) or |grad C| (dm_mode 0).
-   f, C, sigma, force: double; phi: context precision.  force holds
-   ndim arrays of N cells, component-major. */
+   SFX_F64: f, C, sigma, force double.  SFX_F32: f double-float pairs, C,
+   phi, sigma, force float (sigma may be NULL); the Langmuir logarithm is
+   taken in double once Gamma/Gamma_inf > 1/2, and the gradient is taken of
+   sigma - sigma0.  force holds ndim arrays of N cells, component-major. */
 sfx_status sfx_marangoni_force(sfx_ctx* ctx, const sfx_params* params,
-                               const double* f, const void* phi,
-                               const double* C, int dm_mode, double* sigma,
-                               double* force, void* stream);
+                               const void* f, const void* phi,
+                               const void* C, int dm_mode, void* sigma,
+                               void* force, void* stream);
 
 /* a9.  Time step of Sec. 3.3: safety * min(h/(umax + D/eps),
    h^2/(2 N_d D)), with umax the largest |face velocity| (reduced on the
@@ -204,6 +220,16 @@ sfx_status sfx_marangoni_force(sfx_ctx* ctx, const sfx_params* params,
 sfx_status sfx_cfl_dt(sfx_ctx* ctx, const void* ux, const void* uy,
                       const void* uz, double D, double eps, double safety,
                       double* dt_out, void* stream);
+
+/* Conversions between double arrays and the double-float pairs of SFX_F32
+   contexts (n cells; device pointers; enqueued on stream). */
+sfx_status sfx_df_pack(const double* in, void* out, size_t n, void* stream);
+sfx_status sfx_df_unpack(const void* in, double* out, size_t n, void* stream);
+/* The folded phase field of SFX_F32 contexts from a double phi: phi where
+   phi <= 1/2, phi - 1 elsewhere (so both phi and 1 - phi keep full relative
+   precision in a float).  sfx_phase_field_build writes this form directly
+   in SFX_F32 contexts; every SFX_F32 call takes phi in this form. */
+sfx_status sfx_phi_fold(const double* phi, float* out, size_t n, void* stream);
 
 /* Instrumentation (not part of the method).  Kernel kinds: */
 typedef enum {

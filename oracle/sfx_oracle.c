@@ -769,9 +769,11 @@ void orc_marangoni(const orc_grid* g, const orc_params* p, const double* f,
           /* READING: delta_m = A_f / V_c with the PLIC area; in the
              axisymmetric case both use the cell-centre radius, so the ratio
              equals the planar one (unit-cell area / h). */
+          /* READING: interface cells are those with 1e-6 < C < 1 - 1e-6;
+             fractions closer to 0 or 1 are round-off of empty or full cells */
           double m[3];
           youngs_normal(g, C, i, j, k, m);
-          dm = orc_plic_area(D, m, C[c]) / g->h;
+          dm = (C[c] > 1e-6 && C[c] < 1.0 - 1e-6) ? orc_plic_area(D, m, C[c]) / g->h : 0.0;
         }
         for (int d = 0; d < D; ++d)
           force[d * N + c] = dm * (gs[d] - n[d * N + c] * nd);

@@ -145,6 +145,30 @@ class Context:
                                          int(dm_mode), _ptr(sigma), _ptr(force), _stream()),
                "sfx_marangoni_force")
 
+    def sfx_df_pack(self, x, out=None):
+        """double tensor -> double-float pairs (float32 tensor, last dim 2)."""
+        import torch
+        if out is None:
+            out = torch.empty(tuple(x.shape) + (2,), dtype=torch.float32, device=x.device)
+        _check(lib().sfx_df_pack(_ptr(x), _ptr(out), x.numel(), _stream()), "sfx_df_pack")
+        return out
+
+    def sfx_df_unpack(self, p, out=None):
+        """double-float pairs (float32, last dim 2) -> double tensor."""
+        import torch
+        if out is None:
+            out = torch.empty(tuple(p.shape[:-1]), dtype=torch.float64, device=p.device)
+        _check(lib().sfx_df_unpack(_ptr(p), _ptr(out), out.numel(), _stream()), "sfx_df_unpack")
+        return out
+
+    def sfx_phi_fold(self, phi, out=None):
+        """double phi -> folded float carrier of SFX_F32 contexts."""
+        import torch
+        if out is None:
+            out = torch.empty(tuple(phi.shape), dtype=torch.float32, device=phi.device)
+        _check(lib().sfx_phi_fold(_ptr(phi), _ptr(out), phi.numel(), _stream()), "sfx_phi_fold")
+        return out
+
     def sfx_profile(self, on: bool):
         _check(lib().sfx_profile(self._h, 1 if on else 0), "sfx_profile")
 

@@ -21,7 +21,8 @@ EXPORTS = [
     "sfx_version", "sfx_status_string", "sfx_last_cuda_error", "sfx_ctx_create",
     "sfx_ctx_destroy", "sfx_default_opts", "sfx_phase_field_build", "sfx_advect",
     "sfx_mg_solve", "sfx_surfactant_step", "sfx_totals", "sfx_marangoni_force", "sfx_cfl_dt",
-    "sfx_profile", "sfx_profile_read", "sfx_totals_noalloc",
+    "sfx_profile", "sfx_profile_read", "sfx_totals_noalloc", "sfx_df_pack", "sfx_df_unpack",
+    "sfx_phi_fold",
 ]
 KERNEL_KINDS = ["smooth_fine", "smooth_coarse", "restrict", "prolong", "setup", "residual",
                 "advect", "totals", "forces", "phase", "other"]
@@ -98,6 +99,12 @@ def load(path: str = SO_PATH):
     L.sfx_profile_read.restype = C.c_int
     L.sfx_profile_read.argtypes = [vp, C.c_int, C.POINTER(C.c_longlong), C.POINTER(C.c_double),
                                    C.POINTER(C.c_longlong)]
+    L.sfx_df_pack.restype = C.c_int
+    L.sfx_df_pack.argtypes = [vp, vp, C.c_size_t, vp]
+    L.sfx_df_unpack.restype = C.c_int
+    L.sfx_df_unpack.argtypes = [vp, vp, C.c_size_t, vp]
+    L.sfx_phi_fold.restype = C.c_int
+    L.sfx_phi_fold.argtypes = [vp, vp, C.c_size_t, vp]
     L.sfx_totals_noalloc.restype = C.c_int
     L.sfx_totals_noalloc.argtypes = [C.POINTER(Grid), C.POINTER(C.c_void_p), C.c_int,
                                      C.POINTER(C.c_double), vp]

@@ -168,6 +168,7 @@ sfx_status sfx_ctx_create(const sfx_grid* grid, int precision, sfx_ctx** out) {
   if (st == SFX_OK) st = dalloc(c, &c->partials, (size_t)2 * 8 * c->n_partial_blocks);
   if (st == SFX_OK) st = dalloc(c, &c->d_norms, 8);
   if (st == SFX_OK) st = dalloc(c, &c->d_sums, 8);
+  if (st == SFX_OK && precision == SFX_F32) st = f32_ensure_scratch(c);
   if (st == SFX_OK) {
     c->d_flag = (int*)(c->d_norms + 7);
     cudaError_t e = cudaMallocHost(&c->h_norms, 8 * sizeof(unsigned long long));
@@ -189,10 +190,13 @@ sfx_status sfx_phase_field_build(sfx_ctx* c, const double* C, double* chi, void*
 }
 
 sfx_status sfx_advect(sfx_ctx* c, const void* ux, const void* uy, const void* uz, double dt,
-                      const double* xi, double bc_in, double* xi_out, void* stream) {
+                      const void* xi, double bc_in, void* xi_out, void* stream) {
   if (!c || !ux || !uy || !xi || !xi_out || xi == xi_out || !(dt > 0.0)) return SFX_ERR_ARG;
   if (c->grid.geom == SFX_CART3D && !uz) return SFX_ERR_ARG;
-  return advect(c, ux, uy, uz, dt, xi, bc_in, xi_out, S(stream));
+  if (c->prec == SFX_F32)
+    return advect32(c, (const float*)ux, (const float*)uy, (const float*)uz, dt,
+                    (const float2*)xi, bc_in, (float2*)xi_out, S(stream));
+  return advect(c, ux, uy, uz, dt, (const double*)xi, bc_in, (double*)xi_out, S(stream));
 }
 
 sfx_status sfx_mg_solve(sfx_ctx* c, double D, const double* Bx, const double* By,
@@ -210,8 +214,8 @@ sfx_status sfx_mg_solve(sfx_ctx* c, double D, const double* Bx, const double* By
 }
 
 sfx_status sfx_surfactant_step(sfx_ctx* c, const sfx_params* params, const void* phi,
-                               const void* ux, const void* uy, const void* uz, double* f,
-                               double* F, double dt, const sfx_solve_opts* opts,
+                               const void* ux, const void* uy, const void* uz, void* f,
+                               void* F, double dt, const sfx_solve_opts* opts,
                                sfx_step_stats* stats, void* stream) {
   if (!c || !params_ok(params) || !phi || !f || !F || f == F || !(dt > 0.0) ||
       !std::isfinite(dt))
@@ -221,24 +225,34 @@ sfx_status sfx_surfactant_step(sfx_ctx* c, const sfx_params* params, const void*
   sfx_default_opts(&o);
   if (opts) o = *opts;
   if (!opts_ok(&o)) return SFX_ERR_ARG;
-  return surfactant_step(c, params, phi, ux, uy, uz, f, F, dt, &o, stats, S(stream));
+  if (c->prec == SFX_F32)
+    return step_f32(c, params, (const float*)phi, (const float*)ux, (const float*)uy,
+                    (const float*)uz, (float2*)f, (float2*)F, dt, &o, stats, S(stream));
+  return surfactant_step(c, params, phi, ux, uy, uz, (double*)f, (double*)F, dt, &o, stats,
+                         S(stream));
 }
 
-sfx_status sfx_totals(sfx_ctx* c, const double* const* fields, int n_fields, double* out,
+sfx_status sfx_totals(sfx_ctx* c, const void* const* fields, int n_fields, double* out,
                       void* stream) {
   if (!c || !fields || !out || n_fields < 1 || n_fields > 8) return SFX_ERR_ARG;
   for (int i = 0; i < n_fields; ++i)
     if (!fields[i]) return SFX_ERR_ARG;
-  return totals(c, fields, n_fields, out, S(stream));
+  if (c->prec == SFX_F32) return totals32(c, fields, n_fields, out, S(stream));
+  return totals(c, (const double* const*)fields, n_fields, out, S(stream));
 }
 
-sfx_status sfx_marangoni_force(sfx_ctx* c, const sfx_params* params, const double* f,
-                               const void* phi, const double* C, int dm_mode, double* sigma,
-                               double* force, void* stream) {
-  if (!c || !params_ok(params) || !f || !phi || !sigma || !force) return SFX_ERR_ARG;
+sfx_status sfx_marangoni_force(sfx_ctx* c, const sfx_params* params, const void* f,
+                               const void* phi, const void* C, int dm_mode, void* sigma,
+                               void* force, void* stream) {
+  if (!c || !params_ok(params) || !f || !phi || !force) return SFX_ERR_ARG;
   if (dm_mode != 0 && dm_mode != 1) return SFX_ERR_ARG;
   if (!C) return SFX_ERR_ARG;
-  return marangoni(c, params, f, phi, C, dm_mode, sigma, force, S(stream));
+  if (c->prec == SFX_F32)
+    return marangoni32(c, params, (const float2*)f, (const float*)phi, (const float*)C, dm_mode,
+                       (float*)sigma, (float*)force, S(stream));
+  if (!sigma) return SFX_ERR_ARG;
+  return marangoni(c, params, (const double*)f, phi, (const double*)C, dm_mode, (double*)sigma,
+                   (double*)force, S(stream));
 }
 
 sfx_status sfx_cfl_dt(sfx_ctx* c, const void* ux, const void* uy, const void* uz, double D,
@@ -254,6 +268,21 @@ sfx_status sfx_cfl_dt(sfx_ctx* c, const void* ux, const void* uy, const void* uz
   double ddiff = h * h / (2.0 * nd * D);
   *dt_out = safety * (dconv < ddiff ? dconv : ddiff);
   return SFX_OK;
+}
+
+sfx_status sfx_df_pack(const double* in, void* out, size_t n, void* stream) {
+  if ((!in || !out) && n) return SFX_ERR_ARG;
+  return df_pack(in, out, n, S(stream));
+}
+
+sfx_status sfx_df_unpack(const void* in, double* out, size_t n, void* stream) {
+  if ((!in || !out) && n) return SFX_ERR_ARG;
+  return df_unpack(in, out, n, S(stream));
+}
+
+sfx_status sfx_phi_fold(const double* phi, float* out, size_t n, void* stream) {
+  if ((!phi || !out) && n) return SFX_ERR_ARG;
+  return phi_fold(phi, out, n, S(stream));
 }
 
 sfx_status sfx_profile(sfx_ctx* c, int on) {

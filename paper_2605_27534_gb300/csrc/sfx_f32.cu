@@ -1,0 +1,712 @@
+// SFX_F32 contexts: the coupled step in FP32 arithmetic with a double-float
+// transported state.
+//
+// State.  f and F are double-float pairs (float2, value hi + lo).  Every
+// residual is evaluated in pair arithmetic (FP32 instructions only) from
+// FP32 coefficients, so the discrete operator is the FP64 one with its
+// coefficients rounded to float (solution within ~1e-7), while residuals
+// resolve ~1e-14 and every face flux is bitwise the same for both cells that
+// share the face (totals conserved to pair precision).  The update
+// a += r/diag adds a float increment to the pair.
+// Carrier.  phi is stored folded (phi if phi <= 1/2, phi - 1 otherwise) so
+// phi and 1 - phi both keep full relative precision.
+//
+// Solver.  The App. C system is relaxed by nonlinear red-black Gauss-Seidel
+// sweeps on the pair state: each cell takes the local Newton (here exact,
+// the equations being linear in the unknown for fixed neighbours and fixed
+// other field) update  a_c += r_c / diag_c  with
+//   r_f = (f* - f)/dt + div G_f + q,   r_F = (F* - F)/dt + div G_F - q,
+//   q = r_a F/(phi+eta) (f_inf - f) - r_d f      (App. C),
+//   G = D (a_R - a_L)/h + B a_up,  a_up upwinded on -B (Sec. 3.2 reading),
+// alternating f sweeps and F sweeps (Picard).  Each colour launch records
+// the residual of every cell it updates, taken just before the update, so
+// the largest such residual bounds the change made by the sweep; the step
+// stops when that bound is below tol |b| for both fields.
+#include <cmath>
+#include <cstring>
+
+#include "sfx_df.cuh"
+#include "sfx_internal.h"
+
+namespace sfx {
+namespace {
+
+__device__ __forceinline__ unsigned int fbits(float v) { return __float_as_uint(v); }
+
+// ------------------------------------------------------------ drifts
+// Face drifts of both problems from the FP32 phase field (App. C):
+// B_f = -Df 2(0.5 - phi)/eps n, B_F = -DF (1 - phi)/eps n, face mean, walls 0.
+__device__ __forceinline__ float normal32(const Level& L, const float* __restrict__ phi, int i,
+                                          int j, int k, int d) {
+  int ip = min(i + 1, L.nx - 1), im = max(i - 1, 0);
+  int jp = min(j + 1, L.ny - 1), jm = max(j - 1, 0);
+  float g0 = dphi(phi[cidx(L, ip, j, k)], phi[cidx(L, im, j, k)]);
+  float g1 = dphi(phi[cidx(L, i, jp, k)], phi[cidx(L, i, jm, k)]);
+  float g2 = 0.0f;
+  if (L.geom == SFX_CART3D) {
+    int kp = min(k + 1, L.nz - 1), km = max(k - 1, 0);
+    g2 = dphi(phi[cidx(L, i, j, kp)], phi[cidx(L, i, j, km)]);
+  }
+  // the 1/(2h) of the centred difference cancels in the normalisation
+  float m2 = g0 * g0 + g1 * g1 + g2 * g2;
+  float g = d == 0 ? g0 : (d == 1 ? g1 : g2);
+  float inv2h = 0.5f / (float)L.h;
+  if (m2 * inv2h * inv2h < 1e-30f) return 0.0f;
+  return g * rsqrtf(m2);
+}
+
+__global__ void k_drift32(Level L, int d, const float* __restrict__ phi, float Df, float DF,
+                          float inv_eps, float* __restrict__ Bf, float* __restrict__ BF) {
+  size_t n = L.nface(d);
+  int fx = L.nx + (d == 0), fy = L.ny + (d == 1);
+  for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < n;
+       q += (size_t)gridDim.x * blockDim.x) {
+    int i = (int)(q % fx), j = (int)((q / fx) % fy), k = (int)(q / ((size_t)fx * fy));
+    int pos = d == 0 ? i : (d == 1 ? j : k);
+    if (pos == 0 || pos == L.extent(d)) { Bf[q] = 0.0f; BF[q] = 0.0f; continue; }
+    int li = i - (d == 0), lj = j - (d == 1), lk = k - (d == 2);
+    float sL = phi[cidx(L, li, lj, lk)], sR = phi[cidx(L, i, j, k)];
+    PhiPair uL = unfold(sL), uR = unfold(sR);
+    // 0.5 - phi from the folded value keeps its precision on both sides
+    float hL = signbit(sL) ? -0.5f - sL : 0.5f - sL;
+    float hR = signbit(sR) ? -0.5f - sR : 0.5f - sR;
+    float nL = normal32(L, phi, li, lj, lk, d), nR = normal32(L, phi, i, j, k, d);
+    Bf[q] = 0.5f * ((-Df * 2.0f * hL * inv_eps) * nL + (-Df * 2.0f * hR * inv_eps) * nR);
+    BF[q] = 0.5f * ((-DF * uL.q * inv_eps) * nL + (-DF * uR.q * inv_eps) * nR);
+  }
+}
+
+// ------------------------------------------------------------ sweeps
+struct Nl32 {
+  Level L;
+  float invh, Doh, inv_dt, ka, kd, ginf, inv_eps, eta;
+  int literal;
+};
+
+// Area weight of a face relative to h^(d-1) (planar, 3D: 1) or to pi h^2
+// (axisymmetric: 2 i for the radial face at r = i h, 2 i + 1 for the axial
+// faces of column i); the cell volume over the same unit times h is w_c h.
+__device__ __forceinline__ float wr_face(int geom, int iface) {
+  return geom == SFX_AXISYM ? 2.0f * (float)iface : 1.0f;
+}
+__device__ __forceinline__ float wz_face(int geom, int i) {
+  return geom == SFX_AXISYM ? 2.0f * (float)i + 1.0f : 1.0f;
+}
+
+// Face quantity G = D (a_R - a_L)/h + B a_up as a pair; adds sgn * w * G to
+// the flux sum S and the residual's derivative in the cell value to diag.
+__device__ __forceinline__ void face32(float w, float Doh, float B, int literal, float2 aL,
+                                       float2 aR, bool cell_is_left, float2& S, float& dg) {
+  const bool upL = literal ? (B > 0.0f) : (B < 0.0f);
+  const float2 G = df_add2(df_mul_f(df_sub2(aR, aL), Doh), df_mul_f(upL ? aL : aR, B));
+  const float2 wG = df_mul_f(G, w);
+  if (cell_is_left) {  // plus face: +G, dG/da_c = -Doh + (upL ? B : 0)
+    S = df_add2(S, wG);
+    dg += w * (Doh - (upL ? B : 0.0f));
+  } else {             // minus face: -G, dG/da_c = Doh + (upL ? 0 : B)
+    S = df_sub2(S, wG);
+    dg += w * (Doh + (upL ? 0.0f : B));
+  }
+}
+
+// (1/V) sum over faces of (+-) A G at cell (i,j,k) as a pair, and its
+// derivative in a_c.
+__device__ __forceinline__ void transport32(const Nl32& p, const float* __restrict__ Bx,
+                                            const float* __restrict__ By,
+                                            const float* __restrict__ Bz, const float2* a,
+                                            int i, int j, int k, size_t c, float2 ac,
+                                            float2& flux, float& diag) {
+  const Level& L = p.L;
+  float2 S = make_float2(0.0f, 0.0f);
+  float dg = 0.0f;
+  if (i > 0)
+    face32(wr_face(L.geom, i), p.Doh, Bx[fidx(L, 0, i, j, k)], p.literal, a[c - 1], ac, false,
+           S, dg);
+  if (i + 1 < L.nx)
+    face32(wr_face(L.geom, i + 1), p.Doh, Bx[fidx(L, 0, i + 1, j, k)], p.literal, ac, a[c + 1],
+           true, S, dg);
+  const float wz = wz_face(L.geom, i);
+  const size_t sy = (size_t)L.nx;
+  if (j > 0)
+    face32(wz, p.Doh, By[fidx(L, 1, i, j, k)], p.literal, a[c - sy], ac, false, S, dg);
+  if (j + 1 < L.ny)
+    face32(wz, p.Doh, By[fidx(L, 1, i, j + 1, k)], p.literal, ac, a[c + sy], true, S, dg);
+  if (L.geom == SFX_CART3D) {
+    const size_t sz = (size_t)L.nx * L.ny;
+    if (k > 0)
+      face32(1.0f, p.Doh, Bz[fidx(L, 2, i, j, k)], p.literal, a[c - sz], ac, false, S, dg);
+    if (k + 1 < L.nz)
+      face32(1.0f, p.Doh, Bz[fidx(L, 2, i, j, k + 1)], p.literal, ac, a[c + sz], true, S, dg);
+  }
+  // divide by the cell volume in the same unit: w_c h
+  const float wc = wz;  // 2i+1 on rings, 1 otherwise
+  flux = df_mul_f(S, p.invh);
+  if (L.geom == SFX_AXISYM) flux = df_div_f(flux, wc);
+  diag = dg * p.invh / wc;
+}
+
+// Exchange term of App. C, q = r_a F/(phi + eta) (f_inf - f) - r_d f, as a
+// pair; the same expression serves both equations, so at a common state
+// the two sources cancel exactly in the totals.
+__device__ __forceinline__ float2 exchange32(const Nl32& p, float c1, float finf, float2 f,
+                                            float2 F) {
+  const float2 fd = df_add(df_neg(f), finf);         // f_inf - f
+  const float2 ads = df_mul_f(df_mul(F, fd), c1);    // r_a F (f_inf - f)/(phi + eta)
+  return df_sub2(ads, df_mul_f(f, p.kd));
+}
+
+// Nonlinear red-black colour sweep of field FIELD (0: f, 1: F) on the
+// double-float state.  norms (optional): max |r| and max |b| of the updated
+// cells, as float bit patterns, in norms[2*FIELD], norms[2*FIELD+1].
+template <int FIELD>
+__global__ void k_nlgs32(Nl32 p, const float* __restrict__ phi, const float* __restrict__ Bx,
+                         const float* __restrict__ By, const float* __restrict__ Bz, float2* a,
+                         const float2* __restrict__ astar, const float2* __restrict__ other,
+                         int color, unsigned int* norms) {
+  const Level& L = p.L;
+  const int j = blockIdx.y, k = blockIdx.z;
+  const int i = 2 * (blockIdx.x * blockDim.x + threadIdx.x) + ((j + k + color) & 1);
+  float rmax = 0.0f, bmax = 0.0f;
+  if (i < L.nx) {
+    const size_t c = cidx(L, i, j, k);
+    const float2 ac = a[c];
+    float2 flux;
+    float diag;
+    transport32(p, Bx, By, Bz, a, i, j, k, c, ac, flux, diag);
+    const PhiPair ph = unfold(phi[c]);
+    const float c1 = p.ka / (ph.p + p.eta);
+    const float finf = p.ginf * ph.p * ph.q * p.inv_eps;
+    const float2 as = astar[c];
+    const float2 ov = other[c];
+    const float2 q = FIELD == 0 ? exchange32(p, c1, finf, ac, ov) : exchange32(p, c1, finf, ov, ac);
+    const float2 tr = df_add2(df_mul_f(df_sub2(as, ac), p.inv_dt), flux);
+    const float2 rr = FIELD == 0 ? df_add2(tr, q) : df_sub2(tr, q);
+    const float r = df_val(rr);
+    float b;
+    if (FIELD == 0) {
+      const float Fv = df_val(ov);
+      diag += p.inv_dt + p.kd + c1 * Fv;
+      b = as.x * p.inv_dt + c1 * Fv * finf;
+    } else {
+      const float fv = df_val(ov);
+      diag += p.inv_dt + c1 * (finf - fv);
+      b = as.x * p.inv_dt + p.kd * fv;
+    }
+    a[c] = df_add(ac, r / diag);
+    rmax = fabsf(r);
+    bmax = fabsf(b);
+    if (!(rmax <= 3.0e38f)) rmax = __int_as_float(0x7f800000);  // NaN -> +inf
+  }
+  if (norms) {
+    rmax = warp_max(rmax);
+    bmax = warp_max(bmax);
+    if ((threadIdx.x & 31) == 0) {
+      atomicMax(&norms[2 * FIELD], fbits(rmax));
+      atomicMax(&norms[2 * FIELD + 1], fbits(bmax));
+    }
+  }
+}
+
+// ------------------------------------------------------------ advection
+__device__ __forceinline__ float mc32(float xm, float x0, float xp) {
+  float dl = x0 - xm, dr = xp - x0;
+  if (dl * dr <= 0.0f) return 0.0f;
+  float dc = 0.5f * (xp - xm);
+  float m = fminf(fabsf(dc), 2.0f * fminf(fabsf(dl), fabsf(dr)));
+  return dc > 0.0f ? m : -m;
+}
+
+struct Adv32 {
+  Level L;
+  float dt, invh;
+  const float* u[3];
+};
+
+__device__ __forceinline__ float vnb(const Level& L, const float2* __restrict__ x, const int* uc,
+                                     size_t U, int d, int s) {
+  int p = uc[d] + s;
+  if (p < 0 || p >= L.extent(d)) return df_val(x[U]);
+  size_t stride = d == 0 ? 1 : (d == 1 ? (size_t)L.nx : (size_t)L.nx * L.ny);
+  return df_val(s > 0 ? x[U + stride] : x[U - stride]);
+}
+
+// BCG face value (see sfx_advect.cu) in FP32 on the pair values.
+__device__ float face32v(const Adv32& A, const float2* __restrict__ x, float bc_in, int d,
+                         const int* f, float u) {
+  const Level& L = A.L;
+  int uc[3] = {f[0], f[1], f[2]};
+  if (u > 0.0f) {
+    if (f[d] == 0) return bc_in;
+    uc[d] -= 1;
+  } else if (f[d] == L.extent(d)) {
+    return bc_in;
+  }
+  size_t U = cidx(L, uc[0], uc[1], uc[2]);
+  float x0 = df_val(x[U]);
+  float slope = mc32(vnb(L, x, uc, U, d, -1), x0, vnb(L, x, uc, U, d, +1));
+  float val = x0 + 0.5f * ((u > 0.0f ? 1.0f : -1.0f) - u * A.dt * A.invh) * slope;
+  for (int t = 0; t < L.ndim(); ++t) {
+    if (t == d) continue;
+    int ap[3] = {uc[0], uc[1], uc[2]};
+    ap[t] += 1;
+    float vbar = 0.5f * (A.u[t][fidx(L, t, uc[0], uc[1], uc[2])] + A.u[t][fidx(L, t, ap[0], ap[1], ap[2])]);
+    float dif = vbar > 0.0f ? x0 - vnb(L, x, uc, U, t, -1) : vnb(L, x, uc, U, t, +1) - x0;
+    val -= 0.5f * A.dt * vbar * dif * A.invh;
+  }
+  return val;
+}
+
+__global__ void k_advect32(Adv32 A, const float2* __restrict__ x, float bc_in,
+                           float2* __restrict__ out) {
+  const Level& L = A.L;
+  const size_t n = L.ncell();
+  for (size_t c = blockIdx.x * (size_t)blockDim.x + threadIdx.x; c < n;
+       c += (size_t)gridDim.x * blockDim.x) {
+    int idx[3] = {(int)(c % L.nx), (int)((c / L.nx) % L.ny), (int)(c / ((size_t)L.nx * L.ny))};
+    // net outflow in area units; each face term is computed bitwise alike
+    // by the two cells that share the face
+    float2 S = make_float2(0.0f, 0.0f);
+    for (int d = 0; d < L.ndim(); ++d) {
+      int pp[3] = {idx[0], idx[1], idx[2]};
+      pp[d] += 1;
+      float um = A.u[d][fidx(L, d, idx[0], idx[1], idx[2])];
+      float up = A.u[d][fidx(L, d, pp[0], pp[1], pp[2])];
+      float wm = d == 0 ? wr_face(L.geom, idx[0]) : (d == 1 ? wz_face(L.geom, idx[0]) : 1.0f);
+      float wp = d == 0 ? wr_face(L.geom, idx[0] + 1) : wm;
+      if (um != 0.0f) {
+        float fv = face32v(A, x, bc_in, d, idx, um);
+        float pr = __fmul_rn(um, fv);
+        S = df_sub2(S, df_mul_f(make_float2(pr, fmaf(um, fv, -pr)), wm));
+      }
+      if (up != 0.0f) {
+        float fv = face32v(A, x, bc_in, d, pp, up);
+        float pr = __fmul_rn(up, fv);
+        S = df_add2(S, df_mul_f(make_float2(pr, fmaf(up, fv, -pr)), wp));
+      }
+    }
+    float2 inc = df_mul_f(df_mul_f(S, -A.dt), A.invh);
+    if (L.geom == SFX_AXISYM) inc = df_div_f(inc, wz_face(L.geom, idx[0]));
+    out[c] = df_add2(x[c], inc);
+  }
+}
+
+// ------------------------------------------------------------ totals
+// Per-thread double-float accumulation of w_i (hi + lo) with w_i the cell
+// volume over its constant factor (1, or 2i+1 on rings); FP64 only across
+// threads.
+__global__ void k_total32_partials(Level L, const float2* __restrict__ x, int fi,
+                                   double* __restrict__ partials) {
+  const size_t n = L.ncell();
+  float2 acc = make_float2(0.0f, 0.0f);
+  for (size_t c = blockIdx.x * (size_t)blockDim.x + threadIdx.x; c < n;
+       c += (size_t)gridDim.x * blockDim.x) {
+    float2 v = x[c];
+    if (L.geom == SFX_AXISYM) {
+      float w = 2.0f * (float)(c % L.nx) + 1.0f;
+      float p = v.x * w;
+      float e = fmaf(v.x, w, -p);               // exact product error
+      v = make_float2(p, e + v.y * w);
+    }
+    acc = df_add2(acc, v);
+  }
+  double s = (double)acc.x, cc = (double)acc.y;
+  warp_sum_comp(s, cc);
+  __shared__ double ss[8], sc[8];
+  int w = threadIdx.x >> 5;
+  if ((threadIdx.x & 31) == 0) { ss[w] = s; sc[w] = cc; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double a = ss[0], b = sc[0];
+    for (int q = 1; q < (int)(blockDim.x >> 5); ++q) {
+      double t, e;
+      two_sum(a, ss[q], t, e);
+      a = t;
+      b += sc[q] + e;
+    }
+    partials[2 * ((size_t)fi * gridDim.x + blockIdx.x)] = a;
+    partials[2 * ((size_t)fi * gridDim.x + blockIdx.x) + 1] = b;
+  }
+}
+
+__global__ void k_total32_final(const double* __restrict__ partials, int nblk, double scale,
+                                double* __restrict__ out) {
+  const int fi = blockIdx.x;
+  double s = 0.0, cc = 0.0;
+  for (int q = threadIdx.x; q < nblk; q += blockDim.x) {
+    double t, e;
+    two_sum(s, partials[2 * ((size_t)fi * nblk + q)], t, e);
+    s = t;
+    cc += partials[2 * ((size_t)fi * nblk + q) + 1] + e;
+  }
+  warp_sum_comp(s, cc);
+  __shared__ double ss[8], sc[8];
+  int w = threadIdx.x >> 5;
+  if ((threadIdx.x & 31) == 0) { ss[w] = s; sc[w] = cc; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double a = ss[0], b = sc[0];
+    for (int q = 1; q < (int)(blockDim.x >> 5); ++q) {
+      double t, e;
+      two_sum(a, ss[q], t, e);
+      a = t;
+      b += sc[q] + e;
+    }
+    out[fi] = (a + b) * scale;
+  }
+}
+
+// ------------------------------------------------------------ EOS, force
+struct Eos32 {
+  float ginf, eps, inv_eps, sigma0, E;
+  int eos;
+};
+
+// sigma - sigma0 (kept for the gradient, where it has full relative
+// precision) and sigma itself.  The Langmuir logarithm is taken in FP64
+// once Gamma/Gamma_inf exceeds 1/2 (near saturation), in FP32 below.
+__global__ void k_eos32(size_t n, Eos32 q, const float2* __restrict__ f,
+                        const float* __restrict__ phi, float* __restrict__ dsig,
+                        float* __restrict__ sigma) {
+  for (size_t c = blockIdx.x * (size_t)blockDim.x + threadIdx.x; c < n;
+       c += (size_t)gridDim.x * blockDim.x) {
+    PhiPair ph = unfold(phi[c]);
+    float del = ph.p * ph.q * q.inv_eps;
+    float G = del >= 1e-3f * q.inv_eps ? df_val(f[c]) / del : 0.0f;
+    float x = G / q.ginf;
+    float ds;
+    if (q.eos == SFX_EOS_LANGMUIR) {
+      if (x > 0.5f) {
+        double xd = fmin((double)x, 1.0 - 1e-12);
+        ds = (float)((double)q.sigma0 * (double)q.E * log1p(-xd));
+      } else {
+        ds = q.sigma0 * q.E * log1pf(-x);
+      }
+    } else if (q.eos == SFX_EOS_LINEAR) {
+      ds = -q.sigma0 * q.E * x;
+    } else {
+      ds = -q.sigma0 * tanhf(q.E * x);
+    }
+    dsig[c] = ds;
+    if (sigma) sigma[c] = q.sigma0 + ds;
+  }
+}
+
+struct VS32 {
+  float v, dv;
+};
+
+// Unit-cube volume below m.x = a (ascending m, sum 1) and its slope, FP32
+// version of the region-wise Scardovelli-Zaleski evaluation.
+__device__ VS32 plic32_half(const float* q, bool three_d, float a) {
+  VS32 r{0.0f, 0.0f};
+  if (a <= 0.0f) return r;
+  if (!three_d) {
+    float lo = q[1], hi = q[2];
+    if (a < lo) { r.v = 0.5f * a * a / (lo * hi); r.dv = a / (lo * hi); }
+    else { r.v = (a - 0.5f * lo) / hi; r.dv = 1.0f / hi; }
+    return r;
+  }
+  float p = q[0], s = q[1], t = q[2];
+  float ist = 1.0f / (s * t);
+  if (a < p) {
+    r.v = a * a * a * ist / (6.0f * p);
+    r.dv = 0.5f * a * a * ist / p;
+  } else if (a < s) {
+    r.v = 0.5f * (a * (a - p) + p * p / 3.0f) * ist;
+    r.dv = (a - 0.5f * p) * ist;
+  } else if (t >= p + s && a >= p + s) {
+    r.v = (a - 0.5f * (p + s)) / t;
+    r.dv = 1.0f / t;
+  } else {
+    float u = a - s, w = fmaxf(a - t, 0.0f);
+    r.v = 0.5f * (a * (a - p) + p * p / 3.0f) * ist - (u * u * u + w * w * w) * ist / (6.0f * p);
+    r.dv = (a - 0.5f * p) * ist - 0.5f * (u * u + w * w) * ist / p;
+  }
+  return r;
+}
+
+__device__ float plic32_area(int nd, const float* m, float C) {
+  if (!(C > 0.0f && C < 1.0f)) return 0.0f;
+  float s = 0.0f, q2 = 0.0f;
+  for (int d = 0; d < nd; ++d) { s += fabsf(m[d]); q2 += m[d] * m[d]; }
+  if (s == 0.0f) return 0.0f;
+  float q[3] = {nd == 3 ? fabsf(m[2]) / s : 0.0f, fabsf(m[0]) / s, fabsf(m[1]) / s};
+  if (q[0] > q[1]) { float t = q[0]; q[0] = q[1]; q[1] = t; }
+  if (q[1] > q[2]) { float t = q[1]; q[1] = q[2]; q[2] = t; }
+  if (q[0] > q[1]) { float t = q[0]; q[0] = q[1]; q[1] = t; }
+  const bool three_d = nd == 3;
+  const bool flip = C > 0.5f;             // V(a) = 1 - V(1 - a)
+  const float target = flip ? 1.0f - C : C;
+  float lo = 0.0f, hi = 0.5f;
+  for (int it = 0; it < 30; ++it) {
+    float mid = 0.5f * (lo + hi);
+    if (plic32_half(q, three_d, mid).v < target) lo = mid;
+    else hi = mid;
+  }
+  return sqrtf(q2) / s * plic32_half(q, three_d, 0.5f * (lo + hi)).dv;
+}
+
+__global__ void k_force32(Level L, const float* __restrict__ phi, const float* __restrict__ C,
+                          const float* __restrict__ dsig, int dm_mode, float* __restrict__ force) {
+  const size_t n = L.ncell();
+  const int nd = L.ndim();
+  const float inv2h = 0.5f / (float)L.h;
+  for (size_t c = blockIdx.x * (size_t)blockDim.x + threadIdx.x; c < n;
+       c += (size_t)gridDim.x * blockDim.x) {
+    int idx[3] = {(int)(c % L.nx), (int)((c / L.nx) % L.ny), (int)(c / ((size_t)L.nx * L.ny))};
+    float gs[3] = {0, 0, 0}, nn[3] = {0, 0, 0}, ndg = 0.0f;
+    float g0 = 0, g1 = 0, g2 = 0, gc2 = 0;
+    for (int d = 0; d < nd; ++d) {
+      int pp[3] = {idx[0], idx[1], idx[2]}, pm[3] = {idx[0], idx[1], idx[2]};
+      pp[d] = min(pp[d] + 1, L.extent(d) - 1);
+      pm[d] = max(pm[d] - 1, 0);
+      size_t cp = cidx(L, pp[0], pp[1], pp[2]), cm = cidx(L, pm[0], pm[1], pm[2]);
+      gs[d] = (dsig[cp] - dsig[cm]) * inv2h;
+      float gp = dphi(phi[cp], phi[cm]);
+      if (d == 0) g0 = gp; else if (d == 1) g1 = gp; else g2 = gp;
+      if (dm_mode == 0) {
+        float gc = (C[cp] - C[cm]) * inv2h;
+        gc2 += gc * gc;
+      }
+    }
+    float m2 = g0 * g0 + g1 * g1 + g2 * g2;
+    float inv = (m2 * inv2h * inv2h < 1e-30f) ? 0.0f : rsqrtf(m2);
+    nn[0] = g0 * inv; nn[1] = g1 * inv; nn[2] = g2 * inv;
+    for (int d = 0; d < nd; ++d) ndg += nn[d] * gs[d];
+    float dm = 0.0f;
+    if (dm_mode == 0) {
+      dm = sqrtf(gc2);
+    } else {
+      float Cc = C[c];
+      if (Cc > 1e-6f && Cc < 1.0f - 1e-6f) {   // interface cells only
+        float m[3] = {0, 0, 0};
+        int kr = nd == 3 ? 1 : 0;
+        for (int dk = -kr; dk <= kr; ++dk)
+          for (int dj = -1; dj <= 1; ++dj)
+            for (int di = -1; di <= 1; ++di) {
+              int a = min(max(idx[0] + di, 0), L.nx - 1);
+              int b = min(max(idx[1] + dj, 0), L.ny - 1);
+              int e = min(max(idx[2] + dk, 0), L.nz - 1);
+              float w = (di == 0 ? 2.0f : 1.0f) * (dj == 0 ? 2.0f : 1.0f) *
+                        (nd == 3 ? (dk == 0 ? 2.0f : 1.0f) : 1.0f);
+              float v = C[cidx(L, a, b, e)];
+              m[0] -= w * di * v;
+              m[1] -= w * dj * v;
+              m[2] -= w * dk * v;
+            }
+        dm = plic32_area(nd, m, Cc) / (float)L.h;
+      }
+    }
+    for (int d = 0; d < nd; ++d) force[(size_t)d * n + c] = dm * (gs[d] - nn[d] * ndg);
+  }
+}
+
+// ------------------------------------------------------------ conversions
+__global__ void k_pack_df(size_t n, const double* __restrict__ in, float2* __restrict__ out) {
+  for (size_t c = blockIdx.x * (size_t)blockDim.x + threadIdx.x; c < n;
+       c += (size_t)gridDim.x * blockDim.x) {
+    double d = in[c];
+    float hi = (float)d;
+    out[c] = make_float2(hi, (float)(d - (double)hi));
+  }
+}
+
+__global__ void k_fold_phi(size_t n, const double* __restrict__ phi, float* __restrict__ out) {
+  for (size_t c = blockIdx.x * (size_t)blockDim.x + threadIdx.x; c < n;
+       c += (size_t)gridDim.x * blockDim.x) {
+    double p = phi[c];
+    out[c] = p <= 0.5 ? (float)p : (float)(p - 1.0);
+  }
+}
+
+__global__ void k_unpack_df(size_t n, const float2* __restrict__ in, double* __restrict__ out) {
+  for (size_t c = blockIdx.x * (size_t)blockDim.x + threadIdx.x; c < n;
+       c += (size_t)gridDim.x * blockDim.x)
+    out[c] = (double)in[c].x + (double)in[c].y;
+}
+
+// ------------------------------------------------------------ host
+sfx_status sweep32(sfx_ctx* c, int field, const Nl32& p, const float* phi, const float* const* B,
+                   float2* a, const float2* astar, const float2* other, bool norms,
+                   cudaStream_t s) {
+  const Level& L = p.L;
+  dim3 blk(128), grd((unsigned)(((L.nx + 1) / 2 + 127) / 128), (unsigned)L.ny, (unsigned)L.nz);
+  unsigned int* nb = norms ? (unsigned int*)c->d_norms : nullptr;
+  for (int color = 0; color < 2; ++color) {
+    if (field == 0)
+      SFX_KERNEL(c, K_SMOOTH_FINE, k_nlgs32<0>, grd, blk, s, p, phi, B[0], B[1], B[2], a, astar,
+                 other, color, nb);
+    else
+      SFX_KERNEL(c, K_SMOOTH_FINE, k_nlgs32<1>, grd, blk, s, p, phi, B[0], B[1], B[2], a, astar,
+                 other, color, nb);
+  }
+  SFX_LAUNCH_CHECK();
+  return SFX_OK;
+}
+
+}  // namespace
+
+sfx_status f32_ensure_scratch(sfx_ctx* c);
+
+sfx_status step_f32(sfx_ctx* c, const sfx_params* pr, const float* phi, const float* ux,
+                    const float* uy, const float* uz, float2* f, float2* F, double dt,
+                    const sfx_solve_opts* o, sfx_step_stats* stats, cudaStream_t s) {
+  sfx_status st = f32_ensure_scratch(c);
+  if (st != SFX_OK) return st;
+  const Level& L = c->lev[0].lv;
+  const size_t n = L.ncell();
+  const int nd = L.ndim();
+  float* Bf[3] = {c->f32.Bf[0], c->f32.Bf[1], nd == 3 ? c->f32.Bf[2] : nullptr};
+  float* BF[3] = {c->f32.BF[0], c->f32.BF[1], nd == 3 ? c->f32.BF[2] : nullptr};
+  for (int d = 0; d < nd; ++d)
+    SFX_KERNEL(c, K_SETUP, k_drift32, blocks_for(L.nface(d), 256), 256, s, L, d, phi,
+               (float)pr->Df, (float)pr->DF, (float)(1.0 / pr->eps), Bf[d], BF[d]);
+  SFX_LAUNCH_CHECK();
+  float2* fs = c->f32.fstar;
+  float2* Fs = c->f32.Fstar;
+  if (ux) {
+    Adv32 A{L, (float)dt, (float)(1.0 / L.h), {ux, uy, uz}};
+    SFX_KERNEL(c, K_ADVECT, k_advect32, blocks_for(n, 256), 256, s, A, f, (float)pr->bc_f, fs);
+    SFX_KERNEL(c, K_ADVECT, k_advect32, blocks_for(n, 256), 256, s, A, F, (float)pr->bc_F, Fs);
+    SFX_LAUNCH_CHECK();
+    SFX_CUDA(cudaMemcpyAsync(f, fs, n * sizeof(float2), cudaMemcpyDeviceToDevice, s));
+    SFX_CUDA(cudaMemcpyAsync(F, Fs, n * sizeof(float2), cudaMemcpyDeviceToDevice, s));
+  } else {
+    SFX_CUDA(cudaMemcpyAsync(fs, f, n * sizeof(float2), cudaMemcpyDeviceToDevice, s));
+    SFX_CUDA(cudaMemcpyAsync(Fs, F, n * sizeof(float2), cudaMemcpyDeviceToDevice, s));
+  }
+  Nl32 pf{L, (float)(1.0 / L.h), (float)(pr->Df / L.h), (float)(1.0 / dt), (float)pr->ka,
+          (float)pr->kd, (float)pr->gamma_inf, (float)(1.0 / pr->eps), (float)pr->eta,
+          pr->literal_upwind};
+  Nl32 pF = pf;
+  pF.Doh = (float)(pr->DF / L.h);
+  const int sweeps = o->nu1 + o->nu2;
+  int it = 0;
+  bool conv = false;
+  float nrm[4] = {0, 0, 0, 0};
+  for (it = 1; it <= o->max_cycles; ++it) {
+    const bool check = (it % o->check_every == 0) || it == o->max_cycles;
+    if (check) SFX_CUDA(cudaMemsetAsync(c->d_norms, 0, 8 * sizeof(unsigned long long), s));
+    for (int q = 0; q < sweeps; ++q) {
+      st = sweep32(c, 0, pf, phi, Bf, f, fs, F, check && q == 0, s);
+      if (st != SFX_OK) return st;
+    }
+    for (int q = 0; q < sweeps; ++q) {
+      st = sweep32(c, 1, pF, phi, BF, F, Fs, f, check && q == 0, s);
+      if (st != SFX_OK) return st;
+    }
+    if (check) {
+      SFX_CUDA(cudaMemcpyAsync(c->h_norms, c->d_norms, 2 * sizeof(unsigned long long),
+                               cudaMemcpyDeviceToHost, s));
+      SFX_CUDA(cudaStreamSynchronize(s));
+      memcpy(nrm, c->h_norms, 4 * sizeof(float));
+      for (int q = 0; q < 4; ++q)
+        if (!std::isfinite(nrm[q])) return SFX_ERR_NONFINITE;
+      double rf = nrm[0] / fmax((double)nrm[1], 1e-300);
+      double rF = nrm[2] / fmax((double)nrm[3], 1e-300);
+      if (rf <= o->tol && rF <= o->tol) {
+        conv = true;
+        break;
+      }
+    }
+  }
+  if (stats) {
+    stats->picard = it > o->max_cycles ? o->max_cycles : it;
+    stats->vcycles = 2 * stats->picard * sweeps;
+    stats->res_f = nrm[0] / fmax((double)nrm[1], 1e-300);
+    stats->res_F = nrm[2] / fmax((double)nrm[3], 1e-300);
+    stats->converged = conv ? 1 : 0;
+    const void* fl[2] = {f, F};
+    double m[2];
+    st = totals32(c, fl, 2, m, s);
+    if (st != SFX_OK) return st;
+    stats->mass_f = m[0];
+    stats->mass_F = m[1];
+  }
+  return conv ? SFX_OK : SFX_ERR_NOT_CONVERGED;
+}
+
+sfx_status advect32(sfx_ctx* c, const float* ux, const float* uy, const float* uz, double dt,
+                    const float2* xi, double bc_in, float2* out, cudaStream_t s) {
+  const Level& L = c->lev[0].lv;
+  Adv32 A{L, (float)dt, (float)(1.0 / L.h), {ux, uy, uz}};
+  SFX_KERNEL(c, K_ADVECT, k_advect32, blocks_for(L.ncell(), 256), 256, s, A, xi, (float)bc_in,
+             out);
+  SFX_LAUNCH_CHECK();
+  return SFX_OK;
+}
+
+sfx_status totals32(sfx_ctx* c, const void* const* fields, int nf, double* out, cudaStream_t s) {
+  const Level& L = c->lev[0].lv;
+  const int nblk = c->n_partial_blocks;
+  for (int i = 0; i < nf; ++i)
+    SFX_KERNEL(c, K_TOTALS, k_total32_partials, nblk, 256, s, L, (const float2*)fields[i], i,
+               c->partials);
+  double h = L.h;
+  double scale = L.geom == SFX_PLANAR2D ? h * h : (L.geom == SFX_CART3D ? h * h * h : kPi * h * h * h);
+  SFX_KERNEL(c, K_TOTALS, k_total32_final, nf, 256, s, c->partials, nblk, scale, c->d_sums);
+  SFX_LAUNCH_CHECK();
+  SFX_CUDA(cudaMemcpyAsync(c->h_sums, c->d_sums, nf * sizeof(double), cudaMemcpyDeviceToHost, s));
+  SFX_CUDA(cudaStreamSynchronize(s));
+  memcpy(out, c->h_sums, nf * sizeof(double));
+  return SFX_OK;
+}
+
+sfx_status marangoni32(sfx_ctx* c, const sfx_params* p, const float2* f, const float* phi,
+                       const float* C, int dm_mode, float* sigma, float* force, cudaStream_t s) {
+  sfx_status st = f32_ensure_scratch(c);
+  if (st != SFX_OK) return st;
+  const Level& L = c->lev[0].lv;
+  const size_t n = L.ncell();
+  Eos32 q{(float)p->gamma_inf, (float)p->eps, (float)(1.0 / p->eps), (float)p->sigma0,
+          (float)p->E, p->eos};
+  SFX_KERNEL(c, K_FORCES, k_eos32, blocks_for(n, 256), 256, s, n, q, f, phi, c->f32.dsig, sigma);
+  SFX_KERNEL(c, K_FORCES, k_force32, blocks_for(n, 256), 256, s, L, phi, C, c->f32.dsig, dm_mode,
+             force);
+  SFX_LAUNCH_CHECK();
+  return SFX_OK;
+}
+
+sfx_status df_pack(const double* in, void* out, size_t n, cudaStream_t s) {
+  if (n == 0) return SFX_OK;
+  k_pack_df<<<blocks_for(n, 256), 256, 0, s>>>(n, in, (float2*)out);
+  SFX_LAUNCH_CHECK();
+  return SFX_OK;
+}
+
+sfx_status phi_fold(const double* phi, float* out, size_t n, cudaStream_t s) {
+  if (n == 0) return SFX_OK;
+  k_fold_phi<<<blocks_for(n, 256), 256, 0, s>>>(n, phi, out);
+  SFX_LAUNCH_CHECK();
+  return SFX_OK;
+}
+
+sfx_status df_unpack(const void* in, double* out, size_t n, cudaStream_t s) {
+  if (n == 0) return SFX_OK;
+  k_unpack_df<<<blocks_for(n, 256), 256, 0, s>>>(n, (const float2*)in, out);
+  SFX_LAUNCH_CHECK();
+  return SFX_OK;
+}
+
+sfx_status f32_ensure_scratch(sfx_ctx* c) {
+  if (c->f32.ready) return SFX_OK;
+  const Level& L = c->lev[0].lv;
+  const size_t n = L.ncell();
+  auto get = [&](size_t bytes, void** p) -> sfx_status {
+    SFX_CUDA(cudaMalloc(p, bytes ? bytes : 4));
+    c->allocations.push_back(*p);
+    return SFX_OK;
+  };
+  sfx_status st;
+  for (int d = 0; d < L.ndim(); ++d) {
+    if ((st = get(L.nface(d) * sizeof(float), (void**)&c->f32.Bf[d])) != SFX_OK) return st;
+    if ((st = get(L.nface(d) * sizeof(float), (void**)&c->f32.BF[d])) != SFX_OK) return st;
+  }
+  if ((st = get(n * sizeof(float2), (void**)&c->f32.fstar)) != SFX_OK) return st;
+  if ((st = get(n * sizeof(float2), (void**)&c->f32.Fstar)) != SFX_OK) return st;
+  if ((st = get(n * sizeof(float), (void**)&c->f32.dsig)) != SFX_OK) return st;
+  c->f32.ready = true;
+  return SFX_OK;
+}
+
+}  // namespace sfx

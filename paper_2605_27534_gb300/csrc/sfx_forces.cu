@@ -211,7 +211,9 @@ __global__ void k_force(Level L, const P* __restrict__ phi, const double* __rest
       dm = sqrt(q);
     } else {
       double Cc = C[c];
-      if (Cc > 0.0 && Cc < 1.0) {
+      // interface cells: 1e-6 < C < 1 - 1e-6 (nearer fractions are the
+      // round-off of empty or full cells)
+      if (Cc > 1e-6 && Cc < 1.0 - 1e-6) {
         // Youngs normal: minus the (1,2,1)-weighted gradient of C
         double m[3] = {0, 0, 0};
         int kr = nd == 3 ? 1 : 0;

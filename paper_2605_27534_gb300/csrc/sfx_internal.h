@@ -30,6 +30,16 @@ enum Kind {
   K_TOTALS, K_FORCES, K_PHASE, K_OTHER, K_COUNT
 };
 
+// Work arrays of SFX_F32 contexts (float drifts, double-float f*, F*).
+struct F32Scratch {
+  bool ready = false;
+  float* Bf[3] = {};
+  float* BF[3] = {};
+  float2* fstar = nullptr;
+  float2* Fstar = nullptr;
+  float* dsig = nullptr;   // sigma - sigma0
+};
+
 struct Prof {
   bool on = false;
   long long launches[K_COUNT] = {};
@@ -60,6 +70,7 @@ struct sfx_ctx {
   int* d_flag = nullptr;
   std::vector<void*> allocations;
   sfx::Prof prof;
+  sfx::F32Scratch f32;
 };
 
 namespace sfx {
@@ -103,6 +114,20 @@ sfx_status totals(sfx_ctx* c, const double* const* fields, int n, double* out, c
 sfx_status marangoni(sfx_ctx* c, const sfx_params* p, const double* f, const void* phi,
                      const double* C, int dm_mode, double* sigma, double* force,
                      cudaStream_t s);
+
+// sfx_f32.cu (SFX_F32 contexts: double-float state, FP32 arithmetic)
+sfx_status f32_ensure_scratch(sfx_ctx* c);
+sfx_status step_f32(sfx_ctx* c, const sfx_params* p, const float* phi, const float* ux,
+                    const float* uy, const float* uz, float2* f, float2* F, double dt,
+                    const sfx_solve_opts* o, sfx_step_stats* st, cudaStream_t s);
+sfx_status advect32(sfx_ctx* c, const float* ux, const float* uy, const float* uz, double dt,
+                    const float2* xi, double bc_in, float2* out, cudaStream_t s);
+sfx_status totals32(sfx_ctx* c, const void* const* fields, int n, double* out, cudaStream_t s);
+sfx_status marangoni32(sfx_ctx* c, const sfx_params* p, const float2* f, const float* phi,
+                       const float* C, int dm_mode, float* sigma, float* force, cudaStream_t s);
+sfx_status df_pack(const double* in, void* out, size_t n, cudaStream_t s);
+sfx_status df_unpack(const void* in, double* out, size_t n, cudaStream_t s);
+sfx_status phi_fold(const double* phi, float* out, size_t n, cudaStream_t s);
 
 inline int blocks_for(size_t n, int threads) {
   size_t b = (n + threads - 1) / threads;
