@@ -67,14 +67,17 @@ def algorithmic_bytes(kind, grid, wbytes):
     d dimensions, 8-byte state (double or double-float pair).
     FP64 colour sweep (k_rbgs): a (all N, as neighbours) + b, lambda (N/2
       each) + d double face arrays + write a (N/2)       = 8 (2.5 + d) N
-    FP32 colour sweep (k_nlgs32): a (all N) + a*, other field (N/2 each,
-      8 B) + phi (N/2, 4 B) + d float face arrays + write a (N/2)
-                                                         = (22 + 4 d) N
+    FP32 fused sweep (k_nlrb32_z, both colours): a in and out, a*, the other
+      field (8 B each), phi (4 B), d float face arrays   = (36 + 4 d) N
     Advection of one field: state in/out 16 N + d velocity arrays."""
     N = grid.ncell
     d = grid.ndim
     if kind == "smooth_fine":
-        return (8.0 * (2.5 + d) if wbytes == 8 else 22.0 + 4.0 * d) * N
+        if wbytes == 8:
+            return 8.0 * (2.5 + d) * N
+        # fused FP32 sweep (both colours in one launch): a in/out, a*, other
+        # field (8 B each), phi, d float face arrays
+        return (36.0 + 4.0 * d) * N
     if kind == "advect":
         return 16.0 * N + wbytes * d * N
     return None
@@ -219,6 +222,8 @@ def run_gpu(a, case, rank, world, local_rank):
     sigma = torch.empty(g.shape, dtype=wdt, device=dev)
     force = torch.empty((3,) + g.shape, dtype=wdt, device=dev)
     opts = sfx.default_opts(tol=a.tol, max_cycles=200)
+    if prec == sfx.SFX_F32:   # one nonlinear red-black sweep per field per Picard iteration
+        opts.nu1, opts.nu2 = 1, 0
     stats = []
 
     def step():

@@ -221,6 +221,15 @@ sfx_status sfx_cfl_dt(sfx_ctx* ctx, const void* ux, const void* uy,
                       const void* uz, double D, double eps, double safety,
                       double* dt_out, void* stream);
 
+/* Tuning knobs (same results, different schedules).  Returns SFX_ERR_ARG
+   for an unknown key or value. */
+typedef enum {
+  SFX_TUNE_FUSED_SWEEP = 0  /* SFX_F32: 1 (default) = one launch per
+                               red-black sweep through shared-memory tiles;
+                               0 = one launch per colour.  Bitwise equal. */
+} sfx_tune_key;
+sfx_status sfx_set_tuning(sfx_ctx* ctx, int key, int value);
+
 /* Conversions between double arrays and the double-float pairs of SFX_F32
    contexts (n cells; device pointers; enqueued on stream). */
 sfx_status sfx_df_pack(const double* in, void* out, size_t n, void* stream);

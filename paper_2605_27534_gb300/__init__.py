@@ -169,6 +169,9 @@ class Context:
         _check(lib().sfx_phi_fold(_ptr(phi), _ptr(out), phi.numel(), _stream()), "sfx_phi_fold")
         return out
 
+    def sfx_set_tuning(self, key: int, value: int):
+        _check(lib().sfx_set_tuning(self._h, int(key), int(value)), "sfx_set_tuning")
+
     def sfx_profile(self, on: bool):
         _check(lib().sfx_profile(self._h, 1 if on else 0), "sfx_profile")
 

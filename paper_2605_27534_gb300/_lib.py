@@ -22,8 +22,9 @@ EXPORTS = [
     "sfx_ctx_destroy", "sfx_default_opts", "sfx_phase_field_build", "sfx_advect",
     "sfx_mg_solve", "sfx_surfactant_step", "sfx_totals", "sfx_marangoni_force", "sfx_cfl_dt",
     "sfx_profile", "sfx_profile_read", "sfx_totals_noalloc", "sfx_df_pack", "sfx_df_unpack",
-    "sfx_phi_fold",
+    "sfx_phi_fold", "sfx_set_tuning",
 ]
+SFX_TUNE_FUSED_SWEEP = 0
 KERNEL_KINDS = ["smooth_fine", "smooth_coarse", "restrict", "prolong", "setup", "residual",
                 "advect", "totals", "forces", "phase", "other"]
 
@@ -103,6 +104,8 @@ def load(path: str = SO_PATH):
     L.sfx_df_pack.argtypes = [vp, vp, C.c_size_t, vp]
     L.sfx_df_unpack.restype = C.c_int
     L.sfx_df_unpack.argtypes = [vp, vp, C.c_size_t, vp]
+    L.sfx_set_tuning.restype = C.c_int
+    L.sfx_set_tuning.argtypes = [vp, C.c_int, C.c_int]
     L.sfx_phi_fold.restype = C.c_int
     L.sfx_phi_fold.argtypes = [vp, vp, C.c_size_t, vp]
     L.sfx_totals_noalloc.restype = C.c_int

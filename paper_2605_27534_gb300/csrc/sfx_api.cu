@@ -270,6 +270,15 @@ sfx_status sfx_cfl_dt(sfx_ctx* c, const void* ux, const void* uy, const void* uz
   return SFX_OK;
 }
 
+sfx_status sfx_set_tuning(sfx_ctx* c, int key, int value) {
+  if (!c) return SFX_ERR_ARG;
+  if (key == SFX_TUNE_FUSED_SWEEP && (value == 0 || value == 1)) {
+    c->f32.fused = value == 1;
+    return SFX_OK;
+  }
+  return SFX_ERR_ARG;
+}
+
 sfx_status sfx_df_pack(const double* in, void* out, size_t n, void* stream) {
   if ((!in || !out) && n) return SFX_ERR_ARG;
   return df_pack(in, out, n, S(stream));

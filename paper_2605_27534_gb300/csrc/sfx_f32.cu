@@ -22,6 +22,7 @@
 // the residual of every cell it updates, taken just before the update, so
 // the largest such residual bounds the change made by the sweep; the step
 // stops when that bound is below tol |b| for both fields.
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 
@@ -93,66 +94,102 @@ __device__ __forceinline__ float wz_face(int geom, int i) {
   return geom == SFX_AXISYM ? 2.0f * (float)i + 1.0f : 1.0f;
 }
 
-// Face quantity G = D (a_R - a_L)/h + B a_up as a pair; adds sgn * w * G to
-// the flux sum S and the residual's derivative in the cell value to diag.
-__device__ __forceinline__ void face32(float w, float Doh, float B, int literal, float2 aL,
-                                       float2 aR, bool cell_is_left, float2& S, float& dg) {
-  const bool upL = literal ? (B > 0.0f) : (B < 0.0f);
-  const float2 G = df_add2(df_mul_f(df_sub2(aR, aL), Doh), df_mul_f(upL ? aL : aR, B));
-  const float2 wG = df_mul_f(G, w);
-  if (cell_is_left) {  // plus face: +G, dG/da_c = -Doh + (upL ? B : 0)
-    S = df_add2(S, wG);
-    dg += w * (Doh - (upL ? B : 0.0f));
-  } else {             // minus face: -G, dG/da_c = Doh + (upL ? 0 : B)
-    S = df_sub2(S, wG);
-    dg += w * (Doh + (upL ? 0.0f : B));
-  }
+// Unnormalised pair accumulator: hi by error-free two-sums, everything else
+// gathered in lo; normalised once at the end.
+struct Acc {
+  float hi, lo;
+};
+__device__ __forceinline__ void acc_add(Acc& s, float2 x) {
+  float2 t = ef_two_sum(s.hi, x.x);
+  s.hi = t.x;
+  s.lo = __fadd_rn(s.lo, __fadd_rn(t.y, x.y));
+}
+__device__ __forceinline__ void acc_sub(Acc& s, float2 x) { acc_add(s, make_float2(-x.x, -x.y)); }
+__device__ __forceinline__ float2 acc_get(const Acc& s) { return ef_fast_two_sum(s.hi, s.lo); }
+
+// unnormalised products and differences (exact leading part + error term)
+__device__ __forceinline__ float2 lp_mul(float2 a, float b) {
+  float p = __fmul_rn(a.x, b);
+  return make_float2(p, fmaf(a.y, b, fmaf(a.x, b, -p)));
+}
+__device__ __forceinline__ float2 lp_sub(float2 a, float2 b) {
+  float2 t = ef_two_sum(a.x, -b.x);
+  return make_float2(t.x, __fadd_rn(t.y, __fsub_rn(a.y, b.y)));
 }
 
-// (1/V) sum over faces of (+-) A G at cell (i,j,k) as a pair, and its
-// derivative in a_c.
-__device__ __forceinline__ void transport32(const Nl32& p, const float* __restrict__ Bx,
-                                            const float* __restrict__ By,
-                                            const float* __restrict__ Bz, const float2* a,
-                                            int i, int j, int k, size_t c, float2 ac,
-                                            float2& flux, float& diag) {
-  const Level& L = p.L;
-  float2 S = make_float2(0.0f, 0.0f);
+// Face quantity G = D (a_R - a_L)/h + B a_up as an unnormalised pair.  Both
+// cells that share the face evaluate it from the same operands in the same
+// order, so their contributions cancel exactly in the totals.
+__device__ __forceinline__ float2 face_G(float Doh, float B, bool upL, float2 aL, float2 aR) {
+  const float2 d = lp_mul(lp_sub(aR, aL), Doh);
+  const float2 u = lp_mul(upL ? aL : aR, B);
+  float2 t = ef_two_sum(d.x, u.x);
+  return make_float2(t.x, __fadd_rn(t.y, __fadd_rn(d.y, u.y)));
+}
+
+// Residual, diagonal and |b| of one cell from its six neighbours (nb[q]
+// valid when has[q]; order x-, x+, y-, y+, z-, z+) and face drifts B[q]:
+//   r = (a* - a)/dt + (1/V) sum +-A G + (FIELD ? -q : q)
+template <int FIELD>
+__device__ __forceinline__ float2 cell_update32(const Nl32& p, int i, float2 ac, const float2* nb,
+                                                const bool* has, const float* B, float phis,
+                                                float2 as, float2 ov, float& r_out,
+                                                float& b_out) {
+  const int geom = p.L.geom;
+  Acc S{0.0f, 0.0f};
   float dg = 0.0f;
-  if (i > 0)
-    face32(wr_face(L.geom, i), p.Doh, Bx[fidx(L, 0, i, j, k)], p.literal, a[c - 1], ac, false,
-           S, dg);
-  if (i + 1 < L.nx)
-    face32(wr_face(L.geom, i + 1), p.Doh, Bx[fidx(L, 0, i + 1, j, k)], p.literal, ac, a[c + 1],
-           true, S, dg);
-  const float wz = wz_face(L.geom, i);
-  const size_t sy = (size_t)L.nx;
-  if (j > 0)
-    face32(wz, p.Doh, By[fidx(L, 1, i, j, k)], p.literal, a[c - sy], ac, false, S, dg);
-  if (j + 1 < L.ny)
-    face32(wz, p.Doh, By[fidx(L, 1, i, j + 1, k)], p.literal, ac, a[c + sy], true, S, dg);
-  if (L.geom == SFX_CART3D) {
-    const size_t sz = (size_t)L.nx * L.ny;
-    if (k > 0)
-      face32(1.0f, p.Doh, Bz[fidx(L, 2, i, j, k)], p.literal, a[c - sz], ac, false, S, dg);
-    if (k + 1 < L.nz)
-      face32(1.0f, p.Doh, Bz[fidx(L, 2, i, j, k + 1)], p.literal, ac, a[c + sz], true, S, dg);
+#pragma unroll
+  for (int q = 0; q < 6; ++q) {
+    if (!has[q]) continue;
+    const bool plus = q & 1;                     // plus face: this cell is the left one
+    const bool upL = p.literal ? (B[q] > 0.0f) : (B[q] < 0.0f);
+    float w = 1.0f;
+    if (geom == SFX_AXISYM) w = q < 2 ? wr_face(geom, i + (plus ? 1 : 0)) : (q < 4 ? wz_face(geom, i) : 1.0f);
+    float2 G = plus ? face_G(p.Doh, B[q], upL, ac, nb[q]) : face_G(p.Doh, B[q], upL, nb[q], ac);
+    if (geom == SFX_AXISYM) G = lp_mul(G, w);
+    if (plus) {
+      acc_add(S, G);
+      dg += w * (p.Doh - (upL ? B[q] : 0.0f));
+    } else {
+      acc_sub(S, G);
+      dg += w * (p.Doh + (upL ? 0.0f : B[q]));
+    }
   }
-  // divide by the cell volume in the same unit: w_c h
-  const float wc = wz;  // 2i+1 on rings, 1 otherwise
-  flux = df_mul_f(S, p.invh);
-  if (L.geom == SFX_AXISYM) flux = df_div_f(flux, wc);
-  diag = dg * p.invh / wc;
-}
-
-// Exchange term of App. C, q = r_a F/(phi + eta) (f_inf - f) - r_d f, as a
-// pair; the same expression serves both equations, so at a common state
-// the two sources cancel exactly in the totals.
-__device__ __forceinline__ float2 exchange32(const Nl32& p, float c1, float finf, float2 f,
-                                            float2 F) {
-  const float2 fd = df_add(df_neg(f), finf);         // f_inf - f
-  const float2 ads = df_mul_f(df_mul(F, fd), c1);    // r_a F (f_inf - f)/(phi + eta)
-  return df_sub2(ads, df_mul_f(f, p.kd));
+  const float wc = wz_face(geom, i);
+  float2 flux = lp_mul(acc_get(S), p.invh);
+  if (geom == SFX_AXISYM) flux = df_div_f(ef_fast_two_sum(flux.x, flux.y), wc);
+  float diag = dg * p.invh;
+  if (geom == SFX_AXISYM) diag = __fdividef(diag, wc);
+  // exchange q = r_a F/(phi+eta) (f_inf - f) - r_d f, shared by both equations
+  const PhiPair ph = unfold(phis);
+  const float c1 = __fdividef(p.ka, ph.p + p.eta);
+  const float finf = p.ginf * ph.p * ph.q * p.inv_eps;
+  const float2 fv2 = FIELD == 0 ? ac : ov;
+  const float2 Fv2 = FIELD == 0 ? ov : ac;
+  float2 fd = ef_two_sum(finf, -fv2.x);
+  fd.y = __fsub_rn(fd.y, fv2.y);
+  float pr = __fmul_rn(Fv2.x, fd.x);
+  float2 FF = make_float2(pr, fmaf(Fv2.y, fd.x, fmaf(Fv2.x, fd.y, fmaf(Fv2.x, fd.x, -pr))));
+  const float2 ads = lp_mul(FF, c1);
+  const float2 des = lp_mul(fv2, p.kd);
+  // r = (a* - a)/dt + flux +- (ads - des)
+  Acc R{0.0f, 0.0f};
+  acc_add(R, lp_mul(lp_sub(as, ac), p.inv_dt));
+  acc_add(R, flux);
+  if (FIELD == 0) { acc_add(R, ads); acc_sub(R, des); }
+  else { acc_sub(R, ads); acc_add(R, des); }
+  const float r = __fadd_rn(R.hi, R.lo);
+  if (FIELD == 0) {
+    const float Fv = __fadd_rn(ov.x, ov.y);
+    diag += p.inv_dt + p.kd + c1 * Fv;
+    b_out = as.x * p.inv_dt + c1 * Fv * finf;
+  } else {
+    const float fv = __fadd_rn(ov.x, ov.y);
+    diag += p.inv_dt + c1 * (finf - fv);
+    b_out = as.x * p.inv_dt + p.kd * fv;
+  }
+  r_out = r;
+  return df_add(ac, __fdividef(r, diag));
 }
 
 // Nonlinear red-black colour sweep of field FIELD (0: f, 1: F) on the
@@ -169,30 +206,17 @@ __global__ void k_nlgs32(Nl32 p, const float* __restrict__ phi, const float* __r
   float rmax = 0.0f, bmax = 0.0f;
   if (i < L.nx) {
     const size_t c = cidx(L, i, j, k);
-    const float2 ac = a[c];
-    float2 flux;
-    float diag;
-    transport32(p, Bx, By, Bz, a, i, j, k, c, ac, flux, diag);
-    const PhiPair ph = unfold(phi[c]);
-    const float c1 = p.ka / (ph.p + p.eta);
-    const float finf = p.ginf * ph.p * ph.q * p.inv_eps;
-    const float2 as = astar[c];
-    const float2 ov = other[c];
-    const float2 q = FIELD == 0 ? exchange32(p, c1, finf, ac, ov) : exchange32(p, c1, finf, ov, ac);
-    const float2 tr = df_add2(df_mul_f(df_sub2(as, ac), p.inv_dt), flux);
-    const float2 rr = FIELD == 0 ? df_add2(tr, q) : df_sub2(tr, q);
-    const float r = df_val(rr);
-    float b;
-    if (FIELD == 0) {
-      const float Fv = df_val(ov);
-      diag += p.inv_dt + p.kd + c1 * Fv;
-      b = as.x * p.inv_dt + c1 * Fv * finf;
-    } else {
-      const float fv = df_val(ov);
-      diag += p.inv_dt + c1 * (finf - fv);
-      b = as.x * p.inv_dt + p.kd * fv;
-    }
-    a[c] = df_add(ac, r / diag);
+    const size_t sy = (size_t)L.nx, sz = (size_t)L.nx * L.ny;
+    bool has[6] = {i > 0, i + 1 < L.nx, j > 0, j + 1 < L.ny,
+                   L.geom == SFX_CART3D && k > 0, L.geom == SFX_CART3D && k + 1 < L.nz};
+    const float2 z2 = make_float2(0.0f, 0.0f);
+    float2 nb[6] = {has[0] ? a[c - 1] : z2, has[1] ? a[c + 1] : z2, has[2] ? a[c - sy] : z2,
+                    has[3] ? a[c + sy] : z2, has[4] ? a[c - sz] : z2, has[5] ? a[c + sz] : z2};
+    float B[6] = {has[0] ? Bx[fidx(L, 0, i, j, k)] : 0.0f, has[1] ? Bx[fidx(L, 0, i + 1, j, k)] : 0.0f,
+                  has[2] ? By[fidx(L, 1, i, j, k)] : 0.0f, has[3] ? By[fidx(L, 1, i, j + 1, k)] : 0.0f,
+                  has[4] ? Bz[fidx(L, 2, i, j, k)] : 0.0f, has[5] ? Bz[fidx(L, 2, i, j, k + 1)] : 0.0f};
+    float r, b;
+    a[c] = cell_update32<FIELD>(p, i, a[c], nb, has, B, phi[c], astar[c], other[c], r, b);
     rmax = fabsf(r);
     bmax = fabsf(b);
     if (!(rmax <= 3.0e38f)) rmax = __int_as_float(0x7f800000);  // NaN -> +inf
@@ -201,6 +225,292 @@ __global__ void k_nlgs32(Nl32 p, const float* __restrict__ phi, const float* __r
     rmax = warp_max(rmax);
     bmax = warp_max(bmax);
     if ((threadIdx.x & 31) == 0) {
+      atomicMax(&norms[2 * FIELD], fbits(rmax));
+      atomicMax(&norms[2 * FIELD + 1], fbits(bmax));
+    }
+  }
+}
+
+// ------------------------------------------------------------ fused sweep
+// One full red-black sweep in a single launch.  A block owns a TXxTYxTZ
+// tile; it stages the old state of the tile and a 2-cell halo in shared
+// memory, recomputes the red updates on the tile and a 1-cell halo (red
+// cells depend on old black values only, so every block obtains the same
+// red values), then updates its black cells from the new red values and
+// writes the tile to `aout`.  Bitwise the result of two colour launches.
+template <int FIELD, int TX, int TY, int TZ>
+__global__ void __launch_bounds__(256) k_nlrb32(Nl32 p, const float* __restrict__ phi,
+                                                const float* __restrict__ Bx,
+                                                const float* __restrict__ By,
+                                                const float* __restrict__ Bz,
+                                                const float2* __restrict__ ain,
+                                                float2* __restrict__ aout,
+                                                const float2* __restrict__ astar,
+                                                const float2* __restrict__ other,
+                                                unsigned int* norms) {
+  constexpr int HZ = TZ > 1 ? 2 : 0;           // no z halo in 2D
+  constexpr int SX = TX + 4, SY = TY + 4, SZ = TZ + 2 * HZ;
+  __shared__ float2 sa[SX * SY * SZ];
+  const Level& L = p.L;
+  const int ox = blockIdx.x * TX, oy = blockIdx.y * TY, oz = blockIdx.z * TZ;
+  const int nthr = blockDim.x;
+  const int tid = threadIdx.x;
+  const size_t sy_g = (size_t)L.nx, sz_g = (size_t)L.nx * L.ny;
+  // stage the old state (tile + 2-cell halo)
+  for (int q = tid; q < SX * SY * SZ; q += nthr) {
+    int li = q % SX - 2, lj = (q / SX) % SY - 2, lk = q / (SX * SY) - HZ;
+    int gi = ox + li, gj = oy + lj, gk = oz + lk;
+    float2 v = make_float2(0.0f, 0.0f);
+    if (gi >= 0 && gi < L.nx && gj >= 0 && gj < L.ny && gk >= 0 && gk < L.nz)
+      v = ain[(size_t)gk * sz_g + (size_t)gj * sy_g + gi];
+    sa[q] = v;
+  }
+  __syncthreads();
+  const int HZ1 = TZ > 1 ? 1 : 0;
+  float rmax = 0.0f, bmax = 0.0f;
+  for (int color = 0; color < 2; ++color) {
+    // red: tile + 1-cell halo; black: tile only
+    const int ex = color == 0 ? 1 : 0, ez = color == 0 ? HZ1 : 0;
+    const int RX = TX + 2 * ex, RY = TY + 2 * ex, RZ = TZ + 2 * ez;
+    for (int q = tid; q < RX * RY * RZ; q += nthr) {
+      int li = q % RX - ex, lj = (q / RX) % RY - ex, lk = q / (RX * RY) - ez;
+      int gi = ox + li, gj = oy + lj, gk = oz + lk;
+      if (gi < 0 || gi >= L.nx || gj < 0 || gj >= L.ny || gk < 0 || gk >= L.nz) continue;
+      if (((gi + gj + gk) & 1) != color) continue;
+      const int sc = ((lk + HZ) * SY + (lj + 2)) * SX + (li + 2);
+      const size_t c = (size_t)gk * sz_g + (size_t)gj * sy_g + gi;
+      bool has[6] = {gi > 0, gi + 1 < L.nx, gj > 0, gj + 1 < L.ny, gk > 0, gk + 1 < L.nz};
+      float2 nb[6] = {sa[sc - 1], sa[sc + 1], sa[sc - SX], sa[sc + SX], make_float2(0.f, 0.f),
+                      make_float2(0.f, 0.f)};
+      float B[6];
+      B[0] = has[0] ? Bx[fidx(L, 0, gi, gj, gk)] : 0.0f;
+      B[1] = has[1] ? Bx[fidx(L, 0, gi + 1, gj, gk)] : 0.0f;
+      B[2] = has[2] ? By[fidx(L, 1, gi, gj, gk)] : 0.0f;
+      B[3] = has[3] ? By[fidx(L, 1, gi, gj + 1, gk)] : 0.0f;
+      if (TZ > 1) {
+        nb[4] = sa[sc - SX * SY];
+        nb[5] = sa[sc + SX * SY];
+        B[4] = has[4] ? Bz[fidx(L, 2, gi, gj, gk)] : 0.0f;
+        B[5] = has[5] ? Bz[fidx(L, 2, gi, gj, gk + 1)] : 0.0f;
+      } else {
+        has[4] = has[5] = false;
+        B[4] = B[5] = 0.0f;
+      }
+      float r, b;
+      const float2 nv = cell_update32<FIELD>(p, gi, sa[sc], nb, has, B, phi[c], astar[c],
+                                             other[c], r, b);
+      sa[sc] = nv;   // red cells read only black values, black only red
+      const bool own = li >= 0 && li < TX && lj >= 0 && lj < TY && lk >= 0 && lk < TZ;
+      if (own) {
+        rmax = fmaxf(rmax, fabsf(r));
+        bmax = fmaxf(bmax, fabsf(b));
+        if (!(fabsf(r) <= 3.0e38f)) rmax = __int_as_float(0x7f800000);
+      }
+    }
+    __syncthreads();
+  }
+  // write the tile
+  for (int q = tid; q < TX * TY * TZ; q += nthr) {
+    int li = q % TX, lj = (q / TX) % TY, lk = q / (TX * TY);
+    int gi = ox + li, gj = oy + lj, gk = oz + lk;
+    if (gi >= L.nx || gj >= L.ny || gk >= L.nz) continue;
+    aout[(size_t)gk * sz_g + (size_t)gj * sy_g + gi] = sa[((lk + HZ) * SY + (lj + 2)) * SX + (li + 2)];
+  }
+  if (norms) {
+    rmax = warp_max(rmax);
+    bmax = warp_max(bmax);
+    if ((tid & 31) == 0) {
+      atomicMax(&norms[2 * FIELD], fbits(rmax));
+      atomicMax(&norms[2 * FIELD + 1], fbits(bmax));
+    }
+  }
+}
+
+// 3D sweep marching in z with asynchronous staging.  A block owns a
+// ZTX x ZTY column tile and a chunk of planes [z0, z1).  Shared memory holds
+// a ring of ZNS state planes (old values, 2-cell xy halo) and a ring of ZNC
+// coefficient planes (a*, the other field, phi and the six drift faces of
+// every cell of the tile plus a 1-cell halo).  Step k: copies of state plane
+// k+3 and coefficient plane k+2 are issued with cp.async; meanwhile the red
+// cells of plane k+1 (tile + halo; they read old black values only) and
+// then the black cells of plane k (they read the new red values of planes
+// k-1..k+1) are updated from shared memory, and plane k of the tile is
+// written out.  Bitwise the result of two colour launches.
+constexpr int ZTX = 64, ZTY = 8;
+constexpr int ZSX = ZTX + 4, ZSY = ZTY + 4;      // state plane with 2-cell halo
+constexpr int ZCX = ZTX + 2, ZCY = ZTY + 2;      // coefficient plane, 1-cell halo
+constexpr int ZNS = 5, ZNC = 3;
+
+struct ZCoef {
+  float2 as[ZCY][ZCX];
+  float2 ot[ZCY][ZCX];
+  float ph[ZCY][ZCX];
+  float bx[ZCY][ZCX + 1];   // x-face on the minus side of cell x (x+1: plus side)
+  float by[ZCY + 1][ZCX];   // y-face on the minus side of row y
+  float bzl[ZCY][ZCX];      // z-faces below and above the plane
+  float bzh[ZCY][ZCX];
+};
+
+struct ZSmem {
+  float2 st[ZNS][ZSY][ZSX];
+  ZCoef cf[ZNC];
+};
+
+__device__ __forceinline__ void cp_async4(void* dst, const void* src) {
+  unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async8(void* dst, const void* src) {
+  unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
+template <int FIELD>
+__global__ void __launch_bounds__(256) k_nlrb32_z(Nl32 p, const float* __restrict__ phi,
+                                                  const float* __restrict__ Bx,
+                                                  const float* __restrict__ By,
+                                                  const float* __restrict__ Bz,
+                                                  const float2* __restrict__ ain,
+                                                  float2* __restrict__ aout,
+                                                  const float2* __restrict__ astar,
+                                                  const float2* __restrict__ other, int zchunk,
+                                                  unsigned int* norms) {
+  extern __shared__ __align__(16) unsigned char zsm_raw[];
+  ZSmem& S = *reinterpret_cast<ZSmem*>(zsm_raw);
+  const Level& L = p.L;
+  const int ox = blockIdx.x * ZTX, oy = blockIdx.y * ZTY;
+  const int z0 = blockIdx.z * zchunk, z1 = min(z0 + zchunk, L.nz);
+  const int tid = threadIdx.x, nth = blockDim.x;
+  const size_t pl = (size_t)L.nx * L.ny;
+  float rmax = 0.0f, bmax = 0.0f;
+
+  auto sslot = [](int gk) { return (gk + 4 * ZNS) % ZNS; };
+  auto cslot = [](int gk) { return (gk + 4 * ZNC) % ZNC; };
+
+  // issue the copies of state plane gk (zeros outside the domain)
+  auto stage_state = [&](int gk) {
+    if (gk < 0 || gk >= L.nz) return;
+    float2(*st)[ZSX] = S.st[sslot(gk)];
+    for (int q = tid; q < ZSX * ZSY; q += nth) {
+      int x = q % ZSX, y = q / ZSX;
+      int gi = ox + x - 2, gj = oy + y - 2;
+      if (gi >= 0 && gi < L.nx && gj >= 0 && gj < L.ny)
+        cp_async8(&st[y][x], &ain[gk * pl + (size_t)gj * L.nx + gi]);
+      else
+        st[y][x] = make_float2(0.0f, 0.0f);
+    }
+  };
+  // issue the copies of coefficient plane gk (tile + 1-cell halo)
+  auto stage_coef = [&](int gk) {
+    if (gk < 0 || gk >= L.nz) return;
+    ZCoef& C = S.cf[cslot(gk)];
+    for (int q = tid; q < ZCX * ZCY; q += nth) {
+      int x = q % ZCX, y = q / ZCX;
+      int gi = ox + x - 1, gj = oy + y - 1;
+      if (gi < 0 || gi >= L.nx || gj < 0 || gj >= L.ny) continue;
+      size_t c = gk * pl + (size_t)gj * L.nx + gi;
+      cp_async8(&C.as[y][x], &astar[c]);
+      cp_async8(&C.ot[y][x], &other[c]);
+      cp_async4(&C.ph[y][x], &phi[c]);
+      cp_async4(&C.bx[y][x], &Bx[fidx(L, 0, gi, gj, gk)]);
+      cp_async4(&C.by[y][x], &By[fidx(L, 1, gi, gj, gk)]);
+      cp_async4(&C.bzl[y][x], &Bz[fidx(L, 2, gi, gj, gk)]);
+      cp_async4(&C.bzh[y][x], &Bz[fidx(L, 2, gi, gj, gk + 1)]);
+      if (x == ZCX - 1 || gi == L.nx - 1) cp_async4(&C.bx[y][x + 1], &Bx[fidx(L, 0, gi + 1, gj, gk)]);
+      if (y == ZCY - 1 || gj == L.ny - 1) cp_async4(&C.by[y + 1][x], &By[fidx(L, 1, gi, gj + 1, gk)]);
+    }
+  };
+  // update one cell of plane gk at tile coordinates (li, lj); sm/s0/sp are
+  // the state planes gk-1, gk, gk+1 and C the coefficients of plane gk
+  auto update = [&](float2 (*sm)[ZSX], float2 (*s0)[ZSX], float2 (*sp)[ZSX], const ZCoef& C,
+                    int gk, int li, int lj, bool own) {
+    const int gi = ox + li, gj = oy + lj;
+    const int x = li + 2, y = lj + 2, cx = li + 1, cy = lj + 1;
+    bool has[6] = {gi > 0, gi + 1 < L.nx, gj > 0, gj + 1 < L.ny, gk > 0, gk + 1 < L.nz};
+    float2 nb[6] = {s0[y][x - 1], s0[y][x + 1], s0[y - 1][x], s0[y + 1][x], sm[y][x], sp[y][x]};
+    float B[6] = {C.bx[cy][cx], C.bx[cy][cx + 1], C.by[cy][cx], C.by[cy + 1][cx], C.bzl[cy][cx],
+                  C.bzh[cy][cx]};
+    float r, b;
+    s0[y][x] = cell_update32<FIELD>(p, gi, s0[y][x], nb, has, B, C.ph[cy][cx], C.as[cy][cx],
+                                    C.ot[cy][cx], r, b);
+    if (own) {
+      rmax = fmaxf(rmax, fabsf(r));
+      bmax = fmaxf(bmax, fabsf(b));
+      if (!(fabsf(r) <= 3.0e38f)) rmax = __int_as_float(0x7f800000);
+    }
+  };
+  // red cells of plane gk on the tile and a 1-cell halo
+  auto red_plane = [&](int gk) {
+    if (gk < 0 || gk >= L.nz) return;
+    const bool own_plane = gk >= z0 && gk < z1;
+    float2(*sm)[ZSX] = S.st[sslot(gk - 1)];
+    float2(*s0)[ZSX] = S.st[sslot(gk)];
+    float2(*sp)[ZSX] = S.st[sslot(gk + 1)];
+    const ZCoef& C = S.cf[cslot(gk)];
+    const int par = (ox - 1 + oy + gk) & 1;   // colour parity of cell (ox-1, oy) ...
+    constexpr int HALF = ZCX / 2, NR = HALF * ZCY;
+    for (int q = tid; q < NR; q += nth) {
+      int lj = q / HALF - 1, gj = oy + lj;
+      int li = -1 + 2 * (q % HALF) + ((par + lj) & 1);   // ... shifted by the row
+      int gi = ox + li;
+      if (li > ZTX || gi < 0 || gi >= L.nx || gj < 0 || gj >= L.ny) continue;
+      update(sm, s0, sp, C, gk, li, lj, own_plane && li >= 0 && li < ZTX && lj >= 0 && lj < ZTY);
+    }
+  };
+  // black cells of plane gk on the tile
+  auto black_plane = [&](int gk) {
+    float2(*sm)[ZSX] = S.st[sslot(gk - 1)];
+    float2(*s0)[ZSX] = S.st[sslot(gk)];
+    float2(*sp)[ZSX] = S.st[sslot(gk + 1)];
+    const ZCoef& C = S.cf[cslot(gk)];
+    const int par = (ox + oy + gk + 1) & 1;
+    constexpr int HALF = ZTX / 2, NB = HALF * ZTY;
+    for (int q = tid; q < NB; q += nth) {
+      int lj = q / HALF, gj = oy + lj;
+      int li = 2 * (q % HALF) + ((par + lj) & 1);
+      int gi = ox + li;
+      if (gi >= L.nx || gj >= L.ny) continue;
+      update(sm, s0, sp, C, gk, li, lj, true);
+    }
+  };
+  auto store_plane = [&](int gk) {
+    float2(*s0)[ZSX] = S.st[sslot(gk)];
+    for (int q = tid; q < ZTX * ZTY; q += nth) {
+      int li = q % ZTX, lj = q / ZTX;
+      int gi = ox + li, gj = oy + lj;
+      if (gi < L.nx && gj < L.ny) aout[gk * pl + (size_t)gj * L.nx + gi] = s0[lj + 2][li + 2];
+    }
+  };
+
+  // prologue: state z0-2..z0+2, coefficients z0-1..z0+1, red of z0-1 and z0
+  for (int d = -2; d <= 2; ++d) stage_state(z0 + d);
+  for (int d = -1; d <= 1; ++d) stage_coef(z0 + d);
+  cp_async_commit();
+  cp_async_wait_all();
+  __syncthreads();
+  red_plane(z0 - 1);
+  __syncthreads();
+  red_plane(z0);
+  __syncthreads();
+  for (int k = z0; k < z1; ++k) {
+    // slots of planes k-2 (state) and k-1 (coefficients) are free now
+    stage_state(k + 3);
+    stage_coef(k + 2);
+    cp_async_commit();
+    red_plane(k + 1);
+    __syncthreads();
+    black_plane(k);
+    __syncthreads();
+    store_plane(k);
+    cp_async_wait_all();
+    __syncthreads();
+  }
+  if (norms) {
+    rmax = warp_max(rmax);
+    bmax = warp_max(bmax);
+    if ((tid & 31) == 0) {
       atomicMax(&norms[2 * FIELD], fbits(rmax));
       atomicMax(&norms[2 * FIELD + 1], fbits(bmax));
     }
@@ -544,6 +854,35 @@ sfx_status sweep32(sfx_ctx* c, int field, const Nl32& p, const float* phi, const
   return SFX_OK;
 }
 
+template <int FIELD>
+sfx_status fused_sweep32(sfx_ctx* c, const Nl32& p, const float* phi, const float* const* B,
+                         const float2* ain, float2* aout, const float2* astar,
+                         const float2* other, bool norms, cudaStream_t s) {
+  const Level& L = p.L;
+  unsigned int* nb = norms ? (unsigned int*)c->d_norms : nullptr;
+  if (L.geom == SFX_CART3D) {
+    const int zchunk = c->f32.zchunk;
+    static bool attr_set[2] = {false, false};
+    if (!attr_set[FIELD]) {
+      SFX_CUDA(cudaFuncSetAttribute(k_nlrb32_z<FIELD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)sizeof(ZSmem)));
+      attr_set[FIELD] = true;
+    }
+    dim3 grd((unsigned)((L.nx + ZTX - 1) / ZTX), (unsigned)((L.ny + ZTY - 1) / ZTY),
+             (unsigned)((L.nz + zchunk - 1) / zchunk));
+    prof_before(c, K_SMOOTH_FINE, s);
+    k_nlrb32_z<FIELD><<<grd, 256, sizeof(ZSmem), s>>>(p, phi, B[0], B[1], B[2], ain, aout, astar,
+                                                       other, zchunk, nb);
+    prof_after(c, K_SMOOTH_FINE, s);
+  } else {
+    dim3 grd((unsigned)((L.nx + 31) / 32), (unsigned)((L.ny + 15) / 16), 1);
+    SFX_KERNEL(c, K_SMOOTH_FINE, (k_nlrb32<FIELD, 32, 16, 1>), grd, 256, s, p, phi, B[0], B[1],
+               B[2], ain, aout, astar, other, nb);
+  }
+  SFX_LAUNCH_CHECK();
+  return SFX_OK;
+}
+
 }  // namespace
 
 sfx_status f32_ensure_scratch(sfx_ctx* c);
@@ -581,18 +920,36 @@ sfx_status step_f32(sfx_ctx* c, const sfx_params* pr, const float* phi, const fl
   Nl32 pF = pf;
   pF.Doh = (float)(pr->DF / L.h);
   const int sweeps = o->nu1 + o->nu2;
+  // current and spare buffers of each field (the fused sweep ping-pongs)
+  float2 *fc = f, *fo = c->f32.falt, *Fc = F, *Fo = c->f32.Falt;
   int it = 0;
   bool conv = false;
   float nrm[4] = {0, 0, 0, 0};
+  // Convergence is tested on the host, which stalls the stream; the step
+  // first runs as many iterations as the previous step needed (minus one,
+  // to keep probing downwards) without testing, then tests every
+  // check_every iterations.
+  const int first = std::min(std::max(c->f32.predicted, 1), o->max_cycles);
   for (it = 1; it <= o->max_cycles; ++it) {
-    const bool check = (it % o->check_every == 0) || it == o->max_cycles;
+    const bool check = (it >= first && (it - first) % o->check_every == 0) ||
+                       it == o->max_cycles;
     if (check) SFX_CUDA(cudaMemsetAsync(c->d_norms, 0, 8 * sizeof(unsigned long long), s));
     for (int q = 0; q < sweeps; ++q) {
-      st = sweep32(c, 0, pf, phi, Bf, f, fs, F, check && q == 0, s);
+      if (c->f32.fused) {
+        st = fused_sweep32<0>(c, pf, phi, Bf, fc, fo, fs, Fc, check && q == 0, s);
+        std::swap(fc, fo);
+      } else {
+        st = sweep32(c, 0, pf, phi, Bf, fc, fs, Fc, check && q == 0, s);
+      }
       if (st != SFX_OK) return st;
     }
     for (int q = 0; q < sweeps; ++q) {
-      st = sweep32(c, 1, pF, phi, BF, F, Fs, f, check && q == 0, s);
+      if (c->f32.fused) {
+        st = fused_sweep32<1>(c, pF, phi, BF, Fc, Fo, Fs, fc, check && q == 0, s);
+        std::swap(Fc, Fo);
+      } else {
+        st = sweep32(c, 1, pF, phi, BF, Fc, Fs, fc, check && q == 0, s);
+      }
       if (st != SFX_OK) return st;
     }
     if (check) {
@@ -610,6 +967,9 @@ sfx_status step_f32(sfx_ctx* c, const sfx_params* pr, const float* phi, const fl
       }
     }
   }
+  c->f32.predicted = conv ? (it == first ? it - 1 : it) : 0;
+  if (fc != f) SFX_CUDA(cudaMemcpyAsync(f, fc, n * sizeof(float2), cudaMemcpyDeviceToDevice, s));
+  if (Fc != F) SFX_CUDA(cudaMemcpyAsync(F, Fc, n * sizeof(float2), cudaMemcpyDeviceToDevice, s));
   if (stats) {
     stats->picard = it > o->max_cycles ? o->max_cycles : it;
     stats->vcycles = 2 * stats->picard * sweeps;
@@ -705,6 +1065,8 @@ sfx_status f32_ensure_scratch(sfx_ctx* c) {
   if ((st = get(n * sizeof(float2), (void**)&c->f32.fstar)) != SFX_OK) return st;
   if ((st = get(n * sizeof(float2), (void**)&c->f32.Fstar)) != SFX_OK) return st;
   if ((st = get(n * sizeof(float), (void**)&c->f32.dsig)) != SFX_OK) return st;
+  if ((st = get(n * sizeof(float2), (void**)&c->f32.falt)) != SFX_OK) return st;
+  if ((st = get(n * sizeof(float2), (void**)&c->f32.Falt)) != SFX_OK) return st;
   c->f32.ready = true;
   return SFX_OK;
 }

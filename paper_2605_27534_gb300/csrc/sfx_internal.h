@@ -38,6 +38,11 @@ struct F32Scratch {
   float2* fstar = nullptr;
   float2* Fstar = nullptr;
   float* dsig = nullptr;   // sigma - sigma0
+  int predicted = 0;       // Picard iterations to run before the first check
+  float2* falt = nullptr;  // ping-pong partners of f and F for fused sweeps
+  float2* Falt = nullptr;
+  bool fused = true;       // one launch per red-black sweep
+  int zchunk = 32;         // planes per block of the 3D fused sweep
 };
 
 struct Prof {

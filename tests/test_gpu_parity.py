@@ -237,6 +237,26 @@ def test_surfactant_step_parity_fp32(sfx, name):
         assert abs(stt.mass_f + stt.mass_F - M0) < MASS_DRIFT * abs(M0)
 
 
+@pytest.mark.parametrize("name", ["adsorption2d", "hr3d", "axi"])
+def test_fused_sweep_equals_colour_launches_bitwise(sfx, name):
+    import torch
+    c, ux, uy, uz = _step_case(name)
+    g, p = c.grid, c.params
+    _, phi, delta = oracle.phase_field_build(g, c.C, c.redist_iters, c.dtau, p.eps)
+    outs = []
+    for fused in (1, 0):
+        ctx = _ctx(sfx, g, 1)
+        ctx.sfx_set_tuning(sfx._lib.SFX_TUNE_FUSED_SWEEP, fused)
+        f, F = _pairs(ctx, 0.2 * delta), _pairs(ctx, c.F0)
+        u = [None if v is None else dev(v, torch.float32) for v in (ux, uy, uz)]
+        o = sfx.default_opts(tol=1e-10, nu1=1, nu2=0)
+        for _ in range(2):
+            ctx.sfx_surfactant_step(p, ctx.sfx_phi_fold(dev(phi)), f, F, c.dt, *u, opts=o)
+        torch.cuda.synchronize()
+        outs.append((f.cpu().numpy().copy(), F.cpu().numpy().copy()))
+    assert np.array_equal(outs[0][0], outs[1][0]) and np.array_equal(outs[0][1], outs[1][1])
+
+
 def test_fp32_mass_drift_over_many_steps(sfx):
     """Closed box, 100 steps of the 2D adsorption physics at tol 1e-10:
     the double-float state keeps sum V (f + F) to 1e-10."""
