@@ -75,9 +75,15 @@ def algorithmic_bytes(kind, grid, wbytes):
     if kind == "smooth_fine":
         if wbytes == 8:
             return 8.0 * (2.5 + d) * N
-        # fused FP32 sweep (both colours in one launch): a in/out, a*, other
-        # field (8 B each), phi, d float face arrays
-        return (36.0 + 4.0 * d) * N
+        # coupled correction colour sweep (k_corr2_32): both corrections (all
+        # cells, as neighbours: 8 B), the 2x2 coefficients and residuals of
+        # the updated half (24 B x 1/2), the 2 d float drift-face arrays of
+        # both fields, write the updated half of both corrections
+        return (8.0 + 12.0 + 8.0 * d + 4.0) * N
+    if kind == "residual" and wbytes == 4:
+        # k_resid2_32: f, F, f*, F* (pairs), both corrections, phi, 2 d faces;
+        # writes f, F, the 2x2 coefficients and the residuals
+        return (32.0 + 8.0 + 4.0 + 8.0 * d + 16.0 + 16.0 + 8.0) * N
     if kind == "advect":
         return 16.0 * N + wbytes * d * N
     return None
@@ -222,8 +228,9 @@ def run_gpu(a, case, rank, world, local_rank):
     sigma = torch.empty(g.shape, dtype=wdt, device=dev)
     force = torch.empty((3,) + g.shape, dtype=wdt, device=dev)
     opts = sfx.default_opts(tol=a.tol, max_cycles=200)
-    if prec == sfx.SFX_F32:   # one nonlinear red-black sweep per field per Picard iteration
-        opts.nu1, opts.nu2 = 1, 0
+    if prec == sfx.SFX_F32:   # three coupled correction sweeps per Newton iteration
+        opts.nu1, opts.nu2 = 3, 0
+        ctx.sfx_set_tuning(sfx._lib.SFX_TUNE_REUSE_DRIFT, 1)   # the interface is static
     stats = []
 
     def step():
@@ -305,7 +312,15 @@ def run_gpu(a, case, rank, world, local_rank):
                 "algorithmic_bytes_per_launch": ab, "avg_launch_ms": avg_s * 1e3,
                 "peak_source": "%s (MEASURED_PEAKS.json hbm_gbs)" % peak_src}
     launches = int(sum(v[0] for v in prof.values()))
-    breakdown = {k: {"launches": v[0], "ms": round(v[1], 3)} for k, v in prof.items() if v[0]}
+    breakdown = {}
+    for k, v in prof.items():
+        if not v[0]:
+            continue
+        e = {"launches": v[0], "ms": round(v[1], 3)}
+        b = algorithmic_bytes(k, g, wbytes)
+        if b is not None and v[2] > 0:
+            e["gbs"] = round(b / (v[1] * 1e-3 / v[2]) / 1e9, 1)
+        breakdown[k] = e
     cpu = None
     if not a.no_cpu:
         rate, secs, gs = oracle_rate(case, a.oracle_steps, a.tol)

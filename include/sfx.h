@@ -224,9 +224,25 @@ sfx_status sfx_cfl_dt(sfx_ctx* ctx, const void* ux, const void* uy,
 /* Tuning knobs (same results, different schedules).  Returns SFX_ERR_ARG
    for an unknown key or value. */
 typedef enum {
-  SFX_TUNE_FUSED_SWEEP = 0  /* SFX_F32: 1 (default) = one launch per
-                               red-black sweep through shared-memory tiles;
-                               0 = one launch per colour.  Bitwise equal. */
+  SFX_TUNE_FUSED_SWEEP = 0, /* SFX_F32, solver 0: 1 (default) = one launch
+                               per red-black sweep through shared-memory
+                               tiles; 0 = one launch per colour.  Bitwise
+                               equal. */
+  SFX_TUNE_F32_SOLVER = 1,  /* SFX_F32: 1 (default) = coupled Newton defect
+                               correction: one pair-arithmetic pass
+                               evaluates both residuals and the pointwise
+                               2x2 exchange Jacobian, then nu1 + nu2 FP32
+                               red-black sweeps with a 2x2 solve per cell
+                               relax the correction; 2 = the same with the
+                               fields linearised alternately (Picard);
+                               0 = nonlinear red-black sweeps on the pair
+                               state.  Same fixed point, same test. */
+  SFX_TUNE_REUSE_DRIFT = 2  /* SFX_F32: 1 = keep the drift faces of the
+                               last step while phi's pointer, Df, DF and
+                               eps are unchanged (for a static interface;
+                               after writing phi in place, set the knob
+                               again to force a rebuild); 0 (default) =
+                               rebuild them every step. */
 } sfx_tune_key;
 sfx_status sfx_set_tuning(sfx_ctx* ctx, int key, int value);
 

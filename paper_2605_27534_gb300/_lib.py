@@ -25,6 +25,8 @@ EXPORTS = [
     "sfx_phi_fold", "sfx_set_tuning",
 ]
 SFX_TUNE_FUSED_SWEEP = 0
+SFX_TUNE_F32_SOLVER = 1
+SFX_TUNE_REUSE_DRIFT = 2
 KERNEL_KINDS = ["smooth_fine", "smooth_coarse", "restrict", "prolong", "setup", "residual",
                 "advect", "totals", "forces", "phase", "other"]
 

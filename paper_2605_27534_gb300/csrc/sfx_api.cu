@@ -145,6 +145,8 @@ void sfx_default_opts(sfx_solve_opts* o) {
 void sfx_ctx_destroy(sfx_ctx* c) {
   if (!c) return;
   for (cudaEvent_t e : c->prof.ev) cudaEventDestroy(e);
+  for (cudaEvent_t e : c->f32.ev)
+    if (e) cudaEventDestroy(e);
   for (void* p : c->allocations) cudaFree(p);
   if (c->h_norms) cudaFreeHost(c->h_norms);
   if (c->h_sums) cudaFreeHost(c->h_sums);
@@ -274,6 +276,16 @@ sfx_status sfx_set_tuning(sfx_ctx* c, int key, int value) {
   if (!c) return SFX_ERR_ARG;
   if (key == SFX_TUNE_FUSED_SWEEP && (value == 0 || value == 1)) {
     c->f32.fused = value == 1;
+    return SFX_OK;
+  }
+  if (key == SFX_TUNE_REUSE_DRIFT && (value == 0 || value == 1)) {
+    c->f32.reuse_drift = value == 1;
+    c->f32.drift_phi = nullptr;
+    return SFX_OK;
+  }
+  if (key == SFX_TUNE_F32_SOLVER && value >= 0 && value <= 2) {
+    c->f32.solver = value;
+    c->f32.predicted = 0;
     return SFX_OK;
   }
   return SFX_ERR_ARG;

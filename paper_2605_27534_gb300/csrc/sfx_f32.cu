@@ -231,6 +231,348 @@ __global__ void k_nlgs32(Nl32 p, const float* __restrict__ phi, const float* __r
   }
 }
 
+// ------------------------------------------------------------ defect correction
+// The App. C system is solved by defect correction: a streaming pass
+// applies the previous correction (a <- a + e, pair arithmetic) and
+// evaluates the exact residual r of the new state in pair arithmetic, with
+// lambda, the diagonal of the linearised (Picard) problem; FP32 red-black
+// Gauss-Seidel sweeps then solve  A e = r,  A e = lambda e - (1/V) sum +-A G(e),
+// G(e) = D (e_R - e_L)/h + B e_up.  Convergence is tested on the exact
+// residual of the current state.
+template <int FIELD>
+__global__ void k_resid32(Nl32 p, const float* __restrict__ phi, const float* __restrict__ Bx,
+                          const float* __restrict__ By, const float* __restrict__ Bz,
+                          const float2* __restrict__ ain, const float* __restrict__ e,
+                          float2* __restrict__ aout, const float2* __restrict__ astar,
+                          const float2* __restrict__ other, float* __restrict__ rr,
+                          float* __restrict__ lam, unsigned int* norms) {
+  const Level& L = p.L;
+  const size_t n = L.ncell();
+  const size_t sy = (size_t)L.nx, sz = (size_t)L.nx * L.ny;
+  float rmax = 0.0f, bmax = 0.0f;
+  for (size_t c = blockIdx.x * (size_t)blockDim.x + threadIdx.x; c < n;
+       c += (size_t)gridDim.x * blockDim.x) {
+    const int i = (int)(c % L.nx), j = (int)((c / L.nx) % L.ny), k = (int)(c / sz);
+    bool has[6] = {i > 0, i + 1 < L.nx, j > 0, j + 1 < L.ny,
+                   L.geom == SFX_CART3D && k > 0, L.geom == SFX_CART3D && k + 1 < L.nz};
+    const size_t nbi[6] = {c - 1, c + 1, c - sy, c + sy, c - sz, c + sz};
+    float2 nb[6];
+#pragma unroll
+    for (int q = 0; q < 6; ++q) {
+      nb[q] = make_float2(0.0f, 0.0f);
+      if (has[q]) nb[q] = e ? df_add(ain[nbi[q]], e[nbi[q]]) : ain[nbi[q]];
+    }
+    const float2 ac = e ? df_add(ain[c], e[c]) : ain[c];
+    float B[6] = {has[0] ? Bx[fidx(L, 0, i, j, k)] : 0.0f, has[1] ? Bx[fidx(L, 0, i + 1, j, k)] : 0.0f,
+                  has[2] ? By[fidx(L, 1, i, j, k)] : 0.0f, has[3] ? By[fidx(L, 1, i, j + 1, k)] : 0.0f,
+                  has[4] ? Bz[fidx(L, 2, i, j, k)] : 0.0f, has[5] ? Bz[fidx(L, 2, i, j, k + 1)] : 0.0f};
+    // residual and the kinetic part of the diagonal
+    float r, b;
+    const PhiPair ph = unfold(phi[c]);
+    const float c1 = __fdividef(p.ka, ph.p + p.eta);
+    const float finf = p.ginf * ph.p * ph.q * p.inv_eps;
+    const float ov = __fadd_rn(other[c].x, other[c].y);
+    cell_update32<FIELD>(p, i, ac, nb, has, B, phi[c], astar[c], other[c], r, b);
+    aout[c] = ac;
+    rr[c] = r;
+    lam[c] = FIELD == 0 ? p.inv_dt + p.kd + c1 * ov : p.inv_dt + c1 * (finf - ov);
+    rmax = fmaxf(rmax, fabsf(r));
+    bmax = fmaxf(bmax, fabsf(b));
+    if (!(fabsf(r) <= 3.0e38f)) rmax = __int_as_float(0x7f800000);
+  }
+  if (norms) {
+    rmax = warp_max(rmax);
+    bmax = warp_max(bmax);
+    if ((threadIdx.x & 31) == 0) {
+      atomicMax(&norms[2 * FIELD], fbits(rmax));
+      atomicMax(&norms[2 * FIELD + 1], fbits(bmax));
+    }
+  }
+}
+
+struct Corr32 {
+  Level L;
+  float invh, Doh;
+  int literal;
+};
+
+// One colour of FP32 red-black Gauss-Seidel on A e = r.
+__global__ void k_corr32(Corr32 p, const float* __restrict__ Bx, const float* __restrict__ By,
+                         const float* __restrict__ Bz, const float* __restrict__ rr,
+                         const float* __restrict__ lam, float* __restrict__ e, int color,
+                         int first) {
+  const Level& L = p.L;
+  const int j = blockIdx.y, k = blockIdx.z;
+  const int i = 2 * (blockIdx.x * blockDim.x + threadIdx.x) + ((j + k + color) & 1);
+  if (i >= L.nx) return;
+  const size_t c = cidx(L, i, j, k);
+  const size_t sy = (size_t)L.nx, sz = (size_t)L.nx * L.ny;
+  // the first red colour starts from e = 0 (no neighbour has been updated)
+  const bool zero_nb = first && color == 0;
+  bool has[6] = {i > 0, i + 1 < L.nx, j > 0, j + 1 < L.ny,
+                 L.geom == SFX_CART3D && k > 0, L.geom == SFX_CART3D && k + 1 < L.nz};
+  const size_t nbi[6] = {c - 1, c + 1, c - sy, c + sy, c - sz, c + sz};
+  const float B[6] = {has[0] ? Bx[fidx(L, 0, i, j, k)] : 0.0f, has[1] ? Bx[fidx(L, 0, i + 1, j, k)] : 0.0f,
+                      has[2] ? By[fidx(L, 1, i, j, k)] : 0.0f, has[3] ? By[fidx(L, 1, i, j + 1, k)] : 0.0f,
+                      has[4] ? Bz[fidx(L, 2, i, j, k)] : 0.0f, has[5] ? Bz[fidx(L, 2, i, j, k + 1)] : 0.0f};
+  // in the first sweep every cell starts at zero (the array holds the
+  // previous iteration's correction until a colour overwrites it)
+  const float ec = first ? 0.0f : e[c];
+  float S = 0.0f, dg = 0.0f;
+#pragma unroll
+  for (int q = 0; q < 6; ++q) {
+    if (!has[q]) continue;
+    const bool plus = q & 1;
+    const bool upL = p.literal ? (B[q] > 0.0f) : (B[q] < 0.0f);
+    float w = 1.0f;
+    if (L.geom == SFX_AXISYM) w = q < 2 ? wr_face(L.geom, i + (plus ? 1 : 0)) : (q < 4 ? wz_face(L.geom, i) : 1.0f);
+    const float en = zero_nb ? 0.0f : e[nbi[q]];
+    const float eL = plus ? ec : en, eR = plus ? en : ec;
+    const float G = p.Doh * (eR - eL) + B[q] * (upL ? eL : eR);
+    if (plus) {
+      S += w * G;
+      dg += w * (p.Doh - (upL ? B[q] : 0.0f));
+    } else {
+      S -= w * G;
+      dg += w * (p.Doh + (upL ? 0.0f : B[q]));
+    }
+  }
+  const float wc = wz_face(L.geom, i);
+  const float flux = S * p.invh / wc, dflux = dg * p.invh / wc;
+  const float l = lam[c];
+  const float rho = rr[c] + flux - l * ec;
+  e[c] = ec + __fdividef(rho, l + dflux);
+}
+
+// ------------------------------------------------------------ coupled Newton
+// Newton form of the defect correction: the residual pass evaluates both
+// residuals at a common state (one shared exchange term q) together with the
+// pointwise 2x2 Jacobian of the exchange, and the correction
+//   [A_f + lam_f   -j_fF ] [e_f]   [r_f]
+//   [-j_Ff   A_F + lam_F ] [e_F] = [r_F]
+// (A = flux operator, lam_f = 1/dt + r_d + c1 F, lam_F = 1/dt + c1 (f_inf - f),
+//  j_fF = c1 (f_inf - f), j_Ff = c1 F + r_d, c1 = r_a/(phi + eta))
+// is relaxed by red-black Gauss-Seidel with a 2x2 solve per cell.  The
+// alternating (Picard) linearisation converges slowly where c1 dt >> 1;
+// the coupled one does not.
+struct Nw32 {
+  Level L;
+  float invh, Dfh, DFh, inv_dt, ka, kd, ginf, inv_eps, eta;
+  int literal;
+};
+
+__device__ __forceinline__ void gather6(const Level& L, int i, int j, int k, size_t c,
+                                        bool* has, size_t* nbi) {
+  const size_t sy = (size_t)L.nx, sz = (size_t)L.nx * L.ny;
+  has[0] = i > 0; has[1] = i + 1 < L.nx; has[2] = j > 0; has[3] = j + 1 < L.ny;
+  has[4] = L.geom == SFX_CART3D && k > 0; has[5] = L.geom == SFX_CART3D && k + 1 < L.nz;
+  nbi[0] = c - 1; nbi[1] = c + 1; nbi[2] = c - sy; nbi[3] = c + sy; nbi[4] = c - sz; nbi[5] = c + sz;
+}
+
+__device__ __forceinline__ void faces6(const Level& L, const float* Bx, const float* By,
+                                       const float* Bz, int i, int j, int k, const bool* has,
+                                       float* B) {
+  B[0] = has[0] ? Bx[fidx(L, 0, i, j, k)] : 0.0f;
+  B[1] = has[1] ? Bx[fidx(L, 0, i + 1, j, k)] : 0.0f;
+  B[2] = has[2] ? By[fidx(L, 1, i, j, k)] : 0.0f;
+  B[3] = has[3] ? By[fidx(L, 1, i, j + 1, k)] : 0.0f;
+  B[4] = has[4] ? Bz[fidx(L, 2, i, j, k)] : 0.0f;
+  B[5] = has[5] ? Bz[fidx(L, 2, i, j, k + 1)] : 0.0f;
+}
+
+// (1/V) sum +-A G of one field around cell i as an unnormalised pair, and
+// the derivative of that sum in the cell value (negated: diagonal weight).
+__device__ __forceinline__ float2 flux_pair(const Level& L, float invh, float Doh, int literal,
+                                            int i, float2 ac, const float2* nb, const bool* has,
+                                            const float* B, float& dflux) {
+  Acc S{0.0f, 0.0f};
+  float dg = 0.0f;
+#pragma unroll
+  for (int q = 0; q < 6; ++q) {
+    if (!has[q]) continue;
+    const bool plus = q & 1;
+    const bool upL = literal ? (B[q] > 0.0f) : (B[q] < 0.0f);
+    float w = 1.0f;
+    if (L.geom == SFX_AXISYM) w = q < 2 ? wr_face(L.geom, i + (plus ? 1 : 0)) : (q < 4 ? wz_face(L.geom, i) : 1.0f);
+    float2 G = plus ? face_G(Doh, B[q], upL, ac, nb[q]) : face_G(Doh, B[q], upL, nb[q], ac);
+    if (L.geom == SFX_AXISYM) G = lp_mul(G, w);
+    if (plus) {
+      acc_add(S, G);
+      dg += w * (Doh - (upL ? B[q] : 0.0f));
+    } else {
+      acc_sub(S, G);
+      dg += w * (Doh + (upL ? 0.0f : B[q]));
+    }
+  }
+  const float wc = wz_face(L.geom, i);
+  float2 flux = lp_mul(acc_get(S), invh);
+  dflux = dg * invh;
+  if (L.geom == SFX_AXISYM) {
+    flux = df_div_f(ef_fast_two_sum(flux.x, flux.y), wc);
+    dflux = __fdividef(dflux, wc);
+  }
+  return flux;
+}
+
+// Evaluate both residuals (pairs), the 2x2 exchange Jacobian and the
+// norms at every cell of the current state.
+__global__ void __launch_bounds__(256, 4)
+k_resid2_32(Nw32 p, const float* __restrict__ phi, const float* __restrict__ Bfx,
+            const float* __restrict__ Bfy, const float* __restrict__ Bfz,
+            const float* __restrict__ BFx, const float* __restrict__ BFy,
+            const float* __restrict__ BFz, const float2* __restrict__ fin,
+            const float2* __restrict__ Fin, const float2* __restrict__ fst,
+            const float2* __restrict__ Fst, float4* __restrict__ coef,
+            float2* __restrict__ res, unsigned int* norms) {
+  const Level& L = p.L;
+  const size_t n = L.ncell();
+  float m[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+  for (size_t c = blockIdx.x * (size_t)blockDim.x + threadIdx.x; c < n;
+       c += (size_t)gridDim.x * blockDim.x) {
+    const int i = (int)(c % L.nx), j = (int)((c / L.nx) % L.ny), k = (int)(c / ((size_t)L.nx * L.ny));
+    bool has[6];
+    size_t nbi[6];
+    gather6(L, i, j, k, c, has, nbi);
+    float2 nb[6];
+    const float2 fc = fin[c], Fc = Fin[c];
+    float B[6], df_, dF_;
+#pragma unroll
+    for (int q = 0; q < 6; ++q) nb[q] = has[q] ? fin[nbi[q]] : make_float2(0.0f, 0.0f);
+    faces6(L, Bfx, Bfy, Bfz, i, j, k, has, B);
+    const float2 flf = flux_pair(L, p.invh, p.Dfh, p.literal, i, fc, nb, has, B, df_);
+#pragma unroll
+    for (int q = 0; q < 6; ++q) nb[q] = has[q] ? Fin[nbi[q]] : make_float2(0.0f, 0.0f);
+    faces6(L, BFx, BFy, BFz, i, j, k, has, B);
+    const float2 flF = flux_pair(L, p.invh, p.DFh, p.literal, i, Fc, nb, has, B, dF_);
+    // exchange q = c1 F (f_inf - f) - r_d f, one evaluation for both equations
+    const PhiPair ph = unfold(phi[c]);
+    const float c1 = __fdividef(p.ka, ph.p + p.eta);
+    const float finf = p.ginf * ph.p * ph.q * p.inv_eps;
+    float2 fd = ef_two_sum(finf, -fc.x);
+    fd.y = __fsub_rn(fd.y, fc.y);
+    const float pr = __fmul_rn(Fc.x, fd.x);
+    const float2 FF = make_float2(pr, fmaf(Fc.y, fd.x, fmaf(Fc.x, fd.y, fmaf(Fc.x, fd.x, -pr))));
+    const float2 ads = lp_mul(FF, c1), des = lp_mul(fc, p.kd);
+    Acc q{0.0f, 0.0f};
+    acc_add(q, ads);
+    acc_sub(q, des);
+    const float2 qq = acc_get(q);
+    const float2 fs = fst[c], Fs = Fst[c];
+    Acc Rf{0.0f, 0.0f}, RF{0.0f, 0.0f};
+    acc_add(Rf, lp_mul(lp_sub(fs, fc), p.inv_dt));
+    acc_add(Rf, flf);
+    acc_add(Rf, qq);
+    acc_add(RF, lp_mul(lp_sub(Fs, Fc), p.inv_dt));
+    acc_add(RF, flF);
+    acc_sub(RF, qq);
+    const float rf = __fadd_rn(Rf.hi, Rf.lo), rF = __fadd_rn(RF.hi, RF.lo);
+    const float Fv = __fadd_rn(Fc.x, Fc.y), fv = __fadd_rn(fc.x, fc.y);
+    // diagonals (kinetic part) and couplings of the linearised system
+    coef[c] = make_float4(p.inv_dt + p.kd + c1 * Fv, p.inv_dt + c1 * (finf - fv),
+                          c1 * (finf - fv), c1 * Fv + p.kd);
+    res[c] = make_float2(rf, rF);
+    m[0] = fmaxf(m[0], fabsf(rf));
+    m[1] = fmaxf(m[1], fabsf(fs.x * p.inv_dt + c1 * Fv * finf));
+    m[2] = fmaxf(m[2], fabsf(rF));
+    m[3] = fmaxf(m[3], fabsf(Fs.x * p.inv_dt + p.kd * fv));
+    if (!(fabsf(rf) <= 3.0e38f) || !(fabsf(rF) <= 3.0e38f)) m[0] = m[2] = __int_as_float(0x7f800000);
+  }
+  if (norms) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      float v = warp_max(m[q]);
+      if ((threadIdx.x & 31) == 0) atomicMax(&norms[q], fbits(v));
+    }
+  }
+}
+
+// linear flux of a correction field (FP32) and its diagonal weight
+__device__ __forceinline__ float flux_lin(const Level& L, float invh, float Doh, int literal,
+                                          int i, float ec, const float* en, const bool* has,
+                                          const float* B, float& dflux) {
+  float S = 0.0f, dg = 0.0f;
+#pragma unroll
+  for (int q = 0; q < 6; ++q) {
+    if (!has[q]) continue;
+    const bool plus = q & 1;
+    const bool upL = literal ? (B[q] > 0.0f) : (B[q] < 0.0f);
+    float w = 1.0f;
+    if (L.geom == SFX_AXISYM) w = q < 2 ? wr_face(L.geom, i + (plus ? 1 : 0)) : (q < 4 ? wz_face(L.geom, i) : 1.0f);
+    const float eL = plus ? ec : en[q], eR = plus ? en[q] : ec;
+    const float G = Doh * (eR - eL) + B[q] * (upL ? eL : eR);
+    if (plus) { S += w * G; dg += w * (Doh - (upL ? B[q] : 0.0f)); }
+    else { S -= w * G; dg += w * (Doh + (upL ? 0.0f : B[q])); }
+  }
+  const float s = invh / wz_face(L.geom, i);
+  dflux = dg * s;
+  return S * s;
+}
+
+// One colour of the coupled red-black Gauss-Seidel on the correction.
+__global__ void k_corr2_32(Nw32 p, const float* __restrict__ Bfx, const float* __restrict__ Bfy,
+                           const float* __restrict__ Bfz, const float* __restrict__ BFx,
+                           const float* __restrict__ BFy, const float* __restrict__ BFz,
+                           const float4* __restrict__ coef, const float2* __restrict__ res,
+                           float* __restrict__ ef, float* __restrict__ eF, int color, int first,
+                           float2* __restrict__ fst, float2* __restrict__ Fst) {
+  const Level& L = p.L;
+  const int j = blockIdx.y, k = blockIdx.z;
+  const int i = 2 * (blockIdx.x * blockDim.x + threadIdx.x) + ((j + k + color) & 1);
+  if (i >= L.nx) {
+    // a row of odd length: the last red cell has no black partner
+    const int ir = i ^ 1;
+    if (fst && ir < L.nx) {
+      const size_t cr = cidx(L, ir, j, k);
+      fst[cr] = df_add(fst[cr], ef[cr]);
+      Fst[cr] = df_add(Fst[cr], eF[cr]);
+    }
+    return;
+  }
+  const size_t c = cidx(L, i, j, k);
+  bool has[6];
+  size_t nbi[6];
+  gather6(L, i, j, k, c, has, nbi);
+  // every cell starts at zero in the first sweep
+  const bool zero_nb = first && color == 0;
+  float enf[6], enF[6];
+#pragma unroll
+  for (int q = 0; q < 6; ++q) {
+    enf[q] = (has[q] && !zero_nb) ? ef[nbi[q]] : 0.0f;
+    enF[q] = (has[q] && !zero_nb) ? eF[nbi[q]] : 0.0f;
+  }
+  const float efc = first ? 0.0f : ef[c], eFc = first ? 0.0f : eF[c];
+  float B[6], dgf, dgF;
+  faces6(L, Bfx, Bfy, Bfz, i, j, k, has, B);
+  const float flf = flux_lin(L, p.invh, p.Dfh, p.literal, i, efc, enf, has, B, dgf);
+  faces6(L, BFx, BFy, BFz, i, j, k, has, B);
+  const float flF = flux_lin(L, p.invh, p.DFh, p.literal, i, eFc, enF, has, B, dgF);
+  const float4 cf = coef[c];
+  const float2 r = res[c];
+  // residuals of the correction equation at this cell
+  const float rhof = r.x + flf - cf.x * efc + cf.z * eFc;
+  const float rhoF = r.y + flF - cf.y * eFc + cf.w * efc;
+  // 2x2 block solve: [a  -b; -d  e] [x; y] = [rhof; rhoF]
+  const float a = cf.x + dgf, bb = cf.z, d = cf.w, e = cf.y + dgF;
+  const float det = a * e - bb * d;
+  const float inv = __fdividef(1.0f, det);
+  const float nf = efc + (e * rhof + bb * rhoF) * inv;
+  const float nF = eFc + (d * rhof + a * rhoF) * inv;
+  ef[c] = nf;
+  eF[c] = nF;
+  if (fst) {
+    // last black colour of the iteration: add the corrections to the state,
+    // for this cell and for the red cell that shares its pair (2t, 2t+1)
+    fst[c] = df_add(fst[c], nf);
+    Fst[c] = df_add(Fst[c], nF);
+    const int ir = i ^ 1;
+    if (ir < L.nx) {
+      const size_t cr = c - i + ir;
+      fst[cr] = df_add(fst[cr], ef[cr]);
+      Fst[cr] = df_add(Fst[cr], eF[cr]);
+    }
+  }
+}
+
 // ------------------------------------------------------------ fused sweep
 // One full red-black sweep in a single launch.  A block owns a TXxTYxTZ
 // tile; it stages the old state of the tile and a 2-cell halo in shared
@@ -887,6 +1229,134 @@ sfx_status fused_sweep32(sfx_ctx* c, const Nl32& p, const float* phi, const floa
 
 sfx_status f32_ensure_scratch(sfx_ctx* c);
 
+namespace {
+
+sfx_status corr_sweeps(sfx_ctx* c, const Corr32& cp, const float* const* B, const float* r,
+                       const float* lam, float* e, int sweeps, cudaStream_t s) {
+  const Level& L = cp.L;
+  dim3 blk(128), grd((unsigned)(((L.nx + 1) / 2 + 127) / 128), (unsigned)L.ny, (unsigned)L.nz);
+  for (int q = 0; q < sweeps; ++q)
+    for (int color = 0; color < 2; ++color)
+      SFX_KERNEL(c, K_SMOOTH_FINE, k_corr32, grd, blk, s, cp, B[0], B[1], B[2], r, lam, e, color,
+                 q == 0 ? 1 : 0);
+  SFX_LAUNCH_CHECK();
+  return SFX_OK;
+}
+
+// Defect-correction solve of the App. C system (see k_resid32).
+sfx_status solve_dc32(sfx_ctx* c, const Nl32& pf, const Nl32& pF, const float* phi,
+                      float* const* Bf, float* const* BF, float2*& fc, float2*& fo,
+                      float2*& Fc, float2*& Fo, const float2* fs, const float2* Fs,
+                      const sfx_solve_opts* o, int* iters, bool* conv, float* nrm,
+                      cudaStream_t s) {
+  const Level& L = pf.L;
+  const size_t n = L.ncell();
+  const int nb = blocks_for(n, 256);
+  Corr32 cf{L, pf.invh, pf.Doh, pf.literal}, cF{L, pF.invh, pF.Doh, pF.literal};
+  float* ef = c->f32.ef;
+  float* eF = c->f32.eF;
+  const int sweeps = std::max(1, o->nu1 + o->nu2);
+  const int first = std::min(std::max(c->f32.predicted, 1), o->max_cycles);
+  int it;
+  *conv = false;
+  for (it = 1; it <= o->max_cycles; ++it) {
+    const bool check = (it >= first && (it - first) % o->check_every == 0) || it == o->max_cycles;
+    unsigned int* nbuf = check ? (unsigned int*)c->d_norms : nullptr;
+    if (check) SFX_CUDA(cudaMemsetAsync(c->d_norms, 0, 8 * sizeof(unsigned long long), s));
+    SFX_KERNEL(c, K_RESIDUAL, k_resid32<0>, nb, 256, s, pf, phi, Bf[0], Bf[1], Bf[2], fc,
+               it == 1 ? nullptr : ef, fo, fs, Fc, c->f32.rf, c->f32.lf, nbuf);
+    std::swap(fc, fo);
+    sfx_status st = corr_sweeps(c, cf, Bf, c->f32.rf, c->f32.lf, ef, sweeps, s);
+    if (st != SFX_OK) return st;
+    SFX_KERNEL(c, K_RESIDUAL, k_resid32<1>, nb, 256, s, pF, phi, BF[0], BF[1], BF[2], Fc,
+               it == 1 ? nullptr : eF, Fo, Fs, fc, c->f32.rF, c->f32.lF, nbuf);
+    std::swap(Fc, Fo);
+    st = corr_sweeps(c, cF, BF, c->f32.rF, c->f32.lF, eF, sweeps, s);
+    if (st != SFX_OK) return st;
+    SFX_LAUNCH_CHECK();
+    if (check) {
+      SFX_CUDA(cudaMemcpyAsync(c->h_norms, c->d_norms, 2 * sizeof(unsigned long long),
+                               cudaMemcpyDeviceToHost, s));
+      SFX_CUDA(cudaStreamSynchronize(s));
+      memcpy(nrm, c->h_norms, 4 * sizeof(float));
+      for (int q = 0; q < 4; ++q)
+        if (!std::isfinite(nrm[q])) return SFX_ERR_NONFINITE;
+      if (nrm[0] <= o->tol * nrm[1] && nrm[2] <= o->tol * nrm[3]) {
+        *conv = true;
+        break;
+      }
+    }
+  }
+  *iters = std::min(it, o->max_cycles);
+  c->f32.predicted = *conv ? (it == first ? it - 1 : it) : 0;
+  return SFX_OK;
+}
+
+// Coupled Newton defect correction (see k_resid2_32).
+sfx_status solve_newton32(sfx_ctx* c, const Nw32& p, const float* phi, float* const* Bf,
+                          float* const* BF, float2*& fc, float2*& fo, float2*& Fc, float2*& Fo,
+                          const float2* fs, const float2* Fs, const sfx_solve_opts* o,
+                          int* iters, bool* conv, float* nrm, cudaStream_t s) {
+  const Level& L = p.L;
+  const size_t n = L.ncell();
+  const int nb = blocks_for(n, 256);
+  const int sweeps = std::max(1, o->nu1 + o->nu2);
+  dim3 blk(128), grd((unsigned)(((L.nx + 1) / 2 + 127) / 128), (unsigned)L.ny, (unsigned)L.nz);
+  unsigned int* dn = (unsigned int*)c->d_norms;        // two 4-slot norm buffers
+  unsigned int* hn = (unsigned int*)c->h_norms;
+  // The host stays one iteration ahead: it waits for the norms of
+  // iteration it-1 while the GPU works on iteration it, so the stream never
+  // drains for a convergence test.
+  *conv = false;
+  int it = 0, done_it = 0;
+  for (it = 1; it <= o->max_cycles; ++it) {
+    unsigned int* nbuf = dn + 4 * (it & 1);
+    SFX_CUDA(cudaMemsetAsync(nbuf, 0, 4 * sizeof(unsigned int), s));
+    SFX_KERNEL(c, K_RESIDUAL, k_resid2_32, nb, 256, s, p, phi, Bf[0], Bf[1], Bf[2], BF[0], BF[1],
+               BF[2], fc, Fc, fs, Fs, c->f32.coef, c->f32.res, nbuf);
+    SFX_CUDA(cudaMemcpyAsync(hn + 4 * (it & 1), nbuf, 4 * sizeof(unsigned int),
+                             cudaMemcpyDeviceToHost, s));
+    SFX_CUDA(cudaEventRecord(c->f32.ev[it & 1], s));
+    for (int q = 0; q < sweeps; ++q)
+      for (int color = 0; color < 2; ++color) {
+        const bool apply = q == sweeps - 1 && color == 1;
+        SFX_KERNEL(c, K_SMOOTH_FINE, k_corr2_32, grd, blk, s, p, Bf[0], Bf[1], Bf[2], BF[0], BF[1],
+                   BF[2], c->f32.coef, c->f32.res, c->f32.ef, c->f32.eF, color, q == 0 ? 1 : 0,
+                   apply ? fc : nullptr, apply ? Fc : nullptr);
+      }
+    SFX_LAUNCH_CHECK();
+    // test the previous iteration (its residuals describe the state that
+    // the current iteration's residual pass started from)
+    const int prev = it - 1;
+    if (prev >= 1) {
+      SFX_CUDA(cudaEventSynchronize(c->f32.ev[prev & 1]));
+      memcpy(nrm, hn + 4 * (prev & 1), 4 * sizeof(float));
+      for (int q = 0; q < 4; ++q)
+        if (!std::isfinite(nrm[q])) return SFX_ERR_NONFINITE;
+      if (nrm[0] <= o->tol * nrm[1] && nrm[2] <= o->tol * nrm[3]) {
+        *conv = true;
+        done_it = prev;
+        break;
+      }
+    }
+  }
+  if (!*conv) {
+    // the last iteration's residuals
+    SFX_CUDA(cudaStreamSynchronize(s));
+    const int last = std::min(it, o->max_cycles);
+    memcpy(nrm, hn + 4 * (last & 1), 4 * sizeof(float));
+    if (nrm[0] <= o->tol * nrm[1] && nrm[2] <= o->tol * nrm[3]) *conv = true;
+    done_it = last;
+  }
+  // the state is the one the converged residual pass wrote (fc, Fc hold
+  // the output of the latest residual pass, which applied one more
+  // correction when the test lagged; both are converged states)
+  *iters = done_it;
+  return SFX_OK;
+}
+
+}  // namespace
+
 sfx_status step_f32(sfx_ctx* c, const sfx_params* pr, const float* phi, const float* ux,
                     const float* uy, const float* uz, float2* f, float2* F, double dt,
                     const sfx_solve_opts* o, sfx_step_stats* stats, cudaStream_t s) {
@@ -897,10 +1367,20 @@ sfx_status step_f32(sfx_ctx* c, const sfx_params* pr, const float* phi, const fl
   const int nd = L.ndim();
   float* Bf[3] = {c->f32.Bf[0], c->f32.Bf[1], nd == 3 ? c->f32.Bf[2] : nullptr};
   float* BF[3] = {c->f32.BF[0], c->f32.BF[1], nd == 3 ? c->f32.BF[2] : nullptr};
-  for (int d = 0; d < nd; ++d)
-    SFX_KERNEL(c, K_SETUP, k_drift32, blocks_for(L.nface(d), 256), 256, s, L, d, phi,
-               (float)pr->Df, (float)pr->DF, (float)(1.0 / pr->eps), Bf[d], BF[d]);
-  SFX_LAUNCH_CHECK();
+  // drift faces depend on phi and (Df, DF, eps) only
+  const bool reuse = c->f32.reuse_drift && c->f32.drift_phi == phi &&
+                     c->f32.drift_key[0] == pr->Df && c->f32.drift_key[1] == pr->DF &&
+                     c->f32.drift_key[2] == pr->eps;
+  if (!reuse) {
+    for (int d = 0; d < nd; ++d)
+      SFX_KERNEL(c, K_SETUP, k_drift32, blocks_for(L.nface(d), 256), 256, s, L, d, phi,
+                 (float)pr->Df, (float)pr->DF, (float)(1.0 / pr->eps), Bf[d], BF[d]);
+    SFX_LAUNCH_CHECK();
+    c->f32.drift_phi = phi;
+    c->f32.drift_key[0] = pr->Df;
+    c->f32.drift_key[1] = pr->DF;
+    c->f32.drift_key[2] = pr->eps;
+  }
   float2* fs = c->f32.fstar;
   float2* Fs = c->f32.Fstar;
   if (ux) {
@@ -923,6 +1403,34 @@ sfx_status step_f32(sfx_ctx* c, const sfx_params* pr, const float* phi, const fl
   // current and spare buffers of each field (the fused sweep ping-pongs)
   float2 *fc = f, *fo = c->f32.falt, *Fc = F, *Fo = c->f32.Falt;
   int it = 0;
+  if (c->f32.solver >= 1) {
+    bool dconv = false;
+    float dn[4] = {0, 0, 0, 0};
+    if (c->f32.solver == 1) {
+      Nw32 pw{L, pf.invh, pf.Doh, pF.Doh, pf.inv_dt, pf.ka, pf.kd, pf.ginf, pf.inv_eps, pf.eta,
+              pf.literal};
+      st = solve_newton32(c, pw, phi, Bf, BF, fc, fo, Fc, Fo, fs, Fs, o, &it, &dconv, dn, s);
+    } else {
+      st = solve_dc32(c, pf, pF, phi, Bf, BF, fc, fo, Fc, Fo, fs, Fs, o, &it, &dconv, dn, s);
+    }
+    if (st != SFX_OK) return st;
+    if (fc != f) SFX_CUDA(cudaMemcpyAsync(f, fc, n * sizeof(float2), cudaMemcpyDeviceToDevice, s));
+    if (Fc != F) SFX_CUDA(cudaMemcpyAsync(F, Fc, n * sizeof(float2), cudaMemcpyDeviceToDevice, s));
+    if (stats) {
+      stats->picard = it;
+      stats->vcycles = 2 * it * std::max(1, o->nu1 + o->nu2);
+      stats->res_f = dn[0] / fmax((double)dn[1], 1e-300);
+      stats->res_F = dn[2] / fmax((double)dn[3], 1e-300);
+      stats->converged = dconv ? 1 : 0;
+      const void* fl[2] = {f, F};
+      double m[2];
+      st = totals32(c, fl, 2, m, s);
+      if (st != SFX_OK) return st;
+      stats->mass_f = m[0];
+      stats->mass_F = m[1];
+    }
+    return dconv ? SFX_OK : SFX_ERR_NOT_CONVERGED;
+  }
   bool conv = false;
   float nrm[4] = {0, 0, 0, 0};
   // Convergence is tested on the host, which stalls the stream; the step
@@ -1067,6 +1575,12 @@ sfx_status f32_ensure_scratch(sfx_ctx* c) {
   if ((st = get(n * sizeof(float), (void**)&c->f32.dsig)) != SFX_OK) return st;
   if ((st = get(n * sizeof(float2), (void**)&c->f32.falt)) != SFX_OK) return st;
   if ((st = get(n * sizeof(float2), (void**)&c->f32.Falt)) != SFX_OK) return st;
+  float** arrs[6] = {&c->f32.ef, &c->f32.eF, &c->f32.rf, &c->f32.rF, &c->f32.lf, &c->f32.lF};
+  for (float** q : arrs)
+    if ((st = get(n * sizeof(float), (void**)q)) != SFX_OK) return st;
+  if ((st = get(n * sizeof(float4), (void**)&c->f32.coef)) != SFX_OK) return st;
+  if ((st = get(n * sizeof(float2), (void**)&c->f32.res)) != SFX_OK) return st;
+  for (int q = 0; q < 2; ++q) SFX_CUDA(cudaEventCreateWithFlags(&c->f32.ev[q], cudaEventDisableTiming));
   c->f32.ready = true;
   return SFX_OK;
 }

@@ -43,6 +43,17 @@ struct F32Scratch {
   float2* Falt = nullptr;
   bool fused = true;       // one launch per red-black sweep
   int zchunk = 32;         // planes per block of the 3D fused sweep
+  int solver = 1;          // 0: nonlinear pair sweeps; 1: coupled Newton
+                           // defect correction; 2: Picard defect correction
+  float4* coef = nullptr;  // lam_f, lam_F, j_fF, j_Ff of the linearised system
+  float2* res = nullptr;   // r_f, r_F
+  cudaEvent_t ev[2] = {nullptr, nullptr};
+  bool reuse_drift = false;         // keep drift faces while phi and D's are unchanged
+  const float* drift_phi = nullptr;
+  double drift_key[3] = {0, 0, 0};
+  float *ef = nullptr, *eF = nullptr;   // corrections
+  float *rf = nullptr, *rF = nullptr;   // residuals
+  float *lf = nullptr, *lF = nullptr;   // diagonals of the linearised problems
 };
 
 struct Prof {

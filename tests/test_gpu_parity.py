@@ -246,6 +246,7 @@ def test_fused_sweep_equals_colour_launches_bitwise(sfx, name):
     outs = []
     for fused in (1, 0):
         ctx = _ctx(sfx, g, 1)
+        ctx.sfx_set_tuning(sfx._lib.SFX_TUNE_F32_SOLVER, 0)
         ctx.sfx_set_tuning(sfx._lib.SFX_TUNE_FUSED_SWEEP, fused)
         f, F = _pairs(ctx, 0.2 * delta), _pairs(ctx, c.F0)
         u = [None if v is None else dev(v, torch.float32) for v in (ux, uy, uz)]
@@ -255,6 +256,29 @@ def test_fused_sweep_equals_colour_launches_bitwise(sfx, name):
         torch.cuda.synchronize()
         outs.append((f.cpu().numpy().copy(), F.cpu().numpy().copy()))
     assert np.array_equal(outs[0][0], outs[1][0]) and np.array_equal(outs[0][1], outs[1][1])
+
+
+@pytest.mark.parametrize("name", ["adsorption2d", "hr3d", "axi"])
+def test_fp32_solvers_agree(sfx, name):
+    """Defect correction and nonlinear pair sweeps reach the same fixed point."""
+    import torch
+    c, ux, uy, uz = _step_case(name)
+    g, p = c.grid, c.params
+    _, phi, delta = oracle.phase_field_build(g, c.C, c.redist_iters, c.dtau, p.eps)
+    outs = []
+    for solver in (0, 1):
+        ctx = _ctx(sfx, g, 1)
+        ctx.sfx_set_tuning(sfx._lib.SFX_TUNE_F32_SOLVER, solver)
+        f, F = _pairs(ctx, 0.2 * delta), _pairs(ctx, c.F0)
+        u = [None if v is None else dev(v, torch.float32) for v in (ux, uy, uz)]
+        o = sfx.default_opts(tol=1e-12, nu1=1, nu2=0, max_cycles=400)
+        for _ in range(2):
+            st = ctx.sfx_surfactant_step(p, ctx.sfx_phi_fold(dev(phi)), f, F, c.dt, *u, opts=o)
+            assert st.converged
+        outs.append((host(ctx.sfx_df_unpack(f)), host(ctx.sfx_df_unpack(F))))
+    scale = max(np.abs(outs[0][0]).max(), np.abs(outs[0][1]).max())
+    assert np.abs(outs[0][0] - outs[1][0]).max() < 1e-10 * scale
+    assert np.abs(outs[0][1] - outs[1][1]).max() < 1e-10 * scale
 
 
 def test_fp32_mass_drift_over_many_steps(sfx):
