@@ -72,7 +72,7 @@ def lib():
         L.orc_redistance.argtypes = [G, _P, C.c_int, C.c_double, _P]
         L.orc_phase_field.argtypes = [G, _P, C.c_double, _P, _P]
         L.orc_phase_field_build.argtypes = [G, _P, C.c_int, C.c_double, C.c_double, _P, _P, _P]
-        L.orc_normals.argtypes = [G, _P, _P]
+        L.orc_normals.argtypes = [G, _P, C.c_double, _P]
         L.orc_face_drift.argtypes = [G, Pp, _P, C.c_int, _P, _P, _P]
         L.orc_apply_operator.argtypes = [G, C.c_double, _P, _P, _P, C.c_int, _P, _P, _P]
         L.orc_elliptic_solve.restype = C.c_int
@@ -158,9 +158,9 @@ def phase_field_build(g, Cf, iters, dtau, eps):
     return chi, phi, delta
 
 
-def normals(g, phi):
+def normals(g, phi, eps):
     n = np.empty((g.ndim, g.nz, g.ny, g.nx))
-    lib().orc_normals(C.byref(cgrid(g)), _ptr(_arr(phi)), _ptr(n))
+    lib().orc_normals(C.byref(cgrid(g)), _ptr(_arr(phi)), float(eps), _ptr(n))
     return n
 
 

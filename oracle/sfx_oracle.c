@@ -180,8 +180,14 @@ void orc_phase_field_build(const orc_grid* g, const double* C, int iters,
   orc_phase_field(g, chi, eps, phi, delta);
 }
 
-/* n = grad phi / |grad phi| with centred differences (Sec. 2.6) */
-void orc_normals(const orc_grid* g, const double* phi, double* n) {
+/* n = grad phi / |grad phi| with centred differences (Sec. 2.6).
+   READING: the paper leaves n undefined where phi is flat.  Beyond the
+   redistancing band phi is flat up to variations many orders below its
+   own profile slope, and there the direction of grad phi is set by those
+   variations (by round-off at the last few bits).  n is taken as 0 where
+   |grad phi| < ORC_NORMAL_KAPPA phi (1 - phi)/eps (the slope of the
+   equilibrium profile is phi (1 - phi)/eps), or where |grad phi| < 1e-30. */
+void orc_normals(const orc_grid* g, const double* phi, double eps, double* n) {
   size_t N = ncell_of(g);
   int D = ndim_of(g);
   for (int k = 0; k < g->nz; ++k)
@@ -195,7 +201,9 @@ void orc_normals(const orc_grid* g, const double* phi, double* n) {
           m2 += gp[d] * gp[d];
         }
         double m = sqrt(m2);
-        for (int d = 0; d < D; ++d) n[d * N + c] = m < 1e-30 ? 0.0 : gp[d] / m;
+        double slope = phi[c] * (1.0 - phi[c]) / eps;
+        int flat = m < 1e-30 || m < ORC_NORMAL_KAPPA * slope;
+        for (int d = 0; d < D; ++d) n[d * N + c] = flat ? 0.0 : gp[d] / m;
       }
 }
 
@@ -207,7 +215,7 @@ void orc_face_drift(const orc_grid* g, const orc_params* p, const double* phi,
   int D = ndim_of(g);
   double* n = (double*)malloc((size_t)D * N * sizeof(double));
   double* Bc = (double*)malloc((size_t)D * N * sizeof(double));
-  orc_normals(g, phi, n);
+  orc_normals(g, phi, p->eps, n);
   for (size_t c = 0; c < N; ++c) {
     double s = which == 0 ? -p->Df * 2.0 * (0.5 - phi[c]) / p->eps
                           : -p->DF * (1.0 - phi[c]) / p->eps;
@@ -745,7 +753,7 @@ void orc_marangoni(const orc_grid* g, const orc_params* p, const double* f,
   int D = ndim_of(g);
   double* n = (double*)malloc((size_t)D * N * sizeof(double));
   orc_eos(g, p, f, phi, NULL, sigma);
-  orc_normals(g, phi, n);
+  orc_normals(g, phi, p->eps, n);
   for (int k = 0; k < g->nz; ++k)
     for (int j = 0; j < g->ny; ++j)
       for (int i = 0; i < g->nx; ++i) {

@@ -80,7 +80,9 @@ void orc_phase_field_build(const orc_grid* g, const double* C, int iters,
 /* unit normal n = grad(phi)/|grad(phi)| at cell centres, centred
    differences, zero-gradient walls; n = 0 where |grad phi| < 1e-30.
    n has 2 (or 3) arrays of N values: n[d*N + c]. */
-void orc_normals(const orc_grid* g, const double* phi, double* n);
+/* n is 0 where |grad phi| < ORC_NORMAL_KAPPA phi (1 - phi)/eps (flat phi) */
+#define ORC_NORMAL_KAPPA 1e-3
+void orc_normals(const orc_grid* g, const double* phi, double eps, double* n);
 
 /* anti-diffusive face drift B at every face of the grid (Sec. 2.6, App. C):
    which = 0 -> B_f = -Df * 2(0.5 - phi)/eps n ; which = 1 -> B_F = -DF (1 - phi)/eps n,

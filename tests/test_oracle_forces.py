@@ -130,7 +130,7 @@ def test_marangoni_force_is_tangential_and_matches_surface_gradient():
         Gam = 1.0 + 0.2 * np.cos(th)
         p = W.Params(eps=0.75 * g.h, eos=W.EOS_LINEAR, sigma0=1.0, E=0.3, gamma_inf=1.0)
         sig, force = oracle.marangoni(g, p, Gam * delta, phi, Cf, dm_mode=1)
-        nrm = oracle.normals(g, phi)
+        nrm = oracle.normals(g, phi, p.eps)
         ndotf = nrm[0] * force[0] + nrm[1] * force[1]
         assert np.abs(ndotf).max() < 1e-12 * np.abs(force).max()
         # compare in interface cells, away from the band edge

@@ -152,7 +152,7 @@ def test_face_drift_is_mean_of_cell_values_and_zero_on_walls():
     Cf = W.circle_vof(n, n, h, 0.5, 0.5, 0.3)
     p = W.Params(Df=0.02, DF=0.03, eps=0.75 * h)
     _, phi, _ = oracle.phase_field_build(g, Cf, 12, 0.5 * h, p.eps)
-    nrm = oracle.normals(g, phi)
+    nrm = oracle.normals(g, phi, p.eps)
     for which, s in ((0, -p.Df * 2 * (0.5 - phi) / p.eps), (1, -p.DF * (1 - phi) / p.eps)):
         Bx, By, _ = oracle.face_drift(g, p, phi, which)
         Bc = s * nrm[0]

@@ -86,7 +86,7 @@ def test_normals_of_circle_are_radial():
     n = 64
     g, Cf, chi_ex = _circle(n)
     phi, _ = oracle.phase_field(g, chi_ex, 0.75 * g.h)
-    nrm = oracle.normals(g, phi)
+    nrm = oracle.normals(g, phi, 0.75 * g.h)
     x = (np.arange(n) + 0.5) * g.h - 0.5
     r = np.hypot(x[None, :], x[:, None])
     band = (np.abs(chi_ex[0]) < 3 * g.h)
