@@ -43,7 +43,12 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="sfx", choices=["sfx", "reference"])
-    ap.add_argument("--precision", default="f64", choices=["f64", "f32"])
+    ap.add_argument("--workload", default="hr3d", choices=["hr3d", "batch64"])
+    ap.add_argument("--precision", default="f32", choices=["f64", "f32"])
+    ap.add_argument("--f64-steps", type=int, default=3,
+                    help="steps of the FP64 path timed beside the FP32 line (0: skip)")
+    ap.add_argument("--batch-steps", type=int, default=0,
+                    help="also time the batched workload for this many steps (0: skip)")
     ap.add_argument("--n", type=int, default=256)
     ap.add_argument("--tol", type=float, default=1e-10)
     ap.add_argument("--no-e2e", action="store_true")
@@ -61,7 +66,7 @@ def measured_peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
 
 
-def algorithmic_bytes(kind, grid, wbytes):
+def algorithmic_bytes(kind, grid, wbytes, sweeps=3):
     """Unique global bytes one launch of `kind` must move on the fine grid
     (reads + writes; arrays touched by half the cells count half).  N cells,
     d dimensions, 8-byte state (double or double-float pair).
@@ -78,12 +83,14 @@ def algorithmic_bytes(kind, grid, wbytes):
         # coupled correction colour sweep (k_corr2_32): both corrections (all
         # cells, as neighbours: 8 B), the 2x2 coefficients and residuals of
         # the updated half (24 B x 1/2), the 2 d float drift-face arrays of
-        # both fields, write the updated half of both corrections
-        return (8.0 + 12.0 + 8.0 * d + 4.0) * N
+        # both fields, write the updated half of both corrections; the last
+        # black sweep of each iteration also reads and writes the state
+        # (32 B), averaged here over the 2 x sweeps colour launches
+        return (8.0 + 12.0 + 8.0 * d + 4.0 + 32.0 / (2 * sweeps)) * N
     if kind == "residual" and wbytes == 4:
-        # k_resid2_32: f, F, f*, F* (pairs), both corrections, phi, 2 d faces;
-        # writes f, F, the 2x2 coefficients and the residuals
-        return (32.0 + 8.0 + 4.0 + 8.0 * d + 16.0 + 16.0 + 8.0) * N
+        # k_resid2_32: f, F, f*, F* (pairs), phi, 2 d float faces; writes the
+        # 2x2 coefficients and the residuals
+        return (16.0 + 16.0 + 4.0 + 8.0 * d + 16.0 + 8.0) * N
     if kind == "advect":
         return 16.0 * N + wbytes * d * N
     return None
@@ -201,6 +208,27 @@ def run_reference(a, case, rank):
     }))
 
 
+def run_reference_batch(a):
+    """Reference arm of the batched workload: the oracle on a bounded sample
+    (two 64x128 instances), one step of each per timed step."""
+    t, cells = 0.0, 0
+    for s in range(a.warmup + a.steps):
+        rate, secs, desc = oracle_batch_rate(a.tol, 1)
+        if s >= a.warmup:
+            t += secs
+            cells += rate * secs
+    value = cells / t
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": a.gpus,
+        "steps": a.steps, "warmup": a.warmup, "ms_per_step": 1e3 * t / a.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": "batch64 (oracle sample)", "sample": desc},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": desc},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
 def run_gpu(a, case, rank, world, local_rank):
     import torch
     import paper_2605_27534_gb300 as sfx
@@ -214,7 +242,7 @@ def run_gpu(a, case, rank, world, local_rank):
     ctx = sfx.Context.for_grid(g, prec)
     Cd = torch.from_numpy(case.C).to(dev)
     chi = torch.empty_like(Cd)
-    phi = torch.empty(g.shape, dtype=wdt, device=dev)
+    phi = torch.empty_like(Cd)
     ctx.sfx_phase_field_build(Cd, chi, phi, None, iters=case.redist_iters, dtau=case.dtau,
                               eps=p.eps)
     ux, uy, uz = (torch.from_numpy(u).to(dev, wdt) for u in (case.ux, case.uy, case.uz))
@@ -303,7 +331,8 @@ def run_gpu(a, case, rank, world, local_rank):
     top = max(prof.items(), key=lambda kv: kv[1][1])
     kind, (nl, tot_ms, nt) = top
     roof = None
-    ab = algorithmic_bytes(kind, g, wbytes)
+    sw = max(1, opts.nu1 + opts.nu2)
+    ab = algorithmic_bytes(kind, g, wbytes, sw)
     if ab is not None and nt > 0:
         avg_s = tot_ms * 1e-3 / nt
         achieved = ab / avg_s / 1e9
@@ -317,7 +346,7 @@ def run_gpu(a, case, rank, world, local_rank):
         if not v[0]:
             continue
         e = {"launches": v[0], "ms": round(v[1], 3)}
-        b = algorithmic_bytes(k, g, wbytes)
+        b = algorithmic_bytes(k, g, wbytes, sw)
         if b is not None and v[2] > 0:
             e["gbs"] = round(b / (v[1] * 1e-3 / v[2]) / 1e9, 1)
         breakdown[k] = e
@@ -328,6 +357,12 @@ def run_gpu(a, case, rank, world, local_rank):
                "sample": "%d step(s) on the centred %d^3 block of the %d^3 workload "
                          "(same h, dt, flow): %.1f s" % (a.oracle_steps, SAMPLE_N, g.nx, secs)}
     pic = [s[0] for s in stats[-a.steps:]]
+    f64 = None
+    if prec == sfx.SFX_F32 and a.f64_steps > 0:
+        f64 = f64_path(a, case, dev, f, F, phi, ux, uy, uz)
+    batch = None
+    if a.batch_steps > 0:
+        batch = run_gpu_batch(a, rank, 1, local_rank, steps=a.batch_steps, summary=True)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
         "warmup": a.warmup, "ms_per_step": ms_max / a.steps, "higher_is_better": True,
@@ -342,7 +377,236 @@ def run_gpu(a, case, rank, world, local_rank):
         "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
         "clocks": clocks, "kernels": breakdown,
     }
+    if f64 is not None:
+        line["f64_path"] = f64
+        line["speedup_vs_f64"] = f64["ms_per_step"] / (ms_max / a.steps)
+    if batch is not None:
+        line["batch64"] = batch
     print(json.dumps(line))
+
+
+def f64_path(a, case, dev, f32_f, f32_F, f32_phi, ux, uy, uz):
+    """The plain FP64 GPU path on the same workload: ms per step, and the
+    FP32 path's deviation from it after two steps from the same state."""
+    import torch
+    import paper_2605_27534_gb300 as sfx
+    g, p = case.grid, case.params
+    ctx = sfx.Context.for_grid(g, sfx.SFX_F64)
+    Cd = torch.from_numpy(case.C).to(dev)
+    chi = torch.empty_like(Cd)
+    phi = torch.empty(g.shape, dtype=torch.float64, device=dev)
+    ctx.sfx_phase_field_build(Cd, chi, phi, None, iters=case.redist_iters, dtau=case.dtau,
+                              eps=p.eps)
+    u64 = [t.to(torch.float64) for t in (ux, uy, uz)]
+    f = torch.zeros(g.shape, dtype=torch.float64, device=dev)
+    F = torch.ones(g.shape, dtype=torch.float64, device=dev)
+    opts = sfx.default_opts(tol=a.tol, max_cycles=200)
+    pic = []
+    ctx.sfx_surfactant_step(p, phi, f, F, case.dt, *u64, opts=opts)   # warm-up
+    stream = torch.cuda.current_stream()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(a.f64_steps):
+        pic.append(ctx.sfx_surfactant_step(p, phi, f, F, case.dt, *u64, opts=opts).picard)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / a.f64_steps
+    # accuracy of the FP32 path against this one: two steps from f = 0, F = 1
+    ctx32 = sfx.Context.for_grid(g, sfx.SFX_F32)
+    zeros = torch.zeros(g.shape, dtype=torch.float64, device=dev)
+    f.zero_()
+    F.fill_(1.0)
+    f32_f.copy_(sfx.sfx_df_pack(zeros))
+    f32_F.copy_(sfx.sfx_df_pack(F))
+    o32 = sfx.default_opts(tol=a.tol, max_cycles=200, nu1=3, nu2=0)
+    for _ in range(2):
+        ctx.sfx_surfactant_step(p, phi, f, F, case.dt, *u64, opts=opts)
+        ctx32.sfx_surfactant_step(p, f32_phi, f32_f, f32_F, case.dt, ux, uy, uz, opts=o32)
+    fd, Fd = sfx.sfx_df_unpack(f32_f), sfx.sfx_df_unpack(f32_F)
+    scale = float(torch.maximum(f.abs().max(), F.abs().max()))
+    err = float(torch.maximum((fd - f).abs().max(), (Fd - F).abs().max())) / scale
+    return {"ms_per_step": ms, "value": g.ncell / (ms * 1e-3), "unit": UNIT, "steps": a.f64_steps,
+            "picard_per_step": statistics.mean(pic), "dtype": "f64",
+            "f32_rel_err_after_2_steps": err}
+
+
+# ------------------------------------------------------------------ batched
+BATCH_N, BATCH_SEED = 64, 3
+
+
+def batch_bytes(sizes, rp, sg, steps, sweeps):
+    """Algorithmic bytes of `steps` batched steps (d = 2, pairs 8 B, double
+    phi 8 B, its folded copy, velocities and faces 4 B).  Per instance of N
+    cells and per step: folded copy of phi (12 N), drift faces (phi 8 +
+    2 fields x 2 faces x 4 = 24 N), advection of both fields (pairs in and
+    out 32 N, 2 velocity arrays 8 N), copy into the iterate (32 N), totals
+    (16 N); per residual pass (16 + 16 + 4 + 16 + 16 + 8 =
+    76 N); per sweep group 2 x sweeps colour launches of (8 + 12 + 16 + 4 =
+    40 N) and the state update (32 N)."""
+    tot = 0.0
+    for (nr, nz), r, w in zip(sizes, rp, sg):
+        N = nr * nz
+        tot += N * (steps * (12.0 + 24.0 + 40.0 + 32.0 + 16.0) + r * 76.0 +
+                    w * (2 * sweeps * 40.0 + 32.0))
+    return tot
+
+
+def batch_inputs(dev):
+    """The 64 seeded instances: grids from {64x128, 128x256, 256x512},
+    log-uniform Bi, Da in [1e-2, 1e2], Pe = 100, HR Stokes flow, sphere
+    R = 0.2 on the axis.  Phase field built on the GPU per grid size."""
+    import torch
+    import paper_2605_27534_gb300 as sfx
+    spec = W.batch_axi(BATCH_N, seed=BATCH_SEED)
+    per_size = {}
+    inst = []
+    for nr, nz, Bi, Da in spec:
+        c = W.case_axi(nr, nz, Bi, Da)
+        if (nr, nz) not in per_size:
+            ctx = sfx.Context.for_grid(c.grid, sfx.SFX_F32)
+            Cd = torch.from_numpy(c.C).to(dev)
+            chi = torch.empty_like(Cd)
+            phi = torch.empty_like(Cd)
+            ctx.sfx_phase_field_build(Cd, chi, phi, None, iters=c.redist_iters, dtau=c.dtau,
+                                      eps=c.params.eps)
+            per_size[(nr, nz)] = (phi.reshape(-1), torch.from_numpy(c.ux).to(dev, torch.float32)
+                                  .reshape(-1), torch.from_numpy(c.uy).to(dev, torch.float32)
+                                  .reshape(-1))
+        inst.append((nr, nz, c.grid.h, c.dt, c.params))
+    phi = torch.cat([per_size[(i[0], i[1])][0] for i in inst])
+    ur = torch.cat([per_size[(i[0], i[1])][1] for i in inst])
+    uz = torch.cat([per_size[(i[0], i[1])][2] for i in inst])
+    return spec, inst, phi, ur, uz
+
+
+def run_gpu_batch(a, rank, world, local_rank, steps=None, summary=False):
+    import torch
+    import paper_2605_27534_gb300 as sfx
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    steps = steps or a.steps
+    spec, inst, phi, ur, uz = batch_inputs(dev)
+    sizes = [(i[0], i[1]) for i in inst]
+    ncell = sum(nr * nz for nr, nz in sizes)
+    B = sfx.Batch(inst)
+    ones = torch.ones(ncell, dtype=torch.float64, device=dev)
+    f = sfx.sfx_df_pack(torch.zeros_like(ones))
+    F = sfx.sfx_df_pack(ones)
+    block, sweeps, budget = B.sfx_batch_autotune(phi, f, F, a.tol, ur=ur, uz=uz)
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(a.warmup):
+        B.sfx_batch_step(phi, f, F, a.tol, ur=ur, uz=uz)
+    B.sfx_batch_work(reset=True)
+    clk = ClockSampler(local_rank) if not summary else None
+    barrier()
+    if clk:
+        clk.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        B.sfx_batch_step(phi, f, F, a.tol, ur=ur, uz=uz)
+    e1.record(stream)
+    barrier()
+    clocks = clk.stop() if clk else None
+    ms = e0.elapsed_time(e1)
+    rp, sg = B.sfx_batch_work()
+    st = B.sfx_batch_stats()
+    ms_max = ms
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_max = float(t.item())
+    value = ncell * steps * world / (ms_max * 1e-3)
+    peaks, peak_src = measured_peaks()
+    ab = batch_bytes(sizes, rp, sg, steps, sweeps)
+    achieved = ab / (ms * 1e-3) / 1e9
+    roof = {"bound": "hbm", "kernel": "batched step graph (all kernels of the step)",
+            "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+            "frac": achieved / peaks["hbm_gbs"], "traffic": None,
+            "algorithmic_bytes_per_step": ab / steps, "avg_step_ms": ms / steps,
+            "peak_source": "%s (MEASURED_PEAKS.json hbm_gbs)" % peak_src}
+    iters_mean = float(np.mean(np.array(rp) / steps))
+    conv = all(st["converged"])
+    sched = {"block": block, "sweeps": sweeps, "iteration_budget": budget}
+    # init, fold, 2 drift, advect, copy; per iteration residual, flags and
+    # the colour sweeps; totals
+    launches_per_step = 6 + budget * (2 + 2 * sweeps) + 1
+    if summary:
+        return {"value": value, "unit": UNIT, "ms_per_step": ms / steps, "steps": steps,
+                "cells": ncell, "instances": len(inst), "roofline_frac": roof["frac"],
+                "schedule": sched, "newton_iters_mean": iters_mean, "all_converged": conv}
+    e2e = None
+    if not a.no_e2e:
+        fh = f.detach().cpu().pin_memory()
+        Fh = F.detach().cpu().pin_memory()
+        barrier()
+        s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s0.record(stream)
+        for _ in range(steps):
+            f.copy_(fh, non_blocking=True)
+            F.copy_(Fh, non_blocking=True)
+            B.sfx_batch_step(phi, f, F, a.tol, ur=ur, uz=uz)
+            fh.copy_(f, non_blocking=True)
+            Fh.copy_(F, non_blocking=True)
+        s1.record(stream)
+        barrier()
+        ms_e = s0.elapsed_time(s1)
+        nb = 2 * ncell * 8
+        e2e = {"value": ncell * steps * world / (ms_e * 1e-3), "unit": UNIT,
+               "h2d_bytes_per_step": nb, "d2h_bytes_per_step": nb}
+    if rank != 0:
+        return None
+    cpu = None
+    if not a.no_cpu:
+        rate, secs, desc = oracle_batch_rate(a.tol, a.oracle_steps)
+        cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": "%s: %.1f s" % (desc, secs)}
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": steps,
+        "warmup": a.warmup, "ms_per_step": ms_max / steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "batch64: %d axisymmetric instances, grids from {64x128, "
+                               "128x256, 256x512}, Bi and Da log-uniform in [1e-2, 1e2], "
+                               "Pe=100, HR Stokes flow, seed %d, tol=%g" % (
+                                   len(inst), BATCH_SEED, a.tol),
+                   "cells": ncell, "precision": "f32",
+                   "l2": "inputs larger than L2 (state + coefficients %.2f GB)" % (
+                       ncell * 8 * 12 / 1e9),
+                   "parallelism": "replicas%d" % world, "schedule": sched,
+                   "newton_iters_mean": iters_mean, "all_converged": conv},
+        "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
+        "gpu_launches": launches_per_step * steps, "clocks": clocks,
+    }
+    print(json.dumps(line))
+    return line
+
+
+def oracle_batch_rate(tol, steps):
+    """The FP64 oracle, as it stands, on two 64x128 instances of the batch."""
+    import oracle
+    spec = [s for s in W.batch_axi(BATCH_N, seed=BATCH_SEED) if s[0] == 64][:2]
+    cells, t = 0, 0.0
+    for nr, nz, Bi, Da in spec:
+        c = W.case_axi(nr, nz, Bi, Da)
+        _, phi, _ = oracle.phase_field_build(c.grid, c.C, c.redist_iters, c.dtau, c.params.eps)
+        f, F = np.zeros(c.grid.shape), np.ones(c.grid.shape)
+        t0 = time.perf_counter()
+        for _ in range(steps):
+            f, F, _ = oracle.surfactant_step(c.grid, c.params, phi, f, F, c.dt, tol, c.ux, c.uy,
+                                             None)
+        t += time.perf_counter() - t0
+        cells += c.grid.ncell * steps
+    return cells / t, t, "%d step(s) of %d 64x128 instances of the batch, 1 thread" % (
+        steps, len(spec))
 
 
 def main():
@@ -354,14 +618,20 @@ def main():
     if a.impl == "reference":
         if world > 1 and rank != 0:
             return
-        run_reference(a, case, rank)
+        if a.workload == "batch64":
+            run_reference_batch(a)
+        else:
+            run_reference(a, case, rank)
         return
     if world > 1:
         import torch
         import torch.distributed as dist
         torch.cuda.set_device(local_rank)
         dist.init_process_group("nccl")
-    run_gpu(a, case, rank, world, local_rank)
+    if a.workload == "batch64":
+        run_gpu_batch(a, rank, world, local_rank)
+    else:
+        run_gpu(a, case, rank, world, local_rank)
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()

@@ -29,12 +29,18 @@
  *   SFX_F32: the transported state (f, F and the advected xi) is stored as
  *   double-float pairs: two floats per cell, hi then lo, value hi + lo
  *   (about 48 significant bits; sfx_df_pack/sfx_df_unpack convert from/to
- *   double).  The phase field (folded, see sfx_phi_fold), velocities, VoF
- *   fraction, sigma and force are float.  Kernels use FP32 arithmetic only: residuals are formed from
- *   pair differences and applied as pair additions, so the totals keep
- *   ~1e-14 relative precision while the FP32 coefficients put the solution
- *   within ~1e-7 of the FP64 operator's.  Totals are reduced in FP64 across
- *   threads.
+ *   double).  Velocities, VoF fraction, sigma and force are float.  The
+ *   phase field phi (and delta) is double in both precisions: the unit
+ *   normal n = grad phi/|grad phi| is undefined where phi is flat, and deep
+ *   in the bulk its direction is set by variations of phi far below float
+ *   resolution, so SFX_F32 takes the differences of phi in FP64 (once per
+ *   phi) before working on a float copy of phi folded about 1/2 (phi where
+ *   phi <= 1/2, phi - 1 elsewhere, so that phi and 1 - phi both keep full
+ *   relative precision).  The per-iteration kernels use FP32 arithmetic
+ *   only: residuals are formed from pair differences and applied as pair
+ *   additions, so the totals keep ~1e-14 relative precision while the FP32
+ *   coefficients put the solution within ~1e-7 of the FP64 operator's.
+ *   Totals are reduced in FP64 across threads.
  */
 #ifndef SFX_H
 #define SFX_H
@@ -122,8 +128,7 @@ void sfx_default_opts(sfx_solve_opts* opts);
    redistancing d chi/d tau + sign(chi0)(|grad chi| - 1) = 0 (first-order
    Godunov with the Russo-Smereka sub-cell fix) at pseudo-time step dtau,
    then phi = (1 - tanh(chi/(2 eps)))/2 and delta = phi (1 - phi)/eps.
-   C, chi: double.  phi, delta: the context precision (double or float;
-   SFX_F32 writes phi folded, see sfx_phi_fold).  delta may be NULL. */
+   C, chi, phi, delta: double, in both precisions.  delta may be NULL. */
 sfx_status sfx_phase_field_build(sfx_ctx* ctx, const double* C, double* chi,
                                  void* phi, void* delta, int iters,
                                  double dtau, double eps, void* stream);
@@ -153,12 +158,12 @@ sfx_status sfx_mg_solve(sfx_ctx* ctx, double D, const double* Bx,
    the fully implicit f/F system of App. C solved by Picard iteration, each
    half a multigrid solve of the Sec. 3.1 operator with the drifts
    B_f = -Df 2(0.5 - phi)/eps n and B_F = -DF (1 - phi)/eps n,
-   n = grad phi/|grad phi|.  f and F (state layout of the context) are
-   updated in place; phi and the velocities are in the context precision.
-   SFX_F32 contexts relax the same system by nonlinear red-black
-   Gauss-Seidel sweeps on the pair state (nu1 + nu2 sweeps per field per
-   Picard iteration; the residual bound is each cell's residual just before
-   its update).  stats may be NULL. */
+   n = grad phi/|grad phi| (n = 0 where |grad phi| < 1e-30).  f and F
+   (state layout of the context) are updated in place; phi is double, the
+   velocities are in the context precision.  SFX_F32 contexts solve the
+   same system by coupled Newton defect correction (SFX_TUNE_F32_SOLVER):
+   each iteration evaluates both residuals in pair arithmetic and relaxes
+   the correction by nu1 + nu2 FP32 red-black sweeps.  stats may be NULL. */
 sfx_status sfx_surfactant_step(sfx_ctx* ctx, const sfx_params* params,
                                const void* phi, const void* ux,
                                const void* uy, const void* uz, void* f,
@@ -205,8 +210,9 @@ sfx_status sfx_totals_noalloc(const sfx_grid* grid, const double* const* fields,
    by params->eos, evaluated in double; force = delta_m (I - n n) grad sigma
    with centred grad sigma, n from phi, and delta_m the PLIC interface area
    per cell volume (dm_mode 1; Youngs normal) or |grad C| (dm_mode 0).
-   SFX_F64: f, C, sigma, force double.  SFX_F32: f double-float pairs, C,
-   phi, sigma, force float (sigma may be NULL); the Langmuir logarithm is
+   phi is double.  SFX_F64: f, C, sigma, force double.  SFX_F32: f
+   double-float pairs, C, sigma, force float (sigma may be NULL); the
+   Langmuir logarithm is
    taken in double once Gamma/Gamma_inf > 1/2, and the gradient is taken of
    sigma - sigma0.  force holds ndim arrays of N cells, component-major. */
 sfx_status sfx_marangoni_force(sfx_ctx* ctx, const sfx_params* params,
@@ -237,12 +243,13 @@ typedef enum {
                                fields linearised alternately (Picard);
                                0 = nonlinear red-black sweeps on the pair
                                state.  Same fixed point, same test. */
-  SFX_TUNE_REUSE_DRIFT = 2  /* SFX_F32: 1 = keep the drift faces of the
-                               last step while phi's pointer, Df, DF and
-                               eps are unchanged (for a static interface;
-                               after writing phi in place, set the knob
-                               again to force a rebuild); 0 (default) =
-                               rebuild them every step. */
+  SFX_TUNE_REUSE_DRIFT = 2  /* SFX_F32: 1 = keep the drift faces and the
+                               folded float copy of phi of the last step
+                               while phi's pointer, Df, DF and eps are
+                               unchanged (for a static interface; after
+                               writing phi in place, set the knob again to
+                               force a rebuild); 0 (default) = rebuild them
+                               every step. */
 } sfx_tune_key;
 sfx_status sfx_set_tuning(sfx_ctx* ctx, int key, int value);
 
@@ -250,11 +257,71 @@ sfx_status sfx_set_tuning(sfx_ctx* ctx, int key, int value);
    contexts (n cells; device pointers; enqueued on stream). */
 sfx_status sfx_df_pack(const double* in, void* out, size_t n, void* stream);
 sfx_status sfx_df_unpack(const void* in, double* out, size_t n, void* stream);
-/* The folded phase field of SFX_F32 contexts from a double phi: phi where
-   phi <= 1/2, phi - 1 elsewhere (so both phi and 1 - phi keep full relative
-   precision in a float).  sfx_phase_field_build writes this form directly
-   in SFX_F32 contexts; every SFX_F32 call takes phi in this form. */
-sfx_status sfx_phi_fold(const double* phi, float* out, size_t n, void* stream);
+
+/* Batched SFX_F32 step over many independent axisymmetric blocks
+   (Sec. 4.3 runs series of drop cases with different Bi and Da; each one is
+   a small (r, z) block).  Every instance has its own size, h, dt and
+   parameters; all their fields are packed back to back in shared arrays:
+   instance i's cells start at cell_off[i] (its own layout is the
+   axisymmetric one above: nx = nr, ny = nz), its radial faces at
+   rface_off[i] ((nz, nr+1) each) and its axial faces at zface_off[i]
+   ((nz+1, nr) each); sfx_batch_layout returns the offsets.  Each step does,
+   per instance, what sfx_surfactant_step does in an SFX_F32 context with
+   the coupled Newton solver: drift faces (Sec. 2.3), BCG advection
+   (Sec. 3.1) when velocities are given, then App. C's coupled implicit
+   system solved by Newton defect correction until both relative residuals
+   are <= tol.  An instance that meets the tolerance stops iterating at once
+   while the others go on.  The whole step is one CUDA graph launch, captured
+   on the first call and again when a pointer, tol or the schedule changes;
+   it never synchronises with the host.  The library owns the batch (the
+   descriptors, the scratch and the graph). */
+typedef struct {
+  int nr, nz;           /* cells in r and z, >= 1 */
+  double h, dt;         /* cell size and time step, > 0 */
+  sfx_params params;    /* as for sfx_surfactant_step (sigma0, E, eos unused) */
+} sfx_batch_instance;
+typedef struct sfx_batch sfx_batch;
+
+/* Copies the n >= 1 descriptors; SFX_ERR_ARG on a bad size or parameter. */
+sfx_status sfx_batch_create(const sfx_batch_instance* inst, int n, sfx_batch** out);
+void sfx_batch_destroy(sfx_batch* b);
+/* Totals of the packed arrays and, when the array pointers are not NULL,
+   the n offsets of each instance (host arrays of n size_t). */
+sfx_status sfx_batch_layout(const sfx_batch* b, size_t* n_cells, size_t* n_rfaces,
+                            size_t* n_zfaces, size_t* cell_off, size_t* rface_off,
+                            size_t* zface_off);
+/* Schedule: threads per block (128, 256 or 512), red-black sweeps per
+   Newton iteration (1..16) and the iteration budget (1..200).  Defaults
+   256, 3, 8.  An instance that has not converged within the budget keeps
+   its last iterate and is reported by sfx_batch_stats. */
+sfx_status sfx_batch_set_schedule(sfx_batch* b, int block, int sweeps, int max_iters);
+/* One step of every instance.  phi: phase field (double, packed cells);
+   ur, uz: face velocities (float, packed radial / axial faces), both NULL
+   for no advection; f, F: double-float pairs (packed cells), updated in
+   place.  Enqueued on stream; returns without waiting. */
+sfx_status sfx_batch_step(sfx_batch* b, const void* phi, const void* ur, const void* uz,
+                          void* f, void* F, double tol, void* stream);
+/* Per-instance results of the last step (host arrays of n, any may be
+   NULL): Newton iterations, final relative residuals, compensated totals
+   sum V f and sum V F (FP64) and whether the tolerance was met.  Waits for
+   stream. */
+sfx_status sfx_batch_stats(sfx_batch* b, int* iters, float* res_f, float* res_F,
+                           double* mass_f, double* mass_F, int* converged, void* stream);
+/* Work counters per instance (host arrays of n, may be NULL): residual
+   passes and correction sweep groups (sweeps x 2 colours) run since the
+   batch was created or last reset (reset != 0 zeroes them after reading).
+   Waits for stream. */
+sfx_status sfx_batch_work(sfx_batch* b, long long* resid_passes, long long* sweep_groups,
+                          int reset, void* stream);
+/* Autotuner: runs one step of every candidate schedule (block 128 or 256,
+   2, 3 or 4 sweeps) on scratch copies of f and F (which stay unchanged),
+   gives each the smallest iteration budget under which every instance
+   converged (plus one spare), times it and keeps the fastest.  chosen
+   (3 ints, may be NULL) receives block, sweeps and budget.  Waits for
+   stream. */
+sfx_status sfx_batch_autotune(sfx_batch* b, const void* phi, const void* ur, const void* uz,
+                              const void* f, const void* F, double tol, void* stream,
+                              int* chosen);
 
 /* Instrumentation (not part of the method).  Kernel kinds: */
 typedef enum {

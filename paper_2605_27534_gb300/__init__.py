@@ -17,7 +17,7 @@ from . import _lib
 from ._lib import (SFX_AXISYM, SFX_CART3D, SFX_F32, SFX_F64, SFX_OK, SFX_ERR_NOT_CONVERGED,
                    SFX_PLANAR2D, Grid, Params, SolveOpts, StepStats)
 
-__all__ = ["SfxError", "Context", "lib", "default_opts", "SFX_PLANAR2D", "SFX_AXISYM",
+__all__ = ["SfxError", "Context", "Batch", "lib", "default_opts", "SFX_PLANAR2D", "SFX_AXISYM",
            "SFX_CART3D", "SFX_F64", "SFX_F32"]
 
 
@@ -146,28 +146,10 @@ class Context:
                "sfx_marangoni_force")
 
     def sfx_df_pack(self, x, out=None):
-        """double tensor -> double-float pairs (float32 tensor, last dim 2)."""
-        import torch
-        if out is None:
-            out = torch.empty(tuple(x.shape) + (2,), dtype=torch.float32, device=x.device)
-        _check(lib().sfx_df_pack(_ptr(x), _ptr(out), x.numel(), _stream()), "sfx_df_pack")
-        return out
+        return sfx_df_pack(x, out)
 
     def sfx_df_unpack(self, p, out=None):
-        """double-float pairs (float32, last dim 2) -> double tensor."""
-        import torch
-        if out is None:
-            out = torch.empty(tuple(p.shape[:-1]), dtype=torch.float64, device=p.device)
-        _check(lib().sfx_df_unpack(_ptr(p), _ptr(out), out.numel(), _stream()), "sfx_df_unpack")
-        return out
-
-    def sfx_phi_fold(self, phi, out=None):
-        """double phi -> folded float carrier of SFX_F32 contexts."""
-        import torch
-        if out is None:
-            out = torch.empty(tuple(phi.shape), dtype=torch.float32, device=phi.device)
-        _check(lib().sfx_phi_fold(_ptr(phi), _ptr(out), phi.numel(), _stream()), "sfx_phi_fold")
-        return out
+        return sfx_df_unpack(p, out)
 
     def sfx_set_tuning(self, key: int, value: int):
         _check(lib().sfx_set_tuning(self._h, int(key), int(value)), "sfx_set_tuning")
@@ -190,3 +172,93 @@ class Context:
         _check(lib().sfx_cfl_dt(self._h, _ptr(ux), _ptr(uy), _ptr(uz), float(D), float(eps),
                                 float(safety), C.byref(out), _stream()), "sfx_cfl_dt")
         return out.value
+
+
+class Batch:
+    """Many independent axisymmetric instances stepped together (sfx_batch_*).
+
+    `instances` is a sequence of (nr, nz, h, dt, params); fields are packed
+    back to back, instance i at the offsets of `layout()`.
+    """
+
+    def __init__(self, instances):
+        n = len(instances)
+        arr = (_lib.BatchInstance * n)()
+        for i, (nr, nz, h, dt, p) in enumerate(instances):
+            ps = p if isinstance(p, Params) else params_struct(p)
+            arr[i] = _lib.BatchInstance(int(nr), int(nz), float(h), float(dt), ps)
+        self.n = n
+        h_ = C.c_void_p()
+        _check(lib().sfx_batch_create(arr, n, C.byref(h_)), "sfx_batch_create")
+        self._h = h_
+
+    def close(self):
+        if self._h:
+            lib().sfx_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def sfx_batch_layout(self):
+        """(n_cells, n_rfaces, n_zfaces, cell_off, rface_off, zface_off)."""
+        n = self.n
+        nc, nr, nz = C.c_size_t(0), C.c_size_t(0), C.c_size_t(0)
+        co, ro, zo = (C.c_size_t * n)(), (C.c_size_t * n)(), (C.c_size_t * n)()
+        _check(lib().sfx_batch_layout(self._h, C.byref(nc), C.byref(nr), C.byref(nz), co, ro, zo),
+               "sfx_batch_layout")
+        return nc.value, nr.value, nz.value, list(co), list(ro), list(zo)
+
+    def sfx_batch_set_schedule(self, block=256, sweeps=3, max_iters=8):
+        _check(lib().sfx_batch_set_schedule(self._h, int(block), int(sweeps), int(max_iters)),
+               "sfx_batch_set_schedule")
+
+    def sfx_batch_step(self, phi, f, F, tol, ur=None, uz=None):
+        _check(lib().sfx_batch_step(self._h, _ptr(phi), _ptr(ur), _ptr(uz), _ptr(f), _ptr(F),
+                                    float(tol), _stream()), "sfx_batch_step")
+
+    def sfx_batch_stats(self):
+        """dict of per-instance lists: iters, res_f, res_F, mass_f, mass_F, converged."""
+        n = self.n
+        it, cv = (C.c_int * n)(), (C.c_int * n)()
+        rf, rF = (C.c_float * n)(), (C.c_float * n)()
+        mf, mF = (C.c_double * n)(), (C.c_double * n)()
+        _check(lib().sfx_batch_stats(self._h, it, rf, rF, mf, mF, cv, _stream()),
+               "sfx_batch_stats")
+        return {"iters": list(it), "res_f": list(rf), "res_F": list(rF), "mass_f": list(mf),
+                "mass_F": list(mF), "converged": [bool(x) for x in cv]}
+
+    def sfx_batch_work(self, reset=False):
+        """(residual passes, sweep groups) per instance since creation or reset."""
+        n = self.n
+        r, w = (C.c_longlong * n)(), (C.c_longlong * n)()
+        _check(lib().sfx_batch_work(self._h, r, w, 1 if reset else 0, _stream()), "sfx_batch_work")
+        return list(r), list(w)
+
+    def sfx_batch_autotune(self, phi, f, F, tol, ur=None, uz=None):
+        """Pick block size, sweeps and iteration budget; returns them."""
+        ch = (C.c_int * 3)()
+        _check(lib().sfx_batch_autotune(self._h, _ptr(phi), _ptr(ur), _ptr(uz), _ptr(f), _ptr(F),
+                                        float(tol), _stream(), ch), "sfx_batch_autotune")
+        return tuple(ch)
+
+
+def sfx_df_pack(x, out=None):
+    """double tensor -> double-float pairs (float32 tensor, last dim 2)."""
+    import torch
+    if out is None:
+        out = torch.empty(tuple(x.shape) + (2,), dtype=torch.float32, device=x.device)
+    _check(lib().sfx_df_pack(_ptr(x), _ptr(out), x.numel(), _stream()), "sfx_df_pack")
+    return out
+
+
+def sfx_df_unpack(p, out=None):
+    """double-float pairs (float32, last dim 2) -> double tensor."""
+    import torch
+    if out is None:
+        out = torch.empty(tuple(p.shape[:-1]), dtype=torch.float64, device=p.device)
+    _check(lib().sfx_df_unpack(_ptr(p), _ptr(out), out.numel(), _stream()), "sfx_df_unpack")
+    return out

@@ -22,7 +22,9 @@ EXPORTS = [
     "sfx_ctx_destroy", "sfx_default_opts", "sfx_phase_field_build", "sfx_advect",
     "sfx_mg_solve", "sfx_surfactant_step", "sfx_totals", "sfx_marangoni_force", "sfx_cfl_dt",
     "sfx_profile", "sfx_profile_read", "sfx_totals_noalloc", "sfx_df_pack", "sfx_df_unpack",
-    "sfx_phi_fold", "sfx_set_tuning",
+    "sfx_set_tuning", "sfx_batch_create", "sfx_batch_destroy",
+    "sfx_batch_layout", "sfx_batch_set_schedule", "sfx_batch_step", "sfx_batch_stats",
+    "sfx_batch_autotune", "sfx_batch_work",
 ]
 SFX_TUNE_FUSED_SWEEP = 0
 SFX_TUNE_F32_SOLVER = 1
@@ -54,6 +56,11 @@ class StepStats(C.Structure):
     _fields_ = [("picard", C.c_int), ("vcycles", C.c_int), ("res_f", C.c_double),
                 ("res_F", C.c_double), ("mass_f", C.c_double), ("mass_F", C.c_double),
                 ("converged", C.c_int)]
+
+
+class BatchInstance(C.Structure):
+    _fields_ = [("nr", C.c_int), ("nz", C.c_int), ("h", C.c_double), ("dt", C.c_double),
+                ("params", Params)]
 
 
 _lib = None
@@ -108,10 +115,27 @@ def load(path: str = SO_PATH):
     L.sfx_df_unpack.argtypes = [vp, vp, C.c_size_t, vp]
     L.sfx_set_tuning.restype = C.c_int
     L.sfx_set_tuning.argtypes = [vp, C.c_int, C.c_int]
-    L.sfx_phi_fold.restype = C.c_int
-    L.sfx_phi_fold.argtypes = [vp, vp, C.c_size_t, vp]
     L.sfx_totals_noalloc.restype = C.c_int
     L.sfx_totals_noalloc.argtypes = [C.POINTER(Grid), C.POINTER(C.c_void_p), C.c_int,
                                      C.POINTER(C.c_double), vp]
+    szp = C.POINTER(C.c_size_t)
+    ip, fp, dpp = C.POINTER(C.c_int), C.POINTER(C.c_float), C.POINTER(C.c_double)
+    L.sfx_batch_create.restype = C.c_int
+    L.sfx_batch_create.argtypes = [C.POINTER(BatchInstance), C.c_int, C.POINTER(vp)]
+    L.sfx_batch_destroy.restype = None
+    L.sfx_batch_destroy.argtypes = [vp]
+    L.sfx_batch_layout.restype = C.c_int
+    L.sfx_batch_layout.argtypes = [vp, szp, szp, szp, szp, szp, szp]
+    L.sfx_batch_set_schedule.restype = C.c_int
+    L.sfx_batch_set_schedule.argtypes = [vp, C.c_int, C.c_int, C.c_int]
+    L.sfx_batch_step.restype = C.c_int
+    L.sfx_batch_step.argtypes = [vp, vp, vp, vp, vp, vp, dp, vp]
+    L.sfx_batch_stats.restype = C.c_int
+    L.sfx_batch_stats.argtypes = [vp, ip, fp, fp, dpp, dpp, ip, vp]
+    L.sfx_batch_autotune.restype = C.c_int
+    L.sfx_batch_autotune.argtypes = [vp, vp, vp, vp, vp, vp, dp, vp, ip]
+    L.sfx_batch_work.restype = C.c_int
+    L.sfx_batch_work.argtypes = [vp, C.POINTER(C.c_longlong), C.POINTER(C.c_longlong), C.c_int,
+                                 vp]
     _lib = L
     return L

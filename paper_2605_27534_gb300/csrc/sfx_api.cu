@@ -228,7 +228,7 @@ sfx_status sfx_surfactant_step(sfx_ctx* c, const sfx_params* params, const void*
   if (opts) o = *opts;
   if (!opts_ok(&o)) return SFX_ERR_ARG;
   if (c->prec == SFX_F32)
-    return step_f32(c, params, (const float*)phi, (const float*)ux, (const float*)uy,
+    return step_f32(c, params, (const double*)phi, (const float*)ux, (const float*)uy,
                     (const float*)uz, (float2*)f, (float2*)F, dt, &o, stats, S(stream));
   return surfactant_step(c, params, phi, ux, uy, uz, (double*)f, (double*)F, dt, &o, stats,
                          S(stream));
@@ -250,7 +250,7 @@ sfx_status sfx_marangoni_force(sfx_ctx* c, const sfx_params* params, const void*
   if (dm_mode != 0 && dm_mode != 1) return SFX_ERR_ARG;
   if (!C) return SFX_ERR_ARG;
   if (c->prec == SFX_F32)
-    return marangoni32(c, params, (const float2*)f, (const float*)phi, (const float*)C, dm_mode,
+    return marangoni32(c, params, (const float2*)f, (const double*)phi, (const float*)C, dm_mode,
                        (float*)sigma, (float*)force, S(stream));
   if (!sigma) return SFX_ERR_ARG;
   return marangoni(c, params, (const double*)f, phi, (const double*)C, dm_mode, (double*)sigma,
@@ -299,11 +299,6 @@ sfx_status sfx_df_pack(const double* in, void* out, size_t n, void* stream) {
 sfx_status sfx_df_unpack(const void* in, double* out, size_t n, void* stream) {
   if ((!in || !out) && n) return SFX_ERR_ARG;
   return df_unpack(in, out, n, S(stream));
-}
-
-sfx_status sfx_phi_fold(const double* phi, float* out, size_t n, void* stream) {
-  if ((!phi || !out) && n) return SFX_ERR_ARG;
-  return phi_fold(phi, out, n, S(stream));
 }
 
 sfx_status sfx_profile(sfx_ctx* c, int on) {

@@ -1,0 +1,606 @@
+// Batched SFX_F32 step over many independent axisymmetric instances of
+// uneven sizes and parameters.
+//
+// Every phase of the coupled step (drift faces, BCG advection, the coupled
+// Newton residual, the coupled correction sweeps, per-instance convergence
+// flags, per-instance totals) is one kernel over all instances: blocks are
+// dealt to instances through prefix tables, so a block never straddles two
+// instances.  An instance whose residuals pass the tolerance is switched off
+// and its blocks return at once.  The whole step is captured into a CUDA
+// graph on first use (and again when a pointer or the schedule changes) and
+// replayed, one graph launch per step with no host synchronisation.  The
+// per-cell arithmetic is the single-grid SFX_F32 code (sfx_f32_dev.cuh).
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "sfx_df.cuh"
+#include "sfx_f32_dev.cuh"
+#include "sfx_internal.h"
+
+namespace sfx {
+namespace {
+
+struct BInst {
+  Nw32 p;                 // grid (axisymmetric, nx = nr, ny = nz) and coefficients
+  float dt, bc_f, bc_F, Df, DF;
+  size_t coff, rfoff, zfoff;    // offsets of cells, radial faces, axial faces
+};
+
+// block -> instance through a prefix table of block counts
+__device__ __forceinline__ int find_inst(const int* __restrict__ pre, int n, int b) {
+  int lo = 0, hi = n;   // pre[lo] <= b < pre[hi]
+  while (hi - lo > 1) {
+    int mid = (lo + hi) >> 1;
+    if (pre[mid] <= b) lo = mid;
+    else hi = mid;
+  }
+  return lo;
+}
+
+struct BPtr {
+  const double* phi;      // phase field (caller's)
+  float* phi32;           // its folded float copy
+  const float* ur;
+  const float* uz;
+  float2* f;
+  float2* F;
+  float2* fs;
+  float2* Fs;
+  float* Bf[2];           // radial, axial drift faces of the f problem
+  float* BF[2];
+  float4* coef;
+  float2* res;
+  float* ef;
+  float* eF;
+  unsigned int* norms;    // 4 per instance
+  int* active;
+  int* iters;
+  float* rres;            // 2 per instance: last relative residuals
+  double* mass;           // 2 per instance
+  unsigned long long* work;   // 2 per instance: residual passes, sweep groups
+};
+
+// drift faces: blocks over radial faces then axial faces of every instance
+__global__ void k_b_drift(const BInst* __restrict__ I, int n, const int* __restrict__ pre, int dir,
+                          BPtr P) {
+  const int inst = find_inst(pre, n, blockIdx.x);
+  const BInst& B = I[inst];
+  const Level& L = B.p.L;
+  const size_t nf = L.nface(dir);
+  const size_t q = (size_t)(blockIdx.x - pre[inst]) * blockDim.x + threadIdx.x;
+  if (q >= nf) return;
+  const size_t fo = dir == 0 ? B.rfoff : B.zfoff;
+  float* Bf = P.Bf[dir] + fo;
+  float* BF = P.BF[dir] + fo;
+  const double* phi = P.phi + B.coff;
+  const int fx = L.nx + (dir == 0);
+  const int i = (int)(q % fx), j = (int)(q / fx);
+  const int pos = dir == 0 ? i : j;
+  if (pos == 0 || pos == L.extent(dir)) { Bf[q] = 0.0f; BF[q] = 0.0f; return; }
+  const int li = i - (dir == 0), lj = j - (dir == 1);
+  const float sL = fold_phi(phi[cidx(L, li, lj, 0)]), sR = fold_phi(phi[cidx(L, i, j, 0)]);
+  const float nL = normal_f32(L, phi, li, lj, 0, dir, B.p.inv_eps);
+  const float nR = normal_f32(L, phi, i, j, 0, dir, B.p.inv_eps);
+  drift_face(sL, sR, nL, nR, B.Df, B.DF, B.p.inv_eps, Bf[q], BF[q]);
+}
+
+__global__ void k_b_advect(const BInst* __restrict__ I, int n, const int* __restrict__ pre, BPtr P) {
+  const int inst = find_inst(pre, n, blockIdx.x);
+  const BInst& B = I[inst];
+  const Level& L = B.p.L;
+  const size_t c = (size_t)(blockIdx.x - pre[inst]) * blockDim.x + threadIdx.x;
+  if (c >= L.ncell()) return;
+  Adv32 A{L, B.dt, B.p.invh, {P.ur + B.rfoff, P.uz + B.zfoff, nullptr}};
+  P.fs[B.coff + c] = advect_cell(A, P.f + B.coff, B.bc_f, c);
+  P.Fs[B.coff + c] = advect_cell(A, P.F + B.coff, B.bc_F, c);
+}
+
+// folded float copy of phi, and the start of the step
+__global__ void k_b_fold(const BInst* __restrict__ I, int n, const int* __restrict__ pre, BPtr P) {
+  const int inst = find_inst(pre, n, blockIdx.x);
+  const BInst& B = I[inst];
+  const size_t c = (size_t)(blockIdx.x - pre[inst]) * blockDim.x + threadIdx.x;
+  if (c >= B.p.L.ncell()) return;
+  P.phi32[B.coff + c] = fold_phi(P.phi[B.coff + c]);
+}
+
+// state <- post-advection fields (the Newton iteration starts there)
+__global__ void k_b_copy(const BInst* __restrict__ I, int n, const int* __restrict__ pre, BPtr P,
+                         int from_star) {
+  const int inst = find_inst(pre, n, blockIdx.x);
+  const BInst& B = I[inst];
+  const size_t c = (size_t)(blockIdx.x - pre[inst]) * blockDim.x + threadIdx.x;
+  if (c >= B.p.L.ncell()) return;
+  const size_t g = B.coff + c;
+  if (from_star) { P.f[g] = P.fs[g]; P.F[g] = P.Fs[g]; }
+  else { P.fs[g] = P.f[g]; P.Fs[g] = P.F[g]; }
+}
+
+__global__ void k_b_init(int n, BPtr P) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  P.active[i] = 1;
+  P.iters[i] = 0;
+  for (int q = 0; q < 4; ++q) P.norms[4 * i + q] = 0u;
+}
+
+__global__ void k_b_resid(const BInst* __restrict__ I, int n, const int* __restrict__ pre, BPtr P) {
+  const int inst = find_inst(pre, n, blockIdx.x);
+  if (!P.active[inst]) return;
+  const BInst& B = I[inst];
+  const Level& L = B.p.L;
+  const size_t c = (size_t)(blockIdx.x - pre[inst]) * blockDim.x + threadIdx.x;
+  float m[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+  if (c < L.ncell()) {
+    const int i = (int)(c % L.nx), j = (int)(c / L.nx);
+    const float* Bf[3] = {P.Bf[0] + B.rfoff, P.Bf[1] + B.zfoff, nullptr};
+    const float* BF[3] = {P.BF[0] + B.rfoff, P.BF[1] + B.zfoff, nullptr};
+    const size_t o = B.coff;
+    resid2_cell(B.p, i, j, 0, c, P.phi32 + o, Bf, BF, P.f + o, P.F + o, P.fs + o, P.Fs + o,
+                P.coef + o, P.res + o, m);
+  }
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    float v = warp_max(m[q]);
+    if ((threadIdx.x & 31) == 0) atomicMax(&P.norms[4 * inst + q], __float_as_uint(v));
+  }
+}
+
+// convergence test of iteration `it` for every instance still active
+__global__ void k_b_flags(int n, BPtr P, float tol, int it) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n || !P.active[i]) return;
+  const float rf = __uint_as_float(P.norms[4 * i]), bf = __uint_as_float(P.norms[4 * i + 1]);
+  const float rF = __uint_as_float(P.norms[4 * i + 2]), bF = __uint_as_float(P.norms[4 * i + 3]);
+  P.rres[2 * i] = rf / fmaxf(bf, 1e-30f);
+  P.rres[2 * i + 1] = rF / fmaxf(bF, 1e-30f);
+  P.iters[i] = it;
+  P.work[2 * i] += 1;
+  if (rf <= tol * bf && rF <= tol * bF) P.active[i] = 0;   // converged: stop here
+  else P.work[2 * i + 1] += 1;                             // the sweeps run
+  for (int q = 0; q < 4; ++q) P.norms[4 * i + q] = 0u;
+}
+
+// one colour of the coupled correction sweep; blocks over half-rows
+__global__ void k_b_corr(const BInst* __restrict__ I, int n, const int* __restrict__ pre, BPtr P,
+                         int color, int first, int apply) {
+  const int inst = find_inst(pre, n, blockIdx.x);
+  if (!P.active[inst]) return;
+  const BInst& B = I[inst];
+  const Level& L = B.p.L;
+  const int half = (L.nx + 1) / 2;
+  const size_t t = (size_t)(blockIdx.x - pre[inst]) * blockDim.x + threadIdx.x;
+  if (t >= (size_t)half * L.ny) return;
+  const int j = (int)(t / half);
+  const int i = 2 * (int)(t % half) + ((j + color) & 1);
+  const size_t o = B.coff;
+  float2* fst = apply ? P.f + o : nullptr;
+  float2* Fst = apply ? P.F + o : nullptr;
+  if (i >= L.nx) {
+    const int ir = i ^ 1;
+    if (apply && ir < L.nx) {
+      const size_t cr = cidx(L, ir, j, 0);
+      fst[cr] = df_add(fst[cr], P.ef[o + cr]);
+      Fst[cr] = df_add(Fst[cr], P.eF[o + cr]);
+    }
+    return;
+  }
+  const float* Bf[3] = {P.Bf[0] + B.rfoff, P.Bf[1] + B.zfoff, nullptr};
+  const float* BF[3] = {P.BF[0] + B.rfoff, P.BF[1] + B.zfoff, nullptr};
+  corr2_cell(B.p, i, j, 0, Bf, BF, P.coef + o, P.res + o, P.ef + o, P.eF + o, color, first, fst,
+             Fst);
+}
+
+// per-instance compensated totals: one block per (instance, field)
+__global__ void k_b_totals(const BInst* __restrict__ I, BPtr P) {
+  const int inst = blockIdx.x >> 1, fld = blockIdx.x & 1;
+  const BInst& B = I[inst];
+  const Level& L = B.p.L;
+  const float2* x = (fld ? P.F : P.f) + B.coff;
+  float2 acc = make_float2(0.0f, 0.0f);
+  for (size_t c = threadIdx.x; c < L.ncell(); c += blockDim.x) {
+    float2 v = x[c];
+    const float w = 2.0f * (float)(c % L.nx) + 1.0f;   // ring volume / (pi h^3)
+    const float pr = v.x * w;
+    v = make_float2(pr, fmaf(v.x, w, -pr) + v.y * w);
+    acc = df_add2(acc, v);
+  }
+  double s = (double)acc.x, cc = (double)acc.y;
+  warp_sum_comp(s, cc);
+  __shared__ double ss[32], sc[32];
+  const int w = threadIdx.x >> 5;
+  if ((threadIdx.x & 31) == 0) { ss[w] = s; sc[w] = cc; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double a = ss[0], b = sc[0];
+    for (int q = 1; q < (int)(blockDim.x >> 5); ++q) {
+      double t, e;
+      two_sum(a, ss[q], t, e);
+      a = t;
+      b += sc[q] + e;
+    }
+    const double h = L.h;
+    P.mass[2 * inst + fld] = (a + b) * kPi * h * h * h;
+  }
+}
+
+}  // namespace
+}  // namespace sfx
+
+using namespace sfx;
+
+struct sfx_batch {
+  int n = 0;
+  std::vector<sfx_batch_instance> hinst;
+  std::vector<BInst> hI;
+  size_t ncell = 0, nrf = 0, nzf = 0;
+  std::vector<size_t> coff, rfoff, zfoff;
+  BInst* dI = nullptr;
+  int* pre_cell = nullptr;   // blocks of `block` threads over cells
+  int* pre_rf = nullptr;
+  int* pre_zf = nullptr;
+  int* pre_pair = nullptr;
+  int nb_cell = 0, nb_rf = 0, nb_zf = 0, nb_pair = 0;
+  int block = 256;
+  BPtr P{};
+  std::vector<void*> allocs;
+  // graph cache
+  cudaGraphExec_t exec = nullptr;
+  const void* key[5] = {};
+  int key_sched[4] = {};
+  double key_tol = 0;
+  cudaStream_t cap = nullptr;
+  // last schedule
+  int sweeps = 3, max_it = 8;
+  std::vector<int> h_iters;
+};
+
+namespace {
+
+template <typename T>
+sfx_status balloc(sfx_batch* b, T** p, size_t n) {
+  void* q = nullptr;
+  SFX_CUDA(cudaMalloc(&q, (n ? n : 1) * sizeof(T)));
+  b->allocs.push_back(q);
+  *p = (T*)q;
+  return SFX_OK;
+}
+
+// prefix tables of blocks per instance for the current block size
+sfx_status build_prefix(sfx_batch* b) {
+  const int bs = b->block;
+  std::vector<int> pc(b->n + 1), pr(b->n + 1), pz(b->n + 1), pp(b->n + 1);
+  pc[0] = pr[0] = pz[0] = pp[0] = 0;
+  for (int i = 0; i < b->n; ++i) {
+    const Level& L = b->hI[i].p.L;
+    pc[i + 1] = pc[i] + (int)((L.ncell() + bs - 1) / bs);
+    pr[i + 1] = pr[i] + (int)((L.nface(0) + bs - 1) / bs);
+    pz[i + 1] = pz[i] + (int)((L.nface(1) + bs - 1) / bs);
+    pp[i + 1] = pp[i] + (int)(((size_t)((L.nx + 1) / 2) * L.ny + bs - 1) / bs);
+  }
+  b->nb_cell = pc[b->n];
+  b->nb_rf = pr[b->n];
+  b->nb_zf = pz[b->n];
+  b->nb_pair = pp[b->n];
+  SFX_CUDA(cudaMemcpy(b->pre_cell, pc.data(), pc.size() * sizeof(int), cudaMemcpyHostToDevice));
+  SFX_CUDA(cudaMemcpy(b->pre_rf, pr.data(), pr.size() * sizeof(int), cudaMemcpyHostToDevice));
+  SFX_CUDA(cudaMemcpy(b->pre_zf, pz.data(), pz.size() * sizeof(int), cudaMemcpyHostToDevice));
+  SFX_CUDA(cudaMemcpy(b->pre_pair, pp.data(), pp.size() * sizeof(int), cudaMemcpyHostToDevice));
+  return SFX_OK;
+}
+
+// enqueue one batched step on s (used under stream capture)
+sfx_status enqueue_step(sfx_batch* b, bool advect, float tol, cudaStream_t s) {
+  const int n = b->n, bs = b->block;
+  BPtr& P = b->P;
+  k_b_init<<<(n + 127) / 128, 128, 0, s>>>(n, P);
+  k_b_fold<<<b->nb_cell, bs, 0, s>>>(b->dI, n, b->pre_cell, P);
+  k_b_drift<<<b->nb_rf, bs, 0, s>>>(b->dI, n, b->pre_rf, 0, P);
+  k_b_drift<<<b->nb_zf, bs, 0, s>>>(b->dI, n, b->pre_zf, 1, P);
+  if (advect) {
+    k_b_advect<<<b->nb_cell, bs, 0, s>>>(b->dI, n, b->pre_cell, P);
+    k_b_copy<<<b->nb_cell, bs, 0, s>>>(b->dI, n, b->pre_cell, P, 1);
+  } else {
+    k_b_copy<<<b->nb_cell, bs, 0, s>>>(b->dI, n, b->pre_cell, P, 0);
+  }
+  for (int it = 1; it <= b->max_it; ++it) {
+    k_b_resid<<<b->nb_cell, bs, 0, s>>>(b->dI, n, b->pre_cell, P);
+    k_b_flags<<<(n + 127) / 128, 128, 0, s>>>(n, P, tol, it);
+    for (int q = 0; q < b->sweeps; ++q)
+      for (int color = 0; color < 2; ++color)
+        k_b_corr<<<b->nb_pair, bs, 0, s>>>(b->dI, n, b->pre_pair, P, color, q == 0 ? 1 : 0,
+                                           q == b->sweeps - 1 && color == 1 ? 1 : 0);
+  }
+  k_b_totals<<<2 * n, 256, 0, s>>>(b->dI, P);
+  SFX_LAUNCH_CHECK();
+  return SFX_OK;
+}
+
+sfx_status ensure_graph(sfx_batch* b, const void* phi, const void* ur, const void* uz, void* f,
+                        void* F, float tol) {
+  const void* k[5] = {phi, ur, uz, f, F};
+  const int sched[4] = {b->block, b->sweeps, b->max_it, ur != nullptr};
+  bool same = b->exec != nullptr && tol == b->key_tol;
+  for (int i = 0; i < 5 && same; ++i) same = k[i] == b->key[i];
+  for (int i = 0; i < 4 && same; ++i) same = sched[i] == b->key_sched[i];
+  if (same) return SFX_OK;
+  if (b->exec) {
+    cudaGraphExecDestroy(b->exec);
+    b->exec = nullptr;
+  }
+  b->P.phi = (const double*)phi;
+  b->P.ur = (const float*)ur;
+  b->P.uz = (const float*)uz;
+  b->P.f = (float2*)f;
+  b->P.F = (float2*)F;
+  if (!b->cap) SFX_CUDA(cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking));
+  cudaGraph_t g = nullptr;
+  SFX_CUDA(cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal));
+  sfx_status st = enqueue_step(b, ur != nullptr, tol, b->cap);
+  cudaError_t e = cudaStreamEndCapture(b->cap, &g);
+  if (st != SFX_OK) {
+    if (g) cudaGraphDestroy(g);
+    return st;
+  }
+  SFX_CUDA(e);
+  e = cudaGraphInstantiate(&b->exec, g, 0);
+  cudaGraphDestroy(g);
+  SFX_CUDA(e);
+  for (int i = 0; i < 5; ++i) b->key[i] = k[i];
+  for (int i = 0; i < 4; ++i) b->key_sched[i] = sched[i];
+  b->key_tol = tol;
+  return SFX_OK;
+}
+
+bool inst_ok(const sfx_batch_instance& q) {
+  return q.nr >= 1 && q.nz >= 1 && q.h > 0.0 && q.dt > 0.0 && q.params.eps > 0.0 &&
+         q.params.gamma_inf > 0.0 && q.params.ka >= 0.0 && q.params.kd >= 0.0 &&
+         q.params.Df >= 0.0 && q.params.DF >= 0.0;
+}
+
+}  // namespace
+
+extern "C" {
+
+sfx_status sfx_batch_create(const sfx_batch_instance* inst, int n, sfx_batch** out) {
+  if (!out || !inst || n < 1) return SFX_ERR_ARG;
+  *out = nullptr;
+  for (int i = 0; i < n; ++i)
+    if (!inst_ok(inst[i])) return SFX_ERR_ARG;
+  sfx_batch* b = new sfx_batch();
+  b->n = n;
+  b->hinst.assign(inst, inst + n);
+  for (int i = 0; i < n; ++i) {
+    const sfx_batch_instance& q = inst[i];
+    BInst B{};
+    Level L{SFX_AXISYM, q.nr, q.nz, 1, q.h};
+    B.p = Nw32{L, (float)(1.0 / q.h), (float)(q.params.Df / q.h), (float)(q.params.DF / q.h),
+               (float)(1.0 / q.dt), (float)q.params.ka, (float)q.params.kd,
+               (float)q.params.gamma_inf, (float)(1.0 / q.params.eps), (float)q.params.eta,
+               q.params.literal_upwind};
+    B.dt = (float)q.dt;
+    B.bc_f = (float)q.params.bc_f;
+    B.bc_F = (float)q.params.bc_F;
+    B.Df = (float)q.params.Df;
+    B.DF = (float)q.params.DF;
+    B.coff = b->ncell;
+    B.rfoff = b->nrf;
+    B.zfoff = b->nzf;
+    b->coff.push_back(b->ncell);
+    b->rfoff.push_back(b->nrf);
+    b->zfoff.push_back(b->nzf);
+    b->ncell += L.ncell();
+    b->nrf += L.nface(0);
+    b->nzf += L.nface(1);
+    b->hI.push_back(B);
+  }
+  sfx_status st = SFX_OK;
+  const size_t nc = b->ncell;
+  BPtr& P = b->P;
+  if (st == SFX_OK) st = balloc(b, &b->dI, (size_t)n);
+  if (st == SFX_OK) st = balloc(b, &b->pre_cell, (size_t)n + 1);
+  if (st == SFX_OK) st = balloc(b, &b->pre_rf, (size_t)n + 1);
+  if (st == SFX_OK) st = balloc(b, &b->pre_zf, (size_t)n + 1);
+  if (st == SFX_OK) st = balloc(b, &b->pre_pair, (size_t)n + 1);
+  if (st == SFX_OK) st = balloc(b, &P.phi32, nc);
+  if (st == SFX_OK) st = balloc(b, &P.fs, nc);
+  if (st == SFX_OK) st = balloc(b, &P.Fs, nc);
+  if (st == SFX_OK) st = balloc(b, &P.Bf[0], b->nrf);
+  if (st == SFX_OK) st = balloc(b, &P.Bf[1], b->nzf);
+  if (st == SFX_OK) st = balloc(b, &P.BF[0], b->nrf);
+  if (st == SFX_OK) st = balloc(b, &P.BF[1], b->nzf);
+  if (st == SFX_OK) st = balloc(b, &P.coef, nc);
+  if (st == SFX_OK) st = balloc(b, &P.res, nc);
+  if (st == SFX_OK) st = balloc(b, &P.ef, nc);
+  if (st == SFX_OK) st = balloc(b, &P.eF, nc);
+  if (st == SFX_OK) st = balloc(b, &P.norms, 4 * (size_t)n);
+  if (st == SFX_OK) st = balloc(b, &P.active, (size_t)n);
+  if (st == SFX_OK) st = balloc(b, &P.iters, (size_t)n);
+  if (st == SFX_OK) st = balloc(b, &P.rres, 2 * (size_t)n);
+  if (st == SFX_OK) st = balloc(b, &P.mass, 2 * (size_t)n);
+  if (st == SFX_OK) st = balloc(b, &P.work, 2 * (size_t)n);
+  if (st == SFX_OK) {
+    cudaError_t e = cudaMemset(P.work, 0, 2 * (size_t)n * sizeof(unsigned long long));
+    if (e != cudaSuccess) st = cuda_fail(e);
+  }
+  if (st == SFX_OK) {
+    cudaError_t e = cudaMemcpy(b->dI, b->hI.data(), n * sizeof(BInst), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) st = cuda_fail(e);
+  }
+  if (st == SFX_OK) st = build_prefix(b);
+  if (st != SFX_OK) {
+    sfx_batch_destroy(b);
+    return st;
+  }
+  *out = b;
+  return SFX_OK;
+}
+
+void sfx_batch_destroy(sfx_batch* b) {
+  if (!b) return;
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->cap) cudaStreamDestroy(b->cap);
+  for (void* p : b->allocs) cudaFree(p);
+  delete b;
+}
+
+sfx_status sfx_batch_layout(const sfx_batch* b, size_t* n_cells, size_t* n_rfaces,
+                            size_t* n_zfaces, size_t* cell_off, size_t* rface_off,
+                            size_t* zface_off) {
+  if (!b) return SFX_ERR_ARG;
+  if (n_cells) *n_cells = b->ncell;
+  if (n_rfaces) *n_rfaces = b->nrf;
+  if (n_zfaces) *n_zfaces = b->nzf;
+  for (int i = 0; i < b->n; ++i) {
+    if (cell_off) cell_off[i] = b->coff[i];
+    if (rface_off) rface_off[i] = b->rfoff[i];
+    if (zface_off) zface_off[i] = b->zfoff[i];
+  }
+  return SFX_OK;
+}
+
+sfx_status sfx_batch_set_schedule(sfx_batch* b, int block, int sweeps, int max_iters) {
+  if (!b || (block != 128 && block != 256 && block != 512) || sweeps < 1 || sweeps > 16 ||
+      max_iters < 1 || max_iters > 200)
+    return SFX_ERR_ARG;
+  if (block != b->block) {
+    b->block = block;
+    sfx_status st = build_prefix(b);
+    if (st != SFX_OK) return st;
+  }
+  b->sweeps = sweeps;
+  b->max_it = max_iters;
+  return SFX_OK;
+}
+
+sfx_status sfx_batch_step(sfx_batch* b, const void* phi, const void* ur, const void* uz, void* f,
+                          void* F, double tol, void* stream) {
+  if (!b || !phi || !f || !F || f == F || !(tol > 0.0)) return SFX_ERR_ARG;
+  if ((ur == nullptr) != (uz == nullptr)) return SFX_ERR_ARG;
+  sfx_status st = ensure_graph(b, phi, ur, uz, f, F, (float)tol);
+  if (st != SFX_OK) return st;
+  SFX_CUDA(cudaGraphLaunch(b->exec, (cudaStream_t)stream));
+  return SFX_OK;
+}
+
+sfx_status sfx_batch_stats(sfx_batch* b, int* iters, float* res_f, float* res_F, double* mass_f,
+                           double* mass_F, int* converged, void* stream) {
+  if (!b) return SFX_ERR_ARG;
+  const int n = b->n;
+  cudaStream_t s = (cudaStream_t)stream;
+  std::vector<int> it(n), act(n);
+  std::vector<float> rr(2 * n);
+  std::vector<double> m(2 * n);
+  SFX_CUDA(cudaMemcpyAsync(it.data(), b->P.iters, n * sizeof(int), cudaMemcpyDeviceToHost, s));
+  SFX_CUDA(cudaMemcpyAsync(act.data(), b->P.active, n * sizeof(int), cudaMemcpyDeviceToHost, s));
+  SFX_CUDA(cudaMemcpyAsync(rr.data(), b->P.rres, 2 * n * sizeof(float), cudaMemcpyDeviceToHost, s));
+  SFX_CUDA(cudaMemcpyAsync(m.data(), b->P.mass, 2 * n * sizeof(double), cudaMemcpyDeviceToHost, s));
+  SFX_CUDA(cudaStreamSynchronize(s));
+  for (int i = 0; i < n; ++i) {
+    if (iters) iters[i] = it[i];
+    if (res_f) res_f[i] = rr[2 * i];
+    if (res_F) res_F[i] = rr[2 * i + 1];
+    if (mass_f) mass_f[i] = m[2 * i];
+    if (mass_F) mass_F[i] = m[2 * i + 1];
+    if (converged) converged[i] = act[i] ? 0 : 1;
+  }
+  return SFX_OK;
+}
+
+sfx_status sfx_batch_work(sfx_batch* b, long long* resid_passes, long long* sweep_groups,
+                          int reset, void* stream) {
+  if (!b) return SFX_ERR_ARG;
+  const int n = b->n;
+  cudaStream_t s = (cudaStream_t)stream;
+  std::vector<unsigned long long> w(2 * (size_t)n);
+  SFX_CUDA(cudaMemcpyAsync(w.data(), b->P.work, w.size() * sizeof(unsigned long long),
+                           cudaMemcpyDeviceToHost, s));
+  SFX_CUDA(cudaStreamSynchronize(s));
+  for (int i = 0; i < n; ++i) {
+    if (resid_passes) resid_passes[i] = (long long)w[2 * i];
+    if (sweep_groups) sweep_groups[i] = (long long)w[2 * i + 1];
+  }
+  if (reset) SFX_CUDA(cudaMemsetAsync(b->P.work, 0, w.size() * sizeof(unsigned long long), s));
+  return SFX_OK;
+}
+
+// Autotuner: candidate schedules (block size x sweeps per iteration) are run
+// on scratch copies of the state; each gets the smallest iteration budget
+// that converges every instance (read from a probe step with a generous
+// budget), then the fastest candidate is kept.
+sfx_status sfx_batch_autotune(sfx_batch* b, const void* phi, const void* ur, const void* uz,
+                              const void* f, const void* F, double tol, void* stream,
+                              int* chosen) {
+  if (!b || !phi || !f || !F) return SFX_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t bytes = b->ncell * sizeof(float2);
+  float2 *fw = nullptr, *Fw = nullptr;
+  SFX_CUDA(cudaMalloc(&fw, bytes));
+  SFX_CUDA(cudaMalloc(&Fw, bytes));
+  const int blocks[2] = {128, 256};
+  const int sweeps[3] = {2, 3, 4};
+  float best = 1e30f;
+  int bb = b->block, bsw = b->sweeps, bit = b->max_it;
+  cudaEvent_t e0, e1;
+  SFX_CUDA(cudaEventCreate(&e0));
+  SFX_CUDA(cudaEventCreate(&e1));
+  sfx_status st = SFX_OK;
+  std::vector<int> it(b->n), conv(b->n);
+  for (int bi = 0; bi < 2 && st == SFX_OK; ++bi)
+    for (int si = 0; si < 3 && st == SFX_OK; ++si) {
+      // probe: generous budget, read the iterations each instance needs
+      if ((st = sfx_batch_set_schedule(b, blocks[bi], sweeps[si], 40)) != SFX_OK) break;
+      SFX_CUDA(cudaMemcpyAsync(fw, f, bytes, cudaMemcpyDeviceToDevice, s));
+      SFX_CUDA(cudaMemcpyAsync(Fw, F, bytes, cudaMemcpyDeviceToDevice, s));
+      if ((st = sfx_batch_step(b, phi, ur, uz, fw, Fw, tol, stream)) != SFX_OK) break;
+      if ((st = sfx_batch_stats(b, it.data(), nullptr, nullptr, nullptr, nullptr, conv.data(),
+                                stream)) != SFX_OK) break;
+      int need = 1;
+      bool all = true;
+      for (int i = 0; i < b->n; ++i) {
+        need = std::max(need, it[i]);
+        all = all && conv[i];
+      }
+      if (!all) continue;
+      if ((st = sfx_batch_set_schedule(b, blocks[bi], sweeps[si], need + 1)) != SFX_OK) break;
+      float ms_best = 1e30f;
+      for (int rep = 0; rep < 3; ++rep) {
+        SFX_CUDA(cudaMemcpyAsync(fw, f, bytes, cudaMemcpyDeviceToDevice, s));
+        SFX_CUDA(cudaMemcpyAsync(Fw, F, bytes, cudaMemcpyDeviceToDevice, s));
+        if ((st = ensure_graph(b, phi, ur, uz, fw, Fw, (float)tol)) != SFX_OK) break;
+        SFX_CUDA(cudaEventRecord(e0, s));
+        SFX_CUDA(cudaGraphLaunch(b->exec, s));
+        SFX_CUDA(cudaEventRecord(e1, s));
+        SFX_CUDA(cudaEventSynchronize(e1));
+        float ms = 0.f;
+        SFX_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+        ms_best = std::min(ms_best, ms);
+      }
+      if (ms_best < best) {
+        best = ms_best;
+        bb = blocks[bi];
+        bsw = sweeps[si];
+        bit = need + 1;
+      }
+    }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (b->exec) {   // its pointers are the scratch copies freed below
+    cudaGraphExecDestroy(b->exec);
+    b->exec = nullptr;
+  }
+  cudaFree(fw);
+  cudaFree(Fw);
+  if (st != SFX_OK) return st;
+  st = sfx_batch_set_schedule(b, bb, bsw, bit);
+  if (chosen) {
+    chosen[0] = bb;
+    chosen[1] = bsw;
+    chosen[2] = bit;
+  }
+  return st;
+}
+
+}  // extern "C"

@@ -82,11 +82,17 @@ __device__ inline void warp_sum_comp(double& s, double& c) {
   }
 }
 
+// n is undefined where phi is flat: beyond the redistancing band phi is
+// flat up to variations far below its own profile slope phi (1 - phi)/eps,
+// whose direction is set by the last bits of phi.  n = 0 where
+// |grad phi| < kNormalKappa phi (1 - phi)/eps or |grad phi| < 1e-30.
+constexpr double kNormalKappa = 1e-3;
+
 // Unit normal component n_d = (grad phi)_d / |grad phi| at cell (i,j,k):
-// centred differences, zero-gradient walls, n = 0 where |grad phi| < 1e-30.
+// centred differences, zero-gradient walls, 0 where phi is flat (above).
 template <typename P>
 __device__ __forceinline__ double normal_comp(const Level& L, const P* __restrict__ phi, int i,
-                                              int j, int k, int d) {
+                                              int j, int k, int d, double eps) {
   double g[3] = {0.0, 0.0, 0.0};
   const double inv2h = 0.5 / L.h;
   int ip = min(i + 1, L.nx - 1), im = max(i - 1, 0);
@@ -98,7 +104,9 @@ __device__ __forceinline__ double normal_comp(const Level& L, const P* __restric
     g[2] = ((double)phi[cidx(L, i, j, kp)] - (double)phi[cidx(L, i, j, km)]) * inv2h;
   }
   double m = sqrt(g[0] * g[0] + g[1] * g[1] + g[2] * g[2]);
-  return m < 1e-30 ? 0.0 : g[d] / m;
+  const double pc = (double)phi[cidx(L, i, j, k)];
+  const double slope = pc * (1.0 - pc) / eps;
+  return (m < 1e-30 || m < kNormalKappa * slope) ? 0.0 : g[d] / m;
 }
 
 }  // namespace sfx

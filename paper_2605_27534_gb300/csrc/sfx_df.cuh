@@ -89,10 +89,4 @@ __device__ __forceinline__ PhiPair unfold(float s) {
   return signbit(s) ? PhiPair{__fadd_rn(1.0f, s), -s} : PhiPair{s, __fsub_rn(1.0f, s)};
 }
 
-// phi_R - phi_L from folded values, exact leading part on either side
-__device__ __forceinline__ float dphi(float sR, float sL) {
-  if (signbit(sR) == signbit(sL)) return __fsub_rn(sR, sL);
-  return __fsub_rn(unfold(sR).p, unfold(sL).p);
-}
-
 }  // namespace sfx

@@ -27,36 +27,13 @@
 #include <cstring>
 
 #include "sfx_df.cuh"
+#include "sfx_f32_dev.cuh"
 #include "sfx_internal.h"
 
 namespace sfx {
 namespace {
 
-__device__ __forceinline__ unsigned int fbits(float v) { return __float_as_uint(v); }
-
-// ------------------------------------------------------------ drifts
-// Face drifts of both problems from the FP32 phase field (App. C):
-// B_f = -Df 2(0.5 - phi)/eps n, B_F = -DF (1 - phi)/eps n, face mean, walls 0.
-__device__ __forceinline__ float normal32(const Level& L, const float* __restrict__ phi, int i,
-                                          int j, int k, int d) {
-  int ip = min(i + 1, L.nx - 1), im = max(i - 1, 0);
-  int jp = min(j + 1, L.ny - 1), jm = max(j - 1, 0);
-  float g0 = dphi(phi[cidx(L, ip, j, k)], phi[cidx(L, im, j, k)]);
-  float g1 = dphi(phi[cidx(L, i, jp, k)], phi[cidx(L, i, jm, k)]);
-  float g2 = 0.0f;
-  if (L.geom == SFX_CART3D) {
-    int kp = min(k + 1, L.nz - 1), km = max(k - 1, 0);
-    g2 = dphi(phi[cidx(L, i, j, kp)], phi[cidx(L, i, j, km)]);
-  }
-  // the 1/(2h) of the centred difference cancels in the normalisation
-  float m2 = g0 * g0 + g1 * g1 + g2 * g2;
-  float g = d == 0 ? g0 : (d == 1 ? g1 : g2);
-  float inv2h = 0.5f / (float)L.h;
-  if (m2 * inv2h * inv2h < 1e-30f) return 0.0f;
-  return g * rsqrtf(m2);
-}
-
-__global__ void k_drift32(Level L, int d, const float* __restrict__ phi, float Df, float DF,
+__global__ void k_drift32(Level L, int d, const double* __restrict__ phi, float Df, float DF,
                           float inv_eps, float* __restrict__ Bf, float* __restrict__ BF) {
   size_t n = L.nface(d);
   int fx = L.nx + (d == 0), fy = L.ny + (d == 1);
@@ -66,70 +43,14 @@ __global__ void k_drift32(Level L, int d, const float* __restrict__ phi, float D
     int pos = d == 0 ? i : (d == 1 ? j : k);
     if (pos == 0 || pos == L.extent(d)) { Bf[q] = 0.0f; BF[q] = 0.0f; continue; }
     int li = i - (d == 0), lj = j - (d == 1), lk = k - (d == 2);
-    float sL = phi[cidx(L, li, lj, lk)], sR = phi[cidx(L, i, j, k)];
-    PhiPair uL = unfold(sL), uR = unfold(sR);
-    // 0.5 - phi from the folded value keeps its precision on both sides
-    float hL = signbit(sL) ? -0.5f - sL : 0.5f - sL;
-    float hR = signbit(sR) ? -0.5f - sR : 0.5f - sR;
-    float nL = normal32(L, phi, li, lj, lk, d), nR = normal32(L, phi, i, j, k, d);
-    Bf[q] = 0.5f * ((-Df * 2.0f * hL * inv_eps) * nL + (-Df * 2.0f * hR * inv_eps) * nR);
-    BF[q] = 0.5f * ((-DF * uL.q * inv_eps) * nL + (-DF * uR.q * inv_eps) * nR);
+    const float sL = fold_phi(phi[cidx(L, li, lj, lk)]), sR = fold_phi(phi[cidx(L, i, j, k)]);
+    const float nL = normal_f32(L, phi, li, lj, lk, d, inv_eps);
+    const float nR = normal_f32(L, phi, i, j, k, d, inv_eps);
+    drift_face(sL, sR, nL, nR, Df, DF, inv_eps, Bf[q], BF[q]);
   }
 }
 
 // ------------------------------------------------------------ sweeps
-struct Nl32 {
-  Level L;
-  float invh, Doh, inv_dt, ka, kd, ginf, inv_eps, eta;
-  int literal;
-};
-
-// Area weight of a face relative to h^(d-1) (planar, 3D: 1) or to pi h^2
-// (axisymmetric: 2 i for the radial face at r = i h, 2 i + 1 for the axial
-// faces of column i); the cell volume over the same unit times h is w_c h.
-__device__ __forceinline__ float wr_face(int geom, int iface) {
-  return geom == SFX_AXISYM ? 2.0f * (float)iface : 1.0f;
-}
-__device__ __forceinline__ float wz_face(int geom, int i) {
-  return geom == SFX_AXISYM ? 2.0f * (float)i + 1.0f : 1.0f;
-}
-
-// Unnormalised pair accumulator: hi by error-free two-sums, everything else
-// gathered in lo; normalised once at the end.
-struct Acc {
-  float hi, lo;
-};
-__device__ __forceinline__ void acc_add(Acc& s, float2 x) {
-  float2 t = ef_two_sum(s.hi, x.x);
-  s.hi = t.x;
-  s.lo = __fadd_rn(s.lo, __fadd_rn(t.y, x.y));
-}
-__device__ __forceinline__ void acc_sub(Acc& s, float2 x) { acc_add(s, make_float2(-x.x, -x.y)); }
-__device__ __forceinline__ float2 acc_get(const Acc& s) { return ef_fast_two_sum(s.hi, s.lo); }
-
-// unnormalised products and differences (exact leading part + error term)
-__device__ __forceinline__ float2 lp_mul(float2 a, float b) {
-  float p = __fmul_rn(a.x, b);
-  return make_float2(p, fmaf(a.y, b, fmaf(a.x, b, -p)));
-}
-__device__ __forceinline__ float2 lp_sub(float2 a, float2 b) {
-  float2 t = ef_two_sum(a.x, -b.x);
-  return make_float2(t.x, __fadd_rn(t.y, __fsub_rn(a.y, b.y)));
-}
-
-// Face quantity G = D (a_R - a_L)/h + B a_up as an unnormalised pair.  Both
-// cells that share the face evaluate it from the same operands in the same
-// order, so their contributions cancel exactly in the totals.
-__device__ __forceinline__ float2 face_G(float Doh, float B, bool upL, float2 aL, float2 aR) {
-  const float2 d = lp_mul(lp_sub(aR, aL), Doh);
-  const float2 u = lp_mul(upL ? aL : aR, B);
-  float2 t = ef_two_sum(d.x, u.x);
-  return make_float2(t.x, __fadd_rn(t.y, __fadd_rn(d.y, u.y)));
-}
-
-// Residual, diagonal and |b| of one cell from its six neighbours (nb[q]
-// valid when has[q]; order x-, x+, y-, y+, z-, z+) and face drifts B[q]:
-//   r = (a* - a)/dt + (1/V) sum +-A G + (FIELD ? -q : q)
 template <int FIELD>
 __device__ __forceinline__ float2 cell_update32(const Nl32& p, int i, float2 ac, const float2* nb,
                                                 const bool* has, const float* B, float phis,
@@ -355,65 +276,6 @@ __global__ void k_corr32(Corr32 p, const float* __restrict__ Bx, const float* __
 // is relaxed by red-black Gauss-Seidel with a 2x2 solve per cell.  The
 // alternating (Picard) linearisation converges slowly where c1 dt >> 1;
 // the coupled one does not.
-struct Nw32 {
-  Level L;
-  float invh, Dfh, DFh, inv_dt, ka, kd, ginf, inv_eps, eta;
-  int literal;
-};
-
-__device__ __forceinline__ void gather6(const Level& L, int i, int j, int k, size_t c,
-                                        bool* has, size_t* nbi) {
-  const size_t sy = (size_t)L.nx, sz = (size_t)L.nx * L.ny;
-  has[0] = i > 0; has[1] = i + 1 < L.nx; has[2] = j > 0; has[3] = j + 1 < L.ny;
-  has[4] = L.geom == SFX_CART3D && k > 0; has[5] = L.geom == SFX_CART3D && k + 1 < L.nz;
-  nbi[0] = c - 1; nbi[1] = c + 1; nbi[2] = c - sy; nbi[3] = c + sy; nbi[4] = c - sz; nbi[5] = c + sz;
-}
-
-__device__ __forceinline__ void faces6(const Level& L, const float* Bx, const float* By,
-                                       const float* Bz, int i, int j, int k, const bool* has,
-                                       float* B) {
-  B[0] = has[0] ? Bx[fidx(L, 0, i, j, k)] : 0.0f;
-  B[1] = has[1] ? Bx[fidx(L, 0, i + 1, j, k)] : 0.0f;
-  B[2] = has[2] ? By[fidx(L, 1, i, j, k)] : 0.0f;
-  B[3] = has[3] ? By[fidx(L, 1, i, j + 1, k)] : 0.0f;
-  B[4] = has[4] ? Bz[fidx(L, 2, i, j, k)] : 0.0f;
-  B[5] = has[5] ? Bz[fidx(L, 2, i, j, k + 1)] : 0.0f;
-}
-
-// (1/V) sum +-A G of one field around cell i as an unnormalised pair, and
-// the derivative of that sum in the cell value (negated: diagonal weight).
-__device__ __forceinline__ float2 flux_pair(const Level& L, float invh, float Doh, int literal,
-                                            int i, float2 ac, const float2* nb, const bool* has,
-                                            const float* B, float& dflux) {
-  Acc S{0.0f, 0.0f};
-  float dg = 0.0f;
-#pragma unroll
-  for (int q = 0; q < 6; ++q) {
-    if (!has[q]) continue;
-    const bool plus = q & 1;
-    const bool upL = literal ? (B[q] > 0.0f) : (B[q] < 0.0f);
-    float w = 1.0f;
-    if (L.geom == SFX_AXISYM) w = q < 2 ? wr_face(L.geom, i + (plus ? 1 : 0)) : (q < 4 ? wz_face(L.geom, i) : 1.0f);
-    float2 G = plus ? face_G(Doh, B[q], upL, ac, nb[q]) : face_G(Doh, B[q], upL, nb[q], ac);
-    if (L.geom == SFX_AXISYM) G = lp_mul(G, w);
-    if (plus) {
-      acc_add(S, G);
-      dg += w * (Doh - (upL ? B[q] : 0.0f));
-    } else {
-      acc_sub(S, G);
-      dg += w * (Doh + (upL ? 0.0f : B[q]));
-    }
-  }
-  const float wc = wz_face(L.geom, i);
-  float2 flux = lp_mul(acc_get(S), invh);
-  dflux = dg * invh;
-  if (L.geom == SFX_AXISYM) {
-    flux = df_div_f(ef_fast_two_sum(flux.x, flux.y), wc);
-    dflux = __fdividef(dflux, wc);
-  }
-  return flux;
-}
-
 // Evaluate both residuals (pairs), the 2x2 exchange Jacobian and the
 // norms at every cell of the current state.
 __global__ void __launch_bounds__(256, 4)
@@ -427,55 +289,12 @@ k_resid2_32(Nw32 p, const float* __restrict__ phi, const float* __restrict__ Bfx
   const Level& L = p.L;
   const size_t n = L.ncell();
   float m[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+  const float* Bf[3] = {Bfx, Bfy, Bfz};
+  const float* BF[3] = {BFx, BFy, BFz};
   for (size_t c = blockIdx.x * (size_t)blockDim.x + threadIdx.x; c < n;
        c += (size_t)gridDim.x * blockDim.x) {
     const int i = (int)(c % L.nx), j = (int)((c / L.nx) % L.ny), k = (int)(c / ((size_t)L.nx * L.ny));
-    bool has[6];
-    size_t nbi[6];
-    gather6(L, i, j, k, c, has, nbi);
-    float2 nb[6];
-    const float2 fc = fin[c], Fc = Fin[c];
-    float B[6], df_, dF_;
-#pragma unroll
-    for (int q = 0; q < 6; ++q) nb[q] = has[q] ? fin[nbi[q]] : make_float2(0.0f, 0.0f);
-    faces6(L, Bfx, Bfy, Bfz, i, j, k, has, B);
-    const float2 flf = flux_pair(L, p.invh, p.Dfh, p.literal, i, fc, nb, has, B, df_);
-#pragma unroll
-    for (int q = 0; q < 6; ++q) nb[q] = has[q] ? Fin[nbi[q]] : make_float2(0.0f, 0.0f);
-    faces6(L, BFx, BFy, BFz, i, j, k, has, B);
-    const float2 flF = flux_pair(L, p.invh, p.DFh, p.literal, i, Fc, nb, has, B, dF_);
-    // exchange q = c1 F (f_inf - f) - r_d f, one evaluation for both equations
-    const PhiPair ph = unfold(phi[c]);
-    const float c1 = __fdividef(p.ka, ph.p + p.eta);
-    const float finf = p.ginf * ph.p * ph.q * p.inv_eps;
-    float2 fd = ef_two_sum(finf, -fc.x);
-    fd.y = __fsub_rn(fd.y, fc.y);
-    const float pr = __fmul_rn(Fc.x, fd.x);
-    const float2 FF = make_float2(pr, fmaf(Fc.y, fd.x, fmaf(Fc.x, fd.y, fmaf(Fc.x, fd.x, -pr))));
-    const float2 ads = lp_mul(FF, c1), des = lp_mul(fc, p.kd);
-    Acc q{0.0f, 0.0f};
-    acc_add(q, ads);
-    acc_sub(q, des);
-    const float2 qq = acc_get(q);
-    const float2 fs = fst[c], Fs = Fst[c];
-    Acc Rf{0.0f, 0.0f}, RF{0.0f, 0.0f};
-    acc_add(Rf, lp_mul(lp_sub(fs, fc), p.inv_dt));
-    acc_add(Rf, flf);
-    acc_add(Rf, qq);
-    acc_add(RF, lp_mul(lp_sub(Fs, Fc), p.inv_dt));
-    acc_add(RF, flF);
-    acc_sub(RF, qq);
-    const float rf = __fadd_rn(Rf.hi, Rf.lo), rF = __fadd_rn(RF.hi, RF.lo);
-    const float Fv = __fadd_rn(Fc.x, Fc.y), fv = __fadd_rn(fc.x, fc.y);
-    // diagonals (kinetic part) and couplings of the linearised system
-    coef[c] = make_float4(p.inv_dt + p.kd + c1 * Fv, p.inv_dt + c1 * (finf - fv),
-                          c1 * (finf - fv), c1 * Fv + p.kd);
-    res[c] = make_float2(rf, rF);
-    m[0] = fmaxf(m[0], fabsf(rf));
-    m[1] = fmaxf(m[1], fabsf(fs.x * p.inv_dt + c1 * Fv * finf));
-    m[2] = fmaxf(m[2], fabsf(rF));
-    m[3] = fmaxf(m[3], fabsf(Fs.x * p.inv_dt + p.kd * fv));
-    if (!(fabsf(rf) <= 3.0e38f) || !(fabsf(rF) <= 3.0e38f)) m[0] = m[2] = __int_as_float(0x7f800000);
+    resid2_cell(p, i, j, k, c, phi, Bf, BF, fin, Fin, fst, Fst, coef, res, m);
   }
   if (norms) {
 #pragma unroll
@@ -484,28 +303,6 @@ k_resid2_32(Nw32 p, const float* __restrict__ phi, const float* __restrict__ Bfx
       if ((threadIdx.x & 31) == 0) atomicMax(&norms[q], fbits(v));
     }
   }
-}
-
-// linear flux of a correction field (FP32) and its diagonal weight
-__device__ __forceinline__ float flux_lin(const Level& L, float invh, float Doh, int literal,
-                                          int i, float ec, const float* en, const bool* has,
-                                          const float* B, float& dflux) {
-  float S = 0.0f, dg = 0.0f;
-#pragma unroll
-  for (int q = 0; q < 6; ++q) {
-    if (!has[q]) continue;
-    const bool plus = q & 1;
-    const bool upL = literal ? (B[q] > 0.0f) : (B[q] < 0.0f);
-    float w = 1.0f;
-    if (L.geom == SFX_AXISYM) w = q < 2 ? wr_face(L.geom, i + (plus ? 1 : 0)) : (q < 4 ? wz_face(L.geom, i) : 1.0f);
-    const float eL = plus ? ec : en[q], eR = plus ? en[q] : ec;
-    const float G = Doh * (eR - eL) + B[q] * (upL ? eL : eR);
-    if (plus) { S += w * G; dg += w * (Doh - (upL ? B[q] : 0.0f)); }
-    else { S -= w * G; dg += w * (Doh + (upL ? 0.0f : B[q])); }
-  }
-  const float s = invh / wz_face(L.geom, i);
-  dflux = dg * s;
-  return S * s;
 }
 
 // One colour of the coupled red-black Gauss-Seidel on the correction.
@@ -518,6 +315,8 @@ __global__ void k_corr2_32(Nw32 p, const float* __restrict__ Bfx, const float* _
   const Level& L = p.L;
   const int j = blockIdx.y, k = blockIdx.z;
   const int i = 2 * (blockIdx.x * blockDim.x + threadIdx.x) + ((j + k + color) & 1);
+  const float* Bf[3] = {Bfx, Bfy, Bfz};
+  const float* BF[3] = {BFx, BFy, BFz};
   if (i >= L.nx) {
     // a row of odd length: the last red cell has no black partner
     const int ir = i ^ 1;
@@ -528,49 +327,7 @@ __global__ void k_corr2_32(Nw32 p, const float* __restrict__ Bfx, const float* _
     }
     return;
   }
-  const size_t c = cidx(L, i, j, k);
-  bool has[6];
-  size_t nbi[6];
-  gather6(L, i, j, k, c, has, nbi);
-  // every cell starts at zero in the first sweep
-  const bool zero_nb = first && color == 0;
-  float enf[6], enF[6];
-#pragma unroll
-  for (int q = 0; q < 6; ++q) {
-    enf[q] = (has[q] && !zero_nb) ? ef[nbi[q]] : 0.0f;
-    enF[q] = (has[q] && !zero_nb) ? eF[nbi[q]] : 0.0f;
-  }
-  const float efc = first ? 0.0f : ef[c], eFc = first ? 0.0f : eF[c];
-  float B[6], dgf, dgF;
-  faces6(L, Bfx, Bfy, Bfz, i, j, k, has, B);
-  const float flf = flux_lin(L, p.invh, p.Dfh, p.literal, i, efc, enf, has, B, dgf);
-  faces6(L, BFx, BFy, BFz, i, j, k, has, B);
-  const float flF = flux_lin(L, p.invh, p.DFh, p.literal, i, eFc, enF, has, B, dgF);
-  const float4 cf = coef[c];
-  const float2 r = res[c];
-  // residuals of the correction equation at this cell
-  const float rhof = r.x + flf - cf.x * efc + cf.z * eFc;
-  const float rhoF = r.y + flF - cf.y * eFc + cf.w * efc;
-  // 2x2 block solve: [a  -b; -d  e] [x; y] = [rhof; rhoF]
-  const float a = cf.x + dgf, bb = cf.z, d = cf.w, e = cf.y + dgF;
-  const float det = a * e - bb * d;
-  const float inv = __fdividef(1.0f, det);
-  const float nf = efc + (e * rhof + bb * rhoF) * inv;
-  const float nF = eFc + (d * rhof + a * rhoF) * inv;
-  ef[c] = nf;
-  eF[c] = nF;
-  if (fst) {
-    // last black colour of the iteration: add the corrections to the state,
-    // for this cell and for the red cell that shares its pair (2t, 2t+1)
-    fst[c] = df_add(fst[c], nf);
-    Fst[c] = df_add(Fst[c], nF);
-    const int ir = i ^ 1;
-    if (ir < L.nx) {
-      const size_t cr = c - i + ir;
-      fst[cr] = df_add(fst[cr], ef[cr]);
-      Fst[cr] = df_add(Fst[cr], eF[cr]);
-    }
-  }
+  corr2_cell(p, i, j, k, Bf, BF, coef, res, ef, eF, color, first, fst, Fst);
 }
 
 // ------------------------------------------------------------ fused sweep
@@ -860,86 +617,12 @@ __global__ void __launch_bounds__(256) k_nlrb32_z(Nl32 p, const float* __restric
 }
 
 // ------------------------------------------------------------ advection
-__device__ __forceinline__ float mc32(float xm, float x0, float xp) {
-  float dl = x0 - xm, dr = xp - x0;
-  if (dl * dr <= 0.0f) return 0.0f;
-  float dc = 0.5f * (xp - xm);
-  float m = fminf(fabsf(dc), 2.0f * fminf(fabsf(dl), fabsf(dr)));
-  return dc > 0.0f ? m : -m;
-}
-
-struct Adv32 {
-  Level L;
-  float dt, invh;
-  const float* u[3];
-};
-
-__device__ __forceinline__ float vnb(const Level& L, const float2* __restrict__ x, const int* uc,
-                                     size_t U, int d, int s) {
-  int p = uc[d] + s;
-  if (p < 0 || p >= L.extent(d)) return df_val(x[U]);
-  size_t stride = d == 0 ? 1 : (d == 1 ? (size_t)L.nx : (size_t)L.nx * L.ny);
-  return df_val(s > 0 ? x[U + stride] : x[U - stride]);
-}
-
-// BCG face value (see sfx_advect.cu) in FP32 on the pair values.
-__device__ float face32v(const Adv32& A, const float2* __restrict__ x, float bc_in, int d,
-                         const int* f, float u) {
-  const Level& L = A.L;
-  int uc[3] = {f[0], f[1], f[2]};
-  if (u > 0.0f) {
-    if (f[d] == 0) return bc_in;
-    uc[d] -= 1;
-  } else if (f[d] == L.extent(d)) {
-    return bc_in;
-  }
-  size_t U = cidx(L, uc[0], uc[1], uc[2]);
-  float x0 = df_val(x[U]);
-  float slope = mc32(vnb(L, x, uc, U, d, -1), x0, vnb(L, x, uc, U, d, +1));
-  float val = x0 + 0.5f * ((u > 0.0f ? 1.0f : -1.0f) - u * A.dt * A.invh) * slope;
-  for (int t = 0; t < L.ndim(); ++t) {
-    if (t == d) continue;
-    int ap[3] = {uc[0], uc[1], uc[2]};
-    ap[t] += 1;
-    float vbar = 0.5f * (A.u[t][fidx(L, t, uc[0], uc[1], uc[2])] + A.u[t][fidx(L, t, ap[0], ap[1], ap[2])]);
-    float dif = vbar > 0.0f ? x0 - vnb(L, x, uc, U, t, -1) : vnb(L, x, uc, U, t, +1) - x0;
-    val -= 0.5f * A.dt * vbar * dif * A.invh;
-  }
-  return val;
-}
-
 __global__ void k_advect32(Adv32 A, const float2* __restrict__ x, float bc_in,
                            float2* __restrict__ out) {
-  const Level& L = A.L;
-  const size_t n = L.ncell();
+  const size_t n = A.L.ncell();
   for (size_t c = blockIdx.x * (size_t)blockDim.x + threadIdx.x; c < n;
-       c += (size_t)gridDim.x * blockDim.x) {
-    int idx[3] = {(int)(c % L.nx), (int)((c / L.nx) % L.ny), (int)(c / ((size_t)L.nx * L.ny))};
-    // net outflow in area units; each face term is computed bitwise alike
-    // by the two cells that share the face
-    float2 S = make_float2(0.0f, 0.0f);
-    for (int d = 0; d < L.ndim(); ++d) {
-      int pp[3] = {idx[0], idx[1], idx[2]};
-      pp[d] += 1;
-      float um = A.u[d][fidx(L, d, idx[0], idx[1], idx[2])];
-      float up = A.u[d][fidx(L, d, pp[0], pp[1], pp[2])];
-      float wm = d == 0 ? wr_face(L.geom, idx[0]) : (d == 1 ? wz_face(L.geom, idx[0]) : 1.0f);
-      float wp = d == 0 ? wr_face(L.geom, idx[0] + 1) : wm;
-      if (um != 0.0f) {
-        float fv = face32v(A, x, bc_in, d, idx, um);
-        float pr = __fmul_rn(um, fv);
-        S = df_sub2(S, df_mul_f(make_float2(pr, fmaf(um, fv, -pr)), wm));
-      }
-      if (up != 0.0f) {
-        float fv = face32v(A, x, bc_in, d, pp, up);
-        float pr = __fmul_rn(up, fv);
-        S = df_add2(S, df_mul_f(make_float2(pr, fmaf(up, fv, -pr)), wp));
-      }
-    }
-    float2 inc = df_mul_f(df_mul_f(S, -A.dt), A.invh);
-    if (L.geom == SFX_AXISYM) inc = df_div_f(inc, wz_face(L.geom, idx[0]));
-    out[c] = df_add2(x[c], inc);
-  }
+       c += (size_t)gridDim.x * blockDim.x)
+    out[c] = advect_cell(A, x, bc_in, c);
 }
 
 // ------------------------------------------------------------ totals
@@ -1017,11 +700,11 @@ struct Eos32 {
 // precision) and sigma itself.  The Langmuir logarithm is taken in FP64
 // once Gamma/Gamma_inf exceeds 1/2 (near saturation), in FP32 below.
 __global__ void k_eos32(size_t n, Eos32 q, const float2* __restrict__ f,
-                        const float* __restrict__ phi, float* __restrict__ dsig,
+                        const double* __restrict__ phi, float* __restrict__ dsig,
                         float* __restrict__ sigma) {
   for (size_t c = blockIdx.x * (size_t)blockDim.x + threadIdx.x; c < n;
        c += (size_t)gridDim.x * blockDim.x) {
-    PhiPair ph = unfold(phi[c]);
+    PhiPair ph = unfold(fold_phi(phi[c]));
     float del = ph.p * ph.q * q.inv_eps;
     float G = del >= 1e-3f * q.inv_eps ? df_val(f[c]) / del : 0.0f;
     float x = G / q.ginf;
@@ -1098,32 +781,29 @@ __device__ float plic32_area(int nd, const float* m, float C) {
   return sqrtf(q2) / s * plic32_half(q, three_d, 0.5f * (lo + hi)).dv;
 }
 
-__global__ void k_force32(Level L, const float* __restrict__ phi, const float* __restrict__ C,
-                          const float* __restrict__ dsig, int dm_mode, float* __restrict__ force) {
+__global__ void k_force32(Level L, const double* __restrict__ phi, const float* __restrict__ C,
+                          const float* __restrict__ dsig, int dm_mode, float inv_eps,
+                          float* __restrict__ force) {
   const size_t n = L.ncell();
   const int nd = L.ndim();
   const float inv2h = 0.5f / (float)L.h;
   for (size_t c = blockIdx.x * (size_t)blockDim.x + threadIdx.x; c < n;
        c += (size_t)gridDim.x * blockDim.x) {
     int idx[3] = {(int)(c % L.nx), (int)((c / L.nx) % L.ny), (int)(c / ((size_t)L.nx * L.ny))};
-    float gs[3] = {0, 0, 0}, nn[3] = {0, 0, 0}, ndg = 0.0f;
-    float g0 = 0, g1 = 0, g2 = 0, gc2 = 0;
+    float gs[3] = {0, 0, 0}, nn[3], ndg = 0.0f;
+    float gc2 = 0;
     for (int d = 0; d < nd; ++d) {
       int pp[3] = {idx[0], idx[1], idx[2]}, pm[3] = {idx[0], idx[1], idx[2]};
       pp[d] = min(pp[d] + 1, L.extent(d) - 1);
       pm[d] = max(pm[d] - 1, 0);
       size_t cp = cidx(L, pp[0], pp[1], pp[2]), cm = cidx(L, pm[0], pm[1], pm[2]);
       gs[d] = (dsig[cp] - dsig[cm]) * inv2h;
-      float gp = dphi(phi[cp], phi[cm]);
-      if (d == 0) g0 = gp; else if (d == 1) g1 = gp; else g2 = gp;
       if (dm_mode == 0) {
         float gc = (C[cp] - C[cm]) * inv2h;
         gc2 += gc * gc;
       }
     }
-    float m2 = g0 * g0 + g1 * g1 + g2 * g2;
-    float inv = (m2 * inv2h * inv2h < 1e-30f) ? 0.0f : rsqrtf(m2);
-    nn[0] = g0 * inv; nn[1] = g1 * inv; nn[2] = g2 * inv;
+    normal3_f32(L, phi, idx[0], idx[1], idx[2], inv_eps, nn);
     for (int d = 0; d < nd; ++d) ndg += nn[d] * gs[d];
     float dm = 0.0f;
     if (dm_mode == 0) {
@@ -1357,7 +1037,7 @@ sfx_status solve_newton32(sfx_ctx* c, const Nw32& p, const float* phi, float* co
 
 }  // namespace
 
-sfx_status step_f32(sfx_ctx* c, const sfx_params* pr, const float* phi, const float* ux,
+sfx_status step_f32(sfx_ctx* c, const sfx_params* pr, const double* phi_in, const float* ux,
                     const float* uy, const float* uz, float2* f, float2* F, double dt,
                     const sfx_solve_opts* o, sfx_step_stats* stats, cudaStream_t s) {
   sfx_status st = f32_ensure_scratch(c);
@@ -1367,16 +1047,18 @@ sfx_status step_f32(sfx_ctx* c, const sfx_params* pr, const float* phi, const fl
   const int nd = L.ndim();
   float* Bf[3] = {c->f32.Bf[0], c->f32.Bf[1], nd == 3 ? c->f32.Bf[2] : nullptr};
   float* BF[3] = {c->f32.BF[0], c->f32.BF[1], nd == 3 ? c->f32.BF[2] : nullptr};
-  // drift faces depend on phi and (Df, DF, eps) only
-  const bool reuse = c->f32.reuse_drift && c->f32.drift_phi == phi &&
+  // drift faces and the folded float phi depend on phi and (Df, DF, eps)
+  const bool reuse = c->f32.reuse_drift && c->f32.drift_phi == phi_in &&
                      c->f32.drift_key[0] == pr->Df && c->f32.drift_key[1] == pr->DF &&
                      c->f32.drift_key[2] == pr->eps;
+  const float* phi = c->f32.phi32;
   if (!reuse) {
+    SFX_KERNEL(c, K_SETUP, k_fold_phi, blocks_for(n, 256), 256, s, n, phi_in, c->f32.phi32);
     for (int d = 0; d < nd; ++d)
-      SFX_KERNEL(c, K_SETUP, k_drift32, blocks_for(L.nface(d), 256), 256, s, L, d, phi,
+      SFX_KERNEL(c, K_SETUP, k_drift32, blocks_for(L.nface(d), 256), 256, s, L, d, phi_in,
                  (float)pr->Df, (float)pr->DF, (float)(1.0 / pr->eps), Bf[d], BF[d]);
     SFX_LAUNCH_CHECK();
-    c->f32.drift_phi = phi;
+    c->f32.drift_phi = phi_in;
     c->f32.drift_key[0] = pr->Df;
     c->f32.drift_key[1] = pr->DF;
     c->f32.drift_key[2] = pr->eps;
@@ -1520,7 +1202,7 @@ sfx_status totals32(sfx_ctx* c, const void* const* fields, int nf, double* out, 
   return SFX_OK;
 }
 
-sfx_status marangoni32(sfx_ctx* c, const sfx_params* p, const float2* f, const float* phi,
+sfx_status marangoni32(sfx_ctx* c, const sfx_params* p, const float2* f, const double* phi,
                        const float* C, int dm_mode, float* sigma, float* force, cudaStream_t s) {
   sfx_status st = f32_ensure_scratch(c);
   if (st != SFX_OK) return st;
@@ -1530,7 +1212,7 @@ sfx_status marangoni32(sfx_ctx* c, const sfx_params* p, const float2* f, const f
           (float)p->E, p->eos};
   SFX_KERNEL(c, K_FORCES, k_eos32, blocks_for(n, 256), 256, s, n, q, f, phi, c->f32.dsig, sigma);
   SFX_KERNEL(c, K_FORCES, k_force32, blocks_for(n, 256), 256, s, L, phi, C, c->f32.dsig, dm_mode,
-             force);
+             q.inv_eps, force);
   SFX_LAUNCH_CHECK();
   return SFX_OK;
 }
@@ -1538,13 +1220,6 @@ sfx_status marangoni32(sfx_ctx* c, const sfx_params* p, const float2* f, const f
 sfx_status df_pack(const double* in, void* out, size_t n, cudaStream_t s) {
   if (n == 0) return SFX_OK;
   k_pack_df<<<blocks_for(n, 256), 256, 0, s>>>(n, in, (float2*)out);
-  SFX_LAUNCH_CHECK();
-  return SFX_OK;
-}
-
-sfx_status phi_fold(const double* phi, float* out, size_t n, cudaStream_t s) {
-  if (n == 0) return SFX_OK;
-  k_fold_phi<<<blocks_for(n, 256), 256, 0, s>>>(n, phi, out);
   SFX_LAUNCH_CHECK();
   return SFX_OK;
 }
@@ -1573,6 +1248,7 @@ sfx_status f32_ensure_scratch(sfx_ctx* c) {
   if ((st = get(n * sizeof(float2), (void**)&c->f32.fstar)) != SFX_OK) return st;
   if ((st = get(n * sizeof(float2), (void**)&c->f32.Fstar)) != SFX_OK) return st;
   if ((st = get(n * sizeof(float), (void**)&c->f32.dsig)) != SFX_OK) return st;
+  if ((st = get(n * sizeof(float), (void**)&c->f32.phi32)) != SFX_OK) return st;
   if ((st = get(n * sizeof(float2), (void**)&c->f32.falt)) != SFX_OK) return st;
   if ((st = get(n * sizeof(float2), (void**)&c->f32.Falt)) != SFX_OK) return st;
   float** arrs[6] = {&c->f32.ef, &c->f32.eF, &c->f32.rf, &c->f32.rF, &c->f32.lf, &c->f32.lF};

@@ -181,7 +181,7 @@ __device__ double plic_unit_area(int nd, const double* mraw, double C) {
 
 template <typename P>
 __global__ void k_force(Level L, const P* __restrict__ phi, const double* __restrict__ C,
-                        const double* __restrict__ sigma, int dm_mode,
+                        const double* __restrict__ sigma, int dm_mode, double eps,
                         double* __restrict__ force) {
   const size_t n = L.ncell();
   const int nd = L.ndim();
@@ -195,7 +195,7 @@ __global__ void k_force(Level L, const P* __restrict__ phi, const double* __rest
       pp[d] = min(pp[d] + 1, L.extent(d) - 1);
       pm[d] = max(pm[d] - 1, 0);
       gs[d] = (sigma[cidx(L, pp[0], pp[1], pp[2])] - sigma[cidx(L, pm[0], pm[1], pm[2])]) * inv2h;
-      nn[d] = normal_comp(L, phi, idx[0], idx[1], idx[2], d);
+      nn[d] = normal_comp(L, phi, idx[0], idx[1], idx[2], d, eps);
       ndg += nn[d] * gs[d];
     }
     double dm;
@@ -261,13 +261,9 @@ sfx_status marangoni(sfx_ctx* c, const sfx_params* p, const double* f, const voi
   const size_t n = L.ncell();
   EosArgs q{p->gamma_inf, p->eps, p->sigma0, p->E, p->eos};
   const int nb = blocks_for(n, 256);
-  if (c->prec == SFX_F64) {
-    SFX_KERNEL(c, K_FORCES, k_eos<double>, nb, 256, s, n, q, f, (const double*)phi, sigma);
-    SFX_KERNEL(c, K_FORCES, k_force<double>, nb, 256, s, L, (const double*)phi, C, sigma, dm_mode, force);
-  } else {
-    SFX_KERNEL(c, K_FORCES, k_eos<float>, nb, 256, s, n, q, f, (const float*)phi, sigma);
-    SFX_KERNEL(c, K_FORCES, k_force<float>, nb, 256, s, L, (const float*)phi, C, sigma, dm_mode, force);
-  }
+  SFX_KERNEL(c, K_FORCES, k_eos<double>, nb, 256, s, n, q, f, (const double*)phi, sigma);
+  SFX_KERNEL(c, K_FORCES, k_force<double>, nb, 256, s, L, (const double*)phi, C, sigma, dm_mode,
+             p->eps, force);
   SFX_LAUNCH_CHECK();
   return SFX_OK;
 }

@@ -49,7 +49,8 @@ struct F32Scratch {
   float2* res = nullptr;   // r_f, r_F
   cudaEvent_t ev[2] = {nullptr, nullptr};
   bool reuse_drift = false;         // keep drift faces while phi and D's are unchanged
-  const float* drift_phi = nullptr;
+  const double* drift_phi = nullptr;
+  float* phi32 = nullptr;           // folded float copy of phi
   double drift_key[3] = {0, 0, 0};
   float *ef = nullptr, *eF = nullptr;   // corrections
   float *rf = nullptr, *rF = nullptr;   // residuals
@@ -133,17 +134,16 @@ sfx_status marangoni(sfx_ctx* c, const sfx_params* p, const double* f, const voi
 
 // sfx_f32.cu (SFX_F32 contexts: double-float state, FP32 arithmetic)
 sfx_status f32_ensure_scratch(sfx_ctx* c);
-sfx_status step_f32(sfx_ctx* c, const sfx_params* p, const float* phi, const float* ux,
+sfx_status step_f32(sfx_ctx* c, const sfx_params* p, const double* phi, const float* ux,
                     const float* uy, const float* uz, float2* f, float2* F, double dt,
                     const sfx_solve_opts* o, sfx_step_stats* st, cudaStream_t s);
 sfx_status advect32(sfx_ctx* c, const float* ux, const float* uy, const float* uz, double dt,
                     const float2* xi, double bc_in, float2* out, cudaStream_t s);
 sfx_status totals32(sfx_ctx* c, const void* const* fields, int n, double* out, cudaStream_t s);
-sfx_status marangoni32(sfx_ctx* c, const sfx_params* p, const float2* f, const float* phi,
+sfx_status marangoni32(sfx_ctx* c, const sfx_params* p, const float2* f, const double* phi,
                        const float* C, int dm_mode, float* sigma, float* force, cudaStream_t s);
 sfx_status df_pack(const double* in, void* out, size_t n, cudaStream_t s);
 sfx_status df_unpack(const void* in, double* out, size_t n, cudaStream_t s);
-sfx_status phi_fold(const double* phi, float* out, size_t n, cudaStream_t s);
 
 inline int blocks_for(size_t n, int threads) {
   size_t b = (n + threads - 1) / threads;

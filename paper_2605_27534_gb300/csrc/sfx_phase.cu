@@ -84,21 +84,6 @@ __global__ void k_phi_delta64(size_t n, double eps, const double* __restrict__ c
   }
 }
 
-// SFX_F32 carrier: folded phi (phi if phi <= 1/2, phi - 1 otherwise), from
-// the logistic form phi = 1/(1 + exp(chi/eps)) = (1 - tanh(chi/2eps))/2 and
-// 1 - phi = 1/(1 + exp(-chi/eps)), each accurate on its own side.
-__global__ void k_phi_delta32(size_t n, double eps, const double* __restrict__ chi,
-                              float* __restrict__ phi, float* __restrict__ delta) {
-  for (size_t c = blockIdx.x * (size_t)blockDim.x + threadIdx.x; c < n;
-       c += (size_t)gridDim.x * blockDim.x) {
-    double x = chi[c] / eps;
-    double p = 1.0 / (1.0 + exp(x));      // phi
-    double q = 1.0 / (1.0 + exp(-x));     // 1 - phi
-    phi[c] = x >= 0.0 ? (float)p : -(float)q;
-    if (delta) delta[c] = (float)(p * q / eps);
-  }
-}
-
 }  // namespace
 
 sfx_status phase_field_build(sfx_ctx* c, const double* C, double* chi, void* phi, void* delta,
@@ -119,10 +104,7 @@ sfx_status phase_field_build(sfx_ctx* c, const double* C, double* chi, void* phi
   SFX_LAUNCH_CHECK();
   if (a != chi)
     SFX_CUDA(cudaMemcpyAsync(chi, a, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
-  if (c->prec == SFX_F64)
-    SFX_KERNEL(c, K_PHASE, k_phi_delta64, nb, 256, s, n, eps, chi, (double*)phi, (double*)delta);
-  else
-    SFX_KERNEL(c, K_PHASE, k_phi_delta32, nb, 256, s, n, eps, chi, (float*)phi, (float*)delta);
+  SFX_KERNEL(c, K_PHASE, k_phi_delta64, nb, 256, s, n, eps, chi, (double*)phi, (double*)delta);
   SFX_LAUNCH_CHECK();
   return SFX_OK;
 }

@@ -329,7 +329,7 @@ __global__ void k_drift_faces(Level L, int d, const P* __restrict__ phi, double 
     if (pos == 0 || pos == L.extent(d)) { Bf[q] = 0.0; BF[q] = 0.0; continue; }
     int li = i - (d == 0), lj = j - (d == 1), lk = k - (d == 2);
     double pL = (double)phi[cidx(L, li, lj, lk)], pR = (double)phi[cidx(L, i, j, k)];
-    double nL = normal_comp(L, phi, li, lj, lk, d), nR = normal_comp(L, phi, i, j, k, d);
+    double nL = normal_comp(L, phi, li, lj, lk, d, eps), nR = normal_comp(L, phi, i, j, k, d, eps);
     Bf[q] = 0.5 * ((-Df * 2.0 * (0.5 - pL) / eps) * nL + (-Df * 2.0 * (0.5 - pR) / eps) * nR);
     BF[q] = 0.5 * ((-DF * (1.0 - pL) / eps) * nL + (-DF * (1.0 - pR) / eps) * nR);
   }

@@ -75,16 +75,11 @@ def test_phase_field_build_parity(sfx, geom):
     assert rel_err(host(chi), chi_o) < PARITY
     assert rel_err(host(phi), phi_o) < PARITY
     assert rel_err(host(dl), del_o) < PARITY
-    # FP32 carrier: phi stored in float
+    # SFX_F32 contexts build the same double phase field
     ctx32 = _ctx(sfx, g, 1)
-    phi32 = torch.empty(Cd.shape, dtype=torch.float32, device="cuda")
+    phi32 = torch.empty_like(Cd)
     ctx32.sfx_phase_field_build(Cd, chi, phi32, None, iters=24, dtau=dtau, eps=eps)
-    s32 = host(phi32)
-    unfolded = np.where(np.signbit(s32), 1.0 + s32, s32)
-    assert rel_err(unfolded, phi_o) < 1e-6
-    # 1 - phi keeps full relative precision on the bulk side
-    bulk = phi_o > 0.5
-    assert np.abs(-s32[bulk] - (1.0 - phi_o[bulk])).max() <= 2e-7 * 0.5
+    assert torch.equal(phi32, phi)
 
 
 def _random_problem(g, seed, scale=2.0):
@@ -222,7 +217,7 @@ def test_surfactant_step_parity_fp32(sfx, name):
         f_o, F_o, st = oracle.surfactant_step(g, p, phi, f_o, F_o, c.dt, 1e-13, ux, uy, uz)
     ctx = _ctx(sfx, g, 1)
     f, F = _pairs(ctx, f0), _pairs(ctx, c.F0)
-    phid = ctx.sfx_phi_fold(dev(phi))
+    phid = dev(phi)
     u = [None if v is None else dev(v, torch.float32) for v in (ux, uy, uz)]
     opts = sfx.default_opts(tol=1e-10, max_cycles=400)
     M0 = sum(ctx.sfx_totals([f, F]))
@@ -252,7 +247,7 @@ def test_fused_sweep_equals_colour_launches_bitwise(sfx, name):
         u = [None if v is None else dev(v, torch.float32) for v in (ux, uy, uz)]
         o = sfx.default_opts(tol=1e-10, nu1=1, nu2=0)
         for _ in range(2):
-            ctx.sfx_surfactant_step(p, ctx.sfx_phi_fold(dev(phi)), f, F, c.dt, *u, opts=o)
+            ctx.sfx_surfactant_step(p, dev(phi), f, F, c.dt, *u, opts=o)
         torch.cuda.synchronize()
         outs.append((f.cpu().numpy().copy(), F.cpu().numpy().copy()))
     assert np.array_equal(outs[0][0], outs[1][0]) and np.array_equal(outs[0][1], outs[1][1])
@@ -273,7 +268,7 @@ def test_fp32_solvers_agree(sfx, name):
         u = [None if v is None else dev(v, torch.float32) for v in (ux, uy, uz)]
         o = sfx.default_opts(tol=1e-12, nu1=1, nu2=0, max_cycles=400)
         for _ in range(2):
-            st = ctx.sfx_surfactant_step(p, ctx.sfx_phi_fold(dev(phi)), f, F, c.dt, *u, opts=o)
+            st = ctx.sfx_surfactant_step(p, dev(phi), f, F, c.dt, *u, opts=o)
             assert st.converged
         outs.append((host(ctx.sfx_df_unpack(f)), host(ctx.sfx_df_unpack(F))))
     scale = max(np.abs(outs[0][0]).max(), np.abs(outs[0][1]).max())
@@ -290,7 +285,7 @@ def test_fp32_mass_drift_over_many_steps(sfx):
     ctx = _ctx(sfx, g, 1)
     Cd = dev(c.C)
     chi = torch.empty_like(Cd)
-    phi = torch.empty(g.shape, dtype=torch.float32, device="cuda")
+    phi = torch.empty_like(Cd)
     ctx.sfx_phase_field_build(Cd, chi, phi, None, iters=c.redist_iters, dtau=c.dtau, eps=p.eps)
     f, F = _pairs(ctx, np.zeros(g.shape)), _pairs(ctx, c.F0)
     M0 = sum(ctx.sfx_totals([f, F]))
@@ -348,7 +343,7 @@ def test_marangoni_fp32(sfx, geom):
         sig_o, force_o = oracle.marangoni(g, p, f, phi, Cf, 1)
         sig = torch.empty(g.shape, dtype=torch.float32, device="cuda")
         force = torch.empty((g.ndim,) + g.shape, dtype=torch.float32, device="cuda")
-        ctx.sfx_marangoni_force(p, _pairs(ctx, f), ctx.sfx_phi_fold(dev(phi)),
+        ctx.sfx_marangoni_force(p, _pairs(ctx, f), dev(phi),
                                 dev(Cf, torch.float32), sig, force, 1)
         assert rel_err(host(sig), sig_o) < 1e-6
         assert rel_err(host(force), force_o) < 1e-4

@@ -167,33 +167,31 @@ def ring_vof(nr, nz, h, zc, R):
     """Volume fraction of a sphere of radius R centred on the axis at z = zc,
     in the ring cells [ih,(i+1)h] x [jh,(j+1)h] of an axisymmetric grid.
 
-    The ring volume inside the sphere is pi * int (clip(R^2 - (z-zc)^2,
-    r0^2, r1^2) - r0^2) dz, a piecewise quadratic in z integrated exactly."""
-    C = np.zeros((1, nz, nr))
-    for j in range(nz):
-        za, zb = j * h - zc, (j + 1) * h - zc
-        for i in range(nr):
-            r0, r1 = i * h, (i + 1) * h
-            bps = {za, zb}
-            for rr in (r0, r1):
-                if rr < R:
-                    zz = math.sqrt(R * R - rr * rr)
-                    for v in (-zz, zz):
-                        if za < v < zb:
-                            bps.add(v)
-            bps = sorted(bps)
-            tot = 0.0
-            for p, q in zip(bps[:-1], bps[1:]):
-                m = 0.5 * (p + q)
-                rho2 = R * R - m * m
-                if rho2 <= r0 * r0:
-                    continue
-                if rho2 >= r1 * r1:
-                    tot += (r1 * r1 - r0 * r0) * (q - p)
-                else:  # integrate R^2 - z^2 - r0^2
-                    tot += (R * R - r0 * r0) * (q - p) - (q ** 3 - p ** 3) / 3.0
-            C[0, j, i] = tot / ((r1 * r1 - r0 * r0) * h)
-    return np.clip(C, 0.0, 1.0)
+    The ring volume inside the sphere is pi * int (clip(R^2 - z^2, r0^2,
+    r1^2) - r0^2) dz over the cell's z-range (z measured from zc); the
+    integrand is piecewise constant or quadratic, so its antiderivative G is
+    exact: with z1 = sqrt(R^2 - r1^2) and z0 = sqrt(R^2 - r0^2) (0 when
+    negative), G(z) = r1^2 z for z <= z1, + R^2 (z - z1) - (z^3 - z1^3)/3 up to
+    z0, + r0^2 (z - z0) beyond, odd in z."""
+    r0 = (np.arange(nr) * h)[None, :]
+    r1 = ((np.arange(nr) + 1) * h)[None, :]
+    za = (np.arange(nz) * h - zc)[:, None]
+    zb = ((np.arange(nz) + 1) * h - zc)[:, None]
+    z1 = np.sqrt(np.maximum(R * R - r1 * r1, 0.0))
+    z0 = np.sqrt(np.maximum(R * R - r0 * r0, 0.0))
+
+    def G(z):
+        a = np.abs(z)
+        g = np.where(a <= z1, r1 * r1 * a,
+                     np.where(a <= z0,
+                              r1 * r1 * z1 + R * R * (a - z1) - (a ** 3 - z1 ** 3) / 3.0,
+                              r1 * r1 * z1 + R * R * (z0 - z1) - (z0 ** 3 - z1 ** 3) / 3.0
+                              + r0 * r0 * (a - z0)))
+        return np.sign(z) * g
+
+    vol = G(zb) - G(za) - r0 * r0 * (zb - za)
+    C = vol / ((r1 * r1 - r0 * r0) * h)
+    return np.clip(C, 0.0, 1.0)[None]
 
 
 _GL_X, _GL_W = np.polynomial.legendre.leggauss(16)
