@@ -49,6 +49,8 @@ def parse():
                     help="steps of the FP64 path timed beside the FP32 line (0: skip)")
     ap.add_argument("--batch-steps", type=int, default=0,
                     help="also time the batched workload for this many steps (0: skip)")
+    ap.add_argument("--adjoint-steps", type=int, default=200,
+                    help="steps of the 256^2 adjoint workload timed beside the line (0: skip)")
     ap.add_argument("--n", type=int, default=256)
     ap.add_argument("--tol", type=float, default=1e-10)
     ap.add_argument("--no-e2e", action="store_true")
@@ -360,6 +362,9 @@ def run_gpu(a, case, rank, world, local_rank):
     f64 = None
     if prec == sfx.SFX_F32 and a.f64_steps > 0:
         f64 = f64_path(a, case, dev, f, F, phi, ux, uy, uz)
+    adj = None
+    if a.adjoint_steps > 0:
+        adj = adjoint_summary(a, dev)
     batch = None
     if a.batch_steps > 0:
         batch = run_gpu_batch(a, rank, 1, local_rank, steps=a.batch_steps, summary=True)
@@ -382,7 +387,45 @@ def run_gpu(a, case, rank, world, local_rank):
         line["speedup_vs_f64"] = f64["ms_per_step"] / (ms_max / a.steps)
     if batch is not None:
         line["batch64"] = batch
+    if adj is not None:
+        line["adjoint2d_256"] = adj
     print(json.dumps(line))
+
+
+def adjoint_summary(a, dev):
+    """Forward and backward of the differentiable rollout on the 2D adjoint
+    workload (256^2 no-flow adsorption, seeded Gamma0 perturbation, loss
+    sum V |F_Ma|^2, checkpoints every 20 steps), FP32 forward."""
+    import torch
+    import paper_2605_27534_gb300 as sfx
+    c = W.case_adjoint_2d(n=256)
+    g, p = c.grid, c.params
+    out = {}
+    for name, prec, tol in (("f32_forward", sfx.SFX_F32, 1e-12), ("f64_forward", sfx.SFX_F64, 1e-12)):
+        ctx = sfx.Context.for_grid(g, prec)
+        Cd = torch.from_numpy(c.C).to(dev)
+        chi, phi = torch.empty_like(Cd), torch.empty_like(Cd)
+        ctx.sfx_phase_field_build(Cd, chi, phi, None, iters=c.redist_iters, dtau=c.dtau, eps=p.eps)
+        setup = sfx.RolloutSetup(context=ctx, params=p, phi=phi, C=Cd,
+                                 F0=torch.from_numpy(c.F0).to(dev), dt=c.dt,
+                                 nsteps=a.adjoint_steps, K=20, tol=tol)
+        theta = torch.tensor([p.ka, p.kd, p.Df, p.DF], dtype=torch.float64, requires_grad=True)
+        g0 = torch.from_numpy(c.gamma0).to(dev).requires_grad_(True)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        L = sfx.SurfactantRollout.apply(g0, theta, setup)
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        L.backward()
+        torch.cuda.synchronize()
+        t2 = time.perf_counter()
+        out[name] = {"loss": L.item(), "forward_ms": 1e3 * (t1 - t0),
+                     "backward_ms": 1e3 * (t2 - t1),
+                     "forward_cell_updates_per_s": g.ncell * a.adjoint_steps / (t1 - t0),
+                     "dL_dtheta": [float(x) for x in theta.grad]}
+    out["steps"] = a.adjoint_steps
+    out["cells"] = g.ncell
+    return out
 
 
 def f64_path(a, case, dev, f32_f, f32_F, f32_phi, ux, uy, uz):

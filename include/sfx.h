@@ -258,6 +258,47 @@ sfx_status sfx_set_tuning(sfx_ctx* ctx, int key, int value);
 sfx_status sfx_df_pack(const double* in, void* out, size_t n, void* stream);
 sfx_status sfx_df_unpack(const void* in, double* out, size_t n, void* stream);
 
+/* a10.  Discrete adjoint of the no-flow coupled step (App. C), FP64 in
+   either context precision; every array below is double.  A step solves
+   R(x1; x0, theta) = 0 for x1 = (f, F) with the App. C residuals
+     R_f = (f^n - f)/dt + N_f f + q,  R_F = (F^n - F)/dt + N_F F - q,
+     q = k_a F (f_inf - f)/(phi + eta) - k_d f,
+   N the Sec. 3.1-3.2 flux divergence of each field.  With J = dR/dx1 at the
+   state after the step, a loss gradient lam1 = dL/dx1 pulls back as
+     (-J)^T nu = lam1,  dL/dx0 = nu/dt,  dL/dtheta += (dR/dtheta)^T nu,
+   theta = (k_a, k_d, D_f, D_F) (Sec. 2.3 / App. C parameters).  The paper
+   has no adjoint: this is the exact derivative of its discrete step. */
+
+/* f = Gamma delta_phi, delta_phi = phi (1 - phi)/eps (Sec. 2.3).  The map
+   is diagonal, so the same call takes dL/df to dL/dGamma. */
+sfx_status sfx_f_from_gamma(sfx_ctx* ctx, const double* gamma, const double* phi, double eps,
+                            double* f, void* stream);
+/* L = sum_c V_c |F_Ma,c|^2 of the sfx_marangoni_force field (FP64), and,
+   when dloss_df != NULL, dL/df per cell.  Waits for stream. */
+sfx_status sfx_marangoni_loss(sfx_ctx* ctx, const sfx_params* params, const double* f,
+                              const double* phi, const double* C, int dm_mode, double* loss,
+                              double* dloss_df, void* stream);
+/* out = (-J) v, or (-J)^T v when transpose != 0, at the state (f, F) after
+   a step of size dt (for checks of the adjoint).  Outputs must not alias
+   inputs. */
+sfx_status sfx_adjoint_apply(sfx_ctx* ctx, const sfx_params* params, const double* phi,
+                             const double* f, const double* F, double dt, int transpose,
+                             const double* vf, const double* vF, double* out_f, double* out_F,
+                             void* stream);
+/* One adjoint step.  f, F: the state after the forward step; lam_f, lam_F:
+   in dL/d(f, F) after the step, out dL/d(f, F) before it (in place);
+   dparams (host, 4 doubles, may be NULL): the step's dL/d(k_a, k_d, D_f,
+   D_F) is added.  The transposed system is relaxed by red-black Gauss-
+   Seidel with a 2x2 solve per cell, nu1 + nu2 sweeps between residual
+   checks, until max|lam1 - (-J)^T nu| <= tol max|lam1| or max_cycles
+   checks (then SFX_ERR_NOT_CONVERGED, outputs written).  stats (may be
+   NULL): picard = checks, vcycles = sweeps, res_f = res_F = the final
+   relative residual.  Waits for stream. */
+sfx_status sfx_adjoint_step(sfx_ctx* ctx, const sfx_params* params, const double* phi,
+                            const double* f, const double* F, double dt, double* lam_f,
+                            double* lam_F, double* dparams, const sfx_solve_opts* opts,
+                            sfx_step_stats* stats, void* stream);
+
 /* Batched SFX_F32 step over many independent axisymmetric blocks
    (Sec. 4.3 runs series of drop cases with different Bi and Da; each one is
    a small (r, z) block).  Every instance has its own size, h, dt and

@@ -17,7 +17,7 @@ from . import _lib
 from ._lib import (SFX_AXISYM, SFX_CART3D, SFX_F32, SFX_F64, SFX_OK, SFX_ERR_NOT_CONVERGED,
                    SFX_PLANAR2D, Grid, Params, SolveOpts, StepStats)
 
-__all__ = ["SfxError", "Context", "Batch", "lib", "default_opts", "SFX_PLANAR2D", "SFX_AXISYM",
+__all__ = ["SfxError", "Context", "Batch", "SurfactantRollout", "RolloutSetup", "lib", "default_opts", "SFX_PLANAR2D", "SFX_AXISYM",
            "SFX_CART3D", "SFX_F64", "SFX_F32"]
 
 
@@ -167,6 +167,52 @@ class Context:
             out[name] = (n.value, ms.value, nt.value)
         return out
 
+    # ------------------------------------------------------------ adjoint
+    def sfx_f_from_gamma(self, gamma, phi, eps, out=None):
+        """f = Gamma delta_phi (double tensors); also maps dL/df to dL/dGamma."""
+        import torch
+        if out is None:
+            out = torch.empty_like(gamma)
+        _check(lib().sfx_f_from_gamma(self._h, _ptr(gamma), _ptr(phi), float(eps), _ptr(out),
+                                      _stream()), "sfx_f_from_gamma")
+        return out
+
+    def sfx_marangoni_loss(self, params, f, phi, Cf, dm_mode=1, grad=True):
+        """(L = sum V |F_Ma|^2, dL/df or None); all double tensors."""
+        import torch
+        ps = params if isinstance(params, Params) else params_struct(params)
+        g = torch.empty_like(f) if grad else None
+        L = C.c_double(0)
+        _check(lib().sfx_marangoni_loss(self._h, C.byref(ps), _ptr(f), _ptr(phi), _ptr(Cf),
+                                        int(dm_mode), C.byref(L), _ptr(g), _stream()),
+               "sfx_marangoni_loss")
+        return L.value, g
+
+    def sfx_adjoint_apply(self, params, phi, f, F, dt, vf, vF, transpose=False):
+        """((-J) v) or ((-J)^T v) at the state (f, F) after a step."""
+        import torch
+        ps = params if isinstance(params, Params) else params_struct(params)
+        of, oF = torch.empty_like(vf), torch.empty_like(vF)
+        _check(lib().sfx_adjoint_apply(self._h, C.byref(ps), _ptr(phi), _ptr(f), _ptr(F),
+                                       float(dt), 1 if transpose else 0, _ptr(vf), _ptr(vF),
+                                       _ptr(of), _ptr(oF), _stream()), "sfx_adjoint_apply")
+        return of, oF
+
+    def sfx_adjoint_step(self, params, phi, f, F, dt, lam_f, lam_F, dparams=None, opts=None):
+        """lam (in place) from dL/dx after the step to dL/dx before it; adds
+        the step's dL/d(k_a, k_d, D_f, D_F) to dparams (4 floats, a list)."""
+        ps = params if isinstance(params, Params) else params_struct(params)
+        o = opts if opts is not None else default_opts(tol=1e-13, max_cycles=500, nu1=4, nu2=4)
+        dp = (C.c_double * 4)(*(dparams if dparams is not None else [0.0] * 4))
+        st_ = StepStats()
+        _check(lib().sfx_adjoint_step(self._h, C.byref(ps), _ptr(phi), _ptr(f), _ptr(F),
+                                      float(dt), _ptr(lam_f), _ptr(lam_F), dp, C.byref(o),
+                                      C.byref(st_), _stream()), "sfx_adjoint_step")
+        if dparams is not None:
+            for k in range(4):
+                dparams[k] = dp[k]
+        return st_
+
     def sfx_cfl_dt(self, ux, uy, uz, D, eps, safety=1.0):
         out = C.c_double(0)
         _check(lib().sfx_cfl_dt(self._h, _ptr(ux), _ptr(uy), _ptr(uz), float(D), float(eps),
@@ -262,3 +308,6 @@ def sfx_df_unpack(p, out=None):
         out = torch.empty(tuple(p.shape[:-1]), dtype=torch.float64, device=p.device)
     _check(lib().sfx_df_unpack(_ptr(p), _ptr(out), out.numel(), _stream()), "sfx_df_unpack")
     return out
+
+
+from .adjoint import RolloutSetup, SurfactantRollout  # noqa: E402

@@ -24,7 +24,8 @@ EXPORTS = [
     "sfx_profile", "sfx_profile_read", "sfx_totals_noalloc", "sfx_df_pack", "sfx_df_unpack",
     "sfx_set_tuning", "sfx_batch_create", "sfx_batch_destroy",
     "sfx_batch_layout", "sfx_batch_set_schedule", "sfx_batch_step", "sfx_batch_stats",
-    "sfx_batch_autotune", "sfx_batch_work",
+    "sfx_batch_autotune", "sfx_batch_work", "sfx_f_from_gamma", "sfx_marangoni_loss",
+    "sfx_adjoint_apply", "sfx_adjoint_step",
 ]
 SFX_TUNE_FUSED_SWEEP = 0
 SFX_TUNE_F32_SOLVER = 1
@@ -137,5 +138,17 @@ def load(path: str = SO_PATH):
     L.sfx_batch_work.restype = C.c_int
     L.sfx_batch_work.argtypes = [vp, C.POINTER(C.c_longlong), C.POINTER(C.c_longlong), C.c_int,
                                  vp]
+    L.sfx_f_from_gamma.restype = C.c_int
+    L.sfx_f_from_gamma.argtypes = [vp, vp, vp, dp, vp, vp]
+    L.sfx_marangoni_loss.restype = C.c_int
+    L.sfx_marangoni_loss.argtypes = [vp, C.POINTER(Params), vp, vp, vp, C.c_int,
+                                     C.POINTER(C.c_double), vp, vp]
+    L.sfx_adjoint_apply.restype = C.c_int
+    L.sfx_adjoint_apply.argtypes = [vp, C.POINTER(Params), vp, vp, vp, dp, C.c_int, vp, vp, vp,
+                                    vp, vp]
+    L.sfx_adjoint_step.restype = C.c_int
+    L.sfx_adjoint_step.argtypes = [vp, C.POINTER(Params), vp, vp, vp, dp, vp, vp,
+                                   C.POINTER(C.c_double), C.POINTER(SolveOpts),
+                                   C.POINTER(StepStats), vp]
     _lib = L
     return L

@@ -150,6 +150,8 @@ void sfx_ctx_destroy(sfx_ctx* c) {
   for (void* p : c->allocations) cudaFree(p);
   if (c->h_norms) cudaFreeHost(c->h_norms);
   if (c->h_sums) cudaFreeHost(c->h_sums);
+  if (c->adj.h_out) cudaFreeHost(c->adj.h_out);
+  if (c->adj.h_nrm) cudaFreeHost(c->adj.h_nrm);
   delete c;
 }
 
@@ -255,6 +257,47 @@ sfx_status sfx_marangoni_force(sfx_ctx* c, const sfx_params* params, const void*
   if (!sigma) return SFX_ERR_ARG;
   return marangoni(c, params, (const double*)f, phi, (const double*)C, dm_mode, (double*)sigma,
                    (double*)force, S(stream));
+}
+
+sfx_status sfx_f_from_gamma(sfx_ctx* c, const double* gamma, const double* phi, double eps,
+                            double* f, void* stream) {
+  if (!c || !gamma || !phi || !f || !(eps > 0.0)) return SFX_ERR_ARG;
+  return f_from_gamma(c, gamma, phi, eps, f, S(stream));
+}
+
+sfx_status sfx_marangoni_loss(sfx_ctx* c, const sfx_params* params, const double* f,
+                              const double* phi, const double* C, int dm_mode, double* loss,
+                              double* dloss_df, void* stream) {
+  if (!c || !params_ok(params) || !f || !phi || !C || !loss) return SFX_ERR_ARG;
+  if (dm_mode != 0 && dm_mode != 1) return SFX_ERR_ARG;
+  return marangoni_loss(c, params, f, phi, C, dm_mode, loss, dloss_df, S(stream));
+}
+
+sfx_status sfx_adjoint_apply(sfx_ctx* c, const sfx_params* params, const double* phi,
+                             const double* f, const double* F, double dt, int transpose,
+                             const double* vf, const double* vF, double* out_f, double* out_F,
+                             void* stream) {
+  if (!c || !params_ok(params) || !phi || !f || !F || !vf || !vF || !out_f || !out_F ||
+      !(dt > 0.0) || !std::isfinite(dt))
+    return SFX_ERR_ARG;
+  if (out_f == out_F || out_f == vf || out_f == vF || out_F == vf || out_F == vF)
+    return SFX_ERR_ARG;
+  return adjoint_apply(c, params, phi, f, F, dt, transpose ? 1 : 0, vf, vF, out_f, out_F,
+                       S(stream));
+}
+
+sfx_status sfx_adjoint_step(sfx_ctx* c, const sfx_params* params, const double* phi,
+                            const double* f, const double* F, double dt, double* lam_f,
+                            double* lam_F, double* dparams, const sfx_solve_opts* opts,
+                            sfx_step_stats* stats, void* stream) {
+  if (!c || !params_ok(params) || !phi || !f || !F || !lam_f || !lam_F || lam_f == lam_F ||
+      !(dt > 0.0) || !std::isfinite(dt))
+    return SFX_ERR_ARG;
+  sfx_solve_opts o;
+  sfx_default_opts(&o);
+  if (opts) o = *opts;
+  if (!opts_ok(&o)) return SFX_ERR_ARG;
+  return adjoint_step(c, params, phi, f, F, dt, lam_f, lam_F, dparams, &o, stats, S(stream));
 }
 
 sfx_status sfx_cfl_dt(sfx_ctx* c, const void* ux, const void* uy, const void* uz, double D,

@@ -4,6 +4,7 @@
 #include <cstring>
 
 #include "sfx_internal.h"
+#include "sfx_op64.cuh"
 
 namespace sfx {
 namespace {
@@ -99,6 +100,16 @@ __global__ void k_eos(size_t n, EosArgs q, const double* __restrict__ f,
   }
 }
 
+// d sigma/d Gamma of the EOS above (0 where the Langmuir sigma is clamped)
+__device__ __forceinline__ double eos_slope(const EosArgs& q, double G) {
+  const double x = G / q.ginf;
+  if (q.eos == SFX_EOS_LANGMUIR)
+    return x < 1.0 - 1e-12 ? -q.sigma0 * q.E / (q.ginf * (1.0 - x)) : 0.0;
+  if (q.eos == SFX_EOS_LINEAR) return -q.sigma0 * q.E / q.ginf;
+  const double t = tanh(q.E * x);
+  return -q.sigma0 * q.E / q.ginf * (1.0 - t * t);
+}
+
 // ------------------------------------------------------------- PLIC area
 // Fraction of the unit cube below the plane m.x = a (m >= 0, sum m = 1;
 // Scardovelli & Zaleski 2000) and its slope dV/da.  The cubic is expanded
@@ -182,7 +193,7 @@ __device__ double plic_unit_area(int nd, const double* mraw, double C) {
 template <typename P>
 __global__ void k_force(Level L, const P* __restrict__ phi, const double* __restrict__ C,
                         const double* __restrict__ sigma, int dm_mode, double eps,
-                        double* __restrict__ force) {
+                        double* __restrict__ force, double* __restrict__ dm_out) {
   const size_t n = L.ncell();
   const int nd = L.ndim();
   const double inv2h = 0.5 / L.h;
@@ -236,10 +247,97 @@ __global__ void k_force(Level L, const P* __restrict__ phi, const double* __rest
       }
     }
     for (int d = 0; d < nd; ++d) force[(size_t)d * n + c] = dm * (gs[d] - nn[d] * ndg);
+    if (dm_out) dm_out[c] = dm;
+  }
+}
+
+// Loss L = sum_c V_c |F_Ma,c|^2: block partials of the sum and, when G is
+// given, G_c = dL/d(grad sigma)_c = 2 V_c delta_m,c F_Ma,c (F_Ma is already
+// tangential, so the projector (I - n n) maps it to itself).
+__global__ void k_loss_partials(Level L, const double* __restrict__ force,
+                                const double* __restrict__ dm, double* __restrict__ G,
+                                double* __restrict__ part) {
+  const size_t n = L.ncell();
+  const int nd = L.ndim();
+  double s = 0.0, e = 0.0;
+  for (size_t c = blockIdx.x * (size_t)blockDim.x + threadIdx.x; c < n;
+       c += (size_t)gridDim.x * blockDim.x) {
+    const double V = cell_volume(L, (int)(c % L.nx));
+    double q = 0.0;
+    for (int d = 0; d < nd; ++d) {
+      const double Fd = force[(size_t)d * n + c];
+      q += Fd * Fd;
+      if (G) G[(size_t)d * n + c] = 2.0 * V * dm[c] * Fd;
+    }
+    double u, w;
+    two_sum(s, V * q, u, w);
+    s = u;
+    e += w;
+  }
+  block_sum_comp<kTotThreads>(s, e);
+  if (threadIdx.x == 0) {
+    part[2 * (size_t)blockIdx.x] = s;
+    part[2 * (size_t)blockIdx.x + 1] = e;
+  }
+}
+
+// dL/df: the transpose of the centred gradient with its one-sided copies at
+// walls (grad sigma_c = (sigma_{c+} - sigma_{c-})/2h, c+ = c at the upper
+// wall, c- = c at the lower one) gives dL/dsigma; then through the EOS and
+// Gamma = f/delta_phi.
+__global__ void k_loss_grad(Level L, EosArgs q, const double* __restrict__ f,
+                            const double* __restrict__ phi, const double* __restrict__ G,
+                            double* __restrict__ out) {
+  const size_t n = L.ncell();
+  const int nd = L.ndim();
+  const double inv2h = 0.5 / L.h;
+  for (size_t c = blockIdx.x * (size_t)blockDim.x + threadIdx.x; c < n;
+       c += (size_t)gridDim.x * blockDim.x) {
+    const int idx[3] = {(int)(c % L.nx), (int)((c / L.nx) % L.ny),
+                        (int)(c / ((size_t)L.nx * L.ny))};
+    double g = 0.0;
+    for (int d = 0; d < nd; ++d) {
+      const double* Gd = G + (size_t)d * n;
+      const size_t st = d == 0 ? 1 : (d == 1 ? (size_t)L.nx : (size_t)L.nx * L.ny);
+      const int p = idx[d], m = L.extent(d);
+      if (p >= 1) g += Gd[c - st];
+      if (p == m - 1) g += Gd[c];
+      if (p <= m - 2) g -= Gd[c + st];
+      if (p == 0) g -= Gd[c];
+    }
+    g *= inv2h;
+    const double ph = phi[c];
+    const double del = ph * (1.0 - ph) / q.eps;
+    out[c] = del >= 1e-3 / q.eps ? g * eos_slope(q, f[c] / del) / del : 0.0;
   }
 }
 
 }  // namespace
+
+sfx_status marangoni_loss(sfx_ctx* c, const sfx_params* p, const double* f, const double* phi,
+                          const double* C, int dm_mode, double* loss, double* grad,
+                          cudaStream_t s) {
+  sfx_status st = adj_ensure_scratch(c);
+  if (st != SFX_OK) return st;
+  const Level& L = c->lev[0].lv;
+  const size_t n = L.ncell();
+  const int nb = blocks_for(n, 256);
+  EosArgs q{p->gamma_inf, p->eps, p->sigma0, p->E, p->eos};
+  SFX_KERNEL(c, K_FORCES, k_eos<double>, nb, 256, s, n, q, f, phi, c->adj.sig);
+  SFX_KERNEL(c, K_FORCES, k_force<double>, nb, 256, s, L, phi, C, c->adj.sig, dm_mode, p->eps,
+             c->adj.force, c->adj.dm);
+  const int nbp = c->adj.nblk;
+  SFX_KERNEL(c, K_FORCES, k_loss_partials, nbp, kTotThreads, s, L, c->adj.force, c->adj.dm,
+             grad ? c->adj.G : nullptr, c->adj.part);
+  SFX_KERNEL(c, K_FORCES, k_total_final, 1, kTotThreads, s, c->adj.part, nbp, c->adj.d_out);
+  if (grad)
+    SFX_KERNEL(c, K_FORCES, k_loss_grad, nb, 256, s, L, q, f, phi, c->adj.G, grad);
+  SFX_LAUNCH_CHECK();
+  SFX_CUDA(cudaMemcpyAsync(c->adj.h_out, c->adj.d_out, sizeof(double), cudaMemcpyDeviceToHost, s));
+  SFX_CUDA(cudaStreamSynchronize(s));
+  *loss = c->adj.h_out[0];
+  return SFX_OK;
+}
 
 sfx_status totals(sfx_ctx* c, const double* const* fields, int nf, double* out, cudaStream_t s) {
   const Level& L = c->lev[0].lv;
@@ -263,7 +361,7 @@ sfx_status marangoni(sfx_ctx* c, const sfx_params* p, const double* f, const voi
   const int nb = blocks_for(n, 256);
   SFX_KERNEL(c, K_FORCES, k_eos<double>, nb, 256, s, n, q, f, (const double*)phi, sigma);
   SFX_KERNEL(c, K_FORCES, k_force<double>, nb, 256, s, L, (const double*)phi, C, sigma, dm_mode,
-             p->eps, force);
+             p->eps, force, (double*)nullptr);
   SFX_LAUNCH_CHECK();
   return SFX_OK;
 }

@@ -57,6 +57,26 @@ struct F32Scratch {
   float *lf = nullptr, *lF = nullptr;   // diagonals of the linearised problems
 };
 
+// Work arrays of the adjoint and of the Marangoni loss (FP64, either
+// context precision), allocated on first use.
+struct AdjScratch {
+  bool ready = false;
+  double* Bf[3] = {};             // drift faces of unit diffusivity, f problem
+  double* BF[3] = {};             // and F problem
+  double* nf = nullptr;           // adjoint unknowns nu_f, nu_F
+  double* nF = nullptr;
+  double* sig = nullptr;          // sigma of the loss
+  double* force = nullptr;        // ndim x N
+  double* dm = nullptr;           // delta_m per cell
+  double* G = nullptr;            // dL/d(grad sigma), ndim x N
+  double* part = nullptr;         // block partial sums, 5 quantities
+  int nblk = 0;
+  double* d_out = nullptr;        // 8 reduced values (device) and mirror
+  double* h_out = nullptr;
+  unsigned long long* d_nrm = nullptr;   // 2 max-norm slots and mirror
+  unsigned long long* h_nrm = nullptr;
+};
+
 struct Prof {
   bool on = false;
   long long launches[K_COUNT] = {};
@@ -88,6 +108,7 @@ struct sfx_ctx {
   std::vector<void*> allocations;
   sfx::Prof prof;
   sfx::F32Scratch f32;
+  sfx::AdjScratch adj;
 };
 
 namespace sfx {
@@ -126,7 +147,23 @@ sfx_status mg_solve(sfx_ctx* c, double D, const double* Bx, const double* By, co
 sfx_status surfactant_step(sfx_ctx* c, const sfx_params* p, const void* phi, const void* ux,
                            const void* uy, const void* uz, double* f, double* F, double dt,
                            const sfx_solve_opts* o, sfx_step_stats* st, cudaStream_t s);
+// sfx_solver.cu: drift faces of both problems from a double phi
+sfx_status drift_faces64(sfx_ctx* c, const double* phi, double Df, double DF, double eps,
+                         double* const* Bf, double* const* BF, cudaStream_t s);
+// sfx_adjoint.cu
+sfx_status adj_ensure_scratch(sfx_ctx* c);
+sfx_status f_from_gamma(sfx_ctx* c, const double* gamma, const double* phi, double eps,
+                        double* f, cudaStream_t s);
+sfx_status adjoint_apply(sfx_ctx* c, const sfx_params* p, const double* phi, const double* f,
+                         const double* F, double dt, int transpose, const double* vf,
+                         const double* vF, double* of, double* oF, cudaStream_t s);
+sfx_status adjoint_step(sfx_ctx* c, const sfx_params* p, const double* phi, const double* f,
+                        const double* F, double dt, double* lf, double* lF, double* dparams,
+                        const sfx_solve_opts* o, sfx_step_stats* st, cudaStream_t s);
 // sfx_forces.cu
+sfx_status marangoni_loss(sfx_ctx* c, const sfx_params* p, const double* f, const double* phi,
+                          const double* C, int dm_mode, double* loss, double* grad,
+                          cudaStream_t s);
 sfx_status totals(sfx_ctx* c, const double* const* fields, int n, double* out, cudaStream_t s);
 sfx_status marangoni(sfx_ctx* c, const sfx_params* p, const double* f, const void* phi,
                      const double* C, int dm_mode, double* sigma, double* force,

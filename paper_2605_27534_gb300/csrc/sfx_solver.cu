@@ -14,78 +14,12 @@
 #include <cstring>
 
 #include "sfx_internal.h"
+#include "sfx_op64.cuh"
 
 namespace sfx {
 namespace {
 
 constexpr int kMaxLevels = 16;
-
-struct Op {
-  double D;
-  const double* B[3];   // face drifts (NULL: zero)
-  int literal;
-  const double* lam;
-};
-
-__device__ __forceinline__ void face_coeffs(double Doh, double B, int literal, double& cL,
-                                            double& cR) {
-  cL = -Doh;
-  cR = Doh;
-  bool left = literal ? (B > 0.0) : (B < 0.0);
-  if (left) cL += B;
-  else cR += B;
-}
-
-__device__ __forceinline__ double faceB(const double* B, size_t f) {
-  return B ? B[f] : 0.0;
-}
-
-// S_d and S_n of cell (i,j,k) (see the file comment).
-__device__ __forceinline__ void flux_terms(const Level& L, const Op& op, const double* __restrict__ a,
-                                           int i, int j, int k, double& sd, double& sn) {
-  const double Doh = op.D / L.h;
-  double cL, cR;
-  sd = 0.0;
-  sn = 0.0;
-  // x (radial in the axisymmetric case)
-  if (i + 1 < L.nx) {
-    double A = face_area(L, 0, i + 1);
-    face_coeffs(Doh, faceB(op.B[0], fidx(L, 0, i + 1, j, k)), op.literal, cL, cR);
-    sd += A * cL;
-    sn += A * cR * a[cidx(L, i + 1, j, k)];
-  }
-  if (i > 0) {
-    double A = face_area(L, 0, i);
-    face_coeffs(Doh, faceB(op.B[0], fidx(L, 0, i, j, k)), op.literal, cL, cR);
-    sd -= A * cR;
-    sn -= A * cL * a[cidx(L, i - 1, j, k)];
-  }
-  // y (axial in the axisymmetric case); both faces share the column's area
-  const double Ay = face_area(L, 1, i);
-  if (j + 1 < L.ny) {
-    face_coeffs(Doh, faceB(op.B[1], fidx(L, 1, i, j + 1, k)), op.literal, cL, cR);
-    sd += Ay * cL;
-    sn += Ay * cR * a[cidx(L, i, j + 1, k)];
-  }
-  if (j > 0) {
-    face_coeffs(Doh, faceB(op.B[1], fidx(L, 1, i, j, k)), op.literal, cL, cR);
-    sd -= Ay * cR;
-    sn -= Ay * cL * a[cidx(L, i, j - 1, k)];
-  }
-  if (L.geom == SFX_CART3D) {
-    const double Az = L.h * L.h;
-    if (k + 1 < L.nz) {
-      face_coeffs(Doh, faceB(op.B[2], fidx(L, 2, i, j, k + 1)), op.literal, cL, cR);
-      sd += Az * cL;
-      sn += Az * cR * a[cidx(L, i, j, k + 1)];
-    }
-    if (k > 0) {
-      face_coeffs(Doh, faceB(op.B[2], fidx(L, 2, i, j, k)), op.literal, cL, cR);
-      sd -= Az * cR;
-      sn -= Az * cL * a[cidx(L, i, j, k - 1)];
-    }
-  }
-}
 
 // One colour of a red-black Gauss-Seidel sweep: a_c = (b_c + S_n/V)/(lam - S_d/V)
 __global__ void k_rbgs(Level L, Op op, const double* __restrict__ b, double* __restrict__ a,
@@ -545,6 +479,16 @@ sfx_status step_impl(sfx_ctx* c, const sfx_params* p, const P* phi, const void* 
 }
 
 }  // namespace
+
+sfx_status drift_faces64(sfx_ctx* c, const double* phi, double Df, double DF, double eps,
+                         double* const* Bf, double* const* BF, cudaStream_t s) {
+  const Level& L = c->lev[0].lv;
+  for (int d = 0; d < L.ndim(); ++d)
+    SFX_KERNEL(c, K_SETUP, k_drift_faces<double>, blocks_for(L.nface(d), 256), 256, s, L, d, phi,
+               Df, DF, eps, Bf[d], BF[d]);
+  SFX_LAUNCH_CHECK();
+  return SFX_OK;
+}
 
 sfx_status surfactant_step(sfx_ctx* c, const sfx_params* p, const void* phi, const void* ux,
                            const void* uy, const void* uz, double* f, double* F, double dt,
