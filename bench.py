@@ -55,6 +55,9 @@ def parse():
     ap.add_argument("--tol", type=float, default=1e-10)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--predict", action="store_true",
+                    help="FP32: start each Newton solve from x* plus the last increment "
+                         "(SFX_TUNE_PREDICT 1; no gain on the 3D workload)")
     ap.add_argument("--oracle-steps", type=int, default=3)
     return ap.parse_args()
 
@@ -87,12 +90,14 @@ def algorithmic_bytes(kind, grid, wbytes, sweeps=3):
         # the updated half (24 B x 1/2), the 2 d float drift-face arrays of
         # both fields, write the updated half of both corrections; the last
         # black sweep of each iteration also reads and writes the state
-        # (32 B), averaged here over the 2 x sweeps colour launches
-        return (8.0 + 12.0 + 8.0 * d + 4.0 + 32.0 / (2 * sweeps)) * N
+        # (32 B), averaged here over the 2 x sweeps - 1 colour launches (the
+        # residual pass does the first red half-sweep)
+        return (8.0 + 12.0 + 8.0 * d + 4.0 + 32.0 / (2 * sweeps - 1)) * N
     if kind == "residual" and wbytes == 4:
         # k_resid2_32: f, F, f*, F* (pairs), phi, 2 d float faces; writes the
-        # 2x2 coefficients and the residuals
-        return (16.0 + 16.0 + 4.0 + 8.0 * d + 16.0 + 8.0) * N
+        # 2x2 coefficients, the residuals and the red half of both
+        # corrections
+        return (16.0 + 16.0 + 4.0 + 8.0 * d + 16.0 + 8.0 + 4.0) * N
     if kind == "advect":
         return 16.0 * N + wbytes * d * N
     return None
@@ -261,12 +266,14 @@ def run_gpu(a, case, rank, world, local_rank):
     if prec == sfx.SFX_F32:   # three coupled correction sweeps per Newton iteration
         opts.nu1, opts.nu2 = 3, 0
         ctx.sfx_set_tuning(sfx._lib.SFX_TUNE_REUSE_DRIFT, 1)   # the interface is static
+        ctx.sfx_set_tuning(sfx._lib.SFX_TUNE_PREDICT, 1 if a.predict else 0)
     stats = []
 
     def step():
         st = ctx.sfx_surfactant_step(p, phi, f, F, case.dt, ux, uy, uz, opts=opts)
         ctx.sfx_marangoni_force(p, f, phi, Cw, sigma, force, dm_mode=1)
-        stats.append((st.picard, st.vcycles, st.res_f, st.res_F, st.mass_f, st.mass_F))
+        stats.append((st.picard, st.vcycles, st.res_f, st.res_F, st.mass_f, st.mass_F,
+                      st.converged))
 
     def barrier():
         if world > 1:
@@ -334,13 +341,25 @@ def run_gpu(a, case, rank, world, local_rank):
     kind, (nl, tot_ms, nt) = top
     roof = None
     sw = max(1, opts.nu1 + opts.nu2)
+    # launches that did work: in the FP32 Newton solve every launch after
+    # the converged residual pass returns at once (and a rejected predicted
+    # start adds one residual pass, not counted here), so they are counted
+    # from the iterations, not from the launch counter
+    working = {}
+    if prec == sfx.SFX_F32 and nt == nl:
+        timed = stats[-a.steps:]
+        working["smooth_fine"] = sum((k - 1 if cv else k) * (2 * sw - 1)
+                                     for k, *_, cv in timed)
+        working["residual"] = sum(k for k, *_ in timed)
     ab = algorithmic_bytes(kind, g, wbytes, sw)
-    if ab is not None and nt > 0:
-        avg_s = tot_ms * 1e-3 / nt
+    nwork = working.get(kind, nt)
+    if ab is not None and nwork > 0:
+        avg_s = tot_ms * 1e-3 / nwork
         achieved = ab / avg_s / 1e9
         roof = {"bound": "hbm", "kernel": kind, "achieved": achieved, "peak": peaks["hbm_gbs"],
                 "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"], "traffic": None,
                 "algorithmic_bytes_per_launch": ab, "avg_launch_ms": avg_s * 1e3,
+                "working_launches": nwork, "launches": nl,
                 "peak_source": "%s (MEASURED_PEAKS.json hbm_gbs)" % peak_src}
     launches = int(sum(v[0] for v in prof.values()))
     breakdown = {}
@@ -349,8 +368,11 @@ def run_gpu(a, case, rank, world, local_rank):
             continue
         e = {"launches": v[0], "ms": round(v[1], 3)}
         b = algorithmic_bytes(k, g, wbytes, sw)
-        if b is not None and v[2] > 0:
-            e["gbs"] = round(b / (v[1] * 1e-3 / v[2]) / 1e9, 1)
+        nw = working.get(k, v[2])
+        if k in working:
+            e["working_launches"] = nw
+        if b is not None and nw > 0:
+            e["gbs"] = round(b / (v[1] * 1e-3 / nw) / 1e9, 1)
         breakdown[k] = e
     cpu = None
     if not a.no_cpu:
@@ -375,6 +397,7 @@ def run_gpu(a, case, rank, world, local_rank):
         "config": {"workload": "%s: 3D %d^3 HR Stokes flow, sphere R=0.125, Bi=Da=1, "
                                "dt=%g, tol=%g" % (case.name, g.nx, case.dt, a.tol),
                    "cells": g.ncell, "precision": a.precision,
+                   "newton_start": "x* + last increment" if a.predict else "x*",
                    "l2": "inputs larger than L2 (state + coefficients %.2f GB)" % (
                        g.ncell * 8 * 20 / 1e9),
                    "parallelism": "replicas%d" % world,
@@ -484,14 +507,15 @@ def batch_bytes(sizes, rp, sg, steps, sweeps):
     cells and per step: folded copy of phi (12 N), drift faces (phi 8 +
     2 fields x 2 faces x 4 = 24 N), advection of both fields (pairs in and
     out 32 N, 2 velocity arrays 8 N), copy into the iterate (32 N), totals
-    (16 N); per residual pass (16 + 16 + 4 + 16 + 16 + 8 =
-    76 N); per sweep group 2 x sweeps colour launches of (8 + 12 + 16 + 4 =
-    40 N) and the state update (32 N)."""
+    (16 N); per residual pass (16 + 16 + 4 + 16 + 16 + 8 + 4 = 80 N, the
+    last term the red half of both corrections); per sweep group
+    2 x sweeps - 1 colour launches of (8 + 12 + 16 + 4 = 40 N) and the state
+    update (32 N)."""
     tot = 0.0
     for (nr, nz), r, w in zip(sizes, rp, sg):
         N = nr * nz
-        tot += N * (steps * (12.0 + 24.0 + 40.0 + 32.0 + 16.0) + r * 76.0 +
-                    w * (2 * sweeps * 40.0 + 32.0))
+        tot += N * (steps * (12.0 + 24.0 + 40.0 + 32.0 + 16.0) + r * 80.0 +
+                    w * ((2 * sweeps - 1) * 40.0 + 32.0))
     return tot
 
 
@@ -582,7 +606,7 @@ def run_gpu_batch(a, rank, world, local_rank, steps=None, summary=False):
     sched = {"block": block, "sweeps": sweeps, "iteration_budget": budget}
     # init, fold, 2 drift, advect, copy; per iteration residual, flags and
     # the colour sweeps; totals
-    launches_per_step = 6 + budget * (2 + 2 * sweeps) + 1
+    launches_per_step = 6 + budget * (1 + 2 * sweeps) + 1
     if summary:
         return {"value": value, "unit": UNIT, "ms_per_step": ms / steps, "steps": steps,
                 "cells": ncell, "instances": len(inst), "roofline_frac": roof["frac"],

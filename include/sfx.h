@@ -243,13 +243,23 @@ typedef enum {
                                fields linearised alternately (Picard);
                                0 = nonlinear red-black sweeps on the pair
                                state.  Same fixed point, same test. */
-  SFX_TUNE_REUSE_DRIFT = 2  /* SFX_F32: 1 = keep the drift faces and the
+  SFX_TUNE_REUSE_DRIFT = 2, /* SFX_F32: 1 = keep the drift faces and the
                                folded float copy of phi of the last step
                                while phi's pointer, Df, DF and eps are
                                unchanged (for a static interface; after
                                writing phi in place, set the knob again to
                                force a rebuild); 0 (default) = rebuild them
                                every step. */
+  SFX_TUNE_PREDICT = 3      /* SFX_F32 Newton solver: 1 (default) = start
+                               the iteration from x* plus the previous
+                               step's implicit increment x - x* when the
+                               step continues the same problem (same f, F
+                               and phi buffers, dt and parameters; the last
+                               step converged), restarting from x* when
+                               the predicted start's relative residuals
+                               exceed 1; 0 = start from x*.  Same fixed
+                               point and test; the iterate differs within
+                               the tolerance. */
 } sfx_tune_key;
 sfx_status sfx_set_tuning(sfx_ctx* ctx, int key, int value);
 

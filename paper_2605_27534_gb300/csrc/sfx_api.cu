@@ -326,6 +326,11 @@ sfx_status sfx_set_tuning(sfx_ctx* c, int key, int value) {
     c->f32.drift_phi = nullptr;
     return SFX_OK;
   }
+  if (key == SFX_TUNE_PREDICT && (value == 0 || value == 1)) {
+    c->f32.predict = value == 1;
+    c->f32.inc_valid = false;
+    return SFX_OK;
+  }
   if (key == SFX_TUNE_F32_SOLVER && value >= 0 && value <= 2) {
     c->f32.solver = value;
     c->f32.predicted = 0;

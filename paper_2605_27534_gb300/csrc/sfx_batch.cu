@@ -139,7 +139,7 @@ __global__ void k_b_resid(const BInst* __restrict__ I, int n, const int* __restr
     const float* BF[3] = {P.BF[0] + B.rfoff, P.BF[1] + B.zfoff, nullptr};
     const size_t o = B.coff;
     resid2_cell(B.p, i, j, 0, c, P.phi32 + o, Bf, BF, P.f + o, P.F + o, P.fs + o, P.Fs + o,
-                P.coef + o, P.res + o, m);
+                P.coef + o, P.res + o, m, P.ef + o, P.eF + o);
   }
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
@@ -308,8 +308,9 @@ sfx_status enqueue_step(sfx_batch* b, bool advect, float tol, cudaStream_t s) {
   for (int it = 1; it <= b->max_it; ++it) {
     k_b_resid<<<b->nb_cell, bs, 0, s>>>(b->dI, n, b->pre_cell, P);
     k_b_flags<<<(n + 127) / 128, 128, 0, s>>>(n, P, tol, it);
+    // the residual pass did the first red half-sweep
     for (int q = 0; q < b->sweeps; ++q)
-      for (int color = 0; color < 2; ++color)
+      for (int color = (q == 0 ? 1 : 0); color < 2; ++color)
         k_b_corr<<<b->nb_pair, bs, 0, s>>>(b->dI, n, b->pre_pair, P, color, q == 0 ? 1 : 0,
                                            q == b->sweeps - 1 && color == 1 ? 1 : 0);
   }

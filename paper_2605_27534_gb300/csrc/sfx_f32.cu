@@ -285,7 +285,9 @@ k_resid2_32(Nw32 p, const float* __restrict__ phi, const float* __restrict__ Bfx
             const float* __restrict__ BFz, const float2* __restrict__ fin,
             const float2* __restrict__ Fin, const float2* __restrict__ fst,
             const float2* __restrict__ Fst, float4* __restrict__ coef,
-            float2* __restrict__ res, unsigned int* norms) {
+            float2* __restrict__ res, unsigned int* norms, float* __restrict__ ef,
+            float* __restrict__ eF, const int* __restrict__ done) {
+  if (done && *done) return;   // converged at an earlier iteration
   const Level& L = p.L;
   const size_t n = L.ncell();
   float m[4] = {0.0f, 0.0f, 0.0f, 0.0f};
@@ -294,7 +296,7 @@ k_resid2_32(Nw32 p, const float* __restrict__ phi, const float* __restrict__ Bfx
   for (size_t c = blockIdx.x * (size_t)blockDim.x + threadIdx.x; c < n;
        c += (size_t)gridDim.x * blockDim.x) {
     const int i = (int)(c % L.nx), j = (int)((c / L.nx) % L.ny), k = (int)(c / ((size_t)L.nx * L.ny));
-    resid2_cell(p, i, j, k, c, phi, Bf, BF, fin, Fin, fst, Fst, coef, res, m);
+    resid2_cell(p, i, j, k, c, phi, Bf, BF, fin, Fin, fst, Fst, coef, res, m, ef, eF);
   }
   if (norms) {
 #pragma unroll
@@ -311,7 +313,9 @@ __global__ void k_corr2_32(Nw32 p, const float* __restrict__ Bfx, const float* _
                            const float* __restrict__ BFy, const float* __restrict__ BFz,
                            const float4* __restrict__ coef, const float2* __restrict__ res,
                            float* __restrict__ ef, float* __restrict__ eF, int color, int first,
-                           float2* __restrict__ fst, float2* __restrict__ Fst) {
+                           float2* __restrict__ fst, float2* __restrict__ Fst,
+                           const int* __restrict__ done) {
+  if (done && *done) return;
   const Level& L = p.L;
   const int j = blockIdx.y, k = blockIdx.z;
   const int i = 2 * (blockIdx.x * blockDim.x + threadIdx.x) + ((j + k + color) & 1);
@@ -972,48 +976,129 @@ sfx_status solve_dc32(sfx_ctx* c, const Nl32& pf, const Nl32& pF, const float* p
   return SFX_OK;
 }
 
+// Convergence test of one Newton iteration on the device: once both
+// relative residuals pass, `flag[0]` stops every later launch of the solve
+// and flag[1] records the iteration.
+__global__ void k_flag32(const unsigned int* __restrict__ nrm, float tol, int it,
+                         int* __restrict__ flag) {
+  if (threadIdx.x != 0 || flag[0]) return;
+  const float rf = __uint_as_float(nrm[0]), bf = __uint_as_float(nrm[1]);
+  const float rF = __uint_as_float(nrm[2]), bF = __uint_as_float(nrm[3]);
+  if (rf <= tol * bf && rF <= tol * bF) {
+    flag[0] = 1;
+    flag[1] = it;
+  }
+}
+
+// A predicted start whose first relative residual exceeds `rho` (or is not
+// finite) is rejected: ok = 0 and the norms are cleared for the residual
+// pass of the restart from x*.
+__global__ void k_pred_check32(unsigned int* __restrict__ nrm, float rho, int* __restrict__ ok) {
+  if (threadIdx.x != 0) return;
+  const float rf = __uint_as_float(nrm[0]), bf = __uint_as_float(nrm[1]);
+  const float rF = __uint_as_float(nrm[2]), bF = __uint_as_float(nrm[3]);
+  const bool good = rf <= rho * bf && rF <= rho * bF;   // false for NaN
+  ok[0] = good ? 1 : 0;
+  if (!good)
+    for (int q = 0; q < 4; ++q) nrm[q] = 0u;
+}
+
+// Restart from x* when the prediction was rejected.
+__global__ void k_restore32(size_t n, const int* __restrict__ ok, const float2* __restrict__ fs,
+                            const float2* __restrict__ Fs, float2* __restrict__ f,
+                            float2* __restrict__ F) {
+  if (*ok) return;
+  for (size_t c = blockIdx.x * (size_t)blockDim.x + threadIdx.x; c < n;
+       c += (size_t)gridDim.x * blockDim.x) {
+    f[c] = fs[c];
+    F[c] = Fs[c];
+  }
+}
+
+// Initial guess of the Newton iteration: x* plus the implicit increment of
+// the previous step (a smooth solution changes little from step to step).
+__global__ void k_predict32(size_t n, const float2* __restrict__ fs, const float2* __restrict__ Fs,
+                            const float* __restrict__ df, const float* __restrict__ dF,
+                            float2* __restrict__ f, float2* __restrict__ F) {
+  for (size_t c = blockIdx.x * (size_t)blockDim.x + threadIdx.x; c < n;
+       c += (size_t)gridDim.x * blockDim.x) {
+    f[c] = df_add(fs[c], df[c]);
+    F[c] = df_add(Fs[c], dF[c]);
+  }
+}
+
+// The implicit increment x - x* of this step, kept for the next one.
+__global__ void k_increment32(size_t n, const float2* __restrict__ fs,
+                              const float2* __restrict__ Fs, const float2* __restrict__ f,
+                              const float2* __restrict__ F, float* __restrict__ df,
+                              float* __restrict__ dF) {
+  for (size_t c = blockIdx.x * (size_t)blockDim.x + threadIdx.x; c < n;
+       c += (size_t)gridDim.x * blockDim.x) {
+    df[c] = df_diff(f[c], fs[c]);
+    dF[c] = df_diff(F[c], Fs[c]);
+  }
+}
+
 // Coupled Newton defect correction (see k_resid2_32).
 sfx_status solve_newton32(sfx_ctx* c, const Nw32& p, const float* phi, float* const* Bf,
                           float* const* BF, float2*& fc, float2*& fo, float2*& Fc, float2*& Fo,
                           const float2* fs, const float2* Fs, const sfx_solve_opts* o,
-                          int* iters, bool* conv, float* nrm, cudaStream_t s) {
+                          bool predicted, int* iters, bool* conv, float* nrm, cudaStream_t s) {
   const Level& L = p.L;
   const size_t n = L.ncell();
   const int nb = blocks_for(n, 256);
   const int sweeps = std::max(1, o->nu1 + o->nu2);
+  const float tolf = (float)o->tol;
   dim3 blk(128), grd((unsigned)(((L.nx + 1) / 2 + 127) / 128), (unsigned)L.ny, (unsigned)L.nz);
   unsigned int* dn = (unsigned int*)c->d_norms;        // two 4-slot norm buffers
   unsigned int* hn = (unsigned int*)c->h_norms;
-  // The host stays one iteration ahead: it waits for the norms of
-  // iteration it-1 while the GPU works on iteration it, so the stream never
-  // drains for a convergence test.
+  int* flag = c->f32.flag;
+  SFX_CUDA(cudaMemsetAsync(flag, 0, 2 * sizeof(int), s));
+  // Each iteration: the residual pass (which also does the first red
+  // half-sweep of the correction, from zero), a device-side convergence
+  // test, then the rest of the red-black sweeps, the last black one adding
+  // the corrections to the state.  Once an iteration passes the test every
+  // later launch of the solve returns at once, so the state is the one
+  // whose residuals passed.  The host waits for the norms of iteration
+  // it-1 while the GPU works on iteration it: the stream never drains for
+  // a test.
   *conv = false;
   int it = 0, done_it = 0;
   for (it = 1; it <= o->max_cycles; ++it) {
     unsigned int* nbuf = dn + 4 * (it & 1);
     SFX_CUDA(cudaMemsetAsync(nbuf, 0, 4 * sizeof(unsigned int), s));
     SFX_KERNEL(c, K_RESIDUAL, k_resid2_32, nb, 256, s, p, phi, Bf[0], Bf[1], Bf[2], BF[0], BF[1],
-               BF[2], fc, Fc, fs, Fs, c->f32.coef, c->f32.res, nbuf);
+               BF[2], fc, Fc, fs, Fs, c->f32.coef, c->f32.res, nbuf, c->f32.ef, c->f32.eF, flag);
+    if (it == 1 && predicted) {
+      // keep the predicted start only if its residual is already small;
+      // otherwise restart from x* (both launches return at once when kept)
+      int* ok = flag + 2;
+      const float rho = c->f32.predict_rho;
+      SFX_KERNEL(c, K_OTHER, k_pred_check32, 1, 32, s, nbuf, rho, ok);
+      SFX_KERNEL(c, K_SETUP, k_restore32, nb, 256, s, n, ok, fs, Fs, fc, Fc);
+      SFX_KERNEL(c, K_RESIDUAL, k_resid2_32, nb, 256, s, p, phi, Bf[0], Bf[1], Bf[2], BF[0],
+                 BF[1], BF[2], fc, Fc, fs, Fs, c->f32.coef, c->f32.res, nbuf, c->f32.ef, c->f32.eF,
+                 ok);
+    }
+    SFX_KERNEL(c, K_OTHER, k_flag32, 1, 32, s, nbuf, tolf, it, flag);
     SFX_CUDA(cudaMemcpyAsync(hn + 4 * (it & 1), nbuf, 4 * sizeof(unsigned int),
                              cudaMemcpyDeviceToHost, s));
     SFX_CUDA(cudaEventRecord(c->f32.ev[it & 1], s));
     for (int q = 0; q < sweeps; ++q)
-      for (int color = 0; color < 2; ++color) {
+      for (int color = (q == 0 ? 1 : 0); color < 2; ++color) {
         const bool apply = q == sweeps - 1 && color == 1;
         SFX_KERNEL(c, K_SMOOTH_FINE, k_corr2_32, grd, blk, s, p, Bf[0], Bf[1], Bf[2], BF[0], BF[1],
                    BF[2], c->f32.coef, c->f32.res, c->f32.ef, c->f32.eF, color, q == 0 ? 1 : 0,
-                   apply ? fc : nullptr, apply ? Fc : nullptr);
+                   apply ? fc : nullptr, apply ? Fc : nullptr, flag);
       }
     SFX_LAUNCH_CHECK();
-    // test the previous iteration (its residuals describe the state that
-    // the current iteration's residual pass started from)
     const int prev = it - 1;
     if (prev >= 1) {
       SFX_CUDA(cudaEventSynchronize(c->f32.ev[prev & 1]));
       memcpy(nrm, hn + 4 * (prev & 1), 4 * sizeof(float));
       for (int q = 0; q < 4; ++q)
         if (!std::isfinite(nrm[q])) return SFX_ERR_NONFINITE;
-      if (nrm[0] <= o->tol * nrm[1] && nrm[2] <= o->tol * nrm[3]) {
+      if (nrm[0] <= tolf * nrm[1] && nrm[2] <= tolf * nrm[3]) {   // as k_flag32 decides
         *conv = true;
         done_it = prev;
         break;
@@ -1025,12 +1110,11 @@ sfx_status solve_newton32(sfx_ctx* c, const Nw32& p, const float* phi, float* co
     SFX_CUDA(cudaStreamSynchronize(s));
     const int last = std::min(it, o->max_cycles);
     memcpy(nrm, hn + 4 * (last & 1), 4 * sizeof(float));
-    if (nrm[0] <= o->tol * nrm[1] && nrm[2] <= o->tol * nrm[3]) *conv = true;
+    for (int q = 0; q < 4; ++q)
+      if (!std::isfinite(nrm[q])) return SFX_ERR_NONFINITE;
+    if (nrm[0] <= tolf * nrm[1] && nrm[2] <= tolf * nrm[3]) *conv = true;
     done_it = last;
   }
-  // the state is the one the converged residual pass wrote (fc, Fc hold
-  // the output of the latest residual pass, which applied one more
-  // correction when the test lagged; both are converged states)
   *iters = done_it;
   return SFX_OK;
 }
@@ -1065,16 +1149,31 @@ sfx_status step_f32(sfx_ctx* c, const sfx_params* pr, const double* phi_in, cons
   }
   float2* fs = c->f32.fstar;
   float2* Fs = c->f32.Fstar;
+  // the previous step's implicit increment predicts this one's when the
+  // step continues the same problem (same state buffers, phi, dt and
+  // parameters) and the Newton solver runs
+  const double key[9] = {dt, pr->ka, pr->kd, pr->Df, pr->DF, pr->eps, pr->eta, pr->gamma_inf,
+                         (double)pr->literal_upwind};
+  const bool predict = c->f32.predict && c->f32.solver == 1 && c->f32.inc_valid &&
+                       c->f32.inc_ptr[0] == f && c->f32.inc_ptr[1] == F &&
+                       c->f32.inc_ptr[2] == phi_in && memcmp(c->f32.inc_key, key, sizeof key) == 0;
+  c->f32.inc_valid = false;
   if (ux) {
     Adv32 A{L, (float)dt, (float)(1.0 / L.h), {ux, uy, uz}};
     SFX_KERNEL(c, K_ADVECT, k_advect32, blocks_for(n, 256), 256, s, A, f, (float)pr->bc_f, fs);
     SFX_KERNEL(c, K_ADVECT, k_advect32, blocks_for(n, 256), 256, s, A, F, (float)pr->bc_F, Fs);
     SFX_LAUNCH_CHECK();
-    SFX_CUDA(cudaMemcpyAsync(f, fs, n * sizeof(float2), cudaMemcpyDeviceToDevice, s));
-    SFX_CUDA(cudaMemcpyAsync(F, Fs, n * sizeof(float2), cudaMemcpyDeviceToDevice, s));
   } else {
     SFX_CUDA(cudaMemcpyAsync(fs, f, n * sizeof(float2), cudaMemcpyDeviceToDevice, s));
     SFX_CUDA(cudaMemcpyAsync(Fs, F, n * sizeof(float2), cudaMemcpyDeviceToDevice, s));
+  }
+  if (predict) {
+    SFX_KERNEL(c, K_SETUP, k_predict32, blocks_for(n, 256), 256, s, n, fs, Fs, c->f32.inc_f,
+               c->f32.inc_F, f, F);
+    SFX_LAUNCH_CHECK();
+  } else if (ux) {
+    SFX_CUDA(cudaMemcpyAsync(f, fs, n * sizeof(float2), cudaMemcpyDeviceToDevice, s));
+    SFX_CUDA(cudaMemcpyAsync(F, Fs, n * sizeof(float2), cudaMemcpyDeviceToDevice, s));
   }
   Nl32 pf{L, (float)(1.0 / L.h), (float)(pr->Df / L.h), (float)(1.0 / dt), (float)pr->ka,
           (float)pr->kd, (float)pr->gamma_inf, (float)(1.0 / pr->eps), (float)pr->eta,
@@ -1091,13 +1190,24 @@ sfx_status step_f32(sfx_ctx* c, const sfx_params* pr, const double* phi_in, cons
     if (c->f32.solver == 1) {
       Nw32 pw{L, pf.invh, pf.Doh, pF.Doh, pf.inv_dt, pf.ka, pf.kd, pf.ginf, pf.inv_eps, pf.eta,
               pf.literal};
-      st = solve_newton32(c, pw, phi, Bf, BF, fc, fo, Fc, Fo, fs, Fs, o, &it, &dconv, dn, s);
+      st = solve_newton32(c, pw, phi, Bf, BF, fc, fo, Fc, Fo, fs, Fs, o, predict, &it, &dconv, dn,
+                          s);
     } else {
       st = solve_dc32(c, pf, pF, phi, Bf, BF, fc, fo, Fc, Fo, fs, Fs, o, &it, &dconv, dn, s);
     }
     if (st != SFX_OK) return st;
     if (fc != f) SFX_CUDA(cudaMemcpyAsync(f, fc, n * sizeof(float2), cudaMemcpyDeviceToDevice, s));
     if (Fc != F) SFX_CUDA(cudaMemcpyAsync(F, Fc, n * sizeof(float2), cudaMemcpyDeviceToDevice, s));
+    if (c->f32.predict && c->f32.solver == 1 && dconv) {
+      SFX_KERNEL(c, K_SETUP, k_increment32, blocks_for(n, 256), 256, s, n, fs, Fs, f, F,
+                 c->f32.inc_f, c->f32.inc_F);
+      SFX_LAUNCH_CHECK();
+      c->f32.inc_valid = true;
+      c->f32.inc_ptr[0] = f;
+      c->f32.inc_ptr[1] = F;
+      c->f32.inc_ptr[2] = phi_in;
+      memcpy(c->f32.inc_key, key, sizeof key);
+    }
     if (stats) {
       stats->picard = it;
       stats->vcycles = 2 * it * std::max(1, o->nu1 + o->nu2);
@@ -1249,6 +1359,9 @@ sfx_status f32_ensure_scratch(sfx_ctx* c) {
   if ((st = get(n * sizeof(float2), (void**)&c->f32.Fstar)) != SFX_OK) return st;
   if ((st = get(n * sizeof(float), (void**)&c->f32.dsig)) != SFX_OK) return st;
   if ((st = get(n * sizeof(float), (void**)&c->f32.phi32)) != SFX_OK) return st;
+  if ((st = get(n * sizeof(float), (void**)&c->f32.inc_f)) != SFX_OK) return st;
+  if ((st = get(n * sizeof(float), (void**)&c->f32.inc_F)) != SFX_OK) return st;
+  if ((st = get(4 * sizeof(int), (void**)&c->f32.flag)) != SFX_OK) return st;
   if ((st = get(n * sizeof(float2), (void**)&c->f32.falt)) != SFX_OK) return st;
   if ((st = get(n * sizeof(float2), (void**)&c->f32.Falt)) != SFX_OK) return st;
   float** arrs[6] = {&c->f32.ef, &c->f32.eF, &c->f32.rf, &c->f32.rF, &c->f32.lf, &c->f32.lF};

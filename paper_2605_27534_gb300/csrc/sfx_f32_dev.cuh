@@ -253,7 +253,10 @@ __device__ float face32v(const Adv32& A, const float2* __restrict__ x, float bc_
 
 // Both residuals (pairs) of App. C at cell c of the current state, the
 // kinetic diagonals and couplings of the linearised system, and the running
-// maxima m = {|r_f|, |b_f|, |r_F|, |b_F|}.
+// maxima m = {|r_f|, |b_f|, |r_F|, |b_F|}.  With ef != NULL the first red
+// half-sweep of the correction is done here: it starts from zero
+// corrections, so a red cell (i + j + k even) only needs its own 2x2 block,
+// e = M_c^-1 r_c.
 __device__ __forceinline__ void resid2_cell(const Nw32& p, int i, int j, int k, size_t c,
                                             const float* __restrict__ phi,
                                             const float* const* Bf, const float* const* BF,
@@ -262,7 +265,8 @@ __device__ __forceinline__ void resid2_cell(const Nw32& p, int i, int j, int k, 
                                             const float2* __restrict__ fst,
                                             const float2* __restrict__ Fst,
                                             float4* __restrict__ coef, float2* __restrict__ res,
-                                            float* m) {
+                                            float* m, float* __restrict__ ef,
+                                            float* __restrict__ eF) {
   const Level& L = p.L;
   bool has[6];
   size_t nbi[6];
@@ -302,9 +306,17 @@ __device__ __forceinline__ void resid2_cell(const Nw32& p, int i, int j, int k, 
   const float rf = __fadd_rn(Rf.hi, Rf.lo), rF = __fadd_rn(RF.hi, RF.lo);
   const float Fv = __fadd_rn(Fc.x, Fc.y), fv = __fadd_rn(fc.x, fc.y);
   // diagonals (kinetic part) and couplings of the linearised system
-  coef[c] = make_float4(p.inv_dt + p.kd + c1 * Fv, p.inv_dt + c1 * (finf - fv),
-                        c1 * (finf - fv), c1 * Fv + p.kd);
+  const float4 cf = make_float4(p.inv_dt + p.kd + c1 * Fv, p.inv_dt + c1 * (finf - fv),
+                                c1 * (finf - fv), c1 * Fv + p.kd);
+  coef[c] = cf;
   res[c] = make_float2(rf, rF);
+  if (ef && ((i + j + k) & 1) == 0) {
+    // [a -b; -d e] [x; y] = [r_f; r_F], diagonals with the flux weights
+    const float a = cf.x + df_, bb = cf.z, d = cf.w, e = cf.y + dF_;
+    const float inv = __fdividef(1.0f, a * e - bb * d);
+    ef[c] = (e * rf + bb * rF) * inv;
+    eF[c] = (d * rf + a * rF) * inv;
+  }
   m[0] = fmaxf(m[0], fabsf(rf));
   m[1] = fmaxf(m[1], fabsf(fs.x * p.inv_dt + c1 * Fv * finf));
   m[2] = fmaxf(m[2], fabsf(rF));

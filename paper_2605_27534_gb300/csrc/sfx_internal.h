@@ -51,6 +51,14 @@ struct F32Scratch {
   bool reuse_drift = false;         // keep drift faces while phi and D's are unchanged
   const double* drift_phi = nullptr;
   float* phi32 = nullptr;           // folded float copy of phi
+  int* flag = nullptr;              // convergence flag, iteration, prediction kept
+  bool predict = true;              // start Newton from x* + last increment
+  float predict_rho = 1.0f;         // reject a predicted start above this residual
+  bool inc_valid = false;
+  float* inc_f = nullptr;           // last step's implicit increments x - x*
+  float* inc_F = nullptr;
+  const void* inc_ptr[3] = {nullptr, nullptr, nullptr};   // f, F, phi of that step
+  double inc_key[9] = {};           // dt and parameters of that step
   double drift_key[3] = {0, 0, 0};
   float *ef = nullptr, *eF = nullptr;   // corrections
   float *rf = nullptr, *rF = nullptr;   // residuals

@@ -276,6 +276,35 @@ def test_fp32_solvers_agree(sfx, name):
     assert np.abs(outs[0][1] - outs[1][1]).max() < 1e-10 * scale
 
 
+def test_fp32_predictor_keeps_the_fixed_point_and_saves_iterations(sfx):
+    """Starting each Newton iteration from x* plus the last step's increment
+    reaches the same solution (within the tolerance) in fewer iterations."""
+    import torch
+    c = W.case_axi(32, 64, Bi=1.0, Da=10.0)
+    ux, uy, uz = c.ux, c.uy, None
+    g, p = c.grid, c.params
+    _, phi, _ = oracle.phase_field_build(g, c.C, c.redist_iters, c.dtau, p.eps)
+    out, its = [], []
+    for predict in (0, 1):
+        ctx = _ctx(sfx, g, 1)
+        ctx.sfx_set_tuning(sfx._lib.SFX_TUNE_PREDICT, predict)
+        f, F = _pairs(ctx, np.zeros(g.shape)), _pairs(ctx, c.F0)
+        u = [None if v is None else dev(v, torch.float32) for v in (ux, uy, uz)]
+        phid = dev(phi)
+        o = sfx.default_opts(tol=1e-11, max_cycles=400, nu1=3, nu2=0)
+        n_it = 0
+        for _ in range(12):
+            st = ctx.sfx_surfactant_step(p, phid, f, F, c.dt, *u, opts=o)
+            assert st.converged and st.res_f <= 1e-11 and st.res_F <= 1e-11
+            n_it += st.picard
+        its.append(n_it)
+        out.append((host(ctx.sfx_df_unpack(f)), host(ctx.sfx_df_unpack(F))))
+    scale = np.abs(out[0][1]).max()
+    assert np.abs(out[0][0] - out[1][0]).max() < 1e-8 * scale
+    assert np.abs(out[0][1] - out[1][1]).max() < 1e-8 * scale
+    assert its[1] < its[0], its
+
+
 def test_fp32_mass_drift_over_many_steps(sfx):
     """Closed box, 100 steps of the 2D adsorption physics at tol 1e-10:
     the double-float state keeps sum V (f + F) to 1e-10."""
