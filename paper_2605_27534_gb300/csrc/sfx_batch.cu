@@ -93,8 +93,8 @@ __global__ void k_b_advect(const BInst* __restrict__ I, int n, const int* __rest
   const size_t c = (size_t)(blockIdx.x - pre[inst]) * blockDim.x + threadIdx.x;
   if (c >= L.ncell()) return;
   Adv32 A{L, B.dt, B.p.invh, {P.ur + B.rfoff, P.uz + B.zfoff, nullptr}};
-  P.fs[B.coff + c] = advect_cell(A, P.f + B.coff, B.bc_f, c);
-  P.Fs[B.coff + c] = advect_cell(A, P.F + B.coff, B.bc_F, c);
+  advect_cell2(A, P.f + B.coff, P.F + B.coff, B.bc_f, B.bc_F, c, P.fs[B.coff + c],
+               P.Fs[B.coff + c]);
 }
 
 // folded float copy of phi, and the start of the step

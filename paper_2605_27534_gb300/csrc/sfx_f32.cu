@@ -278,7 +278,7 @@ __global__ void k_corr32(Corr32 p, const float* __restrict__ Bx, const float* __
 // the coupled one does not.
 // Evaluate both residuals (pairs), the 2x2 exchange Jacobian and the
 // norms at every cell of the current state.
-__global__ void __launch_bounds__(256, 4)
+__global__ void __launch_bounds__(256, 5)
 k_resid2_32(Nw32 p, const float* __restrict__ phi, const float* __restrict__ Bfx,
             const float* __restrict__ Bfy, const float* __restrict__ Bfz,
             const float* __restrict__ BFx, const float* __restrict__ BFy,
@@ -308,7 +308,7 @@ k_resid2_32(Nw32 p, const float* __restrict__ phi, const float* __restrict__ Bfx
 }
 
 // One colour of the coupled red-black Gauss-Seidel on the correction.
-__global__ void k_corr2_32(Nw32 p, const float* __restrict__ Bfx, const float* __restrict__ Bfy,
+__global__ void __launch_bounds__(128, 12) k_corr2_32(Nw32 p, const float* __restrict__ Bfx, const float* __restrict__ Bfy,
                            const float* __restrict__ Bfz, const float* __restrict__ BFx,
                            const float* __restrict__ BFy, const float* __restrict__ BFz,
                            const float4* __restrict__ coef, const float2* __restrict__ res,
@@ -627,6 +627,21 @@ __global__ void k_advect32(Adv32 A, const float2* __restrict__ x, float bc_in,
   for (size_t c = blockIdx.x * (size_t)blockDim.x + threadIdx.x; c < n;
        c += (size_t)gridDim.x * blockDim.x)
     out[c] = advect_cell(A, x, bc_in, c);
+}
+
+// Both transported fields of a step in one pass.
+__global__ void __launch_bounds__(256) k_advect2_32(Adv32 A, const float2* __restrict__ f,
+                                                    const float2* __restrict__ F, float bc_f,
+                                                    float bc_F, float2* __restrict__ fo,
+                                                    float2* __restrict__ Fo) {
+  const size_t n = A.L.ncell();
+  for (size_t c = blockIdx.x * (size_t)blockDim.x + threadIdx.x; c < n;
+       c += (size_t)gridDim.x * blockDim.x) {
+    float2 a, b;
+    advect_cell2(A, f, F, bc_f, bc_F, c, a, b);
+    fo[c] = a;
+    Fo[c] = b;
+  }
 }
 
 // ------------------------------------------------------------ totals
@@ -1160,8 +1175,8 @@ sfx_status step_f32(sfx_ctx* c, const sfx_params* pr, const double* phi_in, cons
   c->f32.inc_valid = false;
   if (ux) {
     Adv32 A{L, (float)dt, (float)(1.0 / L.h), {ux, uy, uz}};
-    SFX_KERNEL(c, K_ADVECT, k_advect32, blocks_for(n, 256), 256, s, A, f, (float)pr->bc_f, fs);
-    SFX_KERNEL(c, K_ADVECT, k_advect32, blocks_for(n, 256), 256, s, A, F, (float)pr->bc_F, Fs);
+    SFX_KERNEL(c, K_ADVECT, k_advect2_32, blocks_for(n, 256), 256, s, A, f, F, (float)pr->bc_f,
+               (float)pr->bc_F, fs, Fs);
     SFX_LAUNCH_CHECK();
   } else {
     SFX_CUDA(cudaMemcpyAsync(fs, f, n * sizeof(float2), cudaMemcpyDeviceToDevice, s));

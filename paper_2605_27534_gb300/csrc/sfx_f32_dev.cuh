@@ -250,6 +250,40 @@ __device__ float face32v(const Adv32& A, const float2* __restrict__ x, float bc_
   return val;
 }
 
+// face32v for two fields at once: the upwind cell, its index and the
+// transverse velocities are shared; each field's arithmetic is that of
+// face32v.
+__device__ __forceinline__ void face32v2(const Adv32& A, const float2* __restrict__ x1,
+                                         const float2* __restrict__ x2, float bc1, float bc2,
+                                         int d, const int* f, float u, float& v1, float& v2) {
+  const Level& L = A.L;
+  int uc[3] = {f[0], f[1], f[2]};
+  if (u > 0.0f) {
+    if (f[d] == 0) { v1 = bc1; v2 = bc2; return; }
+    uc[d] -= 1;
+  } else if (f[d] == L.extent(d)) {
+    v1 = bc1;
+    v2 = bc2;
+    return;
+  }
+  const size_t U = cidx(L, uc[0], uc[1], uc[2]);
+  const float a1 = df_val(x1[U]), a2 = df_val(x2[U]);
+  const float cfl = 0.5f * ((u > 0.0f ? 1.0f : -1.0f) - u * A.dt * A.invh);
+  v1 = a1 + cfl * mc32(vnb(L, x1, uc, U, d, -1), a1, vnb(L, x1, uc, U, d, +1));
+  v2 = a2 + cfl * mc32(vnb(L, x2, uc, U, d, -1), a2, vnb(L, x2, uc, U, d, +1));
+  for (int t = 0; t < L.ndim(); ++t) {
+    if (t == d) continue;
+    int ap[3] = {uc[0], uc[1], uc[2]};
+    ap[t] += 1;
+    const float vbar = 0.5f * (A.u[t][fidx(L, t, uc[0], uc[1], uc[2])] +
+                               A.u[t][fidx(L, t, ap[0], ap[1], ap[2])]);
+    const bool up = vbar > 0.0f;
+    const float d1 = up ? a1 - vnb(L, x1, uc, U, t, -1) : vnb(L, x1, uc, U, t, +1) - a1;
+    const float d2 = up ? a2 - vnb(L, x2, uc, U, t, -1) : vnb(L, x2, uc, U, t, +1) - a2;
+    v1 -= 0.5f * A.dt * vbar * d1 * A.invh;
+    v2 -= 0.5f * A.dt * vbar * d2 * A.invh;
+  }
+}
 
 // Both residuals (pairs) of App. C at cell c of the current state, the
 // kinetic diagonals and couplings of the linearised system, and the running
@@ -410,6 +444,48 @@ __device__ __forceinline__ float2 advect_cell(const Adv32& A, const float2* __re
   float2 inc = df_mul_f(df_mul_f(S, -A.dt), A.invh);
   if (L.geom == SFX_AXISYM) inc = df_div_f(inc, wz_face(L.geom, idx[0]));
   return df_add2(x[c], inc);
+}
+
+// advect_cell for two fields sharing the face geometry (bitwise the same
+// per field).
+__device__ __forceinline__ void advect_cell2(const Adv32& A, const float2* __restrict__ x1,
+                                             const float2* __restrict__ x2, float bc1, float bc2,
+                                             size_t c, float2& o1, float2& o2) {
+  const Level& L = A.L;
+  int idx[3] = {(int)(c % L.nx), (int)((c / L.nx) % L.ny), (int)(c / ((size_t)L.nx * L.ny))};
+  float2 S1 = make_float2(0.0f, 0.0f), S2 = make_float2(0.0f, 0.0f);
+  for (int d = 0; d < L.ndim(); ++d) {
+    int pp[3] = {idx[0], idx[1], idx[2]};
+    pp[d] += 1;
+    const float um = A.u[d][fidx(L, d, idx[0], idx[1], idx[2])];
+    const float up = A.u[d][fidx(L, d, pp[0], pp[1], pp[2])];
+    const float wm = d == 0 ? wr_face(L.geom, idx[0]) : (d == 1 ? wz_face(L.geom, idx[0]) : 1.0f);
+    const float wp = d == 0 ? wr_face(L.geom, idx[0] + 1) : wm;
+    if (um != 0.0f) {
+      float v1, v2;
+      face32v2(A, x1, x2, bc1, bc2, d, idx, um, v1, v2);
+      float pr = __fmul_rn(um, v1);
+      S1 = df_sub2(S1, df_mul_f(make_float2(pr, fmaf(um, v1, -pr)), wm));
+      pr = __fmul_rn(um, v2);
+      S2 = df_sub2(S2, df_mul_f(make_float2(pr, fmaf(um, v2, -pr)), wm));
+    }
+    if (up != 0.0f) {
+      float v1, v2;
+      face32v2(A, x1, x2, bc1, bc2, d, pp, up, v1, v2);
+      float pr = __fmul_rn(up, v1);
+      S1 = df_add2(S1, df_mul_f(make_float2(pr, fmaf(up, v1, -pr)), wp));
+      pr = __fmul_rn(up, v2);
+      S2 = df_add2(S2, df_mul_f(make_float2(pr, fmaf(up, v2, -pr)), wp));
+    }
+  }
+  float2 i1 = df_mul_f(df_mul_f(S1, -A.dt), A.invh);
+  float2 i2 = df_mul_f(df_mul_f(S2, -A.dt), A.invh);
+  if (L.geom == SFX_AXISYM) {
+    i1 = df_div_f(i1, wz_face(L.geom, idx[0]));
+    i2 = df_div_f(i2, wz_face(L.geom, idx[0]));
+  }
+  o1 = df_add2(x1[c], i1);
+  o2 = df_add2(x2[c], i2);
 }
 
 }  // namespace
