@@ -278,7 +278,7 @@ __global__ void k_corr32(Corr32 p, const float* __restrict__ Bx, const float* __
 // the coupled one does not.
 // Evaluate both residuals (pairs), the 2x2 exchange Jacobian and the
 // norms at every cell of the current state.
-__global__ void __launch_bounds__(256, 5)
+__global__ void __launch_bounds__(256, 4)
 k_resid2_32(Nw32 p, const float* __restrict__ phi, const float* __restrict__ Bfx,
             const float* __restrict__ Bfy, const float* __restrict__ Bfz,
             const float* __restrict__ BFx, const float* __restrict__ BFy,

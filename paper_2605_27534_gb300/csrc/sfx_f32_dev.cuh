@@ -135,45 +135,60 @@ __device__ __forceinline__ void gather6(const Level& L, int i, int j, int k, siz
   nbi[0] = c - 1; nbi[1] = c + 1; nbi[2] = c - sy; nbi[3] = c + sy; nbi[4] = c - sz; nbi[5] = c + sz;
 }
 
+// The six face drifts of cell c = (i,j,k).  With row = k ny + j the face
+// indices are c + row (x), c + k nx (y) and c (z) on the minus side, plus
+// 1, nx and nx ny on the plus side.
 __device__ __forceinline__ void faces6(const Level& L, const float* Bx, const float* By,
                                        const float* Bz, int i, int j, int k, const bool* has,
                                        float* B) {
-  B[0] = has[0] ? Bx[fidx(L, 0, i, j, k)] : 0.0f;
-  B[1] = has[1] ? Bx[fidx(L, 0, i + 1, j, k)] : 0.0f;
-  B[2] = has[2] ? By[fidx(L, 1, i, j, k)] : 0.0f;
-  B[3] = has[3] ? By[fidx(L, 1, i, j + 1, k)] : 0.0f;
-  B[4] = has[4] ? Bz[fidx(L, 2, i, j, k)] : 0.0f;
-  B[5] = has[5] ? Bz[fidx(L, 2, i, j, k + 1)] : 0.0f;
+  const size_t c = cidx(L, i, j, k);
+  const size_t fx = c + (size_t)k * L.ny + j, fy = c + (size_t)k * L.nx;
+  B[0] = has[0] ? Bx[fx] : 0.0f;
+  B[1] = has[1] ? Bx[fx + 1] : 0.0f;
+  B[2] = has[2] ? By[fy] : 0.0f;
+  B[3] = has[3] ? By[fy + L.nx] : 0.0f;
+  B[4] = has[4] ? Bz[c] : 0.0f;
+  B[5] = has[5] ? Bz[c + (size_t)L.nx * L.ny] : 0.0f;
 }
 
 // (1/V) sum +-A G of one field around cell i as an unnormalised pair, and
 // the derivative of that sum in the cell value (negated: diagonal weight).
+// The diffusive part is gathered as Doh (sum_q w_q a_q - W a_c), W = sum_q
+// w_q, one pair product instead of one per face; the drift part as
+// sum_q +-w_q B_q a_up(q).
 __device__ __forceinline__ float2 flux_pair(const Level& L, float invh, float Doh, int literal,
                                             int i, float2 ac, const float2* nb, const bool* has,
                                             const float* B, float& dflux) {
-  Acc S{0.0f, 0.0f};
-  float dg = 0.0f;
+  const bool axi = L.geom == SFX_AXISYM;
+  Acc D{0.0f, 0.0f}, T{0.0f, 0.0f};
+  float W = 0.0f, dg = 0.0f;
 #pragma unroll
   for (int q = 0; q < 6; ++q) {
     if (!has[q]) continue;
     const bool plus = q & 1;
     const bool upL = literal ? (B[q] > 0.0f) : (B[q] < 0.0f);
     float w = 1.0f;
-    if (L.geom == SFX_AXISYM) w = q < 2 ? wr_face(L.geom, i + (plus ? 1 : 0)) : (q < 4 ? wz_face(L.geom, i) : 1.0f);
-    float2 G = plus ? face_G(Doh, B[q], upL, ac, nb[q]) : face_G(Doh, B[q], upL, nb[q], ac);
-    if (L.geom == SFX_AXISYM) G = lp_mul(G, w);
+    if (axi) w = q < 2 ? wr_face(L.geom, i + (plus ? 1 : 0)) : (q < 4 ? wz_face(L.geom, i) : 1.0f);
+    acc_add(D, axi ? lp_mul(nb[q], w) : nb[q]);
+    W += w;
+    // upwind value: the left cell when upL; this cell is left on plus faces
+    const float2 aup = (plus == upL) ? ac : nb[q];
+    float2 u = lp_mul(aup, B[q]);
+    if (axi) u = lp_mul(u, w);   // B w in float would round the drift itself
     if (plus) {
-      acc_add(S, G);
+      acc_add(T, u);
       dg += w * (Doh - (upL ? B[q] : 0.0f));
     } else {
-      acc_sub(S, G);
+      acc_sub(T, u);
       dg += w * (Doh + (upL ? 0.0f : B[q]));
     }
   }
-  const float wc = wz_face(L.geom, i);
-  float2 flux = lp_mul(acc_get(S), invh);
+  acc_sub(D, lp_mul(ac, W));
+  acc_add(T, lp_mul(acc_get(D), Doh));
+  float2 flux = lp_mul(acc_get(T), invh);
   dflux = dg * invh;
-  if (L.geom == SFX_AXISYM) {
+  if (axi) {
+    const float wc = wz_face(L.geom, i);
     flux = df_div_f(ef_fast_two_sum(flux.x, flux.y), wc);
     dflux = __fdividef(dflux, wc);
   }
