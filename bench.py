@@ -55,6 +55,8 @@ def parse():
     ap.add_argument("--tol", type=float, default=1e-10)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--sweeps", type=int, default=4,
+                    help="FP32: red-black correction sweeps per Newton iteration")
     ap.add_argument("--predict", action="store_true",
                     help="FP32: start each Newton solve from x* plus the last increment "
                          "(SFX_TUNE_PREDICT 1; no gain on the 3D workload)")
@@ -87,12 +89,12 @@ def algorithmic_bytes(kind, grid, wbytes, sweeps=3):
             return 8.0 * (2.5 + d) * N
         # coupled correction colour sweep (k_corr2_32): both corrections (all
         # cells, as neighbours: 8 B), the 2x2 coefficients and residuals of
-        # the updated half (24 B x 1/2), the 2 d float drift-face arrays of
-        # both fields, write the updated half of both corrections; the last
-        # black sweep of each iteration also reads and writes the state
-        # (32 B), averaged here over the 2 x sweeps - 1 colour launches (the
-        # residual pass does the first red half-sweep)
-        return (8.0 + 12.0 + 8.0 * d + 4.0 + 32.0 / (2 * sweeps - 1)) * N
+        # the updated half (24 B x 1/2), the d half-precision drift-face
+        # arrays of both fields (2 B each), write the updated half of both
+        # corrections; the last black sweep of each iteration also reads and
+        # writes the state (32 B), averaged here over the 2 x sweeps - 1
+        # colour launches (the residual pass does the first red half-sweep)
+        return (8.0 + 12.0 + 4.0 * d + 4.0 + 32.0 / (2 * sweeps - 1)) * N
     if kind == "residual" and wbytes == 4:
         # k_resid2_32: f, F, f*, F* (pairs), phi, 2 d float faces; writes the
         # 2x2 coefficients, the residuals and the red half of both
@@ -263,8 +265,8 @@ def run_gpu(a, case, rank, world, local_rank):
     sigma = torch.empty(g.shape, dtype=wdt, device=dev)
     force = torch.empty((3,) + g.shape, dtype=wdt, device=dev)
     opts = sfx.default_opts(tol=a.tol, max_cycles=200)
-    if prec == sfx.SFX_F32:   # three coupled correction sweeps per Newton iteration
-        opts.nu1, opts.nu2 = 3, 0
+    if prec == sfx.SFX_F32:   # coupled correction sweeps per Newton iteration
+        opts.nu1, opts.nu2 = a.sweeps, 0
         ctx.sfx_set_tuning(sfx._lib.SFX_TUNE_REUSE_DRIFT, 1)   # the interface is static
         ctx.sfx_set_tuning(sfx._lib.SFX_TUNE_PREDICT, 1 if a.predict else 0)
     stats = []
@@ -505,17 +507,17 @@ def batch_bytes(sizes, rp, sg, steps, sweeps):
     """Algorithmic bytes of `steps` batched steps (d = 2, pairs 8 B, double
     phi 8 B, its folded copy, velocities and faces 4 B).  Per instance of N
     cells and per step: folded copy of phi (12 N), drift faces (phi 8 +
-    2 fields x 2 faces x 4 = 24 N), advection of both fields (pairs in and
+    2 fields x 2 faces x (4 + 2) = 32 N), advection of both fields (pairs in and
     out 32 N, 2 velocity arrays 8 N), copy into the iterate (32 N), totals
     (16 N); per residual pass (16 + 16 + 4 + 16 + 16 + 8 + 4 = 80 N, the
     last term the red half of both corrections); per sweep group
-    2 x sweeps - 1 colour launches of (8 + 12 + 16 + 4 = 40 N) and the state
-    update (32 N)."""
+    2 x sweeps - 1 colour launches of (8 + 12 + 8 + 4 = 32 N, half-precision
+    faces) and the state update (32 N)."""
     tot = 0.0
     for (nr, nz), r, w in zip(sizes, rp, sg):
         N = nr * nz
-        tot += N * (steps * (12.0 + 24.0 + 40.0 + 32.0 + 16.0) + r * 80.0 +
-                    w * ((2 * sweeps - 1) * 40.0 + 32.0))
+        tot += N * (steps * (12.0 + 32.0 + 40.0 + 32.0 + 16.0) + r * 80.0 +
+                    w * ((2 * sweeps - 1) * 32.0 + 32.0))
     return tot
 
 

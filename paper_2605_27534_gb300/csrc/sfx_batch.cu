@@ -26,6 +26,7 @@ struct BInst {
   Nw32 p;                 // grid (axisymmetric, nx = nr, ny = nz) and coefficients
   float dt, bc_f, bc_F, Df, DF;
   size_t coff, rfoff, zfoff;    // offsets of cells, radial faces, axial faces
+  size_t poff;                  // offset of the colour-packed Newton work arrays
 };
 
 // block -> instance through a prefix table of block counts
@@ -50,6 +51,8 @@ struct BPtr {
   float2* Fs;
   float* Bf[2];           // radial, axial drift faces of the f problem
   float* BF[2];
+  __half* Hf[2];          // the same in half precision (correction sweeps)
+  __half* HF[2];
   float4* coef;
   float2* res;
   float* ef;
@@ -78,12 +81,18 @@ __global__ void k_b_drift(const BInst* __restrict__ I, int n, const int* __restr
   const int fx = L.nx + (dir == 0);
   const int i = (int)(q % fx), j = (int)(q / fx);
   const int pos = dir == 0 ? i : j;
-  if (pos == 0 || pos == L.extent(dir)) { Bf[q] = 0.0f; BF[q] = 0.0f; return; }
-  const int li = i - (dir == 0), lj = j - (dir == 1);
-  const float sL = fold_phi(phi[cidx(L, li, lj, 0)]), sR = fold_phi(phi[cidx(L, i, j, 0)]);
-  const float nL = normal_f32(L, phi, li, lj, 0, dir, B.p.inv_eps);
-  const float nR = normal_f32(L, phi, i, j, 0, dir, B.p.inv_eps);
-  drift_face(sL, sR, nL, nR, B.Df, B.DF, B.p.inv_eps, Bf[q], BF[q]);
+  float bf = 0.0f, bF = 0.0f;
+  if (pos > 0 && pos < L.extent(dir)) {
+    const int li = i - (dir == 0), lj = j - (dir == 1);
+    const float sL = fold_phi(phi[cidx(L, li, lj, 0)]), sR = fold_phi(phi[cidx(L, i, j, 0)]);
+    const float nL = normal_f32(L, phi, li, lj, 0, dir, B.p.inv_eps);
+    const float nR = normal_f32(L, phi, i, j, 0, dir, B.p.inv_eps);
+    drift_face(sL, sR, nL, nR, B.Df, B.DF, B.p.inv_eps, bf, bF);
+  }
+  Bf[q] = bf;
+  BF[q] = bF;
+  P.Hf[dir][fo + q] = __float2half_rn(bf);
+  P.HF[dir][fo + q] = __float2half_rn(bF);
 }
 
 __global__ void k_b_advect(const BInst* __restrict__ I, int n, const int* __restrict__ pre, BPtr P) {
@@ -137,9 +146,9 @@ __global__ void k_b_resid(const BInst* __restrict__ I, int n, const int* __restr
     const int i = (int)(c % L.nx), j = (int)(c / L.nx);
     const float* Bf[3] = {P.Bf[0] + B.rfoff, P.Bf[1] + B.zfoff, nullptr};
     const float* BF[3] = {P.BF[0] + B.rfoff, P.BF[1] + B.zfoff, nullptr};
-    const size_t o = B.coff;
+    const size_t o = B.coff, w = B.poff;
     resid2_cell(B.p, i, j, 0, c, P.phi32 + o, Bf, BF, P.f + o, P.F + o, P.fs + o, P.Fs + o,
-                P.coef + o, P.res + o, m, P.ef + o, P.eF + o);
+                P.coef + w, P.res + w, m, P.ef + w, P.eF + w);
   }
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
@@ -175,21 +184,23 @@ __global__ void k_b_corr(const BInst* __restrict__ I, int n, const int* __restri
   if (t >= (size_t)half * L.ny) return;
   const int j = (int)(t / half);
   const int i = 2 * (int)(t % half) + ((j + color) & 1);
-  const size_t o = B.coff;
+  const size_t o = B.coff, w = B.poff;
   float2* fst = apply ? P.f + o : nullptr;
   float2* Fst = apply ? P.F + o : nullptr;
   if (i >= L.nx) {
     const int ir = i ^ 1;
     if (apply && ir < L.nx) {
       const size_t cr = cidx(L, ir, j, 0);
-      fst[cr] = df_add(fst[cr], P.ef[o + cr]);
-      Fst[cr] = df_add(Fst[cr], P.eF[o + cr]);
+      const RBIdx rb = rb_index(L, i, j, 0);
+      const size_t pr = w + (1 - color) * rb.plane + rb.pos;   // ir's packed slot
+      fst[cr] = df_add(fst[cr], P.ef[pr]);
+      Fst[cr] = df_add(Fst[cr], P.eF[pr]);
     }
     return;
   }
-  const float* Bf[3] = {P.Bf[0] + B.rfoff, P.Bf[1] + B.zfoff, nullptr};
-  const float* BF[3] = {P.BF[0] + B.rfoff, P.BF[1] + B.zfoff, nullptr};
-  corr2_cell(B.p, i, j, 0, Bf, BF, P.coef + o, P.res + o, P.ef + o, P.eF + o, color, first, fst,
+  const __half* Bf[3] = {P.Hf[0] + B.rfoff, P.Hf[1] + B.zfoff, nullptr};
+  const __half* BF[3] = {P.HF[0] + B.rfoff, P.HF[1] + B.zfoff, nullptr};
+  corr2_cell(B.p, i, j, 0, Bf, BF, P.coef + w, P.res + w, P.ef + w, P.eF + w, color, first, fst,
              Fst);
 }
 
@@ -235,7 +246,7 @@ struct sfx_batch {
   int n = 0;
   std::vector<sfx_batch_instance> hinst;
   std::vector<BInst> hI;
-  size_t ncell = 0, nrf = 0, nzf = 0;
+  size_t ncell = 0, nrf = 0, nzf = 0, npack = 0;
   std::vector<size_t> coff, rfoff, zfoff;
   BInst* dI = nullptr;
   int* pre_cell = nullptr;   // blocks of `block` threads over cells
@@ -389,6 +400,8 @@ sfx_status sfx_batch_create(const sfx_batch_instance* inst, int n, sfx_batch** o
     B.coff = b->ncell;
     B.rfoff = b->nrf;
     B.zfoff = b->nzf;
+    B.poff = b->npack;
+    b->npack += 2 * (size_t)L.ny * ((L.nx + 1) / 2);
     b->coff.push_back(b->ncell);
     b->rfoff.push_back(b->nrf);
     b->zfoff.push_back(b->nzf);
@@ -412,10 +425,14 @@ sfx_status sfx_batch_create(const sfx_batch_instance* inst, int n, sfx_batch** o
   if (st == SFX_OK) st = balloc(b, &P.Bf[1], b->nzf);
   if (st == SFX_OK) st = balloc(b, &P.BF[0], b->nrf);
   if (st == SFX_OK) st = balloc(b, &P.BF[1], b->nzf);
-  if (st == SFX_OK) st = balloc(b, &P.coef, nc);
-  if (st == SFX_OK) st = balloc(b, &P.res, nc);
-  if (st == SFX_OK) st = balloc(b, &P.ef, nc);
-  if (st == SFX_OK) st = balloc(b, &P.eF, nc);
+  if (st == SFX_OK) st = balloc(b, &P.Hf[0], b->nrf);
+  if (st == SFX_OK) st = balloc(b, &P.Hf[1], b->nzf);
+  if (st == SFX_OK) st = balloc(b, &P.HF[0], b->nrf);
+  if (st == SFX_OK) st = balloc(b, &P.HF[1], b->nzf);
+  if (st == SFX_OK) st = balloc(b, &P.coef, b->npack);
+  if (st == SFX_OK) st = balloc(b, &P.res, b->npack);
+  if (st == SFX_OK) st = balloc(b, &P.ef, b->npack);
+  if (st == SFX_OK) st = balloc(b, &P.eF, b->npack);
   if (st == SFX_OK) st = balloc(b, &P.norms, 4 * (size_t)n);
   if (st == SFX_OK) st = balloc(b, &P.active, (size_t)n);
   if (st == SFX_OK) st = balloc(b, &P.iters, (size_t)n);

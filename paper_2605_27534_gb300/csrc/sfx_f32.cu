@@ -34,19 +34,26 @@ namespace sfx {
 namespace {
 
 __global__ void k_drift32(Level L, int d, const double* __restrict__ phi, float Df, float DF,
-                          float inv_eps, float* __restrict__ Bf, float* __restrict__ BF) {
+                          float inv_eps, float* __restrict__ Bf, float* __restrict__ BF,
+                          __half* __restrict__ Hf, __half* __restrict__ HF) {
   size_t n = L.nface(d);
   int fx = L.nx + (d == 0), fy = L.ny + (d == 1);
   for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < n;
        q += (size_t)gridDim.x * blockDim.x) {
     int i = (int)(q % fx), j = (int)((q / fx) % fy), k = (int)(q / ((size_t)fx * fy));
     int pos = d == 0 ? i : (d == 1 ? j : k);
-    if (pos == 0 || pos == L.extent(d)) { Bf[q] = 0.0f; BF[q] = 0.0f; continue; }
-    int li = i - (d == 0), lj = j - (d == 1), lk = k - (d == 2);
-    const float sL = fold_phi(phi[cidx(L, li, lj, lk)]), sR = fold_phi(phi[cidx(L, i, j, k)]);
-    const float nL = normal_f32(L, phi, li, lj, lk, d, inv_eps);
-    const float nR = normal_f32(L, phi, i, j, k, d, inv_eps);
-    drift_face(sL, sR, nL, nR, Df, DF, inv_eps, Bf[q], BF[q]);
+    float bf = 0.0f, bF = 0.0f;
+    if (pos > 0 && pos < L.extent(d)) {
+      int li = i - (d == 0), lj = j - (d == 1), lk = k - (d == 2);
+      const float sL = fold_phi(phi[cidx(L, li, lj, lk)]), sR = fold_phi(phi[cidx(L, i, j, k)]);
+      const float nL = normal_f32(L, phi, li, lj, lk, d, inv_eps);
+      const float nR = normal_f32(L, phi, i, j, k, d, inv_eps);
+      drift_face(sL, sR, nL, nR, Df, DF, inv_eps, bf, bF);
+    }
+    Bf[q] = bf;
+    BF[q] = bF;
+    Hf[q] = __float2half_rn(bf);
+    HF[q] = __float2half_rn(bF);
   }
 }
 
@@ -308,9 +315,10 @@ k_resid2_32(Nw32 p, const float* __restrict__ phi, const float* __restrict__ Bfx
 }
 
 // One colour of the coupled red-black Gauss-Seidel on the correction.
-__global__ void __launch_bounds__(128, 12) k_corr2_32(Nw32 p, const float* __restrict__ Bfx, const float* __restrict__ Bfy,
-                           const float* __restrict__ Bfz, const float* __restrict__ BFx,
-                           const float* __restrict__ BFy, const float* __restrict__ BFz,
+__global__ void __launch_bounds__(128, 10)
+k_corr2_32(Nw32 p, const __half* __restrict__ Bfx, const __half* __restrict__ Bfy,
+           const __half* __restrict__ Bfz, const __half* __restrict__ BFx,
+           const __half* __restrict__ BFy, const __half* __restrict__ BFz,
                            const float4* __restrict__ coef, const float2* __restrict__ res,
                            float* __restrict__ ef, float* __restrict__ eF, int color, int first,
                            float2* __restrict__ fst, float2* __restrict__ Fst,
@@ -319,15 +327,17 @@ __global__ void __launch_bounds__(128, 12) k_corr2_32(Nw32 p, const float* __res
   const Level& L = p.L;
   const int j = blockIdx.y, k = blockIdx.z;
   const int i = 2 * (blockIdx.x * blockDim.x + threadIdx.x) + ((j + k + color) & 1);
-  const float* Bf[3] = {Bfx, Bfy, Bfz};
-  const float* BF[3] = {BFx, BFy, BFz};
+  const __half* Bf[3] = {Bfx, Bfy, Bfz};
+  const __half* BF[3] = {BFx, BFy, BFz};
   if (i >= L.nx) {
     // a row of odd length: the last red cell has no black partner
     const int ir = i ^ 1;
     if (fst && ir < L.nx) {
       const size_t cr = cidx(L, ir, j, k);
-      fst[cr] = df_add(fst[cr], ef[cr]);
-      Fst[cr] = df_add(Fst[cr], eF[cr]);
+      const RBIdx rb = rb_index(L, i, j, k);
+      const size_t pr = (1 - color) * rb.plane + rb.pos;   // ir's packed slot
+      fst[cr] = df_add(fst[cr], ef[pr]);
+      Fst[cr] = df_add(Fst[cr], eF[pr]);
     }
     return;
   }
@@ -1068,6 +1078,8 @@ sfx_status solve_newton32(sfx_ctx* c, const Nw32& p, const float* phi, float* co
   unsigned int* dn = (unsigned int*)c->d_norms;        // two 4-slot norm buffers
   unsigned int* hn = (unsigned int*)c->h_norms;
   int* flag = c->f32.flag;
+  const __half* Hz_f = L.ndim() == 3 ? c->f32.Hf[2] : nullptr;
+  const __half* Hz_F = L.ndim() == 3 ? c->f32.HF[2] : nullptr;
   SFX_CUDA(cudaMemsetAsync(flag, 0, 2 * sizeof(int), s));
   // Each iteration: the residual pass (which also does the first red
   // half-sweep of the correction, from zero), a device-side convergence
@@ -1102,9 +1114,10 @@ sfx_status solve_newton32(sfx_ctx* c, const Nw32& p, const float* phi, float* co
     for (int q = 0; q < sweeps; ++q)
       for (int color = (q == 0 ? 1 : 0); color < 2; ++color) {
         const bool apply = q == sweeps - 1 && color == 1;
-        SFX_KERNEL(c, K_SMOOTH_FINE, k_corr2_32, grd, blk, s, p, Bf[0], Bf[1], Bf[2], BF[0], BF[1],
-                   BF[2], c->f32.coef, c->f32.res, c->f32.ef, c->f32.eF, color, q == 0 ? 1 : 0,
-                   apply ? fc : nullptr, apply ? Fc : nullptr, flag);
+        SFX_KERNEL(c, K_SMOOTH_FINE, k_corr2_32, grd, blk, s, p, c->f32.Hf[0], c->f32.Hf[1], Hz_f,
+                   c->f32.HF[0], c->f32.HF[1], Hz_F, c->f32.coef, c->f32.res, c->f32.ef,
+                   c->f32.eF, color, q == 0 ? 1 : 0, apply ? fc : nullptr, apply ? Fc : nullptr,
+                   flag);
       }
     SFX_LAUNCH_CHECK();
     const int prev = it - 1;
@@ -1155,7 +1168,8 @@ sfx_status step_f32(sfx_ctx* c, const sfx_params* pr, const double* phi_in, cons
     SFX_KERNEL(c, K_SETUP, k_fold_phi, blocks_for(n, 256), 256, s, n, phi_in, c->f32.phi32);
     for (int d = 0; d < nd; ++d)
       SFX_KERNEL(c, K_SETUP, k_drift32, blocks_for(L.nface(d), 256), 256, s, L, d, phi_in,
-                 (float)pr->Df, (float)pr->DF, (float)(1.0 / pr->eps), Bf[d], BF[d]);
+                 (float)pr->Df, (float)pr->DF, (float)(1.0 / pr->eps), Bf[d], BF[d],
+                 c->f32.Hf[d], c->f32.HF[d]);
     SFX_LAUNCH_CHECK();
     c->f32.drift_phi = phi_in;
     c->f32.drift_key[0] = pr->Df;
@@ -1369,6 +1383,8 @@ sfx_status f32_ensure_scratch(sfx_ctx* c) {
   for (int d = 0; d < L.ndim(); ++d) {
     if ((st = get(L.nface(d) * sizeof(float), (void**)&c->f32.Bf[d])) != SFX_OK) return st;
     if ((st = get(L.nface(d) * sizeof(float), (void**)&c->f32.BF[d])) != SFX_OK) return st;
+    if ((st = get(L.nface(d) * sizeof(__half), (void**)&c->f32.Hf[d])) != SFX_OK) return st;
+    if ((st = get(L.nface(d) * sizeof(__half), (void**)&c->f32.HF[d])) != SFX_OK) return st;
   }
   if ((st = get(n * sizeof(float2), (void**)&c->f32.fstar)) != SFX_OK) return st;
   if ((st = get(n * sizeof(float2), (void**)&c->f32.Fstar)) != SFX_OK) return st;
@@ -1379,11 +1395,13 @@ sfx_status f32_ensure_scratch(sfx_ctx* c) {
   if ((st = get(4 * sizeof(int), (void**)&c->f32.flag)) != SFX_OK) return st;
   if ((st = get(n * sizeof(float2), (void**)&c->f32.falt)) != SFX_OK) return st;
   if ((st = get(n * sizeof(float2), (void**)&c->f32.Falt)) != SFX_OK) return st;
+  // the Newton work arrays are colour-packed: 2 planes of ny nz ceil(nx/2)
+  const size_t np = std::max(n, 2 * (size_t)L.ny * L.nz * ((L.nx + 1) / 2));
   float** arrs[6] = {&c->f32.ef, &c->f32.eF, &c->f32.rf, &c->f32.rF, &c->f32.lf, &c->f32.lF};
   for (float** q : arrs)
-    if ((st = get(n * sizeof(float), (void**)q)) != SFX_OK) return st;
-  if ((st = get(n * sizeof(float4), (void**)&c->f32.coef)) != SFX_OK) return st;
-  if ((st = get(n * sizeof(float2), (void**)&c->f32.res)) != SFX_OK) return st;
+    if ((st = get(np * sizeof(float), (void**)q)) != SFX_OK) return st;
+  if ((st = get(np * sizeof(float4), (void**)&c->f32.coef)) != SFX_OK) return st;
+  if ((st = get(np * sizeof(float2), (void**)&c->f32.res)) != SFX_OK) return st;
   for (int q = 0; q < 2; ++q) SFX_CUDA(cudaEventCreateWithFlags(&c->f32.ev[q], cudaEventDisableTiming));
   c->f32.ready = true;
   return SFX_OK;

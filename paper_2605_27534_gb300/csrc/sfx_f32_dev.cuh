@@ -3,6 +3,8 @@
 // batched kernels so that both evaluate identical expressions.
 #pragma once
 
+#include <cuda_fp16.h>
+
 #include "sfx_common.cuh"
 #include "sfx_df.cuh"
 
@@ -135,20 +137,42 @@ __device__ __forceinline__ void gather6(const Level& L, int i, int j, int k, siz
   nbi[0] = c - 1; nbi[1] = c + 1; nbi[2] = c - sy; nbi[3] = c + sy; nbi[4] = c - sz; nbi[5] = c + sz;
 }
 
+// Colour-packed layout of the Newton work arrays (corrections, 2x2
+// coefficients, residuals): the cells of each red-black colour are stored
+// contiguously, `half` = ceil(nx/2) per row, red plane first.  A colour
+// launch then reads and writes whole cache lines, and the neighbours of a
+// cell (all of the other colour) sit at pos - 1 + (i & 1), pos + (i & 1)
+// (x), pos -+ half (y) and pos -+ ny half (z) of the other plane.
+struct RBIdx {
+  size_t plane, pos;
+  int half;
+};
+__device__ __forceinline__ RBIdx rb_index(const Level& L, int i, int j, int k) {
+  RBIdx r;
+  r.half = (L.nx + 1) >> 1;
+  r.plane = (size_t)L.ny * L.nz * r.half;
+  r.pos = ((size_t)k * L.ny + j) * r.half + (i >> 1);
+  return r;
+}
+
 // The six face drifts of cell c = (i,j,k).  With row = k ny + j the face
 // indices are c + row (x), c + k nx (y) and c (z) on the minus side, plus
 // 1, nx and nx ny on the plus side.
-__device__ __forceinline__ void faces6(const Level& L, const float* Bx, const float* By,
-                                       const float* Bz, int i, int j, int k, const bool* has,
+__device__ __forceinline__ float face_val(float b) { return b; }
+__device__ __forceinline__ float face_val(__half b) { return __half2float(b); }
+
+template <typename T>
+__device__ __forceinline__ void faces6(const Level& L, const T* Bx, const T* By,
+                                       const T* Bz, int i, int j, int k, const bool* has,
                                        float* B) {
   const size_t c = cidx(L, i, j, k);
   const size_t fx = c + (size_t)k * L.ny + j, fy = c + (size_t)k * L.nx;
-  B[0] = has[0] ? Bx[fx] : 0.0f;
-  B[1] = has[1] ? Bx[fx + 1] : 0.0f;
-  B[2] = has[2] ? By[fy] : 0.0f;
-  B[3] = has[3] ? By[fy + L.nx] : 0.0f;
-  B[4] = has[4] ? Bz[c] : 0.0f;
-  B[5] = has[5] ? Bz[c + (size_t)L.nx * L.ny] : 0.0f;
+  B[0] = has[0] ? face_val(Bx[fx]) : 0.0f;
+  B[1] = has[1] ? face_val(Bx[fx + 1]) : 0.0f;
+  B[2] = has[2] ? face_val(By[fy]) : 0.0f;
+  B[3] = has[3] ? face_val(By[fy + L.nx]) : 0.0f;
+  B[4] = has[4] ? face_val(Bz[c]) : 0.0f;
+  B[5] = has[5] ? face_val(Bz[c + (size_t)L.nx * L.ny]) : 0.0f;
 }
 
 // (1/V) sum +-A G of one field around cell i as an unnormalised pair, and
@@ -357,14 +381,16 @@ __device__ __forceinline__ void resid2_cell(const Nw32& p, int i, int j, int k, 
   // diagonals (kinetic part) and couplings of the linearised system
   const float4 cf = make_float4(p.inv_dt + p.kd + c1 * Fv, p.inv_dt + c1 * (finf - fv),
                                 c1 * (finf - fv), c1 * Fv + p.kd);
-  coef[c] = cf;
-  res[c] = make_float2(rf, rF);
+  const RBIdx rb = rb_index(L, i, j, k);
+  const size_t own = ((i + j + k) & 1) * rb.plane + rb.pos;
+  coef[own] = cf;
+  res[own] = make_float2(rf, rF);
   if (ef && ((i + j + k) & 1) == 0) {
     // [a -b; -d e] [x; y] = [r_f; r_F], diagonals with the flux weights
     const float a = cf.x + df_, bb = cf.z, d = cf.w, e = cf.y + dF_;
     const float inv = __fdividef(1.0f, a * e - bb * d);
-    ef[c] = (e * rf + bb * rF) * inv;
-    eF[c] = (d * rf + a * rF) * inv;
+    ef[own] = (e * rf + bb * rF) * inv;
+    eF[own] = (d * rf + a * rF) * inv;
   }
   m[0] = fmaxf(m[0], fabsf(rf));
   m[1] = fmaxf(m[1], fabsf(fs.x * p.inv_dt + c1 * Fv * finf));
@@ -375,9 +401,12 @@ __device__ __forceinline__ void resid2_cell(const Nw32& p, int i, int j, int k, 
 
 // One cell of the coupled red-black Gauss-Seidel on the correction; with
 // fst != NULL (the last black colour of an iteration) the corrections of
-// this cell and of its red pair partner are added to the state.
+// this cell and of its red pair partner are added to the state.  The sweeps
+// only precondition the Newton correction (the residual pass fixes the
+// solution), so they read the face drifts in half precision (relative
+// 5e-4), halving their face traffic.
 __device__ __forceinline__ void corr2_cell(const Nw32& p, int i, int j, int k,
-                                           const float* const* Bf, const float* const* BF,
+                                           const __half* const* Bf, const __half* const* BF,
                                            const float4* __restrict__ coef,
                                            const float2* __restrict__ res,
                                            float* __restrict__ ef, float* __restrict__ eF,
@@ -388,6 +417,17 @@ __device__ __forceinline__ void corr2_cell(const Nw32& p, int i, int j, int k,
   bool has[6];
   size_t nbi[6];
   gather6(L, i, j, k, c, has, nbi);
+  // the work arrays are colour-packed: own cell and the other colour's plane
+  const RBIdx rb = rb_index(L, i, j, k);
+  const size_t own = color * rb.plane + rb.pos;
+  const size_t oth = (1 - color) * rb.plane + rb.pos;
+  const size_t sz = (size_t)L.ny * rb.half;
+  nbi[0] = oth - 1 + (i & 1);
+  nbi[1] = oth + (i & 1);
+  nbi[2] = oth - rb.half;
+  nbi[3] = oth + rb.half;
+  nbi[4] = oth - sz;
+  nbi[5] = oth + sz;
   // every cell starts at zero in the first sweep
   const bool zero_nb = first && color == 0;
   float enf[6], enF[6];
@@ -396,14 +436,14 @@ __device__ __forceinline__ void corr2_cell(const Nw32& p, int i, int j, int k,
     enf[q] = (has[q] && !zero_nb) ? ef[nbi[q]] : 0.0f;
     enF[q] = (has[q] && !zero_nb) ? eF[nbi[q]] : 0.0f;
   }
-  const float efc = first ? 0.0f : ef[c], eFc = first ? 0.0f : eF[c];
+  const float efc = first ? 0.0f : ef[own], eFc = first ? 0.0f : eF[own];
   float B[6], dgf, dgF;
   faces6(L, Bf[0], Bf[1], Bf[2], i, j, k, has, B);
   const float flf = flux_lin(L, p.invh, p.Dfh, p.literal, i, efc, enf, has, B, dgf);
   faces6(L, BF[0], BF[1], BF[2], i, j, k, has, B);
   const float flF = flux_lin(L, p.invh, p.DFh, p.literal, i, eFc, enF, has, B, dgF);
-  const float4 cf = coef[c];
-  const float2 r = res[c];
+  const float4 cf = coef[own];
+  const float2 r = res[own];
   // residuals of the correction equation at this cell
   const float rhof = r.x + flf - cf.x * efc + cf.z * eFc;
   const float rhoF = r.y + flF - cf.y * eFc + cf.w * efc;
@@ -413,18 +453,19 @@ __device__ __forceinline__ void corr2_cell(const Nw32& p, int i, int j, int k,
   const float inv = __fdividef(1.0f, det);
   const float nf = efc + (e * rhof + bb * rhoF) * inv;
   const float nF = eFc + (d * rhof + a * rhoF) * inv;
-  ef[c] = nf;
-  eF[c] = nF;
+  ef[own] = nf;
+  eF[own] = nF;
   if (fst) {
     // last black colour of the iteration: add the corrections to the state,
-    // for this cell and for the red cell that shares its pair (2t, 2t+1)
+    // for this cell and for the red cell that shares its pair (2t, 2t+1),
+    // which sits at the same packed position of the other plane
     fst[c] = df_add(fst[c], nf);
     Fst[c] = df_add(Fst[c], nF);
     const int ir = i ^ 1;
     if (ir < L.nx) {
       const size_t cr = c - i + ir;
-      fst[cr] = df_add(fst[cr], ef[cr]);
-      Fst[cr] = df_add(Fst[cr], eF[cr]);
+      fst[cr] = df_add(fst[cr], ef[oth]);
+      Fst[cr] = df_add(Fst[cr], eF[oth]);
     }
   }
 }

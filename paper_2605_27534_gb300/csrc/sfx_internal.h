@@ -2,6 +2,7 @@
 // each translation unit provides.
 #pragma once
 
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 #include <string>
@@ -35,6 +36,8 @@ struct F32Scratch {
   bool ready = false;
   float* Bf[3] = {};
   float* BF[3] = {};
+  __half* Hf[3] = {};     // the same drifts in half precision (correction sweeps)
+  __half* HF[3] = {};
   float2* fstar = nullptr;
   float2* Fstar = nullptr;
   float* dsig = nullptr;   // sigma - sigma0
