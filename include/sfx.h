@@ -117,7 +117,9 @@ const char* sfx_last_cuda_error(void);
 
 /* Context for one grid shape and precision: allocates the multigrid
    pyramid and work arrays on the current CUDA device (cudaMalloc).
-   Returns SFX_ERR_ARG for a bad grid, SFX_ERR_CUDA if allocation fails. */
+   Returns SFX_ERR_ARG for a bad grid (for SFX_F32 also when a face array
+   would reach 2^31 entries: its kernels index with 32-bit integers),
+   SFX_ERR_CUDA if allocation fails. */
 sfx_status sfx_ctx_create(const sfx_grid* grid, int precision, sfx_ctx** out);
 void sfx_ctx_destroy(sfx_ctx* ctx);
 /* Fill opts with the defaults used when a call gets opts = NULL. */

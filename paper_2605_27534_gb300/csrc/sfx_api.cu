@@ -1,5 +1,6 @@
 // C-ABI of libsfx: argument checks, the context (multigrid pyramid and work
 // arrays) and dispatch to the kernels of the other translation units.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -159,6 +160,14 @@ sfx_status sfx_ctx_create(const sfx_grid* grid, int precision, sfx_ctx** out) {
   if (!out) return SFX_ERR_ARG;
   *out = nullptr;
   if (!grid_ok(grid) || (precision != SFX_F64 && precision != SFX_F32)) return SFX_ERR_ARG;
+  if (precision == SFX_F32) {
+    // the FP32 kernels index cells, faces and the colour-packed work arrays
+    // with 32-bit integers
+    const size_t nx = grid->nx, ny = grid->ny, nz = grid->nz;
+    const size_t most = std::max({(nx + 1) * ny * nz, nx * (ny + 1) * nz, nx * ny * (nz + 1),
+                                  2 * ny * nz * ((nx + 1) / 2)});
+    if (most >= ((size_t)1 << 31)) return SFX_ERR_ARG;
+  }
   sfx_ctx* c = new sfx_ctx();
   c->grid = *grid;
   c->prec = precision;

@@ -102,7 +102,8 @@ __global__ void k_b_advect(const BInst* __restrict__ I, int n, const int* __rest
   const size_t c = (size_t)(blockIdx.x - pre[inst]) * blockDim.x + threadIdx.x;
   if (c >= L.ncell()) return;
   Adv32 A{L, B.dt, B.p.invh, {P.ur + B.rfoff, P.uz + B.zfoff, nullptr}};
-  advect_cell2(A, P.f + B.coff, P.F + B.coff, B.bc_f, B.bc_F, c, P.fs[B.coff + c],
+  const int i = (int)((ix)c % (ix)L.nx), j = (int)((ix)c / (ix)L.nx);
+  advect_cell2(A, P.f + B.coff, P.F + B.coff, B.bc_f, B.bc_F, i, j, 0, (ix)c, P.fs[B.coff + c],
                P.Fs[B.coff + c]);
 }
 
@@ -143,7 +144,7 @@ __global__ void k_b_resid(const BInst* __restrict__ I, int n, const int* __restr
   const size_t c = (size_t)(blockIdx.x - pre[inst]) * blockDim.x + threadIdx.x;
   float m[4] = {0.0f, 0.0f, 0.0f, 0.0f};
   if (c < L.ncell()) {
-    const int i = (int)(c % L.nx), j = (int)(c / L.nx);
+    const int i = (int)((ix)c % (ix)L.nx), j = (int)((ix)c / (ix)L.nx);
     const float* Bf[3] = {P.Bf[0] + B.rfoff, P.Bf[1] + B.zfoff, nullptr};
     const float* BF[3] = {P.BF[0] + B.rfoff, P.BF[1] + B.zfoff, nullptr};
     const size_t o = B.coff, w = B.poff;
@@ -213,7 +214,7 @@ __global__ void k_b_totals(const BInst* __restrict__ I, BPtr P) {
   float2 acc = make_float2(0.0f, 0.0f);
   for (size_t c = threadIdx.x; c < L.ncell(); c += blockDim.x) {
     float2 v = x[c];
-    const float w = 2.0f * (float)(c % L.nx) + 1.0f;   // ring volume / (pi h^3)
+    const float w = 2.0f * (float)((ix)c % (ix)L.nx) + 1.0f;   // ring volume / (pi h^3)
     const float pr = v.x * w;
     v = make_float2(pr, fmaf(v.x, w, -pr) + v.y * w);
     acc = df_add2(acc, v);
@@ -412,6 +413,11 @@ sfx_status sfx_batch_create(const sfx_batch_instance* inst, int n, sfx_batch** o
   }
   sfx_status st = SFX_OK;
   const size_t nc = b->ncell;
+  // the FP32 kernels index cells and faces with 32-bit integers
+  if (std::max(std::max(nc, b->npack), std::max(b->nrf, b->nzf)) >= ((size_t)1 << 31)) {
+    delete b;
+    return SFX_ERR_ARG;
+  }
   BPtr& P = b->P;
   if (st == SFX_OK) st = balloc(b, &b->dI, (size_t)n);
   if (st == SFX_OK) st = balloc(b, &b->pre_cell, (size_t)n + 1);

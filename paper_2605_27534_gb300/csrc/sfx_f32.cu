@@ -296,20 +296,31 @@ k_resid2_32(Nw32 p, const float* __restrict__ phi, const float* __restrict__ Bfx
             float* __restrict__ eF, const int* __restrict__ done) {
   if (done && *done) return;   // converged at an earlier iteration
   const Level& L = p.L;
-  const size_t n = L.ncell();
   float m[4] = {0.0f, 0.0f, 0.0f, 0.0f};
   const float* Bf[3] = {Bfx, Bfy, Bfz};
   const float* BF[3] = {BFx, BFy, BFz};
-  for (size_t c = blockIdx.x * (size_t)blockDim.x + threadIdx.x; c < n;
-       c += (size_t)gridDim.x * blockDim.x) {
-    const int i = (int)(c % L.nx), j = (int)((c / L.nx) % L.ny), k = (int)(c / ((size_t)L.nx * L.ny));
-    resid2_cell(p, i, j, k, c, phi, Bf, BF, fin, Fin, fst, Fst, coef, res, m, ef, eF);
+  // blocks over (x chunk, rows); each block walks rows r = k ny + j
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const ix rows = (ix)L.ny * (ix)L.nz;
+  for (ix r = blockIdx.y; r < rows; r += gridDim.y) {
+    const int j = (int)(r % (ix)L.ny), k = (int)(r / (ix)L.ny);
+    if (i < L.nx)
+      resid2_cell(p, i, j, k, r * (ix)L.nx + (ix)i, phi, Bf, BF, fin, Fin, fst, Fst, coef, res, m,
+                  ef, eF);
   }
   if (norms) {
+    // warp maxima, then one atomic per block and norm
+    __shared__ float wm[4][8];
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
-      float v = warp_max(m[q]);
-      if ((threadIdx.x & 31) == 0) atomicMax(&norms[q], fbits(v));
+      const float v = warp_max(m[q]);
+      if ((threadIdx.x & 31) == 0) wm[q][threadIdx.x >> 5] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < 4) {
+      float v = 0.0f;
+      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) v = fmaxf(v, wm[threadIdx.x][w]);
+      atomicMax(&norms[threadIdx.x], fbits(v));
     }
   }
 }
@@ -644,11 +655,15 @@ __global__ void __launch_bounds__(256) k_advect2_32(Adv32 A, const float2* __res
                                                     const float2* __restrict__ F, float bc_f,
                                                     float bc_F, float2* __restrict__ fo,
                                                     float2* __restrict__ Fo) {
-  const size_t n = A.L.ncell();
-  for (size_t c = blockIdx.x * (size_t)blockDim.x + threadIdx.x; c < n;
-       c += (size_t)gridDim.x * blockDim.x) {
+  const Level& L = A.L;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= L.nx) return;
+  const ix rows = (ix)L.ny * (ix)L.nz;
+  for (ix r = blockIdx.y; r < rows; r += gridDim.y) {
+    const int j = (int)(r % (ix)L.ny), k = (int)(r / (ix)L.ny);
+    const ix c = r * (ix)L.nx + (ix)i;
     float2 a, b;
-    advect_cell2(A, f, F, bc_f, bc_F, c, a, b);
+    advect_cell2(A, f, F, bc_f, bc_F, i, j, k, c, a, b);
     fo[c] = a;
     Fo[c] = b;
   }
@@ -1064,6 +1079,22 @@ __global__ void k_increment32(size_t n, const float2* __restrict__ fs,
   }
 }
 
+// Launch shape of the row-walking kernels: x chunks of up to 256 threads
+// (a multiple of 32) and enough row groups for ~8 blocks per SM.
+struct RowGrid {
+  dim3 grid, block;
+};
+RowGrid row_grid(const Level& L) {
+  RowGrid g;
+  const int tx = L.nx >= 256 ? 256 : ((L.nx + 31) / 32) * 32;
+  const int xb = (L.nx + tx - 1) / tx;
+  const long long rows = (long long)L.ny * L.nz;
+  const long long want = std::max(1LL, (152LL * 8) / xb);
+  g.block = dim3(tx);
+  g.grid = dim3(xb, (unsigned)std::min(rows, std::min(want, 65535LL)));
+  return g;
+}
+
 // Coupled Newton defect correction (see k_resid2_32).
 sfx_status solve_newton32(sfx_ctx* c, const Nw32& p, const float* phi, float* const* Bf,
                           float* const* BF, float2*& fc, float2*& fo, float2*& Fc, float2*& Fo,
@@ -1078,6 +1109,7 @@ sfx_status solve_newton32(sfx_ctx* c, const Nw32& p, const float* phi, float* co
   unsigned int* dn = (unsigned int*)c->d_norms;        // two 4-slot norm buffers
   unsigned int* hn = (unsigned int*)c->h_norms;
   int* flag = c->f32.flag;
+  const RowGrid rg = row_grid(L);
   const __half* Hz_f = L.ndim() == 3 ? c->f32.Hf[2] : nullptr;
   const __half* Hz_F = L.ndim() == 3 ? c->f32.HF[2] : nullptr;
   SFX_CUDA(cudaMemsetAsync(flag, 0, 2 * sizeof(int), s));
@@ -1094,7 +1126,7 @@ sfx_status solve_newton32(sfx_ctx* c, const Nw32& p, const float* phi, float* co
   for (it = 1; it <= o->max_cycles; ++it) {
     unsigned int* nbuf = dn + 4 * (it & 1);
     SFX_CUDA(cudaMemsetAsync(nbuf, 0, 4 * sizeof(unsigned int), s));
-    SFX_KERNEL(c, K_RESIDUAL, k_resid2_32, nb, 256, s, p, phi, Bf[0], Bf[1], Bf[2], BF[0], BF[1],
+    SFX_KERNEL(c, K_RESIDUAL, k_resid2_32, rg.grid, rg.block, s, p, phi, Bf[0], Bf[1], Bf[2], BF[0], BF[1],
                BF[2], fc, Fc, fs, Fs, c->f32.coef, c->f32.res, nbuf, c->f32.ef, c->f32.eF, flag);
     if (it == 1 && predicted) {
       // keep the predicted start only if its residual is already small;
@@ -1103,7 +1135,7 @@ sfx_status solve_newton32(sfx_ctx* c, const Nw32& p, const float* phi, float* co
       const float rho = c->f32.predict_rho;
       SFX_KERNEL(c, K_OTHER, k_pred_check32, 1, 32, s, nbuf, rho, ok);
       SFX_KERNEL(c, K_SETUP, k_restore32, nb, 256, s, n, ok, fs, Fs, fc, Fc);
-      SFX_KERNEL(c, K_RESIDUAL, k_resid2_32, nb, 256, s, p, phi, Bf[0], Bf[1], Bf[2], BF[0],
+      SFX_KERNEL(c, K_RESIDUAL, k_resid2_32, rg.grid, rg.block, s, p, phi, Bf[0], Bf[1], Bf[2], BF[0],
                  BF[1], BF[2], fc, Fc, fs, Fs, c->f32.coef, c->f32.res, nbuf, c->f32.ef, c->f32.eF,
                  ok);
     }
@@ -1189,7 +1221,8 @@ sfx_status step_f32(sfx_ctx* c, const sfx_params* pr, const double* phi_in, cons
   c->f32.inc_valid = false;
   if (ux) {
     Adv32 A{L, (float)dt, (float)(1.0 / L.h), {ux, uy, uz}};
-    SFX_KERNEL(c, K_ADVECT, k_advect2_32, blocks_for(n, 256), 256, s, A, f, F, (float)pr->bc_f,
+    const RowGrid ag = row_grid(L);
+    SFX_KERNEL(c, K_ADVECT, k_advect2_32, ag.grid, ag.block, s, A, f, F, (float)pr->bc_f,
                (float)pr->bc_F, fs, Fs);
     SFX_LAUNCH_CHECK();
   } else {

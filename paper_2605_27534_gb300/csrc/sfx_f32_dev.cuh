@@ -129,9 +129,17 @@ struct Nw32 {
   int literal;
 };
 
-__device__ __forceinline__ void gather6(const Level& L, int i, int j, int k, size_t c,
-                                        bool* has, size_t* nbi) {
-  const size_t sy = (size_t)L.nx, sz = (size_t)L.nx * L.ny;
+// Cell and face indices of the FP32 kernels are 32-bit: an SFX_F32 context
+// refuses grids whose cells or faces reach 2^31 (sfx_ctx_create).
+using ix = unsigned int;
+
+__device__ __forceinline__ ix cidx32(const Level& L, int i, int j, int k) {
+  return ((ix)k * (ix)L.ny + (ix)j) * (ix)L.nx + (ix)i;
+}
+
+__device__ __forceinline__ void gather6(const Level& L, int i, int j, int k, ix c,
+                                        bool* has, ix* nbi) {
+  const ix sy = (ix)L.nx, sz = (ix)L.nx * (ix)L.ny;
   has[0] = i > 0; has[1] = i + 1 < L.nx; has[2] = j > 0; has[3] = j + 1 < L.ny;
   has[4] = L.geom == SFX_CART3D && k > 0; has[5] = L.geom == SFX_CART3D && k + 1 < L.nz;
   nbi[0] = c - 1; nbi[1] = c + 1; nbi[2] = c - sy; nbi[3] = c + sy; nbi[4] = c - sz; nbi[5] = c + sz;
@@ -144,14 +152,13 @@ __device__ __forceinline__ void gather6(const Level& L, int i, int j, int k, siz
 // cell (all of the other colour) sit at pos - 1 + (i & 1), pos + (i & 1)
 // (x), pos -+ half (y) and pos -+ ny half (z) of the other plane.
 struct RBIdx {
-  size_t plane, pos;
-  int half;
+  ix plane, pos, half;
 };
 __device__ __forceinline__ RBIdx rb_index(const Level& L, int i, int j, int k) {
   RBIdx r;
-  r.half = (L.nx + 1) >> 1;
-  r.plane = (size_t)L.ny * L.nz * r.half;
-  r.pos = ((size_t)k * L.ny + j) * r.half + (i >> 1);
+  r.half = (ix)((L.nx + 1) >> 1);
+  r.plane = (ix)L.ny * (ix)L.nz * r.half;
+  r.pos = ((ix)k * (ix)L.ny + (ix)j) * r.half + (ix)(i >> 1);
   return r;
 }
 
@@ -165,14 +172,14 @@ template <typename T>
 __device__ __forceinline__ void faces6(const Level& L, const T* Bx, const T* By,
                                        const T* Bz, int i, int j, int k, const bool* has,
                                        float* B) {
-  const size_t c = cidx(L, i, j, k);
-  const size_t fx = c + (size_t)k * L.ny + j, fy = c + (size_t)k * L.nx;
+  const ix c = cidx32(L, i, j, k);
+  const ix fx = c + (ix)k * (ix)L.ny + (ix)j, fy = c + (ix)k * (ix)L.nx;
   B[0] = has[0] ? face_val(Bx[fx]) : 0.0f;
   B[1] = has[1] ? face_val(Bx[fx + 1]) : 0.0f;
   B[2] = has[2] ? face_val(By[fy]) : 0.0f;
   B[3] = has[3] ? face_val(By[fy + L.nx]) : 0.0f;
   B[4] = has[4] ? face_val(Bz[c]) : 0.0f;
-  B[5] = has[5] ? face_val(Bz[c + (size_t)L.nx * L.ny]) : 0.0f;
+  B[5] = has[5] ? face_val(Bz[c + (ix)L.nx * (ix)L.ny]) : 0.0f;
 }
 
 // (1/V) sum +-A G of one field around cell i as an unnormalised pair, and
@@ -330,7 +337,7 @@ __device__ __forceinline__ void face32v2(const Adv32& A, const float2* __restric
 // half-sweep of the correction is done here: it starts from zero
 // corrections, so a red cell (i + j + k even) only needs its own 2x2 block,
 // e = M_c^-1 r_c.
-__device__ __forceinline__ void resid2_cell(const Nw32& p, int i, int j, int k, size_t c,
+__device__ __forceinline__ void resid2_cell(const Nw32& p, int i, int j, int k, ix c,
                                             const float* __restrict__ phi,
                                             const float* const* Bf, const float* const* BF,
                                             const float2* __restrict__ fin,
@@ -342,7 +349,7 @@ __device__ __forceinline__ void resid2_cell(const Nw32& p, int i, int j, int k, 
                                             float* __restrict__ eF) {
   const Level& L = p.L;
   bool has[6];
-  size_t nbi[6];
+  ix nbi[6];
   gather6(L, i, j, k, c, has, nbi);
   float2 nb[6];
   const float2 fc = fin[c], Fc = Fin[c];
@@ -382,7 +389,7 @@ __device__ __forceinline__ void resid2_cell(const Nw32& p, int i, int j, int k, 
   const float4 cf = make_float4(p.inv_dt + p.kd + c1 * Fv, p.inv_dt + c1 * (finf - fv),
                                 c1 * (finf - fv), c1 * Fv + p.kd);
   const RBIdx rb = rb_index(L, i, j, k);
-  const size_t own = ((i + j + k) & 1) * rb.plane + rb.pos;
+  const ix own = (ix)((i + j + k) & 1) * rb.plane + rb.pos;
   coef[own] = cf;
   res[own] = make_float2(rf, rF);
   if (ef && ((i + j + k) & 1) == 0) {
@@ -413,15 +420,15 @@ __device__ __forceinline__ void corr2_cell(const Nw32& p, int i, int j, int k,
                                            int color, int first, float2* __restrict__ fst,
                                            float2* __restrict__ Fst) {
   const Level& L = p.L;
-  const size_t c = cidx(L, i, j, k);
+  const ix c = cidx32(L, i, j, k);
   bool has[6];
-  size_t nbi[6];
+  ix nbi[6];
   gather6(L, i, j, k, c, has, nbi);
   // the work arrays are colour-packed: own cell and the other colour's plane
   const RBIdx rb = rb_index(L, i, j, k);
-  const size_t own = color * rb.plane + rb.pos;
-  const size_t oth = (1 - color) * rb.plane + rb.pos;
-  const size_t sz = (size_t)L.ny * rb.half;
+  const ix own = (ix)color * rb.plane + rb.pos;
+  const ix oth = (ix)(1 - color) * rb.plane + rb.pos;
+  const ix sz = (ix)L.ny * rb.half;
   nbi[0] = oth - 1 + (i & 1);
   nbi[1] = oth + (i & 1);
   nbi[2] = oth - rb.half;
@@ -463,7 +470,7 @@ __device__ __forceinline__ void corr2_cell(const Nw32& p, int i, int j, int k,
     Fst[c] = df_add(Fst[c], nF);
     const int ir = i ^ 1;
     if (ir < L.nx) {
-      const size_t cr = c - i + ir;
+      const ix cr = c - (ix)i + (ix)ir;
       fst[cr] = df_add(fst[cr], ef[oth]);
       Fst[cr] = df_add(Fst[cr], eF[oth]);
     }
@@ -506,9 +513,10 @@ __device__ __forceinline__ float2 advect_cell(const Adv32& A, const float2* __re
 // per field).
 __device__ __forceinline__ void advect_cell2(const Adv32& A, const float2* __restrict__ x1,
                                              const float2* __restrict__ x2, float bc1, float bc2,
-                                             size_t c, float2& o1, float2& o2) {
+                                             int i, int j, int k, ix c, float2& o1,
+                                             float2& o2) {
   const Level& L = A.L;
-  int idx[3] = {(int)(c % L.nx), (int)((c / L.nx) % L.ny), (int)(c / ((size_t)L.nx * L.ny))};
+  int idx[3] = {i, j, k};
   float2 S1 = make_float2(0.0f, 0.0f), S2 = make_float2(0.0f, 0.0f);
   for (int d = 0; d < L.ndim(); ++d) {
     int pp[3] = {idx[0], idx[1], idx[2]};
