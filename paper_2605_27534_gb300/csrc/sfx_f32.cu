@@ -5,23 +5,28 @@
 // residual is evaluated in pair arithmetic (FP32 instructions only) from
 // FP32 coefficients, so the discrete operator is the FP64 one with its
 // coefficients rounded to float (solution within ~1e-7), while residuals
-// resolve ~1e-14 and every face flux is bitwise the same for both cells that
-// share the face (totals conserved to pair precision).  The update
-// a += r/diag adds a float increment to the pair.
-// Carrier.  phi is stored folded (phi if phi <= 1/2, phi - 1 otherwise) so
-// phi and 1 - phi both keep full relative precision.
+// resolve ~1e-14 and the face terms cancel between the two cells of a face
+// (totals conserved to pair precision).
+// Phase field.  The caller passes the double phi.  The drift faces take
+// the normal from FP64 differences of it (sfx_f32_dev.cuh, normal_f32); the
+// per-iteration kernels read a float copy folded about 1/2 (phi if
+// phi <= 1/2, phi - 1 otherwise) so that phi and 1 - phi both keep full
+// relative precision.
 //
-// Solver.  The App. C system is relaxed by nonlinear red-black Gauss-Seidel
-// sweeps on the pair state: each cell takes the local Newton (here exact,
-// the equations being linear in the unknown for fixed neighbours and fixed
-// other field) update  a_c += r_c / diag_c  with
+// Solvers of the App. C system (SFX_TUNE_F32_SOLVER), with
 //   r_f = (f* - f)/dt + div G_f + q,   r_F = (F* - F)/dt + div G_F - q,
-//   q = r_a F/(phi+eta) (f_inf - f) - r_d f      (App. C, L1414),
-//   G = D (a_R - a_L)/h + B a_up,  a_up upwinded on -B (Sec. 3.2 reading),
-// alternating f sweeps and F sweeps (Picard).  Each colour launch records
-// the residual of every cell it updates, taken just before the update, so
-// the largest such residual bounds the change made by the sweep; the step
-// stops when that bound is below tol |b| for both fields.
+//   q = r_a F/(phi+eta) (f_inf - f) - r_d f      (App. C),
+//   G = D (a_R - a_L)/h + B a_up,  a_up upwinded on -B (Sec. 3.2 reading):
+//  1 (default) coupled Newton defect correction: a pair residual pass also
+//    forms the pointwise 2x2 exchange Jacobian; FP32 red-black sweeps with a
+//    2x2 solve per cell relax the correction (their face drifts in half
+//    precision, their work arrays colour-packed) and the last black colour
+//    adds it to the state.  The convergence test runs on the device and
+//    stops every later launch of the solve; the host reads it one iteration
+//    late without draining the stream.
+//  2 the same with the two fields linearised alternately (Picard).
+//  0 nonlinear red-black Gauss-Seidel on the pair state, f and F sweeps in
+//    turn, each cell taking a_c += r_c/diag_c.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
