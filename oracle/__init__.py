@@ -79,6 +79,7 @@ def lib():
         L.orc_elliptic_solve.argtypes = [G, C.c_double, _P, _P, _P, C.c_int, _P, _P, _P,
                                          C.c_double, C.c_int, _P]
         L.orc_advect_bcg.argtypes = [G, _P, _P, _P, C.c_double, _P, C.c_double, _P]
+        L.orc_vof_advect.argtypes = [G, _P, _P, _P, C.c_double, C.c_int, _P]
         L.orc_coupled_implicit.argtypes = [G, Pp, _P, _P, _P, C.c_double, C.POINTER(Opts),
                                            _P, _P, C.POINTER(Stats)]
         L.orc_surfactant_step.argtypes = [G, Pp, _P, _P, _P, _P, C.c_double,
@@ -201,6 +202,15 @@ def advect_bcg(g, ux, uy, uz, dt, xi, bc_in):
     uzp = _arr(uz) if g.ndim == 3 else np.zeros(1)
     lib().orc_advect_bcg(C.byref(cgrid(g)), _ptr(_arr(ux)), _ptr(_arr(uy)), _ptr(uzp),
                          float(dt), _ptr(_arr(xi)), float(bc_in), _ptr(out))
+    return out
+
+
+def vof_advect(g, ux, uy, uz, dt, Cf, order=0):
+    """One split PLIC step of the volume fraction (returns a new array)."""
+    out = np.array(Cf, dtype=np.float64, copy=True)
+    uzp = _arr(uz) if g.ndim == 3 else np.zeros(1)
+    lib().orc_vof_advect(C.byref(cgrid(g)), _ptr(_arr(ux)), _ptr(_arr(uy)), _ptr(uzp),
+                         float(dt), int(order), _ptr(out))
     return out
 
 

@@ -107,6 +107,12 @@ void orc_advect_bcg(const orc_grid* g, const double* ux, const double* uy,
                     const double* uz, double dt, const double* xi,
                     double bc_in, double* xi_star);
 
+/* a3': one step of directionally split conservative PLIC advection of the
+   volume fraction C (in place), direction order 0 (x, y, z) or 1
+   (reversed); planar 2D and 3D grids. */
+void orc_vof_advect(const orc_grid* g, const double* ux, const double* uy,
+                    const double* uz, double dt, int order, double* C);
+
 /* a4: coupled implicit source step of App. C for (f, F), Picard on the
    two elliptic problems.  fstar/Fstar are the post-advection fields; f and F
    are overwritten with the new state. */
