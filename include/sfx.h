@@ -155,6 +155,21 @@ sfx_status sfx_mg_solve(sfx_ctx* ctx, double D, const double* Bx,
                         const sfx_solve_opts* opts, int* cycles_out,
                         double* res_out, void* stream);
 
+/* a3'.  Geometric VoF advection of the volume fraction C (Sec. 2 tracks
+   the interface with a geometric VoF method; the scheme is read as
+   directionally split conservative PLIC advection): for each direction in
+   turn (order 0: x, y, z; 1: reversed, alternate between steps), with face
+   Courant numbers c_f = u_f dt/h,
+     C <- C - (Q_+ - Q_-) + H (c_+ - c_-),
+   Q_f the fluid of the upwind cell's PLIC reconstruction (Youngs normal)
+   within |c_f| h of the face and H = [C > 1/2] at the start of the step.
+   Conserves sum C exactly for divergence-free velocities; bounded for
+   |c_f| <= 1/2.  Walls carry no flux.  C: double, in place; velocities in
+   the context precision.  Planar 2D and 3D (SFX_ERR_ARG for axisymmetric
+   grids).  The context allocates two scratch arrays on first use. */
+sfx_status sfx_vof_advect(sfx_ctx* ctx, const void* ux, const void* uy, const void* uz,
+                          double dt, int order, double* C, void* stream);
+
 /* a2 + a3 + a4 + a5 + a6.  One coupled surfactant step (Sec. 3.1 splitting;
    App. C source): explicit BCG advection of f and F when ux != NULL, then
    the fully implicit f/F system of App. C solved by Picard iteration, each

@@ -111,6 +111,11 @@ class Context:
         _check(lib().sfx_advect(self._h, _ptr(ux), _ptr(uy), _ptr(uz), float(dt), _ptr(xi),
                                 float(bc_in), _ptr(xi_out), _stream()), "sfx_advect")
 
+    def sfx_vof_advect(self, ux, uy, uz, dt, Cf, order=0):
+        """One split PLIC step of the volume fraction Cf (double, in place)."""
+        _check(lib().sfx_vof_advect(self._h, _ptr(ux), _ptr(uy), _ptr(uz), float(dt), int(order),
+                                    _ptr(Cf), _stream()), "sfx_vof_advect")
+
     def sfx_mg_solve(self, D, Bx, By, Bz, lam, b, a, opts=None, literal_upwind=0):
         o = opts if opts is not None else default_opts()
         cyc, res = C.c_int(0), C.c_double(0)

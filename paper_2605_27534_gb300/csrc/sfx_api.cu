@@ -268,6 +268,14 @@ sfx_status sfx_marangoni_force(sfx_ctx* c, const sfx_params* params, const void*
                    (double*)force, S(stream));
 }
 
+sfx_status sfx_vof_advect(sfx_ctx* c, const void* ux, const void* uy, const void* uz, double dt,
+                          int order, double* C, void* stream) {
+  if (!c || !ux || !uy || !C || !(dt > 0.0) || !std::isfinite(dt)) return SFX_ERR_ARG;
+  if (c->grid.geom == SFX_AXISYM) return SFX_ERR_ARG;
+  if (c->grid.geom == SFX_CART3D && !uz) return SFX_ERR_ARG;
+  return vof_advect(c, ux, uy, uz, dt, order ? 1 : 0, C, S(stream));
+}
+
 sfx_status sfx_f_from_gamma(sfx_ctx* c, const double* gamma, const double* phi, double eps,
                             double* f, void* stream) {
   if (!c || !gamma || !phi || !f || !(eps > 0.0)) return SFX_ERR_ARG;

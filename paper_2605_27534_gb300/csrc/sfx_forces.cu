@@ -5,6 +5,7 @@
 
 #include "sfx_internal.h"
 #include "sfx_op64.cuh"
+#include "sfx_plic.cuh"
 
 namespace sfx {
 namespace {
@@ -108,86 +109,6 @@ __device__ __forceinline__ double eos_slope(const EosArgs& q, double G) {
   if (q.eos == SFX_EOS_LINEAR) return -q.sigma0 * q.E / q.ginf;
   const double t = tanh(q.E * x);
   return -q.sigma0 * q.E / q.ginf * (1.0 - t * t);
-}
-
-// ------------------------------------------------------------- PLIC area
-// Fraction of the unit cube below the plane m.x = a (m >= 0, sum m = 1;
-// Scardovelli & Zaleski 2000) and its slope dV/da.  The cubic is expanded
-// per region so that near-zero components cost no precision; V(a) =
-// 1 - V(1 - a) folds a into [0, 1/2].  `q` holds the components in
-// ascending order (q[0] = 0 in 2D).
-struct VolSlope {
-  double v, dv;
-};
-
-__device__ VolSlope plic_lower_half(const double* q, bool three_d, double a) {
-  VolSlope r{0.0, 0.0};
-  if (a <= 0.0) return r;
-  if (!three_d) {
-    const double lo = q[1], hi = q[2];
-    if (a < lo) {
-      r.v = 0.5 * a * a / (lo * hi);
-      r.dv = a / (lo * hi);
-    } else {
-      r.v = (a - 0.5 * lo) / hi;
-      r.dv = 1.0 / hi;
-    }
-    return r;
-  }
-  const double p = q[0], s = q[1], t = q[2];
-  const double inv_st = 1.0 / (s * t);
-  if (a < p) {
-    r.v = a * a * a * inv_st / (6.0 * p);
-    r.dv = 0.5 * a * a * inv_st / p;
-  } else if (a < s) {
-    r.v = 0.5 * (a * (a - p) + p * p / 3.0) * inv_st;
-    r.dv = (a - 0.5 * p) * inv_st;
-  } else if (t >= p + s) {
-    if (a < p + s) {
-      double u = a - s;
-      r.v = (a * a - a * p + p * p / 3.0) * 0.5 * inv_st - u * u * u * inv_st / (6.0 * p);
-      r.dv = (a - 0.5 * p) * inv_st - 0.5 * u * u * inv_st / p;
-    } else {
-      r.v = (a - 0.5 * (p + s)) / t;
-      r.dv = 1.0 / t;
-    }
-  } else {
-    double u = a - s, w = fmax(a - t, 0.0);
-    r.v = (a * a - a * p + p * p / 3.0) * 0.5 * inv_st - (u * u * u + w * w * w) * inv_st / (6.0 * p);
-    r.dv = (a - 0.5 * p) * inv_st - 0.5 * (u * u + w * w) * inv_st / p;
-  }
-  return r;
-}
-
-__device__ VolSlope plic_volume(const double* q, bool three_d, double a) {
-  if (a <= 0.0) return VolSlope{0.0, 0.0};
-  if (a >= 1.0) return VolSlope{1.0, 0.0};
-  if (a <= 0.5) return plic_lower_half(q, three_d, a);
-  VolSlope r = plic_lower_half(q, three_d, 1.0 - a);
-  r.v = 1.0 - r.v;
-  return r;
-}
-
-// Interface area inside the unit cell holding fraction C with normal m.
-__device__ double plic_unit_area(int nd, const double* mraw, double C) {
-  if (!(C > 0.0 && C < 1.0)) return 0.0;
-  double s = 0.0, q2 = 0.0;
-  for (int d = 0; d < nd; ++d) { s += fabs(mraw[d]); q2 += mraw[d] * mraw[d]; }
-  if (s == 0.0) return 0.0;
-  double q[3] = {0.0, fabs(mraw[0]) / s, fabs(mraw[1]) / s};
-  if (nd == 3) q[0] = fabs(mraw[2]) / s;
-  // ascending order
-  if (q[0] > q[1]) { double t = q[0]; q[0] = q[1]; q[1] = t; }
-  if (q[1] > q[2]) { double t = q[1]; q[1] = q[2]; q[2] = t; }
-  if (q[0] > q[1]) { double t = q[0]; q[0] = q[1]; q[1] = t; }
-  const bool three_d = nd == 3;
-  double lo = 0.0, hi = 1.0;
-  for (int it = 0; it < 64; ++it) {
-    double mid = 0.5 * (lo + hi);
-    if (plic_volume(q, three_d, mid).v < C) lo = mid;
-    else hi = mid;
-  }
-  return (sqrt(q2) / s) * plic_volume(q, three_d, 0.5 * (lo + hi)).dv;
 }
 
 template <typename P>

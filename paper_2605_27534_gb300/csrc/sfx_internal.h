@@ -120,6 +120,8 @@ struct sfx_ctx {
   sfx::Prof prof;
   sfx::F32Scratch f32;
   sfx::AdjScratch adj;
+  double* vofH = nullptr;            // VoF: indicator H, face fluxes Q
+  double* vofQ = nullptr;
 };
 
 namespace sfx {
@@ -161,6 +163,9 @@ sfx_status surfactant_step(sfx_ctx* c, const sfx_params* p, const void* phi, con
 // sfx_solver.cu: drift faces of both problems from a double phi
 sfx_status drift_faces64(sfx_ctx* c, const double* phi, double Df, double DF, double eps,
                          double* const* Bf, double* const* BF, cudaStream_t s);
+// sfx_vof.cu
+sfx_status vof_advect(sfx_ctx* c, const void* ux, const void* uy, const void* uz, double dt,
+                      int order, double* C, cudaStream_t s);
 // sfx_adjoint.cu
 sfx_status adj_ensure_scratch(sfx_ctx* c);
 sfx_status f_from_gamma(sfx_ctx* c, const double* gamma, const double* phi, double eps,
