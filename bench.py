@@ -19,6 +19,7 @@ from __future__ import annotations
 
 import argparse
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -43,7 +44,10 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="sfx", choices=["sfx", "reference"])
-    ap.add_argument("--workload", default="hr3d", choices=["hr3d", "batch64"])
+    ap.add_argument("--workload", default="hr3d", choices=["hr3d", "batch64", "vortex512"])
+    ap.add_argument("--vortex-steps", type=int, default=100,
+                    help="steps of the 512^2 moving-interface vortex timed beside the line "
+                         "(0: skip)")
     ap.add_argument("--precision", default="f32", choices=["f64", "f32"])
     ap.add_argument("--f64-steps", type=int, default=3,
                     help="steps of the FP64 path timed beside the FP32 line (0: skip)")
@@ -214,6 +218,41 @@ def run_reference(a, case, rank):
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
                          "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+def run_gpu_vortex(a, rank, world, local_rank):
+    """The 512^2 moving-interface vortex as the line itself (FP32 context;
+    the FP64 path beside it).  The working set (~40 MB) is L2-resident, so
+    no HBM roofline is claimed for it."""
+    import torch
+    import paper_2605_27534_gb300 as sfx
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    r32 = vortex_run(a, dev, a.steps, sfx.SFX_F32, warmup=a.warmup)
+    r64 = vortex_run(a, dev, max(1, a.steps // 10), sfx.SFX_F64, warmup=1)
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([r32["ms_per_step"]], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        r32["ms_per_step"] = float(t.item())
+    if rank != 0:
+        return
+    ms = r32["ms_per_step"]
+    print(json.dumps({
+        "metric": METRIC, "value": r32["cells"] * world / (ms * 1e-3), "unit": UNIT,
+        "n_gpus": world, "steps": a.steps, "warmup": a.warmup, "ms_per_step": ms,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": "vortex512: 2D single vortex 512^2, T=4, soluble (Bi=Da=1), "
+                               "geometric VoF + phase-field rebuild + coupled step + Marangoni, "
+                               "tol=%g" % a.tol,
+                   "cells": r32["cells"], "l2": "working set L2-resident (no HBM claim)",
+                   "parallelism": "replicas%d" % world},
+        "roofline": None, "cpu_baseline": None, "e2e": None, "f64_path": r64,
+        "kernels_one_step_ms": r32["one_step_kernel_ms"],
+        "newton_iters": r32["newton_or_picard_iters"],
+        "speedup_vs_f64": r64["ms_per_step"] / ms, "gpu_launches": None,
     }))
 
 
@@ -389,6 +428,10 @@ def run_gpu(a, case, rank, world, local_rank):
     adj = None
     if a.adjoint_steps > 0:
         adj = adjoint_summary(a, dev)
+    vortex = None
+    if a.vortex_steps > 0:
+        vortex = {"f32": vortex_run(a, dev, a.vortex_steps, sfx.SFX_F32),
+                  "f64": vortex_run(a, dev, max(1, a.vortex_steps // 10), sfx.SFX_F64)}
     batch = None
     if a.batch_steps > 0:
         batch = run_gpu_batch(a, rank, 1, local_rank, steps=a.batch_steps, summary=True)
@@ -414,7 +457,77 @@ def run_gpu(a, case, rank, world, local_rank):
         line["batch64"] = batch
     if adj is not None:
         line["adjoint2d_256"] = adj
+    if vortex is not None:
+        line["vortex512"] = vortex
     print(json.dumps(line))
+
+
+def vortex_run(a, dev, steps, prec, warmup=3):
+    """The 2D moving-interface workload: 512^2 single vortex (T = 4) with
+    the soluble surfactant (Bi = Da = 1), from t = 0.  One step = geometric
+    VoF advection of C, the phase-field rebuild from C, the coupled step
+    with the same velocity, EOS and Marangoni force.  The face velocities
+    are cos(pi t/T) times the t = 0 field (the stream function factorises),
+    scaled on the device before each step (input preparation)."""
+    import torch
+    import paper_2605_27534_gb300 as sfx
+    c = W.case_vortex_2d(n=512, soluble=True)
+    g, p = c.grid, c.params
+    T = c.extra["T"]
+    f32 = prec == sfx.SFX_F32
+    vt = torch.float32 if f32 else torch.float64
+    ctx = sfx.Context.for_grid(g, prec)
+    u0 = [torch.from_numpy(u).to(dev, vt) for u in W.single_vortex_faces(512, g.h, 0.0, T)]
+    u = [torch.empty_like(x) for x in u0]
+    Cd = torch.from_numpy(c.C).to(dev)
+    chi, phi, delta = torch.empty_like(Cd), torch.empty_like(Cd), torch.empty_like(Cd)
+    ctx.sfx_phase_field_build(Cd, chi, phi, delta, iters=c.redist_iters, dtau=c.dtau, eps=p.eps)
+    F = torch.from_numpy(c.F0).to(dev)
+    f = torch.zeros_like(F)
+    if f32:
+        f, F = ctx.sfx_df_pack(f), ctx.sfx_df_pack(F)
+    Cw = Cd.to(vt)
+    sig = torch.empty(g.shape, dtype=vt, device=dev)
+    force = torch.empty((2,) + g.shape, dtype=vt, device=dev)
+    opts = sfx.default_opts(tol=a.tol, max_cycles=200)
+    if f32:
+        opts.nu1, opts.nu2 = a.sweeps, 0
+    pic = []
+
+    def step(n):
+        t = (n + 0.5) * c.dt
+        for x, x0 in zip(u, u0):
+            torch.mul(x0, math.cos(math.pi * t / T), out=x)
+        ctx.sfx_vof_advect(u[0], u[1], None, c.dt, Cd, n % 2)
+        ctx.sfx_phase_field_build(Cd, chi, phi, None, iters=c.redist_iters, dtau=c.dtau,
+                                  eps=p.eps)
+        st = ctx.sfx_surfactant_step(p, phi, f, F, c.dt, u[0], u[1], None, opts=opts)
+        if f32:
+            Cw.copy_(Cd)
+        ctx.sfx_marangoni_force(p, f, phi, Cw if f32 else Cd, sig, force, dm_mode=1)
+        pic.append(st.picard)
+
+    for n in range(warmup):
+        step(n)
+    stream = torch.cuda.current_stream()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for n in range(warmup, warmup + steps):
+        step(n)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    # where the time goes: one more step with the library's event brackets
+    ctx.sfx_profile(True)
+    step(warmup + steps)
+    torch.cuda.synchronize()
+    ctx.sfx_profile(False)
+    kinds = {k: round(v[1], 4) for k, v in ctx.sfx_profile_read().items() if v[0]}
+    return {"ms_per_step": ms, "value": g.ncell / (ms * 1e-3), "unit": UNIT, "steps": steps,
+            "cells": g.ncell, "newton_or_picard_iters": statistics.mean(pic[-steps:]),
+            "dt": c.dt, "dtype": "f32" if f32 else "f64", "one_step_kernel_ms": kinds,
+            "mass_C": float(Cd.sum().item()) * g.h * g.h}
 
 
 def adjoint_summary(a, dev):
@@ -699,6 +812,8 @@ def main():
         dist.init_process_group("nccl")
     if a.workload == "batch64":
         run_gpu_batch(a, rank, world, local_rank)
+    elif a.workload == "vortex512":
+        run_gpu_vortex(a, rank, world, local_rank)
     else:
         run_gpu(a, case, rank, world, local_rank)
     if world > 1:

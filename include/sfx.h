@@ -130,7 +130,9 @@ void sfx_default_opts(sfx_solve_opts* opts);
    redistancing d chi/d tau + sign(chi0)(|grad chi| - 1) = 0 (first-order
    Godunov with the Russo-Smereka sub-cell fix) at pseudo-time step dtau,
    then phi = (1 - tanh(chi/(2 eps)))/2 and delta = phi (1 - phi)/eps.
-   C, chi, phi, delta: double, in both precisions.  delta may be NULL. */
+   C, chi, phi, delta: double, in both precisions; SFX_F32 contexts iterate
+   the redistancing in FP32 (chi within ~1e-7 h of the FP64 iterate).
+   delta may be NULL. */
 sfx_status sfx_phase_field_build(sfx_ctx* ctx, const double* C, double* chi,
                                  void* phi, void* delta, int iters,
                                  double dtau, double eps, void* stream);

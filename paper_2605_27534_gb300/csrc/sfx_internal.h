@@ -120,6 +120,7 @@ struct sfx_ctx {
   sfx::Prof prof;
   sfx::F32Scratch f32;
   sfx::AdjScratch adj;
+  float* chi32 = nullptr;            // SFX_F32 redistancing: chi0, two iterates
   double* vofH = nullptr;            // VoF: indicator H, face fluxes Q
   double* vofQ = nullptr;
 };

@@ -9,6 +9,7 @@
 //   in cells whose chi0 changes sign against a face neighbour (the
 //   Russo-Smereka sub-cell fix)  chi <- chi - (dtau/h)(s |chi| - d)
 //     with d = h chi0 / |Delta chi0| the distance estimated from chi0 alone.
+#include <algorithm>
 #include <cmath>
 
 #include "sfx_internal.h"
@@ -26,52 +27,78 @@ __global__ void k_chi0(size_t n, double h, const double* __restrict__ C, double*
   }
 }
 
-__global__ void k_redistance_step(Level L, double dtau, const double* __restrict__ chi0,
-                                  const double* __restrict__ cin, double* __restrict__ cout) {
-  const size_t n = L.ncell();
+template <typename T> __device__ __forceinline__ T tiny_pos();
+template <> __device__ __forceinline__ double tiny_pos<double>() { return 1e-300; }
+template <> __device__ __forceinline__ float tiny_pos<float>() { return 1e-30f; }
+
+// One Jacobi step; blocks cover (x chunk, rows) and walk rows r = k ny + j.
+template <typename T>
+__global__ void k_redistance_step(Level L, T dtau, const T* __restrict__ chi0,
+                                  const T* __restrict__ cin, T* __restrict__ cout) {
   const int nd = L.ndim();
-  const double h = L.h;
-  for (size_t c = blockIdx.x * (size_t)blockDim.x + threadIdx.x; c < n;
-       c += (size_t)gridDim.x * blockDim.x) {
-    int idx[3] = {(int)(c % L.nx), (int)((c / L.nx) % L.ny), (int)(c / ((size_t)L.nx * L.ny))};
-    const double s0 = chi0[c];
-    const double sg = s0 > 0.0 ? 1.0 : (s0 < 0.0 ? -1.0 : 0.0);
-    const double x0 = cin[c];
-    // neighbour offsets along each direction (0 outside: mirrored wall)
-    size_t stride[3] = {1, (size_t)L.nx, (size_t)L.nx * L.ny};
+  const T h = (T)L.h, invh = (T)(1.0 / L.h), dtau_h = dtau / h;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= L.nx) return;
+  const unsigned rows = (unsigned)L.ny * (unsigned)L.nz;
+  const unsigned stride[3] = {1u, (unsigned)L.nx, (unsigned)L.nx * (unsigned)L.ny};
+  for (unsigned r = blockIdx.y; r < rows; r += gridDim.y) {
+    const int idx[3] = {i, (int)(r % (unsigned)L.ny), (int)(r / (unsigned)L.ny)};
+    const unsigned c = r * (unsigned)L.nx + (unsigned)i;
+    const T s0 = chi0[c];
+    const T sg = s0 > (T)0 ? (T)1 : (s0 < (T)0 ? (T)-1 : (T)0);
+    const T x0 = cin[c];
+    // neighbour offsets along each direction (the cell itself at a wall)
     bool cut = false;
-    double gsum = 0.0, dsum = 0.0;
+    T gsum = 0, dsum = 0;
     for (int d = 0; d < nd; ++d) {
-      bool hasm = idx[d] > 0, hasp = idx[d] + 1 < L.extent(d);
-      size_t cm = hasm ? c - stride[d] : c, cp = hasp ? c + stride[d] : c;
-      double z0m = chi0[cm], z0p = chi0[cp];
-      if ((hasm && s0 * z0m < 0.0) || (hasp && s0 * z0p < 0.0)) cut = true;
+      const bool hasm = idx[d] > 0, hasp = idx[d] + 1 < L.extent(d);
+      const unsigned cm = hasm ? c - stride[d] : c, cp = hasp ? c + stride[d] : c;
+      const T z0m = chi0[cm], z0p = chi0[cp];
+      if ((hasm && s0 * z0m < (T)0) || (hasp && s0 * z0p < (T)0)) cut = true;
       // sub-cell estimate of |grad chi0| h along d
-      double q = fabs(z0p - z0m) * 0.5;
+      T q = fabs(z0p - z0m) * (T)0.5;
       q = fmax(q, fabs(z0p - s0));
       q = fmax(q, fabs(s0 - z0m));
       dsum += q * q;
       // Godunov upwind gradient of the current iterate
-      double bwd = (x0 - cin[cm]) / h, fwd = (cin[cp] - x0) / h;
-      double t;
-      if (sg > 0.0) {
-        double ap = fmax(bwd, 0.0), bm = fmin(fwd, 0.0);
+      const T bwd = (x0 - cin[cm]) * invh, fwd = (cin[cp] - x0) * invh;
+      T t;
+      if (sg > (T)0) {
+        const T ap = fmax(bwd, (T)0), bm = fmin(fwd, (T)0);
         t = fmax(ap * ap, bm * bm);
       } else {
-        double am = fmin(bwd, 0.0), bp = fmax(fwd, 0.0);
+        const T am = fmin(bwd, (T)0), bp = fmax(fwd, (T)0);
         t = fmax(am * am, bp * bp);
       }
       gsum += t;
     }
-    double v;
+    T v;
     if (cut) {
-      double dchi = fmax(sqrt(dsum), 1e-300);
-      v = x0 - (dtau / h) * (sg * fabs(x0) - h * s0 / dchi);
+      const T dchi = fmax(sqrt(dsum), (T)tiny_pos<T>());
+      v = x0 - dtau_h * (sg * fabs(x0) - h * s0 / dchi);
     } else {
-      v = x0 - dtau * sg * (sqrt(gsum) - 1.0);
+      v = x0 - dtau * sg * (sqrt(gsum) - (T)1);
     }
     cout[c] = v;
   }
+}
+
+// SFX_F32 contexts iterate the redistancing in FP32 (their solution depends
+// on phi only to ~1e-8 through it): chi0 and the float iterate.
+__global__ void k_chi0_32(size_t n, double h, const double* __restrict__ C,
+                          float* __restrict__ chi0, float* __restrict__ chi) {
+  for (size_t c = blockIdx.x * (size_t)blockDim.x + threadIdx.x; c < n;
+       c += (size_t)gridDim.x * blockDim.x) {
+    const float v = (float)(2.0 * h * (C[c] - 0.5));
+    chi0[c] = v;
+    chi[c] = v;
+  }
+}
+
+__global__ void k_widen(size_t n, const float* __restrict__ x, double* __restrict__ y) {
+  for (size_t c = blockIdx.x * (size_t)blockDim.x + threadIdx.x; c < n;
+       c += (size_t)gridDim.x * blockDim.x)
+    y[c] = (double)x[c];
 }
 
 __global__ void k_phi_delta64(size_t n, double eps, const double* __restrict__ chi,
@@ -91,19 +118,44 @@ sfx_status phase_field_build(sfx_ctx* c, const double* C, double* chi, void* phi
   const Level& L = c->lev[0].lv;
   const size_t n = L.ncell();
   const int nb = blocks_for(n, 256);
-  SFX_KERNEL(c, K_PHASE, k_chi0, nb, 256, s, n, L.h, C, c->chi0, chi);
-  SFX_LAUNCH_CHECK();
-  double* a = chi;
-  double* b = c->chi_tmp;
-  for (int it = 0; it < iters; ++it) {
-    SFX_KERNEL(c, K_PHASE, k_redistance_step, nb, 256, s, L, dtau, c->chi0, a, b);
-    double* t = a;
-    a = b;
-    b = t;
+  const int tx = L.nx >= 256 ? 256 : ((L.nx + 31) / 32) * 32;
+  const unsigned xb = (unsigned)((L.nx + tx - 1) / tx);
+  const long long rows = (long long)L.ny * L.nz;
+  const unsigned yb = (unsigned)std::min(rows, std::min(std::max(1LL, 152LL * 8 / xb), 65535LL));
+  if (c->prec == SFX_F32) {
+    if (!c->chi32) {
+      SFX_CUDA(cudaMalloc((void**)&c->chi32, 3 * n * sizeof(float)));
+      c->allocations.push_back(c->chi32);
+    }
+    float* z0 = c->chi32;
+    float* a = c->chi32 + n;
+    float* b = c->chi32 + 2 * n;
+    SFX_KERNEL(c, K_PHASE, k_chi0_32, nb, 256, s, n, L.h, C, z0, a);
+    for (int it = 0; it < iters; ++it) {
+      SFX_KERNEL(c, K_PHASE, k_redistance_step<float>, dim3(xb, yb), dim3(tx), s, L, (float)dtau,
+                 z0, a, b);
+      float* t = a;
+      a = b;
+      b = t;
+    }
+    SFX_KERNEL(c, K_PHASE, k_widen, nb, 256, s, n, a, chi);
+    SFX_LAUNCH_CHECK();
+  } else {
+    SFX_KERNEL(c, K_PHASE, k_chi0, nb, 256, s, n, L.h, C, c->chi0, chi);
+    SFX_LAUNCH_CHECK();
+    double* a = chi;
+    double* b = c->chi_tmp;
+    for (int it = 0; it < iters; ++it) {
+      SFX_KERNEL(c, K_PHASE, k_redistance_step<double>, dim3(xb, yb), dim3(tx), s, L, dtau,
+                 c->chi0, a, b);
+      double* t = a;
+      a = b;
+      b = t;
+    }
+    SFX_LAUNCH_CHECK();
+    if (a != chi)
+      SFX_CUDA(cudaMemcpyAsync(chi, a, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
   }
-  SFX_LAUNCH_CHECK();
-  if (a != chi)
-    SFX_CUDA(cudaMemcpyAsync(chi, a, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
   SFX_KERNEL(c, K_PHASE, k_phi_delta64, nb, 256, s, n, eps, chi, (double*)phi, (double*)delta);
   SFX_LAUNCH_CHECK();
   return SFX_OK;

@@ -21,18 +21,21 @@ __global__ void k_vof_indicator(size_t n, const double* __restrict__ C, double* 
     H[c] = C[c] > 0.5 ? 1.0 : 0.0;
 }
 
-// Volume fractions crossing the faces of direction d.
+// Volume fractions crossing the faces of direction d; blocks cover
+// (x chunk, rows of faces) and walk the rows.
 template <typename U>
 __global__ void k_vof_flux(Level L, int d, const double* __restrict__ C,
-                           const U* __restrict__ u, double dt, double* __restrict__ Q) {
-  const size_t nf = L.nface(d);
-  const int fx = L.nx + (d == 0), fy = L.ny + (d == 1);
+                           const U* __restrict__ u, double dt_h, double* __restrict__ Q) {
+  const int fx = L.nx + (d == 0), fy = L.ny + (d == 1), fz = L.nz + (d == 2);
   const int nd = L.ndim();
-  for (size_t f = blockIdx.x * (size_t)blockDim.x + threadIdx.x; f < nf;
-       f += (size_t)gridDim.x * blockDim.x) {
-    const int i = (int)(f % fx), j = (int)((f / fx) % fy), k = (int)(f / ((size_t)fx * fy));
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= fx) return;
+  const unsigned rows = (unsigned)fy * (unsigned)fz;
+  for (unsigned r = blockIdx.y; r < rows; r += gridDim.y) {
+    const int j = (int)(r % (unsigned)fy), k = (int)(r / (unsigned)fy);
+    const unsigned f = r * (unsigned)fx + (unsigned)i;
     const int pos = d == 0 ? i : (d == 1 ? j : k);
-    const double cf = (double)u[f] * dt / L.h;
+    const double cf = (double)u[f] * dt_h;
     if (pos == 0 || pos == L.extent(d) || cf == 0.0) {
       Q[f] = 0.0;
       continue;
@@ -41,27 +44,37 @@ __global__ void k_vof_flux(Level L, int d, const double* __restrict__ C,
     const int ui = (cf > 0.0 && d == 0) ? i - 1 : i;
     const int uj = (cf > 0.0 && d == 1) ? j - 1 : j;
     const int uk = (cf > 0.0 && d == 2) ? k - 1 : k;
-    double m[3];
-    youngs_normal(L, C, ui, uj, uk, m);
     const double cu = C[cidx(L, ui, uj, uk)];
+    double m[3] = {0.0, 0.0, 0.0};
+    if (cu > 0.0 && cu < 1.0) youngs_normal(L, C, ui, uj, uk, m);   // empty/full: no plane
     Q[f] = cf > 0.0 ? plic_slab(nd, m, cu, d, 1.0 - cf, 1.0)
                     : -plic_slab(nd, m, cu, d, 0.0, -cf);
   }
 }
 
 template <typename U>
-__global__ void k_vof_update(Level L, int d, const U* __restrict__ u, double dt,
+__global__ void k_vof_update(Level L, int d, const U* __restrict__ u, double dt_h,
                              const double* __restrict__ Q, const double* __restrict__ H,
                              double* __restrict__ C) {
-  const size_t n = L.ncell();
-  for (size_t c = blockIdx.x * (size_t)blockDim.x + threadIdx.x; c < n;
-       c += (size_t)gridDim.x * blockDim.x) {
-    const int i = (int)(c % L.nx), j = (int)((c / L.nx) % L.ny), k = (int)(c / ((size_t)L.nx * L.ny));
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= L.nx) return;
+  const unsigned rows = (unsigned)L.ny * (unsigned)L.nz;
+  for (unsigned r = blockIdx.y; r < rows; r += gridDim.y) {
+    const int j = (int)(r % (unsigned)L.ny), k = (int)(r / (unsigned)L.ny);
+    const unsigned c = r * (unsigned)L.nx + (unsigned)i;
     const size_t fm = fidx(L, d, i, j, k);
     const size_t fp = fidx(L, d, i + (d == 0), j + (d == 1), k + (d == 2));
-    const double cm = (double)u[fm] * dt / L.h, cp = (double)u[fp] * dt / L.h;
+    const double cm = (double)u[fm] * dt_h, cp = (double)u[fp] * dt_h;
     C[c] = C[c] - (Q[fp] - Q[fm]) + H[c] * (cp - cm);
   }
+}
+
+// (x chunks of up to 256 threads, row groups) for an x extent and a row count
+void rows_launch(int nxl, long long rows, dim3& grid, dim3& block) {
+  const int tx = nxl >= 256 ? 256 : ((nxl + 31) / 32) * 32;
+  const unsigned xb = (unsigned)((nxl + tx - 1) / tx);
+  block = dim3(tx);
+  grid = dim3(xb, (unsigned)std::min(rows, std::min(std::max(1LL, 152LL * 8 / xb), 65535LL)));
 }
 
 template <typename U>
@@ -70,13 +83,16 @@ sfx_status vof_impl(sfx_ctx* c, const U* const* u, double dt, int order, double*
   const Level& L = c->lev[0].lv;
   const size_t n = L.ncell();
   const int nd = L.ndim();
+  const double dt_h = dt / L.h;
   SFX_KERNEL(c, K_OTHER, k_vof_indicator, blocks_for(n, 256), 256, s, n, C, c->vofH);
+  dim3 gc, bc;
+  rows_launch(L.nx, (long long)L.ny * L.nz, gc, bc);
   for (int q = 0; q < nd; ++q) {
     const int d = order ? nd - 1 - q : q;
-    SFX_KERNEL(c, K_OTHER, (k_vof_flux<U>), blocks_for(L.nface(d), 128), 128, s, L, d, C, u[d],
-               dt, c->vofQ);
-    SFX_KERNEL(c, K_OTHER, (k_vof_update<U>), blocks_for(n, 256), 256, s, L, d, u[d], dt,
-               c->vofQ, c->vofH, C);
+    dim3 gf, bf;
+    rows_launch(L.nx + (d == 0), (long long)(L.ny + (d == 1)) * (L.nz + (d == 2)), gf, bf);
+    SFX_KERNEL(c, K_OTHER, (k_vof_flux<U>), gf, bf, s, L, d, C, u[d], dt_h, c->vofQ);
+    SFX_KERNEL(c, K_OTHER, (k_vof_update<U>), gc, bc, s, L, d, u[d], dt_h, c->vofQ, c->vofH, C);
   }
   SFX_LAUNCH_CHECK();
   return SFX_OK;

@@ -75,11 +75,12 @@ def test_phase_field_build_parity(sfx, geom):
     assert rel_err(host(chi), chi_o) < PARITY
     assert rel_err(host(phi), phi_o) < PARITY
     assert rel_err(host(dl), del_o) < PARITY
-    # SFX_F32 contexts build the same double phase field
+    # SFX_F32 contexts iterate the redistancing in FP32
     ctx32 = _ctx(sfx, g, 1)
-    phi32 = torch.empty_like(Cd)
-    ctx32.sfx_phase_field_build(Cd, chi, phi32, None, iters=24, dtau=dtau, eps=eps)
-    assert torch.equal(phi32, phi)
+    phi32, chi32 = torch.empty_like(Cd), torch.empty_like(Cd)
+    ctx32.sfx_phase_field_build(Cd, chi32, phi32, None, iters=24, dtau=dtau, eps=eps)
+    assert rel_err(host(chi32), chi_o) < 1e-6      # float iterate
+    assert np.abs(host(phi32) - phi_o).max() < 5e-6
 
 
 def _random_problem(g, seed, scale=2.0):
