@@ -616,21 +616,22 @@ def f64_path(a, case, dev, f32_f, f32_F, f32_phi, ux, uy, uz):
 BATCH_N, BATCH_SEED = 64, 3
 
 
-def batch_bytes(sizes, rp, sg, steps, sweeps):
+def batch_bytes(sizes, rp, sg, steps, sweeps, static_phi=True):
     """Algorithmic bytes of `steps` batched steps (d = 2, pairs 8 B, double
     phi 8 B, its folded copy, velocities and faces 4 B).  Per instance of N
     cells and per step: folded copy of phi (12 N), drift faces (phi 8 +
     2 fields x 2 faces x (4 + 2) = 32 N), advection of both fields (pairs in and
     out 32 N, 2 velocity arrays 8 N), copy into the iterate (32 N), totals
-    (16 N); per residual pass (16 + 16 + 4 + 16 + 16 + 8 + 4 = 80 N, the
+    (16 N) (the folded phi and the drifts are left out when phi is static:
+    they are built once, outside the step); per residual pass (16 + 16 + 4 + 16 + 16 + 8 + 4 = 80 N, the
     last term the red half of both corrections); per sweep group
     2 x sweeps - 1 colour launches of (8 + 12 + 8 + 4 = 32 N, half-precision
     faces) and the state update (32 N)."""
     tot = 0.0
     for (nr, nz), r, w in zip(sizes, rp, sg):
         N = nr * nz
-        tot += N * (steps * (12.0 + 32.0 + 40.0 + 32.0 + 16.0) + r * 80.0 +
-                    w * ((2 * sweeps - 1) * 32.0 + 32.0))
+        per_step = (0.0 if static_phi else 12.0 + 32.0) + 40.0 + 32.0 + 16.0
+        tot += N * (steps * per_step + r * 80.0 + w * ((2 * sweeps - 1) * 32.0 + 32.0))
     return tot
 
 
@@ -672,6 +673,7 @@ def run_gpu_batch(a, rank, world, local_rank, steps=None, summary=False):
     sizes = [(i[0], i[1]) for i in inst]
     ncell = sum(nr * nz for nr, nz in sizes)
     B = sfx.Batch(inst)
+    B.sfx_batch_reuse_phi(True)        # the interfaces are static
     ones = torch.ones(ncell, dtype=torch.float64, device=dev)
     f = sfx.sfx_df_pack(torch.zeros_like(ones))
     F = sfx.sfx_df_pack(ones)
@@ -719,9 +721,9 @@ def run_gpu_batch(a, rank, world, local_rank, steps=None, summary=False):
     iters_mean = float(np.mean(np.array(rp) / steps))
     conv = all(st["converged"])
     sched = {"block": block, "sweeps": sweeps, "iteration_budget": budget}
-    # init, fold, 2 drift, advect, copy; per iteration residual, flags and
-    # the colour sweeps; totals
-    launches_per_step = 6 + budget * (1 + 2 * sweeps) + 1
+    # init, advect, copy (phi static: no fold or drifts); per iteration
+    # residual, flags and the 2 sweeps - 1 colour sweeps; totals and final
+    launches_per_step = 3 + budget * (1 + 2 * sweeps) + 2
     if summary:
         return {"value": value, "unit": UNIT, "ms_per_step": ms / steps, "steps": steps,
                 "cells": ncell, "instances": len(inst), "roofline_frac": roof["frac"],

@@ -371,6 +371,12 @@ sfx_status sfx_batch_set_schedule(sfx_batch* b, int block, int sweeps, int max_i
    place.  Enqueued on stream; returns without waiting. */
 sfx_status sfx_batch_step(sfx_batch* b, const void* phi, const void* ur, const void* uz,
                           void* f, void* F, double tol, void* stream);
+/* on != 0: phi is static (a fixed interface).  Its folded copy and the
+   drift faces are then built once, outside the step graph, on the next
+   step and whenever the phi pointer changes; after writing phi in place,
+   call again to force a rebuild.  on = 0 (default): every step rebuilds
+   them inside the graph. */
+sfx_status sfx_batch_reuse_phi(sfx_batch* b, int on);
 /* Per-instance results of the last step (host arrays of n, any may be
    NULL): Newton iterations, final relative residuals, compensated totals
    sum V f and sum V F (FP64) and whether the tolerance was met.  Waits for

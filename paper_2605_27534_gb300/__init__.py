@@ -267,6 +267,10 @@ class Batch:
         _check(lib().sfx_batch_set_schedule(self._h, int(block), int(sweeps), int(max_iters)),
                "sfx_batch_set_schedule")
 
+    def sfx_batch_reuse_phi(self, on=True):
+        """Static phi: fold and drift faces outside the step graph."""
+        _check(lib().sfx_batch_reuse_phi(self._h, 1 if on else 0), "sfx_batch_reuse_phi")
+
     def sfx_batch_step(self, phi, f, F, tol, ur=None, uz=None):
         _check(lib().sfx_batch_step(self._h, _ptr(phi), _ptr(ur), _ptr(uz), _ptr(f), _ptr(F),
                                     float(tol), _stream()), "sfx_batch_step")

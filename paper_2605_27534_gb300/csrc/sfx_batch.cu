@@ -63,6 +63,8 @@ struct BPtr {
   float* rres;            // 2 per instance: last relative residuals
   double* mass;           // 2 per instance
   unsigned long long* work;   // 2 per instance: residual passes, sweep groups
+  float* part;            // per cell block: the 4 residual maxima
+  double* tpart;          // per cell block: (s, c) compensated sums of f and F
 };
 
 // drift faces: blocks over radial faces then axial faces of every instance
@@ -151,26 +153,48 @@ __global__ void k_b_resid(const BInst* __restrict__ I, int n, const int* __restr
     resid2_cell(B.p, i, j, 0, c, P.phi32 + o, Bf, BF, P.f + o, P.F + o, P.fs + o, P.Fs + o,
                 P.coef + w, P.res + w, m, P.ef + w, P.eF + w);
   }
+  // block maxima; the flags kernel combines the blocks of each instance
+  __shared__ float wm[4][16];
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
-    float v = warp_max(m[q]);
-    if ((threadIdx.x & 31) == 0) atomicMax(&P.norms[4 * inst + q], __float_as_uint(v));
+    const float v = warp_max(m[q]);
+    if ((threadIdx.x & 31) == 0) wm[q][threadIdx.x >> 5] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < 4) {
+    float v = 0.0f;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) v = fmaxf(v, wm[threadIdx.x][w]);
+    P.part[4 * (size_t)blockIdx.x + threadIdx.x] = v;
   }
 }
 
-// convergence test of iteration `it` for every instance still active
-__global__ void k_b_flags(int n, BPtr P, float tol, int it) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+// convergence test of iteration `it`: one block per instance still active
+// combines the residual maxima of the instance's blocks
+__global__ void k_b_flags(int n, const int* __restrict__ pre, BPtr P, float tol, int it) {
+  const int i = blockIdx.x;
   if (i >= n || !P.active[i]) return;
-  const float rf = __uint_as_float(P.norms[4 * i]), bf = __uint_as_float(P.norms[4 * i + 1]);
-  const float rF = __uint_as_float(P.norms[4 * i + 2]), bF = __uint_as_float(P.norms[4 * i + 3]);
+  float mx[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+  for (int b = pre[i] + threadIdx.x; b < pre[i + 1]; b += blockDim.x)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) mx[q] = fmaxf(mx[q], P.part[4 * (size_t)b + q]);
+  __shared__ float wm[4][8];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    mx[q] = warp_max(mx[q]);
+    if ((threadIdx.x & 31) == 0) wm[q][threadIdx.x >> 5] = mx[q];
+  }
+  __syncthreads();
+  if (threadIdx.x != 0) return;
+  for (int w = 1; w < (int)(blockDim.x >> 5); ++w)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) mx[q] = fmaxf(mx[q], wm[q][w]);
+  const float rf = mx[0], bf = mx[1], rF = mx[2], bF = mx[3];
   P.rres[2 * i] = rf / fmaxf(bf, 1e-30f);
   P.rres[2 * i + 1] = rF / fmaxf(bF, 1e-30f);
   P.iters[i] = it;
   P.work[2 * i] += 1;
   if (rf <= tol * bf && rF <= tol * bF) P.active[i] = 0;   // converged: stop here
   else P.work[2 * i + 1] += 1;                             // the sweeps run
-  for (int q = 0; q < 4; ++q) P.norms[4 * i + q] = 0u;
 }
 
 // one colour of the coupled correction sweep; blocks over half-rows
@@ -205,36 +229,68 @@ __global__ void k_b_corr(const BInst* __restrict__ I, int n, const int* __restri
              Fst);
 }
 
-// per-instance compensated totals: one block per (instance, field)
+// per-instance compensated totals: kTotBlocks blocks per instance each walk
+// a share of its cells, accumulate both fields in double-float pairs and
+// combine their threads in compensated doubles ...
+constexpr int kTotBlocks = 8;
 __global__ void k_b_totals(const BInst* __restrict__ I, BPtr P) {
-  const int inst = blockIdx.x >> 1, fld = blockIdx.x & 1;
+  const int inst = blockIdx.x / kTotBlocks, part = blockIdx.x % kTotBlocks;
   const BInst& B = I[inst];
   const Level& L = B.p.L;
-  const float2* x = (fld ? P.F : P.f) + B.coff;
-  float2 acc = make_float2(0.0f, 0.0f);
-  for (size_t c = threadIdx.x; c < L.ncell(); c += blockDim.x) {
-    float2 v = x[c];
-    const float w = 2.0f * (float)((ix)c % (ix)L.nx) + 1.0f;   // ring volume / (pi h^3)
-    const float pr = v.x * w;
-    v = make_float2(pr, fmaf(v.x, w, -pr) + v.y * w);
-    acc = df_add2(acc, v);
+  const ix n = (ix)L.ncell(), nx = (ix)L.nx;
+  float2 acc[2] = {make_float2(0.0f, 0.0f), make_float2(0.0f, 0.0f)};
+  for (ix c = part * blockDim.x + threadIdx.x; c < n; c += kTotBlocks * blockDim.x) {
+    const float w = 2.0f * (float)(c % nx) + 1.0f;   // ring volume / (pi h^3)
+#pragma unroll
+    for (int fld = 0; fld < 2; ++fld) {
+      float2 v = (fld ? P.F : P.f)[B.coff + c];
+      const float pr = v.x * w;
+      v = make_float2(pr, fmaf(v.x, w, -pr) + v.y * w);
+      acc[fld] = df_add2(acc[fld], v);
+    }
   }
-  double s = (double)acc.x, cc = (double)acc.y;
-  warp_sum_comp(s, cc);
-  __shared__ double ss[32], sc[32];
-  const int w = threadIdx.x >> 5;
-  if ((threadIdx.x & 31) == 0) { ss[w] = s; sc[w] = cc; }
+  __shared__ double ss[2][16], sc[2][16];
+#pragma unroll
+  for (int fld = 0; fld < 2; ++fld) {
+    double s = (double)acc[fld].x, cc = (double)acc[fld].y;
+    warp_sum_comp(s, cc);
+    if ((threadIdx.x & 31) == 0) {
+      ss[fld][threadIdx.x >> 5] = s;
+      sc[fld][threadIdx.x >> 5] = cc;
+    }
+  }
   __syncthreads();
-  if (threadIdx.x == 0) {
-    double a = ss[0], b = sc[0];
+  if (threadIdx.x < 2) {
+    const int fld = threadIdx.x;
+    double a = ss[fld][0], b = sc[fld][0];
     for (int q = 1; q < (int)(blockDim.x >> 5); ++q) {
       double t, e;
-      two_sum(a, ss[q], t, e);
+      two_sum(a, ss[fld][q], t, e);
       a = t;
-      b += sc[q] + e;
+      b += sc[fld][q] + e;
     }
-    const double h = L.h;
-    P.mass[2 * inst + fld] = (a + b) * kPi * h * h * h;
+    P.tpart[4 * (size_t)blockIdx.x + 2 * fld] = a;
+    P.tpart[4 * (size_t)blockIdx.x + 2 * fld + 1] = b;
+  }
+}
+
+// ... and one warp per instance combines its blocks in a fixed order
+__global__ void k_b_totals_final(const BInst* __restrict__ I, int n, BPtr P) {
+  const int inst = blockIdx.x;
+  if (inst >= n) return;
+  for (int fld = 0; fld < 2; ++fld) {
+    double s = 0.0, cc = 0.0;
+    for (int b = inst * kTotBlocks + threadIdx.x; b < (inst + 1) * kTotBlocks; b += blockDim.x) {
+      double t, e;
+      two_sum(s, P.tpart[4 * (size_t)b + 2 * fld], t, e);
+      s = t;
+      cc += P.tpart[4 * (size_t)b + 2 * fld + 1] + e;
+    }
+    warp_sum_comp(s, cc);
+    if (threadIdx.x == 0) {
+      const double h = I[inst].p.L.h;
+      P.mass[2 * inst + fld] = (s + cc) * kPi * h * h * h;
+    }
   }
 }
 
@@ -261,7 +317,9 @@ struct sfx_batch {
   // graph cache
   cudaGraphExec_t exec = nullptr;
   const void* key[5] = {};
-  int key_sched[4] = {};
+  int key_sched[5] = {};
+  bool reuse_phi = false;         // phi static: fold and drifts outside the graph
+  const void* drift_phi = nullptr;
   double key_tol = 0;
   cudaStream_t cap = nullptr;
   // last schedule
@@ -308,9 +366,11 @@ sfx_status enqueue_step(sfx_batch* b, bool advect, float tol, cudaStream_t s) {
   const int n = b->n, bs = b->block;
   BPtr& P = b->P;
   k_b_init<<<(n + 127) / 128, 128, 0, s>>>(n, P);
-  k_b_fold<<<b->nb_cell, bs, 0, s>>>(b->dI, n, b->pre_cell, P);
-  k_b_drift<<<b->nb_rf, bs, 0, s>>>(b->dI, n, b->pre_rf, 0, P);
-  k_b_drift<<<b->nb_zf, bs, 0, s>>>(b->dI, n, b->pre_zf, 1, P);
+  if (!b->reuse_phi) {
+    k_b_fold<<<b->nb_cell, bs, 0, s>>>(b->dI, n, b->pre_cell, P);
+    k_b_drift<<<b->nb_rf, bs, 0, s>>>(b->dI, n, b->pre_rf, 0, P);
+    k_b_drift<<<b->nb_zf, bs, 0, s>>>(b->dI, n, b->pre_zf, 1, P);
+  }
   if (advect) {
     k_b_advect<<<b->nb_cell, bs, 0, s>>>(b->dI, n, b->pre_cell, P);
     k_b_copy<<<b->nb_cell, bs, 0, s>>>(b->dI, n, b->pre_cell, P, 1);
@@ -319,14 +379,15 @@ sfx_status enqueue_step(sfx_batch* b, bool advect, float tol, cudaStream_t s) {
   }
   for (int it = 1; it <= b->max_it; ++it) {
     k_b_resid<<<b->nb_cell, bs, 0, s>>>(b->dI, n, b->pre_cell, P);
-    k_b_flags<<<(n + 127) / 128, 128, 0, s>>>(n, P, tol, it);
+    k_b_flags<<<n, 256, 0, s>>>(n, b->pre_cell, P, tol, it);
     // the residual pass did the first red half-sweep
     for (int q = 0; q < b->sweeps; ++q)
       for (int color = (q == 0 ? 1 : 0); color < 2; ++color)
         k_b_corr<<<b->nb_pair, bs, 0, s>>>(b->dI, n, b->pre_pair, P, color, q == 0 ? 1 : 0,
                                            q == b->sweeps - 1 && color == 1 ? 1 : 0);
   }
-  k_b_totals<<<2 * n, 256, 0, s>>>(b->dI, P);
+  k_b_totals<<<n * kTotBlocks, 256, 0, s>>>(b->dI, P);
+  k_b_totals_final<<<n, 32, 0, s>>>(b->dI, n, P);
   SFX_LAUNCH_CHECK();
   return SFX_OK;
 }
@@ -334,10 +395,10 @@ sfx_status enqueue_step(sfx_batch* b, bool advect, float tol, cudaStream_t s) {
 sfx_status ensure_graph(sfx_batch* b, const void* phi, const void* ur, const void* uz, void* f,
                         void* F, float tol) {
   const void* k[5] = {phi, ur, uz, f, F};
-  const int sched[4] = {b->block, b->sweeps, b->max_it, ur != nullptr};
+  const int sched[5] = {b->block, b->sweeps, b->max_it, ur != nullptr, b->reuse_phi ? 1 : 0};
   bool same = b->exec != nullptr && tol == b->key_tol;
   for (int i = 0; i < 5 && same; ++i) same = k[i] == b->key[i];
-  for (int i = 0; i < 4 && same; ++i) same = sched[i] == b->key_sched[i];
+  for (int i = 0; i < 5 && same; ++i) same = sched[i] == b->key_sched[i];
   if (same) return SFX_OK;
   if (b->exec) {
     cudaGraphExecDestroy(b->exec);
@@ -362,7 +423,7 @@ sfx_status ensure_graph(sfx_batch* b, const void* phi, const void* ur, const voi
   cudaGraphDestroy(g);
   SFX_CUDA(e);
   for (int i = 0; i < 5; ++i) b->key[i] = k[i];
-  for (int i = 0; i < 4; ++i) b->key_sched[i] = sched[i];
+  for (int i = 0; i < 5; ++i) b->key_sched[i] = sched[i];
   b->key_tol = tol;
   return SFX_OK;
 }
@@ -445,6 +506,10 @@ sfx_status sfx_batch_create(const sfx_batch_instance* inst, int n, sfx_batch** o
   if (st == SFX_OK) st = balloc(b, &P.rres, 2 * (size_t)n);
   if (st == SFX_OK) st = balloc(b, &P.mass, 2 * (size_t)n);
   if (st == SFX_OK) st = balloc(b, &P.work, 2 * (size_t)n);
+  // block partials: at most one block per 128 cells of each instance
+  const size_t maxblk = nc / 128 + (size_t)n + 1;
+  if (st == SFX_OK) st = balloc(b, &P.part, 4 * maxblk);
+  if (st == SFX_OK) st = balloc(b, &P.tpart, 4 * (size_t)n * kTotBlocks);
   if (st == SFX_OK) {
     cudaError_t e = cudaMemset(P.work, 0, 2 * (size_t)n * sizeof(unsigned long long));
     if (e != cudaSuccess) st = cuda_fail(e);
@@ -505,7 +570,24 @@ sfx_status sfx_batch_step(sfx_batch* b, const void* phi, const void* ur, const v
   if ((ur == nullptr) != (uz == nullptr)) return SFX_ERR_ARG;
   sfx_status st = ensure_graph(b, phi, ur, uz, f, F, (float)tol);
   if (st != SFX_OK) return st;
+  if (b->reuse_phi && b->drift_phi != phi) {
+    // phi declared static: its folded copy and the drifts once, outside the graph
+    cudaStream_t s = (cudaStream_t)stream;
+    const int n = b->n, bs = b->block;
+    k_b_fold<<<b->nb_cell, bs, 0, s>>>(b->dI, n, b->pre_cell, b->P);
+    k_b_drift<<<b->nb_rf, bs, 0, s>>>(b->dI, n, b->pre_rf, 0, b->P);
+    k_b_drift<<<b->nb_zf, bs, 0, s>>>(b->dI, n, b->pre_zf, 1, b->P);
+    SFX_LAUNCH_CHECK();
+    b->drift_phi = phi;
+  }
   SFX_CUDA(cudaGraphLaunch(b->exec, (cudaStream_t)stream));
+  return SFX_OK;
+}
+
+sfx_status sfx_batch_reuse_phi(sfx_batch* b, int on) {
+  if (!b) return SFX_ERR_ARG;
+  b->reuse_phi = on != 0;
+  b->drift_phi = nullptr;   // rebuild on the next step
   return SFX_OK;
 }
 

@@ -179,6 +179,23 @@ def test_graph_cache_follows_pointers(sfx):
     assert torch.equal(B.f, f3) and torch.equal(B.F, F3)
 
 
+def test_static_phi_gives_the_same_steps(sfx):
+    """With phi declared static the fold and the drifts run once outside the
+    graph; the steps are bitwise those that rebuild them every step."""
+    import torch
+    inst = _instances(seed=3)
+    outs = []
+    for reuse in (False, True):
+        B = _Batch(sfx, inst)
+        B.b.sfx_batch_set_schedule(256, 3, 20)
+        B.b.sfx_batch_reuse_phi(reuse)
+        for _ in range(3):
+            B.step(1e-10)
+        torch.cuda.synchronize()
+        outs.append((B.f.clone(), B.F.clone()))
+    assert torch.equal(outs[0][0], outs[1][0]) and torch.equal(outs[0][1], outs[1][1])
+
+
 def test_autotune_keeps_state_and_converges(sfx):
     import torch
     inst = _instances(seed=9)
