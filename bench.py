@@ -77,6 +77,24 @@ def measured_peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
 
 
+def max_over_ranks(x, world, device):
+    """The largest of x over all ranks (timings: the job is as slow as its
+    slowest replica); x itself on a single rank."""
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(units_per_rank, world, ms):
+    """Whole-job throughput: the units all ranks processed over the slowest
+    rank's time."""
+    return units_per_rank * world / (ms * 1e-3)
+
+
 def algorithmic_bytes(kind, grid, wbytes, sweeps=3):
     """Unique global bytes one launch of `kind` must move on the fine grid
     (reads + writes; arrays touched by half the cells count half).  N cells,
@@ -231,16 +249,12 @@ def run_gpu_vortex(a, rank, world, local_rank):
     torch.cuda.set_device(dev)
     r32 = vortex_run(a, dev, a.steps, sfx.SFX_F32, warmup=a.warmup)
     r64 = vortex_run(a, dev, max(1, a.steps // 10), sfx.SFX_F64, warmup=1)
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([r32["ms_per_step"]], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        r32["ms_per_step"] = float(t.item())
+    r32["ms_per_step"] = max_over_ranks(r32["ms_per_step"], world, dev)
     if rank != 0:
         return
     ms = r32["ms_per_step"]
     print(json.dumps({
-        "metric": METRIC, "value": r32["cells"] * world / (ms * 1e-3), "unit": UNIT,
+        "metric": METRIC, "value": job_rate(r32["cells"], world, ms), "unit": UNIT,
         "n_gpus": world, "steps": a.steps, "warmup": a.warmup, "ms_per_step": ms,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic",
@@ -339,14 +353,9 @@ def run_gpu(a, case, rank, world, local_rank):
     ctx.sfx_profile(False)
     ms = e0.elapsed_time(e1)
     prof = ctx.sfx_profile_read()
-    ms_max = ms
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_max = float(t.item())
+    ms_max = max_over_ranks(ms, world, dev)
     cells = g.ncell * a.steps * world
-    value = cells / (ms_max * 1e-3)
+    value = job_rate(g.ncell * a.steps, world, ms_max)
 
     # ---- end to end through the C-ABI with host buffers (pinned)
     e2e = None
@@ -365,11 +374,7 @@ def run_gpu(a, case, rank, world, local_rank):
         s1.record(stream)
         barrier()
         ms_e = s0.elapsed_time(s1)
-        if world > 1:
-            import torch.distributed as dist
-            t = torch.tensor([ms_e], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms_e = float(t.item())
+        ms_e = max_over_ranks(ms_e, world, dev)
         nb = 2 * g.ncell * 8
         e2e = {"value": cells / (ms_e * 1e-3), "unit": UNIT, "h2d_bytes_per_step": nb,
                "d2h_bytes_per_step": nb}
@@ -704,11 +709,7 @@ def run_gpu_batch(a, rank, world, local_rank, steps=None, summary=False):
     rp, sg = B.sfx_batch_work()
     st = B.sfx_batch_stats()
     ms_max = ms
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_max = float(t.item())
+    ms_max = max_over_ranks(ms, world, dev)
     value = ncell * steps * world / (ms_max * 1e-3)
     peaks, peak_src = measured_peaks()
     ab = batch_bytes(sizes, rp, sg, steps, sweeps)
