@@ -90,6 +90,7 @@ def lib():
         L.orc_total.argtypes = [G, _P]
         L.orc_eos.argtypes = [G, Pp, _P, _P, _P, _P]
         L.orc_marangoni.argtypes = [G, Pp, _P, _P, _P, C.c_int, _P, _P]
+        L.orc_capillary.argtypes = [G, _P, _P, _P, C.c_double, _P, _P]
         L.orc_plic_volume.restype = C.c_double
         L.orc_plic_volume.argtypes = [C.c_int, _P, C.c_double]
         L.orc_plic_area.restype = C.c_double
@@ -267,6 +268,15 @@ def marangoni(g, p, f, phi, Cf, dm_mode=1):
     lib().orc_marangoni(C.byref(cgrid(g)), C.byref(cparams(p)), _ptr(_arr(f)), _ptr(_arr(phi)),
                         _ptr(_arr(Cf)), int(dm_mode), _ptr(sig), _ptr(force))
     return sig, force
+
+
+def capillary(g, phi, Cf, sigma, eps):
+    """(kappa, force): curvature -div n and F_cap = sigma kappa |grad C| n."""
+    kap = np.empty((g.nz, g.ny, g.nx))
+    force = np.empty((g.ndim, g.nz, g.ny, g.nx))
+    lib().orc_capillary(C.byref(cgrid(g)), _ptr(_arr(phi)), _ptr(_arr(Cf)), _ptr(_arr(sigma)),
+                        float(eps), _ptr(kap), _ptr(force))
+    return kap, force
 
 
 def plic_volume(dim, m, alpha):

@@ -789,6 +789,59 @@ void orc_marangoni(const orc_grid* g, const orc_params* p, const double* f,
   free(n);
 }
 
+/* ------------------------------------------------------ capillary force */
+
+/* Capillary force F_cap = sigma kappa delta_s n (Sec. 2.4) with the mean
+   curvature kappa = -div n (Sec. 2.2) and delta_s = |grad C|.
+   READING: n is the cell-centred unit normal of orc_normals (grad phi /
+   |grad phi|, zero where phi is flat).  div n is taken in flux form over
+   the faces of the cell, (1/V_c) sum_f (+-) A_f nbar_f, nbar_f the mean of
+   the two adjacent cells' normal components along the face normal: on a
+   planar grid this is the centred difference, on the axisymmetric grid the
+   face areas add the hoop term n_r/r.  A wall face carries no normal
+   component (walls are symmetry planes, so the interface meets them at a
+   right angle); the axis face has zero area.  grad C is centred with
+   zero-gradient ghosts, as delta_m = |grad C| of the Marangoni force.
+   sigma is any cell field (the EOS output); kappa may be NULL. */
+void orc_capillary(const orc_grid* g, const double* phi, const double* C,
+                   const double* sigma, double eps, double* kappa,
+                   double* force) {
+  size_t N = ncell_of(g);
+  int D = ndim_of(g);
+  double* n = (double*)malloc((size_t)D * N * sizeof(double));
+  orc_normals(g, phi, eps, n);
+  for (int k = 0; k < g->nz; ++k)
+    for (int j = 0; j < g->ny; ++j)
+      for (int i = 0; i < g->nx; ++i) {
+        size_t c = idx(g, i, j, k);
+        double div = 0.0;
+        for (int d = 0; d < D; ++d) {
+          const double* nd = n + (size_t)d * N;
+          for (int s = -1; s <= 1; s += 2) {
+            int a = i, b = j, e = k;
+            if (!shift(g, d, s, &a, &b, &e)) continue;   /* wall or axis face */
+            /* the face between the cell and its neighbour: minus face of
+               the cell (s = -1) or of the neighbour (s = +1) */
+            double A = s < 0 ? face_area(g, d, i, j, k) : face_area(g, d, a, b, e);
+            double nbar = 0.5 * (nd[c] + nd[idx(g, a, b, e)]);
+            div += s * A * nbar;
+          }
+        }
+        double kap = -div / orc_cell_volume(g, i, j, k);
+        double q = 0.0;
+        for (int d = 0; d < D; ++d) {
+          double gc = (nb_or_self(g, C, i, j, k, d, +1) -
+                       nb_or_self(g, C, i, j, k, d, -1)) / (2.0 * g->h);
+          q += gc * gc;
+        }
+        double ds = sqrt(q);
+        if (kappa) kappa[c] = kap;
+        for (int d = 0; d < D; ++d)
+          force[(size_t)d * N + c] = sigma[c] * kap * ds * n[(size_t)d * N + c];
+      }
+  free(n);
+}
+
 /* --------------------------------------------------------------- a9: CFL */
 
 /* dt = safety * min(h / (|u|max + D/eps), h^2 / (2 N_d D))  (Sec. 3.3) */

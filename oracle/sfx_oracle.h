@@ -151,6 +151,13 @@ void orc_marangoni(const orc_grid* g, const orc_params* p, const double* f,
 double orc_plic_volume(int dim, const double* m, double alpha);
 double orc_plic_area(int dim, const double* m, double C);
 
+/* Capillary force F_cap = sigma kappa delta_s n, kappa = -div n (flux
+   form over the faces), delta_s = |grad C| (Sec. 2.2, 2.4).  force holds
+   ndim component arrays; kappa (may be NULL) receives the curvature. */
+void orc_capillary(const orc_grid* g, const double* phi, const double* C,
+                   const double* sigma, double eps, double* kappa,
+                   double* force);
+
 /* a9: time step from the CFL criterion of Sec. 3.3 */
 double orc_cfl_dt(int ndim, double h, double umax, double D, double eps,
                   double safety);
