@@ -37,6 +37,35 @@ METRIC = "cell-updates/s of coupled surfactant step (FP32/batched vs FP64), % HB
 UNIT = "cell-updates/s"
 SAMPLE_N = 64          # oracle sample: centred 64^3 block of the same grid
 
+# DRAM bytes (read + write) per launch of a dominant kernel from one ncu
+# capture, per cell of the captured grid, with a digest of the sources the
+# kernel was built from: scaled by the cell count to the timed grid, and
+# withdrawn (None) as soon as those sources differ from the captured ones.
+NCU_TRAFFIC = {
+    ("smooth_fine", "f32", 3): {
+        "bytes_per_cell": 154.4e6 / 160 ** 3,
+        "sources": ["sfx_f32.cu", "sfx_f32_dev.cuh", "sfx_df.cuh", "sfx_common.cuh"],
+        "sha256_16": "97b3f73e6ee1e6bd",
+        "capture": "profiles/corr2_hr3d160_f32.md (160^3, launches 5-7, weighted 6:1 as in an "
+                   "iteration of 4 sweeps), scaled by the cell count",
+    },
+}
+
+
+def ncu_traffic(kind, precision, ndim, ncell):
+    """Captured DRAM bytes per launch for the timed grid, or None."""
+    import hashlib
+    e = NCU_TRAFFIC.get((kind, precision, ndim))
+    if e is None:
+        return None, None
+    h = hashlib.sha256()
+    for f in e["sources"]:
+        with open(os.path.join(ROOT, "paper_2605_27534_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    if h.hexdigest()[:16] != e["sha256_16"]:
+        return None, "kernel sources changed since the capture"
+    return e["bytes_per_cell"] * ncell, e["capture"]
+
 
 def parse():
     ap = argparse.ArgumentParser()
@@ -402,8 +431,10 @@ def run_gpu(a, case, rank, world, local_rank):
     if ab is not None and nwork > 0:
         avg_s = tot_ms * 1e-3 / nwork
         achieved = ab / avg_s / 1e9
+        traffic, tsrc = ncu_traffic(kind, a.precision, g.ndim, g.ncell)
         roof = {"bound": "hbm", "kernel": kind, "achieved": achieved, "peak": peaks["hbm_gbs"],
-                "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"], "traffic": None,
+                "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"], "traffic": traffic,
+                "traffic_source": tsrc,
                 "algorithmic_bytes_per_launch": ab, "avg_launch_ms": avg_s * 1e3,
                 "working_launches": nwork, "launches": nl,
                 "peak_source": "%s (MEASURED_PEAKS.json hbm_gbs)" % peak_src}

@@ -239,6 +239,26 @@ sfx_status sfx_marangoni_force(sfx_ctx* ctx, const sfx_params* params,
                                const void* C, int dm_mode, void* sigma,
                                void* force, void* stream);
 
+/* Capillary force (Sec. 2.4, curvature of Sec. 2.2):
+     F_cap = sigma kappa delta_s n,  kappa = -div n,  delta_s = |grad C|,
+   n = grad phi/|grad phi| at cell centres (centred differences, 0 where
+   phi is flat), div n in flux form over the cell's faces with each face
+   taking the mean of its two cells' normal components (the axisymmetric
+   face areas add the hoop term n_r/r), no normal component on wall faces,
+   zero area on the axis; grad C centred with zero-gradient ghosts.  sigma
+   is any cell field, normally the EOS output of sfx_marangoni_force.
+   params: only eps is used.  phi is double.  SFX_F64: C, sigma, kappa,
+   force double, FP64 arithmetic.  SFX_F32: C, sigma, kappa, force float;
+   the differences of phi are taken in FP64 and the rest in FP32 (kappa is
+   a difference of unit vectors over h, so its rounding grows as 2^-24/h).
+   kappa (may be NULL) receives the curvature; force holds ndim arrays of N
+   cells, component-major.  Caller-owned device arrays; SFX_ERR_ARG on a
+   null argument. */
+sfx_status sfx_capillary_force(sfx_ctx* ctx, const sfx_params* params,
+                               const double* phi, const void* C,
+                               const void* sigma, void* kappa, void* force,
+                               void* stream);
+
 /* a9.  Time step of Sec. 3.3: safety * min(h/(umax + D/eps),
    h^2/(2 N_d D)), with umax the largest |face velocity| (reduced on the
    device from ux, uy, uz in the context precision).  Host result. */

@@ -150,6 +150,14 @@ class Context:
                                          int(dm_mode), _ptr(sigma), _ptr(force), _stream()),
                "sfx_marangoni_force")
 
+    def sfx_capillary_force(self, params, phi, Cf, sigma, force, kappa=None):
+        """F_cap = sigma kappa |grad C| n into `force` (ndim x N), the
+        curvature into `kappa` when given."""
+        ps = params if isinstance(params, Params) else params_struct(params)
+        _check(lib().sfx_capillary_force(self._h, C.byref(ps), _ptr(phi), _ptr(Cf), _ptr(sigma),
+                                         _ptr(kappa), _ptr(force), _stream()),
+               "sfx_capillary_force")
+
     def sfx_df_pack(self, x, out=None):
         return sfx_df_pack(x, out)
 

@@ -268,6 +268,13 @@ sfx_status sfx_marangoni_force(sfx_ctx* c, const sfx_params* params, const void*
                    (double*)force, S(stream));
 }
 
+sfx_status sfx_capillary_force(sfx_ctx* c, const sfx_params* params, const double* phi,
+                               const void* C, const void* sigma, void* kappa, void* force,
+                               void* stream) {
+  if (!c || !params_ok(params) || !phi || !C || !sigma || !force) return SFX_ERR_ARG;
+  return capillary(c, params, phi, C, sigma, kappa, force, S(stream));
+}
+
 sfx_status sfx_vof_advect(sfx_ctx* c, const void* ux, const void* uy, const void* uz, double dt,
                           int order, double* C, void* stream) {
   if (!c || !ux || !uy || !C || !(dt > 0.0) || !std::isfinite(dt)) return SFX_ERR_ARG;

@@ -164,6 +164,9 @@ sfx_status surfactant_step(sfx_ctx* c, const sfx_params* p, const void* phi, con
 // sfx_solver.cu: drift faces of both problems from a double phi
 sfx_status drift_faces64(sfx_ctx* c, const double* phi, double Df, double DF, double eps,
                          double* const* Bf, double* const* BF, cudaStream_t s);
+// sfx_capillary.cu
+sfx_status capillary(sfx_ctx* c, const sfx_params* p, const double* phi, const void* C,
+                     const void* sigma, void* kappa, void* force, cudaStream_t s);
 // sfx_vof.cu
 sfx_status vof_advect(sfx_ctx* c, const void* ux, const void* uy, const void* uz, double dt,
                       int order, double* C, cudaStream_t s);
