@@ -5,9 +5,11 @@ Default workload: 3D bubble-like transport, 256^3 unit cube, sphere R = 0.125,
 prescribed Hadamard-Rybczynski Stokes flow (viscosity ratio 0.01, unit
 far-field velocity), F = 1 and Gamma = 0 initially, Bi = Da = 1, Langmuir EOS
 sigma0 = 1, E = 0.2, dt = 5e-5.  One step = BCG advection of f and F, the
-App. C implicit source system solved to tolerance (Picard + multigrid),
-compensated totals, EOS and Marangoni force.  The phase field is built once
-(the interface is static in this workload).
+App. C implicit source system solved to tolerance,
+compensated totals, EOS and Marangoni force.  In an SFX_F32 context the
+App. C system is solved by a coupled Newton defect correction (FP64
+contexts: Picard + multigrid).  The phase field is built once (the interface
+is static in this workload).
 
 Arms:
   (default)          libsfx on cuda:LOCAL_RANK, one independent replica per
@@ -629,23 +631,30 @@ def f64_path(a, case, dev, f32_f, f32_F, f32_phi, ux, uy, uz):
     e1.record(stream)
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / a.f64_steps
-    # accuracy of the FP32 path against this one: two steps from f = 0, F = 1
+    # accuracy of the FP32 path against this one: two steps from f = 0, F = 1,
+    # from this path's phi (the step alone) and from the FP32 context's own
+    # phi (the FP32 phase-field build as well)
     ctx32 = sfx.Context.for_grid(g, sfx.SFX_F32)
     zeros = torch.zeros(g.shape, dtype=torch.float64, device=dev)
     f.zero_()
     F.fill_(1.0)
-    f32_f.copy_(sfx.sfx_df_pack(zeros))
-    f32_F.copy_(sfx.sfx_df_pack(F))
     o32 = sfx.default_opts(tol=a.tol, max_cycles=200, nu1=3, nu2=0)
     for _ in range(2):
         ctx.sfx_surfactant_step(p, phi, f, F, case.dt, *u64, opts=opts)
-        ctx32.sfx_surfactant_step(p, f32_phi, f32_f, f32_F, case.dt, ux, uy, uz, opts=o32)
-    fd, Fd = sfx.sfx_df_unpack(f32_f), sfx.sfx_df_unpack(f32_F)
     scale = float(torch.maximum(f.abs().max(), F.abs().max()))
-    err = float(torch.maximum((fd - f).abs().max(), (Fd - F).abs().max())) / scale
+    errs = []
+    for phi32 in (phi, f32_phi):
+        f32_f.copy_(sfx.sfx_df_pack(zeros))
+        f32_F.copy_(sfx.sfx_df_pack(zeros + 1.0))
+        for _ in range(2):
+            ctx32.sfx_surfactant_step(p, phi32, f32_f, f32_F, case.dt, ux, uy, uz, opts=o32)
+        fd, Fd = sfx.sfx_df_unpack(f32_f), sfx.sfx_df_unpack(f32_F)
+        errs.append(float(torch.maximum((fd - f).abs().max(), (Fd - F).abs().max())) / scale)
     return {"ms_per_step": ms, "value": g.ncell / (ms * 1e-3), "unit": UNIT, "steps": a.f64_steps,
             "picard_per_step": statistics.mean(pic), "dtype": "f64",
-            "f32_rel_err_after_2_steps": err}
+            "f32_rel_err_after_2_steps": errs[0],
+            "f32_with_own_phi_rel_err_after_2_steps": errs[1],
+            "phi_f32_build_max_abs_diff": float((f32_phi - phi).abs().max())}
 
 
 # ------------------------------------------------------------------ batched

@@ -51,12 +51,10 @@ struct BPtr {
   float2* Fs;
   float* Bf[2];           // radial, axial drift faces of the f problem
   float* BF[2];
-  __half* Hf[2];          // the same in half precision (correction sweeps)
-  __half* HF[2];
+  __half2* H2[2];         // (B_f, B_F) in half precision (correction sweeps)
   float4* coef;
   float2* res;
-  float* ef;
-  float* eF;
+  float2* e2;             // Newton corrections (e_f, e_F), colour-packed
   unsigned int* norms;    // 4 per instance
   int* active;
   int* iters;
@@ -93,8 +91,7 @@ __global__ void k_b_drift(const BInst* __restrict__ I, int n, const int* __restr
   }
   Bf[q] = bf;
   BF[q] = bF;
-  P.Hf[dir][fo + q] = __float2half_rn(bf);
-  P.HF[dir][fo + q] = __float2half_rn(bF);
+  P.H2[dir][fo + q] = __floats2half2_rn(bf, bF);
 }
 
 __global__ void k_b_advect(const BInst* __restrict__ I, int n, const int* __restrict__ pre, BPtr P) {
@@ -151,7 +148,7 @@ __global__ void k_b_resid(const BInst* __restrict__ I, int n, const int* __restr
     const float* BF[3] = {P.BF[0] + B.rfoff, P.BF[1] + B.zfoff, nullptr};
     const size_t o = B.coff, w = B.poff;
     resid2_cell(B.p, i, j, 0, c, P.phi32 + o, Bf, BF, P.f + o, P.F + o, P.fs + o, P.Fs + o,
-                P.coef + w, P.res + w, m, P.ef + w, P.eF + w);
+                P.coef + w, P.res + w, m, P.e2 + w);
   }
   // block maxima; the flags kernel combines the blocks of each instance
   __shared__ float wm[4][16];
@@ -218,15 +215,14 @@ __global__ void k_b_corr(const BInst* __restrict__ I, int n, const int* __restri
       const size_t cr = cidx(L, ir, j, 0);
       const RBIdx rb = rb_index(L, i, j, 0);
       const size_t pr = w + (1 - color) * rb.plane + rb.pos;   // ir's packed slot
-      fst[cr] = df_add(fst[cr], P.ef[pr]);
-      Fst[cr] = df_add(Fst[cr], P.eF[pr]);
+      const float2 er = P.e2[pr];
+      fst[cr] = df_add(fst[cr], er.x);
+      Fst[cr] = df_add(Fst[cr], er.y);
     }
     return;
   }
-  const __half* Bf[3] = {P.Hf[0] + B.rfoff, P.Hf[1] + B.zfoff, nullptr};
-  const __half* BF[3] = {P.HF[0] + B.rfoff, P.HF[1] + B.zfoff, nullptr};
-  corr2_cell(B.p, i, j, 0, Bf, BF, P.coef + w, P.res + w, P.ef + w, P.eF + w, color, first, fst,
-             Fst);
+  const __half2* H[3] = {P.H2[0] + B.rfoff, P.H2[1] + B.zfoff, nullptr};
+  corr2_cell(B.p, i, j, 0, H, P.coef + w, P.res + w, P.e2 + w, color, first, fst, Fst);
 }
 
 // per-instance compensated totals: kTotBlocks blocks per instance each walk
@@ -492,14 +488,11 @@ sfx_status sfx_batch_create(const sfx_batch_instance* inst, int n, sfx_batch** o
   if (st == SFX_OK) st = balloc(b, &P.Bf[1], b->nzf);
   if (st == SFX_OK) st = balloc(b, &P.BF[0], b->nrf);
   if (st == SFX_OK) st = balloc(b, &P.BF[1], b->nzf);
-  if (st == SFX_OK) st = balloc(b, &P.Hf[0], b->nrf);
-  if (st == SFX_OK) st = balloc(b, &P.Hf[1], b->nzf);
-  if (st == SFX_OK) st = balloc(b, &P.HF[0], b->nrf);
-  if (st == SFX_OK) st = balloc(b, &P.HF[1], b->nzf);
+  if (st == SFX_OK) st = balloc(b, &P.H2[0], b->nrf);
+  if (st == SFX_OK) st = balloc(b, &P.H2[1], b->nzf);
   if (st == SFX_OK) st = balloc(b, &P.coef, b->npack);
   if (st == SFX_OK) st = balloc(b, &P.res, b->npack);
-  if (st == SFX_OK) st = balloc(b, &P.ef, b->npack);
-  if (st == SFX_OK) st = balloc(b, &P.eF, b->npack);
+  if (st == SFX_OK) st = balloc(b, &P.e2, b->npack);
   if (st == SFX_OK) st = balloc(b, &P.norms, 4 * (size_t)n);
   if (st == SFX_OK) st = balloc(b, &P.active, (size_t)n);
   if (st == SFX_OK) st = balloc(b, &P.iters, (size_t)n);

@@ -40,7 +40,7 @@ namespace {
 
 __global__ void k_drift32(Level L, int d, const double* __restrict__ phi, float Df, float DF,
                           float inv_eps, float* __restrict__ Bf, float* __restrict__ BF,
-                          __half* __restrict__ Hf, __half* __restrict__ HF) {
+                          __half2* __restrict__ H2) {
   size_t n = L.nface(d);
   int fx = L.nx + (d == 0), fy = L.ny + (d == 1);
   for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < n;
@@ -57,8 +57,7 @@ __global__ void k_drift32(Level L, int d, const double* __restrict__ phi, float 
     }
     Bf[q] = bf;
     BF[q] = bF;
-    Hf[q] = __float2half_rn(bf);
-    HF[q] = __float2half_rn(bF);
+    H2[q] = __floats2half2_rn(bf, bF);
   }
 }
 
@@ -297,8 +296,8 @@ k_resid2_32(Nw32 p, const float* __restrict__ phi, const float* __restrict__ Bfx
             const float* __restrict__ BFz, const float2* __restrict__ fin,
             const float2* __restrict__ Fin, const float2* __restrict__ fst,
             const float2* __restrict__ Fst, float4* __restrict__ coef,
-            float2* __restrict__ res, unsigned int* norms, float* __restrict__ ef,
-            float* __restrict__ eF, const int* __restrict__ done) {
+            float2* __restrict__ res, unsigned int* norms, float2* __restrict__ e2,
+            const int* __restrict__ done) {
   if (done && *done) return;   // converged at an earlier iteration
   const Level& L = p.L;
   float m[4] = {0.0f, 0.0f, 0.0f, 0.0f};
@@ -311,7 +310,7 @@ k_resid2_32(Nw32 p, const float* __restrict__ phi, const float* __restrict__ Bfx
     const int j = (int)(r % (ix)L.ny), k = (int)(r / (ix)L.ny);
     if (i < L.nx)
       resid2_cell(p, i, j, k, r * (ix)L.nx + (ix)i, phi, Bf, BF, fin, Fin, fst, Fst, coef, res, m,
-                  ef, eF);
+                  e2);
   }
   if (norms) {
     // warp maxima, then one atomic per block and norm
@@ -332,19 +331,15 @@ k_resid2_32(Nw32 p, const float* __restrict__ phi, const float* __restrict__ Bfx
 
 // One colour of the coupled red-black Gauss-Seidel on the correction.
 __global__ void __launch_bounds__(128, 10)
-k_corr2_32(Nw32 p, const __half* __restrict__ Bfx, const __half* __restrict__ Bfy,
-           const __half* __restrict__ Bfz, const __half* __restrict__ BFx,
-           const __half* __restrict__ BFy, const __half* __restrict__ BFz,
-                           const float4* __restrict__ coef, const float2* __restrict__ res,
-                           float* __restrict__ ef, float* __restrict__ eF, int color, int first,
-                           float2* __restrict__ fst, float2* __restrict__ Fst,
-                           const int* __restrict__ done) {
+k_corr2_32(Nw32 p, const __half2* __restrict__ Hx, const __half2* __restrict__ Hy,
+           const __half2* __restrict__ Hz, const float4* __restrict__ coef,
+           const float2* __restrict__ res, float2* __restrict__ e2, int color, int first,
+           float2* __restrict__ fst, float2* __restrict__ Fst, const int* __restrict__ done) {
   if (done && *done) return;
   const Level& L = p.L;
   const int j = blockIdx.y, k = blockIdx.z;
   const int i = 2 * (blockIdx.x * blockDim.x + threadIdx.x) + ((j + k + color) & 1);
-  const __half* Bf[3] = {Bfx, Bfy, Bfz};
-  const __half* BF[3] = {BFx, BFy, BFz};
+  const __half2* H[3] = {Hx, Hy, Hz};
   if (i >= L.nx) {
     // a row of odd length: the last red cell has no black partner
     const int ir = i ^ 1;
@@ -352,12 +347,13 @@ k_corr2_32(Nw32 p, const __half* __restrict__ Bfx, const __half* __restrict__ Bf
       const size_t cr = cidx(L, ir, j, k);
       const RBIdx rb = rb_index(L, i, j, k);
       const size_t pr = (1 - color) * rb.plane + rb.pos;   // ir's packed slot
-      fst[cr] = df_add(fst[cr], ef[pr]);
-      Fst[cr] = df_add(Fst[cr], eF[pr]);
+      const float2 er = e2[pr];
+      fst[cr] = df_add(fst[cr], er.x);
+      Fst[cr] = df_add(Fst[cr], er.y);
     }
     return;
   }
-  corr2_cell(p, i, j, k, Bf, BF, coef, res, ef, eF, color, first, fst, Fst);
+  corr2_cell(p, i, j, k, H, coef, res, e2, color, first, fst, Fst);
 }
 
 // ------------------------------------------------------------ fused sweep
@@ -1115,8 +1111,7 @@ sfx_status solve_newton32(sfx_ctx* c, const Nw32& p, const float* phi, float* co
   unsigned int* hn = (unsigned int*)c->h_norms;
   int* flag = c->f32.flag;
   const RowGrid rg = row_grid(L);
-  const __half* Hz_f = L.ndim() == 3 ? c->f32.Hf[2] : nullptr;
-  const __half* Hz_F = L.ndim() == 3 ? c->f32.HF[2] : nullptr;
+  const __half2* Hz = L.ndim() == 3 ? c->f32.H2[2] : nullptr;
   SFX_CUDA(cudaMemsetAsync(flag, 0, 2 * sizeof(int), s));
   // Each iteration: the residual pass (which also does the first red
   // half-sweep of the correction, from zero), a device-side convergence
@@ -1132,7 +1127,7 @@ sfx_status solve_newton32(sfx_ctx* c, const Nw32& p, const float* phi, float* co
     unsigned int* nbuf = dn + 4 * (it & 1);
     SFX_CUDA(cudaMemsetAsync(nbuf, 0, 4 * sizeof(unsigned int), s));
     SFX_KERNEL(c, K_RESIDUAL, k_resid2_32, rg.grid, rg.block, s, p, phi, Bf[0], Bf[1], Bf[2], BF[0], BF[1],
-               BF[2], fc, Fc, fs, Fs, c->f32.coef, c->f32.res, nbuf, c->f32.ef, c->f32.eF, flag);
+               BF[2], fc, Fc, fs, Fs, c->f32.coef, c->f32.res, nbuf, c->f32.e2, flag);
     if (it == 1 && predicted) {
       // keep the predicted start only if its residual is already small;
       // otherwise restart from x* (both launches return at once when kept)
@@ -1141,8 +1136,7 @@ sfx_status solve_newton32(sfx_ctx* c, const Nw32& p, const float* phi, float* co
       SFX_KERNEL(c, K_OTHER, k_pred_check32, 1, 32, s, nbuf, rho, ok);
       SFX_KERNEL(c, K_SETUP, k_restore32, nb, 256, s, n, ok, fs, Fs, fc, Fc);
       SFX_KERNEL(c, K_RESIDUAL, k_resid2_32, rg.grid, rg.block, s, p, phi, Bf[0], Bf[1], Bf[2], BF[0],
-                 BF[1], BF[2], fc, Fc, fs, Fs, c->f32.coef, c->f32.res, nbuf, c->f32.ef, c->f32.eF,
-                 ok);
+                 BF[1], BF[2], fc, Fc, fs, Fs, c->f32.coef, c->f32.res, nbuf, c->f32.e2, ok);
     }
     SFX_KERNEL(c, K_OTHER, k_flag32, 1, 32, s, nbuf, tolf, it, flag);
     SFX_CUDA(cudaMemcpyAsync(hn + 4 * (it & 1), nbuf, 4 * sizeof(unsigned int),
@@ -1151,10 +1145,9 @@ sfx_status solve_newton32(sfx_ctx* c, const Nw32& p, const float* phi, float* co
     for (int q = 0; q < sweeps; ++q)
       for (int color = (q == 0 ? 1 : 0); color < 2; ++color) {
         const bool apply = q == sweeps - 1 && color == 1;
-        SFX_KERNEL(c, K_SMOOTH_FINE, k_corr2_32, grd, blk, s, p, c->f32.Hf[0], c->f32.Hf[1], Hz_f,
-                   c->f32.HF[0], c->f32.HF[1], Hz_F, c->f32.coef, c->f32.res, c->f32.ef,
-                   c->f32.eF, color, q == 0 ? 1 : 0, apply ? fc : nullptr, apply ? Fc : nullptr,
-                   flag);
+        SFX_KERNEL(c, K_SMOOTH_FINE, k_corr2_32, grd, blk, s, p, c->f32.H2[0], c->f32.H2[1], Hz,
+                   c->f32.coef, c->f32.res, c->f32.e2, color, q == 0 ? 1 : 0,
+                   apply ? fc : nullptr, apply ? Fc : nullptr, flag);
       }
     SFX_LAUNCH_CHECK();
     const int prev = it - 1;
@@ -1206,7 +1199,7 @@ sfx_status step_f32(sfx_ctx* c, const sfx_params* pr, const double* phi_in, cons
     for (int d = 0; d < nd; ++d)
       SFX_KERNEL(c, K_SETUP, k_drift32, blocks_for(L.nface(d), 256), 256, s, L, d, phi_in,
                  (float)pr->Df, (float)pr->DF, (float)(1.0 / pr->eps), Bf[d], BF[d],
-                 c->f32.Hf[d], c->f32.HF[d]);
+                 c->f32.H2[d]);
     SFX_LAUNCH_CHECK();
     c->f32.drift_phi = phi_in;
     c->f32.drift_key[0] = pr->Df;
@@ -1421,8 +1414,7 @@ sfx_status f32_ensure_scratch(sfx_ctx* c) {
   for (int d = 0; d < L.ndim(); ++d) {
     if ((st = get(L.nface(d) * sizeof(float), (void**)&c->f32.Bf[d])) != SFX_OK) return st;
     if ((st = get(L.nface(d) * sizeof(float), (void**)&c->f32.BF[d])) != SFX_OK) return st;
-    if ((st = get(L.nface(d) * sizeof(__half), (void**)&c->f32.Hf[d])) != SFX_OK) return st;
-    if ((st = get(L.nface(d) * sizeof(__half), (void**)&c->f32.HF[d])) != SFX_OK) return st;
+    if ((st = get(L.nface(d) * sizeof(__half2), (void**)&c->f32.H2[d])) != SFX_OK) return st;
   }
   if ((st = get(n * sizeof(float2), (void**)&c->f32.fstar)) != SFX_OK) return st;
   if ((st = get(n * sizeof(float2), (void**)&c->f32.Fstar)) != SFX_OK) return st;
@@ -1438,6 +1430,7 @@ sfx_status f32_ensure_scratch(sfx_ctx* c) {
   float** arrs[6] = {&c->f32.ef, &c->f32.eF, &c->f32.rf, &c->f32.rF, &c->f32.lf, &c->f32.lF};
   for (float** q : arrs)
     if ((st = get(np * sizeof(float), (void**)q)) != SFX_OK) return st;
+  if ((st = get(np * sizeof(float2), (void**)&c->f32.e2)) != SFX_OK) return st;
   if ((st = get(np * sizeof(float4), (void**)&c->f32.coef)) != SFX_OK) return st;
   if ((st = get(np * sizeof(float2), (void**)&c->f32.res)) != SFX_OK) return st;
   for (int q = 0; q < 2; ++q) SFX_CUDA(cudaEventCreateWithFlags(&c->f32.ev[q], cudaEventDisableTiming));

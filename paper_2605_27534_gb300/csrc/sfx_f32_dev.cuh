@@ -182,6 +182,28 @@ __device__ __forceinline__ void faces6(const Level& L, const T* Bx, const T* By,
   B[5] = has[5] ? face_val(Bz[c + (ix)L.nx * (ix)L.ny]) : 0.0f;
 }
 
+// faces6 for both fields at once from the packed (B_f, B_F) half2 faces.
+__device__ __forceinline__ void faces6x2(const Level& L, const __half2* Hx, const __half2* Hy,
+                                         const __half2* Hz, int i, int j, int k, const bool* has,
+                                         float* Bf, float* BF) {
+  const ix c = cidx32(L, i, j, k);
+  const ix fx = c + (ix)k * (ix)L.ny + (ix)j, fy = c + (ix)k * (ix)L.nx;
+  const __half2 z = __floats2half2_rn(0.0f, 0.0f);
+  __half2 h[6];
+  h[0] = has[0] ? Hx[fx] : z;
+  h[1] = has[1] ? Hx[fx + 1] : z;
+  h[2] = has[2] ? Hy[fy] : z;
+  h[3] = has[3] ? Hy[fy + L.nx] : z;
+  h[4] = has[4] ? Hz[c] : z;
+  h[5] = has[5] ? Hz[c + (ix)L.nx * (ix)L.ny] : z;
+#pragma unroll
+  for (int q = 0; q < 6; ++q) {
+    const float2 v = __half22float2(h[q]);
+    Bf[q] = v.x;
+    BF[q] = v.y;
+  }
+}
+
 // (1/V) sum +-A G of one field around cell i as an unnormalised pair, and
 // the derivative of that sum in the cell value (negated: diagonal weight).
 // The diffusive part is gathered as Doh (sum_q w_q a_q - W a_c), W = sum_q
@@ -333,7 +355,7 @@ __device__ __forceinline__ void face32v2(const Adv32& A, const float2* __restric
 
 // Both residuals (pairs) of App. C at cell c of the current state, the
 // kinetic diagonals and couplings of the linearised system, and the running
-// maxima m = {|r_f|, |b_f|, |r_F|, |b_F|}.  With ef != NULL the first red
+// maxima m = {|r_f|, |b_f|, |r_F|, |b_F|}.  With e2 != NULL the first red
 // half-sweep of the correction is done here: it starts from zero
 // corrections, so a red cell (i + j + k even) only needs its own 2x2 block,
 // e = M_c^-1 r_c.
@@ -345,8 +367,7 @@ __device__ __forceinline__ void resid2_cell(const Nw32& p, int i, int j, int k, 
                                             const float2* __restrict__ fst,
                                             const float2* __restrict__ Fst,
                                             float4* __restrict__ coef, float2* __restrict__ res,
-                                            float* m, float* __restrict__ ef,
-                                            float* __restrict__ eF) {
+                                            float* m, float2* __restrict__ e2) {
   const Level& L = p.L;
   bool has[6];
   ix nbi[6];
@@ -392,12 +413,11 @@ __device__ __forceinline__ void resid2_cell(const Nw32& p, int i, int j, int k, 
   const ix own = (ix)((i + j + k) & 1) * rb.plane + rb.pos;
   coef[own] = cf;
   res[own] = make_float2(rf, rF);
-  if (ef && ((i + j + k) & 1) == 0) {
+  if (e2 && ((i + j + k) & 1) == 0) {
     // [a -b; -d e] [x; y] = [r_f; r_F], diagonals with the flux weights
     const float a = cf.x + df_, bb = cf.z, d = cf.w, e = cf.y + dF_;
     const float inv = __fdividef(1.0f, a * e - bb * d);
-    ef[own] = (e * rf + bb * rF) * inv;
-    eF[own] = (d * rf + a * rF) * inv;
+    e2[own] = make_float2((e * rf + bb * rF) * inv, (d * rf + a * rF) * inv);
   }
   m[0] = fmaxf(m[0], fabsf(rf));
   m[1] = fmaxf(m[1], fabsf(fs.x * p.inv_dt + c1 * Fv * finf));
@@ -413,12 +433,11 @@ __device__ __forceinline__ void resid2_cell(const Nw32& p, int i, int j, int k, 
 // solution), so they read the face drifts in half precision (relative
 // 5e-4), halving their face traffic.
 __device__ __forceinline__ void corr2_cell(const Nw32& p, int i, int j, int k,
-                                           const __half* const* Bf, const __half* const* BF,
+                                           const __half2* const* H,
                                            const float4* __restrict__ coef,
                                            const float2* __restrict__ res,
-                                           float* __restrict__ ef, float* __restrict__ eF,
-                                           int color, int first, float2* __restrict__ fst,
-                                           float2* __restrict__ Fst) {
+                                           float2* __restrict__ e2, int color, int first,
+                                           float2* __restrict__ fst, float2* __restrict__ Fst) {
   const Level& L = p.L;
   const ix c = cidx32(L, i, j, k);
   bool has[6];
@@ -440,15 +459,16 @@ __device__ __forceinline__ void corr2_cell(const Nw32& p, int i, int j, int k,
   float enf[6], enF[6];
 #pragma unroll
   for (int q = 0; q < 6; ++q) {
-    enf[q] = (has[q] && !zero_nb) ? ef[nbi[q]] : 0.0f;
-    enF[q] = (has[q] && !zero_nb) ? eF[nbi[q]] : 0.0f;
+    const float2 v = (has[q] && !zero_nb) ? e2[nbi[q]] : make_float2(0.0f, 0.0f);
+    enf[q] = v.x;
+    enF[q] = v.y;
   }
-  const float efc = first ? 0.0f : ef[own], eFc = first ? 0.0f : eF[own];
-  float B[6], dgf, dgF;
-  faces6(L, Bf[0], Bf[1], Bf[2], i, j, k, has, B);
-  const float flf = flux_lin(L, p.invh, p.Dfh, p.literal, i, efc, enf, has, B, dgf);
-  faces6(L, BF[0], BF[1], BF[2], i, j, k, has, B);
-  const float flF = flux_lin(L, p.invh, p.DFh, p.literal, i, eFc, enF, has, B, dgF);
+  const float2 ec = first ? make_float2(0.0f, 0.0f) : e2[own];
+  const float efc = ec.x, eFc = ec.y;
+  float Bf[6], BF[6], dgf, dgF;
+  faces6x2(L, H[0], H[1], H[2], i, j, k, has, Bf, BF);
+  const float flf = flux_lin(L, p.invh, p.Dfh, p.literal, i, efc, enf, has, Bf, dgf);
+  const float flF = flux_lin(L, p.invh, p.DFh, p.literal, i, eFc, enF, has, BF, dgF);
   const float4 cf = coef[own];
   const float2 r = res[own];
   // residuals of the correction equation at this cell
@@ -460,8 +480,7 @@ __device__ __forceinline__ void corr2_cell(const Nw32& p, int i, int j, int k,
   const float inv = __fdividef(1.0f, det);
   const float nf = efc + (e * rhof + bb * rhoF) * inv;
   const float nF = eFc + (d * rhof + a * rhoF) * inv;
-  ef[own] = nf;
-  eF[own] = nF;
+  e2[own] = make_float2(nf, nF);
   if (fst) {
     // last black colour of the iteration: add the corrections to the state,
     // for this cell and for the red cell that shares its pair (2t, 2t+1),
@@ -471,8 +490,9 @@ __device__ __forceinline__ void corr2_cell(const Nw32& p, int i, int j, int k,
     const int ir = i ^ 1;
     if (ir < L.nx) {
       const ix cr = c - (ix)i + (ix)ir;
-      fst[cr] = df_add(fst[cr], ef[oth]);
-      Fst[cr] = df_add(Fst[cr], eF[oth]);
+      const float2 er = e2[oth];
+      fst[cr] = df_add(fst[cr], er.x);
+      Fst[cr] = df_add(Fst[cr], er.y);
     }
   }
 }

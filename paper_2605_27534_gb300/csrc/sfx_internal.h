@@ -36,8 +36,7 @@ struct F32Scratch {
   bool ready = false;
   float* Bf[3] = {};
   float* BF[3] = {};
-  __half* Hf[3] = {};     // the same drifts in half precision (correction sweeps)
-  __half* HF[3] = {};
+  __half2* H2[3] = {};    // (B_f, B_F) per face in half precision (correction sweeps)
   float2* fstar = nullptr;
   float2* Fstar = nullptr;
   float* dsig = nullptr;   // sigma - sigma0
@@ -63,7 +62,8 @@ struct F32Scratch {
   const void* inc_ptr[3] = {nullptr, nullptr, nullptr};   // f, F, phi of that step
   double inc_key[9] = {};           // dt and parameters of that step
   double drift_key[3] = {0, 0, 0};
-  float *ef = nullptr, *eF = nullptr;   // corrections
+  float *ef = nullptr, *eF = nullptr;   // corrections (Picard defect correction)
+  float2* e2 = nullptr;                 // Newton corrections (e_f, e_F), colour-packed
   float *rf = nullptr, *rF = nullptr;   // residuals
   float *lf = nullptr, *lF = nullptr;   // diagonals of the linearised problems
 };
