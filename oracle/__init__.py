@@ -91,6 +91,7 @@ def lib():
         L.orc_eos.argtypes = [G, Pp, _P, _P, _P, _P]
         L.orc_marangoni.argtypes = [G, Pp, _P, _P, _P, C.c_int, _P, _P]
         L.orc_capillary.argtypes = [G, _P, _P, _P, C.c_double, _P, _P]
+        L.orc_acdi_step.argtypes = [G, _P, _P, _P, C.c_double, C.c_double, C.c_double, _P, _P]
         L.orc_plic_volume.restype = C.c_double
         L.orc_plic_volume.argtypes = [C.c_int, _P, C.c_double]
         L.orc_plic_area.restype = C.c_double
@@ -268,6 +269,19 @@ def marangoni(g, p, f, phi, Cf, dm_mode=1):
     lib().orc_marangoni(C.byref(cgrid(g)), C.byref(cparams(p)), _ptr(_arr(f)), _ptr(_arr(phi)),
                         _ptr(_arr(Cf)), int(dm_mode), _ptr(sig), _ptr(force))
     return sig, force
+
+
+def acdi_step(g, phi, dt, zeta, eps, ux=None, uy=None, uz=None):
+    """One ACDI step of phi (advection when ux is given); returns a new array."""
+    out = np.empty((g.nz, g.ny, g.nx))
+    if ux is None:
+        lib().orc_acdi_step(C.byref(cgrid(g)), None, None, None, float(dt), float(zeta), float(eps),
+                            _ptr(_arr(phi)), _ptr(out))
+    else:
+        uzp = _arr(uz) if g.ndim == 3 else np.zeros(1)
+        lib().orc_acdi_step(C.byref(cgrid(g)), _ptr(_arr(ux)), _ptr(_arr(uy)), _ptr(uzp), float(dt),
+                            float(zeta), float(eps), _ptr(_arr(phi)), _ptr(out))
+    return out
 
 
 def capillary(g, phi, Cf, sigma, eps):

@@ -789,6 +789,79 @@ void orc_marangoni(const orc_grid* g, const orc_params* p, const double* f,
   free(n);
 }
 
+/* ------------------------------------------------ ACDI transport of phi */
+
+/* One step of the ACDI phase-field equation (Sec. 2.5):
+     d phi/dt + div(u phi) = div(zeta {eps grad phi
+                                - 1/4 (1 - tanh^2(psi/(2 eps))) grad psi/|grad psi|}),
+     psi = eps ln((phi + veps)/(1 - phi + veps)),  veps = 1e-6.
+   READING: the paper gives the model but not its discretisation.  The
+   advective part is the explicit BCG step of Sec. 3.1 (the step of f and
+   F; inflow faces carry phi = 1, fluid 2); the regularisation is explicit
+   (forward Euler) on the advected phi* in flux form with the central face
+   fluxes of Jain (2022): on the face between cells L and R along d,
+     a_f = zeta [eps (phi*_R - phi*_L)/h
+                 - 1/4 (1 - tanh^2(psi_f/(2 eps))) nbar_f],
+   psi_f = (psi_L + psi_R)/2 and nbar_f the mean of the two cells' d
+   components of n = grad psi/|grad psi| (centred differences with
+   zero-gradient ghosts, n = 0 where |grad psi| < 1e-30).  Wall faces carry
+   no flux, the axis face has zero area:
+     phi = phi* + dt/V_c sum_f (+-) A_f a_f. */
+void orc_acdi_step(const orc_grid* g, const double* ux, const double* uy,
+                   const double* uz, double dt, double zeta, double eps,
+                   const double* phi, double* phi_out) {
+  const double veps = 1e-6;
+  size_t N = ncell_of(g);
+  int D = ndim_of(g);
+  double* ps = (double*)malloc(N * sizeof(double));
+  double* psi = (double*)malloc(N * sizeof(double));
+  double* n = (double*)malloc((size_t)D * N * sizeof(double));
+  if (ux)
+    orc_advect_bcg(g, ux, uy, uz, dt, phi, 1.0, ps);
+  else
+    memcpy(ps, phi, N * sizeof(double));
+  for (size_t c = 0; c < N; ++c)
+    psi[c] = eps * log((ps[c] + veps) / (1.0 - ps[c] + veps));
+  for (int k = 0; k < g->nz; ++k)
+    for (int j = 0; j < g->ny; ++j)
+      for (int i = 0; i < g->nx; ++i) {
+        size_t c = idx(g, i, j, k);
+        double gp[3] = {0, 0, 0}, m2 = 0;
+        for (int d = 0; d < D; ++d) {
+          gp[d] = (nb_or_self(g, psi, i, j, k, d, +1) -
+                   nb_or_self(g, psi, i, j, k, d, -1)) / (2.0 * g->h);
+          m2 += gp[d] * gp[d];
+        }
+        double m = sqrt(m2);
+        for (int d = 0; d < D; ++d) n[(size_t)d * N + c] = m < 1e-30 ? 0.0 : gp[d] / m;
+      }
+  for (int k = 0; k < g->nz; ++k)
+    for (int j = 0; j < g->ny; ++j)
+      for (int i = 0; i < g->nx; ++i) {
+        size_t c = idx(g, i, j, k);
+        double div = 0.0;
+        for (int d = 0; d < D; ++d) {
+          for (int s = -1; s <= 1; s += 2) {
+            int a = i, b = j, e = k;
+            if (!shift(g, d, s, &a, &b, &e)) continue;   /* wall or axis face */
+            size_t o = idx(g, a, b, e);
+            /* L and R along +d */
+            size_t cL = s < 0 ? o : c, cR = s < 0 ? c : o;
+            double A = s < 0 ? face_area(g, d, i, j, k) : face_area(g, d, a, b, e);
+            double psif = 0.5 * (psi[cL] + psi[cR]);
+            double t = tanh(psif / (2.0 * eps));
+            double nbar = 0.5 * (n[(size_t)d * N + cL] + n[(size_t)d * N + cR]);
+            double af = zeta * (eps * (ps[cR] - ps[cL]) / g->h - 0.25 * (1.0 - t * t) * nbar);
+            div += s * A * af;
+          }
+        }
+        phi_out[c] = ps[c] + dt * div / orc_cell_volume(g, i, j, k);
+      }
+  free(ps);
+  free(psi);
+  free(n);
+}
+
 /* ------------------------------------------------------ capillary force */
 
 /* Capillary force F_cap = sigma kappa delta_s n (Sec. 2.4) with the mean

@@ -151,6 +151,13 @@ void orc_marangoni(const orc_grid* g, const orc_params* p, const double* f,
 double orc_plic_volume(int dim, const double* m, double alpha);
 double orc_plic_area(int dim, const double* m, double C);
 
+/* One step of the ACDI phase-field equation (Sec. 2.5): BCG advection of
+   phi (skipped when ux is NULL), then the explicit central regularisation
+   flux with velocity scale zeta and width eps; phi_out may not alias phi. */
+void orc_acdi_step(const orc_grid* g, const double* ux, const double* uy,
+                   const double* uz, double dt, double zeta, double eps,
+                   const double* phi, double* phi_out);
+
 /* Capillary force F_cap = sigma kappa delta_s n, kappa = -div n (flux
    form over the faces), delta_s = |grad C| (Sec. 2.2, 2.4).  force holds
    ndim component arrays; kappa (may be NULL) receives the curvature. */

@@ -1,0 +1,154 @@
+"""Pins of the oracle's ACDI step of the phase field (Sec. 2.5, central face
+fluxes of the regularisation after a BCG advection): the equilibrium tanh
+profile of width eps and its O((h/eps)^2) discrete residual, relaxation of
+a wider profile to the thickness integral eps, exact conservation in closed
+divergence-free flows (planar, axisymmetric, 3D), commutation with an exact
+Courant-1 shift, and mirror symmetry."""
+import numpy as np
+
+import oracle
+import workloads as W
+
+
+def _slab(n, L=1.0):
+    """A planar strip n x 4 of width L along x."""
+    h = L / n
+    g = W.Grid(W.PLANAR, n, 4, 1, h)
+    x = (np.arange(n) + 0.5) * h
+    return g, np.broadcast_to(x[None, None, :], g.shape).copy()
+
+
+def _tanh_profile(x, x0, w):
+    # phi = 1/2 (1 + tanh((x - x0)/(2 w))): phi -> 1 (fluid 2) for x > x0
+    return 0.5 * (1.0 + np.tanh((x - x0) / (2.0 * w)))
+
+
+def test_equilibrium_profile_residual_is_second_order():
+    """The continuous tanh profile of width eps is a steady state of the
+    regularisation; the discrete rate |phi1 - phi0|/(dt zeta) of its
+    sampled profile falls by ~4 per halving of h (eps fixed)."""
+    eps, zeta, dt = 0.05, 1.0, 1e-5
+    rates = []
+    for n in (64, 128, 256):
+        g, X = _slab(n)
+        phi0 = _tanh_profile(X, 0.5, eps)
+        phi1 = oracle.acdi_step(g, phi0, dt, zeta, eps)
+        rates.append(np.abs(phi1 - phi0).max() / (dt * zeta))
+    assert rates[2] < 2e-3, rates
+    assert rates[0] / rates[1] > 3.5 and rates[1] / rates[2] > 3.5, rates
+
+
+def test_wide_profile_relaxes_to_the_equilibrium_width():
+    """A profile of width 2 eps relaxes (u = 0) to the tanh of width eps: the
+    thickness integral sum phi (1 - phi) h matches that of the equilibrium
+    tanh over the box (eps up to the tails) to 1e-4, and the profile matches
+    the tanh whose position keeps the mass, the error falling as (h/eps)^2."""
+    eps, zeta = 0.05, 1.0
+    errs = []
+    for n in (64, 128):
+        g, X = _slab(n)
+        h = g.h
+        dt = 0.2 * h * h / (zeta * eps)
+        phi = _tanh_profile(X, 0.5, 2 * eps)
+        mass0 = phi.sum()
+        for _ in range(int(3.0 / dt)):     # ~15 decay times of the width
+            phi = oracle.acdi_step(g, phi, dt, zeta, eps)
+        assert abs(phi.sum() - mass0) <= 1e-12 * mass0
+        thick = (phi * (1 - phi))[0, 0].sum() * h
+        x = X[0, 0]
+        # position of the equilibrium tanh with the same mass: 1 - x0 = mass
+        x0 = 1.0 - phi[0, 0].sum() * h
+        # its thickness integral over the box [0, 1] (eps up to the tails)
+        want = 0.5 * eps * (np.tanh((1.0 - x0) / (2 * eps)) + np.tanh(x0 / (2 * eps)))
+        errs.append((abs(thick / want - 1.0),
+                     np.abs(phi[0, 0] - _tanh_profile(x, x0, eps)).max()))
+    assert errs[0][0] < 1e-4 and errs[1][0] < 1e-4, errs
+    assert errs[1][1] < 1e-4 and errs[0][1] / errs[1][1] > 3.5, errs
+
+
+def _circle_phi(g, xc, yc, R, eps):
+    x = (np.arange(g.nx) + 0.5) * g.h
+    y = (np.arange(g.ny) + 0.5) * g.h
+    r = np.hypot(x[None, :] - xc, y[:, None] - yc)[None]
+    return _tanh_profile(r, R, eps)
+
+
+def _closed_axi_faces(nr, nz, h):
+    """Ring fluxes from Psi = r^2 sin^2(pi r/R) sin^2(pi z/Z), zero on the
+    walls: no flow through them, and divergence-free per ring cell."""
+    rv = np.arange(nr + 1) * h
+    zv = np.arange(nz + 1) * h
+    Z, Rr = np.meshgrid(zv, rv, indexing="ij")
+    Psi = Rr ** 2 * np.sin(np.pi * Rr / rv[-1]) ** 2 * np.sin(np.pi * Z / zv[-1]) ** 2
+    Psi[:, -1] = 0.0
+    Psi[0, :] = Psi[-1, :] = 0.0
+    flux_r = -2 * np.pi * (Psi[1:, :] - Psi[:-1, :])
+    area_r = 2 * np.pi * rv[None, :] * h
+    ur = np.where(area_r > 0, flux_r / np.where(area_r > 0, area_r, 1.0), 0.0)
+    flux_z = 2 * np.pi * (Psi[:, 1:] - Psi[:, :-1])
+    uz = flux_z / (np.pi * (rv[1:] ** 2 - rv[:-1] ** 2)[None, :])
+    return ur[None], uz[None]
+
+
+def test_conserved_in_closed_divergence_free_flow():
+    """Single-vortex flow (no normal velocity on the walls) on the planar
+    grid and in every plane of the 3D grid, a closed ring vortex on the
+    axisymmetric grid: sum V phi is kept to round-off over 20 steps."""
+    n = 48
+    g = W.Grid(W.PLANAR, n, n, 1, 1.0 / n)
+    ux, uy = W.single_vortex_faces(n, g.h, 0.0, 4.0)
+    cases = [(g, _circle_phi(g, 0.5, 0.75, 0.15, 0.75 * g.h), (ux, uy, None))]
+    ga = W.Grid(W.AXI, 24, 48, 1, 1.0 / 24)
+    ur, uz = _closed_axi_faces(24, 48, ga.h)
+    r = (np.arange(24) + 0.5) * ga.h
+    z = (np.arange(48) + 0.5) * ga.h
+    rho = np.hypot(r[None, :], z[:, None] - 1.0)[None]
+    cases.append((ga, _tanh_profile(rho, 0.3, 0.75 * ga.h), (ur, uz, None)))
+    n3 = 16
+    g3 = W.Grid(W.CART3D, n3, n3, n3, 1.0 / n3)
+    vx, vy = W.single_vortex_faces(n3, g3.h, 0.0, 4.0)
+    u3 = (np.repeat(vx, n3, axis=0), np.repeat(vy, n3, axis=0), np.zeros((n3 + 1, n3, n3)))
+    c3 = (np.arange(n3) + 0.5) * g3.h
+    Z, Y, X = np.meshgrid(c3, c3, c3, indexing="ij")
+    rho3 = np.sqrt((X - 0.6) ** 2 + (Y - 0.5) ** 2 + (Z - 0.5) ** 2)
+    cases.append((g3, _tanh_profile(rho3, 0.25, 0.75 * g3.h), u3))
+    for gg, phi, u in cases:
+        V = oracle.cell_volumes(gg)
+        umax = max(np.abs(a).max() for a in u if a is not None)
+        dt = 0.25 * gg.h / umax
+        m0 = (V * phi).sum()
+        for _ in range(20):
+            phi = oracle.acdi_step(gg, phi, dt, 1.1 * umax, 0.75 * gg.h, *u)
+        assert abs((V * phi).sum() - m0) <= 1e-13 * m0, gg.geom
+        assert phi.min() > -1e-3 and phi.max() < 1 + 1e-3, gg.geom
+
+
+def test_commutes_with_an_exact_courant_one_shift():
+    """u = h/dt along x: the BCG step is an exact shift by one cell and the
+    regularisation is translation invariant, so away from the walls the step
+    equals the shifted step of the same profile at rest."""
+    n = 40
+    g = W.Grid(W.PLANAR, n, n, 1, 1.0 / n)
+    dt = 1e-3
+    u = g.h / dt
+    ux = np.full((1, n, n + 1), u)
+    uy = np.zeros((1, n + 1, n))
+    eps = 0.75 * g.h
+    phi0 = _circle_phi(g, 0.45, 0.5, 0.2, eps)
+    moved = oracle.acdi_step(g, phi0, dt, 1.1 * u, eps, ux, uy, None)
+    rest = oracle.acdi_step(g, np.roll(phi0, 1, axis=2), dt, 1.1 * u, eps)
+    inner = (slice(None), slice(3, -3), slice(4, -3))
+    assert np.abs(moved[inner] - rest[inner]).max() < 1e-13
+
+
+def test_centred_circle_stays_mirror_symmetric():
+    n = 40
+    g = W.Grid(W.PLANAR, n, n, 1, 1.0 / n)
+    eps = 0.75 * g.h
+    phi = _circle_phi(g, 0.5, 0.5, 0.2, eps)
+    for _ in range(5):
+        phi = oracle.acdi_step(g, phi, 2e-3, 1.0, eps)
+    p = phi[0]
+    assert np.abs(p - p[:, ::-1]).max() < 1e-14
+    assert np.abs(p - p[::-1, :]).max() < 1e-14
+    assert np.abs(p - p.T).max() < 1e-14
