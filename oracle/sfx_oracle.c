@@ -804,9 +804,18 @@ void orc_marangoni(const orc_grid* g, const orc_params* p, const double* f,
                  - 1/4 (1 - tanh^2(psi_f/(2 eps))) nbar_f],
    psi_f = (psi_L + psi_R)/2 and nbar_f the mean of the two cells' d
    components of n = grad psi/|grad psi| (centred differences with
-   zero-gradient ghosts, n = 0 where |grad psi| < 1e-30).  Wall faces carry
-   no flux, the axis face has zero area:
-     phi = phi* + dt/V_c sum_f (+-) A_f a_f. */
+   zero-gradient ghosts).  Wall faces carry no flux, the axis face has zero
+   area:
+     phi = phi* + dt/V_c sum_f (+-) A_f a_f.
+   READING: Sec. 2.5 defines the normal as grad psi/|grad psi| only.  Where
+   phi saturates (1 - phi or phi far below veps) psi is flat to round-off
+   and the direction of its gradient is set by the last bits of phi, while
+   1 - tanh^2 there is ~4 veps, not 0: the regularisation would then move
+   phi by ~zeta veps dt/h per step in a direction set by round-off.  As for
+   the normal of the surfactant drifts, n = 0 where |grad psi| is below
+   ORC_ACDI_KAPPA times its equilibrium value 1 (psi is a signed distance
+   at equilibrium), or below 1e-30. */
+#define ORC_ACDI_KAPPA 1e-3
 void orc_acdi_step(const orc_grid* g, const double* ux, const double* uy,
                    const double* uz, double dt, double zeta, double eps,
                    const double* phi, double* phi_out) {
@@ -833,7 +842,8 @@ void orc_acdi_step(const orc_grid* g, const double* ux, const double* uy,
           m2 += gp[d] * gp[d];
         }
         double m = sqrt(m2);
-        for (int d = 0; d < D; ++d) n[(size_t)d * N + c] = m < 1e-30 ? 0.0 : gp[d] / m;
+        int flat = m < 1e-30 || m < ORC_ACDI_KAPPA;
+        for (int d = 0; d < D; ++d) n[(size_t)d * N + c] = flat ? 0.0 : gp[d] / m;
       }
   for (int k = 0; k < g->nz; ++k)
     for (int j = 0; j < g->ny; ++j)

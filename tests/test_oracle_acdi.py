@@ -3,7 +3,8 @@ fluxes of the regularisation after a BCG advection): the equilibrium tanh
 profile of width eps and its O((h/eps)^2) discrete residual, relaxation of
 a wider profile to the thickness integral eps, exact conservation in closed
 divergence-free flows (planar, axisymmetric, 3D), commutation with an exact
-Courant-1 shift, and mirror symmetry."""
+Courant-1 shift, mirror symmetry, and the reading of the normal where psi
+is flat (no normal there, so that the step is well conditioned)."""
 import numpy as np
 
 import oracle
@@ -73,23 +74,6 @@ def _circle_phi(g, xc, yc, R, eps):
     return _tanh_profile(r, R, eps)
 
 
-def _closed_axi_faces(nr, nz, h):
-    """Ring fluxes from Psi = r^2 sin^2(pi r/R) sin^2(pi z/Z), zero on the
-    walls: no flow through them, and divergence-free per ring cell."""
-    rv = np.arange(nr + 1) * h
-    zv = np.arange(nz + 1) * h
-    Z, Rr = np.meshgrid(zv, rv, indexing="ij")
-    Psi = Rr ** 2 * np.sin(np.pi * Rr / rv[-1]) ** 2 * np.sin(np.pi * Z / zv[-1]) ** 2
-    Psi[:, -1] = 0.0
-    Psi[0, :] = Psi[-1, :] = 0.0
-    flux_r = -2 * np.pi * (Psi[1:, :] - Psi[:-1, :])
-    area_r = 2 * np.pi * rv[None, :] * h
-    ur = np.where(area_r > 0, flux_r / np.where(area_r > 0, area_r, 1.0), 0.0)
-    flux_z = 2 * np.pi * (Psi[:, 1:] - Psi[:, :-1])
-    uz = flux_z / (np.pi * (rv[1:] ** 2 - rv[:-1] ** 2)[None, :])
-    return ur[None], uz[None]
-
-
 def test_conserved_in_closed_divergence_free_flow():
     """Single-vortex flow (no normal velocity on the walls) on the planar
     grid and in every plane of the 3D grid, a closed ring vortex on the
@@ -99,7 +83,7 @@ def test_conserved_in_closed_divergence_free_flow():
     ux, uy = W.single_vortex_faces(n, g.h, 0.0, 4.0)
     cases = [(g, _circle_phi(g, 0.5, 0.75, 0.15, 0.75 * g.h), (ux, uy, None))]
     ga = W.Grid(W.AXI, 24, 48, 1, 1.0 / 24)
-    ur, uz = _closed_axi_faces(24, 48, ga.h)
+    ur, uz = W.ring_vortex_faces_axi(24, 48, ga.h)
     r = (np.arange(24) + 0.5) * ga.h
     z = (np.arange(48) + 0.5) * ga.h
     rho = np.hypot(r[None, :], z[:, None] - 1.0)[None]
@@ -152,3 +136,36 @@ def test_centred_circle_stays_mirror_symmetric():
     assert np.abs(p - p[:, ::-1]).max() < 1e-14
     assert np.abs(p - p[::-1, :]).max() < 1e-14
     assert np.abs(p - p.T).max() < 1e-14
+
+
+def test_step_is_well_conditioned_where_phi_saturates():
+    """Where phi saturates psi is flat to round-off and its gradient has no
+    direction; with n = 0 there (|grad psi| < 1e-3) perturbing phi by 1e-15
+    relative moves a step by < 1e-12.  With the round-off direction kept it
+    moves by ~1e-6 (1 - tanh^2 is ~4e-6 there, not 0)."""
+    n = 64
+    g = W.Grid(W.PLANAR, n, n, 1, 1.0 / n)
+    eps = 0.75 * g.h
+    phi0 = _circle_phi(g, 0.5, 0.55, 0.2, eps)
+    rng = np.random.default_rng(3)
+    phi1 = phi0 * (1.0 + 1e-15 * rng.standard_normal(phi0.shape))
+    for u in ((None, None, None), W.single_vortex_faces(n, g.h, 0.0, 4.0) + (None,)):
+        a = oracle.acdi_step(g, phi0, 0.3 * g.h, 1.1, eps, *u)
+        b = oracle.acdi_step(g, phi1, 0.3 * g.h, 1.1, eps, *u)
+        assert np.abs(a - b).max() < 1e-12
+
+
+def test_flat_plateau_only_diffuses():
+    """A saturated plateau phi = 1e-12 (1 + noise) far below veps: psi is
+    flat, n = 0 everywhere, and the step is the pure discrete diffusion
+    zeta eps lap(phi) of the noise (no-flux walls)."""
+    n = 16
+    g = W.Grid(W.PLANAR, n, n, 1, 1.0 / n)
+    rng = np.random.default_rng(5)
+    phi = 1e-12 * (1.0 + rng.uniform(0, 1, g.shape))
+    eps, zeta, dt = 0.75 * g.h, 1.0, 1e-4
+    out = oracle.acdi_step(g, phi, dt, zeta, eps)
+    p = np.pad(phi[0], 1, mode="edge")
+    lap = (p[1:-1, 2:] + p[1:-1, :-2] + p[2:, 1:-1] + p[:-2, 1:-1] - 4 * p[1:-1, 1:-1]) / g.h ** 2
+    want = dt * zeta * eps * lap
+    np.testing.assert_allclose(out[0] - phi[0], want, rtol=0, atol=1e-9 * np.abs(want).max())

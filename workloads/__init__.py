@@ -309,6 +309,25 @@ def hr_faces_axi(nr, nz, h, zc, R, U=1.0, lam=0.01):
     return ur[None], uz[None]
 
 
+def ring_vortex_faces_axi(nr, nz, h):
+    """A closed axisymmetric ring vortex: ring fluxes from the stream
+    function Psi = r^2 sin^2(pi r/R) sin^2(pi z/Z) on the box [0, R] x
+    [0, Z] (R = nr h, Z = nz h), zero on every wall, so no flow crosses
+    them and every ring cell is divergence-free."""
+    rv = np.arange(nr + 1) * h
+    zv = np.arange(nz + 1) * h
+    Z, Rr = np.meshgrid(zv, rv, indexing="ij")
+    Psi = Rr ** 2 * np.sin(np.pi * Rr / rv[-1]) ** 2 * np.sin(np.pi * Z / zv[-1]) ** 2
+    Psi[:, -1] = 0.0
+    Psi[0, :] = Psi[-1, :] = 0.0
+    flux_r = -2 * np.pi * (Psi[1:, :] - Psi[:-1, :])
+    area_r = 2 * np.pi * rv[None, :] * h
+    ur = np.where(area_r > 0, flux_r / np.where(area_r > 0, area_r, 1.0), 0.0)
+    flux_z = 2 * np.pi * (Psi[:, 1:] - Psi[:, :-1])
+    uz = flux_z / (np.pi * (rv[1:] ** 2 - rv[:-1] ** 2)[None, :])
+    return ur[None], uz[None]
+
+
 def solid_rotation_faces(n, h, centre, omega):
     """Solid-body rotation about `centre` from psi = -omega/2 |x - c|^2."""
     x = np.arange(n + 1) * h - centre[0]
