@@ -814,8 +814,11 @@ void orc_marangoni(const orc_grid* g, const orc_params* p, const double* f,
    phi by ~zeta veps dt/h per step in a direction set by round-off.  As for
    the normal of the surfactant drifts, n = 0 where |grad psi| is below
    ORC_ACDI_KAPPA times its equilibrium value 1 (psi is a signed distance
-   at equilibrium), or below 1e-30. */
-#define ORC_ACDI_KAPPA 1e-3
+   at equilibrium), or below 1e-30.  |grad psi| falls below 0.1 only where
+   veps dominates psi (phi or 1 - phi below ~0.1 veps); a threshold of 1e-3
+   still left cells whose normal turned by 1e-6 under a 1e-15 change of
+   phi. */
+#define ORC_ACDI_KAPPA 0.1
 void orc_acdi_step(const orc_grid* g, const double* ux, const double* uy,
                    const double* uz, double dt, double zeta, double eps,
                    const double* phi, double* phi_out) {
