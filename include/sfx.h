@@ -239,6 +239,27 @@ sfx_status sfx_marangoni_force(sfx_ctx* ctx, const sfx_params* params,
                                const void* C, int dm_mode, void* sigma,
                                void* force, void* stream);
 
+/* One step of the ACDI phase-field equation (Sec. 2.5):
+     d phi/dt + div(u phi) = div(zeta {eps grad phi
+                               - 1/4 (1 - tanh^2(psi/(2 eps))) grad psi/|grad psi|}),
+     psi = eps ln((phi + 1e-6)/(1 - phi + 1e-6)).
+   The advective part is the BCG step of sfx_advect (skipped when ux is
+   NULL; inflow faces carry phi = 1); the regularisation is explicit, in
+   flux form, with central face fluxes: eps (phi_R - phi_L)/h, and the mean
+   of the two cells' unit normals of psi (centred differences; 0 where
+   |grad psi| < 0.1, i.e. where phi saturates and psi is flat to round-off)
+   times 1 - tanh^2 of the face mean of psi/(2 eps).  Wall faces carry no
+   flux.
+   The paper takes zeta = 1.1 max|u| and eps = 0.75 h.  phi: double, in
+   place, in both precisions; ux, uy, uz: face velocities in the context
+   precision (uz NULL in 2D).  Stable for zeta eps dt/h^2 <= 1/(2 ndim) and
+   the BCG Courant limit.  The context allocates (3 + ndim) N doubles of
+   scratch on first use.  SFX_ERR_ARG on a null phi, dt <= 0, eps <= 0 or
+   zeta < 0. */
+sfx_status sfx_acdi_step(sfx_ctx* ctx, const void* ux, const void* uy,
+                         const void* uz, double dt, double zeta, double eps,
+                         double* phi, void* stream);
+
 /* Capillary force (Sec. 2.4, curvature of Sec. 2.2):
      F_cap = sigma kappa delta_s n,  kappa = -div n,  delta_s = |grad C|,
    n = grad phi/|grad phi| at cell centres (centred differences, 0 where

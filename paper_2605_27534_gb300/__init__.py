@@ -150,6 +150,11 @@ class Context:
                                          int(dm_mode), _ptr(sigma), _ptr(force), _stream()),
                "sfx_marangoni_force")
 
+    def sfx_acdi_step(self, phi, dt, zeta, eps, ux=None, uy=None, uz=None):
+        """One ACDI step of the double phase field `phi`, in place."""
+        _check(lib().sfx_acdi_step(self._h, _ptr(ux), _ptr(uy), _ptr(uz), float(dt), float(zeta),
+                                   float(eps), _ptr(phi), _stream()), "sfx_acdi_step")
+
     def sfx_capillary_force(self, params, phi, Cf, sigma, force, kappa=None):
         """F_cap = sigma kappa |grad C| n into `force` (ndim x N), the
         curvature into `kappa` when given."""

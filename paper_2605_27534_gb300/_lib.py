@@ -25,7 +25,7 @@ EXPORTS = [
     "sfx_set_tuning", "sfx_batch_create", "sfx_batch_destroy",
     "sfx_batch_layout", "sfx_batch_set_schedule", "sfx_batch_step", "sfx_batch_stats",
     "sfx_batch_autotune", "sfx_batch_work", "sfx_f_from_gamma", "sfx_marangoni_loss",
-    "sfx_adjoint_apply", "sfx_adjoint_step", "sfx_vof_advect", "sfx_capillary_force", "sfx_batch_reuse_phi",
+    "sfx_adjoint_apply", "sfx_adjoint_step", "sfx_vof_advect", "sfx_capillary_force", "sfx_acdi_step", "sfx_batch_reuse_phi",
 ]
 SFX_TUNE_FUSED_SWEEP = 0
 SFX_TUNE_F32_SOLVER = 1
@@ -151,6 +151,8 @@ def load(path: str = SO_PATH):
     L.sfx_adjoint_step.argtypes = [vp, C.POINTER(Params), vp, vp, vp, dp, vp, vp,
                                    C.POINTER(C.c_double), C.POINTER(SolveOpts),
                                    C.POINTER(StepStats), vp]
+    L.sfx_acdi_step.restype = C.c_int
+    L.sfx_acdi_step.argtypes = [vp, vp, vp, vp, dp, dp, dp, vp, vp]
     L.sfx_capillary_force.restype = C.c_int
     L.sfx_capillary_force.argtypes = [vp, C.POINTER(Params), vp, vp, vp, vp, vp, vp]
     L.sfx_vof_advect.restype = C.c_int

@@ -123,6 +123,7 @@ struct sfx_ctx {
   float* chi32 = nullptr;            // SFX_F32 redistancing: chi0, two iterates
   double* vofH = nullptr;            // VoF: indicator H, face fluxes Q
   double* vofQ = nullptr;
+  double* acdi = nullptr;            // ACDI: phi*, r, psi, unit normals
 };
 
 namespace sfx {
@@ -164,6 +165,9 @@ sfx_status surfactant_step(sfx_ctx* c, const sfx_params* p, const void* phi, con
 // sfx_solver.cu: drift faces of both problems from a double phi
 sfx_status drift_faces64(sfx_ctx* c, const double* phi, double Df, double DF, double eps,
                          double* const* Bf, double* const* BF, cudaStream_t s);
+// sfx_acdi.cu
+sfx_status acdi_step(sfx_ctx* c, const void* ux, const void* uy, const void* uz, double dt,
+                     double zeta, double eps, double* phi, cudaStream_t s);
 // sfx_capillary.cu
 sfx_status capillary(sfx_ctx* c, const sfx_params* p, const double* phi, const void* C,
                      const void* sigma, void* kappa, void* force, cudaStream_t s);
