@@ -45,9 +45,9 @@ SAMPLE_N = 64          # oracle sample: centred 64^3 block of the same grid
 # withdrawn (None) as soon as those sources differ from the captured ones.
 NCU_TRAFFIC = {
     ("smooth_fine", "f32", 3): {
-        "bytes_per_cell": 154.4e6 / 160 ** 3,
+        "bytes_per_cell": (6 * 139.33e6 + 239.17e6) / 7 / 160 ** 3,
         "sources": ["sfx_f32.cu", "sfx_f32_dev.cuh", "sfx_df.cuh", "sfx_common.cuh"],
-        "sha256_16": "97b3f73e6ee1e6bd",
+        "sha256_16": "c40fed5129b4990d",
         "capture": "profiles/corr2_hr3d160_f32.md (160^3, launches 5-7, weighted 6:1 as in an "
                    "iteration of 4 sweeps), scaled by the cell count",
     },
@@ -280,6 +280,7 @@ def run_gpu_vortex(a, rank, world, local_rank):
     torch.cuda.set_device(dev)
     r32 = vortex_run(a, dev, a.steps, sfx.SFX_F32, warmup=a.warmup)
     r64 = vortex_run(a, dev, max(1, a.steps // 10), sfx.SFX_F64, warmup=1)
+    racdi = vortex_run(a, dev, a.steps, sfx.SFX_F32, warmup=a.warmup, rebuild_every=10)
     r32["ms_per_step"] = max_over_ranks(r32["ms_per_step"], world, dev)
     if rank != 0:
         return
@@ -295,6 +296,7 @@ def run_gpu_vortex(a, rank, world, local_rank):
                    "cells": r32["cells"], "l2": "working set L2-resident (no HBM claim)",
                    "parallelism": "replicas%d" % world},
         "roofline": None, "cpu_baseline": None, "e2e": None, "f64_path": r64,
+        "f32_acdi_rebuild_every_10": racdi,
         "kernels_one_step_ms": r32["one_step_kernel_ms"],
         "newton_iters": r32["newton_or_picard_iters"],
         "speedup_vs_f64": r64["ms_per_step"] / ms, "gpu_launches": None,
@@ -469,6 +471,7 @@ def run_gpu(a, case, rank, world, local_rank):
     vortex = None
     if a.vortex_steps > 0:
         vortex = {"f32": vortex_run(a, dev, a.vortex_steps, sfx.SFX_F32),
+                  "f32_acdi": vortex_run(a, dev, a.vortex_steps, sfx.SFX_F32, rebuild_every=10),
                   "f64": vortex_run(a, dev, max(1, a.vortex_steps // 10), sfx.SFX_F64)}
     batch = None
     if a.batch_steps > 0:
@@ -500,12 +503,14 @@ def run_gpu(a, case, rank, world, local_rank):
     print(json.dumps(line))
 
 
-def vortex_run(a, dev, steps, prec, warmup=3):
+def vortex_run(a, dev, steps, prec, warmup=3, rebuild_every=1):
     """The 2D moving-interface workload: 512^2 single vortex (T = 4) with
     the soluble surfactant (Bi = Da = 1), from t = 0.  One step = geometric
-    VoF advection of C, the phase-field rebuild from C, the coupled step
-    with the same velocity, EOS and Marangoni force.  The face velocities
-    are cos(pi t/T) times the t = 0 field (the stream function factorises),
+    VoF advection of C, the phase field (rebuilt from C, or with
+    rebuild_every > 1 carried by one ACDI step with zeta = 1.1 max|u| and
+    rebuilt from C every rebuild_every steps), the coupled step with the
+    same velocity, EOS and Marangoni force.  The face velocities are
+    cos(pi t/T) times the t = 0 field (the stream function factorises),
     scaled on the device before each step (input preparation)."""
     import torch
     import paper_2605_27534_gb300 as sfx
@@ -515,7 +520,9 @@ def vortex_run(a, dev, steps, prec, warmup=3):
     f32 = prec == sfx.SFX_F32
     vt = torch.float32 if f32 else torch.float64
     ctx = sfx.Context.for_grid(g, prec)
-    u0 = [torch.from_numpy(u).to(dev, vt) for u in W.single_vortex_faces(512, g.h, 0.0, T)]
+    u0h = W.single_vortex_faces(512, g.h, 0.0, T)
+    umax0 = max(float(np.abs(x).max()) for x in u0h)
+    u0 = [torch.from_numpy(x).to(dev, vt) for x in u0h]
     u = [torch.empty_like(x) for x in u0]
     Cd = torch.from_numpy(c.C).to(dev)
     chi, phi, delta = torch.empty_like(Cd), torch.empty_like(Cd), torch.empty_like(Cd)
@@ -537,8 +544,12 @@ def vortex_run(a, dev, steps, prec, warmup=3):
         for x, x0 in zip(u, u0):
             torch.mul(x0, math.cos(math.pi * t / T), out=x)
         ctx.sfx_vof_advect(u[0], u[1], None, c.dt, Cd, n % 2)
-        ctx.sfx_phase_field_build(Cd, chi, phi, None, iters=c.redist_iters, dtau=c.dtau,
-                                  eps=p.eps)
+        if rebuild_every <= 1 or n % rebuild_every == 0:
+            ctx.sfx_phase_field_build(Cd, chi, phi, None, iters=c.redist_iters, dtau=c.dtau,
+                                      eps=p.eps)
+        else:
+            zeta = 1.1 * umax0 * abs(math.cos(math.pi * t / T))
+            ctx.sfx_acdi_step(phi, c.dt, zeta, p.eps, u[0], u[1])
         st = ctx.sfx_surfactant_step(p, phi, f, F, c.dt, u[0], u[1], None, opts=opts)
         if f32:
             Cw.copy_(Cd)
@@ -565,6 +576,8 @@ def vortex_run(a, dev, steps, prec, warmup=3):
     return {"ms_per_step": ms, "value": g.ncell / (ms * 1e-3), "unit": UNIT, "steps": steps,
             "cells": g.ncell, "newton_or_picard_iters": statistics.mean(pic[-steps:]),
             "dt": c.dt, "dtype": "f32" if f32 else "f64", "one_step_kernel_ms": kinds,
+            "phase_field": ("rebuilt from C every step" if rebuild_every <= 1 else
+                            "ACDI step, rebuilt from C every %d steps" % rebuild_every),
             "mass_C": float(Cd.sum().item()) * g.h * g.h}
 
 
