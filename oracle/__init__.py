@@ -91,7 +91,8 @@ def lib():
         L.orc_eos.argtypes = [G, Pp, _P, _P, _P, _P]
         L.orc_marangoni.argtypes = [G, Pp, _P, _P, _P, C.c_int, _P, _P]
         L.orc_capillary.argtypes = [G, _P, _P, _P, C.c_double, _P, _P]
-        L.orc_acdi_step.argtypes = [G, _P, _P, _P, C.c_double, C.c_double, C.c_double, _P, _P]
+        L.orc_acdi_step.argtypes = [G, _P, _P, _P, C.c_double, C.c_double, C.c_double, C.c_int,
+                                    _P, _P]
         L.orc_plic_volume.restype = C.c_double
         L.orc_plic_volume.argtypes = [C.c_int, _P, C.c_double]
         L.orc_plic_area.restype = C.c_double
@@ -271,16 +272,18 @@ def marangoni(g, p, f, phi, Cf, dm_mode=1):
     return sig, force
 
 
-def acdi_step(g, phi, dt, zeta, eps, ux=None, uy=None, uz=None):
-    """One ACDI step of phi (advection when ux is given); returns a new array."""
+def acdi_step(g, phi, dt, zeta, eps, ux=None, uy=None, uz=None, clip=False):
+    """One ACDI step of phi (advection when ux is given; result clipped to
+    [0, 1] with clip); returns a new array."""
     out = np.empty((g.nz, g.ny, g.nx))
+    cl = 1 if clip else 0
     if ux is None:
         lib().orc_acdi_step(C.byref(cgrid(g)), None, None, None, float(dt), float(zeta), float(eps),
-                            _ptr(_arr(phi)), _ptr(out))
+                            cl, _ptr(_arr(phi)), _ptr(out))
     else:
         uzp = _arr(uz) if g.ndim == 3 else np.zeros(1)
         lib().orc_acdi_step(C.byref(cgrid(g)), _ptr(_arr(ux)), _ptr(_arr(uy)), _ptr(uzp), float(dt),
-                            float(zeta), float(eps), _ptr(_arr(phi)), _ptr(out))
+                            float(zeta), float(eps), cl, _ptr(_arr(phi)), _ptr(out))
     return out
 
 

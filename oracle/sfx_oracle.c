@@ -814,13 +814,20 @@ void orc_marangoni(const orc_grid* g, const orc_params* p, const double* f,
    phi by ~zeta veps dt/h per step in a direction set by round-off.  As for
    the normal of the surfactant drifts, n = 0 where |grad psi| is below
    ORC_ACDI_KAPPA times its equilibrium value 1 (psi is a signed distance
-   at equilibrium), or below 1e-30.  |grad psi| falls below 0.1 only where
+   at equilibrium), or below 1e-30.
+   READING: with veps the model's phi saturates towards -veps and 1 + veps,
+   and the explicit step overshoots [0, 1] by O(veps) where phi saturates;
+   past 1 + veps the logarithm of psi has no value.  psi is formed from phi*
+   clipped to [0, 1]; with clip = 1 the result is clipped to [0, 1] as well
+   (the paper requires phi in [0, 1], and the surfactant step divides by
+   phi + eta, eta = veps), with clip = 0 it keeps the overshoots and sum V
+   phi is conserved exactly.  |grad psi| falls below 0.1 only where
    veps dominates psi (phi or 1 - phi below ~0.1 veps); a threshold of 1e-3
    still left cells whose normal turned by 1e-6 under a 1e-15 change of
    phi. */
 #define ORC_ACDI_KAPPA 0.1
 void orc_acdi_step(const orc_grid* g, const double* ux, const double* uy,
-                   const double* uz, double dt, double zeta, double eps,
+                   const double* uz, double dt, double zeta, double eps, int clip,
                    const double* phi, double* phi_out) {
   const double veps = 1e-6;
   size_t N = ncell_of(g);
@@ -832,8 +839,10 @@ void orc_acdi_step(const orc_grid* g, const double* ux, const double* uy,
     orc_advect_bcg(g, ux, uy, uz, dt, phi, 1.0, ps);
   else
     memcpy(ps, phi, N * sizeof(double));
-  for (size_t c = 0; c < N; ++c)
-    psi[c] = eps * log((ps[c] + veps) / (1.0 - ps[c] + veps));
+  for (size_t c = 0; c < N; ++c) {
+    double pc = ps[c] < 0.0 ? 0.0 : (ps[c] > 1.0 ? 1.0 : ps[c]);
+    psi[c] = eps * log((pc + veps) / (1.0 - pc + veps));
+  }
   for (int k = 0; k < g->nz; ++k)
     for (int j = 0; j < g->ny; ++j)
       for (int i = 0; i < g->nx; ++i) {
@@ -868,7 +877,9 @@ void orc_acdi_step(const orc_grid* g, const double* ux, const double* uy,
             div += s * A * af;
           }
         }
-        phi_out[c] = ps[c] + dt * div / orc_cell_volume(g, i, j, k);
+        double v = ps[c] + dt * div / orc_cell_volume(g, i, j, k);
+        if (clip) v = v < 0.0 ? 0.0 : (v > 1.0 ? 1.0 : v);
+        phi_out[c] = v;
       }
   free(ps);
   free(psi);

@@ -153,9 +153,10 @@ double orc_plic_area(int dim, const double* m, double C);
 
 /* One step of the ACDI phase-field equation (Sec. 2.5): BCG advection of
    phi (skipped when ux is NULL), then the explicit central regularisation
-   flux with velocity scale zeta and width eps; phi_out may not alias phi. */
+   flux with velocity scale zeta and width eps; clip = 1 clips the result
+   to [0, 1]; phi_out may not alias phi. */
 void orc_acdi_step(const orc_grid* g, const double* ux, const double* uy,
-                   const double* uz, double dt, double zeta, double eps,
+                   const double* uz, double dt, double zeta, double eps, int clip,
                    const double* phi, double* phi_out);
 
 /* Capillary force F_cap = sigma kappa delta_s n, kappa = -div n (flux

@@ -171,3 +171,25 @@ def test_flat_plateau_only_diffuses():
     lap = (p[1:-1, 2:] + p[1:-1, :-2] + p[2:, 1:-1] + p[:-2, 1:-1] - 4 * p[1:-1, 1:-1]) / g.h ** 2
     want = dt * zeta * eps * lap
     np.testing.assert_allclose(out[0] - phi[0], want, rtol=0, atol=1e-9 * np.abs(want).max())
+
+
+def test_overshoots_past_one_plus_veps_stay_finite_and_clip_bounds():
+    """phi* beyond 1 + veps (or below -veps) has no psi; psi is formed from
+    phi* clipped to [0, 1], so the step stays finite.  With clip the result
+    lies in [0, 1] and differs from the unclipped step only where that one
+    leaves [0, 1]; the unclipped step conserves sum V phi."""
+    n = 32
+    g = W.Grid(W.PLANAR, n, n, 1, 1.0 / n)
+    eps = 0.75 * g.h
+    phi = _circle_phi(g, 0.5, 0.5, 0.25, eps)
+    phi[phi > 1.0 - 1e-6] = 1.0 + 3e-6
+    phi[phi < 1e-6] = -3e-6
+    raw = oracle.acdi_step(g, phi, 2e-3, 1.0, eps)
+    cl = oracle.acdi_step(g, phi, 2e-3, 1.0, eps, clip=True)
+    assert np.all(np.isfinite(raw))
+    assert abs(raw.sum() - phi.sum()) <= 1e-13 * phi.sum()
+    assert cl.min() >= 0.0 and cl.max() <= 1.0
+    inside = (raw >= 0.0) & (raw <= 1.0)
+    assert np.array_equal(cl[inside], raw[inside])
+    assert np.array_equal(cl[raw > 1.0], np.ones(int((raw > 1.0).sum())))
+    assert np.all(cl[raw < 0.0] == 0.0)
