@@ -549,7 +549,7 @@ def vortex_run(a, dev, steps, prec, warmup=3, rebuild_every=1):
                                       eps=p.eps)
         else:
             zeta = 1.1 * umax0 * abs(math.cos(math.pi * t / T))
-            ctx.sfx_acdi_step(phi, c.dt, zeta, p.eps, u[0], u[1])
+            ctx.sfx_acdi_step(phi, c.dt, zeta, p.eps, u[0], u[1], clip=True)
         st = ctx.sfx_surfactant_step(p, phi, f, F, c.dt, u[0], u[1], None, opts=opts)
         if f32:
             Cw.copy_(Cd)

@@ -250,15 +250,19 @@ sfx_status sfx_marangoni_force(sfx_ctx* ctx, const sfx_params* params,
    |grad psi| < 0.1, i.e. where phi saturates and psi is flat to round-off)
    times 1 - tanh^2 of the face mean of psi/(2 eps).  Wall faces carry no
    flux.
-   The paper takes zeta = 1.1 max|u| and eps = 0.75 h.  phi: double, in
-   place, in both precisions; ux, uy, uz: face velocities in the context
+   The paper takes zeta = 1.1 max|u| and eps = 0.75 h.  With veps the
+   scheme's phi saturates towards -veps and 1 + veps and overshoots [0, 1]
+   by O(veps) there; psi is formed from phi clipped to [0, 1].  clip = 1
+   clips the result to [0, 1] (what the surfactant step needs: it divides
+   by phi + eta); clip = 0 keeps the overshoots and conserves sum V phi
+   exactly.  phi: double, in place, in both precisions; ux, uy, uz: face velocities in the context
    precision (uz NULL in 2D).  Stable for zeta eps dt/h^2 <= 1/(2 ndim) and
    the BCG Courant limit.  The context allocates (3 + ndim) N doubles of
    scratch on first use.  SFX_ERR_ARG on a null phi, dt <= 0, eps <= 0 or
    zeta < 0. */
 sfx_status sfx_acdi_step(sfx_ctx* ctx, const void* ux, const void* uy,
                          const void* uz, double dt, double zeta, double eps,
-                         double* phi, void* stream);
+                         int clip, double* phi, void* stream);
 
 /* Capillary force (Sec. 2.4, curvature of Sec. 2.2):
      F_cap = sigma kappa delta_s n,  kappa = -div n,  delta_s = |grad C|,

@@ -150,10 +150,12 @@ class Context:
                                          int(dm_mode), _ptr(sigma), _ptr(force), _stream()),
                "sfx_marangoni_force")
 
-    def sfx_acdi_step(self, phi, dt, zeta, eps, ux=None, uy=None, uz=None):
-        """One ACDI step of the double phase field `phi`, in place."""
+    def sfx_acdi_step(self, phi, dt, zeta, eps, ux=None, uy=None, uz=None, clip=False):
+        """One ACDI step of the double phase field `phi`, in place (result
+        clipped to [0, 1] with clip)."""
         _check(lib().sfx_acdi_step(self._h, _ptr(ux), _ptr(uy), _ptr(uz), float(dt), float(zeta),
-                                   float(eps), _ptr(phi), _stream()), "sfx_acdi_step")
+                                   float(eps), 1 if clip else 0, _ptr(phi), _stream()),
+               "sfx_acdi_step")
 
     def sfx_capillary_force(self, params, phi, Cf, sigma, force, kappa=None):
         """F_cap = sigma kappa |grad C| n into `force` (ndim x N), the

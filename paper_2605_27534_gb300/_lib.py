@@ -152,7 +152,7 @@ def load(path: str = SO_PATH):
                                    C.POINTER(C.c_double), C.POINTER(SolveOpts),
                                    C.POINTER(StepStats), vp]
     L.sfx_acdi_step.restype = C.c_int
-    L.sfx_acdi_step.argtypes = [vp, vp, vp, vp, dp, dp, dp, vp, vp]
+    L.sfx_acdi_step.argtypes = [vp, vp, vp, vp, dp, dp, dp, C.c_int, vp, vp]
     L.sfx_capillary_force.restype = C.c_int
     L.sfx_capillary_force.argtypes = [vp, C.POINTER(Params), vp, vp, vp, vp, vp, vp]
     L.sfx_vof_advect.restype = C.c_int

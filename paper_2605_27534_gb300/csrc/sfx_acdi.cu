@@ -13,7 +13,9 @@
 // the face needs no transcendental beyond the square root.
 //
 // Three passes over the grid: r and psi per cell, the unit normals of psi
-// per cell, then the face fluxes and the update.
+// per cell, then the face fluxes and the update (clipped to [0, 1] on
+// request: the scheme overshoots by O(veps) where phi saturates, and the
+// surfactant step divides by phi + eta).
 #include <algorithm>
 
 #include "sfx_internal.h"
@@ -34,7 +36,9 @@ __global__ void k_acdi_psi(size_t n, const double* __restrict__ ps, double eps,
                            double* __restrict__ r, double* __restrict__ psi) {
   for (size_t c = blockIdx.x * (size_t)blockDim.x + threadIdx.x; c < n;
        c += (size_t)gridDim.x * blockDim.x) {
-    const double p = ps[c];
+    // phi* may overshoot [0, 1] by O(veps) where it saturates; past
+    // 1 + veps psi would have no value, so it is formed from phi* in [0, 1]
+    const double p = fmin(fmax(ps[c], 0.0), 1.0);
     const double rc = (p + kAcdiVeps) / (1.0 - p + kAcdiVeps);
     r[c] = rc;
     psi[c] = eps * log(rc);
@@ -69,7 +73,8 @@ __global__ void k_acdi_normal(Level L, const double* __restrict__ psi, double* _
 // axis face has zero area
 __global__ void k_acdi_update(Level L, const double* __restrict__ ps,
                               const double* __restrict__ r, const double* __restrict__ nv,
-                              double zeta, double eps, double dt, double* __restrict__ phi) {
+                              double zeta, double eps, double dt, int clip,
+                              double* __restrict__ phi) {
   const size_t n = L.ncell();
   const int nd = L.ndim();
   const double invh = 1.0 / L.h;
@@ -101,14 +106,15 @@ __global__ void k_acdi_update(Level L, const double* __restrict__ ps,
         div += (double)s * w * af;
       }
     }
-    phi[c] = pc + dt * div * invh;
+    const double v = pc + dt * div * invh;
+    phi[c] = clip ? fmin(fmax(v, 0.0), 1.0) : v;
   }
 }
 
 }  // namespace
 
 sfx_status acdi_step(sfx_ctx* c, const void* ux, const void* uy, const void* uz, double dt,
-                     double zeta, double eps, double* phi, cudaStream_t s) {
+                     double zeta, double eps, int clip, double* phi, cudaStream_t s) {
   const Level& L = c->lev[0].lv;
   const size_t n = L.ncell();
   if (!c->acdi) {
@@ -128,7 +134,7 @@ sfx_status acdi_step(sfx_ctx* c, const void* ux, const void* uy, const void* uz,
   const int nb = blocks_for(n, 256);
   SFX_KERNEL(c, K_PHASE, k_acdi_psi, nb, 256, s, n, ps, eps, r, psi);
   SFX_KERNEL(c, K_PHASE, k_acdi_normal, nb, 256, s, L, psi, nv);
-  SFX_KERNEL(c, K_PHASE, k_acdi_update, nb, 256, s, L, ps, r, nv, zeta, eps, dt, phi);
+  SFX_KERNEL(c, K_PHASE, k_acdi_update, nb, 256, s, L, ps, r, nv, zeta, eps, dt, clip, phi);
   SFX_LAUNCH_CHECK();
   return SFX_OK;
 }

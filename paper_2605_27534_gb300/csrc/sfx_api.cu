@@ -269,12 +269,12 @@ sfx_status sfx_marangoni_force(sfx_ctx* c, const sfx_params* params, const void*
 }
 
 sfx_status sfx_acdi_step(sfx_ctx* c, const void* ux, const void* uy, const void* uz, double dt,
-                         double zeta, double eps, double* phi, void* stream) {
+                         double zeta, double eps, int clip, double* phi, void* stream) {
   if (!c || !phi || !(dt > 0.0) || !std::isfinite(dt)) return SFX_ERR_ARG;
   if (!(eps > 0.0) || !(zeta >= 0.0) || !std::isfinite(eps) || !std::isfinite(zeta))
     return SFX_ERR_ARG;
   if (ux && (!uy || (c->grid.geom == SFX_CART3D && !uz))) return SFX_ERR_ARG;
-  return acdi_step(c, ux, uy, uz, dt, zeta, eps, phi, S(stream));
+  return acdi_step(c, ux, uy, uz, dt, zeta, eps, clip ? 1 : 0, phi, S(stream));
 }
 
 sfx_status sfx_capillary_force(sfx_ctx* c, const sfx_params* params, const double* phi,

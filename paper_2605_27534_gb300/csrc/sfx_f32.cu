@@ -651,22 +651,103 @@ __global__ void k_advect32(Adv32 A, const float2* __restrict__ x, float bc_in,
     out[c] = advect_cell(A, x, bc_in, c);
 }
 
-// Both transported fields of a step in one pass.
-__global__ void __launch_bounds__(256) k_advect2_32(Adv32 A, const float2* __restrict__ f,
-                                                    const float2* __restrict__ F, float bc_f,
-                                                    float bc_F, float2* __restrict__ fo,
-                                                    float2* __restrict__ Fo) {
+// Both fields in one pass with every face evaluated once.  A block owns a
+// tile of (kAdvX - 1) x (kAdvY - 1) cells and walks up to kAdvZ planes.
+// Thread (tx, ty) evaluates the x and y faces on the minus side of cell
+// (i0 + tx, j0 + ty) of the current plane (the last column and row give the
+// tile's plus faces) and shares them through shared memory; the z face on
+// the plus side of its cell is carried into the next plane as that plane's
+// minus face.  Each face term is the weighted pair flux w u v of
+// advect_cell2 and the cell sums them in its order (minus then plus face,
+// x, y, z), so the result is bitwise that of advect_cell2 (the batched
+// kernels).
+constexpr int kAdvX = 32, kAdvY = 8, kAdvZ = 32;
+
+// weighted pair fluxes of one face for both fields: (f.hi, f.lo, F.hi, F.lo)
+__device__ __forceinline__ float4 face_flux2(const Adv32& A, const float2* __restrict__ x1,
+                                             const float2* __restrict__ x2, float bc1, float bc2,
+                                             int d, int* fc, float u, float w) {
+  if (u == 0.0f) return make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+  float v1, v2;
+  face32v2(A, x1, x2, bc1, bc2, d, fc, u, v1, v2);
+  float pr = __fmul_rn(u, v1);
+  const float2 a = df_mul_f(make_float2(pr, fmaf(u, v1, -pr)), w);
+  pr = __fmul_rn(u, v2);
+  const float2 b = df_mul_f(make_float2(pr, fmaf(u, v2, -pr)), w);
+  return make_float4(a.x, a.y, b.x, b.y);
+}
+
+__device__ __forceinline__ void acc_face(float2& S1, float2& S2, float4 q, bool plus) {
+  if (plus) {
+    S1 = df_add2(S1, make_float2(q.x, q.y));
+    S2 = df_add2(S2, make_float2(q.z, q.w));
+  } else {
+    S1 = df_sub2(S1, make_float2(q.x, q.y));
+    S2 = df_sub2(S2, make_float2(q.z, q.w));
+  }
+}
+
+__global__ void __launch_bounds__(kAdvX* kAdvY)
+    k_advect2t_32(Adv32 A, const float2* __restrict__ f, const float2* __restrict__ F,
+                  float bc_f, float bc_F, float2* __restrict__ fo, float2* __restrict__ Fo) {
+  __shared__ float4 sx[kAdvY][kAdvX];
+  __shared__ float4 sy[kAdvY][kAdvX];
   const Level& L = A.L;
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= L.nx) return;
-  const ix rows = (ix)L.ny * (ix)L.nz;
-  for (ix r = blockIdx.y; r < rows; r += gridDim.y) {
-    const int j = (int)(r % (ix)L.ny), k = (int)(r / (ix)L.ny);
-    const ix c = r * (ix)L.nx + (ix)i;
-    float2 a, b;
-    advect_cell2(A, f, F, bc_f, bc_F, i, j, k, c, a, b);
-    fo[c] = a;
-    Fo[c] = b;
+  const int tx = threadIdx.x % kAdvX, ty = threadIdx.x / kAdvX;
+  const int i = blockIdx.x * (kAdvX - 1) + tx, j = blockIdx.y * (kAdvY - 1) + ty;
+  const bool is3d = L.geom == SFX_CART3D;
+  const int k0 = is3d ? blockIdx.z * kAdvZ : 0;
+  const int k1 = is3d ? min(k0 + kAdvZ, L.nz) : 1;
+  const bool cell = tx < kAdvX - 1 && ty < kAdvY - 1 && i < L.nx && j < L.ny;
+  const float wxm = wr_face(L.geom, i), wy = wz_face(L.geom, i);
+  float4 zm = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+  float uzm = 0.0f;
+  if (is3d && cell) {
+    int fcz[3] = {i, j, k0};
+    uzm = A.u[2][cidx32(L, i, j, k0)];
+    zm = face_flux2(A, f, F, bc_f, bc_F, 2, fcz, uzm, 1.0f);
+  }
+  for (int k = k0; k < k1; ++k) {
+    float4 qx = make_float4(0.0f, 0.0f, 0.0f, 0.0f), qy = qx;
+    if (i <= L.nx && j < L.ny) {
+      int fcx[3] = {i, j, k};
+      qx = face_flux2(A, f, F, bc_f, bc_F, 0, fcx, A.u[0][fidx(L, 0, i, j, k)], wxm);
+    }
+    if (i < L.nx && j <= L.ny) {
+      int fcy[3] = {i, j, k};
+      qy = face_flux2(A, f, F, bc_f, bc_F, 1, fcy, A.u[1][fidx(L, 1, i, j, k)], wy);
+    }
+    sx[ty][tx] = qx;
+    sy[ty][tx] = qy;
+    __syncthreads();
+    if (cell) {
+      float2 S1 = make_float2(0.0f, 0.0f), S2 = S1;
+      const float uxm = A.u[0][fidx(L, 0, i, j, k)], uxp = A.u[0][fidx(L, 0, i + 1, j, k)];
+      const float uym = A.u[1][fidx(L, 1, i, j, k)], uyp = A.u[1][fidx(L, 1, i, j + 1, k)];
+      if (uxm != 0.0f) acc_face(S1, S2, sx[ty][tx], false);
+      if (uxp != 0.0f) acc_face(S1, S2, sx[ty][tx + 1], true);
+      if (uym != 0.0f) acc_face(S1, S2, sy[ty][tx], false);
+      if (uyp != 0.0f) acc_face(S1, S2, sy[ty + 1][tx], true);
+      if (is3d) {
+        int fcz[3] = {i, j, k + 1};
+        const float uzp = A.u[2][fidx(L, 2, i, j, k + 1)];
+        const float4 zp = face_flux2(A, f, F, bc_f, bc_F, 2, fcz, uzp, 1.0f);
+        if (uzm != 0.0f) acc_face(S1, S2, zm, false);
+        if (uzp != 0.0f) acc_face(S1, S2, zp, true);
+        zm = zp;
+        uzm = uzp;
+      }
+      float2 i1 = df_mul_f(df_mul_f(S1, -A.dt), A.invh);
+      float2 i2 = df_mul_f(df_mul_f(S2, -A.dt), A.invh);
+      if (L.geom == SFX_AXISYM) {
+        i1 = df_div_f(i1, wz_face(L.geom, i));
+        i2 = df_div_f(i2, wz_face(L.geom, i));
+      }
+      const ix c = cidx32(L, i, j, k);
+      fo[c] = df_add2(f[c], i1);
+      Fo[c] = df_add2(F[c], i2);
+    }
+    __syncthreads();
   }
 }
 
@@ -826,55 +907,71 @@ __device__ float plic32_area(int nd, const float* m, float C) {
   return sqrtf(q2) / s * plic32_half(q, three_d, 0.5f * (lo + hi)).dv;
 }
 
+// One cell of the Marangoni force (F32 context).  With dm_mode 1 only
+// interface cells (1e-6 < C < 1 - 1e-6) carry a PLIC area, so every other
+// cell's force is zero and skips the gradient and the normal.
+__device__ __forceinline__ void force32_cell(const Level& L, const double* __restrict__ phi,
+                                             const float* __restrict__ C,
+                                             const float* __restrict__ dsig, int dm_mode,
+                                             float inv_eps, int i, int j, int k, ix c, ix n,
+                                             float* __restrict__ force) {
+  const int nd = L.ndim();
+  const float Cc = C[c];
+  if (dm_mode != 0 && !(Cc > 1e-6f && Cc < 1.0f - 1e-6f)) {
+    for (int d = 0; d < nd; ++d) force[(ix)d * n + c] = 0.0f;
+    return;
+  }
+  const int idx[3] = {i, j, k};
+  const float inv2h = 0.5f / (float)L.h;
+  float gs[3] = {0, 0, 0}, nn[3], ndg = 0.0f;
+  float gc2 = 0;
+  for (int d = 0; d < nd; ++d) {
+    int pp[3] = {idx[0], idx[1], idx[2]}, pm[3] = {idx[0], idx[1], idx[2]};
+    pp[d] = min(pp[d] + 1, L.extent(d) - 1);
+    pm[d] = max(pm[d] - 1, 0);
+    const ix cp = cidx32(L, pp[0], pp[1], pp[2]), cm = cidx32(L, pm[0], pm[1], pm[2]);
+    gs[d] = (dsig[cp] - dsig[cm]) * inv2h;
+    if (dm_mode == 0) {
+      float gc = (C[cp] - C[cm]) * inv2h;
+      gc2 += gc * gc;
+    }
+  }
+  normal3_f32(L, phi, idx[0], idx[1], idx[2], inv_eps, nn);
+  for (int d = 0; d < nd; ++d) ndg += nn[d] * gs[d];
+  float dm;
+  if (dm_mode == 0) {
+    dm = sqrtf(gc2);
+  } else {
+    float m[3] = {0, 0, 0};
+    const int kr = nd == 3 ? 1 : 0;
+    for (int dk = -kr; dk <= kr; ++dk)
+      for (int dj = -1; dj <= 1; ++dj)
+        for (int di = -1; di <= 1; ++di) {
+          const int a = min(max(idx[0] + di, 0), L.nx - 1);
+          const int b = min(max(idx[1] + dj, 0), L.ny - 1);
+          const int e = min(max(idx[2] + dk, 0), L.nz - 1);
+          const float w = (di == 0 ? 2.0f : 1.0f) * (dj == 0 ? 2.0f : 1.0f) *
+                          (nd == 3 ? (dk == 0 ? 2.0f : 1.0f) : 1.0f);
+          const float v = C[cidx32(L, a, b, e)];
+          m[0] -= w * di * v;
+          m[1] -= w * dj * v;
+          m[2] -= w * dk * v;
+        }
+    dm = plic32_area(nd, m, Cc) / (float)L.h;
+  }
+  for (int d = 0; d < nd; ++d) force[(ix)d * n + c] = dm * (gs[d] - nn[d] * ndg);
+}
+
+// blocks over (x chunk, rows); each block walks rows r = k ny + j
 __global__ void k_force32(Level L, const double* __restrict__ phi, const float* __restrict__ C,
                           const float* __restrict__ dsig, int dm_mode, float inv_eps,
                           float* __restrict__ force) {
-  const size_t n = L.ncell();
-  const int nd = L.ndim();
-  const float inv2h = 0.5f / (float)L.h;
-  for (size_t c = blockIdx.x * (size_t)blockDim.x + threadIdx.x; c < n;
-       c += (size_t)gridDim.x * blockDim.x) {
-    int idx[3] = {(int)(c % L.nx), (int)((c / L.nx) % L.ny), (int)(c / ((size_t)L.nx * L.ny))};
-    float gs[3] = {0, 0, 0}, nn[3], ndg = 0.0f;
-    float gc2 = 0;
-    for (int d = 0; d < nd; ++d) {
-      int pp[3] = {idx[0], idx[1], idx[2]}, pm[3] = {idx[0], idx[1], idx[2]};
-      pp[d] = min(pp[d] + 1, L.extent(d) - 1);
-      pm[d] = max(pm[d] - 1, 0);
-      size_t cp = cidx(L, pp[0], pp[1], pp[2]), cm = cidx(L, pm[0], pm[1], pm[2]);
-      gs[d] = (dsig[cp] - dsig[cm]) * inv2h;
-      if (dm_mode == 0) {
-        float gc = (C[cp] - C[cm]) * inv2h;
-        gc2 += gc * gc;
-      }
-    }
-    normal3_f32(L, phi, idx[0], idx[1], idx[2], inv_eps, nn);
-    for (int d = 0; d < nd; ++d) ndg += nn[d] * gs[d];
-    float dm = 0.0f;
-    if (dm_mode == 0) {
-      dm = sqrtf(gc2);
-    } else {
-      float Cc = C[c];
-      if (Cc > 1e-6f && Cc < 1.0f - 1e-6f) {   // interface cells only
-        float m[3] = {0, 0, 0};
-        int kr = nd == 3 ? 1 : 0;
-        for (int dk = -kr; dk <= kr; ++dk)
-          for (int dj = -1; dj <= 1; ++dj)
-            for (int di = -1; di <= 1; ++di) {
-              int a = min(max(idx[0] + di, 0), L.nx - 1);
-              int b = min(max(idx[1] + dj, 0), L.ny - 1);
-              int e = min(max(idx[2] + dk, 0), L.nz - 1);
-              float w = (di == 0 ? 2.0f : 1.0f) * (dj == 0 ? 2.0f : 1.0f) *
-                        (nd == 3 ? (dk == 0 ? 2.0f : 1.0f) : 1.0f);
-              float v = C[cidx(L, a, b, e)];
-              m[0] -= w * di * v;
-              m[1] -= w * dj * v;
-              m[2] -= w * dk * v;
-            }
-        dm = plic32_area(nd, m, Cc) / (float)L.h;
-      }
-    }
-    for (int d = 0; d < nd; ++d) force[(size_t)d * n + c] = dm * (gs[d] - nn[d] * ndg);
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= L.nx) return;
+  const ix rows = (ix)L.ny * (ix)L.nz, n = rows * (ix)L.nx;
+  for (ix r = blockIdx.y; r < rows; r += gridDim.y) {
+    const int j = (int)(r % (ix)L.ny), k = (int)(r / (ix)L.ny);
+    force32_cell(L, phi, C, dsig, dm_mode, inv_eps, i, j, k, r * (ix)L.nx + (ix)i, n, force);
   }
 }
 
@@ -1219,8 +1316,10 @@ sfx_status step_f32(sfx_ctx* c, const sfx_params* pr, const double* phi_in, cons
   c->f32.inc_valid = false;
   if (ux) {
     Adv32 A{L, (float)dt, (float)(1.0 / L.h), {ux, uy, uz}};
-    const RowGrid ag = row_grid(L);
-    SFX_KERNEL(c, K_ADVECT, k_advect2_32, ag.grid, ag.block, s, A, f, F, (float)pr->bc_f,
+    const dim3 ag((unsigned)((L.nx + kAdvX - 2) / (kAdvX - 1)),
+                  (unsigned)((L.ny + kAdvY - 2) / (kAdvY - 1)),
+                  L.geom == SFX_CART3D ? (unsigned)((L.nz + kAdvZ - 1) / kAdvZ) : 1u);
+    SFX_KERNEL(c, K_ADVECT, k_advect2t_32, ag, kAdvX * kAdvY, s, A, f, F, (float)pr->bc_f,
                (float)pr->bc_F, fs, Fs);
     SFX_LAUNCH_CHECK();
   } else {
@@ -1381,7 +1480,8 @@ sfx_status marangoni32(sfx_ctx* c, const sfx_params* p, const float2* f, const d
   Eos32 q{(float)p->gamma_inf, (float)p->eps, (float)(1.0 / p->eps), (float)p->sigma0,
           (float)p->E, p->eos};
   SFX_KERNEL(c, K_FORCES, k_eos32, blocks_for(n, 256), 256, s, n, q, f, phi, c->f32.dsig, sigma);
-  SFX_KERNEL(c, K_FORCES, k_force32, blocks_for(n, 256), 256, s, L, phi, C, c->f32.dsig, dm_mode,
+  const RowGrid fg = row_grid(L);
+  SFX_KERNEL(c, K_FORCES, k_force32, fg.grid, fg.block, s, L, phi, C, c->f32.dsig, dm_mode,
              q.inv_eps, force);
   SFX_LAUNCH_CHECK();
   return SFX_OK;

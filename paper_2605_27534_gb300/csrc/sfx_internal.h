@@ -167,7 +167,7 @@ sfx_status drift_faces64(sfx_ctx* c, const double* phi, double Df, double DF, do
                          double* const* Bf, double* const* BF, cudaStream_t s);
 // sfx_acdi.cu
 sfx_status acdi_step(sfx_ctx* c, const void* ux, const void* uy, const void* uz, double dt,
-                     double zeta, double eps, double* phi, cudaStream_t s);
+                     double zeta, double eps, int clip, double* phi, cudaStream_t s);
 // sfx_capillary.cu
 sfx_status capillary(sfx_ctx* c, const sfx_params* p, const double* phi, const void* C,
                      const void* sigma, void* kappa, void* force, cudaStream_t s);

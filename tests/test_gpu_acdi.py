@@ -111,6 +111,31 @@ def test_acdi_in_fp32_contexts_matches_the_oracle(sfx, geom):
     assert ud[0].dtype == torch.float32
 
 
+@pytest.mark.parametrize("clip", [False, True])
+def test_acdi_overshoots_and_clipping_match_the_oracle(sfx, clip):
+    """phi beyond 1 + veps and below -veps (no psi there without the clamp),
+    with and without clipping of the result, in the closed planar flow."""
+    g, phi0, u = _case("planar")
+    phi0 = phi0.copy()
+    phi0[phi0 > 1.0 - 1e-6] = 1.0 + 3e-6
+    phi0[phi0 < 1e-6] = -3e-6
+    umax = max(np.abs(a).max() for a in u if a is not None)
+    dt, zeta, eps = 0.3 * g.h / umax, 1.1 * umax, 0.75 * g.h
+    want = phi0
+    for _ in range(3):
+        want = oracle.acdi_step(g, want, dt, zeta, eps, *u, clip=clip)
+    ctx = sfx.Context.for_grid(g, sfx.SFX_F64)
+    phi = dev(phi0)
+    ud = [dev(a) if a is not None else None for a in u]
+    for _ in range(3):
+        ctx.sfx_acdi_step(phi, dt, zeta, eps, *ud, clip=clip)
+    got = host(phi)
+    assert np.all(np.isfinite(got))
+    assert rel_err(got, want) < PARITY
+    if clip:
+        assert got.min() >= 0.0 and got.max() <= 1.0
+
+
 def test_acdi_rejects_bad_arguments(sfx):
     g, phi0, u = _case("planar")
     ctx = sfx.Context.for_grid(g, sfx.SFX_F64)

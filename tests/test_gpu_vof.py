@@ -82,10 +82,13 @@ def test_vof_rejects_axisymmetric_grids(sfx):
         ctx.sfx_vof_advect(ur, uz, None, 1e-3, C)
 
 
-def test_moving_interface_pipeline_matches_oracle(sfx):
+@pytest.mark.parametrize("rebuild_every", [1, 3])
+def test_moving_interface_pipeline_matches_oracle(sfx, rebuild_every):
     """Single vortex with a soluble surfactant at 48^2: each step advects C,
-    rebuilds phi from it and takes the coupled step with the same velocity,
-    in the oracle and in an FP64 context."""
+    rebuilds phi from it (or, between rebuilds every rebuild_every steps,
+    carries phi by one ACDI step with zeta = 1.1 max|u|) and takes the
+    coupled step with the same velocity, in the oracle and in an FP64
+    context."""
     import torch
     n = 48
     c = W.case_vortex_2d(n=n, soluble=True)
@@ -103,13 +106,21 @@ def test_moving_interface_pipeline_matches_oracle(sfx):
     for s in range(6):
         ux, uy = W.single_vortex_faces(n, g.h, (s + 0.5) * dt, T)
         Co = oracle.vof_advect(g, ux, uy, None, dt, Co, s % 2)
-        _, phio, _ = oracle.phase_field_build(g, Co, c.redist_iters, c.dtau, p.eps)
+        rebuild = s % rebuild_every == 0
+        zeta = 1.1 * max(np.abs(ux).max(), np.abs(uy).max())
+        if rebuild:
+            _, phio, _ = oracle.phase_field_build(g, Co, c.redist_iters, c.dtau, p.eps)
+        else:
+            phio = oracle.acdi_step(g, phio, dt, zeta, p.eps, ux, uy, None, clip=True)
         fo, Fo, st = oracle.surfactant_step(g, p, phio, fo, Fo, dt, 1e-13, ux, uy, None)
         assert st.converged
         uxd, uyd = dev(ux), dev(uy)
         ctx.sfx_vof_advect(uxd, uyd, None, dt, Cd, s % 2)
-        ctx.sfx_phase_field_build(Cd, chi, phid, None, iters=c.redist_iters, dtau=c.dtau,
-                                  eps=p.eps)
+        if rebuild:
+            ctx.sfx_phase_field_build(Cd, chi, phid, None, iters=c.redist_iters, dtau=c.dtau,
+                                      eps=p.eps)
+        else:
+            ctx.sfx_acdi_step(phid, dt, zeta, p.eps, uxd, uyd, clip=True)
         stt = ctx.sfx_surfactant_step(p, phid, fd, Fd, dt, uxd, uyd, None, opts=opts)
         assert stt.converged
     assert np.abs(host(Cd) - Co).max() <= 1e-12
