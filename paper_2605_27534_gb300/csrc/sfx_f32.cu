@@ -661,7 +661,7 @@ __global__ void k_advect32(Adv32 A, const float2* __restrict__ x, float bc_in,
 // advect_cell2 and the cell sums them in its order (minus then plus face,
 // x, y, z), so the result is bitwise that of advect_cell2 (the batched
 // kernels).
-constexpr int kAdvX = 32, kAdvY = 8, kAdvZ = 32;
+constexpr int kAdvX = 32, kAdvY = 8, kAdvZ = 8;
 
 // weighted pair fluxes of one face for both fields: (f.hi, f.lo, F.hi, F.lo)
 __device__ __forceinline__ float4 face_flux2(const Adv32& A, const float2* __restrict__ x1,
