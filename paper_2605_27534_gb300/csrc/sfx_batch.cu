@@ -61,6 +61,7 @@ struct BPtr {
   float* rres;            // 2 per instance: last relative residuals
   double* mass;           // 2 per instance
   unsigned long long* work;   // 2 per instance: residual passes, sweep groups
+  int* loop;              // Newton iterations done in the current step
   float* part;            // per cell block: the 4 residual maxima
   double* tpart;          // per cell block: (s, c) compensated sums of f and F
 };
@@ -129,6 +130,7 @@ __global__ void k_b_copy(const BInst* __restrict__ I, int n, const int* __restri
 
 __global__ void k_b_init(int n, BPtr P) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i == 0) *P.loop = 0;
   if (i >= n) return;
   P.active[i] = 1;
   P.iters[i] = 0;
@@ -165,11 +167,12 @@ __global__ void k_b_resid(const BInst* __restrict__ I, int n, const int* __restr
   }
 }
 
-// convergence test of iteration `it`: one block per instance still active
-// combines the residual maxima of the instance's blocks
-__global__ void k_b_flags(int n, const int* __restrict__ pre, BPtr P, float tol, int it) {
+// convergence test of the current iteration: one block per instance still
+// active combines the residual maxima of the instance's blocks
+__global__ void k_b_flags(int n, const int* __restrict__ pre, BPtr P, float tol) {
   const int i = blockIdx.x;
   if (i >= n || !P.active[i]) return;
+  const int it = *P.loop + 1;
   float mx[4] = {0.0f, 0.0f, 0.0f, 0.0f};
   for (int b = pre[i] + threadIdx.x; b < pre[i + 1]; b += blockDim.x)
 #pragma unroll
@@ -192,6 +195,19 @@ __global__ void k_b_flags(int n, const int* __restrict__ pre, BPtr P, float tol,
   P.work[2 * i] += 1;
   if (rf <= tol * bf && rF <= tol * bF) P.active[i] = 0;   // converged: stop here
   else P.work[2 * i + 1] += 1;                             // the sweeps run
+}
+
+// end of an iteration: count it, and let the step's loop run again while
+// an instance is active and the iteration budget lasts
+__global__ void k_b_next(int n, BPtr P, int max_it, cudaGraphConditionalHandle loop) {
+  int any = 0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) any |= P.active[i];
+  any = __syncthreads_or(any);
+  if (threadIdx.x == 0) {
+    const int done = *P.loop + 1;
+    *P.loop = done;
+    cudaGraphSetConditional(loop, (any && done < max_it) ? 1u : 0u);
+  }
 }
 
 // one colour of the coupled correction sweep; blocks over half-rows
@@ -318,6 +334,7 @@ struct sfx_batch {
   const void* drift_phi = nullptr;
   double key_tol = 0;
   cudaStream_t cap = nullptr;
+  cudaStream_t cap_body = nullptr;   // captures the body of the iteration loop
   // last schedule
   int sweeps = 3, max_it = 8;
   std::vector<int> h_iters;
@@ -357,7 +374,10 @@ sfx_status build_prefix(sfx_batch* b) {
   return SFX_OK;
 }
 
-// enqueue one batched step on s (used under stream capture)
+// Enqueue one batched step on s under stream capture: the set-up kernels,
+// the Newton iterations as the body of a conditional while node (run again
+// while an instance is active and the budget lasts, so a step whose
+// instances converge early launches no further kernels), then the totals.
 sfx_status enqueue_step(sfx_batch* b, bool advect, float tol, cudaStream_t s) {
   const int n = b->n, bs = b->block;
   BPtr& P = b->P;
@@ -373,15 +393,42 @@ sfx_status enqueue_step(sfx_batch* b, bool advect, float tol, cudaStream_t s) {
   } else {
     k_b_copy<<<b->nb_cell, bs, 0, s>>>(b->dI, n, b->pre_cell, P, 0);
   }
-  for (int it = 1; it <= b->max_it; ++it) {
-    k_b_resid<<<b->nb_cell, bs, 0, s>>>(b->dI, n, b->pre_cell, P);
-    k_b_flags<<<n, 256, 0, s>>>(n, b->pre_cell, P, tol, it);
-    // the residual pass did the first red half-sweep
-    for (int q = 0; q < b->sweeps; ++q)
-      for (int color = (q == 0 ? 1 : 0); color < 2; ++color)
-        k_b_corr<<<b->nb_pair, bs, 0, s>>>(b->dI, n, b->pre_pair, P, color, q == 0 ? 1 : 0,
-                                           q == b->sweeps - 1 && color == 1 ? 1 : 0);
-  }
+  SFX_LAUNCH_CHECK();
+  // the while node, after everything captured so far
+  cudaStreamCaptureStatus cs;
+  cudaGraph_t cg = nullptr;
+  const cudaGraphNode_t* deps = nullptr;
+  size_t ndeps = 0;
+  SFX_CUDA(cudaStreamGetCaptureInfo(s, &cs, nullptr, &cg, &deps, nullptr, &ndeps));
+  cudaGraphConditionalHandle loop;
+  SFX_CUDA(cudaGraphConditionalHandleCreate(&loop, cg, 1u, cudaGraphCondAssignDefault));
+  cudaGraphNodeParams cp = {};
+  cp.type = cudaGraphNodeTypeConditional;
+  cp.conditional.handle = loop;
+  cp.conditional.type = cudaGraphCondTypeWhile;
+  cp.conditional.size = 1;
+  cudaGraphNode_t cnode;
+  SFX_CUDA(cudaGraphAddNode(&cnode, cg, deps, nullptr, ndeps, &cp));
+  cudaGraph_t body = cp.conditional.phGraph_out[0];
+  if (!b->cap_body) SFX_CUDA(cudaStreamCreateWithFlags(&b->cap_body, cudaStreamNonBlocking));
+  cudaStream_t sb = b->cap_body;
+  SFX_CUDA(cudaStreamBeginCaptureToGraph(sb, body, nullptr, nullptr, 0,
+                                         cudaStreamCaptureModeThreadLocal));
+  k_b_resid<<<b->nb_cell, bs, 0, sb>>>(b->dI, n, b->pre_cell, P);
+  k_b_flags<<<n, 256, 0, sb>>>(n, b->pre_cell, P, tol);
+  // the residual pass did the first red half-sweep
+  for (int q = 0; q < b->sweeps; ++q)
+    for (int color = (q == 0 ? 1 : 0); color < 2; ++color)
+      k_b_corr<<<b->nb_pair, bs, 0, sb>>>(b->dI, n, b->pre_pair, P, color, q == 0 ? 1 : 0,
+                                          q == b->sweeps - 1 && color == 1 ? 1 : 0);
+  k_b_next<<<1, 256, 0, sb>>>(n, P, b->max_it, loop);
+  const cudaError_t le = cudaGetLastError();
+  cudaGraph_t body_out = nullptr;
+  const cudaError_t be = cudaStreamEndCapture(sb, &body_out);
+  SFX_CUDA(le);
+  SFX_CUDA(be);
+  SFX_CUDA(cudaStreamUpdateCaptureDependencies(s, &cnode, nullptr, 1,
+                                               cudaStreamSetCaptureDependencies));
   k_b_totals<<<n * kTotBlocks, 256, 0, s>>>(b->dI, P);
   k_b_totals_final<<<n, 32, 0, s>>>(b->dI, n, P);
   SFX_LAUNCH_CHECK();
@@ -496,6 +543,7 @@ sfx_status sfx_batch_create(const sfx_batch_instance* inst, int n, sfx_batch** o
   if (st == SFX_OK) st = balloc(b, &P.norms, 4 * (size_t)n);
   if (st == SFX_OK) st = balloc(b, &P.active, (size_t)n);
   if (st == SFX_OK) st = balloc(b, &P.iters, (size_t)n);
+  if (st == SFX_OK) st = balloc(b, &P.loop, (size_t)1);
   if (st == SFX_OK) st = balloc(b, &P.rres, 2 * (size_t)n);
   if (st == SFX_OK) st = balloc(b, &P.mass, 2 * (size_t)n);
   if (st == SFX_OK) st = balloc(b, &P.work, 2 * (size_t)n);
@@ -524,6 +572,7 @@ void sfx_batch_destroy(sfx_batch* b) {
   if (!b) return;
   if (b->exec) cudaGraphExecDestroy(b->exec);
   if (b->cap) cudaStreamDestroy(b->cap);
+  if (b->cap_body) cudaStreamDestroy(b->cap_body);
   for (void* p : b->allocs) cudaFree(p);
   delete b;
 }
