@@ -66,6 +66,28 @@ __device__ inline VolSlope plic_volume(const double* q, bool three_d, double a) 
   return r;
 }
 
+// Plane offset alpha in [0, 1] with volume fraction C: the root of the
+// increasing V(alpha) - C by Newton steps on the slope dV/dalpha, kept
+// inside a bracket that every evaluation narrows (a bisection step replaces
+// a Newton step that leaves it); stops when the step falls below 1e-17, the
+// bracket closes, or after 100 evaluations.  The same root as a bisection
+// to double precision, in a handful of evaluations.
+__device__ inline double plic_alpha(const double* q, bool three_d, double C) {
+  double lo = 0.0, hi = 1.0, a = C;
+  for (int it = 0; it < 100; ++it) {
+    const VolSlope r = plic_volume(q, three_d, a);
+    const double f = r.v - C;
+    if (f == 0.0) return a;
+    if (f < 0.0) lo = a;
+    else hi = a;
+    double an = r.dv > 0.0 ? a - f / r.dv : 0.5 * (lo + hi);
+    if (!(an > lo && an < hi)) an = 0.5 * (lo + hi);
+    if (fabs(an - a) <= 1e-17 || !(hi - lo > 0.0)) return an;
+    a = an;
+  }
+  return a;
+}
+
 // Interface area inside the unit cell holding fraction C with normal m.
 __device__ inline double plic_unit_area(int nd, const double* mraw, double C) {
   if (!(C > 0.0 && C < 1.0)) return 0.0;
@@ -79,13 +101,7 @@ __device__ inline double plic_unit_area(int nd, const double* mraw, double C) {
   if (q[1] > q[2]) { double t = q[1]; q[1] = q[2]; q[2] = t; }
   if (q[0] > q[1]) { double t = q[0]; q[0] = q[1]; q[1] = t; }
   const bool three_d = nd == 3;
-  double lo = 0.0, hi = 1.0;
-  for (int it = 0; it < 64; ++it) {
-    double mid = 0.5 * (lo + hi);
-    if (plic_volume(q, three_d, mid).v < C) lo = mid;
-    else hi = mid;
-  }
-  return (sqrt(q2) / s) * plic_volume(q, three_d, 0.5 * (lo + hi)).dv;
+  return (sqrt(q2) / s) * plic_volume(q, three_d, plic_alpha(q, three_d, C)).dv;
 }
 
 
@@ -101,17 +117,6 @@ __device__ inline bool plic_sorted(int nd, const double* m, double* q) {
   if (q[1] > q[2]) { double t = q[1]; q[1] = q[2]; q[2] = t; }
   if (q[0] > q[1]) { double t = q[0]; q[0] = q[1]; q[1] = t; }
   return true;
-}
-
-// Plane offset alpha in [0, 1] with volume fraction C (bisection).
-__device__ inline double plic_alpha(const double* q, bool three_d, double C) {
-  double lo = 0.0, hi = 1.0;
-  for (int it = 0; it < 64; ++it) {
-    const double mid = 0.5 * (lo + hi);
-    if (plic_volume(q, three_d, mid).v < C) lo = mid;
-    else hi = mid;
-  }
-  return 0.5 * (lo + hi);
 }
 
 // Fluid {n.z <= alpha} (n = |m|/sum|m|, z reflected where m < 0) with
