@@ -167,7 +167,8 @@ sfx_status sfx_mg_solve(sfx_ctx* ctx, double D, const double* Bx,
    within |c_f| h of the face and H = [C > 1/2] at the start of the step.
    Conserves sum C exactly for divergence-free velocities; bounded for
    |c_f| <= 1/2.  Walls carry no flux.  C: double, in place; velocities in
-   the context precision.  Planar 2D and 3D (SFX_ERR_ARG for axisymmetric
+   the context precision; SFX_F32 contexts evaluate the PLIC geometry of the
+   fluxes in FP32 (fluxes to ~1e-7, C still conserved exactly).  Planar 2D and 3D (SFX_ERR_ARG for axisymmetric
    grids).  The context allocates two scratch arrays on first use. */
 sfx_status sfx_vof_advect(sfx_ctx* ctx, const void* ux, const void* uy, const void* uz,
                           double dt, int order, double* C, void* stream);

@@ -1,12 +1,13 @@
 // Geometric VoF advection of the volume fraction C (the paper's interface
-// tracking, Sec. 2), FP64: directionally split conservative PLIC
-// advection.  For each direction d in turn, with face Courant numbers
+// tracking, Sec. 2): directionally split conservative PLIC advection.  For each direction d in turn, with face Courant numbers
 // c_f = u_f dt/h,
 //   C <- C - (Q_+ - Q_-) + H (c_+ - c_-),
 // Q_f the volume fraction crossing face f (the fluid of the upwind cell's
 // PLIC reconstruction within |c_f| h of the face, signed with u_f) and
 // H = [C > 1/2] at the start of the step; the direction order alternates
-// from step to step.  Walls carry no flux.  Planar 2D and 3D.
+// from step to step.  Walls carry no flux.  Planar 2D and 3D.  C is double
+// in both precisions; SFX_F32 contexts evaluate the PLIC geometry of the
+// fluxes in FP32.
 #include <algorithm>
 
 #include "sfx_internal.h"
@@ -22,8 +23,11 @@ __global__ void k_vof_indicator(size_t n, const double* __restrict__ C, double* 
 }
 
 // Volume fractions crossing the faces of direction d; blocks cover
-// (x chunk, rows of faces) and walk the rows.
-template <typename U>
+// (x chunk, rows of faces) and walk the rows.  G is the arithmetic of the
+// PLIC geometry (double in SFX_F64 contexts, float in SFX_F32 contexts: the
+// fluxes then carry float rounding, while C and its update stay double and
+// the update stays exactly conservative).
+template <typename U, typename G>
 __global__ void k_vof_flux(Level L, int d, const double* __restrict__ C,
                            const U* __restrict__ u, double dt_h, double* __restrict__ Q) {
   const int fx = L.nx + (d == 0), fy = L.ny + (d == 1), fz = L.nz + (d == 2);
@@ -45,10 +49,11 @@ __global__ void k_vof_flux(Level L, int d, const double* __restrict__ C,
     const int uj = (cf > 0.0 && d == 1) ? j - 1 : j;
     const int uk = (cf > 0.0 && d == 2) ? k - 1 : k;
     const double cu = C[cidx(L, ui, uj, uk)];
-    double m[3] = {0.0, 0.0, 0.0};
+    G m[3] = {G(0), G(0), G(0)};
     if (cu > 0.0 && cu < 1.0) youngs_normal(L, C, ui, uj, uk, m);   // empty/full: no plane
-    Q[f] = cf > 0.0 ? plic_slab(nd, m, cu, d, 1.0 - cf, 1.0)
-                    : -plic_slab(nd, m, cu, d, 0.0, -cf);
+    const G cg = (G)cu;
+    Q[f] = cf > 0.0 ? (double)plic_slab<G>(nd, m, cg, d, G(1) - (G)cf, G(1))
+                    : -(double)plic_slab<G>(nd, m, cg, d, G(0), (G)(-cf));
   }
 }
 
@@ -77,7 +82,7 @@ void rows_launch(int nxl, long long rows, dim3& grid, dim3& block) {
   grid = dim3(xb, (unsigned)std::min(rows, std::min(std::max(1LL, 152LL * 8 / xb), 65535LL)));
 }
 
-template <typename U>
+template <typename U, typename G>
 sfx_status vof_impl(sfx_ctx* c, const U* const* u, double dt, int order, double* C,
                     cudaStream_t s) {
   const Level& L = c->lev[0].lv;
@@ -91,7 +96,7 @@ sfx_status vof_impl(sfx_ctx* c, const U* const* u, double dt, int order, double*
     const int d = order ? nd - 1 - q : q;
     dim3 gf, bf;
     rows_launch(L.nx + (d == 0), (long long)(L.ny + (d == 1)) * (L.nz + (d == 2)), gf, bf);
-    SFX_KERNEL(c, K_OTHER, (k_vof_flux<U>), gf, bf, s, L, d, C, u[d], dt_h, c->vofQ);
+    SFX_KERNEL(c, K_OTHER, (k_vof_flux<U, G>), gf, bf, s, L, d, C, u[d], dt_h, c->vofQ);
     SFX_KERNEL(c, K_OTHER, (k_vof_update<U>), gc, bc, s, L, d, u[d], dt_h, c->vofQ, c->vofH, C);
   }
   SFX_LAUNCH_CHECK();
@@ -112,10 +117,10 @@ sfx_status vof_advect(sfx_ctx* c, const void* ux, const void* uy, const void* uz
   }
   if (c->prec == SFX_F32) {
     const float* u[3] = {(const float*)ux, (const float*)uy, (const float*)uz};
-    return vof_impl(c, u, dt, order, C, s);
+    return vof_impl<float, float>(c, u, dt, order, C, s);
   }
   const double* u[3] = {(const double*)ux, (const double*)uy, (const double*)uz};
-  return vof_impl(c, u, dt, order, C, s);
+  return vof_impl<double, double>(c, u, dt, order, C, s);
 }
 
 }  // namespace sfx

@@ -49,7 +49,15 @@ def test_vof_matches_oracle_in_the_single_vortex(sfx, precision):
         uxd, uyd = dev(ux, vt), dev(uy, vt)
         ctx.sfx_vof_advect(uxd, uyd, None, dt, Cd, s % 2)
         Co = oracle.vof_advect(g, host(uxd), host(uyd), None, dt, Co, s % 2)
-    assert np.abs(host(Cd) - Co).max() <= 1e-12
+    # SFX_F32 contexts evaluate the PLIC geometry in float: each flux carries
+    # a few float roundings (~1e-7 of the Courant number), four fluxes per
+    # cell and step over 40 steps stay below 1e-5; the update itself is
+    # double and conservative
+    tol = 1e-5 if precision else 1e-12
+    assert np.abs(host(Cd) - Co).max() <= tol
+    # sum C is kept up to the discrete divergence of the face velocities,
+    # which rounding them to float (6e-8) makes non-zero
+    assert abs(host(Cd).sum() - Cf.sum()) <= (1e-10 if precision else 1e-12) * Cf.sum()
 
 
 def test_vof_matches_oracle_in_3d_and_conserves(sfx):
