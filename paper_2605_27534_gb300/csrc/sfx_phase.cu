@@ -31,6 +31,43 @@ template <typename T> __device__ __forceinline__ T tiny_pos();
 template <> __device__ __forceinline__ double tiny_pos<double>() { return 1e-300; }
 template <> __device__ __forceinline__ float tiny_pos<float>() { return 1e-30f; }
 
+// One Jacobi update of chi at a cell from its own chi0 (s0) and iterate
+// (x0) and those of its neighbours along each direction (the cell itself at
+// a wall): Godunov upwind |grad chi| away from the interface, the
+// Russo-Smereka sub-cell fix in cells where chi0 changes sign.
+template <typename T>
+__device__ __forceinline__ T redist_update(int nd, T s0, T x0, const T* z0m, const T* z0p,
+                                           const T* xm, const T* xp, const bool* hasm,
+                                           const bool* hasp, T h, T invh, T dtau, T dtau_h) {
+  const T sg = s0 > (T)0 ? (T)1 : (s0 < (T)0 ? (T)-1 : (T)0);
+  bool cut = false;
+  T gsum = 0, dsum = 0;
+  for (int d = 0; d < nd; ++d) {
+    if ((hasm[d] && s0 * z0m[d] < (T)0) || (hasp[d] && s0 * z0p[d] < (T)0)) cut = true;
+    // sub-cell estimate of |grad chi0| h along d
+    T q = fabs(z0p[d] - z0m[d]) * (T)0.5;
+    q = fmax(q, fabs(z0p[d] - s0));
+    q = fmax(q, fabs(s0 - z0m[d]));
+    dsum += q * q;
+    // Godunov upwind gradient of the current iterate
+    const T bwd = (x0 - xm[d]) * invh, fwd = (xp[d] - x0) * invh;
+    T t;
+    if (sg > (T)0) {
+      const T ap = fmax(bwd, (T)0), bm = fmin(fwd, (T)0);
+      t = fmax(ap * ap, bm * bm);
+    } else {
+      const T am = fmin(bwd, (T)0), bp = fmax(fwd, (T)0);
+      t = fmax(am * am, bp * bp);
+    }
+    gsum += t;
+  }
+  if (cut) {
+    const T dchi = fmax(sqrt(dsum), (T)tiny_pos<T>());
+    return x0 - dtau_h * (sg * fabs(x0) - h * s0 / dchi);
+  }
+  return x0 - dtau * sg * (sqrt(gsum) - (T)1);
+}
+
 // One Jacobi step; blocks cover (x chunk, rows) and walk rows r = k ny + j.
 template <typename T>
 __global__ void k_redistance_step(Level L, T dtau, const T* __restrict__ chi0,
@@ -44,42 +81,79 @@ __global__ void k_redistance_step(Level L, T dtau, const T* __restrict__ chi0,
   for (unsigned r = blockIdx.y; r < rows; r += gridDim.y) {
     const int idx[3] = {i, (int)(r % (unsigned)L.ny), (int)(r / (unsigned)L.ny)};
     const unsigned c = r * (unsigned)L.nx + (unsigned)i;
-    const T s0 = chi0[c];
-    const T sg = s0 > (T)0 ? (T)1 : (s0 < (T)0 ? (T)-1 : (T)0);
-    const T x0 = cin[c];
-    // neighbour offsets along each direction (the cell itself at a wall)
-    bool cut = false;
-    T gsum = 0, dsum = 0;
+    T z0m[3], z0p[3], xm[3], xp[3];
+    bool hasm[3], hasp[3];
     for (int d = 0; d < nd; ++d) {
-      const bool hasm = idx[d] > 0, hasp = idx[d] + 1 < L.extent(d);
-      const unsigned cm = hasm ? c - stride[d] : c, cp = hasp ? c + stride[d] : c;
-      const T z0m = chi0[cm], z0p = chi0[cp];
-      if ((hasm && s0 * z0m < (T)0) || (hasp && s0 * z0p < (T)0)) cut = true;
-      // sub-cell estimate of |grad chi0| h along d
-      T q = fabs(z0p - z0m) * (T)0.5;
-      q = fmax(q, fabs(z0p - s0));
-      q = fmax(q, fabs(s0 - z0m));
-      dsum += q * q;
-      // Godunov upwind gradient of the current iterate
-      const T bwd = (x0 - cin[cm]) * invh, fwd = (cin[cp] - x0) * invh;
-      T t;
-      if (sg > (T)0) {
-        const T ap = fmax(bwd, (T)0), bm = fmin(fwd, (T)0);
-        t = fmax(ap * ap, bm * bm);
-      } else {
-        const T am = fmin(bwd, (T)0), bp = fmax(fwd, (T)0);
-        t = fmax(am * am, bp * bp);
-      }
-      gsum += t;
+      hasm[d] = idx[d] > 0;
+      hasp[d] = idx[d] + 1 < L.extent(d);
+      const unsigned cm = hasm[d] ? c - stride[d] : c, cp = hasp[d] ? c + stride[d] : c;
+      z0m[d] = chi0[cm];
+      z0p[d] = chi0[cp];
+      xm[d] = cin[cm];
+      xp[d] = cin[cp];
     }
-    T v;
-    if (cut) {
-      const T dchi = fmax(sqrt(dsum), (T)tiny_pos<T>());
-      v = x0 - dtau_h * (sg * fabs(x0) - h * s0 / dchi);
-    } else {
-      v = x0 - dtau * sg * (sqrt(gsum) - (T)1);
+    cout[c] = redist_update<T>(nd, chi0[c], cin[c], z0m, z0p, xm, xp, hasm, hasp, h, invh, dtau,
+                               dtau_h);
+  }
+}
+
+// Up to kRdK Jacobi steps of a 2D grid in one launch: a block loads a
+// (kRdX + 2 kRdK) x (kRdY + 2 kRdK) window of chi0 and the iterate into
+// shared memory and updates a window that shrinks by one cell per step, so
+// that after `steps` steps its kRdX x kRdY core holds exactly the values of
+// `steps` single-step launches (the same update of the same operands).
+constexpr int kRdX = 64, kRdY = 32, kRdK = 8;
+constexpr int kRdWX = kRdX + 2 * kRdK, kRdWY = kRdY + 2 * kRdK;
+
+__global__ void __launch_bounds__(256)
+    k_redistance_fused2d(Level L, float dtau, const float* __restrict__ chi0,
+                         const float* __restrict__ cin, float* __restrict__ cout, int steps) {
+  __shared__ float sz[kRdWY][kRdWX];
+  __shared__ float sx[2][kRdWY][kRdWX];
+  const float h = (float)L.h, invh = (float)(1.0 / L.h), dtau_h = dtau / h;
+  const int gx0 = blockIdx.x * kRdX - kRdK, gy0 = blockIdx.y * kRdY - kRdK;
+  for (int q = threadIdx.x; q < kRdWX * kRdWY; q += blockDim.x) {
+    const int lx = q % kRdWX, ly = q / kRdWX;
+    const int gx = gx0 + lx, gy = gy0 + ly;
+    float z = 0.0f, x = 0.0f;
+    if (gx >= 0 && gx < L.nx && gy >= 0 && gy < L.ny) {
+      const unsigned c = (unsigned)gy * (unsigned)L.nx + (unsigned)gx;
+      z = chi0[c];
+      x = cin[c];
     }
-    cout[c] = v;
+    sz[ly][lx] = z;
+    sx[0][ly][lx] = x;
+  }
+  __syncthreads();
+  int cur = 0;
+  for (int st = 0; st < steps; ++st) {
+    // cells at least st + 1 away from the window edge can be updated
+    const int lo = st + 1, nxw = kRdWX - 2 * lo, nyw = kRdWY - 2 * lo;
+    for (int q = threadIdx.x; q < nxw * nyw; q += blockDim.x) {
+      const int lx = lo + q % nxw, ly = lo + q / nxw;
+      const int gx = gx0 + lx, gy = gy0 + ly;
+      if (gx < 0 || gx >= L.nx || gy < 0 || gy >= L.ny) continue;
+      bool hasm[2] = {gx > 0, gy > 0}, hasp[2] = {gx + 1 < L.nx, gy + 1 < L.ny};
+      const float s0 = sz[ly][lx], x0 = sx[cur][ly][lx];
+      float z0m[2], z0p[2], xm[2], xp[2];
+      z0m[0] = hasm[0] ? sz[ly][lx - 1] : s0;
+      z0p[0] = hasp[0] ? sz[ly][lx + 1] : s0;
+      z0m[1] = hasm[1] ? sz[ly - 1][lx] : s0;
+      z0p[1] = hasp[1] ? sz[ly + 1][lx] : s0;
+      xm[0] = hasm[0] ? sx[cur][ly][lx - 1] : x0;
+      xp[0] = hasp[0] ? sx[cur][ly][lx + 1] : x0;
+      xm[1] = hasm[1] ? sx[cur][ly - 1][lx] : x0;
+      xp[1] = hasp[1] ? sx[cur][ly + 1][lx] : x0;
+      sx[cur ^ 1][ly][lx] = redist_update<float>(2, s0, x0, z0m, z0p, xm, xp, hasm, hasp, h, invh,
+                                                 dtau, dtau_h);
+    }
+    __syncthreads();
+    cur ^= 1;
+  }
+  for (int q = threadIdx.x; q < kRdX * kRdY; q += blockDim.x) {
+    const int lx = kRdK + q % kRdX, ly = kRdK + q / kRdX;
+    const int gx = gx0 + lx, gy = gy0 + ly;
+    if (gx < L.nx && gy < L.ny) cout[(unsigned)gy * (unsigned)L.nx + (unsigned)gx] = sx[cur][ly][lx];
   }
 }
 
@@ -131,12 +205,24 @@ sfx_status phase_field_build(sfx_ctx* c, const double* C, double* chi, void* phi
     float* a = c->chi32 + n;
     float* b = c->chi32 + 2 * n;
     SFX_KERNEL(c, K_PHASE, k_chi0_32, nb, 256, s, n, L.h, C, z0, a);
-    for (int it = 0; it < iters; ++it) {
-      SFX_KERNEL(c, K_PHASE, k_redistance_step<float>, dim3(xb, yb), dim3(tx), s, L, (float)dtau,
-                 z0, a, b);
-      float* t = a;
-      a = b;
-      b = t;
+    if (L.ndim() == 2) {
+      // kRdK steps per launch
+      const dim3 fg((unsigned)((L.nx + kRdX - 1) / kRdX), (unsigned)((L.ny + kRdY - 1) / kRdY));
+      for (int it = 0; it < iters; it += kRdK) {
+        const int steps = std::min(kRdK, iters - it);
+        SFX_KERNEL(c, K_PHASE, k_redistance_fused2d, fg, 256, s, L, (float)dtau, z0, a, b, steps);
+        float* t = a;
+        a = b;
+        b = t;
+      }
+    } else {
+      for (int it = 0; it < iters; ++it) {
+        SFX_KERNEL(c, K_PHASE, k_redistance_step<float>, dim3(xb, yb), dim3(tx), s, L,
+                   (float)dtau, z0, a, b);
+        float* t = a;
+        a = b;
+        b = t;
+      }
     }
     SFX_KERNEL(c, K_PHASE, k_widen, nb, 256, s, n, a, chi);
     SFX_LAUNCH_CHECK();

@@ -83,6 +83,24 @@ def test_phase_field_build_parity(sfx, geom):
     assert np.abs(host(phi32) - phi_o).max() < 5e-6
 
 
+@pytest.mark.parametrize("geom", ["planar", "axi"])
+@pytest.mark.parametrize("iters", [1, 8, 13, 17])
+def test_fp32_redistancing_step_counts(sfx, geom, iters):
+    """2D SFX_F32 contexts take up to eight redistancing steps per launch in
+    shared memory; step counts below, at and between multiples of eight
+    against the FP64 oracle."""
+    import torch
+    g, Cf = GEOMS[geom]()
+    eps, dtau = 0.75 * g.h, 0.5 * g.h
+    chi_o, phi_o, _ = oracle.phase_field_build(g, Cf, iters, dtau, eps)
+    ctx32 = _ctx(sfx, g, 1)
+    Cd = dev(Cf)
+    phi32, chi32 = torch.empty_like(Cd), torch.empty_like(Cd)
+    ctx32.sfx_phase_field_build(Cd, chi32, phi32, None, iters=iters, dtau=dtau, eps=eps)
+    assert rel_err(host(chi32), chi_o) < 1e-6
+    assert np.abs(host(phi32) - phi_o).max() < 5e-6
+
+
 def _random_problem(g, seed, scale=2.0):
     rng = np.random.default_rng(seed)
     nz, ny, nx = g.shape
