@@ -84,6 +84,9 @@ def parse():
                     help="steps of the FP64 path timed beside the FP32 line (0: skip)")
     ap.add_argument("--batch-steps", type=int, default=0,
                     help="also time the batched workload for this many steps (0: skip)")
+    ap.add_argument("--kinetics-steps", type=int, default=20,
+                    help="steps of the flat-interface kinetics sweep timed beside the line "
+                         "(0: skip)")
     ap.add_argument("--adjoint-steps", type=int, default=200,
                     help="steps of the 256^2 adjoint workload timed beside the line (0: skip)")
     ap.add_argument("--n", type=int, default=256)
@@ -476,6 +479,9 @@ def run_gpu(a, case, rank, world, local_rank):
     batch = None
     if a.batch_steps > 0:
         batch = run_gpu_batch(a, rank, 1, local_rank, steps=a.batch_steps, summary=True)
+    kin = None
+    if a.kinetics_steps > 0:
+        kin = kinetics_sweep_run(a, dev, a.kinetics_steps)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
         "warmup": a.warmup, "ms_per_step": ms_max / a.steps, "higher_is_better": True,
@@ -500,7 +506,59 @@ def run_gpu(a, case, rank, world, local_rank):
         line["adjoint2d_256"] = adj
     if vortex is not None:
         line["vortex512"] = vortex
+    if kin is not None:
+        line["kinetics_sweep"] = kin
     print(json.dumps(line))
+
+
+def kinetics_sweep_run(a, dev, steps, n_inst=512, ny=256, nx=8, warmup=3):
+    """The flat-interface kinetics of Sec. 4.3 as a batched sweep: n_inst
+    planar columns (nx x ny over y in [-4, 4], interface at y = 0, F = 1 above
+    a clean interface, no flow) with log10 Bi, log10 Da uniform in [-2, 2],
+    stepped together in one graph per step (SFX_F32 batched form).  The
+    phase field is built once on the GPU (every column has the same
+    interface) and declared static."""
+    import torch
+    import paper_2605_27534_gb300 as sfx
+    cases = W.batch_flat_kinetics(n_inst, ny, nx)
+    c0 = cases[0]
+    g = c0.grid
+    ctx = sfx.Context.for_grid(g, sfx.SFX_F32)
+    Cd = torch.from_numpy(c0.C).to(dev)
+    chi, phi1 = torch.empty_like(Cd), torch.empty_like(Cd)
+    ctx.sfx_phase_field_build(Cd, chi, phi1, None, iters=c0.redist_iters, dtau=c0.dtau,
+                              eps=c0.params.eps)
+    phi = phi1.reshape(-1).repeat(n_inst)
+    B = sfx.Batch([(nx, ny, g.h, c.dt, c.params) for c in cases], geom=sfx.SFX_PLANAR2D)
+    B.sfx_batch_reuse_phi(True)
+    F0 = torch.from_numpy(np.concatenate([c.F0.ravel() for c in cases])).to(dev)
+    f = sfx.sfx_df_pack(torch.zeros_like(F0))
+    F = sfx.sfx_df_pack(F0)
+    block, sweeps, budget = B.sfx_batch_autotune(phi, f, F, a.tol)
+    for _ in range(warmup):
+        B.sfx_batch_step(phi, f, F, a.tol)
+    B.sfx_batch_work(reset=True)
+    stream = torch.cuda.current_stream()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        B.sfx_batch_step(phi, f, F, a.tol)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    rp, _ = B.sfx_batch_work()
+    st = B.sfx_batch_stats()
+    ncell = n_inst * nx * ny
+    # interface concentration Gamma = sum h^2 f / (interface length nx h)
+    gam = np.array(st["mass_f"]) / (nx * g.h)
+    return {"ms_per_step": ms, "value": ncell / (ms * 1e-3), "unit": UNIT, "steps": steps,
+            "instances": n_inst, "cells": ncell, "grid": "%dx%d planar, h=%g" % (nx, ny, g.h),
+            "dt": c0.dt, "schedule": {"block": block, "sweeps": sweeps, "iteration_budget": budget},
+            "newton_iters_mean": float(np.mean(np.array(rp) / steps)),
+            "all_converged": bool(all(st["converged"])),
+            "gamma_range_after": [float(gam.min()), float(gam.max())],
+            "t_after": c0.dt * (warmup + steps)}
 
 
 def vortex_run(a, dev, steps, prec, warmup=3, rebuild_every=1):
@@ -777,7 +835,9 @@ def run_gpu_batch(a, rank, world, local_rank, steps=None, summary=False):
     sched = {"block": block, "sweeps": sweeps, "iteration_budget": budget}
     # init, advect, copy (phi static: no fold or drifts); per iteration
     # residual, flags and the 2 sweeps - 1 colour sweeps; totals and final
-    launches_per_step = 3 + budget * (1 + 2 * sweeps) + 2
+    # the iteration loop runs as long as an instance is active: residual,
+    # flags, 2 sweeps - 1 colour sweeps and the loop test per iteration
+    launches_per_step = 3 + max(st["iters"]) * (2 + 2 * sweeps) + 2
     if summary:
         return {"value": value, "unit": UNIT, "ms_per_step": ms / steps, "steps": steps,
                 "cells": ncell, "instances": len(inst), "roofline_frac": roof["frac"],

@@ -400,6 +400,12 @@ typedef struct sfx_batch sfx_batch;
 
 /* Copies the n >= 1 descriptors; SFX_ERR_ARG on a bad size or parameter. */
 sfx_status sfx_batch_create(const sfx_batch_instance* inst, int n, sfx_batch** out);
+/* The same with the geometry of every instance: SFX_AXISYM (as
+   sfx_batch_create; nr x nz rings) or SFX_PLANAR2D (nr x nz planar cells of
+   unit depth, e.g. the flat-interface columns of Sec. 4.3); totals are then
+   sum h^2 x.  SFX_ERR_ARG for another geometry. */
+sfx_status sfx_batch_create_geom(const sfx_batch_instance* inst, int n, int geom,
+                                 sfx_batch** out);
 void sfx_batch_destroy(sfx_batch* b);
 /* Totals of the packed arrays and, when the array pointers are not NULL,
    the n offsets of each instance (host arrays of n size_t). */
@@ -438,9 +444,12 @@ sfx_status sfx_batch_work(sfx_batch* b, long long* resid_passes, long long* swee
 /* Autotuner: runs one step of every candidate schedule (block 128 or 256,
    2, 3 or 4 sweeps) on scratch copies of f and F (which stay unchanged),
    gives each the smallest iteration budget under which every instance
-   converged (plus one spare), times it and keeps the fastest.  chosen
-   (3 ints, may be NULL) receives block, sweeps and budget.  Waits for
-   stream. */
+   converged (plus one spare), times it and keeps the fastest schedule.
+   Since a step's iterations end on the device once every instance has
+   converged, the budget kept is only a cap: twice the probed one, at least
+   16 (at most 200; 200 when no candidate converged every instance within
+   40 iterations).  chosen (3 ints, may be NULL) receives block, sweeps and
+   budget.  Waits for stream. */
 sfx_status sfx_batch_autotune(sfx_batch* b, const void* phi, const void* ur, const void* uz,
                               const void* f, const void* F, double tol, void* stream,
                               int* chosen);

@@ -241,13 +241,14 @@ class Context:
 
 
 class Batch:
-    """Many independent axisymmetric instances stepped together (sfx_batch_*).
+    """Many independent instances stepped together (sfx_batch_*).
 
     `instances` is a sequence of (nr, nz, h, dt, params); fields are packed
-    back to back, instance i at the offsets of `layout()`.
+    back to back, instance i at the offsets of `layout()`.  geom is
+    SFX_AXISYM (rings) or SFX_PLANAR2D (planar cells of unit depth).
     """
 
-    def __init__(self, instances):
+    def __init__(self, instances, geom=None):
         n = len(instances)
         arr = (_lib.BatchInstance * n)()
         for i, (nr, nz, h, dt, p) in enumerate(instances):
@@ -255,7 +256,11 @@ class Batch:
             arr[i] = _lib.BatchInstance(int(nr), int(nz), float(h), float(dt), ps)
         self.n = n
         h_ = C.c_void_p()
-        _check(lib().sfx_batch_create(arr, n, C.byref(h_)), "sfx_batch_create")
+        if geom is None:
+            _check(lib().sfx_batch_create(arr, n, C.byref(h_)), "sfx_batch_create")
+        else:
+            _check(lib().sfx_batch_create_geom(arr, n, int(geom), C.byref(h_)),
+                   "sfx_batch_create_geom")
         self._h = h_
 
     def close(self):

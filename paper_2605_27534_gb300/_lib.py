@@ -22,7 +22,7 @@ EXPORTS = [
     "sfx_ctx_destroy", "sfx_default_opts", "sfx_phase_field_build", "sfx_advect",
     "sfx_mg_solve", "sfx_surfactant_step", "sfx_totals", "sfx_marangoni_force", "sfx_cfl_dt",
     "sfx_profile", "sfx_profile_read", "sfx_totals_noalloc", "sfx_df_pack", "sfx_df_unpack",
-    "sfx_set_tuning", "sfx_batch_create", "sfx_batch_destroy",
+    "sfx_set_tuning", "sfx_batch_create", "sfx_batch_create_geom", "sfx_batch_destroy",
     "sfx_batch_layout", "sfx_batch_set_schedule", "sfx_batch_step", "sfx_batch_stats",
     "sfx_batch_autotune", "sfx_batch_work", "sfx_f_from_gamma", "sfx_marangoni_loss",
     "sfx_adjoint_apply", "sfx_adjoint_step", "sfx_vof_advect", "sfx_capillary_force", "sfx_acdi_step", "sfx_batch_reuse_phi",
@@ -124,6 +124,8 @@ def load(path: str = SO_PATH):
     ip, fp, dpp = C.POINTER(C.c_int), C.POINTER(C.c_float), C.POINTER(C.c_double)
     L.sfx_batch_create.restype = C.c_int
     L.sfx_batch_create.argtypes = [C.POINTER(BatchInstance), C.c_int, C.POINTER(vp)]
+    L.sfx_batch_create_geom.restype = C.c_int
+    L.sfx_batch_create_geom.argtypes = [C.POINTER(BatchInstance), C.c_int, C.c_int, C.POINTER(vp)]
     L.sfx_batch_destroy.restype = None
     L.sfx_batch_destroy.argtypes = [vp]
     L.sfx_batch_layout.restype = C.c_int

@@ -252,7 +252,8 @@ __global__ void k_b_totals(const BInst* __restrict__ I, BPtr P) {
   const ix n = (ix)L.ncell(), nx = (ix)L.nx;
   float2 acc[2] = {make_float2(0.0f, 0.0f), make_float2(0.0f, 0.0f)};
   for (ix c = part * blockDim.x + threadIdx.x; c < n; c += kTotBlocks * blockDim.x) {
-    const float w = 2.0f * (float)(c % nx) + 1.0f;   // ring volume / (pi h^3)
+    // ring volume / (pi h^3), or 1 for planar cells (volume h^2)
+    const float w = L.geom == SFX_AXISYM ? 2.0f * (float)(c % nx) + 1.0f : 1.0f;
 #pragma unroll
     for (int fld = 0; fld < 2; ++fld) {
       float2 v = (fld ? P.F : P.f)[B.coff + c];
@@ -300,8 +301,9 @@ __global__ void k_b_totals_final(const BInst* __restrict__ I, int n, BPtr P) {
     }
     warp_sum_comp(s, cc);
     if (threadIdx.x == 0) {
-      const double h = I[inst].p.L.h;
-      P.mass[2 * inst + fld] = (s + cc) * kPi * h * h * h;
+      const Level& L = I[inst].p.L;
+      const double h = L.h;
+      P.mass[2 * inst + fld] = (s + cc) * (L.geom == SFX_AXISYM ? kPi * h * h * h : h * h);
     }
   }
 }
@@ -482,7 +484,13 @@ bool inst_ok(const sfx_batch_instance& q) {
 extern "C" {
 
 sfx_status sfx_batch_create(const sfx_batch_instance* inst, int n, sfx_batch** out) {
+  return sfx_batch_create_geom(inst, n, SFX_AXISYM, out);
+}
+
+sfx_status sfx_batch_create_geom(const sfx_batch_instance* inst, int n, int geom,
+                                 sfx_batch** out) {
   if (!out || !inst || n < 1) return SFX_ERR_ARG;
+  if (geom != SFX_AXISYM && geom != SFX_PLANAR2D) return SFX_ERR_ARG;
   *out = nullptr;
   for (int i = 0; i < n; ++i)
     if (!inst_ok(inst[i])) return SFX_ERR_ARG;
@@ -492,7 +500,7 @@ sfx_status sfx_batch_create(const sfx_batch_instance* inst, int n, sfx_batch** o
   for (int i = 0; i < n; ++i) {
     const sfx_batch_instance& q = inst[i];
     BInst B{};
-    Level L{SFX_AXISYM, q.nr, q.nz, 1, q.h};
+    Level L{geom, q.nr, q.nz, 1, q.h};
     B.p = Nw32{L, (float)(1.0 / q.h), (float)(q.params.Df / q.h), (float)(q.params.DF / q.h),
                (float)(1.0 / q.dt), (float)q.params.ka, (float)q.params.kd,
                (float)q.params.gamma_inf, (float)(1.0 / q.params.eps), (float)q.params.eta,
@@ -742,6 +750,11 @@ sfx_status sfx_batch_autotune(sfx_batch* b, const void* phi, const void* ur, con
   cudaFree(fw);
   cudaFree(Fw);
   if (st != SFX_OK) return st;
+  // the iteration loop ends on the device once every instance converged,
+  // so the budget is only a cap: keep room for later steps that need more
+  // iterations than the probed one
+  // (200 when no candidate converged every instance within the probe's 40)
+  bit = best < 1e30f ? std::min(200, std::max(2 * bit, 16)) : 200;
   st = sfx_batch_set_schedule(b, bb, bsw, bit);
   if (chosen) {
     chosen[0] = bb;

@@ -45,10 +45,11 @@ def _pack(arrs):
 class _Batch:
     """Device arrays of a batch built from _instances()."""
 
-    def __init__(self, sfx, inst, flow=True):
+    def __init__(self, sfx, inst, flow=True, geom=None):
         import torch
         self.inst = inst
-        self.b = sfx.Batch([(c.grid.nx, c.grid.ny, c.grid.h, c.dt, c.params) for c, _, _ in inst])
+        self.b = sfx.Batch([(c.grid.nx, c.grid.ny, c.grid.h, c.dt, c.params) for c, _, _ in inst],
+                           geom=geom)
         nc, nrf, nzf, co, ro, zo = self.b.sfx_batch_layout()
         self.co = co
         assert nc == sum(c.grid.nx * c.grid.ny for c, _, _ in inst)
@@ -204,7 +205,7 @@ def test_autotune_keeps_state_and_converges(sfx):
     block, sweeps, budget = B.b.sfx_batch_autotune(B.phi, B.f, B.F, 1e-10, ur=B.ur, uz=B.uz)
     torch.cuda.synchronize()
     assert torch.equal(B.f, f0) and torch.equal(B.F, F0)
-    assert block in (128, 256) and sweeps in (2, 3, 4) and 2 <= budget <= 41
+    assert block in (128, 256) and sweeps in (2, 3, 4) and 16 <= budget <= 200
     B.step(1e-10)
     st = B.b.sfx_batch_stats()
     assert all(st["converged"]) and max(st["iters"]) <= budget
@@ -223,3 +224,72 @@ def test_batch_rejects_bad_arguments(sfx):
         B.b.sfx_batch_step(B.phi, B.f, B.F, 1e-10, ur=B.ur, uz=None)
     with pytest.raises(sfx.SfxError):
         B.b.sfx_batch_step(B.phi, B.f, B.f, 1e-10)
+
+
+def _flat_instances(seed=13):
+    """Flat-interface columns of Sec. 4.3 (planar) of uneven sizes, Langmuir
+    kinetics with log10 Bi, log10 Da in [-2, 2]."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for nx, ny in [(4, 64), (8, 96), (5, 50), (8, 128), (3, 40)]:
+        Bi, Da = 10.0 ** rng.uniform(-2, 2, size=2)
+        c = W.case_flat_kinetics(ny, Bi, Da, nx=nx, steps=3)
+        _, phi, _ = oracle.phase_field_build(c.grid, c.C, c.redist_iters, c.dtau, c.params.eps)
+        out.append((c, phi, np.zeros(c.grid.shape)))
+    return out
+
+
+def test_planar_kinetics_sweep_matches_oracle_and_conserves(sfx):
+    """The batched form on planar instances (sfx_batch_create_geom): each
+    column against the FP64 oracle after three no-flow steps, and the total
+    sum h^2 (f + F) of every column kept to 1e-10."""
+    inst = _flat_instances()
+    B = _Batch(sfx, inst, flow=False, geom=sfx.SFX_PLANAR2D)
+    B.b.sfx_batch_set_schedule(256, 3, 60)
+    for _ in range(3):
+        B.step(1e-10)
+        st = B.b.sfx_batch_stats()
+        assert all(st["converged"]), st
+    got = B.fields(sfx)
+    for k, ((c, phi, f0), (fg, Fg)) in enumerate(zip(inst, got)):
+        f_o, F_o = f0.copy(), c.F0.copy()
+        for _ in range(3):
+            f_o, F_o, so = oracle.surfactant_step(c.grid, c.params, phi, f_o, F_o, c.dt, 1e-13)
+            assert so.converged
+        scale = max(np.abs(F_o).max(), np.abs(f_o).max())
+        assert np.abs(Fg - F_o).max() / scale < F32_TOL, k
+        assert np.abs(fg - f_o).max() / scale < F32_TOL, k
+        M0 = c.grid.h ** 2 * (f0 + c.F0).sum()
+        M = st["mass_f"][k] + st["mass_F"][k]
+        assert abs(M - M0) <= 1e-10 * M0, k
+        assert abs(st["mass_f"][k] - c.grid.h ** 2 * fg.sum()) <= 1e-12 * M0, k
+
+
+def test_planar_batch_bitwise_equals_single_grid_steps(sfx):
+    """Fixed budget: planar batched kernels run the single-grid SFX_F32
+    arithmetic cell for cell, as the axisymmetric ones do."""
+    import torch
+    inst = _flat_instances(seed=21)
+    B = _Batch(sfx, inst, flow=False, geom=sfx.SFX_PLANAR2D)
+    B.b.sfx_batch_set_schedule(128, 2, 4)
+    for _ in range(2):
+        B.step(1e-30)
+    fb, Fb = B.f.cpu().numpy(), B.F.cpu().numpy()
+    o = sfx.default_opts(tol=1e-30, max_cycles=4, nu1=2, nu2=0)
+    for k, (c, phi, f0) in enumerate(inst):
+        ctx = sfx.Context.for_grid(c.grid, sfx.SFX_F32)
+        f, F = sfx.sfx_df_pack(dev(f0)), sfx.sfx_df_pack(dev(c.F0))
+        for _ in range(2):
+            ctx.sfx_surfactant_step(c.params, dev(phi), f, F, c.dt, opts=o,
+                                    allow_not_converged=True)
+        torch.cuda.synchronize()
+        n = c.grid.nx * c.grid.ny
+        off = B.co[k]
+        assert np.array_equal(f.cpu().numpy().reshape(-1, 2), fb[off:off + n]), k
+        assert np.array_equal(F.cpu().numpy().reshape(-1, 2), Fb[off:off + n]), k
+
+
+def test_batch_rejects_a_3d_geometry(sfx):
+    c, _, _ = _flat_instances()[0]
+    with pytest.raises(sfx.SfxError):
+        sfx.Batch([(c.grid.nx, c.grid.ny, c.grid.h, c.dt, c.params)], geom=sfx.SFX_CART3D)

@@ -458,6 +458,34 @@ def batch_axi(n_inst=64, seed=3, steps=500):
     return out
 
 
+def case_flat_kinetics(ny, Bi, Da, nx=8, eps_cells=0.75, dt=1e-3, steps=100):
+    """Flat-interface kinetics of Sec. 4.3 as a planar column: y in [-4, 4]
+    (L = 1), interface at y = 0 with fluid 1 (no bulk surfactant) below, no
+    flow, a clean interface and F = 1 above it.  Langmuir kinetics with
+    Gamma_inf = F_inf = D_F = D_f = 1, so that Da = r_a Gamma_inf^2/(D_F
+    F_inf) = k_a and Bi = r_d = k_d in the scalings of Sec. 4.3."""
+    h = 8.0 / ny
+    g = Grid(PLANAR, nx, ny, 1, h)
+    y = -4.0 + (np.arange(ny) + 0.5) * h
+    C = np.zeros(g.shape)
+    C[0, y < 0.0, :] = 1.0
+    p = Params(ka=Da, kd=Bi, gamma_inf=1.0, Df=1.0, DF=1.0, eps=eps_cells * h,
+               bc_F=1.0, bc_f=0.0)
+    return Case("flat_%dx%d" % (nx, ny), g, p, C, 1.0 - C, np.zeros_like(C), dt=dt,
+                steps=steps, extra=dict(Bi=Bi, Da=Da))
+
+
+def batch_flat_kinetics(n_inst=512, ny=256, nx=8, seed=5, steps=100, dt=2.5e-4):
+    """A sweep of flat-interface columns with log10 Bi, log10 Da uniform in
+    [-2, 2] (seeded); dt = 2.5e-4 keeps D dt/h^2 = 0.26 at ny = 256."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for _ in range(n_inst):
+        Bi, Da = 10.0 ** rng.uniform(-2, 2), 10.0 ** rng.uniform(-2, 2)
+        out.append(case_flat_kinetics(ny, Bi, Da, nx=nx, steps=steps, dt=dt))
+    return out
+
+
 def case_adjoint_2d(n=256, seed=4, corr=4.0):
     """Adjoint workload: the 2D adsorption physics at n^2 with a seeded
     interfacial perturbation Gamma0 = 0.05 (1 + g), g smooth noise."""
