@@ -49,8 +49,7 @@ struct BPtr {
   float2* F;
   float2* fs;
   float2* Fs;
-  float* Bf[2];           // radial, axial drift faces of the f problem
-  float* BF[2];
+  float2* B2[2];          // radial, axial drift faces (B_f, B_F)
   __half2* H2[2];         // (B_f, B_F) in half precision (correction sweeps)
   float4* coef;
   float2* res;
@@ -76,8 +75,7 @@ __global__ void k_b_drift(const BInst* __restrict__ I, int n, const int* __restr
   const size_t q = (size_t)(blockIdx.x - pre[inst]) * blockDim.x + threadIdx.x;
   if (q >= nf) return;
   const size_t fo = dir == 0 ? B.rfoff : B.zfoff;
-  float* Bf = P.Bf[dir] + fo;
-  float* BF = P.BF[dir] + fo;
+  float2* B2 = P.B2[dir] + fo;
   const double* phi = P.phi + B.coff;
   const int fx = L.nx + (dir == 0);
   const int i = (int)(q % fx), j = (int)(q / fx);
@@ -90,8 +88,7 @@ __global__ void k_b_drift(const BInst* __restrict__ I, int n, const int* __restr
     const float nR = normal_f32(L, phi, i, j, 0, dir, B.p.inv_eps);
     drift_face(sL, sR, nL, nR, B.Df, B.DF, B.p.inv_eps, bf, bF);
   }
-  Bf[q] = bf;
-  BF[q] = bF;
+  B2[q] = make_float2(bf, bF);
   P.H2[dir][fo + q] = __floats2half2_rn(bf, bF);
 }
 
@@ -146,10 +143,9 @@ __global__ void k_b_resid(const BInst* __restrict__ I, int n, const int* __restr
   float m[4] = {0.0f, 0.0f, 0.0f, 0.0f};
   if (c < L.ncell()) {
     const int i = (int)((ix)c % (ix)L.nx), j = (int)((ix)c / (ix)L.nx);
-    const float* Bf[3] = {P.Bf[0] + B.rfoff, P.Bf[1] + B.zfoff, nullptr};
-    const float* BF[3] = {P.BF[0] + B.rfoff, P.BF[1] + B.zfoff, nullptr};
+    const float2* B2[3] = {P.B2[0] + B.rfoff, P.B2[1] + B.zfoff, nullptr};
     const size_t o = B.coff, w = B.poff;
-    resid2_cell(B.p, i, j, 0, c, P.phi32 + o, Bf, BF, P.f + o, P.F + o, P.fs + o, P.Fs + o,
+    resid2_cell(B.p, i, j, 0, c, P.phi32 + o, B2, P.f + o, P.F + o, P.fs + o, P.Fs + o,
                 P.coef + w, P.res + w, m, P.e2 + w);
   }
   // block maxima; the flags kernel combines the blocks of each instance
@@ -539,10 +535,8 @@ sfx_status sfx_batch_create_geom(const sfx_batch_instance* inst, int n, int geom
   if (st == SFX_OK) st = balloc(b, &P.phi32, nc);
   if (st == SFX_OK) st = balloc(b, &P.fs, nc);
   if (st == SFX_OK) st = balloc(b, &P.Fs, nc);
-  if (st == SFX_OK) st = balloc(b, &P.Bf[0], b->nrf);
-  if (st == SFX_OK) st = balloc(b, &P.Bf[1], b->nzf);
-  if (st == SFX_OK) st = balloc(b, &P.BF[0], b->nrf);
-  if (st == SFX_OK) st = balloc(b, &P.BF[1], b->nzf);
+  if (st == SFX_OK) st = balloc(b, &P.B2[0], b->nrf);
+  if (st == SFX_OK) st = balloc(b, &P.B2[1], b->nzf);
   if (st == SFX_OK) st = balloc(b, &P.H2[0], b->nrf);
   if (st == SFX_OK) st = balloc(b, &P.H2[1], b->nzf);
   if (st == SFX_OK) st = balloc(b, &P.coef, b->npack);

@@ -40,7 +40,7 @@ namespace {
 
 __global__ void k_drift32(Level L, int d, const double* __restrict__ phi, float Df, float DF,
                           float inv_eps, float* __restrict__ Bf, float* __restrict__ BF,
-                          __half2* __restrict__ H2) {
+                          float2* __restrict__ B2, __half2* __restrict__ H2) {
   size_t n = L.nface(d);
   int fx = L.nx + (d == 0), fy = L.ny + (d == 1);
   for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < n;
@@ -57,6 +57,7 @@ __global__ void k_drift32(Level L, int d, const double* __restrict__ phi, float 
     }
     Bf[q] = bf;
     BF[q] = bF;
+    B2[q] = make_float2(bf, bF);
     H2[q] = __floats2half2_rn(bf, bF);
   }
 }
@@ -289,11 +290,10 @@ __global__ void k_corr32(Corr32 p, const float* __restrict__ Bx, const float* __
 // the coupled one does not.
 // Evaluate both residuals (pairs), the 2x2 exchange Jacobian and the
 // norms at every cell of the current state.
-__global__ void __launch_bounds__(256, 4)
-k_resid2_32(Nw32 p, const float* __restrict__ phi, const float* __restrict__ Bfx,
-            const float* __restrict__ Bfy, const float* __restrict__ Bfz,
-            const float* __restrict__ BFx, const float* __restrict__ BFy,
-            const float* __restrict__ BFz, const float2* __restrict__ fin,
+__global__ void __launch_bounds__(256, 5)
+k_resid2_32(Nw32 p, const float* __restrict__ phi, const float2* __restrict__ B2x,
+            const float2* __restrict__ B2y, const float2* __restrict__ B2z,
+            const float2* __restrict__ fin,
             const float2* __restrict__ Fin, const float2* __restrict__ fst,
             const float2* __restrict__ Fst, float4* __restrict__ coef,
             float2* __restrict__ res, unsigned int* norms, float2* __restrict__ e2,
@@ -301,16 +301,14 @@ k_resid2_32(Nw32 p, const float* __restrict__ phi, const float* __restrict__ Bfx
   if (done && *done) return;   // converged at an earlier iteration
   const Level& L = p.L;
   float m[4] = {0.0f, 0.0f, 0.0f, 0.0f};
-  const float* Bf[3] = {Bfx, Bfy, Bfz};
-  const float* BF[3] = {BFx, BFy, BFz};
+  const float2* B2[3] = {B2x, B2y, B2z};
   // blocks over (x chunk, rows); each block walks rows r = k ny + j
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const ix rows = (ix)L.ny * (ix)L.nz;
   for (ix r = blockIdx.y; r < rows; r += gridDim.y) {
     const int j = (int)(r % (ix)L.ny), k = (int)(r / (ix)L.ny);
     if (i < L.nx)
-      resid2_cell(p, i, j, k, r * (ix)L.nx + (ix)i, phi, Bf, BF, fin, Fin, fst, Fst, coef, res, m,
-                  e2);
+      resid2_cell(p, i, j, k, r * (ix)L.nx + (ix)i, phi, B2, fin, Fin, fst, Fst, coef, res, m, e2);
   }
   if (norms) {
     // warp maxima, then one atomic per block and norm
@@ -1209,6 +1207,7 @@ sfx_status solve_newton32(sfx_ctx* c, const Nw32& p, const float* phi, float* co
   int* flag = c->f32.flag;
   const RowGrid rg = row_grid(L);
   const __half2* Hz = L.ndim() == 3 ? c->f32.H2[2] : nullptr;
+  const float2* B2[3] = {c->f32.B2[0], c->f32.B2[1], L.ndim() == 3 ? c->f32.B2[2] : nullptr};
   SFX_CUDA(cudaMemsetAsync(flag, 0, 2 * sizeof(int), s));
   // Each iteration: the residual pass (which also does the first red
   // half-sweep of the correction, from zero), a device-side convergence
@@ -1223,8 +1222,8 @@ sfx_status solve_newton32(sfx_ctx* c, const Nw32& p, const float* phi, float* co
   for (it = 1; it <= o->max_cycles; ++it) {
     unsigned int* nbuf = dn + 4 * (it & 1);
     SFX_CUDA(cudaMemsetAsync(nbuf, 0, 4 * sizeof(unsigned int), s));
-    SFX_KERNEL(c, K_RESIDUAL, k_resid2_32, rg.grid, rg.block, s, p, phi, Bf[0], Bf[1], Bf[2], BF[0], BF[1],
-               BF[2], fc, Fc, fs, Fs, c->f32.coef, c->f32.res, nbuf, c->f32.e2, flag);
+    SFX_KERNEL(c, K_RESIDUAL, k_resid2_32, rg.grid, rg.block, s, p, phi, B2[0], B2[1], B2[2], fc,
+               Fc, fs, Fs, c->f32.coef, c->f32.res, nbuf, c->f32.e2, flag);
     if (it == 1 && predicted) {
       // keep the predicted start only if its residual is already small;
       // otherwise restart from x* (both launches return at once when kept)
@@ -1232,8 +1231,8 @@ sfx_status solve_newton32(sfx_ctx* c, const Nw32& p, const float* phi, float* co
       const float rho = c->f32.predict_rho;
       SFX_KERNEL(c, K_OTHER, k_pred_check32, 1, 32, s, nbuf, rho, ok);
       SFX_KERNEL(c, K_SETUP, k_restore32, nb, 256, s, n, ok, fs, Fs, fc, Fc);
-      SFX_KERNEL(c, K_RESIDUAL, k_resid2_32, rg.grid, rg.block, s, p, phi, Bf[0], Bf[1], Bf[2], BF[0],
-                 BF[1], BF[2], fc, Fc, fs, Fs, c->f32.coef, c->f32.res, nbuf, c->f32.e2, ok);
+      SFX_KERNEL(c, K_RESIDUAL, k_resid2_32, rg.grid, rg.block, s, p, phi, B2[0], B2[1], B2[2],
+                 fc, Fc, fs, Fs, c->f32.coef, c->f32.res, nbuf, c->f32.e2, ok);
     }
     SFX_KERNEL(c, K_OTHER, k_flag32, 1, 32, s, nbuf, tolf, it, flag);
     SFX_CUDA(cudaMemcpyAsync(hn + 4 * (it & 1), nbuf, 4 * sizeof(unsigned int),
@@ -1296,7 +1295,7 @@ sfx_status step_f32(sfx_ctx* c, const sfx_params* pr, const double* phi_in, cons
     for (int d = 0; d < nd; ++d)
       SFX_KERNEL(c, K_SETUP, k_drift32, blocks_for(L.nface(d), 256), 256, s, L, d, phi_in,
                  (float)pr->Df, (float)pr->DF, (float)(1.0 / pr->eps), Bf[d], BF[d],
-                 c->f32.H2[d]);
+                 c->f32.B2[d], c->f32.H2[d]);
     SFX_LAUNCH_CHECK();
     c->f32.drift_phi = phi_in;
     c->f32.drift_key[0] = pr->Df;
@@ -1514,6 +1513,7 @@ sfx_status f32_ensure_scratch(sfx_ctx* c) {
   for (int d = 0; d < L.ndim(); ++d) {
     if ((st = get(L.nface(d) * sizeof(float), (void**)&c->f32.Bf[d])) != SFX_OK) return st;
     if ((st = get(L.nface(d) * sizeof(float), (void**)&c->f32.BF[d])) != SFX_OK) return st;
+    if ((st = get(L.nface(d) * sizeof(float2), (void**)&c->f32.B2[d])) != SFX_OK) return st;
     if ((st = get(L.nface(d) * sizeof(__half2), (void**)&c->f32.H2[d])) != SFX_OK) return st;
   }
   if ((st = get(n * sizeof(float2), (void**)&c->f32.fstar)) != SFX_OK) return st;

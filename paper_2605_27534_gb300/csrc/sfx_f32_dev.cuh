@@ -182,6 +182,27 @@ __device__ __forceinline__ void faces6(const Level& L, const T* Bx, const T* By,
   B[5] = has[5] ? face_val(Bz[c + (ix)L.nx * (ix)L.ny]) : 0.0f;
 }
 
+// faces6 for both fields at once from packed (B_f, B_F) float2 faces.
+__device__ __forceinline__ void faces6f2(const Level& L, const float2* Bx, const float2* By,
+                                         const float2* Bz, int i, int j, int k, const bool* has,
+                                         float* Bf, float* BF) {
+  const ix c = cidx32(L, i, j, k);
+  const ix fx = c + (ix)k * (ix)L.ny + (ix)j, fy = c + (ix)k * (ix)L.nx;
+  const float2 z = make_float2(0.0f, 0.0f);
+  float2 v[6];
+  v[0] = has[0] ? Bx[fx] : z;
+  v[1] = has[1] ? Bx[fx + 1] : z;
+  v[2] = has[2] ? By[fy] : z;
+  v[3] = has[3] ? By[fy + L.nx] : z;
+  v[4] = has[4] ? Bz[c] : z;
+  v[5] = has[5] ? Bz[c + (ix)L.nx * (ix)L.ny] : z;
+#pragma unroll
+  for (int q = 0; q < 6; ++q) {
+    Bf[q] = v[q].x;
+    BF[q] = v[q].y;
+  }
+}
+
 // faces6 for both fields at once from the packed (B_f, B_F) half2 faces.
 __device__ __forceinline__ void faces6x2(const Level& L, const __half2* Hx, const __half2* Hy,
                                          const __half2* Hz, int i, int j, int k, const bool* has,
@@ -361,7 +382,7 @@ __device__ __forceinline__ void face32v2(const Adv32& A, const float2* __restric
 // e = M_c^-1 r_c.
 __device__ __forceinline__ void resid2_cell(const Nw32& p, int i, int j, int k, ix c,
                                             const float* __restrict__ phi,
-                                            const float* const* Bf, const float* const* BF,
+                                            const float2* const* B2,
                                             const float2* __restrict__ fin,
                                             const float2* __restrict__ Fin,
                                             const float2* __restrict__ fst,
@@ -374,15 +395,14 @@ __device__ __forceinline__ void resid2_cell(const Nw32& p, int i, int j, int k, 
   gather6(L, i, j, k, c, has, nbi);
   float2 nb[6];
   const float2 fc = fin[c], Fc = Fin[c];
-  float B[6], df_, dF_;
+  float Bf[6], BF[6], df_, dF_;
+  faces6f2(L, B2[0], B2[1], B2[2], i, j, k, has, Bf, BF);
 #pragma unroll
   for (int q = 0; q < 6; ++q) nb[q] = has[q] ? fin[nbi[q]] : make_float2(0.0f, 0.0f);
-  faces6(L, Bf[0], Bf[1], Bf[2], i, j, k, has, B);
-  const float2 flf = flux_pair(L, p.invh, p.Dfh, p.literal, i, fc, nb, has, B, df_);
+  const float2 flf = flux_pair(L, p.invh, p.Dfh, p.literal, i, fc, nb, has, Bf, df_);
 #pragma unroll
   for (int q = 0; q < 6; ++q) nb[q] = has[q] ? Fin[nbi[q]] : make_float2(0.0f, 0.0f);
-  faces6(L, BF[0], BF[1], BF[2], i, j, k, has, B);
-  const float2 flF = flux_pair(L, p.invh, p.DFh, p.literal, i, Fc, nb, has, B, dF_);
+  const float2 flF = flux_pair(L, p.invh, p.DFh, p.literal, i, Fc, nb, has, BF, dF_);
   // exchange q = c1 F (f_inf - f) - r_d f, one evaluation for both equations
   const PhiPair ph = unfold(phi[c]);
   const float c1 = __fdividef(p.ka, ph.p + p.eta);

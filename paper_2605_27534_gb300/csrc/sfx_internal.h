@@ -36,6 +36,7 @@ struct F32Scratch {
   bool ready = false;
   float* Bf[3] = {};
   float* BF[3] = {};
+  float2* B2[3] = {};     // (B_f, B_F) per face (the Newton residual pass)
   __half2* H2[3] = {};    // (B_f, B_F) per face in half precision (correction sweeps)
   float2* fstar = nullptr;
   float2* Fstar = nullptr;
