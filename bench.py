@@ -45,9 +45,9 @@ SAMPLE_N = 64          # oracle sample: centred 64^3 block of the same grid
 # withdrawn (None) as soon as those sources differ from the captured ones.
 NCU_TRAFFIC = {
     ("smooth_fine", "f32", 3): {
-        "bytes_per_cell": (6 * 139.64e6 + 239.35e6) / 7 / 160 ** 3,
+        "bytes_per_cell": (6 * 139.73e6 + 240.27e6) / 7 / 160 ** 3,
         "sources": ["sfx_f32.cu", "sfx_f32_dev.cuh", "sfx_df.cuh", "sfx_common.cuh"],
-        "sha256_16": "0b85afe765401a29",
+        "sha256_16": "cf167fd2b422ad93",
         "capture": "profiles/corr2_hr3d160_f32.md (160^3, launches 5-7, weighted 6:1 as in an "
                    "iteration of 4 sweeps), scaled by the cell count",
     },
