@@ -458,6 +458,9 @@ __device__ __forceinline__ void corr2_cell(const Nw32& p, int i, int j, int k,
                                            const float2* __restrict__ res,
                                            float2* __restrict__ e2, int color, int first,
                                            float2* __restrict__ fst, float2* __restrict__ Fst) {
+  // the other colour's corrections are only read in this launch: read them
+  // through a separate read-only view of the array
+  const float2* __restrict__ eo = e2;
   const Level& L = p.L;
   const ix c = cidx32(L, i, j, k);
   bool has[6];
@@ -479,7 +482,7 @@ __device__ __forceinline__ void corr2_cell(const Nw32& p, int i, int j, int k,
   float enf[6], enF[6];
 #pragma unroll
   for (int q = 0; q < 6; ++q) {
-    const float2 v = (has[q] && !zero_nb) ? e2[nbi[q]] : make_float2(0.0f, 0.0f);
+    const float2 v = (has[q] && !zero_nb) ? __ldg(eo + nbi[q]) : make_float2(0.0f, 0.0f);
     enf[q] = v.x;
     enF[q] = v.y;
   }
@@ -510,7 +513,7 @@ __device__ __forceinline__ void corr2_cell(const Nw32& p, int i, int j, int k,
     const int ir = i ^ 1;
     if (ir < L.nx) {
       const ix cr = c - (ix)i + (ix)ir;
-      const float2 er = e2[oth];
+      const float2 er = __ldg(eo + oth);
       fst[cr] = df_add(fst[cr], er.x);
       Fst[cr] = df_add(Fst[cr], er.y);
     }
