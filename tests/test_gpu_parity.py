@@ -251,6 +251,30 @@ def test_surfactant_step_parity_fp32(sfx, name):
         assert abs(stt.mass_f + stt.mass_F - M0) < MASS_DRIFT * abs(M0)
 
 
+@pytest.mark.parametrize("Bi", [0.1, 1.0, 10.0])
+@pytest.mark.parametrize("Da", [0.1, 1.0, 10.0])
+def test_hr3d_kinetics_grid_fp32(sfx, Bi, Da):
+    """The 3D HR configuration over (Bi, Da) in {0.1, 1, 10}^2 (the bench
+    times (1, 1)): two SFX_F32 steps at 24^3 against the FP64 oracle."""
+    import torch
+    c = W.case_hr_3d(n=24, Bi=Bi, Da=Da, steps=2)
+    g, p = c.grid, c.params
+    _, phi, _ = oracle.phase_field_build(g, c.C, c.redist_iters, c.dtau, p.eps)
+    f_o, F_o = np.zeros(g.shape), c.F0.copy()
+    for _ in range(2):
+        f_o, F_o, st = oracle.surfactant_step(g, p, phi, f_o, F_o, c.dt, 1e-13, c.ux, c.uy, c.uz)
+        assert st.converged
+    ctx = _ctx(sfx, g, 1)
+    f, F = _pairs(ctx, np.zeros(g.shape)), _pairs(ctx, c.F0)
+    u = [dev(v, torch.float32) for v in (c.ux, c.uy, c.uz)]
+    opts = sfx.default_opts(tol=1e-10, max_cycles=400)
+    for _ in range(2):
+        assert ctx.sfx_surfactant_step(p, dev(phi), f, F, c.dt, *u, opts=opts).converged
+    scale = max(np.abs(F_o).max(), np.abs(f_o).max())
+    assert np.abs(host(ctx.sfx_df_unpack(F)) - F_o).max() / scale < F32_TOL
+    assert np.abs(host(ctx.sfx_df_unpack(f)) - f_o).max() / scale < F32_TOL
+
+
 @pytest.mark.parametrize("name", ["adsorption2d", "hr3d", "axi"])
 def test_fused_sweep_equals_colour_launches_bitwise(sfx, name):
     import torch
