@@ -363,12 +363,14 @@ sfx_status sfx_adjoint_apply(sfx_ctx* ctx, const sfx_params* params, const doubl
 /* One adjoint step.  f, F: the state after the forward step; lam_f, lam_F:
    in dL/d(f, F) after the step, out dL/d(f, F) before it (in place);
    dparams (host, 4 doubles, may be NULL): the step's dL/d(k_a, k_d, D_f,
-   D_F) is added.  The transposed system is relaxed by red-black Gauss-
-   Seidel with a 2x2 solve per cell, nu1 + nu2 sweeps between residual
-   checks, until max|lam1 - (-J)^T nu| <= tol max|lam1| or max_cycles
-   checks (then SFX_ERR_NOT_CONVERGED, outputs written).  stats (may be
-   NULL): picard = checks, vcycles = sweeps, res_f = res_F = the final
-   relative residual.  Waits for stream. */
+   D_F) is added.  The transposed system is solved by defect correction:
+   each check evaluates the FP64 residual r = lam1 - (-J)^T nu, and until
+   max|r| <= tol max|lam1| the correction of (-J)^T e = r is relaxed by
+   nu1 + nu2 FP32 red-black Gauss-Seidel sweeps (2x2 solve per cell, on
+   coefficients computed once per step from the FP64 operator) and added to
+   nu; after max_cycles checks SFX_ERR_NOT_CONVERGED (outputs written).
+   stats (may be NULL): picard = checks, vcycles = sweeps, res_f = res_F =
+   the final relative residual.  Waits for stream. */
 sfx_status sfx_adjoint_step(sfx_ctx* ctx, const sfx_params* params, const double* phi,
                             const double* f, const double* F, double dt, double* lam_f,
                             double* lam_F, double* dparams, const sfx_solve_opts* opts,

@@ -222,7 +222,7 @@ class Context:
         """lam (in place) from dL/dx after the step to dL/dx before it; adds
         the step's dL/d(k_a, k_d, D_f, D_F) to dparams (4 floats, a list)."""
         ps = params if isinstance(params, Params) else params_struct(params)
-        o = opts if opts is not None else default_opts(tol=1e-13, max_cycles=500, nu1=4, nu2=4)
+        o = opts if opts is not None else default_opts(tol=1e-13, max_cycles=500, nu1=10, nu2=10)
         dp = (C.c_double * 4)(*(dparams if dparams is not None else [0.0] * 4))
         st_ = StepStats()
         _check(lib().sfx_adjoint_step(self._h, C.byref(ps), _ptr(phi), _ptr(f), _ptr(F),

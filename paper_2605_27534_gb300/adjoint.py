@@ -92,7 +92,7 @@ class SurfactantRollout(torch.autograd.Function):
         from . import default_opts
         setup, ps = fctx.setup, fctx.ps
         ctx = setup.context
-        o = default_opts(tol=setup.adj_tol, max_cycles=1000, nu1=4, nu2=4)
+        o = default_opts(tol=setup.adj_tol, max_cycles=1000, nu1=10, nu2=10)
         # the final state, for dL/df
         last_f, last_F = (t.clone() for t in fctx.checkpoints[-1])
         rem = setup.nsteps - setup.K * (len(fctx.checkpoints) - 1)

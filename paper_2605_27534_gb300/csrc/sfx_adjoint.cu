@@ -13,8 +13,11 @@
 //   (-J)^T nu = lam1,   lam0 = nu/dt,   dL/dtheta += (dR/dtheta)^T nu,
 // with dR_f/dk_a = F (f_inf - f)/(phi + eta) = -dR_F/dk_a,
 // dR_f/dk_d = -f = -dR_F/dk_d, dR_f/dD_f = N^_f f and dR_F/dD_F = N^_F F
-// (N^ at unit diffusivity).  The transposed system is relaxed by red-black
-// Gauss-Seidel with a 2x2 solve per cell (the coupling is pointwise).
+// (N^ at unit diffusivity).  The transposed system is solved by defect
+// correction: the FP64 residual r = lam - (-J)^T nu decides convergence and
+// the correction e of (-J)^T e = r is relaxed by FP32 red-black Gauss-Seidel
+// with a 2x2 solve per cell (the coupling is pointwise) on coefficients
+// precomputed once per step from the FP64 operator.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -113,32 +116,13 @@ __global__ void k_adj_init(size_t n, double dt, const double* __restrict__ lf,
   }
 }
 
-// One colour of the red-black block Gauss-Seidel on (-J)^T nu = lam
-__global__ void k_adj_sweep(AdjP p, const double* __restrict__ phi, const double* __restrict__ f,
-                            const double* __restrict__ F, const double* __restrict__ lf,
-                            const double* __restrict__ lF, double* __restrict__ nf,
-                            double* __restrict__ nF, int color) {
-  const Level& L = p.L;
-  const int j = blockIdx.y, k = blockIdx.z;
-  const int i = 2 * (blockIdx.x * blockDim.x + threadIdx.x) + ((j + k + color) & 1);
-  if (i >= L.nx) return;
-  const size_t c = cidx(L, i, j, k);
-  const Kin q = kin_at(p, phi[c], f[c], F[c]);
-  double dTf, nTf, dTF, nTF;
-  flux_terms_T(L, op_of(p, 0, p.Df), nf, i, j, k, dTf, nTf);
-  flux_terms_T(L, op_of(p, 1, p.DF), nF, i, j, k, dTF, nTF);
-  const double A11 = q.a - dTf, A22 = q.e - dTF;
-  const double rf = lf[c] + nTf, rF = lF[c] + nTF;
-  const double det = A11 * A22 - q.d * q.b;
-  nf[c] = (A22 * rf + q.d * rF) / det;
-  nF[c] = (q.b * rf + A11 * rF) / det;
-}
-
-// max |lam - (-J)^T nu| and max |lam| over both fields
+// r = lam - (-J)^T nu (rounded to float into rout), max |r| and max |lam|
+// over both fields
 __global__ void k_adj_resid(AdjP p, const double* __restrict__ phi, const double* __restrict__ f,
                             const double* __restrict__ F, const double* __restrict__ lf,
                             const double* __restrict__ lF, const double* __restrict__ nf,
-                            const double* __restrict__ nF, unsigned long long* nrm) {
+                            const double* __restrict__ nF, float2* __restrict__ rout,
+                            unsigned long long* nrm) {
   const Level& L = p.L;
   const size_t n = L.ncell();
   const Op opf = op_of(p, 0, p.Df), opF = op_of(p, 1, p.DF);
@@ -153,6 +137,7 @@ __global__ void k_adj_resid(AdjP p, const double* __restrict__ phi, const double
     const double rf = lf[c] - (q.a * nf[c] - (dT * nf[c] + nT) - q.d * nF[c]);
     flux_terms_T(L, opF, nF, i, j, k, dT, nT);
     const double rF = lF[c] - (-q.b * nf[c] + q.e * nF[c] - (dT * nF[c] + nT));
+    rout[c] = make_float2((float)rf, (float)rF);
     double r = fmax(fabs(rf), fabs(rF));
     if (!(r <= 1e300)) r = INFINITY;   // NaN or Inf: never converged
     mr = fmax(mr, r);
@@ -163,6 +148,72 @@ __global__ void k_adj_resid(AdjP p, const double* __restrict__ phi, const double
   if ((threadIdx.x & 31) == 0) {
     atomic_max_nonneg(&nrm[0], mr);
     atomic_max_nonneg(&nrm[1], mb);
+  }
+}
+
+// Coefficients of the FP32 relaxation: per cell the inverse of the 2x2
+// block [[A11, -d], [-b, A22]] of (-J)^T (A11 = a - dT_f, A22 = e - dT_F) as
+// (A22, d, b, A11)/det, and the neighbour weights of N^T of both fields
+// (W[q N + c] for f, W[(6 + q) N + c] for F).
+__global__ void k_adj_coef(AdjP p, const double* __restrict__ phi, const double* __restrict__ f,
+                           const double* __restrict__ F, float4* __restrict__ K,
+                           float* __restrict__ W) {
+  const Level& L = p.L;
+  const size_t n = L.ncell();
+  const Op opf = op_of(p, 0, p.Df), opF = op_of(p, 1, p.DF);
+  for (size_t c = blockIdx.x * (size_t)blockDim.x + threadIdx.x; c < n;
+       c += (size_t)gridDim.x * blockDim.x) {
+    int i, j, k;
+    cell_ijk(L, c, i, j, k);
+    const Kin q = kin_at(p, phi[c], f[c], F[c]);
+    double dTf, dTF, wf[6], wF[6];
+    flux_weights_T(L, opf, i, j, k, dTf, wf);
+    flux_weights_T(L, opF, i, j, k, dTF, wF);
+    const double A11 = q.a - dTf, A22 = q.e - dTF;
+    const double idet = 1.0 / (A11 * A22 - q.d * q.b);
+    K[c] = make_float4((float)(A22 * idet), (float)(q.d * idet), (float)(q.b * idet),
+                       (float)(A11 * idet));
+#pragma unroll
+    for (int m = 0; m < 6; ++m) {
+      W[(size_t)m * n + c] = (float)wf[m];
+      W[(size_t)(6 + m) * n + c] = (float)wF[m];
+    }
+  }
+}
+
+// One colour of the FP32 red-black Gauss-Seidel on (-J)^T e = r
+__global__ void k_adj_csweep(Level L, const float4* __restrict__ K, const float* __restrict__ W,
+                             const float2* __restrict__ r, float2* __restrict__ e, int color) {
+  const int j = blockIdx.y, k = blockIdx.z;
+  const int i = 2 * (blockIdx.x * blockDim.x + threadIdx.x) + ((j + k + color) & 1);
+  if (i >= L.nx) return;
+  const size_t n = L.ncell();
+  const size_t c = cidx(L, i, j, k);
+  const size_t sy = (size_t)L.nx, sz = (size_t)L.nx * L.ny;
+  const bool has[6] = {i > 0, i + 1 < L.nx, j > 0, j + 1 < L.ny,
+                       L.geom == SFX_CART3D && k > 0, L.geom == SFX_CART3D && k + 1 < L.nz};
+  const size_t nb[6] = {c - 1, c + 1, c - sy, c + sy, c - sz, c + sz};
+  const float2 rc = r[c];
+  float sf = rc.x, sF = rc.y;
+#pragma unroll
+  for (int m = 0; m < 6; ++m) {
+    if (!has[m]) continue;
+    const float2 v = e[nb[m]];
+    sf += W[(size_t)m * n + c] * v.x;
+    sF += W[(size_t)(6 + m) * n + c] * v.y;
+  }
+  const float4 q = K[c];
+  e[c] = make_float2(q.x * sf + q.y * sF, q.z * sf + q.w * sF);
+}
+
+// nu += e
+__global__ void k_adj_add(size_t n, const float2* __restrict__ e, double* __restrict__ nf,
+                          double* __restrict__ nF) {
+  for (size_t c = blockIdx.x * (size_t)blockDim.x + threadIdx.x; c < n;
+       c += (size_t)gridDim.x * blockDim.x) {
+    const float2 v = e[c];
+    nf[c] += (double)v.x;
+    nF[c] += (double)v.y;
   }
 }
 
@@ -284,6 +335,10 @@ sfx_status adj_ensure_scratch(sfx_ctx* c) {
     return st;
   if ((st = get(8 * sizeof(double), (void**)&c->adj.d_out)) != SFX_OK) return st;
   if ((st = get(2 * sizeof(unsigned long long), (void**)&c->adj.d_nrm)) != SFX_OK) return st;
+  if ((st = get(n * sizeof(float4), (void**)&c->adj.K)) != SFX_OK) return st;
+  if ((st = get(12 * n * sizeof(float), (void**)&c->adj.W)) != SFX_OK) return st;
+  if ((st = get(n * sizeof(float2), (void**)&c->adj.r)) != SFX_OK) return st;
+  if ((st = get(n * sizeof(float2), (void**)&c->adj.e)) != SFX_OK) return st;
   SFX_CUDA(cudaMallocHost((void**)&c->adj.h_out, 8 * sizeof(double)));
   SFX_CUDA(cudaMallocHost((void**)&c->adj.h_nrm, 2 * sizeof(unsigned long long)));
   c->adj.ready = true;
@@ -325,20 +380,17 @@ sfx_status adjoint_step(sfx_ctx* c, const sfx_params* pr, const double* phi, con
   double* nf = c->adj.nf;
   double* nF = c->adj.nF;
   SFX_KERNEL(c, K_SETUP, k_adj_init, nb, kAdjThreads, s, n, dt, lf, lF, nf, nF);
+  SFX_KERNEL(c, K_SETUP, k_adj_coef, nb, kAdjThreads, s, p, phi, f, F, c->adj.K, c->adj.W);
   dim3 blk(128), grd((unsigned)(((L.nx + 1) / 2 + 127) / 128), (unsigned)L.ny, (unsigned)L.nz);
   const int sweeps = std::max(1, o->nu1 + o->nu2);
   bool conv = false;
   double rel = INFINITY;
   int checks = 0, total_sweeps = 0;
   for (checks = 1; checks <= o->max_cycles; ++checks) {
-    for (int q = 0; q < sweeps; ++q)
-      for (int color = 0; color < 2; ++color)
-        SFX_KERNEL(c, K_SMOOTH_FINE, k_adj_sweep, grd, blk, s, p, phi, f, F, lf, lF, nf, nF,
-                   color);
-    total_sweeps += sweeps;
+    // FP64 residual of the current nu: the convergence test and the defect
     SFX_CUDA(cudaMemsetAsync(c->adj.d_nrm, 0, 2 * sizeof(unsigned long long), s));
     SFX_KERNEL(c, K_RESIDUAL, k_adj_resid, nb, kAdjThreads, s, p, phi, f, F, lf, lF, nf, nF,
-               c->adj.d_nrm);
+               c->adj.r, c->adj.d_nrm);
     SFX_LAUNCH_CHECK();
     SFX_CUDA(cudaMemcpyAsync(c->adj.h_nrm, c->adj.d_nrm, 2 * sizeof(unsigned long long),
                              cudaMemcpyDeviceToHost, s));
@@ -352,6 +404,15 @@ sfx_status adjoint_step(sfx_ctx* c, const sfx_params* pr, const double* phi, con
       conv = true;
       break;
     }
+    if (checks == o->max_cycles) break;
+    // FP32 relaxation of the defect equation from e = 0, then nu += e
+    SFX_CUDA(cudaMemsetAsync(c->adj.e, 0, n * sizeof(float2), s));
+    for (int q = 0; q < sweeps; ++q)
+      for (int color = 0; color < 2; ++color)
+        SFX_KERNEL(c, K_SMOOTH_FINE, k_adj_csweep, grd, blk, s, L, c->adj.K, c->adj.W, c->adj.r,
+                   c->adj.e, color);
+    SFX_KERNEL(c, K_OTHER, k_adj_add, nb, kAdjThreads, s, n, c->adj.e, nf, nF);
+    total_sweeps += sweeps;
   }
   const int nbf = c->adj.nblk;
   SFX_KERNEL(c, K_OTHER, k_adj_finish, nbf, kAdjThreads, s, p, phi, f, F, nf, nF, lf, lF,

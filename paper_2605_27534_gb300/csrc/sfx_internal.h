@@ -87,6 +87,10 @@ struct AdjScratch {
   double* h_out = nullptr;
   unsigned long long* d_nrm = nullptr;   // 2 max-norm slots and mirror
   unsigned long long* h_nrm = nullptr;
+  float4* K = nullptr;            // FP32 relaxation: inverse 2x2 block per cell
+  float* W = nullptr;             // 12 x N neighbour weights (6 per field)
+  float2* r = nullptr;            // FP64 residual rounded to float
+  float2* e = nullptr;            // correction (e_f, e_F)
 };
 
 struct Prof {

@@ -133,6 +133,54 @@ __device__ __forceinline__ void flux_terms_T(const Level& L, const Op& op,
   dT = sd / Vc;
 }
 
+// The same transposed operator as coefficients: (N^T nu)_c = dT nu_c +
+// sum_q w[q] nu_(neighbour q), q = x-, x+, y-, y+, z-, z+ (w = 0 where the
+// neighbour does not exist).
+__device__ __forceinline__ void flux_weights_T(const Level& L, const Op& op, int i, int j, int k,
+                                               double& dT, double* w) {
+  const double Doh = op.D / L.h;
+  const double Vc = cell_volume(L, i);
+  double cL, cR, sd = 0.0;
+  for (int q = 0; q < 6; ++q) w[q] = 0.0;
+  if (i + 1 < L.nx) {
+    const double A = face_area(L, 0, i + 1);
+    face_coeffs(Doh, faceB(op, 0, fidx(L, 0, i + 1, j, k)), op.literal, cL, cR);
+    sd += A * cL;
+    w[1] = -A * cL / cell_volume(L, i + 1);
+  }
+  if (i > 0) {
+    const double A = face_area(L, 0, i);
+    face_coeffs(Doh, faceB(op, 0, fidx(L, 0, i, j, k)), op.literal, cL, cR);
+    sd -= A * cR;
+    w[0] = A * cR / cell_volume(L, i - 1);
+  }
+  const double Ay = face_area(L, 1, i);
+  if (j + 1 < L.ny) {
+    face_coeffs(Doh, faceB(op, 1, fidx(L, 1, i, j + 1, k)), op.literal, cL, cR);
+    sd += Ay * cL;
+    w[3] = -Ay * cL / Vc;
+  }
+  if (j > 0) {
+    face_coeffs(Doh, faceB(op, 1, fidx(L, 1, i, j, k)), op.literal, cL, cR);
+    sd -= Ay * cR;
+    w[2] = Ay * cR / Vc;
+  }
+  if (L.geom == SFX_CART3D) {
+    const double Az = L.h * L.h;
+    if (k + 1 < L.nz) {
+      face_coeffs(Doh, faceB(op, 2, fidx(L, 2, i, j, k + 1)), op.literal, cL, cR);
+      sd += Az * cL;
+      w[5] = -Az * cL / Vc;
+    }
+    if (k > 0) {
+      face_coeffs(Doh, faceB(op, 2, fidx(L, 2, i, j, k)), op.literal, cL, cR);
+      sd -= Az * cR;
+      w[4] = Az * cR / Vc;
+    }
+  }
+  dT = sd / Vc;
+}
+
 // Compensated block reduction of (s, c) pairs; thread 0 receives the
 // block's pair in (s, c).  NT threads per block, a multiple of 32.
 template <int NT>
