@@ -134,6 +134,9 @@ __global__ void k_b_init(int n, BPtr P) {
   for (int q = 0; q < 4; ++q) P.norms[4 * i + q] = 0u;
 }
 
+// G: the geometry of every instance of the batch (compile time, as in the
+// single-grid Newton kernels, so that both run the same cell arithmetic)
+template <int G>
 __global__ void k_b_resid(const BInst* __restrict__ I, int n, const int* __restrict__ pre, BPtr P) {
   const int inst = find_inst(pre, n, blockIdx.x);
   if (!P.active[inst]) return;
@@ -145,7 +148,7 @@ __global__ void k_b_resid(const BInst* __restrict__ I, int n, const int* __restr
     const int i = (int)((ix)c % (ix)L.nx), j = (int)((ix)c / (ix)L.nx);
     const float2* B2[3] = {P.B2[0] + B.rfoff, P.B2[1] + B.zfoff, nullptr};
     const size_t o = B.coff, w = B.poff;
-    resid2_cell(B.p, i, j, 0, c, P.phi32 + o, B2, P.f + o, P.F + o, P.fs + o, P.Fs + o,
+    resid2_cell<G>(B.p, i, j, 0, c, P.phi32 + o, B2, P.f + o, P.F + o, P.fs + o, P.Fs + o,
                 P.coef + w, P.res + w, m, P.e2 + w);
   }
   // block maxima; the flags kernel combines the blocks of each instance
@@ -207,6 +210,7 @@ __global__ void k_b_next(int n, BPtr P, int max_it, cudaGraphConditionalHandle l
 }
 
 // one colour of the coupled correction sweep; blocks over half-rows
+template <int G>
 __global__ void k_b_corr(const BInst* __restrict__ I, int n, const int* __restrict__ pre, BPtr P,
                          int color, int first, int apply) {
   const int inst = find_inst(pre, n, blockIdx.x);
@@ -234,7 +238,7 @@ __global__ void k_b_corr(const BInst* __restrict__ I, int n, const int* __restri
     return;
   }
   const __half2* H[3] = {P.H2[0] + B.rfoff, P.H2[1] + B.zfoff, nullptr};
-  corr2_cell(B.p, i, j, 0, H, P.coef + w, P.res + w, P.e2 + w, color, first, fst, Fst);
+  corr2_cell<G>(B.p, i, j, 0, H, P.coef + w, P.res + w, P.e2 + w, color, first, fst, Fst);
 }
 
 // per-instance compensated totals: kTotBlocks blocks per instance each walk
@@ -322,6 +326,7 @@ struct sfx_batch {
   int* pre_pair = nullptr;
   int nb_cell = 0, nb_rf = 0, nb_zf = 0, nb_pair = 0;
   int block = 256;
+  int geom = SFX_AXISYM;   // of every instance
   BPtr P{};
   std::vector<void*> allocs;
   // graph cache
@@ -412,13 +417,16 @@ sfx_status enqueue_step(sfx_batch* b, bool advect, float tol, cudaStream_t s) {
   cudaStream_t sb = b->cap_body;
   SFX_CUDA(cudaStreamBeginCaptureToGraph(sb, body, nullptr, nullptr, 0,
                                          cudaStreamCaptureModeThreadLocal));
-  k_b_resid<<<b->nb_cell, bs, 0, sb>>>(b->dI, n, b->pre_cell, P);
+  const bool axi = b->geom == SFX_AXISYM;
+  auto resid = axi ? &k_b_resid<SFX_AXISYM> : &k_b_resid<SFX_PLANAR2D>;
+  auto corr = axi ? &k_b_corr<SFX_AXISYM> : &k_b_corr<SFX_PLANAR2D>;
+  resid<<<b->nb_cell, bs, 0, sb>>>(b->dI, n, b->pre_cell, P);
   k_b_flags<<<n, 256, 0, sb>>>(n, b->pre_cell, P, tol);
   // the residual pass did the first red half-sweep
   for (int q = 0; q < b->sweeps; ++q)
     for (int color = (q == 0 ? 1 : 0); color < 2; ++color)
-      k_b_corr<<<b->nb_pair, bs, 0, sb>>>(b->dI, n, b->pre_pair, P, color, q == 0 ? 1 : 0,
-                                          q == b->sweeps - 1 && color == 1 ? 1 : 0);
+      corr<<<b->nb_pair, bs, 0, sb>>>(b->dI, n, b->pre_pair, P, color, q == 0 ? 1 : 0,
+                                      q == b->sweeps - 1 && color == 1 ? 1 : 0);
   k_b_next<<<1, 256, 0, sb>>>(n, P, b->max_it, loop);
   const cudaError_t le = cudaGetLastError();
   cudaGraph_t body_out = nullptr;
@@ -492,6 +500,7 @@ sfx_status sfx_batch_create_geom(const sfx_batch_instance* inst, int n, int geom
     if (!inst_ok(inst[i])) return SFX_ERR_ARG;
   sfx_batch* b = new sfx_batch();
   b->n = n;
+  b->geom = geom;
   b->hinst.assign(inst, inst + n);
   for (int i = 0; i < n; ++i) {
     const sfx_batch_instance& q = inst[i];

@@ -290,6 +290,7 @@ __global__ void k_corr32(Corr32 p, const float* __restrict__ Bx, const float* __
 // the coupled one does not.
 // Evaluate both residuals (pairs), the 2x2 exchange Jacobian and the
 // norms at every cell of the current state.
+template <int G>
 __global__ void __launch_bounds__(256, 5)
 k_resid2_32(Nw32 p, const float* __restrict__ phi, const float2* __restrict__ B2x,
             const float2* __restrict__ B2y, const float2* __restrict__ B2z,
@@ -308,7 +309,7 @@ k_resid2_32(Nw32 p, const float* __restrict__ phi, const float2* __restrict__ B2
   for (ix r = blockIdx.y; r < rows; r += gridDim.y) {
     const int j = (int)(r % (ix)L.ny), k = (int)(r / (ix)L.ny);
     if (i < L.nx)
-      resid2_cell(p, i, j, k, r * (ix)L.nx + (ix)i, phi, B2, fin, Fin, fst, Fst, coef, res, m, e2);
+      resid2_cell<G>(p, i, j, k, r * (ix)L.nx + (ix)i, phi, B2, fin, Fin, fst, Fst, coef, res, m, e2);
   }
   if (norms) {
     // warp maxima, then one atomic per block and norm
@@ -328,6 +329,7 @@ k_resid2_32(Nw32 p, const float* __restrict__ phi, const float2* __restrict__ B2
 }
 
 // One colour of the coupled red-black Gauss-Seidel on the correction.
+template <int G>
 __global__ void __launch_bounds__(128, 10)
 k_corr2_32(Nw32 p, const __half2* __restrict__ Hx, const __half2* __restrict__ Hy,
            const __half2* __restrict__ Hz, const float4* __restrict__ coef,
@@ -351,7 +353,27 @@ k_corr2_32(Nw32 p, const __half2* __restrict__ Hx, const __half2* __restrict__ H
     }
     return;
   }
-  corr2_cell(p, i, j, k, H, coef, res, e2, color, first, fst, Fst);
+  corr2_cell<G>(p, i, j, k, H, coef, res, e2, color, first, fst, Fst);
+}
+
+// The Newton kernels of one geometry (the branches on the geometry in the
+// cell functions fold at compile time).  The 3D residual keeps the branch
+// at run time: specialised it needs more registers than its occupancy
+// bound allows and spills.
+struct NewtonKernels {
+  decltype(&k_resid2_32<kGeomRuntime>) resid;
+  decltype(&k_corr2_32<SFX_CART3D>) corr;
+};
+template <int G>
+NewtonKernels newton_kernels_of() {
+  return NewtonKernels{&k_resid2_32<G>, &k_corr2_32<G>};
+}
+NewtonKernels newton_kernels(int geom) {
+  switch (geom) {
+    case SFX_AXISYM: return newton_kernels_of<SFX_AXISYM>();
+    case SFX_PLANAR2D: return newton_kernels_of<SFX_PLANAR2D>();
+    default: return NewtonKernels{&k_resid2_32<kGeomRuntime>, &k_corr2_32<SFX_CART3D>};
+  }
 }
 
 // ------------------------------------------------------------ fused sweep
@@ -1206,6 +1228,7 @@ sfx_status solve_newton32(sfx_ctx* c, const Nw32& p, const float* phi, float* co
   unsigned int* hn = (unsigned int*)c->h_norms;
   int* flag = c->f32.flag;
   const RowGrid rg = row_grid(L);
+  const NewtonKernels nk = newton_kernels(L.geom);
   const __half2* Hz = L.ndim() == 3 ? c->f32.H2[2] : nullptr;
   const float2* B2[3] = {c->f32.B2[0], c->f32.B2[1], L.ndim() == 3 ? c->f32.B2[2] : nullptr};
   SFX_CUDA(cudaMemsetAsync(flag, 0, 2 * sizeof(int), s));
@@ -1222,7 +1245,7 @@ sfx_status solve_newton32(sfx_ctx* c, const Nw32& p, const float* phi, float* co
   for (it = 1; it <= o->max_cycles; ++it) {
     unsigned int* nbuf = dn + 4 * (it & 1);
     SFX_CUDA(cudaMemsetAsync(nbuf, 0, 4 * sizeof(unsigned int), s));
-    SFX_KERNEL(c, K_RESIDUAL, k_resid2_32, rg.grid, rg.block, s, p, phi, B2[0], B2[1], B2[2], fc,
+    SFX_KERNEL(c, K_RESIDUAL, nk.resid, rg.grid, rg.block, s, p, phi, B2[0], B2[1], B2[2], fc,
                Fc, fs, Fs, c->f32.coef, c->f32.res, nbuf, c->f32.e2, flag);
     if (it == 1 && predicted) {
       // keep the predicted start only if its residual is already small;
@@ -1231,7 +1254,7 @@ sfx_status solve_newton32(sfx_ctx* c, const Nw32& p, const float* phi, float* co
       const float rho = c->f32.predict_rho;
       SFX_KERNEL(c, K_OTHER, k_pred_check32, 1, 32, s, nbuf, rho, ok);
       SFX_KERNEL(c, K_SETUP, k_restore32, nb, 256, s, n, ok, fs, Fs, fc, Fc);
-      SFX_KERNEL(c, K_RESIDUAL, k_resid2_32, rg.grid, rg.block, s, p, phi, B2[0], B2[1], B2[2],
+      SFX_KERNEL(c, K_RESIDUAL, nk.resid, rg.grid, rg.block, s, p, phi, B2[0], B2[1], B2[2],
                  fc, Fc, fs, Fs, c->f32.coef, c->f32.res, nbuf, c->f32.e2, ok);
     }
     SFX_KERNEL(c, K_OTHER, k_flag32, 1, 32, s, nbuf, tolf, it, flag);
@@ -1241,7 +1264,7 @@ sfx_status solve_newton32(sfx_ctx* c, const Nw32& p, const float* phi, float* co
     for (int q = 0; q < sweeps; ++q)
       for (int color = (q == 0 ? 1 : 0); color < 2; ++color) {
         const bool apply = q == sweeps - 1 && color == 1;
-        SFX_KERNEL(c, K_SMOOTH_FINE, k_corr2_32, grd, blk, s, p, c->f32.H2[0], c->f32.H2[1], Hz,
+        SFX_KERNEL(c, K_SMOOTH_FINE, nk.corr, grd, blk, s, p, c->f32.H2[0], c->f32.H2[1], Hz,
                    c->f32.coef, c->f32.res, c->f32.e2, color, q == 0 ? 1 : 0,
                    apply ? fc : nullptr, apply ? Fc : nullptr, flag);
       }

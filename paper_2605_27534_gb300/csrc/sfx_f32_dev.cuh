@@ -137,11 +137,22 @@ __device__ __forceinline__ ix cidx32(const Level& L, int i, int j, int k) {
   return ((ix)k * (ix)L.ny + (ix)j) * (ix)L.nx + (ix)i;
 }
 
+// G: the grid's geometry as a compile-time constant (the Newton kernels are
+// instantiated per geometry; L.geom == G), or kGeomRuntime to read it from
+// the level at run time
+constexpr int kGeomRuntime = -1;
+template <int G>
+__device__ __forceinline__ int geom_of(const Level& L) {
+  return G == kGeomRuntime ? L.geom : G;
+}
+
+template <int G>
 __device__ __forceinline__ void gather6(const Level& L, int i, int j, int k, ix c,
                                         bool* has, ix* nbi) {
   const ix sy = (ix)L.nx, sz = (ix)L.nx * (ix)L.ny;
   has[0] = i > 0; has[1] = i + 1 < L.nx; has[2] = j > 0; has[3] = j + 1 < L.ny;
-  has[4] = L.geom == SFX_CART3D && k > 0; has[5] = L.geom == SFX_CART3D && k + 1 < L.nz;
+  const bool three_d = geom_of<G>(L) == SFX_CART3D;
+  has[4] = three_d && k > 0; has[5] = three_d && k + 1 < L.nz;
   nbi[0] = c - 1; nbi[1] = c + 1; nbi[2] = c - sy; nbi[3] = c + sy; nbi[4] = c - sz; nbi[5] = c + sz;
 }
 
@@ -230,10 +241,11 @@ __device__ __forceinline__ void faces6x2(const Level& L, const __half2* Hx, cons
 // The diffusive part is gathered as Doh (sum_q w_q a_q - W a_c), W = sum_q
 // w_q, one pair product instead of one per face; the drift part as
 // sum_q +-w_q B_q a_up(q).
+template <int G>
 __device__ __forceinline__ float2 flux_pair(const Level& L, float invh, float Doh, int literal,
                                             int i, float2 ac, const float2* nb, const bool* has,
                                             const float* B, float& dflux) {
-  const bool axi = L.geom == SFX_AXISYM;
+  const bool axi = geom_of<G>(L) == SFX_AXISYM;
   Acc D{0.0f, 0.0f}, T{0.0f, 0.0f};
   float W = 0.0f, dg = 0.0f;
 #pragma unroll
@@ -242,27 +254,28 @@ __device__ __forceinline__ float2 flux_pair(const Level& L, float invh, float Do
     const bool plus = q & 1;
     const bool upL = literal ? (B[q] > 0.0f) : (B[q] < 0.0f);
     float w = 1.0f;
-    if (axi) w = q < 2 ? wr_face(L.geom, i + (plus ? 1 : 0)) : (q < 4 ? wz_face(L.geom, i) : 1.0f);
+    const int g = geom_of<G>(L);
+    if (axi) w = q < 2 ? wr_face(g, i + (plus ? 1 : 0)) : (q < 4 ? wz_face(g, i) : 1.0f);
     acc_add(D, axi ? lp_mul(nb[q], w) : nb[q]);
-    W += w;
+    W = __fadd_rn(W, w);
     // upwind value: the left cell when upL; this cell is left on plus faces
     const float2 aup = (plus == upL) ? ac : nb[q];
     float2 u = lp_mul(aup, B[q]);
     if (axi) u = lp_mul(u, w);   // B w in float would round the drift itself
     if (plus) {
       acc_add(T, u);
-      dg += w * (Doh - (upL ? B[q] : 0.0f));
+      dg = __fmaf_rn(w, __fsub_rn(Doh, upL ? B[q] : 0.0f), dg);
     } else {
       acc_sub(T, u);
-      dg += w * (Doh + (upL ? 0.0f : B[q]));
+      dg = __fmaf_rn(w, __fadd_rn(Doh, upL ? 0.0f : B[q]), dg);
     }
   }
   acc_sub(D, lp_mul(ac, W));
   acc_add(T, lp_mul(acc_get(D), Doh));
   float2 flux = lp_mul(acc_get(T), invh);
-  dflux = dg * invh;
+  dflux = __fmul_rn(dg, invh);
   if (axi) {
-    const float wc = wz_face(L.geom, i);
+    const float wc = wz_face(geom_of<G>(L), i);
     flux = df_div_f(ef_fast_two_sum(flux.x, flux.y), wc);
     dflux = __fdividef(dflux, wc);
   }
@@ -270,6 +283,7 @@ __device__ __forceinline__ float2 flux_pair(const Level& L, float invh, float Do
 }
 
 // linear flux of a correction field (FP32) and its diagonal weight
+template <int G>
 __device__ __forceinline__ float flux_lin(const Level& L, float invh, float Doh, int literal,
                                           int i, float ec, const float* en, const bool* has,
                                           const float* B, float& dflux) {
@@ -280,15 +294,21 @@ __device__ __forceinline__ float flux_lin(const Level& L, float invh, float Doh,
     const bool plus = q & 1;
     const bool upL = literal ? (B[q] > 0.0f) : (B[q] < 0.0f);
     float w = 1.0f;
-    if (L.geom == SFX_AXISYM) w = q < 2 ? wr_face(L.geom, i + (plus ? 1 : 0)) : (q < 4 ? wz_face(L.geom, i) : 1.0f);
+    const int g = geom_of<G>(L);
+    if (g == SFX_AXISYM) w = q < 2 ? wr_face(g, i + (plus ? 1 : 0)) : (q < 4 ? wz_face(g, i) : 1.0f);
     const float eL = plus ? ec : en[q], eR = plus ? en[q] : ec;
-    const float G = Doh * (eR - eL) + B[q] * (upL ? eL : eR);
-    if (plus) { S += w * G; dg += w * (Doh - (upL ? B[q] : 0.0f)); }
-    else { S -= w * G; dg += w * (Doh + (upL ? 0.0f : B[q])); }
+    const float fq = __fmaf_rn(Doh, __fsub_rn(eR, eL), __fmul_rn(B[q], upL ? eL : eR));
+    if (plus) {
+      S = __fmaf_rn(w, fq, S);
+      dg = __fmaf_rn(w, __fsub_rn(Doh, upL ? B[q] : 0.0f), dg);
+    } else {
+      S = __fmaf_rn(-w, fq, S);
+      dg = __fmaf_rn(w, __fadd_rn(Doh, upL ? 0.0f : B[q]), dg);
+    }
   }
-  const float s = invh / wz_face(L.geom, i);
-  dflux = dg * s;
-  return S * s;
+  const float s = invh / wz_face(geom_of<G>(L), i);
+  dflux = __fmul_rn(dg, s);
+  return __fmul_rn(S, s);
 }
 
 __device__ __forceinline__ float mc32(float xm, float x0, float xp) {
@@ -380,6 +400,7 @@ __device__ __forceinline__ void face32v2(const Adv32& A, const float2* __restric
 // half-sweep of the correction is done here: it starts from zero
 // corrections, so a red cell (i + j + k even) only needs its own 2x2 block,
 // e = M_c^-1 r_c.
+template <int G>
 __device__ __forceinline__ void resid2_cell(const Nw32& p, int i, int j, int k, ix c,
                                             const float* __restrict__ phi,
                                             const float2* const* B2,
@@ -392,21 +413,21 @@ __device__ __forceinline__ void resid2_cell(const Nw32& p, int i, int j, int k, 
   const Level& L = p.L;
   bool has[6];
   ix nbi[6];
-  gather6(L, i, j, k, c, has, nbi);
+  gather6<G>(L, i, j, k, c, has, nbi);
   float2 nb[6];
   const float2 fc = fin[c], Fc = Fin[c];
   float Bf[6], BF[6], df_, dF_;
   faces6f2(L, B2[0], B2[1], B2[2], i, j, k, has, Bf, BF);
 #pragma unroll
   for (int q = 0; q < 6; ++q) nb[q] = has[q] ? fin[nbi[q]] : make_float2(0.0f, 0.0f);
-  const float2 flf = flux_pair(L, p.invh, p.Dfh, p.literal, i, fc, nb, has, Bf, df_);
+  const float2 flf = flux_pair<G>(L, p.invh, p.Dfh, p.literal, i, fc, nb, has, Bf, df_);
 #pragma unroll
   for (int q = 0; q < 6; ++q) nb[q] = has[q] ? Fin[nbi[q]] : make_float2(0.0f, 0.0f);
-  const float2 flF = flux_pair(L, p.invh, p.DFh, p.literal, i, Fc, nb, has, BF, dF_);
+  const float2 flF = flux_pair<G>(L, p.invh, p.DFh, p.literal, i, Fc, nb, has, BF, dF_);
   // exchange q = c1 F (f_inf - f) - r_d f, one evaluation for both equations
   const PhiPair ph = unfold(phi[c]);
   const float c1 = __fdividef(p.ka, ph.p + p.eta);
-  const float finf = p.ginf * ph.p * ph.q * p.inv_eps;
+  const float finf = __fmul_rn(__fmul_rn(__fmul_rn(p.ginf, ph.p), ph.q), p.inv_eps);
   float2 fd = ef_two_sum(finf, -fc.x);
   fd.y = __fsub_rn(fd.y, fc.y);
   const float pr = __fmul_rn(Fc.x, fd.x);
@@ -427,22 +448,25 @@ __device__ __forceinline__ void resid2_cell(const Nw32& p, int i, int j, int k, 
   const float rf = __fadd_rn(Rf.hi, Rf.lo), rF = __fadd_rn(RF.hi, RF.lo);
   const float Fv = __fadd_rn(Fc.x, Fc.y), fv = __fadd_rn(fc.x, fc.y);
   // diagonals (kinetic part) and couplings of the linearised system
-  const float4 cf = make_float4(p.inv_dt + p.kd + c1 * Fv, p.inv_dt + c1 * (finf - fv),
-                                c1 * (finf - fv), c1 * Fv + p.kd);
+  const float xf = __fsub_rn(finf, fv);
+  const float4 cf = make_float4(__fmaf_rn(c1, Fv, __fadd_rn(p.inv_dt, p.kd)),
+                                __fmaf_rn(c1, xf, p.inv_dt), __fmul_rn(c1, xf),
+                                __fmaf_rn(c1, Fv, p.kd));
   const RBIdx rb = rb_index(L, i, j, k);
   const ix own = (ix)((i + j + k) & 1) * rb.plane + rb.pos;
   coef[own] = cf;
   res[own] = make_float2(rf, rF);
   if (e2 && ((i + j + k) & 1) == 0) {
     // [a -b; -d e] [x; y] = [r_f; r_F], diagonals with the flux weights
-    const float a = cf.x + df_, bb = cf.z, d = cf.w, e = cf.y + dF_;
-    const float inv = __fdividef(1.0f, a * e - bb * d);
-    e2[own] = make_float2((e * rf + bb * rF) * inv, (d * rf + a * rF) * inv);
+    const float a = __fadd_rn(cf.x, df_), bb = cf.z, d = cf.w, e = __fadd_rn(cf.y, dF_);
+    const float inv = __fdividef(1.0f, __fmaf_rn(a, e, -__fmul_rn(bb, d)));
+    e2[own] = make_float2(__fmul_rn(__fmaf_rn(e, rf, __fmul_rn(bb, rF)), inv),
+                          __fmul_rn(__fmaf_rn(d, rf, __fmul_rn(a, rF)), inv));
   }
   m[0] = fmaxf(m[0], fabsf(rf));
-  m[1] = fmaxf(m[1], fabsf(fs.x * p.inv_dt + c1 * Fv * finf));
+  m[1] = fmaxf(m[1], fabsf(__fmaf_rn(fs.x, p.inv_dt, __fmul_rn(__fmul_rn(c1, Fv), finf))));
   m[2] = fmaxf(m[2], fabsf(rF));
-  m[3] = fmaxf(m[3], fabsf(Fs.x * p.inv_dt + p.kd * fv));
+  m[3] = fmaxf(m[3], fabsf(__fmaf_rn(Fs.x, p.inv_dt, __fmul_rn(p.kd, fv))));
   if (!(fabsf(rf) <= 3.0e38f) || !(fabsf(rF) <= 3.0e38f)) m[0] = m[2] = __int_as_float(0x7f800000);
 }
 
@@ -452,6 +476,7 @@ __device__ __forceinline__ void resid2_cell(const Nw32& p, int i, int j, int k, 
 // only precondition the Newton correction (the residual pass fixes the
 // solution), so they read the face drifts in half precision (relative
 // 5e-4), halving their face traffic.
+template <int G>
 __device__ __forceinline__ void corr2_cell(const Nw32& p, int i, int j, int k,
                                            const __half2* const* H,
                                            const float4* __restrict__ coef,
@@ -465,7 +490,7 @@ __device__ __forceinline__ void corr2_cell(const Nw32& p, int i, int j, int k,
   const ix c = cidx32(L, i, j, k);
   bool has[6];
   ix nbi[6];
-  gather6(L, i, j, k, c, has, nbi);
+  gather6<G>(L, i, j, k, c, has, nbi);
   // the work arrays are colour-packed: own cell and the other colour's plane
   const RBIdx rb = rb_index(L, i, j, k);
   const ix own = (ix)color * rb.plane + rb.pos;
@@ -490,19 +515,21 @@ __device__ __forceinline__ void corr2_cell(const Nw32& p, int i, int j, int k,
   const float efc = ec.x, eFc = ec.y;
   float Bf[6], BF[6], dgf, dgF;
   faces6x2(L, H[0], H[1], H[2], i, j, k, has, Bf, BF);
-  const float flf = flux_lin(L, p.invh, p.Dfh, p.literal, i, efc, enf, has, Bf, dgf);
-  const float flF = flux_lin(L, p.invh, p.DFh, p.literal, i, eFc, enF, has, BF, dgF);
+  const float flf = flux_lin<G>(L, p.invh, p.Dfh, p.literal, i, efc, enf, has, Bf, dgf);
+  const float flF = flux_lin<G>(L, p.invh, p.DFh, p.literal, i, eFc, enF, has, BF, dgF);
   const float4 cf = coef[own];
   const float2 r = res[own];
   // residuals of the correction equation at this cell
-  const float rhof = r.x + flf - cf.x * efc + cf.z * eFc;
-  const float rhoF = r.y + flF - cf.y * eFc + cf.w * efc;
+  // (every rounding is spelled out, so that each kernel that inlines this
+  // cell computes the same bits)
+  const float rhof = __fmaf_rn(cf.z, eFc, __fmaf_rn(-cf.x, efc, __fadd_rn(r.x, flf)));
+  const float rhoF = __fmaf_rn(cf.w, efc, __fmaf_rn(-cf.y, eFc, __fadd_rn(r.y, flF)));
   // 2x2 block solve: [a  -b; -d  e] [x; y] = [rhof; rhoF]
-  const float a = cf.x + dgf, bb = cf.z, d = cf.w, e = cf.y + dgF;
-  const float det = a * e - bb * d;
+  const float a = __fadd_rn(cf.x, dgf), bb = cf.z, d = cf.w, e = __fadd_rn(cf.y, dgF);
+  const float det = __fmaf_rn(a, e, -__fmul_rn(bb, d));
   const float inv = __fdividef(1.0f, det);
-  const float nf = efc + (e * rhof + bb * rhoF) * inv;
-  const float nF = eFc + (d * rhof + a * rhoF) * inv;
+  const float nf = __fmaf_rn(__fmaf_rn(e, rhof, __fmul_rn(bb, rhoF)), inv, efc);
+  const float nF = __fmaf_rn(__fmaf_rn(d, rhof, __fmul_rn(a, rhoF)), inv, eFc);
   e2[own] = make_float2(nf, nF);
   if (fst) {
     // last black colour of the iteration: add the corrections to the state,
