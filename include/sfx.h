@@ -370,7 +370,9 @@ sfx_status sfx_adjoint_apply(sfx_ctx* ctx, const sfx_params* params, const doubl
    coefficients computed once per step from the FP64 operator) and added to
    nu; after max_cycles checks SFX_ERR_NOT_CONVERGED (outputs written).
    stats (may be NULL): picard = checks, vcycles = sweeps, res_f = res_F =
-   the final relative residual.  Waits for stream. */
+   the final relative residual.  The relaxation of a check runs as one CUDA
+   graph launch, captured on the context's first call (and again when
+   nu1 + nu2 changes) on a stream the context owns.  Waits for stream. */
 sfx_status sfx_adjoint_step(sfx_ctx* ctx, const sfx_params* params, const double* phi,
                             const double* f, const double* F, double dt, double* lam_f,
                             double* lam_F, double* dparams, const sfx_solve_opts* opts,

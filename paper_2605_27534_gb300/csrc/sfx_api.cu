@@ -153,6 +153,8 @@ void sfx_ctx_destroy(sfx_ctx* c) {
   if (c->h_sums) cudaFreeHost(c->h_sums);
   if (c->adj.h_out) cudaFreeHost(c->adj.h_out);
   if (c->adj.h_nrm) cudaFreeHost(c->adj.h_nrm);
+  if (c->adj.relax) cudaGraphExecDestroy(c->adj.relax);
+  if (c->adj.cap) cudaStreamDestroy(c->adj.cap);
   delete c;
 }
 

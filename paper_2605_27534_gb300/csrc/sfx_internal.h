@@ -91,6 +91,11 @@ struct AdjScratch {
   float* W = nullptr;             // 12 x N neighbour weights (6 per field)
   float2* r = nullptr;            // FP64 residual rounded to float
   float2* e = nullptr;            // correction (e_f, e_F)
+  // the relaxation of one defect-correction check (e = 0, the colour
+  // sweeps, nu += e) as a CUDA graph: one launch instead of 2 S + 2
+  cudaStream_t cap = nullptr;     // private stream the graph is captured on
+  cudaGraphExec_t relax = nullptr;
+  int relax_sweeps = 0;           // S of the captured graph
 };
 
 struct Prof {
