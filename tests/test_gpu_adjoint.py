@@ -91,6 +91,36 @@ def test_adjoint_step_matches_the_oracle(sfx, geom):
         assert abs(dp[k] - dth[k]) <= 1e-10 * max(abs(dth[k]), 1e-3 * np.abs(dth).max()), k
 
 
+def test_adjoint_relaxation_graph_follows_the_sweep_count(sfx):
+    """The relaxation of a check is a graph captured per context and sweep
+    count: a context that changes nu1 + nu2 between steps (recapturing)
+    gives bitwise the results of fresh contexts, and the same sweep count
+    again gives the same bits as the first call."""
+    g, p, Cf, phi, f, F = _state_case(W.AXI, seed=2)
+    dt = 2e-3
+    rng = np.random.default_rng(7)
+    lf, lF = rng.standard_normal(g.shape), rng.standard_normal(g.shape)
+    d = [dev(a) for a in (phi, f, F)]
+
+    def run(ctx, nu):
+        a, b = dev(lf), dev(lF)
+        dp = [0.0] * 4
+        st = ctx.sfx_adjoint_step(p, *d, dt, a, b, dp,
+                                  sfx.default_opts(tol=1e-13, max_cycles=2000, nu1=nu, nu2=nu))
+        assert st.converged and st.vcycles % (2 * nu) == 0
+        return host(a), host(b), dp
+
+    shared = sfx.Context.for_grid(g, sfx.SFX_F64)
+    got = [run(shared, nu) for nu in (3, 7, 3)]
+    for nu, r in zip((3, 7, 3), got):
+        ref = run(sfx.Context.for_grid(g, sfx.SFX_F64), nu)
+        assert np.array_equal(r[0], ref[0]) and np.array_equal(r[1], ref[1]), nu
+        assert r[2] == ref[2], nu
+    assert np.array_equal(got[0][0], got[2][0]) and got[0][2] == got[2][2]
+    # different sweep counts reach the same adjoint within the tolerance
+    assert rel_err(got[1][0], got[0][0]) < 1e-10
+
+
 @pytest.mark.parametrize("geom", [W.PLANAR, W.AXI])
 def test_marangoni_loss_and_gradient_match_the_oracle(sfx, geom):
     g, p, Cf, phi, f, F = _state_case(geom, seed=2)
