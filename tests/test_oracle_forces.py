@@ -82,6 +82,69 @@ def test_plic_volume_matches_brute_force():
         assert abs(oracle.plic_volume(3, m, a) - inside) < 4e-3
 
 
+def _ie_volume(mp, a):
+    """Fraction of the unit square/cube with mp.x <= a (mp > 0) by
+    inclusion-exclusion over the vertices v: sum (-1)^|v| (a - mp.v)_+^d
+    / (d! prod mp)."""
+    import itertools
+    d = len(mp)
+    s = 0.0
+    for v in itertools.product((0, 1), repeat=d):
+        t = a - float(np.dot(mp, v))
+        if t > 0:
+            s += (-1) ** sum(v) * t ** d
+    return s / (math.factorial(d) * float(np.prod(mp)))
+
+
+def _cut_measure(mp, a):
+    """Length (2D) or area (3D) of {mp.x = a} inside the unit square/cube:
+    the points where the plane crosses the edges, ordered by angle about
+    their centroid, as a segment or a polygon."""
+    import itertools
+    d = len(mp)
+    pts = []
+    for v in itertools.product((0, 1), repeat=d):
+        for e in range(d):
+            if v[e]:
+                continue
+            w = list(v)
+            w[e] = 1
+            fa, fb = float(np.dot(mp, v)) - a, float(np.dot(mp, w)) - a
+            if fa * fb < 0:
+                t = fa / (fa - fb)
+                pts.append(np.array(v, float) + t * (np.array(w, float) - np.array(v, float)))
+    P = np.array(pts)
+    if d == 2:
+        assert len(P) == 2
+        return float(np.linalg.norm(P[1] - P[0]))
+    n = mp / np.linalg.norm(mp)
+    u = np.cross(n, [1.0, 0.0, 0.0] if abs(n[0]) < 0.9 else [0.0, 1.0, 0.0])
+    u /= np.linalg.norm(u)
+    w = np.cross(n, u)
+    c = P.mean(axis=0)
+    P = P[np.argsort(np.arctan2((P - c) @ w, (P - c) @ u))]
+    x, y = (P - c) @ u, (P - c) @ w
+    return 0.5 * abs(float(np.dot(x, np.roll(y, -1)) - np.dot(y, np.roll(x, -1))))
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_plic_volume_and_area_match_the_exact_cut(dim):
+    """Random normals (either sign) and plane offsets: the volume below the
+    plane against the inclusion-exclusion form, and the interface area for
+    that volume fraction against the polygon (segment) the plane cuts out
+    of the cell."""
+    rng = np.random.default_rng(11 + dim)
+    for _ in range(40):
+        m = rng.uniform(0.1, 1.0, dim) * rng.choice([-1.0, 1.0], dim)
+        mp = np.abs(m) / np.abs(m).sum()
+        a = rng.uniform(0.02, 0.98)
+        C = _ie_volume(mp, a)
+        if not 1e-3 < C < 1 - 1e-3:
+            continue
+        assert abs(oracle.plic_volume(dim, m, a) - C) < 1e-10, (m, a)
+        assert abs(oracle.plic_area(dim, m, C) - _cut_measure(mp, a)) < 1e-9, (m, a)
+
+
 def test_plic_delta_integrates_to_perimeter():
     for n in (32, 64):
         g = W.Grid(W.PLANAR, n, n, 1, 1.0 / n)
