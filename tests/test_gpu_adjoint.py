@@ -121,6 +121,42 @@ def test_adjoint_relaxation_graph_follows_the_sweep_count(sfx):
     assert rel_err(got[1][0], got[0][0]) < 1e-10
 
 
+def test_adjoint_step_reports_the_checks_it_ran(sfx):
+    """With too few checks the step stops after max_cycles of them
+    (SFX_ERR_NOT_CONVERGED, relaxations between them only), and with enough
+    it stops at the first check that passes: running it again with that
+    check as the limit gives the same bits."""
+    import ctypes as C
+    g, p, Cf, phi, f, F = _state_case(W.PLANAR, seed=3)
+    dt = 2e-3
+    rng = np.random.default_rng(8)
+    lf, lF = rng.standard_normal(g.shape), rng.standard_normal(g.shape)
+    d = [dev(a) for a in (phi, f, F)]
+    ctx = sfx.Context.for_grid(g, sfx.SFX_F64)
+    ps = sfx.params_struct(p)
+
+    def raw(max_cycles, nu=3):
+        a, b = dev(lf), dev(lF)
+        o = sfx.default_opts(tol=1e-13, max_cycles=max_cycles, nu1=nu, nu2=nu)
+        st = sfx.StepStats()
+        dp = (C.c_double * 4)()
+        code = sfx.lib().sfx_adjoint_step(ctx.handle, C.byref(ps), sfx._ptr(d[0]),
+                                          sfx._ptr(d[1]), sfx._ptr(d[2]), float(dt), sfx._ptr(a),
+                                          sfx._ptr(b), dp, C.byref(o), C.byref(st),
+                                          sfx._stream())
+        return code, st, host(a), host(b), list(dp)
+
+    code, st, *_ = raw(2)
+    assert code == sfx.SFX_ERR_NOT_CONVERGED
+    assert (st.picard, st.vcycles, st.converged) == (2, 6, 0) and st.res_f > 1e-13
+    code, st, a1, b1, dp1 = raw(1000)
+    assert code == sfx.SFX_OK and st.converged and st.res_f <= 1e-13
+    assert st.vcycles == (st.picard - 1) * 6
+    code, st2, a2, b2, dp2 = raw(st.picard)
+    assert code == sfx.SFX_OK and st2.picard == st.picard and st2.vcycles == st.vcycles
+    assert np.array_equal(a1, a2) and np.array_equal(b1, b2) and dp1 == dp2
+
+
 @pytest.mark.parametrize("geom", [W.PLANAR, W.AXI])
 def test_marangoni_loss_and_gradient_match_the_oracle(sfx, geom):
     g, p, Cf, phi, f, F = _state_case(geom, seed=2)
