@@ -467,6 +467,42 @@ def test_cfl_dt_matches_oracle(sfx):
 
 
 # ----------------------------------------------------------------- edges
+def test_flat_interface_axisymmetric_and_3d_steps_reduce_to_the_planar_column(sfx):
+    """A flat interface normal to y, its phase field built and stepped by
+    the FP64 GPU path on planar, axisymmetric and 3D blocks: every ring and
+    every 3D column reproduce the oracle's planar column (whose own
+    axisymmetric and 3D runs reduce to it to round-off)."""
+    import torch
+    ny, half, dt, steps = 48, 1.0, 2e-3, 6
+    h = 2 * half / ny
+    y = -half + (np.arange(ny) + 0.5) * h
+    p = W.Params(ka=2.0, kd=0.5, gamma_inf=1.0, Df=0.3, DF=1.0, eps=2 * h)
+    ref = None
+    for geom, nx, nz in ((W.PLANAR, 2, 1), (W.AXI, 4, 1), (W.CART3D, 2, 2)):
+        g = W.Grid(geom, nx, ny, nz, h)
+        Cf = np.zeros(g.shape)
+        Cf[:, y < 0, :] = 1.0
+        dtau = h / 3 if geom == W.CART3D else 0.5 * h
+        if ref is None:
+            _, phi_o, del_o = oracle.phase_field_build(g, Cf, 200, dtau, p.eps)
+            f_o, F_o = 0.2 * del_o, phi_o.copy()
+            for _ in range(steps):
+                f_o, F_o, st = oracle.surfactant_step(g, p, phi_o, f_o, F_o, dt, TOL / 10)
+                assert st.converged
+            ref = [a[0, :, 0] for a in (phi_o, f_o, F_o)]
+        ctx = _ctx(sfx, g)
+        Cd = dev(Cf)
+        chi, phi, dl = torch.empty_like(Cd), torch.empty_like(Cd), torch.empty_like(Cd)
+        ctx.sfx_phase_field_build(Cd, chi, phi, dl, iters=200, dtau=dtau, eps=p.eps)
+        f, F = 0.2 * dl, phi.clone()
+        opts = sfx.default_opts(tol=TOL, max_cycles=200)
+        for _ in range(steps):
+            assert ctx.sfx_surfactant_step(p, phi, f, F, dt, opts=opts).converged
+        for a, r in zip((host(phi), host(f), host(F)), ref):
+            err = np.abs(a - r[None, :, None]).max() / np.abs(r).max()
+            assert err < PARITY, (geom, err)
+
+
 def test_degenerate_single_cell_reduces_to_kinetics(sfx):
     """One cell: no faces, so App. C reduces to the pointwise kinetic system."""
     g = W.Grid(W.PLANAR, 1, 1, 1, 0.1)
