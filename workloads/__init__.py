@@ -338,6 +338,62 @@ def solid_rotation_faces(n, h, centre, omega):
     return ux[None], uy[None]
 
 
+def radial_expansion_faces(shape, h, origin, K):
+    """Face velocities of the isotropic expansion u = K (x - c) of Sec. 4.1
+    (u = K r e_r) on a 3D grid whose lower corner sits at `origin` relative
+    to the centre c; each face carries the normal component at its centre.
+    Not divergence-free (div u = 3 K)."""
+    nz, ny, nx = shape
+    xf = origin[0] + np.arange(nx + 1) * h
+    yf = origin[1] + np.arange(ny + 1) * h
+    zf = origin[2] + np.arange(nz + 1) * h
+    ux = np.broadcast_to(K * xf[None, None, :], (nz, ny, nx + 1)).copy()
+    uy = np.broadcast_to(K * yf[None, :, None], (nz, ny + 1, nx)).copy()
+    uz = np.broadcast_to(K * zf[:, None, None], (nz + 1, ny, nx)).copy()
+    return ux, uy, uz
+
+
+def cell_centre_offsets(shape, h, origin):
+    """Coordinates (x, y, z) of every cell centre, arrays of the cell shape
+    (nz, ny, nx), for a grid whose lower corner lies at `origin`."""
+    nz, ny, nx = shape
+    x = origin[0] + (np.arange(nx) + 0.5) * h
+    y = origin[1] + (np.arange(ny) + 0.5) * h
+    z = origin[2] + (np.arange(nz) + 0.5) * h
+    Z, Y, X = np.meshgrid(z, y, x, indexing="ij")
+    return X, Y, Z
+
+
+def expanding_sphere(N, ds=0.5, half=1.0, K=1.0, octant=True):
+    """Expanding sphere of Sec. 4.1: a sphere of diameter ds at the centre of
+    the box [-half, half]^3 resolved by N cells per side, in the flow
+    u = K r e_r.  With octant=True only the octant [0, half]^3 is gridded
+    (N/2 cells per side): its three inner walls are mirror planes of the
+    problem (zero normal velocity, zero-gradient walls).  Returns the grid,
+    the cell-centre radius r (cell shape) and the face velocities."""
+    h = 2.0 * half / N
+    n = N // 2 if octant else N
+    g = Grid(CART3D, n, n, n, h)
+    org = (0.0, 0.0, 0.0) if octant else (-half, -half, -half)
+    X, Y, Z = cell_centre_offsets(g.shape, h, org)
+    faces = radial_expansion_faces(g.shape, h, org, K)
+    return g, np.sqrt(X * X + Y * Y + Z * Z), faces
+
+
+def rotating_circle(N, db=1.0, domain_over_db=2.0, omega=1.0):
+    """Rotating circle of Sec. 4.2: a circle of diameter db at the centre of
+    the square [0, L]^2, L = domain_over_db * db, N cells per side, in the
+    solid-body rotation of angular velocity omega about the centre.
+    Returns the grid, the cell-centre radius and polar angle (cell shape)
+    and the face velocities (ux, uy)."""
+    L = domain_over_db * db
+    h = L / N
+    g = Grid(PLANAR, N, N, 1, h)
+    X, Y, _ = cell_centre_offsets((1, N, N), h, (-0.5 * L, -0.5 * L, 0.0))
+    ux, uy = solid_rotation_faces(N, h, (0.5 * L, 0.5 * L), omega)
+    return g, np.sqrt(X * X + Y * Y), np.arctan2(Y, X), (ux, uy)
+
+
 def uniform_faces(grid: Grid, vel):
     """Uniform translation velocity on every face."""
     nz, ny, nx = grid.shape
