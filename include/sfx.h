@@ -137,6 +137,16 @@ sfx_status sfx_phase_field_build(sfx_ctx* ctx, const double* C, double* chi,
                                  void* phi, void* delta, int iters,
                                  double dtau, double eps, void* stream);
 
+/* a2 alone.  The carrier from a given signed distance (Sec. 2.5):
+   phi = (1 - tanh(chi/(2 eps)))/2 and delta = phi (1 - phi)/eps, chi > 0
+   inside fluid 1.  For interfaces whose distance is known (an exact
+   circle or sphere, or a distance computed elsewhere) instead of a VoF
+   fraction.  chi, phi, delta: double cell arrays (device) in both
+   precisions; delta may be NULL; no output may alias chi.  SFX_ERR_ARG on a
+   null chi or phi, an output aliasing chi, or eps <= 0. */
+sfx_status sfx_phase_field_from_chi(sfx_ctx* ctx, const double* chi, double* phi,
+                                    double* delta, double eps, void* stream);
+
 /* a3.  Explicit BCG advection xi* = xi - dt div(u xi) (Sec. 3.1) of one
    state field (double, or double-float pairs in SFX_F32 contexts) with face
    velocities u (context precision); bc_in is the value carried in through

@@ -107,6 +107,10 @@ class Context:
                                            int(iters), float(dtau), float(eps), _stream()),
                "sfx_phase_field_build")
 
+    def sfx_phase_field_from_chi(self, chi, phi, delta=None, eps=None):
+        _check(lib().sfx_phase_field_from_chi(self._h, _ptr(chi), _ptr(phi), _ptr(delta),
+                                              float(eps), _stream()), "sfx_phase_field_from_chi")
+
     def sfx_advect(self, ux, uy, uz, dt, xi, bc_in, xi_out):
         _check(lib().sfx_advect(self._h, _ptr(ux), _ptr(uy), _ptr(uz), float(dt), _ptr(xi),
                                 float(bc_in), _ptr(xi_out), _stream()), "sfx_advect")

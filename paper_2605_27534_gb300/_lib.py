@@ -26,6 +26,7 @@ EXPORTS = [
     "sfx_batch_layout", "sfx_batch_set_schedule", "sfx_batch_step", "sfx_batch_stats",
     "sfx_batch_autotune", "sfx_batch_work", "sfx_f_from_gamma", "sfx_marangoni_loss",
     "sfx_adjoint_apply", "sfx_adjoint_step", "sfx_vof_advect", "sfx_capillary_force", "sfx_acdi_step", "sfx_batch_reuse_phi",
+    "sfx_phase_field_from_chi",
 ]
 SFX_TUNE_FUSED_SWEEP = 0
 SFX_TUNE_F32_SOLVER = 1
@@ -92,6 +93,8 @@ def load(path: str = SO_PATH):
     L.sfx_default_opts.argtypes = [C.POINTER(SolveOpts)]
     L.sfx_phase_field_build.restype = C.c_int
     L.sfx_phase_field_build.argtypes = [vp, vp, vp, vp, vp, C.c_int, dp, dp, vp]
+    L.sfx_phase_field_from_chi.restype = C.c_int
+    L.sfx_phase_field_from_chi.argtypes = [vp, vp, vp, vp, dp, vp]
     L.sfx_advect.restype = C.c_int
     L.sfx_advect.argtypes = [vp, vp, vp, vp, dp, vp, dp, vp, vp]
     L.sfx_mg_solve.restype = C.c_int

@@ -204,6 +204,12 @@ sfx_status sfx_phase_field_build(sfx_ctx* c, const double* C, double* chi, void*
   return phase_field_build(c, C, chi, phi, delta, iters, dtau, eps, S(stream));
 }
 
+sfx_status sfx_phase_field_from_chi(sfx_ctx* c, const double* chi, double* phi, double* delta,
+                                    double eps, void* stream) {
+  if (!c || !chi || !phi || !(eps > 0.0) || phi == chi || delta == chi) return SFX_ERR_ARG;
+  return phase_field_from_chi(c, chi, phi, delta, eps, S(stream));
+}
+
 sfx_status sfx_advect(sfx_ctx* c, const void* ux, const void* uy, const void* uz, double dt,
                       const void* xi, double bc_in, void* xi_out, void* stream) {
   if (!c || !ux || !uy || !xi || !xi_out || xi == xi_out || !(dt > 0.0)) return SFX_ERR_ARG;

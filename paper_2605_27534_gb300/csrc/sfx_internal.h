@@ -160,6 +160,8 @@ void prof_after(sfx_ctx* c, int kind, cudaStream_t s);
 // sfx_phase.cu
 sfx_status phase_field_build(sfx_ctx* c, const double* C, double* chi, void* phi, void* delta,
                              int iters, double dtau, double eps, cudaStream_t s);
+sfx_status phase_field_from_chi(sfx_ctx* c, const double* chi, double* phi, double* delta,
+                                double eps, cudaStream_t s);
 // sfx_advect.cu
 sfx_status advect(sfx_ctx* c, const void* ux, const void* uy, const void* uz, double dt,
                   const double* xi, double bc_in, double* out, cudaStream_t s);

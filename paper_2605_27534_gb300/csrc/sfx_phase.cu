@@ -247,4 +247,12 @@ sfx_status phase_field_build(sfx_ctx* c, const double* C, double* chi, void* phi
   return SFX_OK;
 }
 
+sfx_status phase_field_from_chi(sfx_ctx* c, const double* chi, double* phi, double* delta,
+                                double eps, cudaStream_t s) {
+  const size_t n = c->lev[0].lv.ncell();
+  SFX_KERNEL(c, K_PHASE, k_phi_delta64, blocks_for(n, 256), 256, s, n, eps, chi, phi, delta);
+  SFX_LAUNCH_CHECK();
+  return SFX_OK;
+}
+
 }  // namespace sfx
