@@ -184,9 +184,12 @@ void orc_phase_field_build(const orc_grid* g, const double* C, int iters,
    READING: the paper leaves n undefined where phi is flat.  Beyond the
    redistancing band phi is flat up to variations many orders below its
    own profile slope, and there the direction of grad phi is set by those
-   variations (by round-off at the last few bits).  n is taken as 0 where
-   |grad phi| < ORC_NORMAL_KAPPA phi (1 - phi)/eps (the slope of the
-   equilibrium profile is phi (1 - phi)/eps), or where |grad phi| < 1e-30. */
+   variations (by round-off at the last few bits).  With
+   q = |grad phi| / (phi (1 - phi)/eps), the ratio to the slope of the
+   equilibrium profile, n is scaled by w = min(max(q/ORC_NORMAL_KAPPA - 1,
+   0), 1): n = 0 where q <= ORC_NORMAL_KAPPA, the unit vector where
+   q >= 2 ORC_NORMAL_KAPPA, and a linear ramp between, so that n (and the
+   step) depends continuously on phi; n = 0 where |grad phi| < 1e-30. */
 void orc_normals(const orc_grid* g, const double* phi, double eps, double* n) {
   size_t N = ncell_of(g);
   int D = ndim_of(g);
@@ -202,8 +205,13 @@ void orc_normals(const orc_grid* g, const double* phi, double eps, double* n) {
         }
         double m = sqrt(m2);
         double slope = phi[c] * (1.0 - phi[c]) / eps;
-        int flat = m < 1e-30 || m < ORC_NORMAL_KAPPA * slope;
-        for (int d = 0; d < D; ++d) n[d * N + c] = flat ? 0.0 : gp[d] / m;
+        double w = 0.0;
+        if (m >= 1e-30) {
+          w = m / (ORC_NORMAL_KAPPA * slope) - 1.0;
+          if (w > 1.0) w = 1.0;
+          if (!(w > 0.0)) w = 0.0;
+        }
+        for (int d = 0; d < D; ++d) n[d * N + c] = w > 0.0 ? w * (gp[d] / m) : 0.0;
       }
 }
 

@@ -79,8 +79,9 @@ void orc_phase_field_build(const orc_grid* g, const double* C, int iters,
 
 /* unit normal n = grad(phi)/|grad(phi)| at cell centres, centred
    differences, zero-gradient walls; n = 0 where |grad phi| < 1e-30.
-   n has 2 (or 3) arrays of N values: n[d*N + c]. */
-/* n is 0 where |grad phi| < ORC_NORMAL_KAPPA phi (1 - phi)/eps (flat phi) */
+   n has 2 (or 3) arrays of N values: n[d*N + c].  Where phi is flat the
+   normal fades out: n is scaled by min(max(q/ORC_NORMAL_KAPPA - 1, 0), 1),
+   q = |grad phi| / (phi (1 - phi)/eps). */
 #define ORC_NORMAL_KAPPA 1e-3
 void orc_normals(const orc_grid* g, const double* phi, double eps, double* n);
 

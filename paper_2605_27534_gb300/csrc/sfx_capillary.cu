@@ -40,14 +40,14 @@ __device__ __forceinline__ void normal3_f64(const Level& L, const double* __rest
   }
   const double m = sqrt(g0 * g0 + g1 * g1 + g2 * g2);
   const double pc = phi[cidx(L, i, j, k)];
-  const double slope = pc * (1.0 - pc) / eps;
-  if (m < 1e-30 || m < kNormalKappa * slope) {
+  const double w = normal_fade(m, pc * (1.0 - pc) / eps);
+  if (!(w > 0.0)) {
     n[0] = n[1] = n[2] = 0.0;
     return;
   }
-  n[0] = g0 / m;
-  n[1] = g1 / m;
-  n[2] = g2 / m;
+  n[0] = w * (g0 / m);
+  n[1] = w * (g1 / m);
+  n[2] = w * (g2 / m);
 }
 
 template <typename T>

@@ -84,12 +84,21 @@ __device__ inline void warp_sum_comp(double& s, double& c) {
 
 // n is undefined where phi is flat: beyond the redistancing band phi is
 // flat up to variations far below its own profile slope phi (1 - phi)/eps,
-// whose direction is set by the last bits of phi.  n = 0 where
-// |grad phi| < kNormalKappa phi (1 - phi)/eps or |grad phi| < 1e-30.
+// whose direction is set by the last bits of phi.  With q = |grad phi| /
+// (phi (1 - phi)/eps), n fades out continuously: it is scaled by
+// w = clamp(q/kNormalKappa - 1, 0, 1) (0 at or below kNormalKappa, the
+// unit vector at or above twice it), and n = 0 where |grad phi| < 1e-30.
+// A hard cut-off would make the step jump when a round-off change of phi
+// moves q of a band-edge cell across it.
 constexpr double kNormalKappa = 1e-3;
 
+__device__ __forceinline__ double normal_fade(double m, double slope) {
+  return m < 1e-30 ? 0.0 : fmin(fmax(m / (kNormalKappa * slope) - 1.0, 0.0), 1.0);
+}
+
 // Unit normal component n_d = (grad phi)_d / |grad phi| at cell (i,j,k):
-// centred differences, zero-gradient walls, 0 where phi is flat (above).
+// centred differences, zero-gradient walls, faded out where phi is flat
+// (above).
 template <typename P>
 __device__ __forceinline__ double normal_comp(const Level& L, const P* __restrict__ phi, int i,
                                               int j, int k, int d, double eps) {
@@ -106,7 +115,8 @@ __device__ __forceinline__ double normal_comp(const Level& L, const P* __restric
   double m = sqrt(g[0] * g[0] + g[1] * g[1] + g[2] * g[2]);
   const double pc = (double)phi[cidx(L, i, j, k)];
   const double slope = pc * (1.0 - pc) / eps;
-  return (m < 1e-30 || m < kNormalKappa * slope) ? 0.0 : g[d] / m;
+  const double w = normal_fade(m, slope);
+  return w > 0.0 ? w * (g[d] / m) : 0.0;
 }
 
 }  // namespace sfx

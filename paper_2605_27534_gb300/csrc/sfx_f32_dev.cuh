@@ -20,8 +20,9 @@ __device__ __forceinline__ float fold_phi(double p) {
 }
 
 // n = grad phi/|grad phi| at cell (i,j,k) (centred differences, one-sided
-// copies at walls), n = 0 where phi is flat: |grad phi| below
-// kNormalKappa phi (1 - phi)/eps or below 1e-30.  The differences are
+// copies at walls), faded out where phi is flat: scaled by
+// clamp(q/kNormalKappa - 1, 0, 1), q = |grad phi| / (phi (1 - phi)/eps),
+// and 0 below |grad phi| = 1e-30.  The differences are
 // taken in FP64 from the double phi: deep in the bulk they are far below
 // float resolution of phi but still fix the direction.  The 1/(2h) of the
 // centred difference cancels in the normalisation; the components are
@@ -45,10 +46,13 @@ __device__ __forceinline__ void normal3_f32(const Level& L, const double* __rest
   const float r = sqrtf(s0 * s0 + s1 * s1 + s2 * s2);   // in [1, sqrt 3]
   const PhiPair pc = unfold(fold_phi(phi[cidx(L, i, j, k)]));
   const float m = mx * r * (0.5f / (float)L.h);
-  if (m < 1e-30f || m < (float)kNormalKappa * (pc.p * pc.q * inv_eps)) return;
-  n[0] = s0 / r;
-  n[1] = s1 / r;
-  n[2] = s2 / r;
+  if (m < 1e-30f) return;
+  const float w = fminf(fmaxf(m / ((float)kNormalKappa * (pc.p * pc.q * inv_eps)) - 1.0f, 0.0f),
+                        1.0f);
+  if (!(w > 0.0f)) return;
+  n[0] = w * (s0 / r);
+  n[1] = w * (s1 / r);
+  n[2] = w * (s2 / r);
 }
 
 __device__ __forceinline__ float normal_f32(const Level& L, const double* __restrict__ phi, int i,

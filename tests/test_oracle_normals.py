@@ -1,6 +1,7 @@
 """Pins of the oracle's unit normal n = grad phi/|grad phi| (Sec. 2.6) and
-of its reading where phi is flat: n = 0 where |grad phi| is below
-1e-3 phi (1 - phi)/eps, the slope of the equilibrium profile."""
+of its reading where phi is flat: with q = |grad phi| / (phi (1 - phi)/eps),
+the ratio to the slope of the equilibrium profile, n = 0 for q <= 1e-3, the
+unit vector for q >= 2e-3 and a linear fade between."""
 import numpy as np
 
 import oracle
@@ -47,8 +48,10 @@ def test_flat_phi_with_round_off_variations_has_no_normal():
 
 
 def test_guard_threshold_is_relative_to_the_profile_slope():
-    """phi = a + s x with |grad phi| = s: above 1e-3 a (1 - a)/eps the
-    normal is e_x, below it 0 (cells away from the walls)."""
+    """phi = a + s x with |grad phi| = s: at or above 2e-3 a (1 - a)/eps the
+    normal is e_x, at or below 1e-3 a (1 - a)/eps it is 0, and between the
+    two it fades linearly (cells away from the walls, where phi's cell
+    value is a + s (x - 1/2), so q varies by a few per cent along x)."""
     n = 16
     g = _grid(n)
     eps = 0.75 * g.h
@@ -62,6 +65,31 @@ def test_guard_threshold_is_relative_to_the_profile_slope():
         nrm = oracle.normals(g, phi, eps)
         np.testing.assert_allclose(nrm[0][inner], want, rtol=0, atol=1e-12)
         assert np.all(nrm[1][inner] == 0.0)
+    # the fade: n_x = q/1e-3 - 1 with q = s/(phi (1 - phi)/eps) per cell
+    s = 1.5e-3 * slope_eq
+    phi = np.broadcast_to(a + s * (x - 0.5)[None, None, :], g.shape).copy()
+    nrm = oracle.normals(g, phi, eps)
+    q = s / (phi * (1 - phi) / eps)
+    np.testing.assert_allclose(nrm[0][inner], (q / 1e-3 - 1.0)[inner], rtol=0, atol=1e-9)
+    assert 0.3 < nrm[0][inner].min() and nrm[0][inner].max() < 0.7
+
+
+def test_normal_depends_continuously_on_phi_where_it_fades():
+    """Across the fade a relative change of 1e-9 in grad phi moves n by at
+    most ~1e-9 / 1e-3 of the ramp's slope, never by a jump."""
+    n = 16
+    g = _grid(n)
+    eps = 0.75 * g.h
+    a = 0.2
+    x = (np.arange(n) + 0.5) * g.h
+    inner = (slice(None), slice(None), slice(3, -3))
+    for fac in np.linspace(0.9e-3, 2.1e-3, 13):
+        s = fac * a * (1 - a) / eps
+        out = []
+        for ds in (0.0, 1e-9):
+            phi = np.broadcast_to(a + s * (1 + ds) * (x - 0.5)[None, None, :], g.shape).copy()
+            out.append(oracle.normals(g, phi, eps)[0][inner])
+        assert np.abs(out[1] - out[0]).max() < 1e-5
 
 
 def test_sphere_normals_are_radial_in_3d():
