@@ -188,7 +188,11 @@ sfx_status sfx_vof_advect(sfx_ctx* ctx, const void* ux, const void* uy, const vo
    the fully implicit f/F system of App. C solved by Picard iteration, each
    half a multigrid solve of the Sec. 3.1 operator with the drifts
    B_f = -Df 2(0.5 - phi)/eps n and B_F = -DF (1 - phi)/eps n,
-   n = grad phi/|grad phi| (n = 0 where |grad phi| < 1e-30).  f and F
+   n = grad phi/|grad phi| by centred differences, faded out where phi is
+   flat: with q = |grad phi| / (phi (1 - phi)/eps), the ratio to the slope
+   of the equilibrium tanh profile, n is scaled by clamp(q/1e-3 - 1, 0, 1)
+   (0 for q <= 1e-3, the unit vector for q >= 2e-3), and n = 0 where
+   |grad phi| < 1e-30.  f and F
    (state layout of the context) are updated in place; phi is double, the
    velocities are in the context precision.  SFX_F32 contexts solve the
    same system by coupled Newton defect correction (SFX_TUNE_F32_SOLVER):
@@ -212,8 +216,8 @@ sfx_status sfx_totals(sfx_ctx* ctx, const void* const* fields, int n_fields,
 /* Largest n_fields that sfx_totals_noalloc accepts. */
 #define SFX_NOALLOC_MAX_FIELDS 8
 
-/* The totals of sfx_totals (same reduction order, same result) without a
-   context and without allocating.  For callers that may not allocate device
+/* The totals of sfx_totals (same launch shape and reduction order, so the
+   same bits) without a context and without allocating.  For callers that may not allocate device
    memory: programs whose device memory belongs to another allocator, and
    code that must avoid the device-wide synchronisation of cudaMalloc and
    cudaFree.  The paper has no counterpart; this is a service of the
@@ -455,15 +459,18 @@ sfx_status sfx_batch_stats(sfx_batch* b, int* iters, float* res_f, float* res_F,
    Waits for stream. */
 sfx_status sfx_batch_work(sfx_batch* b, long long* resid_passes, long long* sweep_groups,
                           int reset, void* stream);
-/* Autotuner: runs one step of every candidate schedule (block 128 or 256,
-   2, 3 or 4 sweeps) on scratch copies of f and F (which stay unchanged),
+/* Autotuner: runs one step of every candidate schedule (tiles of 128, 256
+   or 512 packed cells per block, 2, 3 or 4 sweeps) on scratch copies of f
+   and F (which stay unchanged),
    gives each the smallest iteration budget under which every instance
    converged (plus one spare), times it and keeps the fastest schedule.
    Since a step's iterations end on the device once every instance has
    converged, the budget kept is only a cap: twice the probed one, at least
    16 (at most 200; 200 when no candidate converged every instance within
    40 iterations).  chosen (3 ints, may be NULL) receives block, sweeps and
-   budget.  Waits for stream. */
+   budget.  Allocates the two scratch copies (cudaMalloc) and releases
+   them, and its events, on every return; on an error the previous schedule
+   is restored.  Waits for stream. */
 sfx_status sfx_batch_autotune(sfx_batch* b, const void* phi, const void* ur, const void* uz,
                               const void* f, const void* F, double tol, void* stream,
                               int* chosen);

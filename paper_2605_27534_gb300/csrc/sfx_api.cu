@@ -179,7 +179,7 @@ sfx_status sfx_ctx_create(const sfx_grid* grid, int precision, sfx_ctx** out) {
   if (st == SFX_OK) st = dalloc(c, &c->Fstar, n);
   if (st == SFX_OK) st = dalloc(c, &c->chi0, n);
   if (st == SFX_OK) st = dalloc(c, &c->chi_tmp, n);
-  c->n_partial_blocks = 152 * 4;
+  c->n_partial_blocks = kTotalsBlocks;
   if (st == SFX_OK) st = dalloc(c, &c->partials, (size_t)2 * 8 * c->n_partial_blocks);
   if (st == SFX_OK) st = dalloc(c, &c->d_norms, 8);
   if (st == SFX_OK) st = dalloc(c, &c->d_sums, 8);

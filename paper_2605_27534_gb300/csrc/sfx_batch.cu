@@ -685,37 +685,38 @@ sfx_status sfx_batch_work(sfx_batch* b, long long* resid_passes, long long* swee
   return SFX_OK;
 }
 
-// Autotuner: candidate schedules (block size x sweeps per iteration) are run
-// on scratch copies of the state; each gets the smallest iteration budget
-// that converges every instance (read from a probe step with a generous
-// budget), then the fastest candidate is kept.
-sfx_status sfx_batch_autotune(sfx_batch* b, const void* phi, const void* ur, const void* uz,
-                              const void* f, const void* F, double tol, void* stream,
-                              int* chosen) {
-  if (!b || !phi || !f || !F) return SFX_ERR_ARG;
-  cudaStream_t s = (cudaStream_t)stream;
-  const size_t bytes = b->ncell * sizeof(float2);
-  float2 *fw = nullptr, *Fw = nullptr;
-  SFX_CUDA(cudaMalloc(&fw, bytes));
-  SFX_CUDA(cudaMalloc(&Fw, bytes));
-  const int blocks[2] = {128, 256};
+// Autotuner: candidate schedules (threads per block, i.e. the tile of
+// packed cells one block updates, x sweeps per iteration) are run on scratch
+// copies of the state; each gets the smallest iteration budget that
+// converges every instance (read from a probe step with a generous budget),
+// then the fastest candidate is kept.
+namespace {
+
+struct TuneBest {
+  float ms = 1e30f;
+  int block = 0, sweeps = 0, iters = 0;
+};
+
+// Probes and times every candidate; returns on the first error (the caller
+// releases the scratch and events on every path).
+sfx_status autotune_candidates(sfx_batch* b, const void* phi, const void* ur, const void* uz,
+                               const void* f, const void* F, float2* fw, float2* Fw,
+                               size_t bytes, double tol, cudaStream_t s, void* stream,
+                               cudaEvent_t e0, cudaEvent_t e1, TuneBest* best) {
+  const int blocks[3] = {128, 256, 512};
   const int sweeps[3] = {2, 3, 4};
-  float best = 1e30f;
-  int bb = b->block, bsw = b->sweeps, bit = b->max_it;
-  cudaEvent_t e0, e1;
-  SFX_CUDA(cudaEventCreate(&e0));
-  SFX_CUDA(cudaEventCreate(&e1));
-  sfx_status st = SFX_OK;
   std::vector<int> it(b->n), conv(b->n);
-  for (int bi = 0; bi < 2 && st == SFX_OK; ++bi)
-    for (int si = 0; si < 3 && st == SFX_OK; ++si) {
+  for (int bi = 0; bi < 3; ++bi)
+    for (int si = 0; si < 3; ++si) {
       // probe: generous budget, read the iterations each instance needs
-      if ((st = sfx_batch_set_schedule(b, blocks[bi], sweeps[si], 40)) != SFX_OK) break;
+      sfx_status st = sfx_batch_set_schedule(b, blocks[bi], sweeps[si], 40);
+      if (st != SFX_OK) return st;
       SFX_CUDA(cudaMemcpyAsync(fw, f, bytes, cudaMemcpyDeviceToDevice, s));
       SFX_CUDA(cudaMemcpyAsync(Fw, F, bytes, cudaMemcpyDeviceToDevice, s));
-      if ((st = sfx_batch_step(b, phi, ur, uz, fw, Fw, tol, stream)) != SFX_OK) break;
+      if ((st = sfx_batch_step(b, phi, ur, uz, fw, Fw, tol, stream)) != SFX_OK) return st;
       if ((st = sfx_batch_stats(b, it.data(), nullptr, nullptr, nullptr, nullptr, conv.data(),
-                                stream)) != SFX_OK) break;
+                                stream)) != SFX_OK)
+        return st;
       int need = 1;
       bool all = true;
       for (int i = 0; i < b->n; ++i) {
@@ -723,12 +724,12 @@ sfx_status sfx_batch_autotune(sfx_batch* b, const void* phi, const void* ur, con
         all = all && conv[i];
       }
       if (!all) continue;
-      if ((st = sfx_batch_set_schedule(b, blocks[bi], sweeps[si], need + 1)) != SFX_OK) break;
+      if ((st = sfx_batch_set_schedule(b, blocks[bi], sweeps[si], need + 1)) != SFX_OK) return st;
       float ms_best = 1e30f;
       for (int rep = 0; rep < 3; ++rep) {
         SFX_CUDA(cudaMemcpyAsync(fw, f, bytes, cudaMemcpyDeviceToDevice, s));
         SFX_CUDA(cudaMemcpyAsync(Fw, F, bytes, cudaMemcpyDeviceToDevice, s));
-        if ((st = ensure_graph(b, phi, ur, uz, fw, Fw, (float)tol)) != SFX_OK) break;
+        if ((st = ensure_graph(b, phi, ur, uz, fw, Fw, (float)tol)) != SFX_OK) return st;
         SFX_CUDA(cudaEventRecord(e0, s));
         SFX_CUDA(cudaGraphLaunch(b->exec, s));
         SFX_CUDA(cudaEventRecord(e1, s));
@@ -737,27 +738,51 @@ sfx_status sfx_batch_autotune(sfx_batch* b, const void* phi, const void* ur, con
         SFX_CUDA(cudaEventElapsedTime(&ms, e0, e1));
         ms_best = std::min(ms_best, ms);
       }
-      if (ms_best < best) {
-        best = ms_best;
-        bb = blocks[bi];
-        bsw = sweeps[si];
-        bit = need + 1;
-      }
+      if (ms_best < best->ms) *best = TuneBest{ms_best, blocks[bi], sweeps[si], need + 1};
     }
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
+  return SFX_OK;
+}
+
+}  // namespace
+
+sfx_status sfx_batch_autotune(sfx_batch* b, const void* phi, const void* ur, const void* uz,
+                              const void* f, const void* F, double tol, void* stream,
+                              int* chosen) {
+  if (!b || !phi || !f || !F) return SFX_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t bytes = b->ncell * sizeof(float2);
+  const int block0 = b->block, sweeps0 = b->sweeps, iters0 = b->max_it;
+  float2 *fw = nullptr, *Fw = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  TuneBest best;
+  sfx_status st = SFX_OK;
+  cudaError_t ce = cudaMalloc(&fw, bytes);
+  if (ce == cudaSuccess) ce = cudaMalloc(&Fw, bytes);
+  if (ce == cudaSuccess) ce = cudaEventCreate(&e0);
+  if (ce == cudaSuccess) ce = cudaEventCreate(&e1);
+  if (ce != cudaSuccess) st = cuda_fail(ce);
+  else
+    st = autotune_candidates(b, phi, ur, uz, f, F, fw, Fw, bytes, tol, s, stream, e0, e1, &best);
+  if (st != SFX_OK) cudaStreamSynchronize(s);   // no copy into the scratch left in flight
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
   if (b->exec) {   // its pointers are the scratch copies freed below
     cudaGraphExecDestroy(b->exec);
     b->exec = nullptr;
   }
-  cudaFree(fw);
-  cudaFree(Fw);
-  if (st != SFX_OK) return st;
+  if (fw) cudaFree(fw);
+  if (Fw) cudaFree(Fw);
+  if (st != SFX_OK) {
+    sfx_batch_set_schedule(b, block0, sweeps0, iters0);
+    return st;
+  }
   // the iteration loop ends on the device once every instance converged,
   // so the budget is only a cap: keep room for later steps that need more
   // iterations than the probed one
   // (200 when no candidate converged every instance within the probe's 40)
-  bit = best < 1e30f ? std::min(200, std::max(2 * bit, 16)) : 200;
+  const bool found = best.ms < 1e30f;
+  const int bb = found ? best.block : block0, bsw = found ? best.sweeps : sweeps0;
+  const int bit = found ? std::min(200, std::max(2 * best.iters, 16)) : 200;
   st = sfx_batch_set_schedule(b, bb, bsw, bit);
   if (chosen) {
     chosen[0] = bb;

@@ -840,11 +840,15 @@ __global__ void k_total32_final(const double* __restrict__ partials, int nblk, d
 struct Eos32 {
   float ginf, eps, inv_eps, sigma0, E;
   int eos;
+  double ginf_d, eps_d, sigma0_d, E_d;   // the same in FP64 (near saturation)
 };
 
 // sigma - sigma0 (kept for the gradient, where it has full relative
-// precision) and sigma itself.  The Langmuir logarithm is taken in FP64
-// once Gamma/Gamma_inf exceeds 1/2 (near saturation), in FP32 below.
+// precision) and sigma itself.  Near saturation (Gamma/Gamma_inf > 1/2) the
+// Langmuir term is formed in FP64 throughout: delta_phi from the double
+// phi, Gamma from the whole double-float pair of f, 1 - Gamma/Gamma_inf and
+// its logarithm, since float spacing in Gamma/Gamma_inf (6e-8) would be a
+// large relative error of 1 - Gamma/Gamma_inf there.  FP32 below.
 __global__ void k_eos32(size_t n, Eos32 q, const float2* __restrict__ f,
                         const double* __restrict__ phi, float* __restrict__ dsig,
                         float* __restrict__ sigma) {
@@ -857,8 +861,11 @@ __global__ void k_eos32(size_t n, Eos32 q, const float2* __restrict__ f,
     float ds;
     if (q.eos == SFX_EOS_LANGMUIR) {
       if (x > 0.5f) {
-        double xd = fmin((double)x, 1.0 - 1e-12);
-        ds = (float)((double)q.sigma0 * (double)q.E * log1p(-xd));
+        const double pd = phi[c];
+        const double deld = pd * (1.0 - pd) / q.eps_d;
+        const float2 fc = f[c];
+        const double xd = ((double)fc.x + (double)fc.y) / deld / q.ginf_d;
+        ds = (float)(q.sigma0_d * q.E_d * log1p(-fmin(xd, 1.0 - 1e-12)));
       } else {
         ds = q.sigma0 * q.E * log1pf(-x);
       }
@@ -1500,7 +1507,7 @@ sfx_status marangoni32(sfx_ctx* c, const sfx_params* p, const float2* f, const d
   const Level& L = c->lev[0].lv;
   const size_t n = L.ncell();
   Eos32 q{(float)p->gamma_inf, (float)p->eps, (float)(1.0 / p->eps), (float)p->sigma0,
-          (float)p->E, p->eos};
+          (float)p->E, p->eos, p->gamma_inf, p->eps, p->sigma0, p->E};
   SFX_KERNEL(c, K_FORCES, k_eos32, blocks_for(n, 256), 256, s, n, q, f, phi, c->f32.dsig, sigma);
   const RowGrid fg = row_grid(L);
   SFX_KERNEL(c, K_FORCES, k_force32, fg.grid, fg.block, s, L, phi, C, c->f32.dsig, dm_mode,

@@ -10,7 +10,7 @@
 namespace sfx {
 namespace {
 
-constexpr int kTotThreads = 256;
+constexpr int kTotThreads = kTotalsThreads;
 
 // Per-block compensated partial sums of V x for field `fi`.
 __global__ void k_total_partials(Level L, const double* __restrict__ x, int fi,

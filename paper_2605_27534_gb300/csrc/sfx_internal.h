@@ -13,6 +13,12 @@
 
 namespace sfx {
 
+// Launch shape of the compensated FP64 totals: blocks of partial sums and
+// threads per block.  sfx_totals and sfx_totals_noalloc both use it, so
+// they reduce in the same order and return the same bits.
+constexpr int kTotalsBlocks = 152 * 4;
+constexpr int kTotalsThreads = 256;
+
 // Device arrays of one multigrid level.  Level 0 (the fine grid) works on
 // the caller's field; its coefficient arrays live here too.
 struct LevelData {

@@ -21,8 +21,8 @@
 namespace sfx {
 namespace {
 
-constexpr int kNaThreads = 256;
-constexpr int kNaBlocks = 152 * 4;
+constexpr int kNaThreads = kTotalsThreads;
+constexpr int kNaBlocks = kTotalsBlocks;
 constexpr int kNaSlots = 2 * SFX_NOALLOC_MAX_FIELDS * kNaBlocks + SFX_NOALLOC_MAX_FIELDS;
 
 // Device scratch: partial sums (s, c) per field and block, then one result

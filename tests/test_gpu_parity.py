@@ -553,3 +553,135 @@ def test_invalid_arguments_rejected(sfx):
         ctx.sfx_surfactant_step(bad, f, f.clone(), f.clone(), 0.1)
     with pytest.raises(sfx.SfxError, match="invalid argument"):
         sfx.Context(W.PLANAR, 8, 8, 2, 0.1)               # nz > 1 in 2D
+
+
+def _wide_case(name):
+    """Grids whose colour rows fill one 128-thread block of the FP32 Newton
+    kernels and spill into more with a ragged tail: planar 520 x 40 (260
+    cells per colour row: 128 + 128 + 4) and 3D 258 x 20 x 16 (129: 128 + 1),
+    a circle (an extruded cylinder in 3D) in solid-body rotation (plus a
+    uniform axial velocity in 3D), soluble surfactant."""
+    nx, ny, nz = (520, 40, 1) if name == "planar520" else (258, 20, 16)
+    h = 1.0 / 64
+    xc, yc, R = 0.5 * nx * h, 0.5 * ny * h, 0.2
+    C2 = W.circle_vof(nx, ny, h, xc, yc, R)
+    ux, uy = W.solid_rotation_faces((nx, ny), h, (xc, yc), 2.0)
+    if nz == 1:
+        g = W.Grid(W.PLANAR, nx, ny, 1, h)
+        Cf, uz = C2, None
+    else:
+        g = W.Grid(W.CART3D, nx, ny, nz, h)
+        Cf = np.repeat(C2, nz, axis=0)
+        ux, uy = np.repeat(ux, nz, axis=0), np.repeat(uy, nz, axis=0)
+        uz = np.full((nz + 1, ny, nx), 0.3)
+    p = W.Params(ka=2.0, kd=0.5, gamma_inf=1.0, Df=2e-3, DF=5e-3, eps=0.75 * h, bc_F=1.0,
+                 bc_f=0.0)
+    return g, Cf, p, ux, uy, uz, 0.25 * h
+
+
+@pytest.mark.parametrize("name", ["planar520", "cyl258"])
+def test_fp32_step_on_rows_wider_than_one_block(sfx, name):
+    """SFX_F32 steps on full and multi-block colour rows with a ragged tail
+    against the FP64 oracle (three steps, 1e-5)."""
+    import torch
+    g, Cf, p, ux, uy, uz, dt = _wide_case(name)
+    redist = W.redist_dtau(g)
+    _, phi, delta = oracle.phase_field_build(g, Cf, 24, redist, p.eps)
+    f0, F0 = 0.3 * delta, 1.0 - Cf
+    f_o, F_o = f0.copy(), F0.copy()
+    for _ in range(3):
+        f_o, F_o, st = oracle.surfactant_step(g, p, phi, f_o, F_o, dt, 1e-13, ux, uy, uz)
+        assert st.converged
+    ctx = _ctx(sfx, g, 1)
+    f, F = _pairs(ctx, f0), _pairs(ctx, F0)
+    u = [None if v is None else dev(v, torch.float32) for v in (ux, uy, uz)]
+    opts = sfx.default_opts(tol=1e-10, max_cycles=400)
+    for _ in range(3):
+        assert ctx.sfx_surfactant_step(p, dev(phi), f, F, dt, *u, opts=opts).converged
+    scale = max(np.abs(F_o).max(), np.abs(f_o).max())
+    assert np.abs(host(ctx.sfx_df_unpack(F)) - F_o).max() / scale < F32_TOL
+    assert np.abs(host(ctx.sfx_df_unpack(f)) - f_o).max() / scale < F32_TOL
+
+
+def test_fp32_phase_field_build_and_step_against_oracle(sfx):
+    """The FP32 form end to end on the 3D HR workload at 40^3: the phase
+    field from the FP32 redistancing of the SFX_F32 context (not the
+    oracle's), then two FP32 steps, against the oracle's FP64 build and
+    steps."""
+    import torch
+    c = W.case_hr_3d(n=40, steps=2)
+    g, p = c.grid, c.params
+    _, phi_o, _ = oracle.phase_field_build(g, c.C, c.redist_iters, c.dtau, p.eps)
+    f_o, F_o = np.zeros(g.shape), c.F0.copy()
+    for _ in range(2):
+        f_o, F_o, st = oracle.surfactant_step(g, p, phi_o, f_o, F_o, c.dt, 1e-13, c.ux, c.uy,
+                                              c.uz)
+        assert st.converged
+    ctx = _ctx(sfx, g, 1)
+    Cd = dev(c.C)
+    chi, phi = torch.empty_like(Cd), torch.empty_like(Cd)
+    ctx.sfx_phase_field_build(Cd, chi, phi, None, iters=c.redist_iters, dtau=c.dtau, eps=p.eps)
+    f, F = _pairs(ctx, np.zeros(g.shape)), _pairs(ctx, c.F0)
+    u = [dev(v, torch.float32) for v in (c.ux, c.uy, c.uz)]
+    opts = sfx.default_opts(tol=1e-10, max_cycles=400)
+    for _ in range(2):
+        assert ctx.sfx_surfactant_step(p, phi, f, F, c.dt, *u, opts=opts).converged
+    scale = max(np.abs(F_o).max(), np.abs(f_o).max())
+    assert np.abs(host(ctx.sfx_df_unpack(F)) - F_o).max() / scale < F32_TOL
+    assert np.abs(host(ctx.sfx_df_unpack(f)) - f_o).max() / scale < F32_TOL
+
+
+def test_fp32_build_and_step_at_256_cubed_match_the_fp64_path(sfx):
+    """The timed 256^3 workload: FP32 phase-field build and two FP32 steps
+    against the FP64 path (phase field from the FP64 build), which the
+    tests above hold to the oracle at 1e-12; the FP32 form within 1e-5."""
+    import torch
+    c = W.case_hr_3d(n=256, steps=2)
+    g, p = c.grid, c.params
+    Cd = dev(c.C)
+    out = []
+    for prec in (0, 1):
+        ctx = _ctx(sfx, g, prec)
+        chi, phi = torch.empty_like(Cd), torch.empty_like(Cd)
+        ctx.sfx_phase_field_build(Cd, chi, phi, None, iters=c.redist_iters, dtau=c.dtau,
+                                  eps=p.eps)
+        del chi
+        vt = torch.float64 if prec == 0 else torch.float32
+        u = [dev(v, vt) for v in (c.ux, c.uy, c.uz)]
+        F0 = dev(c.F0)
+        f, F = (torch.zeros_like(F0), F0) if prec == 0 else \
+            (ctx.sfx_df_pack(torch.zeros_like(F0)), ctx.sfx_df_pack(F0))
+        opts = sfx.default_opts(tol=1e-12 if prec == 0 else 1e-10, max_cycles=400)
+        for _ in range(2):
+            assert ctx.sfx_surfactant_step(p, phi, f, F, c.dt, *u, opts=opts).converged
+        if prec == 1:
+            f, F = ctx.sfx_df_unpack(f), ctx.sfx_df_unpack(F)
+        out.append((host(f), host(F)))
+        del ctx, u, phi
+        torch.cuda.empty_cache()
+    scale = max(np.abs(out[0][0]).max(), np.abs(out[0][1]).max())
+    assert np.abs(out[1][0] - out[0][0]).max() / scale < F32_TOL
+    assert np.abs(out[1][1] - out[0][1]).max() / scale < F32_TOL
+
+
+def test_fp32_langmuir_sigma_near_saturation(sfx):
+    """Gamma/Gamma_inf in [1 - 1e-6, 1 - 1e-9]: float spacing of the ratio
+    (6e-8) would be a large relative error of 1 - Gamma/Gamma_inf, so the
+    SFX_F32 EOS forms the Langmuir term in FP64 from the double phi and the
+    whole pair of f; sigma against the oracle's."""
+    import torch
+    g, Cf = GEOMS["planar"]()
+    p = W.Params(eps=0.75 * g.h, sigma0=1.0, E=0.2, gamma_inf=1.3, eos=W.EOS_LANGMUIR)
+    _, phi, delta = oracle.phase_field_build(g, Cf, 24, 0.5 * g.h, p.eps)
+    rng = np.random.default_rng(11)
+    x = 1.0 - 10.0 ** rng.uniform(-9.0, -6.0, g.shape)
+    f = x * p.gamma_inf * delta
+    sig_o, _ = oracle.marangoni(g, p, f, phi, Cf, 1)
+    band = delta >= 1e-3 / p.eps
+    assert band.sum() > 100
+    ctx = _ctx(sfx, g, 1)
+    sig = torch.empty(g.shape, dtype=torch.float32, device="cuda")
+    force = torch.empty((g.ndim,) + g.shape, dtype=torch.float32, device="cuda")
+    ctx.sfx_marangoni_force(p, _pairs(ctx, f), dev(phi), dev(Cf, torch.float32), sig, force, 1)
+    got = host(sig)
+    assert np.abs(got[band] - sig_o[band]).max() < 1e-6 * np.abs(sig_o[band]).max()

@@ -5,6 +5,7 @@ C-ABI and compared with sfx_totals on two calls in a row; the second call
 must not see the first call's leftover scratch.  This file is collected
 last on purpose."""
 import ctypes as C
+import math
 
 import numpy as np
 import pytest
@@ -15,7 +16,7 @@ from gpu_util import dev
 
 pytestmark = pytest.mark.gpu
 
-TOL = 4e-16   # relative to sum |V x|, as for the other totals tests
+TOL = 4e-16   # against the exact sum, relative to sum |V x| (as the other totals tests)
 
 
 @pytest.fixture(scope="module")
@@ -52,12 +53,13 @@ def test_noalloc_totals_match_context_totals_on_consecutive_calls(sfx):
         assert st == 0, sfx.lib().sfx_status_string(st)
         ref = sfx.Context.for_grid(g).sfx_totals(fields)
         V = oracle.cell_volumes(g)
-        scales = [np.abs(V * a).sum() for a in arrays]
-        for val, r, sc in zip(got, ref, scales):
-            assert abs(val - r) <= TOL * sc
-        # a second call on fewer fields right after: same answer again
+        for val, a in zip(got, arrays):
+            assert abs(val - math.fsum((V * a).ravel())) <= TOL * np.abs(V * a).sum()
+        # the same reduction order as sfx_totals: the same bits
+        assert got == ref
+        # a second call on fewer fields right after: the same bits again
         st2, got2 = _noalloc(sfx, g, fields[:1])
-        assert st2 == 0 and abs(got2[0] - ref[0]) <= TOL * scales[0]
+        assert st2 == 0 and got2[0] == ref[0]
 
 
 def test_noalloc_rejects_more_fields_than_its_scratch_holds(sfx):

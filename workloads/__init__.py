@@ -329,9 +329,11 @@ def ring_vortex_faces_axi(nr, nz, h):
 
 
 def solid_rotation_faces(n, h, centre, omega):
-    """Solid-body rotation about `centre` from psi = -omega/2 |x - c|^2."""
-    x = np.arange(n + 1) * h - centre[0]
-    y = np.arange(n + 1) * h - centre[1]
+    """Solid-body rotation about `centre` from psi = -omega/2 |x - c|^2 on
+    an n x n grid (n an int) or an nx x ny grid (n = (nx, ny))."""
+    nx, ny = (n, n) if np.isscalar(n) else n
+    x = np.arange(nx + 1) * h - centre[0]
+    y = np.arange(ny + 1) * h - centre[1]
     psi = -0.5 * omega * (x[None, :] ** 2 + y[:, None] ** 2)
     ux = (psi[1:, :] - psi[:-1, :]) / h
     uy = -(psi[:, 1:] - psi[:, :-1]) / h
