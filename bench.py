@@ -83,8 +83,11 @@ def parse():
     ap.add_argument("--precision", default="f32", choices=["f64", "f32"])
     ap.add_argument("--f64-steps", type=int, default=3,
                     help="steps of the FP64 path timed beside the FP32 line (0: skip)")
-    ap.add_argument("--batch-steps", type=int, default=0,
+    ap.add_argument("--batch-steps", type=int, default=30,
                     help="also time the batched workload for this many steps (0: skip)")
+    ap.add_argument("--adsorption-steps", type=int, default=1000,
+                    help="steps of the 128^2 FP64 no-flow adsorption workload timed beside "
+                         "the line (0: skip)")
     ap.add_argument("--kinetics-steps", type=int, default=20,
                     help="steps of the flat-interface kinetics sweep timed beside the line "
                          "(0: skip)")
@@ -131,13 +134,12 @@ def job_rate(units_per_rank, world, ms):
 
 
 def algorithmic_bytes(kind, grid, wbytes, sweeps=3):
-    """Unique global bytes one launch of `kind` must move on the fine grid
-    (reads + writes; arrays touched by half the cells count half).  N cells,
-    d dimensions, 8-byte state (double or double-float pair).
+    """Unique global bytes one launch of `kind` moves on the fine grid in
+    this design (reads + writes of the state and of the solver's own work
+    arrays; arrays touched by half the cells count half).  N cells, d
+    dimensions, 8-byte state (double or double-float pair).
     FP64 colour sweep (k_rbgs): a (all N, as neighbours) + b, lambda (N/2
       each) + d double face arrays + write a (N/2)       = 8 (2.5 + d) N
-    FP32 fused sweep (k_nlrb32_z, both colours): a in and out, a*, the other
-      field (8 B each), phi (4 B), d float face arrays   = (36 + 4 d) N
     Advection of one field: state in/out 16 N + d velocity arrays."""
     N = grid.ncell
     d = grid.ndim
@@ -145,20 +147,48 @@ def algorithmic_bytes(kind, grid, wbytes, sweeps=3):
         if wbytes == 8:
             return 8.0 * (2.5 + d) * N
         # coupled correction colour sweep (k_corr2_32): both corrections (all
-        # cells, as neighbours: 8 B), the 2x2 coefficients and residuals of
-        # the updated half (24 B x 1/2), the d half-precision drift-face
-        # arrays of both fields (2 B each), write the updated half of both
-        # corrections; the last black sweep of each iteration also reads and
-        # writes the state (32 B), averaged here over the 2 x sweeps - 1
-        # colour launches (the residual pass does the first red half-sweep)
-        return (8.0 + 12.0 + 4.0 * d + 4.0 + 32.0 / (2 * sweeps - 1)) * N
+        # cells, as neighbours: 8 B), the residuals and exchange Jacobian of
+        # the updated half (float4: 16 B x 1/2), the d half-precision
+        # drift-face arrays of both fields (2 B each), write the updated
+        # half of both corrections; the last black sweep of each iteration
+        # also reads and writes the state (32 B), averaged here over the
+        # 2 x sweeps - 1 colour launches (the residual pass does the first
+        # red half-sweep)
+        return (8.0 + 8.0 + 4.0 * d + 4.0 + 32.0 / (2 * sweeps - 1)) * N
     if kind == "residual" and wbytes == 4:
         # k_resid2_32: f, F, f*, F* (pairs), phi, 2 d float faces; writes the
-        # 2x2 coefficients, the residuals and the red half of both
+        # residuals and exchange Jacobian (float4) and the red half of both
         # corrections
-        return (16.0 + 16.0 + 4.0 + 8.0 * d + 16.0 + 8.0 + 4.0) * N
+        return (16.0 + 16.0 + 4.0 + 8.0 * d + 16.0 + 4.0) * N
     if kind == "advect":
         return 16.0 * N + wbytes * d * N
+    return None
+
+
+def method_bytes(kind, grid, s):
+    """Bytes one launch of `kind` must move by the per-pass minimum of the
+    method's measurement plan, independent of this design's work arrays
+    (s = 4 for the FP32 form, 8 for FP64; N cells, d dimensions):
+      a smoother sweep of one field reads its iterate, the right-hand side,
+        the coupling field and phi and writes the iterate: 5 s N; a colour
+        launch of the coupled two-field sweep does half a sweep of both
+        fields: 5 s N; an FP64 colour sweep of one field: 2.5 s N;
+      a residual evaluation of one field: 5 s N (the FP32 pass evaluates
+        both: 10 s N);
+      advection of f and F: read both and the d face velocities, write
+        both: (4 + d) s N;
+      totals of f and F: 2 s N; EOS and Marangoni force: (2 + d) s N."""
+    N, d = grid.ncell, grid.ndim
+    if kind == "smooth_fine":
+        return (5.0 if s == 4 else 2.5) * s * N
+    if kind == "residual":
+        return (10.0 if s == 4 else 5.0) * s * N
+    if kind == "advect":
+        return (4.0 + d) * s * N
+    if kind == "totals":
+        return 2.0 * s * N
+    if kind == "forces":
+        return (2.0 + d) * s * N
     return None
 
 
@@ -234,19 +264,43 @@ def sample_block(case, n_s=SAMPLE_N):
             np.ascontiguousarray(case.uz[s1, s, s]))
 
 
-def oracle_rate(case, steps, tol):
-    """The FP64 CPU oracle, as it stands, on a bounded sample (single thread)."""
+def oracle_rate(case, steps, tol, openmp=False):
+    """The FP64 CPU oracle, as it stands, on a bounded sample: the serial
+    build (one thread) or the OpenMP build (its order-independent loops on
+    every host core; the Gauss-Seidel sweeps stay serial).  Returns the
+    rate, the seconds, the sample grid and the threads used."""
     import oracle
-    g, Cs, ux, uy, uz = sample_block(case)
-    p = case.params
-    _, phi, _ = oracle.phase_field_build(g, Cs, case.redist_iters, case.dtau, p.eps)
-    f, F = np.zeros(g.shape), np.ones(g.shape)
-    t0 = time.perf_counter()
-    for _ in range(steps):
-        f, F, st = oracle.surfactant_step(g, p, phi, f, F, case.dt, tol, ux, uy, uz)
-        oracle.marangoni(g, p, f, phi, Cs, 1)
-    dt = time.perf_counter() - t0
-    return g.ncell * steps / dt, dt, g
+    oracle.use_openmp(openmp)
+    try:
+        g, Cs, ux, uy, uz = sample_block(case)
+        p = case.params
+        _, phi, _ = oracle.phase_field_build(g, Cs, case.redist_iters, case.dtau, p.eps)
+        f, F = np.zeros(g.shape), np.ones(g.shape)
+        t0 = time.perf_counter()
+        for _ in range(steps):
+            f, F, st = oracle.surfactant_step(g, p, phi, f, F, case.dt, tol, ux, uy, uz)
+            oracle.marangoni(g, p, f, phi, Cs, 1)
+        dt = time.perf_counter() - t0
+        return g.ncell * steps / dt, dt, g, oracle.threads()
+    finally:
+        oracle.use_openmp(False)
+
+
+def cpu_legs(case, steps, tol):
+    """cpu_baseline: the OpenMP oracle over all host cores, with the
+    single-thread oracle beside it (same sample)."""
+    sample = "%d step(s) on the centred %d^3 block of the %d^3 workload (same h, dt, flow)" % (
+        steps, SAMPLE_N, case.grid.nx)
+    r1, s1, _, _ = oracle_rate(case, steps, tol, openmp=False)
+    try:
+        rn, sn, _, th = oracle_rate(case, steps, tol, openmp=True)
+    except (OSError, subprocess.CalledProcessError) as e:   # no OpenMP toolchain
+        return {"value": r1, "unit": UNIT, "cores": 1, "kind": "oracle",
+                "sample": "%s: %.1f s" % (sample, s1),
+                "openmp": "unavailable: %s" % str(e).splitlines()[0]}
+    return {"value": rn, "unit": UNIT, "cores": th, "kind": "oracle",
+            "sample": "%s, OpenMP build, %d threads: %.1f s" % (sample, th, sn),
+            "single_thread": {"value": r1, "unit": UNIT, "cores": 1, "seconds": s1}}
 
 
 # ------------------------------------------------------------------ arms
@@ -254,6 +308,12 @@ def run_reference(a, case, rank):
     if rank != 0:
         return
     import oracle
+    try:
+        oracle.build(openmp=True)
+        oracle.use_openmp(True)
+    except (OSError, subprocess.CalledProcessError):
+        oracle.use_openmp(False)          # no OpenMP toolchain: the serial build
+    threads = oracle.threads()
     g, Cs, ux, uy, uz = sample_block(case)
     p = case.params
     _, phi, _ = oracle.phase_field_build(g, Cs, case.redist_iters, case.dtau, p.eps)
@@ -267,8 +327,8 @@ def run_reference(a, case, rank):
             times.append(time.perf_counter() - t0)
     tot = sum(times)
     value = g.ncell * a.steps / tot
-    sample = "centred %d^3 block of the %d^3 workload (same h, dt, flow), 1 thread" % (
-        SAMPLE_N, case.grid.nx)
+    sample = "centred %d^3 block of the %d^3 workload (same h, dt, flow), %d thread(s)%s" % (
+        SAMPLE_N, case.grid.nx, threads, ", OpenMP build" if threads > 1 else "")
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": a.gpus,
         "steps": a.steps, "warmup": a.warmup, "ms_per_step": 1e3 * tot / a.steps,
@@ -276,7 +336,7 @@ def run_reference(a, case, rank):
         "data": "synthetic",
         "config": {"workload": case.name + " (oracle sample)", "sample": sample,
                    "tol": a.tol},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
                          "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }))
@@ -443,36 +503,62 @@ def run_gpu(a, case, rank, world, local_rank):
                                      for k, *_, cv in timed)
         working["residual"] = sum(k for k, *_ in timed)
     ab = algorithmic_bytes(kind, g, wbytes, sw)
+    mb = method_bytes(kind, g, wbytes)
     nwork = working.get(kind, nt)
-    if ab is not None and nwork > 0:
+    if mb is not None and nwork > 0:
         avg_s = tot_ms * 1e-3 / nwork
-        achieved = ab / avg_s / 1e9
+        achieved = mb / avg_s / 1e9
         traffic, tsrc = ncu_traffic(kind, a.precision, g.ndim, g.ncell)
         roof = {"bound": "hbm", "kernel": kind, "achieved": achieved, "peak": peaks["hbm_gbs"],
                 "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"], "traffic": traffic,
                 "traffic_source": tsrc,
-                "algorithmic_bytes_per_launch": ab, "avg_launch_ms": avg_s * 1e3,
-                "working_launches": nwork, "launches": nl,
-                "peak_source": "%s (MEASURED_PEAKS.json hbm_gbs)" % peak_src}
+                "algorithmic_bytes_per_launch": mb,
+                "algorithmic_bytes_note": "the method's per-pass minimum (5 s per cell per "
+                                          "field and sweep, s = %d), not this design's work "
+                                          "arrays" % wbytes,
+                "avg_launch_ms": avg_s * 1e3, "working_launches": nwork, "launches": nl,
+                "peak_source": "%s (MEASURED_PEAKS.json hbm_gbs)" % peak_src,
+                "per_kernel": True}
+        if ab is not None:
+            roof["design_bytes_per_launch"] = ab
+            roof["design_bytes_achieved"] = ab / avg_s / 1e9
+            roof["design_bytes_frac"] = ab / avg_s / 1e9 / peaks["hbm_gbs"]
     launches = int(sum(v[0] for v in prof.values()))
     breakdown = {}
+    step_method, step_design = 0.0, 0.0
     for k, v in prof.items():
         if not v[0]:
             continue
         e = {"launches": v[0], "ms": round(v[1], 3)}
         b = algorithmic_bytes(k, g, wbytes, sw)
+        m = method_bytes(k, g, wbytes)
         nw = working.get(k, v[2])
         if k in working:
             e["working_launches"] = nw
+        if k in ("totals", "forces"):
+            nw_m = a.steps            # one pass per step, whatever the launch count
+        else:
+            nw_m = nw
+        if m is not None and nw > 0:
+            e["method_gbs"] = round(m / (v[1] * 1e-3 / nw) / 1e9, 1)
+            step_method += m * nw_m
         if b is not None and nw > 0:
-            e["gbs"] = round(b / (v[1] * 1e-3 / nw) / 1e9, 1)
+            e["design_gbs"] = round(b / (v[1] * 1e-3 / nw) / 1e9, 1)
+            step_design += b * nw
         breakdown[k] = e
+    step_s = ms_max * 1e-3
+    step_level = {
+        "method_bytes_per_step": step_method / a.steps,
+        "method_frac": step_method / step_s / 1e9 / peaks["hbm_gbs"],
+        "design_bytes_per_step": step_design / a.steps,
+        "design_frac": step_design / step_s / 1e9 / peaks["hbm_gbs"],
+        "note": "bytes of every pass of the timed steps (advection, residual passes, colour "
+                "sweeps that did work, totals, EOS and force) over the whole step time; "
+                "method = the per-pass minimum, design = this design's arrays (the kinds "
+                "without a figure, e.g. set-up and flags, count as time only)"}
     cpu = None
     if not a.no_cpu:
-        rate, secs, gs = oracle_rate(case, a.oracle_steps, a.tol)
-        cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": "%d step(s) on the centred %d^3 block of the %d^3 workload "
-                         "(same h, dt, flow): %.1f s" % (a.oracle_steps, SAMPLE_N, g.nx, secs)}
+        cpu = cpu_legs(case, a.oracle_steps, a.tol)
     pic = [s[0] for s in stats[-a.steps:]]
     f64 = None
     if prec == sfx.SFX_F32 and a.f64_steps > 0:
@@ -491,6 +577,9 @@ def run_gpu(a, case, rank, world, local_rank):
     kin = None
     if a.kinetics_steps > 0:
         kin = kinetics_sweep_run(a, dev, a.kinetics_steps)
+    ads = None
+    if a.adsorption_steps > 0:
+        ads = adsorption_run(a, dev, a.adsorption_steps)
     if roof is not None:
         roof["frac_of_nominal"] = roof["achieved"] / NOMINAL_HBM_GBS
         roof["nominal_peak"] = NOMINAL_HBM_GBS
@@ -514,7 +603,8 @@ def run_gpu(a, case, rank, world, local_rank):
                        g.ncell * 8 * 20 / 1e9),
                    "parallelism": "replicas%d" % world,
                    "picard_per_step": statistics.mean(pic) if pic else None},
-        "roofline": roof, "state_only_roofline": state_only, "cpu_baseline": cpu, "e2e": e2e,
+        "roofline": roof, "step_roofline": step_level, "state_only_roofline": state_only,
+        "cpu_baseline": cpu, "e2e": e2e,
         "gpu_launches": launches,
         "clocks": clocks, "kernels": breakdown,
     }
@@ -529,7 +619,52 @@ def run_gpu(a, case, rank, world, local_rank):
         line["vortex512"] = vortex
     if kin is not None:
         line["kinetics_sweep"] = kin
+    if ads is not None:
+        line["adsorption2d_128"] = ads
     print(json.dumps(line))
+
+
+def adsorption_run(a, dev, steps, warmup=3):
+    """The 2D planar no-flow adsorption workload in FP64 as specified: 128^2
+    unit box, circle R = 0.25, phase-field width 1.5 cells, F = 1 outside and
+    0 inside, clean interface, Langmuir k_a = 1, k_d = 0.1, D = 1e-2,
+    multigrid to residual 1e-10, dt = 1e-3, `steps` steps (1000: t = 1)
+    timed as one run (latency-bound: 16 k cells).  Reports the interface
+    average Gamma = sum V f / sum V delta_phi at the end and the total."""
+    import torch
+    import paper_2605_27534_gb300 as sfx
+    c = W.case_adsorption_2d(n=128, steps=steps, tol=1e-10)
+    g, p = c.grid, c.params
+    ctx = sfx.Context.for_grid(g, sfx.SFX_F64)
+    Cd = torch.from_numpy(c.C).to(dev)
+    chi, phi, delta = torch.empty_like(Cd), torch.empty_like(Cd), torch.empty_like(Cd)
+    ctx.sfx_phase_field_build(Cd, chi, phi, delta, iters=c.redist_iters, dtau=c.dtau, eps=p.eps)
+    F0 = torch.from_numpy(c.F0).to(dev)
+    f, F = torch.zeros_like(F0), F0.clone()
+    opts = sfx.default_opts(tol=1e-10, max_cycles=200)
+    M0 = sum(ctx.sfx_totals([f, F]))
+    for _ in range(warmup):                      # warm-up on a scratch copy
+        ff, FF = f.clone(), F.clone()
+        ctx.sfx_surfactant_step(p, phi, ff, FF, c.dt, opts=opts)
+    pic, conv = [], True
+    stream = torch.cuda.current_stream()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        st = ctx.sfx_surfactant_step(p, phi, f, F, c.dt, opts=opts)
+        pic.append(st.picard)
+        conv = conv and bool(st.converged)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    mf, mF = ctx.sfx_totals([f, F])
+    md = ctx.sfx_totals([delta])[0]
+    return {"ms_total": ms, "ms_per_step": ms / steps, "value": g.ncell * steps / (ms * 1e-3),
+            "unit": UNIT, "steps": steps, "cells": g.ncell, "dtype": "f64",
+            "picard_per_step": statistics.mean(pic), "all_converged": conv,
+            "t_end": steps * c.dt, "gamma_mean_end": mf / md,
+            "mass_rel_drift": (mf + mF - M0) / M0}
 
 
 def kinetics_sweep_run(a, dev, steps, n_inst=512, ny=256, nx=8, warmup=3):
@@ -599,6 +734,8 @@ def vortex_run(a, dev, steps, prec, warmup=3, rebuild_every=1):
     f32 = prec == sfx.SFX_F32
     vt = torch.float32 if f32 else torch.float64
     ctx = sfx.Context.for_grid(g, prec)
+    if f32:   # the phase field is rebuilt every step: FP32 redistancing (fused 2D kernel)
+        ctx.sfx_set_tuning(sfx._lib.SFX_TUNE_F32_REDIST, 1)
     u0h = W.single_vortex_faces(512, g.h, 0.0, T)
     umax0 = max(float(np.abs(x).max()) for x in u0h)
     u0 = [torch.from_numpy(x).to(dev, vt) for x in u0h]

@@ -130,9 +130,9 @@ void sfx_default_opts(sfx_solve_opts* opts);
    redistancing d chi/d tau + sign(chi0)(|grad chi| - 1) = 0 (first-order
    Godunov with the Russo-Smereka sub-cell fix) at pseudo-time step dtau,
    then phi = (1 - tanh(chi/(2 eps)))/2 and delta = phi (1 - phi)/eps.
-   C, chi, phi, delta: double, in both precisions; SFX_F32 contexts iterate
-   the redistancing in FP32 (chi within ~1e-7 h of the FP64 iterate).
-   delta may be NULL. */
+   C, chi, phi, delta: double, in both precisions; the iterations are FP64
+   unless an SFX_F32 context sets SFX_TUNE_F32_REDIST (FP32 iterate, chi
+   within ~1e-7 h of the FP64 one).  delta may be NULL. */
 sfx_status sfx_phase_field_build(sfx_ctx* ctx, const double* C, double* chi,
                                  void* phi, void* delta, int iters,
                                  double dtau, double eps, void* stream);
@@ -329,6 +329,16 @@ typedef enum {
                                writing phi in place, set the knob again to
                                force a rebuild); 0 (default) = rebuild them
                                every step. */
+  SFX_TUNE_F32_REDIST = 4,  /* SFX_F32: 1 = iterate the redistancing of
+                               sfx_phase_field_build in FP32 (2D: eight
+                               Jacobi steps per launch in shared memory);
+                               chi within ~1e-7 h of the FP64 iterate, but
+                               where |grad chi| is small (the front of the
+                               redistanced band) the direction of grad phi,
+                               and with it the drift, follows chi's float
+                               rounding: with F = 1 inside a 256^3 sphere
+                               the step then moves by 5e-5.  0 (default) =
+                               FP64 redistancing as in SFX_F64 contexts. */
   SFX_TUNE_PREDICT = 3      /* SFX_F32 Newton solver: 1 (default) = start
                                the iteration from x* plus the previous
                                step's implicit increment x - x* when the

@@ -20,19 +20,39 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "sfx_oracle.c")
 _BUILD = os.path.join(_HERE, "_build")
 _SO = os.path.join(_BUILD, "liboracle.so")
+_SO_OMP = os.path.join(_BUILD, "liboracle_omp.so")
 
 
-def build(force: bool = False) -> str:
-    """Compile the oracle with gcc (plain -O2, no FMA contraction)."""
+def _compile(out, extra):
+    tmp = out + ".%d.tmp" % os.getpid()
+    subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-fPIC", "-shared", "-std=c99",
+                           *extra, "-o", tmp, _SRC, "-lm"])
+    os.replace(tmp, out)
+
+
+def build(force: bool = False, openmp: bool = False) -> str:
+    """Compile the oracle with gcc (plain -O2, no FMA contraction).  With
+    openmp=True the same source with -fopenmp: its order-independent loops
+    (operator applications, residual maxima, coefficients, advection,
+    normals) run on all host cores; the Gauss-Seidel sweeps stay serial, so
+    every result is bitwise the serial one."""
     os.makedirs(_BUILD, exist_ok=True)
-    stale = (not os.path.exists(_SO)) or os.path.getmtime(_SO) < max(
+    so = _SO_OMP if openmp else _SO
+    stale = (not os.path.exists(so)) or os.path.getmtime(so) < max(
         os.path.getmtime(_SRC), os.path.getmtime(os.path.join(_HERE, "sfx_oracle.h")))
     if force or stale:
-        tmp = _SO + ".%d.tmp" % os.getpid()
-        subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-fPIC", "-shared",
-                               "-std=c99", "-o", tmp, _SRC, "-lm"])
-        os.replace(tmp, _SO)
-    return _SO
+        _compile(so, ["-fopenmp"] if openmp else [])
+    return so
+
+
+_use_openmp = False
+
+
+def use_openmp(on: bool) -> None:
+    """Route the calls below to the OpenMP build (threads: OMP_NUM_THREADS,
+    else every host core) or back to the serial one."""
+    global _use_openmp
+    _use_openmp = bool(on)
 
 
 class Grid(C.Structure):
@@ -58,15 +78,17 @@ class Stats(C.Structure):
                 ("mass_F", C.c_double), ("converged", C.c_int)]
 
 
-_lib = None
+_libs = {}
 _P = C.POINTER(C.c_double)
 
 
 def lib():
-    global _lib
-    if _lib is None:
-        L = C.CDLL(build())
+    key = bool(_use_openmp)
+    if key not in _libs:
+        L = C.CDLL(build(openmp=key))
         G, Pp = C.POINTER(Grid), C.POINTER(Params)
+        L.orc_threads.restype = C.c_int
+        L.orc_threads.argtypes = []
         L.orc_cell_volume.restype = C.c_double
         L.orc_cell_volume.argtypes = [G, C.c_int, C.c_int, C.c_int]
         L.orc_redistance.argtypes = [G, _P, C.c_int, C.c_double, _P]
@@ -100,8 +122,8 @@ def lib():
         L.orc_cfl_dt.restype = C.c_double
         L.orc_cfl_dt.argtypes = [C.c_int, C.c_double, C.c_double, C.c_double, C.c_double,
                                  C.c_double]
-        _lib = L
-    return _lib
+        _libs[key] = L
+    return _libs[key]
 
 
 # ------------------------------------------------------------ helpers
@@ -131,6 +153,11 @@ def _face_shapes(g):
 
 
 # ------------------------------------------------------------ API
+def threads():
+    """Threads of the build in use (1 for the serial oracle)."""
+    return int(lib().orc_threads())
+
+
 def cell_volumes(g):
     L, G = lib(), cgrid(g)
     V = np.empty((g.nz, g.ny, g.nx))

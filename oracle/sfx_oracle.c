@@ -10,6 +10,9 @@
  * Readings of points the paper leaves open are marked READING and listed in
  * the design notes of the repository.
  */
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 #include "sfx_oracle.h"
 
 #include <math.h>
@@ -33,6 +36,15 @@ static int extent(const orc_grid* g, int d) {
 
 /* Cell volume: h^2 (planar, unit depth), h^3 (3D), and the exact ring
    volume pi (r+^2 - r-^2) dz of App. B with r- = i h, r+ = (i+1) h. */
+/* threads the order-independent loops run on (1 in the serial build) */
+int orc_threads(void) {
+#ifdef _OPENMP
+  return omp_get_max_threads();
+#else
+  return 1;
+#endif
+}
+
 double orc_cell_volume(const orc_grid* g, int i, int j, int k) {
   (void)j; (void)k;
   double h = g->h;
@@ -193,6 +205,7 @@ void orc_phase_field_build(const orc_grid* g, const double* C, int iters,
 void orc_normals(const orc_grid* g, const double* phi, double eps, double* n) {
   size_t N = ncell_of(g);
   int D = ndim_of(g);
+#pragma omp parallel for collapse(2)
   for (int k = 0; k < g->nz; ++k)
     for (int j = 0; j < g->ny; ++j)
       for (int i = 0; i < g->nx; ++i) {
@@ -307,6 +320,7 @@ static void cell_operator(const orc_grid* g, double D, const double* Bx,
 void orc_apply_operator(const orc_grid* g, double D, const double* Bx,
                         const double* By, const double* Bz, int literal_upwind,
                         const double* lambda, const double* a, double* out) {
+#pragma omp parallel for collapse(2)
   for (int k = 0; k < g->nz; ++k)
     for (int j = 0; j < g->ny; ++j)
       for (int i = 0; i < g->nx; ++i) {
@@ -322,6 +336,10 @@ static double rel_residual(const orc_grid* g, double D, const double* Bx,
                            const double* lambda, const double* b,
                            const double* a) {
   double rmax = 0.0, bmax = 0.0;
+  int nan = 0;
+  /* the maxima do not depend on the order: the OpenMP build of the oracle
+     (a CPU baseline over all host cores) gives the same value */
+#pragma omp parallel for collapse(2) reduction(max : rmax, bmax) reduction(| : nan)
   for (int k = 0; k < g->nz; ++k)
     for (int j = 0; j < g->ny; ++j)
       for (int i = 0; i < g->nx; ++i) {
@@ -329,9 +347,11 @@ static double rel_residual(const orc_grid* g, double D, const double* Bx,
         double Lc, dg;
         cell_operator(g, D, Bx, By, Bz, literal, lambda, a, i, j, k, &Lc, &dg);
         double r = fabs(b[c] - Lc);
-        if (r > rmax || r != r) rmax = r;
+        if (r != r) nan = 1;
+        else if (r > rmax) rmax = r;
         if (fabs(b[c]) > bmax) bmax = fabs(b[c]);
       }
+  if (nan) return NAN;
   return rmax / (bmax > 1e-300 ? bmax : 1e-300);
 }
 
@@ -424,6 +444,7 @@ static double bcg_face_value(const orc_grid* g, const double* ux,
 void orc_advect_bcg(const orc_grid* g, const double* ux, const double* uy,
                     const double* uz, double dt, const double* xi,
                     double bc_in, double* xi_star) {
+#pragma omp parallel for collapse(2)
   for (int k = 0; k < g->nz; ++k)
     for (int j = 0; j < g->ny; ++j)
       for (int i = 0; i < g->nx; ++i) {
@@ -490,6 +511,7 @@ static void coupled_ws_free(coupled_ws* w) {
 static void f_problem(const orc_grid* g, const orc_params* p, coupled_ws* w,
                       const double* fstar, const double* F, double dt) {
   size_t N = ncell_of(g);
+#pragma omp parallel for
   for (size_t c = 0; c < N; ++c) {
     double Fs = F[c] / w->pe[c];
     w->lam[c] = 1.0 / dt + p->kd + p->ka * Fs;
@@ -502,6 +524,7 @@ static void f_problem(const orc_grid* g, const orc_params* p, coupled_ws* w,
 static void F_problem(const orc_grid* g, const orc_params* p, coupled_ws* w,
                       const double* Fstar, const double* f, double dt) {
   size_t N = ncell_of(g);
+#pragma omp parallel for
   for (size_t c = 0; c < N; ++c) {
     w->lam[c] = 1.0 / dt + p->ka * (w->finf[c] - f[c]) / w->pe[c];
     w->rhs[c] = Fstar[c] / dt + p->kd * f[c];

@@ -62,6 +62,9 @@ typedef struct {
   int converged;
 } orc_stats;
 
+/* threads of the build: omp_get_max_threads() in the OpenMP build, else 1 */
+int orc_threads(void);
+
 /* cell volume and face areas (Sec. 3.2, App. A, App. B) */
 double orc_cell_volume(const orc_grid* g, int i, int j, int k);
 

@@ -51,8 +51,7 @@ struct BPtr {
   float2* Fs;
   float2* B2[2];          // radial, axial drift faces (B_f, B_F)
   __half2* H2[2];         // (B_f, B_F) in half precision (correction sweeps)
-  float4* coef;
-  float2* res;
+  float4* rc;             // r_f, r_F, u = c1 F, v = c1 (f_inf - f) per cell (colour-packed)
   float2* e2;             // Newton corrections (e_f, e_F), colour-packed
   unsigned int* norms;    // 4 per instance
   int* active;
@@ -149,7 +148,7 @@ __global__ void k_b_resid(const BInst* __restrict__ I, int n, const int* __restr
     const float2* B2[3] = {P.B2[0] + B.rfoff, P.B2[1] + B.zfoff, nullptr};
     const size_t o = B.coff, w = B.poff;
     resid2_cell<G>(B.p, i, j, 0, c, P.phi32 + o, B2, P.f + o, P.F + o, P.fs + o, P.Fs + o,
-                P.coef + w, P.res + w, m, P.e2 + w);
+                P.rc + w, m, P.e2 + w);
   }
   // block maxima; the flags kernel combines the blocks of each instance
   __shared__ float wm[4][16];
@@ -238,7 +237,7 @@ __global__ void k_b_corr(const BInst* __restrict__ I, int n, const int* __restri
     return;
   }
   const __half2* H[3] = {P.H2[0] + B.rfoff, P.H2[1] + B.zfoff, nullptr};
-  corr2_cell<G>(B.p, i, j, 0, H, P.coef + w, P.res + w, P.e2 + w, color, first, fst, Fst);
+  corr2_cell<G>(B.p, i, j, 0, H, P.rc + w, P.e2 + w, color, first, fst, Fst);
 }
 
 // per-instance compensated totals: kTotBlocks blocks per instance each walk
@@ -548,8 +547,7 @@ sfx_status sfx_batch_create_geom(const sfx_batch_instance* inst, int n, int geom
   if (st == SFX_OK) st = balloc(b, &P.B2[1], b->nzf);
   if (st == SFX_OK) st = balloc(b, &P.H2[0], b->nrf);
   if (st == SFX_OK) st = balloc(b, &P.H2[1], b->nzf);
-  if (st == SFX_OK) st = balloc(b, &P.coef, b->npack);
-  if (st == SFX_OK) st = balloc(b, &P.res, b->npack);
+  if (st == SFX_OK) st = balloc(b, &P.rc, b->npack);
   if (st == SFX_OK) st = balloc(b, &P.e2, b->npack);
   if (st == SFX_OK) st = balloc(b, &P.norms, 4 * (size_t)n);
   if (st == SFX_OK) st = balloc(b, &P.active, (size_t)n);

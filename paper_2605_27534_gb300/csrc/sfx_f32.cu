@@ -296,8 +296,8 @@ k_resid2_32(Nw32 p, const float* __restrict__ phi, const float2* __restrict__ B2
             const float2* __restrict__ B2y, const float2* __restrict__ B2z,
             const float2* __restrict__ fin,
             const float2* __restrict__ Fin, const float2* __restrict__ fst,
-            const float2* __restrict__ Fst, float4* __restrict__ coef,
-            float2* __restrict__ res, unsigned int* norms, float2* __restrict__ e2,
+            const float2* __restrict__ Fst, float4* __restrict__ rc,
+            unsigned int* norms, float2* __restrict__ e2,
             const int* __restrict__ done) {
   if (done && *done) return;   // converged at an earlier iteration
   const Level& L = p.L;
@@ -309,7 +309,7 @@ k_resid2_32(Nw32 p, const float* __restrict__ phi, const float2* __restrict__ B2
   for (ix r = blockIdx.y; r < rows; r += gridDim.y) {
     const int j = (int)(r % (ix)L.ny), k = (int)(r / (ix)L.ny);
     if (i < L.nx)
-      resid2_cell<G>(p, i, j, k, r * (ix)L.nx + (ix)i, phi, B2, fin, Fin, fst, Fst, coef, res, m, e2);
+      resid2_cell<G>(p, i, j, k, r * (ix)L.nx + (ix)i, phi, B2, fin, Fin, fst, Fst, rc, m, e2);
   }
   if (norms) {
     // warp maxima, then one atomic per block and norm
@@ -332,8 +332,8 @@ k_resid2_32(Nw32 p, const float* __restrict__ phi, const float2* __restrict__ B2
 template <int G>
 __global__ void __launch_bounds__(128, 10)
 k_corr2_32(Nw32 p, const __half2* __restrict__ Hx, const __half2* __restrict__ Hy,
-           const __half2* __restrict__ Hz, const float4* __restrict__ coef,
-           const float2* __restrict__ res, float2* __restrict__ e2, int color, int first,
+           const __half2* __restrict__ Hz, const float4* __restrict__ rc,
+           float2* __restrict__ e2, int color, int first,
            float2* __restrict__ fst, float2* __restrict__ Fst, const int* __restrict__ done) {
   if (done && *done) return;
   const Level& L = p.L;
@@ -353,7 +353,7 @@ k_corr2_32(Nw32 p, const __half2* __restrict__ Hx, const __half2* __restrict__ H
     }
     return;
   }
-  corr2_cell<G>(p, i, j, k, H, coef, res, e2, color, first, fst, Fst);
+  corr2_cell<G>(p, i, j, k, H, rc, e2, color, first, fst, Fst);
 }
 
 // The Newton kernels of one geometry (the branches on the geometry in the
@@ -1253,7 +1253,7 @@ sfx_status solve_newton32(sfx_ctx* c, const Nw32& p, const float* phi, float* co
     unsigned int* nbuf = dn + 4 * (it & 1);
     SFX_CUDA(cudaMemsetAsync(nbuf, 0, 4 * sizeof(unsigned int), s));
     SFX_KERNEL(c, K_RESIDUAL, nk.resid, rg.grid, rg.block, s, p, phi, B2[0], B2[1], B2[2], fc,
-               Fc, fs, Fs, c->f32.coef, c->f32.res, nbuf, c->f32.e2, flag);
+               Fc, fs, Fs, c->f32.rc, nbuf, c->f32.e2, flag);
     if (it == 1 && predicted) {
       // keep the predicted start only if its residual is already small;
       // otherwise restart from x* (both launches return at once when kept)
@@ -1262,7 +1262,7 @@ sfx_status solve_newton32(sfx_ctx* c, const Nw32& p, const float* phi, float* co
       SFX_KERNEL(c, K_OTHER, k_pred_check32, 1, 32, s, nbuf, rho, ok);
       SFX_KERNEL(c, K_SETUP, k_restore32, nb, 256, s, n, ok, fs, Fs, fc, Fc);
       SFX_KERNEL(c, K_RESIDUAL, nk.resid, rg.grid, rg.block, s, p, phi, B2[0], B2[1], B2[2],
-                 fc, Fc, fs, Fs, c->f32.coef, c->f32.res, nbuf, c->f32.e2, ok);
+                 fc, Fc, fs, Fs, c->f32.rc, nbuf, c->f32.e2, ok);
     }
     SFX_KERNEL(c, K_OTHER, k_flag32, 1, 32, s, nbuf, tolf, it, flag);
     SFX_CUDA(cudaMemcpyAsync(hn + 4 * (it & 1), nbuf, 4 * sizeof(unsigned int),
@@ -1272,7 +1272,7 @@ sfx_status solve_newton32(sfx_ctx* c, const Nw32& p, const float* phi, float* co
       for (int color = (q == 0 ? 1 : 0); color < 2; ++color) {
         const bool apply = q == sweeps - 1 && color == 1;
         SFX_KERNEL(c, K_SMOOTH_FINE, nk.corr, grd, blk, s, p, c->f32.H2[0], c->f32.H2[1], Hz,
-                   c->f32.coef, c->f32.res, c->f32.e2, color, q == 0 ? 1 : 0,
+                   c->f32.rc, c->f32.e2, color, q == 0 ? 1 : 0,
                    apply ? fc : nullptr, apply ? Fc : nullptr, flag);
       }
     SFX_LAUNCH_CHECK();
@@ -1561,8 +1561,7 @@ sfx_status f32_ensure_scratch(sfx_ctx* c) {
   for (float** q : arrs)
     if ((st = get(np * sizeof(float), (void**)q)) != SFX_OK) return st;
   if ((st = get(np * sizeof(float2), (void**)&c->f32.e2)) != SFX_OK) return st;
-  if ((st = get(np * sizeof(float4), (void**)&c->f32.coef)) != SFX_OK) return st;
-  if ((st = get(np * sizeof(float2), (void**)&c->f32.res)) != SFX_OK) return st;
+  if ((st = get(np * sizeof(float4), (void**)&c->f32.rc)) != SFX_OK) return st;
   for (int q = 0; q < 2; ++q) SFX_CUDA(cudaEventCreateWithFlags(&c->f32.ev[q], cudaEventDisableTiming));
   c->f32.ready = true;
   return SFX_OK;

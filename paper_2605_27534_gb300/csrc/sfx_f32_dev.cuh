@@ -404,6 +404,19 @@ __device__ __forceinline__ void face32v2(const Adv32& A, const float2* __restric
 // half-sweep of the correction is done here: it starts from zero
 // corrections, so a red cell (i + j + k even) only needs its own 2x2 block,
 // e = M_c^-1 r_c.
+// Kinetic part of the pointwise 2x2 Jacobian of the App. C exchange at one
+// cell, from u = c1 F and v = c1 (f_inf - f) (c1 = r_a/(phi + eta)):
+//   [ff  -fF] = [1/dt + r_d + u    -v      ]
+//   [-Ff  FF]   [-(u + r_d)        1/dt + v]
+// (the flux operators add their diagonal weights to ff and FF).
+struct Jac2 {
+  float ff, fF, Ff, FF;
+};
+__device__ __forceinline__ Jac2 jac2(const Nw32& p, float u, float v) {
+  return Jac2{__fadd_rn(__fadd_rn(p.inv_dt, p.kd), u), v, __fadd_rn(u, p.kd),
+              __fadd_rn(p.inv_dt, v)};
+}
+
 template <int G>
 __device__ __forceinline__ void resid2_cell(const Nw32& p, int i, int j, int k, ix c,
                                             const float* __restrict__ phi,
@@ -412,8 +425,8 @@ __device__ __forceinline__ void resid2_cell(const Nw32& p, int i, int j, int k, 
                                             const float2* __restrict__ Fin,
                                             const float2* __restrict__ fst,
                                             const float2* __restrict__ Fst,
-                                            float4* __restrict__ coef, float2* __restrict__ res,
-                                            float* m, float2* __restrict__ e2) {
+                                            float4* __restrict__ rc, float* m,
+                                            float2* __restrict__ e2) {
   const Level& L = p.L;
   bool has[6];
   ix nbi[6];
@@ -451,21 +464,19 @@ __device__ __forceinline__ void resid2_cell(const Nw32& p, int i, int j, int k, 
   acc_sub(RF, qq);
   const float rf = __fadd_rn(Rf.hi, Rf.lo), rF = __fadd_rn(RF.hi, RF.lo);
   const float Fv = __fadd_rn(Fc.x, Fc.y), fv = __fadd_rn(fc.x, fc.y);
-  // diagonals (kinetic part) and couplings of the linearised system
-  const float xf = __fsub_rn(finf, fv);
-  const float4 cf = make_float4(__fmaf_rn(c1, Fv, __fadd_rn(p.inv_dt, p.kd)),
-                                __fmaf_rn(c1, xf, p.inv_dt), __fmul_rn(c1, xf),
-                                __fmaf_rn(c1, Fv, p.kd));
+  // the linearised exchange: u = c1 F and v = c1 (f_inf - f) fix the 2x2
+  // block (Jac2); stored with the residuals as one float4 per cell
+  const float u = __fmul_rn(c1, Fv), v = __fmul_rn(c1, __fsub_rn(finf, fv));
   const RBIdx rb = rb_index(L, i, j, k);
   const ix own = (ix)((i + j + k) & 1) * rb.plane + rb.pos;
-  coef[own] = cf;
-  res[own] = make_float2(rf, rF);
+  rc[own] = make_float4(rf, rF, u, v);
   if (e2 && ((i + j + k) & 1) == 0) {
     // [a -b; -d e] [x; y] = [r_f; r_F], diagonals with the flux weights
-    const float a = __fadd_rn(cf.x, df_), bb = cf.z, d = cf.w, e = __fadd_rn(cf.y, dF_);
-    const float inv = __fdividef(1.0f, __fmaf_rn(a, e, -__fmul_rn(bb, d)));
-    e2[own] = make_float2(__fmul_rn(__fmaf_rn(e, rf, __fmul_rn(bb, rF)), inv),
-                          __fmul_rn(__fmaf_rn(d, rf, __fmul_rn(a, rF)), inv));
+    const Jac2 J = jac2(p, u, v);
+    const float a = __fadd_rn(J.ff, df_), e = __fadd_rn(J.FF, dF_);
+    const float inv = __fdividef(1.0f, __fmaf_rn(a, e, -__fmul_rn(J.fF, J.Ff)));
+    e2[own] = make_float2(__fmul_rn(__fmaf_rn(e, rf, __fmul_rn(J.fF, rF)), inv),
+                          __fmul_rn(__fmaf_rn(J.Ff, rf, __fmul_rn(a, rF)), inv));
   }
   m[0] = fmaxf(m[0], fabsf(rf));
   m[1] = fmaxf(m[1], fabsf(__fmaf_rn(fs.x, p.inv_dt, __fmul_rn(__fmul_rn(c1, Fv), finf))));
@@ -483,8 +494,7 @@ __device__ __forceinline__ void resid2_cell(const Nw32& p, int i, int j, int k, 
 template <int G>
 __device__ __forceinline__ void corr2_cell(const Nw32& p, int i, int j, int k,
                                            const __half2* const* H,
-                                           const float4* __restrict__ coef,
-                                           const float2* __restrict__ res,
+                                           const float4* __restrict__ rc,
                                            float2* __restrict__ e2, int color, int first,
                                            float2* __restrict__ fst, float2* __restrict__ Fst) {
   // the other colour's corrections are only read in this launch: read them
@@ -521,15 +531,15 @@ __device__ __forceinline__ void corr2_cell(const Nw32& p, int i, int j, int k,
   faces6x2(L, H[0], H[1], H[2], i, j, k, has, Bf, BF);
   const float flf = flux_lin<G>(L, p.invh, p.Dfh, p.literal, i, efc, enf, has, Bf, dgf);
   const float flF = flux_lin<G>(L, p.invh, p.DFh, p.literal, i, eFc, enF, has, BF, dgF);
-  const float4 cf = coef[own];
-  const float2 r = res[own];
+  const float4 q4 = rc[own];
+  const Jac2 J = jac2(p, q4.z, q4.w);
   // residuals of the correction equation at this cell
   // (every rounding is spelled out, so that each kernel that inlines this
   // cell computes the same bits)
-  const float rhof = __fmaf_rn(cf.z, eFc, __fmaf_rn(-cf.x, efc, __fadd_rn(r.x, flf)));
-  const float rhoF = __fmaf_rn(cf.w, efc, __fmaf_rn(-cf.y, eFc, __fadd_rn(r.y, flF)));
+  const float rhof = __fmaf_rn(J.fF, eFc, __fmaf_rn(-J.ff, efc, __fadd_rn(q4.x, flf)));
+  const float rhoF = __fmaf_rn(J.Ff, efc, __fmaf_rn(-J.FF, eFc, __fadd_rn(q4.y, flF)));
   // 2x2 block solve: [a  -b; -d  e] [x; y] = [rhof; rhoF]
-  const float a = __fadd_rn(cf.x, dgf), bb = cf.z, d = cf.w, e = __fadd_rn(cf.y, dgF);
+  const float a = __fadd_rn(J.ff, dgf), bb = J.fF, d = J.Ff, e = __fadd_rn(J.FF, dgF);
   const float det = __fmaf_rn(a, e, -__fmul_rn(bb, d));
   const float inv = __fdividef(1.0f, det);
   const float nf = __fmaf_rn(__fmaf_rn(e, rhof, __fmul_rn(bb, rhoF)), inv, efc);

@@ -54,14 +54,15 @@ struct F32Scratch {
   int zchunk = 32;         // planes per block of the 3D fused sweep
   int solver = 1;          // 0: nonlinear pair sweeps; 1: coupled Newton
                            // defect correction; 2: Picard defect correction
-  float4* coef = nullptr;  // lam_f, lam_F, j_fF, j_Ff of the linearised system
-  float2* res = nullptr;   // r_f, r_F
+  float4* rc = nullptr;    // r_f, r_F and the exchange Jacobian's u = c1 F,
+                           // v = c1 (f_inf - f), colour-packed
   cudaEvent_t ev[2] = {nullptr, nullptr};
   bool reuse_drift = false;         // keep drift faces while phi and D's are unchanged
   const double* drift_phi = nullptr;
   float* phi32 = nullptr;           // folded float copy of phi
   int* flag = nullptr;              // convergence flag, iteration, prediction kept
   bool predict = true;              // start Newton from x* + last increment
+  bool redist32 = false;            // redistance in FP32 (else FP64)
   float predict_rho = 1.0f;         // reject a predicted start above this residual
   bool inc_valid = false;
   float* inc_f = nullptr;           // last step's implicit increments x - x*

@@ -196,7 +196,7 @@ sfx_status phase_field_build(sfx_ctx* c, const double* C, double* chi, void* phi
   const unsigned xb = (unsigned)((L.nx + tx - 1) / tx);
   const long long rows = (long long)L.ny * L.nz;
   const unsigned yb = (unsigned)std::min(rows, std::min(std::max(1LL, 152LL * 8 / xb), 65535LL));
-  if (c->prec == SFX_F32) {
+  if (c->prec == SFX_F32 && c->f32.redist32) {
     if (!c->chi32) {
       SFX_CUDA(cudaMalloc((void**)&c->chi32, 3 * n * sizeof(float)));
       c->allocations.push_back(c->chi32);

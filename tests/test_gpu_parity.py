@@ -75,9 +75,13 @@ def test_phase_field_build_parity(sfx, geom):
     assert rel_err(host(chi), chi_o) < PARITY
     assert rel_err(host(phi), phi_o) < PARITY
     assert rel_err(host(dl), del_o) < PARITY
-    # SFX_F32 contexts iterate the redistancing in FP32
+    # SFX_F32 contexts redistance in FP64 by default (the same bits) ...
     ctx32 = _ctx(sfx, g, 1)
     phi32, chi32 = torch.empty_like(Cd), torch.empty_like(Cd)
+    ctx32.sfx_phase_field_build(Cd, chi32, phi32, None, iters=24, dtau=dtau, eps=eps)
+    assert np.array_equal(host(chi32), host(chi)) and np.array_equal(host(phi32), host(phi))
+    # ... and in FP32 with SFX_TUNE_F32_REDIST
+    ctx32.sfx_set_tuning(sfx._lib.SFX_TUNE_F32_REDIST, 1)
     ctx32.sfx_phase_field_build(Cd, chi32, phi32, None, iters=24, dtau=dtau, eps=eps)
     assert rel_err(host(chi32), chi_o) < 1e-6      # float iterate
     assert np.abs(host(phi32) - phi_o).max() < 5e-6
@@ -94,6 +98,7 @@ def test_fp32_redistancing_step_counts(sfx, geom, iters):
     eps, dtau = 0.75 * g.h, 0.5 * g.h
     chi_o, phi_o, _ = oracle.phase_field_build(g, Cf, iters, dtau, eps)
     ctx32 = _ctx(sfx, g, 1)
+    ctx32.sfx_set_tuning(sfx._lib.SFX_TUNE_F32_REDIST, 1)
     Cd = dev(Cf)
     phi32, chi32 = torch.empty_like(Cd), torch.empty_like(Cd)
     ctx32.sfx_phase_field_build(Cd, chi32, phi32, None, iters=iters, dtau=dtau, eps=eps)
@@ -418,7 +423,7 @@ def test_marangoni_fp32(sfx, geom):
         ctx.sfx_marangoni_force(p, _pairs(ctx, f), dev(phi),
                                 dev(Cf, torch.float32), sig, force, 1)
         assert rel_err(host(sig), sig_o) < 1e-6
-        assert rel_err(host(force), force_o) < 1e-4
+        assert rel_err(host(force), force_o) < 1e-5
 
 
 def test_totals_match_exact_sum(sfx):
@@ -603,11 +608,12 @@ def test_fp32_step_on_rows_wider_than_one_block(sfx, name):
     assert np.abs(host(ctx.sfx_df_unpack(f)) - f_o).max() / scale < F32_TOL
 
 
-def test_fp32_phase_field_build_and_step_against_oracle(sfx):
+@pytest.mark.parametrize("redist32", [0, 1])
+def test_fp32_phase_field_build_and_step_against_oracle(sfx, redist32):
     """The FP32 form end to end on the 3D HR workload at 40^3: the phase
-    field from the FP32 redistancing of the SFX_F32 context (not the
-    oracle's), then two FP32 steps, against the oracle's FP64 build and
-    steps."""
+    field from the SFX_F32 context's own build (FP64 redistancing, or FP32
+    with SFX_TUNE_F32_REDIST), then two FP32 steps, against the oracle's
+    FP64 build and steps."""
     import torch
     c = W.case_hr_3d(n=40, steps=2)
     g, p = c.grid, c.params
@@ -618,6 +624,7 @@ def test_fp32_phase_field_build_and_step_against_oracle(sfx):
                                               c.uz)
         assert st.converged
     ctx = _ctx(sfx, g, 1)
+    ctx.sfx_set_tuning(sfx._lib.SFX_TUNE_F32_REDIST, redist32)
     Cd = dev(c.C)
     chi, phi = torch.empty_like(Cd), torch.empty_like(Cd)
     ctx.sfx_phase_field_build(Cd, chi, phi, None, iters=c.redist_iters, dtau=c.dtau, eps=p.eps)
@@ -632,9 +639,12 @@ def test_fp32_phase_field_build_and_step_against_oracle(sfx):
 
 
 def test_fp32_build_and_step_at_256_cubed_match_the_fp64_path(sfx):
-    """The timed 256^3 workload: FP32 phase-field build and two FP32 steps
-    against the FP64 path (phase field from the FP64 build), which the
-    tests above hold to the oracle at 1e-12; the FP32 form within 1e-5."""
+    """The timed 256^3 workload: the SFX_F32 context's own phase-field build
+    (FP64 redistancing, the default) and two FP32 steps against the FP64
+    path, which the tests above hold to the oracle at 1e-12; the FP32 form
+    within 1e-5.  (With SFX_TUNE_F32_REDIST the float redistancing moves
+    the step by 5e-5 here: F = 1 fills the sphere, and at the front of the
+    redistanced band the drift's direction follows chi's float rounding.)"""
     import torch
     c = W.case_hr_3d(n=256, steps=2)
     g, p = c.grid, c.params

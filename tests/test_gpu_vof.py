@@ -151,6 +151,7 @@ def test_fp32_moving_interface_pipeline_matches_oracle(sfx):
     f0 = 0.5 * delta0
     Co, fo, Fo = c.C.copy(), f0.copy(), c.F0.copy()
     ctx = sfx.Context.for_grid(g, 1)
+    ctx.sfx_set_tuning(sfx._lib.SFX_TUNE_F32_REDIST, 1)
     Cd = dev(c.C)
     fd, Fd = ctx.sfx_df_pack(dev(f0)), ctx.sfx_df_pack(dev(c.F0))
     chi, phid = torch.empty_like(Cd), torch.empty_like(Cd)
