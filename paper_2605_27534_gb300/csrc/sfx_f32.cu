@@ -1224,7 +1224,8 @@ RowGrid row_grid(const Level& L) {
 sfx_status solve_newton32(sfx_ctx* c, const Nw32& p, const float* phi, float* const* Bf,
                           float* const* BF, float2*& fc, float2*& fo, float2*& Fc, float2*& Fo,
                           const float2* fs, const float2* Fs, const sfx_solve_opts* o,
-                          bool predicted, int* iters, bool* conv, float* nrm, cudaStream_t s) {
+                          bool predicted, int mgl, const Mg32Coef& kc, int* iters, bool* conv,
+                          float* nrm, cudaStream_t s) {
   const Level& L = p.L;
   const size_t n = L.ncell();
   const int nb = blocks_for(n, 256);
@@ -1268,13 +1269,33 @@ sfx_status solve_newton32(sfx_ctx* c, const Nw32& p, const float* phi, float* co
     SFX_CUDA(cudaMemcpyAsync(hn + 4 * (it & 1), nbuf, 4 * sizeof(unsigned int),
                              cudaMemcpyDeviceToHost, s));
     SFX_CUDA(cudaEventRecord(c->f32.ev[it & 1], s));
-    for (int q = 0; q < sweeps; ++q)
-      for (int color = (q == 0 ? 1 : 0); color < 2; ++color) {
-        const bool apply = q == sweeps - 1 && color == 1;
-        SFX_KERNEL(c, K_SMOOTH_FINE, nk.corr, grd, blk, s, p, c->f32.H2[0], c->f32.H2[1], Hz,
-                   c->f32.rc, c->f32.e2, color, q == 0 ? 1 : 0,
-                   apply ? fc : nullptr, apply ? Fc : nullptr, flag);
-      }
+    if (mgl >= 2) {
+      // a V-cycle on the correction: finish the first sweep, pre - 1 more
+      // fine sweeps, the coarse levels, then post fine sweeps, the last
+      // black one adding the corrections to the state
+      const int pre = std::max(1, o->nu1), post = std::max(1, o->nu2);
+      for (int q = 0; q < pre; ++q)
+        for (int color = (q == 0 ? 1 : 0); color < 2; ++color)
+          SFX_KERNEL(c, K_SMOOTH_FINE, nk.corr, grd, blk, s, p, c->f32.H2[0], c->f32.H2[1], Hz,
+                     c->f32.rc, c->f32.e2, color, q == 0 ? 1 : 0, nullptr, nullptr, flag);
+      sfx_status st = mg32_cycle(c, kc, mgl, pre, post, o->coarse_sweeps, flag, s);
+      if (st != SFX_OK) return st;
+      for (int q = 0; q < post; ++q)
+        for (int color = 0; color < 2; ++color) {
+          const bool apply = q == post - 1 && color == 1;
+          SFX_KERNEL(c, K_SMOOTH_FINE, nk.corr, grd, blk, s, p, c->f32.H2[0], c->f32.H2[1], Hz,
+                     c->f32.rc, c->f32.e2, color, 0, apply ? fc : nullptr, apply ? Fc : nullptr,
+                     flag);
+        }
+    } else {
+      for (int q = 0; q < sweeps; ++q)
+        for (int color = (q == 0 ? 1 : 0); color < 2; ++color) {
+          const bool apply = q == sweeps - 1 && color == 1;
+          SFX_KERNEL(c, K_SMOOTH_FINE, nk.corr, grd, blk, s, p, c->f32.H2[0], c->f32.H2[1], Hz,
+                     c->f32.rc, c->f32.e2, color, q == 0 ? 1 : 0,
+                     apply ? fc : nullptr, apply ? Fc : nullptr, flag);
+        }
+    }
     SFX_LAUNCH_CHECK();
     const int prev = it - 1;
     if (prev >= 1) {
@@ -1327,6 +1348,7 @@ sfx_status step_f32(sfx_ctx* c, const sfx_params* pr, const double* phi_in, cons
                  (float)pr->Df, (float)pr->DF, (float)(1.0 / pr->eps), Bf[d], BF[d],
                  c->f32.B2[d], c->f32.H2[d]);
     SFX_LAUNCH_CHECK();
+    ++c->f32.drift_epoch;
     c->f32.drift_phi = phi_in;
     c->f32.drift_key[0] = pr->Df;
     c->f32.drift_key[1] = pr->DF;
@@ -1378,8 +1400,20 @@ sfx_status step_f32(sfx_ctx* c, const sfx_params* pr, const double* phi_in, cons
     if (c->f32.solver == 1) {
       Nw32 pw{L, pf.invh, pf.Doh, pF.Doh, pf.inv_dt, pf.ka, pf.kd, pf.ginf, pf.inv_eps, pf.eta,
               pf.literal};
-      st = solve_newton32(c, pw, phi, Bf, BF, fc, fo, Fc, Fo, fs, Fs, o, predict, &it, &dconv, dn,
-                          s);
+      // multigrid on the correction (Sec. 3.1 solves each implicit half by
+      // multigrid): mg_levels >= 2 levels, 1 = relaxation only, 0 = chosen
+      // by the diffusion number D dt/h^2 (relaxation alone converges fast
+      // below 1)
+      const int built = (int)c->lev.size();
+      const double dnum = std::max(pr->Df, pr->DF) * dt / (L.h * L.h);
+      int mgl = o->mg_levels == 0 ? (dnum > 1.0 ? built : 1) : std::min(o->mg_levels, built);
+      if (mgl >= 2) {
+        st = mg32_prepare(c, mgl, s);
+        if (st != SFX_OK) return st;
+      }
+      const Mg32Coef kc{(float)pr->Df, (float)pr->DF, pf.inv_dt, pf.kd, pr->literal_upwind};
+      st = solve_newton32(c, pw, phi, Bf, BF, fc, fo, Fc, Fo, fs, Fs, o, predict, mgl, kc, &it,
+                          &dconv, dn, s);
     } else {
       st = solve_dc32(c, pf, pF, phi, Bf, BF, fc, fo, Fc, Fo, fs, Fs, o, &it, &dconv, dn, s);
     }

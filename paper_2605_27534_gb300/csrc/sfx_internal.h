@@ -37,6 +37,21 @@ enum Kind {
   K_TOTALS, K_FORCES, K_PHASE, K_OTHER, K_COUNT
 };
 
+// One coarse level of the FP32 multigrid for the coupled Newton correction
+// (plain cell layout; the fine level keeps the colour-packed arrays).
+struct Mg32Level {
+  float2* e = nullptr;      // correction (e_f, e_F)
+  float2* r = nullptr;      // right-hand side of the correction equation
+  float2* J = nullptr;      // exchange Jacobian (u, v), volume averages
+  float2* B[3] = {};        // drift faces (B_f, B_F), area averages
+};
+
+// Coefficients of the correction equation that do not depend on the level.
+struct Mg32Coef {
+  float Df, DF, inv_dt, kd;
+  int literal;
+};
+
 // Work arrays of SFX_F32 contexts (float drifts, double-float f*, F*).
 struct F32Scratch {
   bool ready = false;
@@ -63,6 +78,9 @@ struct F32Scratch {
   int* flag = nullptr;              // convergence flag, iteration, prediction kept
   bool predict = true;              // start Newton from x* + last increment
   bool redist32 = false;            // redistance in FP32 (else FP64)
+  std::vector<Mg32Level> mg;        // coarse levels of the correction's V-cycle (0 unused)
+  const void* mg_faces_of = nullptr;  // drift faces the coarse faces were restricted from
+  unsigned long long drift_epoch = 0, mg_epoch = ~0ull;  // rebuilds of the drift faces
   float predict_rho = 1.0f;         // reject a predicted start above this residual
   bool inc_valid = false;
   float* inc_f = nullptr;           // last step's implicit increments x - x*
@@ -167,6 +185,15 @@ void prof_after(sfx_ctx* c, int kind, cudaStream_t s);
 // sfx_phase.cu
 sfx_status phase_field_build(sfx_ctx* c, const double* C, double* chi, void* phi, void* delta,
                              int iters, double dtau, double eps, cudaStream_t s);
+// FP32 multigrid of the coupled Newton correction (sfx_mg32.cu).
+// mg32_prepare allocates levels 1 .. nlev-1 and restricts the drift faces
+// (when they were rebuilt); mg32_cycle takes the fine correction after
+// pre-smoothing, restricts its residual, runs the coarse V-cycle and adds
+// the prolonged coarse correction to it (fine post-smoothing is the
+// caller's).
+sfx_status mg32_prepare(sfx_ctx* c, int nlev, cudaStream_t s);
+sfx_status mg32_cycle(sfx_ctx* c, const Mg32Coef& k, int nlev, int nu1, int nu2,
+                      int coarse_sweeps, const int* done, cudaStream_t s);
 sfx_status phase_field_from_chi(sfx_ctx* c, const double* chi, double* phi, double* delta,
                                 double eps, cudaStream_t s);
 // sfx_advect.cu

@@ -52,6 +52,102 @@ __global__ void k_coarse_solve(Level L, Op op, const double* __restrict__ b, dou
     }
 }
 
+// ---------------------------------------------------------- V-cycle tail
+// The coarse levels of a V-cycle are too small to fill the GPU: each of
+// their sweeps, restrictions and prolongations would be a launch whose
+// cost is its latency.  Every level from the first one with at most
+// kTailCells cells down to the coarsest runs in one block instead
+// (__syncthreads between phases), with the per-cell arithmetic of the
+// multi-launch path (k_rbgs, k_resid_restrict, k_prolong_add): red-black
+// updates within a colour are independent, so the result is the same.
+constexpr int kTailCells = 4096;
+constexpr int kMaxTail = 8;
+
+struct TailLevels {
+  int n;                  // levels in the tail; T.L[n - 1] is the coarsest
+  Level L[kMaxTail];
+  Op op[kMaxTail];
+  double* a[kMaxTail];    // a[0]: the correction of the tail's first level
+  double* b[kMaxTail];    // b[0]: its right-hand side; b[t >= 1] are written
+  int nu1, nu2, coarse_sweeps;
+};
+
+__device__ void tail_smooth(const Level& L, const Op& op, const double* b, double* a,
+                            int sweeps) {
+  const int hx = (L.nx + 1) / 2;
+  const int nwork = hx * L.ny * L.nz;
+  for (int it = 0; it < sweeps; ++it)
+    for (int color = 0; color < 2; ++color) {
+      for (int w = threadIdx.x; w < nwork; w += blockDim.x) {
+        const int ih = w % hx, j = (w / hx) % L.ny, k = w / (hx * L.ny);
+        const int i = 2 * ih + ((j + k + color) & 1);
+        if (i >= L.nx) continue;
+        double sd, sn;
+        flux_terms(L, op, a, i, j, k, sd, sn);
+        const size_t c = cidx(L, i, j, k);
+        const double iv = 1.0 / cell_volume(L, i);
+        a[c] = (b[c] + sn * iv) / (op.lam[c] - sd * iv);
+      }
+      __syncthreads();
+    }
+}
+
+__global__ void __launch_bounds__(1024) k_vcycle_tail(TailLevels T) {
+  for (int t = 0; t + 1 < T.n; ++t) {
+    const Level& Lf = T.L[t];
+    const Level& Lc = T.L[t + 1];
+    tail_smooth(Lf, T.op[t], T.b[t], T.a[t], T.nu1);
+    const int n = (int)Lc.ncell();
+    const int kz = Lf.geom == SFX_CART3D ? 2 : 1;
+    for (int c = threadIdx.x; c < n; c += blockDim.x) {
+      const int I = c % Lc.nx, J = (c / Lc.nx) % Lc.ny, K = c / (Lc.nx * Lc.ny);
+      double acc = 0.0;
+      for (int dk = 0; dk < kz; ++dk)
+        for (int dj = 0; dj < 2; ++dj)
+          for (int di = 0; di < 2; ++di) {
+            const int i = 2 * I + di, j = 2 * J + dj, k = kz == 2 ? 2 * K + dk : 0;
+            double sd, sn;
+            flux_terms(Lf, T.op[t], T.a[t], i, j, k, sd, sn);
+            const size_t f = cidx(Lf, i, j, k);
+            const double V = cell_volume(Lf, i);
+            acc += V * T.b[t][f] - ((T.op[t].lam[f] * V - sd) * T.a[t][f] - sn);
+          }
+      T.b[t + 1][c] = acc / cell_volume(Lc, I);
+      T.a[t + 1][c] = 0.0;
+    }
+    __syncthreads();
+  }
+  const int last = T.n - 1;
+  tail_smooth(T.L[last], T.op[last], T.b[last], T.a[last], T.coarse_sweeps);
+  for (int t = T.n - 2; t >= 0; --t) {
+    const Level& Lc = T.L[t + 1];
+    const Level& Lf = T.L[t];
+    const bool is3 = Lf.geom == SFX_CART3D;
+    const double* ec = T.a[t + 1];
+    const int n = (int)Lf.ncell();
+    for (int c = threadIdx.x; c < n; c += blockDim.x) {
+      const int i = c % Lf.nx, j = (c / Lf.nx) % Lf.ny, k = c / (Lf.nx * Lf.ny);
+      const int I = i >> 1, J = j >> 1, K = k >> 1;
+      const int I2 = min(max(I + ((i & 1) ? 1 : -1), 0), Lc.nx - 1);
+      const int J2 = min(max(J + ((j & 1) ? 1 : -1), 0), Lc.ny - 1);
+      double v;
+      if (!is3) {
+        v = 0.5625 * ec[cidx(Lc, I, J, 0)] + 0.1875 * ec[cidx(Lc, I2, J, 0)] +
+            0.1875 * ec[cidx(Lc, I, J2, 0)] + 0.0625 * ec[cidx(Lc, I2, J2, 0)];
+      } else {
+        const int K2 = min(max(K + ((k & 1) ? 1 : -1), 0), Lc.nz - 1);
+        v = 0.421875 * ec[cidx(Lc, I, J, K)] +
+            0.140625 * (ec[cidx(Lc, I2, J, K)] + ec[cidx(Lc, I, J2, K)] + ec[cidx(Lc, I, J, K2)]) +
+            0.046875 * (ec[cidx(Lc, I2, J2, K)] + ec[cidx(Lc, I2, J, K2)] + ec[cidx(Lc, I, J2, K2)]) +
+            0.015625 * ec[cidx(Lc, I2, J2, K2)];
+      }
+      T.a[t][c] += v;
+    }
+    __syncthreads();
+    tail_smooth(Lf, T.op[t], T.b[t], T.a[t], T.nu2);
+  }
+}
+
 // Volume-weighted restriction of the residual b - L(a) to the coarse grid.
 __global__ void k_resid_restrict(Level Lf, Level Lc, Op op, const double* __restrict__ b,
                                  const double* __restrict__ a, double* __restrict__ rc) {
@@ -317,6 +413,23 @@ sfx_status vcycle(sfx_ctx* c, const Hier& H, int l, double* a, const double* b,
                   const sfx_solve_opts* o, cudaStream_t s) {
   const Level& L = c->lev[l].lv;
   Op op = op_at(H, l);
+  if (l >= 1 && l < H.nlev - 1 && L.ncell() <= (size_t)kTailCells && H.nlev - l <= kMaxTail) {
+    // this level and every coarser one in one block
+    TailLevels T{};
+    T.n = H.nlev - l;
+    for (int t = 0; t < T.n; ++t) {
+      T.L[t] = c->lev[l + t].lv;
+      T.op[t] = op_at(H, l + t);
+      T.a[t] = t == 0 ? a : c->lev[l + t].a;
+      T.b[t] = t == 0 ? const_cast<double*>(b) : c->lev[l + t].b;
+    }
+    T.nu1 = o->nu1;
+    T.nu2 = o->nu2;
+    T.coarse_sweeps = o->coarse_sweeps;
+    SFX_KERNEL(c, K_SMOOTH_COARSE, k_vcycle_tail, 1, 1024, s, T);
+    SFX_LAUNCH_CHECK();
+    return SFX_OK;
+  }
   if (l == H.nlev - 1) return coarse_solve(c, L, op, b, a, o->coarse_sweeps, s);
   const int kind = l == 0 ? K_SMOOTH_FINE : K_SMOOTH_COARSE;
   sfx_status st = smooth(c, kind, L, op, b, a, o->nu1, s);
