@@ -237,7 +237,7 @@ __global__ void k_b_corr(const BInst* __restrict__ I, int n, const int* __restri
     return;
   }
   const __half2* H[3] = {P.H2[0] + B.rfoff, P.H2[1] + B.zfoff, nullptr};
-  corr2_cell<G>(B.p, i, j, 0, H, P.rc + w, P.e2 + w, color, first, fst, Fst);
+  corr2_cell<G>(B.p, i, j, 0, H, P.rc + w, P.e2 + w, color, first, fst, Fst, fst, Fst);
 }
 
 // per-instance compensated totals: kTotBlocks blocks per instance each walk

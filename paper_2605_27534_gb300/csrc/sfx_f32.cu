@@ -334,7 +334,8 @@ __global__ void __launch_bounds__(128, 10)
 k_corr2_32(Nw32 p, const __half2* __restrict__ Hx, const __half2* __restrict__ Hy,
            const __half2* __restrict__ Hz, const float4* __restrict__ rc,
            float2* __restrict__ e2, int color, int first,
-           float2* __restrict__ fst, float2* __restrict__ Fst, const int* __restrict__ done) {
+           float2* fst, float2* Fst, const float2* fsrc, const float2* Fsrc,
+           const int* __restrict__ done) {
   if (done && *done) return;
   const Level& L = p.L;
   const int j = blockIdx.y, k = blockIdx.z;
@@ -348,12 +349,12 @@ k_corr2_32(Nw32 p, const __half2* __restrict__ Hx, const __half2* __restrict__ H
       const RBIdx rb = rb_index(L, i, j, k);
       const size_t pr = (1 - color) * rb.plane + rb.pos;   // ir's packed slot
       const float2 er = e2[pr];
-      fst[cr] = df_add(fst[cr], er.x);
-      Fst[cr] = df_add(Fst[cr], er.y);
+      fst[cr] = df_add(fsrc[cr], er.x);
+      Fst[cr] = df_add(Fsrc[cr], er.y);
     }
     return;
   }
-  corr2_cell<G>(p, i, j, k, H, rc, e2, color, first, fst, Fst);
+  corr2_cell<G>(p, i, j, k, H, rc, e2, color, first, fst, Fst, fsrc, Fsrc);
 }
 
 // The Newton kernels of one geometry (the branches on the geometry in the
@@ -1182,6 +1183,18 @@ __global__ void k_restore32(size_t n, const int* __restrict__ ok, const float2* 
 
 // Initial guess of the Newton iteration: x* plus the implicit increment of
 // the previous step (a smooth solution changes little from step to step).
+// (f, F) <- (f*, F*) when the Newton solve converged at its first check
+// (flag[1] = 1): its state updates then never ran.
+__global__ void k_copy_if_first32(size_t n, const int* __restrict__ flag,
+                                  const float2* __restrict__ fs, const float2* __restrict__ Fs,
+                                  float2* __restrict__ f, float2* __restrict__ F) {
+  if (!(flag[0] && flag[1] == 1)) return;
+  for (size_t c = blockIdx.x * (size_t)blockDim.x + threadIdx.x; c < n;
+       c += (size_t)gridDim.x * blockDim.x) {
+    f[c] = fs[c];
+    F[c] = Fs[c];
+  }
+}
 __global__ void k_predict32(size_t n, const float2* __restrict__ fs, const float2* __restrict__ Fs,
                             const float* __restrict__ df, const float* __restrict__ dF,
                             float2* __restrict__ f, float2* __restrict__ F) {
@@ -1224,8 +1237,8 @@ RowGrid row_grid(const Level& L) {
 sfx_status solve_newton32(sfx_ctx* c, const Nw32& p, const float* phi, float* const* Bf,
                           float* const* BF, float2*& fc, float2*& fo, float2*& Fc, float2*& Fo,
                           const float2* fs, const float2* Fs, const sfx_solve_opts* o,
-                          bool predicted, int mgl, const Mg32Coef& kc, int* iters, bool* conv,
-                          float* nrm, cudaStream_t s) {
+                          bool predicted, bool from_star, int mgl, const Mg32Coef& kc,
+                          int* iters, bool* conv, float* nrm, cudaStream_t s) {
   const Level& L = p.L;
   const size_t n = L.ncell();
   const int nb = blocks_for(n, 256);
@@ -1253,8 +1266,13 @@ sfx_status solve_newton32(sfx_ctx* c, const Nw32& p, const float* phi, float* co
   for (it = 1; it <= o->max_cycles; ++it) {
     unsigned int* nbuf = dn + 4 * (it & 1);
     SFX_CUDA(cudaMemsetAsync(nbuf, 0, 4 * sizeof(unsigned int), s));
-    SFX_KERNEL(c, K_RESIDUAL, nk.resid, rg.grid, rg.block, s, p, phi, B2[0], B2[1], B2[2], fc,
-               Fc, fs, Fs, c->f32.rc, nbuf, c->f32.e2, flag);
+    // from_star: the first iterate is x* itself, read from (f*, F*); the
+    // first state update writes x* + e into (f, F), so no copy precedes it
+    const bool star = from_star && it == 1;
+    const float2* fsrc = star ? fs : fc;
+    const float2* Fsrc = star ? Fs : Fc;
+    SFX_KERNEL(c, K_RESIDUAL, nk.resid, rg.grid, rg.block, s, p, phi, B2[0], B2[1], B2[2], fsrc,
+               Fsrc, fs, Fs, c->f32.rc, nbuf, c->f32.e2, flag);
     if (it == 1 && predicted) {
       // keep the predicted start only if its residual is already small;
       // otherwise restart from x* (both launches return at once when kept)
@@ -1277,7 +1295,8 @@ sfx_status solve_newton32(sfx_ctx* c, const Nw32& p, const float* phi, float* co
       for (int q = 0; q < pre; ++q)
         for (int color = (q == 0 ? 1 : 0); color < 2; ++color)
           SFX_KERNEL(c, K_SMOOTH_FINE, nk.corr, grd, blk, s, p, c->f32.H2[0], c->f32.H2[1], Hz,
-                     c->f32.rc, c->f32.e2, color, q == 0 ? 1 : 0, nullptr, nullptr, flag);
+                     c->f32.rc, c->f32.e2, color, q == 0 ? 1 : 0, nullptr, nullptr, nullptr,
+                     nullptr, flag);
       sfx_status st = mg32_cycle(c, kc, mgl, pre, post, o->coarse_sweeps, flag, s);
       if (st != SFX_OK) return st;
       for (int q = 0; q < post; ++q)
@@ -1285,7 +1304,7 @@ sfx_status solve_newton32(sfx_ctx* c, const Nw32& p, const float* phi, float* co
           const bool apply = q == post - 1 && color == 1;
           SFX_KERNEL(c, K_SMOOTH_FINE, nk.corr, grd, blk, s, p, c->f32.H2[0], c->f32.H2[1], Hz,
                      c->f32.rc, c->f32.e2, color, 0, apply ? fc : nullptr, apply ? Fc : nullptr,
-                     flag);
+                     fsrc, Fsrc, flag);
         }
     } else {
       for (int q = 0; q < sweeps; ++q)
@@ -1293,7 +1312,7 @@ sfx_status solve_newton32(sfx_ctx* c, const Nw32& p, const float* phi, float* co
           const bool apply = q == sweeps - 1 && color == 1;
           SFX_KERNEL(c, K_SMOOTH_FINE, nk.corr, grd, blk, s, p, c->f32.H2[0], c->f32.H2[1], Hz,
                      c->f32.rc, c->f32.e2, color, q == 0 ? 1 : 0,
-                     apply ? fc : nullptr, apply ? Fc : nullptr, flag);
+                     apply ? fc : nullptr, apply ? Fc : nullptr, fsrc, Fsrc, flag);
         }
     }
     SFX_LAUNCH_CHECK();
@@ -1309,6 +1328,11 @@ sfx_status solve_newton32(sfx_ctx* c, const Nw32& p, const float* phi, float* co
         break;
       }
     }
+  }
+  if (from_star) {
+    // converged at the first check: x* was the answer and was never copied
+    SFX_KERNEL(c, K_SETUP, k_copy_if_first32, nb, 256, s, n, flag, fs, Fs, fc, Fc);
+    SFX_LAUNCH_CHECK();
   }
   if (!*conv) {
     // the last iteration's residuals
@@ -1377,11 +1401,13 @@ sfx_status step_f32(sfx_ctx* c, const sfx_params* pr, const double* phi_in, cons
     SFX_CUDA(cudaMemcpyAsync(fs, f, n * sizeof(float2), cudaMemcpyDeviceToDevice, s));
     SFX_CUDA(cudaMemcpyAsync(Fs, F, n * sizeof(float2), cudaMemcpyDeviceToDevice, s));
   }
+  // the Newton solver starts from x* in place (no copy into f, F)
+  const bool from_star = ux && !predict && c->f32.solver == 1;
   if (predict) {
     SFX_KERNEL(c, K_SETUP, k_predict32, blocks_for(n, 256), 256, s, n, fs, Fs, c->f32.inc_f,
                c->f32.inc_F, f, F);
     SFX_LAUNCH_CHECK();
-  } else if (ux) {
+  } else if (ux && !from_star) {
     SFX_CUDA(cudaMemcpyAsync(f, fs, n * sizeof(float2), cudaMemcpyDeviceToDevice, s));
     SFX_CUDA(cudaMemcpyAsync(F, Fs, n * sizeof(float2), cudaMemcpyDeviceToDevice, s));
   }
@@ -1412,8 +1438,8 @@ sfx_status step_f32(sfx_ctx* c, const sfx_params* pr, const double* phi_in, cons
         if (st != SFX_OK) return st;
       }
       const Mg32Coef kc{(float)pr->Df, (float)pr->DF, pf.inv_dt, pf.kd, pr->literal_upwind};
-      st = solve_newton32(c, pw, phi, Bf, BF, fc, fo, Fc, Fo, fs, Fs, o, predict, mgl, kc, &it,
-                          &dconv, dn, s);
+      st = solve_newton32(c, pw, phi, Bf, BF, fc, fo, Fc, Fo, fs, Fs, o, predict, from_star, mgl,
+                          kc, &it, &dconv, dn, s);
     } else {
       st = solve_dc32(c, pf, pF, phi, Bf, BF, fc, fo, Fc, Fo, fs, Fs, o, &it, &dconv, dn, s);
     }

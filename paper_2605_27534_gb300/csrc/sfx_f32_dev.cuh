@@ -496,7 +496,8 @@ __device__ __forceinline__ void corr2_cell(const Nw32& p, int i, int j, int k,
                                            const __half2* const* H,
                                            const float4* __restrict__ rc,
                                            float2* __restrict__ e2, int color, int first,
-                                           float2* __restrict__ fst, float2* __restrict__ Fst) {
+                                           float2* fst, float2* Fst,
+                                           const float2* fsrc, const float2* Fsrc) {
   // the other colour's corrections are only read in this launch: read them
   // through a separate read-only view of the array
   const float2* __restrict__ eo = e2;
@@ -546,17 +547,19 @@ __device__ __forceinline__ void corr2_cell(const Nw32& p, int i, int j, int k,
   const float nF = __fmaf_rn(__fmaf_rn(d, rhof, __fmul_rn(a, rhoF)), inv, eFc);
   e2[own] = make_float2(nf, nF);
   if (fst) {
-    // last black colour of the iteration: add the corrections to the state,
-    // for this cell and for the red cell that shares its pair (2t, 2t+1),
-    // which sits at the same packed position of the other plane
-    fst[c] = df_add(fst[c], nf);
-    Fst[c] = df_add(Fst[c], nF);
+    // last black colour of the iteration: the state becomes src + correction
+    // (src = the state itself, or the advected x* in the first iteration,
+    // which then needs no copy into the state), for this cell and for the
+    // red cell that shares its pair (2t, 2t+1), which sits at the same
+    // packed position of the other plane
+    fst[c] = df_add(fsrc[c], nf);
+    Fst[c] = df_add(Fsrc[c], nF);
     const int ir = i ^ 1;
     if (ir < L.nx) {
       const ix cr = c - (ix)i + (ix)ir;
       const float2 er = __ldg(eo + oth);
-      fst[cr] = df_add(fst[cr], er.x);
-      Fst[cr] = df_add(Fst[cr], er.y);
+      fst[cr] = df_add(fsrc[cr], er.x);
+      Fst[cr] = df_add(Fsrc[cr], er.y);
     }
   }
 }

@@ -60,7 +60,11 @@ __global__ void k_coarse_solve(Level L, Op op, const double* __restrict__ b, dou
 // (__syncthreads between phases), with the per-cell arithmetic of the
 // multi-launch path (k_rbgs, k_resid_restrict, k_prolong_add): red-black
 // updates within a colour are independent, so the result is the same.
-constexpr int kTailCells = 4096;
+// One SM's FP64 pipe bounds a phase: at 4096 cells (64^2) a phase took
+// longer in one block than as a launch over the whole GPU (the 512^2
+// FP64 vortex step went from 9.4 to 12.3 ms), at 1024 cells the two are
+// about even, so the tail starts there.
+constexpr int kTailCells = 1024;
 constexpr int kMaxTail = 8;
 
 struct TailLevels {
