@@ -85,6 +85,9 @@ def parse():
                     help="steps of the FP64 path timed beside the FP32 line (0: skip)")
     ap.add_argument("--batch-steps", type=int, default=30,
                     help="also time the batched workload for this many steps (0: skip)")
+    ap.add_argument("--vof-steps", type=int, default=20,
+                    help="steps of the 256^3 geometric VoF advection timed beside the line "
+                         "(0: skip)")
     ap.add_argument("--adsorption-steps", type=int, default=1000,
                     help="steps of the 128^2 FP64 no-flow adsorption workload timed beside "
                          "the line (0: skip)")
@@ -99,6 +102,9 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--sweeps", type=int, default=4,
                     help="FP32: red-black correction sweeps per Newton iteration")
+    ap.add_argument("--sweep-planes", type=int, default=2, choices=[1, 2],
+                    help="FP32 3D: z-planes per thread of the correction sweep "
+                         "(SFX_TUNE_SWEEP_PLANES)")
     ap.add_argument("--predict", action="store_true",
                     help="FP32: start each Newton solve from x* plus the last increment "
                          "(SFX_TUNE_PREDICT 1; no gain on the 3D workload)")
@@ -427,6 +433,7 @@ def run_gpu(a, case, rank, world, local_rank):
         opts.nu1, opts.nu2 = a.sweeps, 0
         ctx.sfx_set_tuning(sfx._lib.SFX_TUNE_REUSE_DRIFT, 1)   # the interface is static
         ctx.sfx_set_tuning(sfx._lib.SFX_TUNE_PREDICT, 1 if a.predict else 0)
+        ctx.sfx_set_tuning(sfx._lib.SFX_TUNE_SWEEP_PLANES, a.sweep_planes)
     stats = []
 
     def step():
@@ -580,6 +587,9 @@ def run_gpu(a, case, rank, world, local_rank):
     ads = None
     if a.adsorption_steps > 0:
         ads = adsorption_run(a, dev, a.adsorption_steps)
+    vof = None
+    if a.vof_steps > 0:
+        vof = vof_run(a, dev, a.vof_steps)
     if roof is not None:
         roof["frac_of_nominal"] = roof["achieved"] / NOMINAL_HBM_GBS
         roof["nominal_peak"] = NOMINAL_HBM_GBS
@@ -621,7 +631,49 @@ def run_gpu(a, case, rank, world, local_rank):
         line["kinetics_sweep"] = kin
     if ads is not None:
         line["adsorption2d_128"] = ads
+    if vof is not None:
+        line["vof3d_256"] = vof
     print(json.dumps(line))
+
+
+def vof_run(a, dev, steps, warmup=3, n=256):
+    """Geometric VoF advection of C on the 256^3 sphere (R = 0.125) in the
+    Hadamard-Rybczynski flow, SFX_F32 context (FP32 PLIC geometry, double
+    C), dt = 2e-4 (face Courant numbers up to ~0.1), direction order
+    alternating.  Roofline of the whole VoF step on its per-pass bytes: the
+    indicator H = [C > 1/2] (C in, H out: 16 B per cell), then per direction
+    the face fluxes (C of the upwind cell, u, Q out: 8 + 4 + 8 B per face)
+    and the update (Q of both faces, u, H, C in, C out: 8 + 4 + 8 + 8 + 8 B
+    per cell): 16 + 3 x 56 = 184 B per cell."""
+    import torch
+    import paper_2605_27534_gb300 as sfx
+    c = W.case_hr_3d(n=n, steps=1)
+    g = c.grid
+    ctx = sfx.Context.for_grid(g, sfx.SFX_F32)
+    Cd = torch.from_numpy(c.C).to(dev)
+    u = [torch.from_numpy(x).to(dev, torch.float32) for x in (c.ux, c.uy, c.uz)]
+    dt = 2e-4
+    for s_ in range(warmup):
+        ctx.sfx_vof_advect(*u, dt, Cd, s_ % 2)
+    m0 = float(Cd.sum().item())
+    stream = torch.cuda.current_stream()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for s_ in range(steps):
+        ctx.sfx_vof_advect(*u, dt, Cd, s_ % 2)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    peaks, src = measured_peaks()
+    ab = 184.0 * g.ncell
+    return {"ms_per_step": ms, "value": g.ncell / (ms * 1e-3), "unit": UNIT, "steps": steps,
+            "cells": g.ncell, "dtype": "f32 PLIC geometry, f64 C",
+            "roofline": {"bound": "hbm", "achieved": ab / (ms * 1e-3) / 1e9,
+                         "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                         "frac": ab / (ms * 1e-3) / 1e9 / peaks["hbm_gbs"],
+                         "bytes_per_step": ab, "kernels": "indicator + 3 x (flux + update)"},
+            "sum_C_rel_change": float(Cd.sum().item()) / m0 - 1.0}
 
 
 def adsorption_run(a, dev, steps, warmup=3):

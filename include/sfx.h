@@ -93,7 +93,11 @@ typedef struct {
   int max_cycles;     /* cap on Picard iterations (each: nu V-cycles per field) */
   int nu1, nu2;       /* red-black Gauss-Seidel sweeps before / after the
                          coarse-grid correction */
-  int mg_levels;      /* levels in the V-cycle (1 = smoother only; 0 = auto) */
+  int mg_levels;      /* levels in the V-cycle (1 = smoother only; 0 = auto:
+                         SFX_F64 every level; SFX_F32 relaxation alone when
+                         max(Df, DF) dt/h^2 <= 1, else a V-cycle on the
+                         Newton correction over the levels whose h <= 3 eps,
+                         at least two) */
   int vcycles;        /* V-cycles per field per Picard iteration (>= 1) */
   int check_every;    /* Picard iterations between residual checks (>= 1) */
   int coarse_sweeps;  /* Gauss-Seidel sweeps on the coarsest level */
@@ -197,7 +201,10 @@ sfx_status sfx_vof_advect(sfx_ctx* ctx, const void* ux, const void* uy, const vo
    velocities are in the context precision.  SFX_F32 contexts solve the
    same system by coupled Newton defect correction (SFX_TUNE_F32_SOLVER):
    each iteration evaluates both residuals in pair arithmetic and relaxes
-   the correction by nu1 + nu2 FP32 red-black sweeps.  stats may be NULL. */
+   the correction by nu1 + nu2 FP32 red-black sweeps with a 2x2 block solve
+   per cell, or, when diffusion dominates (opts->mg_levels), by an FP32
+   V-cycle: nu1 fine sweeps, the coarse levels (the same block smoother on
+   re-discretised operators), nu2 fine sweeps.  stats may be NULL. */
 sfx_status sfx_surfactant_step(sfx_ctx* ctx, const sfx_params* params,
                                const void* phi, const void* ux,
                                const void* uy, const void* uz, void* f,
@@ -339,6 +346,11 @@ typedef enum {
                                rounding: with F = 1 inside a 256^3 sphere
                                the step then moves by 5e-5.  0 (default) =
                                FP64 redistancing as in SFX_F64 contexts. */
+  SFX_TUNE_SWEEP_PLANES = 5, /* SFX_F32, 3D: z-planes each thread of the
+                               Newton correction sweep updates, 1 or 2
+                               (default: two independent cells' loads in
+                               flight per thread; 5 % faster at 256^3).
+                               Bitwise equal. */
   SFX_TUNE_PREDICT = 3      /* SFX_F32 Newton solver: 1 (default) = start
                                the iteration from x* plus the previous
                                step's implicit increment x - x* when the

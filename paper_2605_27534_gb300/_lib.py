@@ -33,6 +33,7 @@ SFX_TUNE_F32_SOLVER = 1
 SFX_TUNE_REUSE_DRIFT = 2
 SFX_TUNE_PREDICT = 3
 SFX_TUNE_F32_REDIST = 4
+SFX_TUNE_SWEEP_PLANES = 5
 KERNEL_KINDS = ["smooth_fine", "smooth_coarse", "restrict", "prolong", "setup", "residual",
                 "advect", "totals", "forces", "phase", "other"]
 

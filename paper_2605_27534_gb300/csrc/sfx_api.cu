@@ -372,6 +372,10 @@ sfx_status sfx_set_tuning(sfx_ctx* c, int key, int value) {
     c->f32.inc_valid = false;
     return SFX_OK;
   }
+  if (key == SFX_TUNE_SWEEP_PLANES && (value == 1 || value == 2)) {
+    c->f32.sweep_planes = value;
+    return SFX_OK;
+  }
   if (key == SFX_TUNE_F32_REDIST && (value == 0 || value == 1)) {
     c->f32.redist32 = value == 1;
     return SFX_OK;

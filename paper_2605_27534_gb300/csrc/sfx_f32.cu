@@ -329,18 +329,17 @@ k_resid2_32(Nw32 p, const float* __restrict__ phi, const float2* __restrict__ B2
 }
 
 // One colour of the coupled red-black Gauss-Seidel on the correction.
-template <int G>
-__global__ void __launch_bounds__(128, 10)
-k_corr2_32(Nw32 p, const __half2* __restrict__ Hx, const __half2* __restrict__ Hy,
-           const __half2* __restrict__ Hz, const float4* __restrict__ rc,
-           float2* __restrict__ e2, int color, int first,
-           float2* fst, float2* Fst, const float2* fsrc, const float2* Fsrc,
-           const int* __restrict__ done) {
-  if (done && *done) return;
+// Block (x chunk, j, k): one colour of one row per block.  With KP = 2 a
+// thread also updates the same cell of plane k + gridDim.z (3D): two
+// independent cells whose loads are in flight together.
+template <int G, int KP>
+__device__ __forceinline__ void corr2_row(const Nw32& p, const __half2* const* H,
+                                          const float4* __restrict__ rc,
+                                          float2* __restrict__ e2, int color, int first,
+                                          float2* fst, float2* Fst, const float2* fsrc,
+                                          const float2* Fsrc, int j, int k) {
   const Level& L = p.L;
-  const int j = blockIdx.y, k = blockIdx.z;
   const int i = 2 * (blockIdx.x * blockDim.x + threadIdx.x) + ((j + k + color) & 1);
-  const __half2* H[3] = {Hx, Hy, Hz};
   if (i >= L.nx) {
     // a row of odd length: the last red cell has no black partner
     const int ir = i ^ 1;
@@ -357,23 +356,58 @@ k_corr2_32(Nw32 p, const __half2* __restrict__ Hx, const __half2* __restrict__ H
   corr2_cell<G>(p, i, j, k, H, rc, e2, color, first, fst, Fst, fsrc, Fsrc);
 }
 
+template <int G, int KP>
+__global__ void __launch_bounds__(128, KP == 1 ? 10 : 8)
+k_corr2_32(Nw32 p, const __half2* __restrict__ Hx, const __half2* __restrict__ Hy,
+           const __half2* __restrict__ Hz, const float4* __restrict__ rc,
+           float2* __restrict__ e2, int color, int first,
+           float2* fst, float2* Fst, const float2* fsrc, const float2* Fsrc,
+           const int* __restrict__ done) {
+  if (done && *done) return;
+  const int j = blockIdx.y, k = blockIdx.z;
+  const __half2* H[3] = {Hx, Hy, Hz};
+  if (KP == 1) {
+    corr2_row<G, 1>(p, H, rc, e2, color, first, fst, Fst, fsrc, Fsrc, j, k);
+    return;
+  }
+  // two planes: both cells' loads are issued before either cell's
+  // arithmetic (rows of even length only; the odd-row tail goes cell by cell)
+  const Level& L = p.L;
+  const int k2 = k + (int)gridDim.z;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  const int i1 = 2 * t + ((j + k + color) & 1), i2 = 2 * t + ((j + k2 + color) & 1);
+  if ((L.nx & 1) || k2 >= L.nz || i1 >= L.nx || i2 >= L.nx) {
+    corr2_row<G, KP>(p, H, rc, e2, color, first, fst, Fst, fsrc, Fsrc, j, k);
+    if (k2 < L.nz) corr2_row<G, KP>(p, H, rc, e2, color, first, fst, Fst, fsrc, Fsrc, j, k2);
+    return;
+  }
+  Corr2In a, b;
+  corr2_load<G>(p, i1, j, k, H, rc, e2, color, first, a);
+  corr2_load<G>(p, i2, j, k2, H, rc, e2, color, first, b);
+  corr2_apply<G>(p, a, e2, fst, Fst, fsrc, Fsrc);
+  corr2_apply<G>(p, b, e2, fst, Fst, fsrc, Fsrc);
+}
+
 // The Newton kernels of one geometry (the branches on the geometry in the
 // cell functions fold at compile time).  The 3D residual keeps the branch
 // at run time: specialised it needs more registers than its occupancy
 // bound allows and spills.
 struct NewtonKernels {
   decltype(&k_resid2_32<kGeomRuntime>) resid;
-  decltype(&k_corr2_32<SFX_CART3D>) corr;
+  decltype(&k_corr2_32<SFX_CART3D, 1>) corr;
+  int kp;   // planes per thread of the correction sweep
 };
 template <int G>
 NewtonKernels newton_kernels_of() {
-  return NewtonKernels{&k_resid2_32<G>, &k_corr2_32<G>};
+  return NewtonKernels{&k_resid2_32<G>, &k_corr2_32<G, 1>, 1};
 }
-NewtonKernels newton_kernels(int geom) {
+NewtonKernels newton_kernels(int geom, int kp) {
   switch (geom) {
     case SFX_AXISYM: return newton_kernels_of<SFX_AXISYM>();
     case SFX_PLANAR2D: return newton_kernels_of<SFX_PLANAR2D>();
-    default: return NewtonKernels{&k_resid2_32<kGeomRuntime>, &k_corr2_32<SFX_CART3D>};
+    default:
+      if (kp == 2) return NewtonKernels{&k_resid2_32<kGeomRuntime>, &k_corr2_32<SFX_CART3D, 2>, 2};
+      return NewtonKernels{&k_resid2_32<kGeomRuntime>, &k_corr2_32<SFX_CART3D, 1>, 1};
   }
 }
 
@@ -1244,12 +1278,14 @@ sfx_status solve_newton32(sfx_ctx* c, const Nw32& p, const float* phi, float* co
   const int nb = blocks_for(n, 256);
   const int sweeps = std::max(1, o->nu1 + o->nu2);
   const float tolf = (float)o->tol;
-  dim3 blk(128), grd((unsigned)(((L.nx + 1) / 2 + 127) / 128), (unsigned)L.ny, (unsigned)L.nz);
+  const NewtonKernels nk = newton_kernels(L.geom, c->f32.sweep_planes);
+  // with two planes per thread the grid covers the lower half of the planes
+  dim3 blk(128), grd((unsigned)(((L.nx + 1) / 2 + 127) / 128), (unsigned)L.ny,
+                     (unsigned)((L.nz + nk.kp - 1) / nk.kp));
   unsigned int* dn = (unsigned int*)c->d_norms;        // two 4-slot norm buffers
   unsigned int* hn = (unsigned int*)c->h_norms;
   int* flag = c->f32.flag;
   const RowGrid rg = row_grid(L);
-  const NewtonKernels nk = newton_kernels(L.geom);
   const __half2* Hz = L.ndim() == 3 ? c->f32.H2[2] : nullptr;
   const float2* B2[3] = {c->f32.B2[0], c->f32.B2[1], L.ndim() == 3 ? c->f32.B2[2] : nullptr};
   SFX_CUDA(cudaMemsetAsync(flag, 0, 2 * sizeof(int), s));
@@ -1429,10 +1465,17 @@ sfx_status step_f32(sfx_ctx* c, const sfx_params* pr, const double* phi_in, cons
       // multigrid on the correction (Sec. 3.1 solves each implicit half by
       // multigrid): mg_levels >= 2 levels, 1 = relaxation only, 0 = chosen
       // by the diffusion number D dt/h^2 (relaxation alone converges fast
-      // below 1)
+      // below 1) and, for its depth, by the phase-field width: a level
+      // whose h exceeds 3 eps no longer resolves the band where the drift
+      // confines f, and its re-discretised correction (measured on a
+      // 64^2 circle at D dt/h^2 = 20) made the V-cycle diverge; the auto
+      // choice keeps the levels with h <= 3 eps (at least one coarse level)
       const int built = (int)c->lev.size();
       const double dnum = std::max(pr->Df, pr->DF) * dt / (L.h * L.h);
-      int mgl = o->mg_levels == 0 ? (dnum > 1.0 ? built : 1) : std::min(o->mg_levels, built);
+      int deep = 1;
+      while (deep < built && c->lev[deep].lv.h <= 3.0 * pr->eps) ++deep;
+      deep = std::min(std::max(deep, 2), built);
+      int mgl = o->mg_levels == 0 ? (dnum > 1.0 ? deep : 1) : std::min(o->mg_levels, built);
       if (mgl >= 2) {
         st = mg32_prepare(c, mgl, s);
         if (st != SFX_OK) return st;

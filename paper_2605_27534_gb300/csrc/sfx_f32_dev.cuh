@@ -491,6 +491,97 @@ __device__ __forceinline__ void resid2_cell(const Nw32& p, int i, int j, int k, 
 // only precondition the Newton correction (the residual pass fixes the
 // solution), so they read the face drifts in half precision (relative
 // 5e-4), halving their face traffic.
+// Everything one cell of the correction sweep reads (split from its
+// arithmetic so that a thread can have two cells' loads in flight).
+struct Corr2In {
+  bool has[6];
+  float enf[6], enF[6], Bf[6], BF[6];
+  float2 ec;
+  float4 q4;
+  ix c, own, oth;
+  int i;
+};
+
+template <int G>
+__device__ __forceinline__ void corr2_load(const Nw32& p, int i, int j, int k,
+                                           const __half2* const* H,
+                                           const float4* __restrict__ rc,
+                                           const float2* __restrict__ e2, int color, int first,
+                                           Corr2In& in) {
+  // the other colour's corrections are only read in this launch: read them
+  // through the read-only path
+  const Level& L = p.L;
+  in.i = i;
+  in.c = cidx32(L, i, j, k);
+  ix nbi[6];
+  gather6<G>(L, i, j, k, in.c, in.has, nbi);
+  // the work arrays are colour-packed: own cell and the other colour's plane
+  const RBIdx rb = rb_index(L, i, j, k);
+  in.own = (ix)color * rb.plane + rb.pos;
+  in.oth = (ix)(1 - color) * rb.plane + rb.pos;
+  const ix sz = (ix)L.ny * rb.half;
+  nbi[0] = in.oth - 1 + (i & 1);
+  nbi[1] = in.oth + (i & 1);
+  nbi[2] = in.oth - rb.half;
+  nbi[3] = in.oth + rb.half;
+  nbi[4] = in.oth - sz;
+  nbi[5] = in.oth + sz;
+  // every cell starts at zero in the first sweep
+  const bool zero_nb = first && color == 0;
+#pragma unroll
+  for (int q = 0; q < 6; ++q) {
+    const float2 v = (in.has[q] && !zero_nb) ? __ldg(e2 + nbi[q]) : make_float2(0.0f, 0.0f);
+    in.enf[q] = v.x;
+    in.enF[q] = v.y;
+  }
+  in.ec = first ? make_float2(0.0f, 0.0f) : e2[in.own];
+  faces6x2(L, H[0], H[1], H[2], i, j, k, in.has, in.Bf, in.BF);
+  in.q4 = rc[in.own];
+}
+
+template <int G>
+__device__ __forceinline__ void corr2_apply(const Nw32& p, const Corr2In& in,
+                                            float2* __restrict__ e2, float2* fst, float2* Fst,
+                                            const float2* fsrc, const float2* Fsrc) {
+  const Level& L = p.L;
+  const float efc = in.ec.x, eFc = in.ec.y;
+  float dgf, dgF;
+  const float flf = flux_lin<G>(L, p.invh, p.Dfh, p.literal, in.i, efc, in.enf, in.has, in.Bf,
+                                dgf);
+  const float flF = flux_lin<G>(L, p.invh, p.DFh, p.literal, in.i, eFc, in.enF, in.has, in.BF,
+                                dgF);
+  const Jac2 J = jac2(p, in.q4.z, in.q4.w);
+  // residuals of the correction equation at this cell
+  // (every rounding is spelled out, so that each kernel that inlines this
+  // cell computes the same bits)
+  const float rhof = __fmaf_rn(J.fF, eFc, __fmaf_rn(-J.ff, efc, __fadd_rn(in.q4.x, flf)));
+  const float rhoF = __fmaf_rn(J.Ff, efc, __fmaf_rn(-J.FF, eFc, __fadd_rn(in.q4.y, flF)));
+  // 2x2 block solve: [a  -b; -d  e] [x; y] = [rhof; rhoF]
+  const float a = __fadd_rn(J.ff, dgf), bb = J.fF, d = J.Ff, e = __fadd_rn(J.FF, dgF);
+  const float det = __fmaf_rn(a, e, -__fmul_rn(bb, d));
+  const float inv = __fdividef(1.0f, det);
+  const float nf = __fmaf_rn(__fmaf_rn(e, rhof, __fmul_rn(bb, rhoF)), inv, efc);
+  const float nF = __fmaf_rn(__fmaf_rn(d, rhof, __fmul_rn(a, rhoF)), inv, eFc);
+  e2[in.own] = make_float2(nf, nF);
+  if (fst) {
+    // last black colour of the iteration: the state becomes src + correction
+    // (src = the state itself, or the advected x* in the first iteration,
+    // which then needs no copy into the state), for this cell and for the
+    // red cell that shares its pair (2t, 2t+1), which sits at the same
+    // packed position of the other plane
+    const ix c = in.c;
+    fst[c] = df_add(fsrc[c], nf);
+    Fst[c] = df_add(Fsrc[c], nF);
+    const int ir = in.i ^ 1;
+    if (ir < L.nx) {
+      const ix cr = c - (ix)in.i + (ix)ir;
+      const float2 er = __ldg(e2 + in.oth);
+      fst[cr] = df_add(fsrc[cr], er.x);
+      Fst[cr] = df_add(Fsrc[cr], er.y);
+    }
+  }
+}
+
 template <int G>
 __device__ __forceinline__ void corr2_cell(const Nw32& p, int i, int j, int k,
                                            const __half2* const* H,
@@ -498,70 +589,9 @@ __device__ __forceinline__ void corr2_cell(const Nw32& p, int i, int j, int k,
                                            float2* __restrict__ e2, int color, int first,
                                            float2* fst, float2* Fst,
                                            const float2* fsrc, const float2* Fsrc) {
-  // the other colour's corrections are only read in this launch: read them
-  // through a separate read-only view of the array
-  const float2* __restrict__ eo = e2;
-  const Level& L = p.L;
-  const ix c = cidx32(L, i, j, k);
-  bool has[6];
-  ix nbi[6];
-  gather6<G>(L, i, j, k, c, has, nbi);
-  // the work arrays are colour-packed: own cell and the other colour's plane
-  const RBIdx rb = rb_index(L, i, j, k);
-  const ix own = (ix)color * rb.plane + rb.pos;
-  const ix oth = (ix)(1 - color) * rb.plane + rb.pos;
-  const ix sz = (ix)L.ny * rb.half;
-  nbi[0] = oth - 1 + (i & 1);
-  nbi[1] = oth + (i & 1);
-  nbi[2] = oth - rb.half;
-  nbi[3] = oth + rb.half;
-  nbi[4] = oth - sz;
-  nbi[5] = oth + sz;
-  // every cell starts at zero in the first sweep
-  const bool zero_nb = first && color == 0;
-  float enf[6], enF[6];
-#pragma unroll
-  for (int q = 0; q < 6; ++q) {
-    const float2 v = (has[q] && !zero_nb) ? __ldg(eo + nbi[q]) : make_float2(0.0f, 0.0f);
-    enf[q] = v.x;
-    enF[q] = v.y;
-  }
-  const float2 ec = first ? make_float2(0.0f, 0.0f) : e2[own];
-  const float efc = ec.x, eFc = ec.y;
-  float Bf[6], BF[6], dgf, dgF;
-  faces6x2(L, H[0], H[1], H[2], i, j, k, has, Bf, BF);
-  const float flf = flux_lin<G>(L, p.invh, p.Dfh, p.literal, i, efc, enf, has, Bf, dgf);
-  const float flF = flux_lin<G>(L, p.invh, p.DFh, p.literal, i, eFc, enF, has, BF, dgF);
-  const float4 q4 = rc[own];
-  const Jac2 J = jac2(p, q4.z, q4.w);
-  // residuals of the correction equation at this cell
-  // (every rounding is spelled out, so that each kernel that inlines this
-  // cell computes the same bits)
-  const float rhof = __fmaf_rn(J.fF, eFc, __fmaf_rn(-J.ff, efc, __fadd_rn(q4.x, flf)));
-  const float rhoF = __fmaf_rn(J.Ff, efc, __fmaf_rn(-J.FF, eFc, __fadd_rn(q4.y, flF)));
-  // 2x2 block solve: [a  -b; -d  e] [x; y] = [rhof; rhoF]
-  const float a = __fadd_rn(J.ff, dgf), bb = J.fF, d = J.Ff, e = __fadd_rn(J.FF, dgF);
-  const float det = __fmaf_rn(a, e, -__fmul_rn(bb, d));
-  const float inv = __fdividef(1.0f, det);
-  const float nf = __fmaf_rn(__fmaf_rn(e, rhof, __fmul_rn(bb, rhoF)), inv, efc);
-  const float nF = __fmaf_rn(__fmaf_rn(d, rhof, __fmul_rn(a, rhoF)), inv, eFc);
-  e2[own] = make_float2(nf, nF);
-  if (fst) {
-    // last black colour of the iteration: the state becomes src + correction
-    // (src = the state itself, or the advected x* in the first iteration,
-    // which then needs no copy into the state), for this cell and for the
-    // red cell that shares its pair (2t, 2t+1), which sits at the same
-    // packed position of the other plane
-    fst[c] = df_add(fsrc[c], nf);
-    Fst[c] = df_add(Fsrc[c], nF);
-    const int ir = i ^ 1;
-    if (ir < L.nx) {
-      const ix cr = c - (ix)i + (ix)ir;
-      const float2 er = __ldg(eo + oth);
-      fst[cr] = df_add(fsrc[cr], er.x);
-      Fst[cr] = df_add(Fsrc[cr], er.y);
-    }
-  }
+  Corr2In in;
+  corr2_load<G>(p, i, j, k, H, rc, e2, color, first, in);
+  corr2_apply<G>(p, in, e2, fst, Fst, fsrc, Fsrc);
 }
 
 // BCG update of one field at cell c: x + (-dt/V) sum of face fluxes,

@@ -78,6 +78,7 @@ struct F32Scratch {
   int* flag = nullptr;              // convergence flag, iteration, prediction kept
   bool predict = true;              // start Newton from x* + last increment
   bool redist32 = false;            // redistance in FP32 (else FP64)
+  int sweep_planes = 2;             // 3D correction sweep: planes per thread (1 or 2)
   std::vector<Mg32Level> mg;        // coarse levels of the correction's V-cycle (0 unused)
   const void* mg_faces_of = nullptr;  // drift faces the coarse faces were restricted from
   unsigned long long drift_epoch = 0, mg_epoch = ~0ull;  // rebuilds of the drift faces

@@ -34,24 +34,6 @@ __global__ void k_rbgs(Level L, Op op, const double* __restrict__ b, double* __r
   a[c] = (b[c] + sn * iv) / (op.lam[c] - sd * iv);
 }
 
-// Coarsest level: all sweeps inside one block.
-__global__ void k_coarse_solve(Level L, Op op, const double* __restrict__ b, double* a,
-                               int sweeps) {
-  const int n = (int)L.ncell();
-  for (int s = 0; s < sweeps; ++s)
-    for (int color = 0; color < 2; ++color) {
-      for (int c = threadIdx.x; c < n; c += blockDim.x) {
-        int i = c % L.nx, j = (c / L.nx) % L.ny, k = c / (L.nx * L.ny);
-        if (((i + j + k) & 1) != color) continue;
-        double sd, sn;
-        flux_terms(L, op, a, i, j, k, sd, sn);
-        double iv = 1.0 / cell_volume(L, i);
-        a[c] = (b[c] + sn * iv) / (op.lam[c] - sd * iv);
-      }
-      __syncthreads();
-    }
-}
-
 // ---------------------------------------------------------- V-cycle tail
 // The coarse levels of a V-cycle are too small to fill the GPU: each of
 // their sweeps, restrictions and prolongations would be a launch whose
@@ -96,6 +78,46 @@ __device__ void tail_smooth(const Level& L, const Op& op, const double* b, doubl
     }
 }
 
+// The coarsest level's many sweeps: from shared memory when it fits (its
+// a, b, lambda and drift faces are staged once; flux_terms reads them
+// through the same generic pointers), else from global memory.
+constexpr int kSmemCells = 512;
+constexpr int kSmemFaces = 768;   // a face array of <= 512 cells, extents >= 2
+
+__device__ void coarsest_sweeps(const Level& L, const Op& op, const double* b, double* a,
+                                int sweeps) {
+  __shared__ double sa[kSmemCells], sb[kSmemCells], sl[kSmemCells];
+  __shared__ double sB[3][kSmemFaces];
+  const int n = (int)L.ncell();
+  const int nd = L.ndim();
+  bool fits = n <= kSmemCells;
+  for (int d = 0; d < nd; ++d) fits = fits && (int)L.nface(d) <= kSmemFaces;
+  if (!fits) {
+    tail_smooth(L, op, b, a, sweeps);
+    return;
+  }
+  for (int c = threadIdx.x; c < n; c += blockDim.x) {
+    sa[c] = a[c];
+    sb[c] = b[c];
+    sl[c] = op.lam[c];
+  }
+  Op so = op;
+  so.lam = sl;
+  for (int d = 0; d < 3; ++d) {
+    if (d >= nd || !op.B[d]) {
+      so.B[d] = d < nd ? nullptr : op.B[d];
+      continue;
+    }
+    const int nf = (int)L.nface(d);
+    for (int f = threadIdx.x; f < nf; f += blockDim.x) sB[d][f] = op.B[d][f];
+    so.B[d] = sB[d];
+  }
+  __syncthreads();
+  tail_smooth(L, so, sb, sa, sweeps);
+  for (int c = threadIdx.x; c < n; c += blockDim.x) a[c] = sa[c];
+  __syncthreads();
+}
+
 __global__ void __launch_bounds__(1024) k_vcycle_tail(TailLevels T) {
   for (int t = 0; t + 1 < T.n; ++t) {
     const Level& Lf = T.L[t];
@@ -122,7 +144,7 @@ __global__ void __launch_bounds__(1024) k_vcycle_tail(TailLevels T) {
     __syncthreads();
   }
   const int last = T.n - 1;
-  tail_smooth(T.L[last], T.op[last], T.b[last], T.a[last], T.coarse_sweeps);
+  coarsest_sweeps(T.L[last], T.op[last], T.b[last], T.a[last], T.coarse_sweeps);
   for (int t = T.n - 2; t >= 0; --t) {
     const Level& Lc = T.L[t + 1];
     const Level& Lf = T.L[t];
@@ -150,6 +172,12 @@ __global__ void __launch_bounds__(1024) k_vcycle_tail(TailLevels T) {
     __syncthreads();
     tail_smooth(Lf, T.op[t], T.b[t], T.a[t], T.nu2);
   }
+}
+
+// Coarsest level alone: all sweeps inside one block.
+__global__ void __launch_bounds__(1024) k_coarse_solve(Level L, Op op, const double* __restrict__ b,
+                                                       double* a, int sweeps) {
+  coarsest_sweeps(L, op, b, a, sweeps);
 }
 
 // Volume-weighted restriction of the residual b - L(a) to the coarse grid.

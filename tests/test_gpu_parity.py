@@ -779,3 +779,28 @@ def test_fp32_multigrid_correction_when_diffusion_dominates(sfx, geom):
             assert np.abs(host(ctx.sfx_df_unpack(F)) - F_o).max() / scale < F32_TOL
             assert np.abs(host(ctx.sfx_df_unpack(f)) - f_o).max() / scale < F32_TOL
     assert iters[0] <= 20 and iters[0] * 2 < iters[1], iters
+
+
+@pytest.mark.parametrize("shape", [(24, 24, 24), (23, 20, 26), (25, 21, 22)])
+def test_sweep_planes_per_thread_bitwise(sfx, shape):
+    """Two planes per thread in the 3D correction sweep (both cells' loads
+    in flight before their arithmetic) give the same bits as one, on even
+    and odd rows and an odd plane count."""
+    import torch
+    nz, ny, nx = shape
+    g, Cf = _sphere(nx, ny, nz, 0.3)
+    ux, uy, uz = W.uniform_faces(g, (0.3, -0.2, 0.25))
+    p = W.Params(ka=2.0, kd=0.5, Df=2e-3, DF=5e-3, eps=0.75 * g.h)
+    _, phi, delta = oracle.phase_field_build(g, Cf, 24, W.redist_dtau(g), p.eps)
+    outs = []
+    for planes in (1, 2):
+        ctx = _ctx(sfx, g, 1)
+        ctx.sfx_set_tuning(sfx._lib.SFX_TUNE_SWEEP_PLANES, planes)
+        f, F = _pairs(ctx, 0.3 * delta), _pairs(ctx, 1.0 - Cf)
+        u = [dev(v, torch.float32) for v in (ux, uy, uz)]
+        for _ in range(2):
+            assert ctx.sfx_surfactant_step(p, dev(phi), f, F, 0.2 * g.h, *u,
+                                           opts=sfx.default_opts(tol=1e-10)).converged
+        torch.cuda.synchronize()
+        outs.append((f.cpu().numpy().copy(), F.cpu().numpy().copy()))
+    assert np.array_equal(outs[0][0], outs[1][0]) and np.array_equal(outs[0][1], outs[1][1])
