@@ -766,26 +766,26 @@ __global__ void __launch_bounds__(kAdvX* kAdvY)
     float4 qx = make_float4(0.0f, 0.0f, 0.0f, 0.0f), qy = qx;
     if (i <= L.nx && j < L.ny) {
       int fcx[3] = {i, j, k};
-      qx = face_flux2(A, f, F, bc_f, bc_F, 0, fcx, A.u[0][fidx(L, 0, i, j, k)], wxm);
+      qx = face_flux2(A, f, F, bc_f, bc_F, 0, fcx, A.u[0][fidx32(L, 0, i, j, k)], wxm);
     }
     if (i < L.nx && j <= L.ny) {
       int fcy[3] = {i, j, k};
-      qy = face_flux2(A, f, F, bc_f, bc_F, 1, fcy, A.u[1][fidx(L, 1, i, j, k)], wy);
+      qy = face_flux2(A, f, F, bc_f, bc_F, 1, fcy, A.u[1][fidx32(L, 1, i, j, k)], wy);
     }
     sx[ty][tx] = qx;
     sy[ty][tx] = qy;
     __syncthreads();
     if (cell) {
       float2 S1 = make_float2(0.0f, 0.0f), S2 = S1;
-      const float uxm = A.u[0][fidx(L, 0, i, j, k)], uxp = A.u[0][fidx(L, 0, i + 1, j, k)];
-      const float uym = A.u[1][fidx(L, 1, i, j, k)], uyp = A.u[1][fidx(L, 1, i, j + 1, k)];
+      const float uxm = A.u[0][fidx32(L, 0, i, j, k)], uxp = A.u[0][fidx32(L, 0, i + 1, j, k)];
+      const float uym = A.u[1][fidx32(L, 1, i, j, k)], uyp = A.u[1][fidx32(L, 1, i, j + 1, k)];
       if (uxm != 0.0f) acc_face(S1, S2, sx[ty][tx], false);
       if (uxp != 0.0f) acc_face(S1, S2, sx[ty][tx + 1], true);
       if (uym != 0.0f) acc_face(S1, S2, sy[ty][tx], false);
       if (uyp != 0.0f) acc_face(S1, S2, sy[ty + 1][tx], true);
       if (is3d) {
         int fcz[3] = {i, j, k + 1};
-        const float uzp = A.u[2][fidx(L, 2, i, j, k + 1)];
+        const float uzp = A.u[2][fidx32(L, 2, i, j, k + 1)];
         const float4 zp = face_flux2(A, f, F, bc_f, bc_F, 2, fcz, uzp, 1.0f);
         if (uzm != 0.0f) acc_face(S1, S2, zm, false);
         if (uzp != 0.0f) acc_face(S1, S2, zp, true);

@@ -366,6 +366,20 @@ __device__ float face32v(const Adv32& A, const float2* __restrict__ x, float bc_
 // face32v for two fields at once: the upwind cell, its index and the
 // transverse velocities are shared; each field's arithmetic is that of
 // face32v.
+// Neighbour value along d with a zero-gradient copy at walls, 32-bit
+// indices (SFX_F32 grids stay below 2^31 faces).
+__device__ __forceinline__ float vnb32(const Level& L, const float2* __restrict__ x, const int* uc,
+                                       ix U, int d, int s) {
+  const int p = uc[d] + s;
+  if (p < 0 || p >= L.extent(d)) return df_val(x[U]);
+  const ix stride = d == 0 ? 1u : (d == 1 ? (ix)L.nx : (ix)L.nx * (ix)L.ny);
+  return df_val(s > 0 ? x[U + stride] : x[U - stride]);
+}
+__device__ __forceinline__ ix fidx32(const Level& L, int d, int i, int j, int k) {
+  const ix fx = (ix)(L.nx + (d == 0)), fy = (ix)(L.ny + (d == 1));
+  return ((ix)k * fy + (ix)j) * fx + (ix)i;
+}
+
 __device__ __forceinline__ void face32v2(const Adv32& A, const float2* __restrict__ x1,
                                          const float2* __restrict__ x2, float bc1, float bc2,
                                          int d, const int* f, float u, float& v1, float& v2) {
@@ -379,20 +393,20 @@ __device__ __forceinline__ void face32v2(const Adv32& A, const float2* __restric
     v2 = bc2;
     return;
   }
-  const size_t U = cidx(L, uc[0], uc[1], uc[2]);
+  const ix U = cidx32(L, uc[0], uc[1], uc[2]);
   const float a1 = df_val(x1[U]), a2 = df_val(x2[U]);
   const float cfl = 0.5f * ((u > 0.0f ? 1.0f : -1.0f) - u * A.dt * A.invh);
-  v1 = a1 + cfl * mc32(vnb(L, x1, uc, U, d, -1), a1, vnb(L, x1, uc, U, d, +1));
-  v2 = a2 + cfl * mc32(vnb(L, x2, uc, U, d, -1), a2, vnb(L, x2, uc, U, d, +1));
+  v1 = a1 + cfl * mc32(vnb32(L, x1, uc, U, d, -1), a1, vnb32(L, x1, uc, U, d, +1));
+  v2 = a2 + cfl * mc32(vnb32(L, x2, uc, U, d, -1), a2, vnb32(L, x2, uc, U, d, +1));
   for (int t = 0; t < L.ndim(); ++t) {
     if (t == d) continue;
     int ap[3] = {uc[0], uc[1], uc[2]};
     ap[t] += 1;
-    const float vbar = 0.5f * (A.u[t][fidx(L, t, uc[0], uc[1], uc[2])] +
-                               A.u[t][fidx(L, t, ap[0], ap[1], ap[2])]);
+    const float vbar = 0.5f * (A.u[t][fidx32(L, t, uc[0], uc[1], uc[2])] +
+                               A.u[t][fidx32(L, t, ap[0], ap[1], ap[2])]);
     const bool up = vbar > 0.0f;
-    const float d1 = up ? a1 - vnb(L, x1, uc, U, t, -1) : vnb(L, x1, uc, U, t, +1) - a1;
-    const float d2 = up ? a2 - vnb(L, x2, uc, U, t, -1) : vnb(L, x2, uc, U, t, +1) - a2;
+    const float d1 = up ? a1 - vnb32(L, x1, uc, U, t, -1) : vnb32(L, x1, uc, U, t, +1) - a1;
+    const float d2 = up ? a2 - vnb32(L, x2, uc, U, t, -1) : vnb32(L, x2, uc, U, t, +1) - a2;
     v1 -= 0.5f * A.dt * vbar * d1 * A.invh;
     v2 -= 0.5f * A.dt * vbar * d2 * A.invh;
   }

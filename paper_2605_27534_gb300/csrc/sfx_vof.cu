@@ -74,12 +74,16 @@ __global__ void k_vof_update(Level L, int d, const U* __restrict__ u, double dt_
   }
 }
 
-// (x chunks of up to 256 threads, row groups) for an x extent and a row count
+// (x chunks of up to 256 threads, row groups) for an x extent and a row count.
+// One row per block where the grid allows it (up to 65535 row groups): a
+// face or cell costs a few dependent loads, so the kernels are bound by
+// latency, and a thread that walked ~50 rows in turn (8 blocks per SM)
+// left the 256^3 flux pass at 11 % of DRAM bandwidth.
 void rows_launch(int nxl, long long rows, dim3& grid, dim3& block) {
   const int tx = nxl >= 256 ? 256 : ((nxl + 31) / 32) * 32;
   const unsigned xb = (unsigned)((nxl + tx - 1) / tx);
   block = dim3(tx);
-  grid = dim3(xb, (unsigned)std::min(rows, std::min(std::max(1LL, 152LL * 8 / xb), 65535LL)));
+  grid = dim3(xb, (unsigned)std::min(std::max(rows, 1LL), 65535LL));
 }
 
 template <typename U, typename G>
