@@ -813,19 +813,36 @@ __global__ void __launch_bounds__(kAdvX* kAdvY)
 __global__ void k_total32_partials(Level L, const float2* __restrict__ x, int fi,
                                    double* __restrict__ partials) {
   const size_t n = L.ncell();
-  float2 acc = make_float2(0.0f, 0.0f);
-  for (size_t c = blockIdx.x * (size_t)blockDim.x + threadIdx.x; c < n;
-       c += (size_t)gridDim.x * blockDim.x) {
-    float2 v = x[c];
-    if (L.geom == SFX_AXISYM) {
-      float w = 2.0f * (float)(c % L.nx) + 1.0f;
-      float p = v.x * w;
-      float e = fmaf(v.x, w, -p);               // exact product error
-      v = make_float2(p, e + v.y * w);
+  // four independent pair accumulators: four loads in flight per thread
+  float2 acc[4] = {make_float2(0.0f, 0.0f), make_float2(0.0f, 0.0f), make_float2(0.0f, 0.0f),
+                   make_float2(0.0f, 0.0f)};
+  const size_t step = (size_t)gridDim.x * blockDim.x;
+  size_t c = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  for (; c < n; c += 4 * step) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const size_t cq = c + (size_t)q * step;
+      if (cq >= n) break;
+      float2 v = x[cq];
+      if (L.geom == SFX_AXISYM) {
+        float w = 2.0f * (float)(cq % L.nx) + 1.0f;
+        float p = v.x * w;
+        float e = fmaf(v.x, w, -p);               // exact product error
+        v = make_float2(p, e + v.y * w);
+      }
+      acc[q] = df_add2(acc[q], v);
     }
-    acc = df_add2(acc, v);
   }
-  double s = (double)acc.x, cc = (double)acc.y;
+  // each pair is exact in FP64 (hi + lo spans < 53 bits); the four are
+  // combined by compensated FP64 sums, then reduced across threads
+  double s = (double)acc[0].x + (double)acc[0].y, cc = 0.0;
+#pragma unroll
+  for (int q = 1; q < 4; ++q) {
+    double t, e;
+    two_sum(s, (double)acc[q].x + (double)acc[q].y, t, e);
+    s = t;
+    cc += e;
+  }
   warp_sum_comp(s, cc);
   __shared__ double ss[8], sc[8];
   int w = threadIdx.x >> 5;

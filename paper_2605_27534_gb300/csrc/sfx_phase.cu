@@ -195,7 +195,10 @@ sfx_status phase_field_build(sfx_ctx* c, const double* C, double* chi, void* phi
   const int tx = L.nx >= 256 ? 256 : ((L.nx + 31) / 32) * 32;
   const unsigned xb = (unsigned)((L.nx + tx - 1) / tx);
   const long long rows = (long long)L.ny * L.nz;
-  const unsigned yb = (unsigned)std::min(rows, std::min(std::max(1LL, 152LL * 8 / xb), 65535LL));
+  // one row per block where the grid allows it: a redistancing step is a
+  // short chain of dependent loads per cell, bound by latency (at 256^3 an
+  // FP64 step took 2.7 ms with ~50 rows walked in turn per thread)
+  const unsigned yb = (unsigned)std::min(std::max(rows, 1LL), 65535LL);
   if (c->prec == SFX_F32 && c->f32.redist32) {
     if (!c->chi32) {
       SFX_CUDA(cudaMalloc((void**)&c->chi32, 3 * n * sizeof(float)));

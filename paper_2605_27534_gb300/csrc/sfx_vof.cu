@@ -39,16 +39,24 @@ __global__ void k_vof_flux(Level L, int d, const double* __restrict__ C,
     const int j = (int)(r % (unsigned)fy), k = (int)(r / (unsigned)fy);
     const unsigned f = r * (unsigned)fx + (unsigned)i;
     const int pos = d == 0 ? i : (d == 1 ? j : k);
-    const double cf = (double)u[f] * dt_h;
-    if (pos == 0 || pos == L.extent(d) || cf == 0.0) {
+    if (pos == 0 || pos == L.extent(d)) {
       Q[f] = 0.0;
       continue;
     }
-    // upwind cell: the one behind the face along the flow
+    // upwind cell: the one behind the face along the flow; both candidates
+    // are loaded with u (independent of its sign), so the face costs one
+    // round of loads rather than u and then C
+    const double cf = (double)u[f] * dt_h;
+    const double cm = C[cidx(L, i - (d == 0), j - (d == 1), k - (d == 2))];
+    const double cq = C[cidx(L, i, j, k)];
+    if (cf == 0.0) {
+      Q[f] = 0.0;
+      continue;
+    }
     const int ui = (cf > 0.0 && d == 0) ? i - 1 : i;
     const int uj = (cf > 0.0 && d == 1) ? j - 1 : j;
     const int uk = (cf > 0.0 && d == 2) ? k - 1 : k;
-    const double cu = C[cidx(L, ui, uj, uk)];
+    const double cu = cf > 0.0 ? cm : cq;
     G m[3] = {G(0), G(0), G(0)};
     if (cu > 0.0 && cu < 1.0) youngs_normal(L, C, ui, uj, uk, m);   // empty/full: no plane
     const G cg = (G)cu;
