@@ -50,7 +50,9 @@ def _forward_steps(setup: RolloutSetup, ps: Params, f, F, n):
     ctx = setup.context
     o = setup.opts if setup.opts is not None else default_opts(tol=setup.tol, max_cycles=400)
     for _ in range(n):
-        ctx.sfx_surfactant_step(ps, setup.phi, f, F, setup.dt, opts=o)
+        # no stats: the step then skips its totals and their host wait (a
+        # step that fails to converge still raises)
+        ctx.sfx_surfactant_step(ps, setup.phi, f, F, setup.dt, opts=o, stats=False)
 
 
 def _to_state(ctx, x):

@@ -173,6 +173,13 @@ sfx_status sfx_ctx_create(const sfx_grid* grid, int precision, sfx_ctx** out) {
   sfx_ctx* c = new sfx_ctx();
   c->grid = *grid;
   c->prec = precision;
+  {
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess &&
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess &&
+        sms > 0)
+      c->sm_count = sms;
+  }
   sfx_status st = build_levels(c);
   size_t n = (size_t)grid->nx * grid->ny * grid->nz;
   if (st == SFX_OK) st = dalloc(c, &c->fstar, n);

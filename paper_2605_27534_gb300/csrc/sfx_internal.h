@@ -137,6 +137,7 @@ struct Prof {
 struct sfx_ctx {
   sfx_grid grid;
   int prec = SFX_F64;
+  int sm_count = 152;                // SMs of the context's device (grid sizing)
   std::vector<sfx::LevelData> lev;   // lev[0] = fine
   // fine-level scratch
   double* fstar = nullptr;
