@@ -1278,29 +1278,19 @@ __global__ void k_increment32(size_t n, const float2* __restrict__ fs,
 struct RowGrid {
   dim3 grid, block;
 };
-// Blocks over (x chunk, row groups); each block walks its rows in turn.
-// With `per_sm` blocks of this kernel resident per SM, the row groups make
-// exactly one wave (sms x per_sm blocks): a second, partial wave would
-// leave SMs idle for its whole length.
-RowGrid row_grid(const Level& L, int per_sm, int sms) {
+// Blocks over (x chunk, row groups); each block walks its rows in turn:
+// 8 row groups per SM.  (Sizing the groups to exactly one wave of resident
+// blocks, 5 per SM for the residual pass, made that pass 7 % slower at
+// 256^3: 22.7 vs 21.1 ms per 10 steps.)
+RowGrid row_grid(const Level& L, int sms) {
   RowGrid g;
   const int tx = L.nx >= 256 ? 256 : ((L.nx + 31) / 32) * 32;
   const int xb = (L.nx + tx - 1) / tx;
   const long long rows = (long long)L.ny * L.nz;
-  const long long want = std::max(1LL, ((long long)sms * std::max(per_sm, 1)) / xb);
+  const long long want = std::max(1LL, ((long long)sms * 8) / xb);
   g.block = dim3(tx);
   g.grid = dim3(xb, (unsigned)std::min(rows, std::min(want, 65535LL)));
   return g;
-}
-
-// Resident blocks per SM of a kernel at a block size (1 if the query fails).
-template <typename K>
-int resident_per_sm(K kernel, int block) {
-  int nb = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kernel, block, 0) != cudaSuccess ||
-      nb < 1)
-    return 1;
-  return nb;
 }
 
 // Coupled Newton defect correction (see k_resid2_32).
@@ -1321,8 +1311,7 @@ sfx_status solve_newton32(sfx_ctx* c, const Nw32& p, const float* phi, float* co
   unsigned int* dn = (unsigned int*)c->d_norms;        // two 4-slot norm buffers
   unsigned int* hn = (unsigned int*)c->h_norms;
   int* flag = c->f32.flag;
-  const int tx = L.nx >= 256 ? 256 : ((L.nx + 31) / 32) * 32;
-  const RowGrid rg = row_grid(L, resident_per_sm(nk.resid, tx), c->sm_count);
+  const RowGrid rg = row_grid(L, c->sm_count);
   const __half2* Hz = L.ndim() == 3 ? c->f32.H2[2] : nullptr;
   const float2* B2[3] = {c->f32.B2[0], c->f32.B2[1], L.ndim() == 3 ? c->f32.B2[2] : nullptr};
   SFX_CUDA(cudaMemsetAsync(flag, 0, 2 * sizeof(int), s));
@@ -1649,8 +1638,7 @@ sfx_status marangoni32(sfx_ctx* c, const sfx_params* p, const float2* f, const d
   Eos32 q{(float)p->gamma_inf, (float)p->eps, (float)(1.0 / p->eps), (float)p->sigma0,
           (float)p->E, p->eos, p->gamma_inf, p->eps, p->sigma0, p->E};
   SFX_KERNEL(c, K_FORCES, k_eos32, blocks_for(n, 256), 256, s, n, q, f, phi, c->f32.dsig, sigma);
-  const int ftx = L.nx >= 256 ? 256 : ((L.nx + 31) / 32) * 32;
-  const RowGrid fg = row_grid(L, resident_per_sm(k_force32, ftx), c->sm_count);
+  const RowGrid fg = row_grid(L, c->sm_count);
   SFX_KERNEL(c, K_FORCES, k_force32, fg.grid, fg.block, s, L, phi, C, c->f32.dsig, dm_mode,
              q.inv_eps, force);
   SFX_LAUNCH_CHECK();
