@@ -46,9 +46,9 @@ NOMINAL_HBM_GBS = 7900.0   # GB300 HBM3e nominal bandwidth (context beside the m
 # withdrawn (None) as soon as those sources differ from the captured ones.
 NCU_TRAFFIC = {
     ("smooth_fine", "f32", 3): {
-        "bytes_per_cell": (6 * 139.60e6 + 240.32e6) / 7 / 160 ** 3,
+        "bytes_per_cell": (6 * 121.15e6 + 229.80e6) / 7 / 160 ** 3,
         "sources": ["sfx_f32.cu", "sfx_f32_dev.cuh", "sfx_df.cuh", "sfx_common.cuh"],
-        "sha256_16": "d47d984788153cf0",
+        "sha256_16": "af386d92668a4e79",
         "capture": "profiles/corr2_hr3d160_f32.md (160^3, launches 5-7, weighted 6:1 as in an "
                    "iteration of 4 sweeps), scaled by the cell count",
     },
