@@ -45,12 +45,13 @@ NOMINAL_HBM_GBS = 7900.0   # GB300 HBM3e nominal bandwidth (context beside the m
 # kernel was built from: scaled by the cell count to the timed grid, and
 # withdrawn (None) as soon as those sources differ from the captured ones.
 NCU_TRAFFIC = {
-    ("smooth_fine", "f32", 3): {
-        "bytes_per_cell": (6 * 121.15e6 + 229.80e6) / 7 / 160 ** 3,
-        "sources": ["sfx_f32.cu", "sfx_f32_dev.cuh", "sfx_df.cuh", "sfx_common.cuh"],
-        "sha256_16": "af386d92668a4e79",
-        "capture": "profiles/corr2_hr3d160_f32.md (160^3, launches 5-7, weighted 6:1 as in an "
-                   "iteration of 4 sweeps), scaled by the cell count",
+    ("smooth_tiled", "f32", 3): {
+        "bytes_per_cell": (234.61e6 + 40.95e6) / 192 ** 3,
+        "sources": ["sfx_tiled.cuh", "sfx_f32_dev.cuh", "sfx_f32.cu", "sfx_df.cuh",
+                    "sfx_common.cuh"],
+        "sha256_16": "2bb5896041f3ea92",
+        "capture": "profiles/corr2_tiled_hr3d192_f32.md (192^3, one launch), scaled by the "
+                   "cell count",
     },
 }
 
@@ -105,6 +106,11 @@ def parse():
     ap.add_argument("--sweep-planes", type=int, default=2, choices=[1, 2],
                     help="FP32 3D: z-planes per thread of the correction sweep "
                          "(SFX_TUNE_SWEEP_PLANES)")
+    ap.add_argument("--tiled", type=int, default=1, choices=[0, 1],
+                    help="FP32 3D: whole red-black sweeps as tiled launches "
+                         "(SFX_TUNE_TILED_SWEEP)")
+    ap.add_argument("--tiled-zchunk", type=int, default=32,
+                    help="z-planes per block of the tiled sweep (SFX_TUNE_TILED_ZCHUNK)")
     ap.add_argument("--predict", action="store_true",
                     help="FP32: start each Newton solve from x* plus the last increment "
                          "(SFX_TUNE_PREDICT 1; no gain on the 3D workload)")
@@ -139,7 +145,7 @@ def job_rate(units_per_rank, world, ms):
     return units_per_rank * world / (ms * 1e-3)
 
 
-def algorithmic_bytes(kind, grid, wbytes, sweeps=3):
+def algorithmic_bytes(kind, grid, wbytes, sweeps=3, tiled=False):
     """Unique global bytes one launch of `kind` moves on the fine grid in
     this design (reads + writes of the state and of the solver's own work
     arrays; arrays touched by half the cells count half).  N cells, d
@@ -160,7 +166,15 @@ def algorithmic_bytes(kind, grid, wbytes, sweeps=3):
         # also reads and writes the state (32 B), averaged here over the
         # 2 x sweeps - 1 colour launches (the residual pass does the first
         # red half-sweep)
-        return (8.0 + 8.0 + 4.0 * d + 4.0 + 32.0 / (2 * sweeps - 1)) * N
+        # (with the tiled sweep every colour launch is the applying one)
+        return (8.0 + 8.0 + 4.0 * d + 4.0 + (32.0 if tiled else 32.0 / (2 * sweeps - 1))) * N
+    if kind == "smooth_tiled":
+        # k_corr2_tiled, one whole sweep: the old corrections of the colour
+        # updated second (4 B: the other colour's old values are not read),
+        # the float4 of both colours (16 B), the d colour-packed half drift
+        # arrays (4 B each), write both corrections (8 B); the staged rings
+        # (halo) are re-reads, not counted
+        return (4.0 + 16.0 + 4.0 * d + 8.0) * N
     if kind == "residual" and wbytes == 4:
         # k_resid2_32: f, F, f*, F* (pairs), phi, 2 d float faces; writes the
         # residuals and exchange Jacobian (float4) and the red half of both
@@ -178,7 +192,8 @@ def method_bytes(kind, grid, s):
       a smoother sweep of one field reads its iterate, the right-hand side,
         the coupling field and phi and writes the iterate: 5 s N; a colour
         launch of the coupled two-field sweep does half a sweep of both
-        fields: 5 s N; an FP64 colour sweep of one field: 2.5 s N;
+        fields: 5 s N, a tiled launch a whole sweep: 10 s N; an FP64 colour
+        sweep of one field: 2.5 s N;
       a residual evaluation of one field: 5 s N (the FP32 pass evaluates
         both: 10 s N);
       advection of f and F: read both and the d face velocities, write
@@ -187,6 +202,8 @@ def method_bytes(kind, grid, s):
     N, d = grid.ncell, grid.ndim
     if kind == "smooth_fine":
         return (5.0 if s == 4 else 2.5) * s * N
+    if kind == "smooth_tiled":
+        return 10.0 * s * N         # a whole sweep of both fields
     if kind == "residual":
         return (10.0 if s == 4 else 5.0) * s * N
     if kind == "advect":
@@ -434,6 +451,8 @@ def run_gpu(a, case, rank, world, local_rank):
         ctx.sfx_set_tuning(sfx._lib.SFX_TUNE_REUSE_DRIFT, 1)   # the interface is static
         ctx.sfx_set_tuning(sfx._lib.SFX_TUNE_PREDICT, 1 if a.predict else 0)
         ctx.sfx_set_tuning(sfx._lib.SFX_TUNE_SWEEP_PLANES, a.sweep_planes)
+        ctx.sfx_set_tuning(sfx._lib.SFX_TUNE_TILED_SWEEP, a.tiled)
+        ctx.sfx_set_tuning(sfx._lib.SFX_TUNE_TILED_ZCHUNK, a.tiled_zchunk)
     stats = []
 
     def step():
@@ -504,12 +523,18 @@ def run_gpu(a, case, rank, world, local_rank):
     # start adds one residual pass, not counted here), so they are counted
     # from the iterations, not from the launch counter
     working = {}
+    tiled = prof.get("smooth_tiled", (0, 0, 0))[0] > 0
     if prec == sfx.SFX_F32 and nt == nl:
         timed = stats[-a.steps:]
-        working["smooth_fine"] = sum((k - 1 if cv else k) * (2 * sw - 1)
-                                     for k, *_, cv in timed)
+        iters = sum((k - 1 if cv else k) for k, *_, cv in timed)
+        if tiled:
+            # sweeps 1 .. S-1 tiled, the last black colour as a colour launch
+            working["smooth_tiled"] = iters * (sw - 1)
+            working["smooth_fine"] = iters
+        else:
+            working["smooth_fine"] = iters * (2 * sw - 1)
         working["residual"] = sum(k for k, *_ in timed)
-    ab = algorithmic_bytes(kind, g, wbytes, sw)
+    ab = algorithmic_bytes(kind, g, wbytes, sw, tiled)
     mb = method_bytes(kind, g, wbytes)
     nwork = working.get(kind, nt)
     if mb is not None and nwork > 0:
@@ -537,7 +562,7 @@ def run_gpu(a, case, rank, world, local_rank):
         if not v[0]:
             continue
         e = {"launches": v[0], "ms": round(v[1], 3)}
-        b = algorithmic_bytes(k, g, wbytes, sw)
+        b = algorithmic_bytes(k, g, wbytes, sw, tiled)
         m = method_bytes(k, g, wbytes)
         nw = working.get(k, v[2])
         if k in working:
@@ -548,6 +573,7 @@ def run_gpu(a, case, rank, world, local_rank):
             nw_m = nw
         if m is not None and nw > 0:
             e["method_gbs"] = round(m / (v[1] * 1e-3 / nw) / 1e9, 1)
+            e["method_frac"] = round(e["method_gbs"] / peaks["hbm_gbs"], 3)
             step_method += m * nw_m
         if b is not None and nw > 0:
             e["design_gbs"] = round(b / (v[1] * 1e-3 / nw) / 1e9, 1)
@@ -609,6 +635,8 @@ def run_gpu(a, case, rank, world, local_rank):
                                "dt=%g, tol=%g" % (case.name, g.nx, case.dt, a.tol),
                    "cells": g.ncell, "precision": a.precision,
                    "newton_start": "x* + last increment" if a.predict else "x*",
+                   "sweeps": "tiled (whole sweep per launch, zchunk %d)" % a.tiled_zchunk
+                             if (a.tiled and prec == sfx.SFX_F32) else "one launch per colour",
                    "l2": "inputs larger than L2 (state + coefficients %.2f GB)" % (
                        g.ncell * 8 * 20 / 1e9),
                    "parallelism": "replicas%d" % world,

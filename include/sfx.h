@@ -351,6 +351,18 @@ typedef enum {
                                (default: two independent cells' loads in
                                flight per thread; 5 % faster at 256^3).
                                Bitwise equal. */
+  SFX_TUNE_TILED_SWEEP = 6, /* SFX_F32 Newton solver, 3D grids with nx a
+                               multiple of 4, relaxation without the V-cycle
+                               (mg_levels < 2): 1 (default) = sweeps 1 .. S-1
+                               of an iteration as one launch each (black,
+                               then red), marching through z-planes staged in
+                               shared memory by tensor copies, the last black
+                               colour as a colour launch; 0 = one launch per
+                               colour.  Bitwise equal.  A staging wait that
+                               gives up (after 1 s) ends the step with
+                               SFX_ERR_TIMEOUT. */
+  SFX_TUNE_TILED_ZCHUNK = 7, /* z-planes per block of the tiled sweep, 4 ..
+                               4096 (default 32). */
   SFX_TUNE_PREDICT = 3      /* SFX_F32 Newton solver: 1 (default) = start
                                the iteration from x* plus the previous
                                step's implicit increment x - x* when the
@@ -510,6 +522,7 @@ typedef enum {
   SFX_K_FORCES,           /* EOS and Marangoni force */
   SFX_K_PHASE,            /* redistancing and phase field */
   SFX_K_OTHER,
+  SFX_K_SMOOTH_TILED,     /* tiled red-black sweep (both colours), fine level */
   SFX_K_COUNT
 } sfx_kernel_kind;
 

@@ -34,8 +34,10 @@ SFX_TUNE_REUSE_DRIFT = 2
 SFX_TUNE_PREDICT = 3
 SFX_TUNE_F32_REDIST = 4
 SFX_TUNE_SWEEP_PLANES = 5
+SFX_TUNE_TILED_SWEEP = 6
+SFX_TUNE_TILED_ZCHUNK = 7
 KERNEL_KINDS = ["smooth_fine", "smooth_coarse", "restrict", "prolong", "setup", "residual",
-                "advect", "totals", "forces", "phase", "other"]
+                "advect", "totals", "forces", "phase", "other", "smooth_tiled"]
 
 
 class Grid(C.Structure):

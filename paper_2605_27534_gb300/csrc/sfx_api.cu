@@ -383,6 +383,14 @@ sfx_status sfx_set_tuning(sfx_ctx* c, int key, int value) {
     c->f32.sweep_planes = value;
     return SFX_OK;
   }
+  if (key == SFX_TUNE_TILED_SWEEP && (value == 0 || value == 1)) {
+    c->f32.tiled = value == 1;
+    return SFX_OK;
+  }
+  if (key == SFX_TUNE_TILED_ZCHUNK && value >= 4 && value <= 4096) {
+    c->f32.tiled_zchunk = value;
+    return SFX_OK;
+  }
   if (key == SFX_TUNE_F32_REDIST && (value == 0 || value == 1)) {
     c->f32.redist32 = value == 1;
     return SFX_OK;

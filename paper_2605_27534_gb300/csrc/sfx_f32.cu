@@ -34,13 +34,19 @@
 #include "sfx_df.cuh"
 #include "sfx_f32_dev.cuh"
 #include "sfx_internal.h"
+#include "sfx_tiled.cuh"
 
 namespace sfx {
 namespace {
 
+// Drift faces of direction d in float (Bf, BF, B2) and half (H2) precision;
+// Hm (may be null): the half pair again, at the colour-packed position of
+// the cell whose minus side the face is (the layout of the tiled sweep,
+// nx even; the far wall's faces have no such cell and are not kept).
 __global__ void k_drift32(Level L, int d, const double* __restrict__ phi, float Df, float DF,
                           float inv_eps, float* __restrict__ Bf, float* __restrict__ BF,
-                          float2* __restrict__ B2, __half2* __restrict__ H2) {
+                          float2* __restrict__ B2, __half2* __restrict__ H2,
+                          __half2* __restrict__ Hm) {
   size_t n = L.nface(d);
   int fx = L.nx + (d == 0), fy = L.ny + (d == 1);
   for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < n;
@@ -58,7 +64,13 @@ __global__ void k_drift32(Level L, int d, const double* __restrict__ phi, float 
     Bf[q] = bf;
     BF[q] = bF;
     B2[q] = make_float2(bf, bF);
-    H2[q] = __floats2half2_rn(bf, bF);
+    const __half2 hv = __floats2half2_rn(bf, bF);
+    H2[q] = hv;
+    if (Hm && pos < L.extent(d)) {
+      const size_t half = (size_t)(L.nx >> 1);
+      Hm[(size_t)((i + j + k) & 1) * half * L.ny * L.nz + ((size_t)k * L.ny + j) * half + (i >> 1)] =
+          hv;
+    }
   }
 }
 
@@ -1201,9 +1213,16 @@ sfx_status solve_dc32(sfx_ctx* c, const Nl32& pf, const Nl32& pF, const float* p
 // Convergence test of one Newton iteration on the device: once both
 // relative residuals pass, `flag[0]` stops every later launch of the solve
 // and flag[1] records the iteration.
-__global__ void k_flag32(const unsigned int* __restrict__ nrm, float tol, int it,
+// A tiled sweep of the previous iteration that gave up waiting for its
+// staged planes (flag[3]) marks the norms with kTimeoutBits instead.
+constexpr unsigned int kTimeoutBits = 0xffffffffu;
+__global__ void k_flag32(unsigned int* __restrict__ nrm, float tol, int it,
                          int* __restrict__ flag) {
   if (threadIdx.x != 0 || flag[0]) return;
+  if (flag[3]) {
+    nrm[1] = nrm[3] = kTimeoutBits;
+    return;
+  }
   const float rf = __uint_as_float(nrm[0]), bf = __uint_as_float(nrm[1]);
   const float rF = __uint_as_float(nrm[2]), bF = __uint_as_float(nrm[3]);
   if (rf <= tol * bf && rF <= tol * bF) {
@@ -1314,7 +1333,15 @@ sfx_status solve_newton32(sfx_ctx* c, const Nw32& p, const float* phi, float* co
   const RowGrid rg = row_grid(L, c->sm_count);
   const __half2* Hz = L.ndim() == 3 ? c->f32.H2[2] : nullptr;
   const float2* B2[3] = {c->f32.B2[0], c->f32.B2[1], L.ndim() == 3 ? c->f32.B2[2] : nullptr};
-  SFX_CUDA(cudaMemsetAsync(flag, 0, 2 * sizeof(int), s));
+  SFX_CUDA(cudaMemsetAsync(flag, 0, 4 * sizeof(int), s));
+  // sweeps 1 .. S-1 (black, then red) as tiled launches where the grid
+  // allows, the last black colour as a colour launch that adds the
+  // corrections to the state
+  bool tiled = mgl < 2 && sweeps >= 2 && c->f32.tiled && tiled_sweep_eligible(L);
+  if (tiled) {
+    const sfx_status ts = tiled_sweep_prepare(c);
+    if (ts != SFX_OK) return ts;
+  }
   // Each iteration: the residual pass (which also does the first red
   // half-sweep of the correction, from zero), a device-side convergence
   // test, then the rest of the red-black sweeps, the last black one adding
@@ -1368,6 +1395,14 @@ sfx_status solve_newton32(sfx_ctx* c, const Nw32& p, const float* phi, float* co
                      c->f32.rc, c->f32.e2, color, 0, apply ? fc : nullptr, apply ? Fc : nullptr,
                      fsrc, Fsrc, flag);
         }
+    } else if (tiled) {
+      int in = 0;   // the residual pass wrote the first red half-sweep into e2
+      for (int q = 0; q + 1 < sweeps; ++q, in ^= 1) {
+        const sfx_status ts = tiled_sweep(c, p, in, flag, s);
+        if (ts != SFX_OK) return ts;
+      }
+      SFX_KERNEL(c, K_SMOOTH_FINE, nk.corr, grd, blk, s, p, c->f32.H2[0], c->f32.H2[1], Hz,
+                 c->f32.rc, in == 0 ? c->f32.e2 : c->f32.e2b, 1, 0, fc, Fc, fsrc, Fsrc, flag);
     } else {
       for (int q = 0; q < sweeps; ++q)
         for (int color = (q == 0 ? 1 : 0); color < 2; ++color) {
@@ -1381,6 +1416,7 @@ sfx_status solve_newton32(sfx_ctx* c, const Nw32& p, const float* phi, float* co
     const int prev = it - 1;
     if (prev >= 1) {
       SFX_CUDA(cudaEventSynchronize(c->f32.ev[prev & 1]));
+      if (hn[4 * (prev & 1) + 1] == kTimeoutBits) return SFX_ERR_TIMEOUT;
       memcpy(nrm, hn + 4 * (prev & 1), 4 * sizeof(float));
       for (int q = 0; q < 4; ++q)
         if (!std::isfinite(nrm[q])) return SFX_ERR_NONFINITE;
@@ -1400,6 +1436,12 @@ sfx_status solve_newton32(sfx_ctx* c, const Nw32& p, const float* phi, float* co
     // the last iteration's residuals
     SFX_CUDA(cudaStreamSynchronize(s));
     const int last = std::min(it, o->max_cycles);
+    if (hn[4 * (last & 1) + 1] == kTimeoutBits) return SFX_ERR_TIMEOUT;
+    if (tiled) {
+      int err = 0;
+      SFX_CUDA(cudaMemcpy(&err, flag + 3, sizeof(int), cudaMemcpyDeviceToHost));
+      if (err) return SFX_ERR_TIMEOUT;
+    }
     memcpy(nrm, hn + 4 * (last & 1), 4 * sizeof(float));
     for (int q = 0; q < 4; ++q)
       if (!std::isfinite(nrm[q])) return SFX_ERR_NONFINITE;
@@ -1432,7 +1474,7 @@ sfx_status step_f32(sfx_ctx* c, const sfx_params* pr, const double* phi_in, cons
     for (int d = 0; d < nd; ++d)
       SFX_KERNEL(c, K_SETUP, k_drift32, blocks_for(L.nface(d), 256), 256, s, L, d, phi_in,
                  (float)pr->Df, (float)pr->DF, (float)(1.0 / pr->eps), Bf[d], BF[d],
-                 c->f32.B2[d], c->f32.H2[d]);
+                 c->f32.B2[d], c->f32.H2[d], c->f32.Hm[d]);
     SFX_LAUNCH_CHECK();
     ++c->f32.drift_epoch;
     c->f32.drift_phi = phi_in;
@@ -1691,6 +1733,11 @@ sfx_status f32_ensure_scratch(sfx_ctx* c) {
     if ((st = get(np * sizeof(float), (void**)q)) != SFX_OK) return st;
   if ((st = get(np * sizeof(float2), (void**)&c->f32.e2)) != SFX_OK) return st;
   if ((st = get(np * sizeof(float4), (void**)&c->f32.rc)) != SFX_OK) return st;
+  if (tiled_sweep_eligible(L)) {
+    if ((st = get(np * sizeof(float2), (void**)&c->f32.e2b)) != SFX_OK) return st;
+    for (int d = 0; d < 3; ++d)
+      if ((st = get(n * sizeof(__half2), (void**)&c->f32.Hm[d])) != SFX_OK) return st;
+  }
   for (int q = 0; q < 2; ++q) SFX_CUDA(cudaEventCreateWithFlags(&c->f32.ev[q], cudaEventDisableTiming));
   c->f32.ready = true;
   return SFX_OK;

@@ -553,29 +553,99 @@ __device__ __forceinline__ void corr2_load(const Nw32& p, int i, int j, int k,
   in.q4 = rc[in.own];
 }
 
+// The block Gauss-Seidel update of one cell's correction (e_f, e_F) from
+// its flux sums (flf, flF), their diagonal weights (dgf, dgF) and its
+// (r_f, r_F, u, v).  Every rounding is spelled out, so that each kernel
+// that inlines it computes the same bits.
+__device__ __forceinline__ float2 corr2_block(const Nw32& p, float4 q4, float efc, float eFc,
+                                              float flf, float flF, float dgf, float dgF) {
+  const Jac2 J = jac2(p, q4.z, q4.w);
+  // residuals of the correction equation at this cell
+  const float rhof = __fmaf_rn(J.fF, eFc, __fmaf_rn(-J.ff, efc, __fadd_rn(q4.x, flf)));
+  const float rhoF = __fmaf_rn(J.Ff, efc, __fmaf_rn(-J.FF, eFc, __fadd_rn(q4.y, flF)));
+  // 2x2 block solve: [a  -b; -d  e] [x; y] = [rhof; rhoF]
+  const float a = __fadd_rn(J.ff, dgf), bb = J.fF, d = J.Ff, e = __fadd_rn(J.FF, dgF);
+  const float det = __fmaf_rn(a, e, -__fmul_rn(bb, d));
+  const float inv = __fdividef(1.0f, det);
+  return make_float2(__fmaf_rn(__fmaf_rn(e, rhof, __fmul_rn(bb, rhoF)), inv, efc),
+                     __fmaf_rn(__fmaf_rn(d, rhof, __fmul_rn(a, rhoF)), inv, eFc));
+}
+
+// The 3D sweeps' flux of one field's correction in neighbour-coefficient
+// form (the same linear operator as flux_lin, fewer instructions: no
+// selects).  A face with drift B between cells L and R carries
+//   G = D (e_R - e_L)/h + B e_up = (alpha e_R - beta e_L)/h,
+//   alpha = D + max(B, 0), beta = D - min(B, 0)      (upwind on -B),
+//   alpha = D + min(B, 0), beta = D - max(B, 0)      (literal: on +B),
+// each from t = D +- |B|/2 and +-B/2 (exact halves) in FMA instructions.
+// For a cell the plus faces' neighbours enter with alpha and the cell with
+// beta, the minus faces' the other way round: the flux is
+// (nbs - dg e_c)/h with nbs = sum of the neighbours' terms and dg the sum
+// over open faces (w = 1) of the cell's terms.  A closed face's neighbour
+// value is zero, so it adds nothing to nbs.  hs = +1/2 (upwind on -B) or
+// -1/2 (literal).
+__device__ __forceinline__ void nb3(float Doh, float hs, const float* en, const float* w,
+                                    const float* B, float& nbs, float& dg) {
+  float s = 0.0f, d = 0.0f;
+#pragma unroll
+  for (int q = 0; q < 6; ++q) {
+    const float t = __fmaf_rn(hs, fabsf(B[q]), Doh);
+    const float al = __fmaf_rn(0.5f, B[q], t), be = __fmaf_rn(-0.5f, B[q], t);
+    s = __fmaf_rn((q & 1) ? al : be, en[q], s);
+    d = __fmaf_rn(w[q], (q & 1) ? be : al, d);
+  }
+  nbs = s;
+  dg = d;
+}
+
+// The block Gauss-Seidel update of one 3D cell in the neighbour-coefficient
+// form: the new correction solves the 2x2 system M e = r + (neighbour sums)
+// directly (M = the exchange Jacobian plus the flux diagonals), so the
+// cell's own old value does not enter.  nbf, nbF, dgf, dgF already over h.
+__device__ __forceinline__ float2 corr2_block_nb(const Nw32& p, float4 q4, float nbf, float nbF,
+                                                 float dgf, float dgF) {
+  const Jac2 J = jac2(p, q4.z, q4.w);
+  const float a = __fadd_rn(J.ff, dgf), bb = J.fF, d = J.Ff, e = __fadd_rn(J.FF, dgF);
+  const float sf = __fadd_rn(q4.x, nbf), sF = __fadd_rn(q4.y, nbF);
+  const float inv = __fdividef(1.0f, __fmaf_rn(a, e, -__fmul_rn(bb, d)));
+  return make_float2(__fmul_rn(__fmaf_rn(e, sf, __fmul_rn(bb, sF)), inv),
+                     __fmul_rn(__fmaf_rn(d, sf, __fmul_rn(a, sF)), inv));
+}
+
+// One 3D correction cell from its gathered inputs (both sweeps of 3D
+// grids, the colour launch and the tiled one, so they agree bit for bit).
+__device__ __forceinline__ float2 corr3_cell(const Nw32& p, const float* enf, const float* enF,
+                                            const float* w, const float* Bf, const float* BF,
+                                            float4 q4) {
+  const float hs = p.literal ? -0.5f : 0.5f;
+  float nbf, nbF, dgf, dgF;
+  nb3(p.Dfh, hs, enf, w, Bf, nbf, dgf);
+  nb3(p.DFh, hs, enF, w, BF, nbF, dgF);
+  return corr2_block_nb(p, q4, __fmul_rn(nbf, p.invh), __fmul_rn(nbF, p.invh),
+                        __fmul_rn(dgf, p.invh), __fmul_rn(dgF, p.invh));
+}
+
 template <int G>
 __device__ __forceinline__ void corr2_apply(const Nw32& p, const Corr2In& in,
                                             float2* __restrict__ e2, float2* fst, float2* Fst,
                                             const float2* fsrc, const float2* Fsrc) {
   const Level& L = p.L;
   const float efc = in.ec.x, eFc = in.ec.y;
-  float dgf, dgF;
-  const float flf = flux_lin<G>(L, p.invh, p.Dfh, p.literal, in.i, efc, in.enf, in.has, in.Bf,
-                                dgf);
-  const float flF = flux_lin<G>(L, p.invh, p.DFh, p.literal, in.i, eFc, in.enF, in.has, in.BF,
-                                dgF);
-  const Jac2 J = jac2(p, in.q4.z, in.q4.w);
-  // residuals of the correction equation at this cell
-  // (every rounding is spelled out, so that each kernel that inlines this
-  // cell computes the same bits)
-  const float rhof = __fmaf_rn(J.fF, eFc, __fmaf_rn(-J.ff, efc, __fadd_rn(in.q4.x, flf)));
-  const float rhoF = __fmaf_rn(J.Ff, efc, __fmaf_rn(-J.FF, eFc, __fadd_rn(in.q4.y, flF)));
-  // 2x2 block solve: [a  -b; -d  e] [x; y] = [rhof; rhoF]
-  const float a = __fadd_rn(J.ff, dgf), bb = J.fF, d = J.Ff, e = __fadd_rn(J.FF, dgF);
-  const float det = __fmaf_rn(a, e, -__fmul_rn(bb, d));
-  const float inv = __fdividef(1.0f, det);
-  const float nf = __fmaf_rn(__fmaf_rn(e, rhof, __fmul_rn(bb, rhoF)), inv, efc);
-  const float nF = __fmaf_rn(__fmaf_rn(d, rhof, __fmul_rn(a, rhoF)), inv, eFc);
+  float2 ne;
+  if (G == SFX_CART3D) {
+    float w[6];
+#pragma unroll
+    for (int q = 0; q < 6; ++q) w[q] = in.has[q] ? 1.0f : 0.0f;
+    ne = corr3_cell(p, in.enf, in.enF, w, in.Bf, in.BF, in.q4);
+  } else {
+    float dgf, dgF;
+    const float flf = flux_lin<G>(L, p.invh, p.Dfh, p.literal, in.i, efc, in.enf, in.has, in.Bf,
+                                  dgf);
+    const float flF = flux_lin<G>(L, p.invh, p.DFh, p.literal, in.i, eFc, in.enF, in.has, in.BF,
+                                  dgF);
+    ne = corr2_block(p, in.q4, efc, eFc, flf, flF, dgf, dgF);
+  }
+  const float nf = ne.x, nF = ne.y;
   e2[in.own] = make_float2(nf, nF);
   if (fst) {
     // last black colour of the iteration: the state becomes src + correction

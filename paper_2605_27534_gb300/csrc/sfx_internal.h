@@ -34,7 +34,7 @@ struct LevelData {
 // on the launching stream) per context; values match sfx_kernel_kind.
 enum Kind {
   K_SMOOTH_FINE = 0, K_SMOOTH_COARSE, K_RESTRICT, K_PROLONG, K_SETUP, K_RESIDUAL, K_ADVECT,
-  K_TOTALS, K_FORCES, K_PHASE, K_OTHER, K_COUNT
+  K_TOTALS, K_FORCES, K_PHASE, K_OTHER, K_SMOOTH_TILED, K_COUNT
 };
 
 // One coarse level of the FP32 multigrid for the coupled Newton correction
@@ -75,7 +75,8 @@ struct F32Scratch {
   bool reuse_drift = false;         // keep drift faces while phi and D's are unchanged
   const double* drift_phi = nullptr;
   float* phi32 = nullptr;           // folded float copy of phi
-  int* flag = nullptr;              // convergence flag, iteration, prediction kept
+  int* flag = nullptr;              // convergence flag, iteration, prediction kept,
+                                    // a tiled sweep that gave up waiting
   bool predict = true;              // start Newton from x* + last increment
   bool redist32 = false;            // redistance in FP32 (else FP64)
   int sweep_planes = 2;             // 3D correction sweep: planes per thread (1 or 2)
@@ -93,6 +94,16 @@ struct F32Scratch {
   float2* e2 = nullptr;                 // Newton corrections (e_f, e_F), colour-packed
   float *rf = nullptr, *rF = nullptr;   // residuals
   float *lf = nullptr, *lF = nullptr;   // diagonals of the linearised problems
+  // tiled sweep of the Newton correction (3D, nx a multiple of 4): a second
+  // correction buffer (the sweep reads one and writes the other), the
+  // minus-side half drifts colour-packed by cell, and the tensor maps of
+  // e2, e2b, rc and the three face arrays
+  bool tiled = true;                    // use it where eligible (SFX_TUNE_TILED_SWEEP)
+  bool tiled_ready = false;
+  int tiled_zchunk = 32;                // planes per block
+  float2* e2b = nullptr;
+  __half2* Hm[3] = {};
+  alignas(64) unsigned char tmaps[6][128] = {};
 };
 
 // Work arrays of the adjoint and of the Marangoni loss (FP64, either

@@ -1,0 +1,419 @@
+// Tiled sweep of the coupled Newton correction (SFX_F32, 3D grids whose nx
+// is a multiple of 8; included by sfx_f32.cu): one launch performs a whole
+// red-black sweep, both colours, from shared memory.
+//
+// A block owns a tile of kTX x kTY cells of the (x, y) plane and a chunk of
+// z-planes [z0, z1), and marches through the planes.  The tensor memory
+// accelerator stages, per plane, the old corrections of colour B (tile + a
+// 2-cell ring), the (r_f, r_F, u, v) float4 of both colours (tile + 1-cell
+// ring) and the half-precision minus-side drifts (B_f, B_F) of the three
+// face directions (colour-packed like the corrections) into a ring of plane
+// slots, kInFlight planes ahead of the one being used.  (Each thread
+// streaming its cells' float4 into registers instead, two steps ahead,
+// made the sweep 26 % slower at 256^3.)  Step t updates the
+// first colour A on plane t + 2 (the tile and its 1-cell ring: A cells read
+// old B values only, so every block computes the same ring values as the
+// block that owns them) and the second colour B on plane t (the tile, from
+// the new A values of planes t - 1 .. t + 1).  The two updates of a step
+// read and write disjoint data, so one block barrier per step orders
+// everything.  Each cell's arithmetic is the 3D colour launch's
+// (corr3_cell), so the sweep equals one B colour launch followed by one A
+// colour launch bit for bit.  The corrections are read from one buffer and
+// written to another: a block's ring reads must see the old values, which
+// a neighbouring block may already have overwritten in place.
+#pragma once
+
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include <algorithm>
+
+#include "sfx_df.cuh"
+#include "sfx_f32_dev.cuh"
+#include "sfx_internal.h"
+
+namespace sfx {
+namespace {
+
+constexpr int kTX = 64, kTY = 8;          // tile: cells along x, rows along y
+constexpr int kPX = kTX / 2;              // packed positions of one colour per tile row
+// staged boxes, per colour (packed positions x rows):
+//   corrections: [ox/2 - 2, + kEX) x [oy - 2, + kEY)
+//   float4:      [ox/2 - 1, + kRX) x [oy - 1, + kRY)
+//   faces:       [ox/2 - 4, + kGX) x [oy - 1, + kFY)   (x start 16 B aligned)
+constexpr int kEX = kPX + 4, kEY = kTY + 4;
+constexpr int kRX = kPX + 2, kRY = kTY + 2;
+constexpr int kGX = kPX + 8, kFY = kTY + 3;
+constexpr int kFPad = 2 * kFY * kGX + 16;  // half2 entries per face array, to 128 B
+#ifndef SFX_TILED_INFLIGHT
+#define SFX_TILED_INFLIGHT 3
+#endif
+constexpr int kInFlight = SFX_TILED_INFLIGHT;   // planes staged ahead of the newest one in use
+constexpr int kRing = 5 + kInFlight;      // a step uses planes t - 1 .. t + 3
+constexpr int kThreads = 32 * (2 * kTY + 3);  // B rows, A rows with the ring rows, ring columns
+
+struct TileSlot {
+  float2 e[2][kEY][kEX];     // corrections (e_f, e_F): old B values (staged), new A values
+  float4 r[2][kRY][kRX];     // (r_f, r_F, u, v) of both colours
+  __half2 f[3][kFPad];       // minus-side drifts (B_f, B_F) of the x, y, z faces, [2][kFY][kGX]
+};
+static_assert(sizeof(TileSlot) % 128 == 0, "slots keep the bulk-copy destinations 128 B aligned");
+static_assert(sizeof(float2) * 2 * kEY * kEX % 128 == 0 && sizeof(float4) * 2 * kRY * kRX % 128 == 0,
+              "each staged array starts 128 B aligned");
+static_assert(kFPad * sizeof(__half2) % 128 == 0, "face array padding");
+constexpr unsigned kSlotBytes = (unsigned)(sizeof(float2) * kEY * kEX +
+                                           sizeof(float4) * 2 * kRY * kRX +
+                                           3 * sizeof(__half2) * 2 * kFY * kGX);
+constexpr size_t kSmemBytes = kRing * sizeof(TileSlot) + kRing * sizeof(unsigned long long) + 16;
+
+__device__ __forceinline__ unsigned smem_u32(const void* p) {
+  return (unsigned)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(unsigned long long* b, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(b)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long* b, unsigned bytes) {
+  asm volatile(
+      "{\n .reg .b64 st;\n mbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n}" ::"r"(
+          smem_u32(b)),
+      "r"(bytes)
+      : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long* b, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(smem_u32(b)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+// Wait for a phase of a slot's barrier; gives up after one second (false).
+__device__ __forceinline__ bool mbar_wait(unsigned long long* b, unsigned parity) {
+  if (mbar_try_wait(b, parity)) return true;
+  const unsigned long long t0 = global_ns();
+  while (!mbar_try_wait(b, parity))
+    if (global_ns() - t0 > 1000000000ull) return false;
+  return true;
+}
+__device__ __forceinline__ void tma_load_4d(void* dst, const CUtensorMap* m, int x, int y, int z,
+                                            int w, unsigned long long* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<unsigned long long>(m)), "r"(x), "r"(y), "r"(z), "r"(w),
+      "r"(smem_u32(bar))
+      : "memory");
+}
+struct TiledArgs {
+  Nw32 p;
+  float2* eout;       // corrections written (colour-packed, the layout of the input)
+  int first_color;    // A: updated on the tile and its ring; B = 1 - A on the tile
+  int zchunk;         // planes per block
+  int* err;           // set to 1 when a staging wait gave up
+  const int* done;    // the solve converged at an earlier iteration
+};
+
+// One cell of colour col from the slots of its plane (S0) and of the
+// planes below (Sm) and above (Sp): pe, ye its packed position and row in
+// the correction box (pe - 1 and ye - 1 in the float4 box, pe + 2 and
+// ye - 1 in the face boxes), par = i & 1, w its open faces (1 or 0).
+// Returns the new correction; keep: also leave it in the correction box.
+__device__ __forceinline__ float2 tiled_cell(const Nw32& p, TileSlot& S0, const TileSlot& Sm,
+                                             const TileSlot& Sp, int col, int pe, int ye,
+                                             int par, const float* w, bool keep) {
+  const int oc = 1 - col;
+  // the other colour's neighbours: x at packed pe - 1 + par and pe + par,
+  // y in the rows above and below, z in the planes below and above
+  float2 nb[6];
+  nb[0] = S0.e[oc][ye][pe - 1 + par];
+  nb[1] = S0.e[oc][ye][pe + par];
+  nb[2] = S0.e[oc][ye - 1][pe];
+  nb[3] = S0.e[oc][ye + 1][pe];
+  nb[4] = Sm.e[oc][ye][pe];
+  nb[5] = Sp.e[oc][ye][pe];
+  // minus faces are the cell's own; a plus face is the minus face of the
+  // neighbour across it (the other colour): x at packed + par, y one row
+  // up, z in the plane above
+  const int pg = pe + 2, fy = ye - 1;
+  const int own = (col * kFY + fy) * kGX + pg, oth = (oc * kFY + fy) * kGX + pg;
+  __half2 hf[6];
+  hf[0] = S0.f[0][own];
+  hf[1] = S0.f[0][oth + par];
+  hf[2] = S0.f[1][own];
+  hf[3] = S0.f[1][oth + kGX];
+  hf[4] = S0.f[2][own];
+  hf[5] = Sp.f[2][oth];
+  const float4 q4 = S0.r[col][ye - 1][pe - 1];
+  float enf[6], enF[6], Bf[6], BF[6];
+#pragma unroll
+  for (int q = 0; q < 6; ++q) {
+    enf[q] = nb[q].x;
+    enF[q] = nb[q].y;
+    const float2 b = __half22float2(hf[q]);
+    Bf[q] = b.x;
+    BF[q] = b.y;
+  }
+  const float2 ne = corr3_cell(p, enf, enF, w, Bf, BF, q4);
+  if (keep) S0.e[col][ye][pe] = ne;
+  return ne;
+}
+
+// The five copies of one plane into its slot, completing on the slot's
+// barrier (issued by one thread).  Of the corrections only colour B is
+// staged: the A cells' old values are never read (each update solves for
+// the cell's new value from its neighbours), and their new values are
+// written by the A updates of this launch.
+struct TiledMaps {
+  const CUtensorMap *e, *r, *fx, *fy, *fz;
+};
+__device__ __forceinline__ void stage_plane(const TiledMaps& tm, TileSlot& S,
+                                            unsigned long long* bar, int ox, int oy, int m,
+                                            int cB) {
+  mbar_expect_tx(bar, kSlotBytes);
+  tma_load_4d(&S.e[cB][0][0], tm.e, ox - 4, oy - 2, m, cB, bar);
+  tma_load_4d(&S.r[0][0][0], tm.r, 2 * ox - 4, oy - 1, m, 0, bar);
+  tma_load_4d(&S.f[0][0], tm.fx, ox / 2 - 4, oy - 1, m, 0, bar);
+  tma_load_4d(&S.f[1][0], tm.fy, ox / 2 - 4, oy - 1, m, 0, bar);
+  tma_load_4d(&S.f[2][0], tm.fz, ox / 2 - 4, oy - 1, m, 0, bar);
+}
+
+__global__ void __launch_bounds__(kThreads, 1)
+k_corr2_tiled(const __grid_constant__ CUtensorMap tm_e, const __grid_constant__ CUtensorMap tm_r,
+              const __grid_constant__ CUtensorMap tm_fx, const __grid_constant__ CUtensorMap tm_fy,
+              const __grid_constant__ CUtensorMap tm_fz, TiledArgs a) {
+  if (a.done && *a.done) return;   // converged at an earlier iteration
+  extern __shared__ __align__(128) unsigned char smem[];
+  TileSlot* ring = reinterpret_cast<TileSlot*>(smem);
+  unsigned long long* bar = reinterpret_cast<unsigned long long*>(smem + kRing * sizeof(TileSlot));
+  const TiledMaps tm{&tm_e, &tm_r, &tm_fx, &tm_fy, &tm_fz};
+  const Level& L = a.p.L;
+  const int ox = blockIdx.x * kTX, oy = blockIdx.y * kTY;
+  const int z0 = blockIdx.z * a.zchunk, z1 = min(z0 + a.zchunk, L.nz);
+  // staged planes z0 - 2 .. z1 + 1, plane m at index q = m - z0 + 2 in
+  // slot q % kRing (use q / kRing of that slot); planes outside the grid
+  // and the parts of a box outside it read as zeros
+  const int nq = (z1 - z0) + 4;
+  const int tid = threadIdx.x;
+  const int cA = a.first_color, cB = 1 - cA;
+  int issued = 0;   // planes staged so far (thread 0)
+  if (tid == 0) {
+    for (int sl = 0; sl < kRing; ++sl) mbar_init(&bar[sl], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  if (tid == 0)
+    for (; issued < min(nq, kInFlight + 2); ++issued)
+      stage_plane(tm, ring[issued % kRing], &bar[issued % kRing], ox, oy, z0 - 2 + issued, cB);
+  // roles: warps 0 .. kTY-1 update B on tile row w; warps kTY .. 2kTY+1
+  // update A on rows -1 .. kTY (the ring rows included); lanes 0 .. kTY-1
+  // of the last warp update the A cell of their row on the ring column
+  // (x = ox - 1 or ox + kTX, whichever has colour A)
+  const int warp = tid >> 5, lane = tid & 31;
+  int role, jr;
+  if (warp < kTY) {
+    role = 0;
+    jr = warp;
+  } else if (warp < 2 * kTY + 2) {
+    role = 1;
+    jr = warp - kTY - 1;
+  } else {
+    role = lane < kTY ? 2 : 3;
+    jr = lane;
+  }
+  const int j = oy + jr;
+  const bool row_in = j >= 0 && j < L.ny;
+  const unsigned half = (unsigned)(L.nx >> 1);
+  const size_t cplane = (size_t)L.ny * L.nz * half;
+  // walls of this thread's cells: y fixed by the row, x by the parity of
+  // the cell in the row (rows of roles 0 and 1: i = ox + 2 lane + par;
+  // role 2: i = ox - 1 (par 1) or ox + kTX (par 0))
+  const float wym = j > 0 ? 1.0f : 0.0f, wyp = j + 1 < L.ny ? 1.0f : 0.0f;
+  const int i0 = role == 2 ? ox + kTX : ox + 2 * lane, i1 = role == 2 ? ox - 1 : ox + 2 * lane + 1;
+  const float wxm0 = i0 > 0 ? 1.0f : 0.0f, wxp0 = i0 + 1 < L.nx ? 1.0f : 0.0f;
+  const float wxm1 = i1 > 0 ? 1.0f : 0.0f, wxp1 = i1 + 1 < L.nx ? 1.0f : 0.0f;
+  // this thread's cell at step st: B on plane t = z0 - 3 + st (role 0) or
+  // A on plane t + 2 (roles 1, 2); upd: update it; zero: an A position
+  // outside the grid, which holds zero (the neighbour of a wall)
+  struct Cell {
+    int plane, i, par, pe;
+    bool upd, zero;
+  };
+  auto cell_at = [&](int st) {
+    Cell c{0, 0, 0, 0, false, false};
+    const int t = z0 - 3 + st;
+    if (role == 0) {
+      c.plane = t;
+      c.par = (j + t + cB) & 1;
+      c.i = ox + 2 * lane + c.par;
+      c.pe = lane + 2;
+      c.upd = row_in && t >= z0 && t < z1 && c.i < L.nx;
+    } else if (role <= 2) {
+      const int m = t + 2;
+      c.plane = m;
+      if (role == 1) {
+        c.par = (j + m + cA) & 1;
+        c.i = ox + 2 * lane + c.par;
+        c.pe = lane + 2;
+      } else {
+        c.par = ((ox - 1 + j + m) & 1) == cA ? 1 : 0;   // x = ox - 1 is odd
+        c.i = c.par ? ox - 1 : ox + kTX;
+        c.pe = c.par ? 1 : kPX + 2;
+      }
+      const bool in_chunk = m >= z0 - 1 && m <= z1;   // the B cells' neighbour planes
+      c.upd = in_chunk && row_in && m >= 0 && m < L.nz && c.i >= 0 && c.i < L.nx;
+      c.zero = in_chunk && !c.upd;
+    }
+    return c;
+  };
+  bool ok = true;
+  for (int q = 0; q < min(nq, 2); ++q) ok = mbar_wait(&bar[q % kRing], (q / kRing) & 1) && ok;
+  const int nsteps = (z1 - z0) + 3;
+  bool aborted = false;
+  for (int st = 0; st < nsteps; ++st) {
+    // stage plane st + kInFlight + 2 into the slot that plane st - 3 left
+    // (last read in step st - 1)
+    if (tid == 0 && issued < nq) {
+      stage_plane(tm, ring[issued % kRing], &bar[issued % kRing], ox, oy, z0 - 2 + issued, cB);
+      ++issued;
+    }
+    const Cell c = cell_at(st);
+    const int qn = st + 2;   // the newest plane this step reads
+    if (qn < nq) ok = mbar_wait(&bar[qn % kRing], (qn / kRing) & 1) && ok;
+    // slots of planes t - 1 .. t + 3 (staged indices st - 2 .. st + 2)
+    const int s2 = st % kRing;
+    const int s1 = s2 == 0 ? kRing - 1 : s2 - 1, s0 = s1 == 0 ? kRing - 1 : s1 - 1;
+    const int s3 = s2 == kRing - 1 ? 0 : s2 + 1, s4 = s3 == kRing - 1 ? 0 : s3 + 1;
+    if (ok && c.upd) {
+      const float w[6] = {c.par ? wxm1 : wxm0, c.par ? wxp1 : wxp0, wym, wyp,
+                          c.plane > 0 ? 1.0f : 0.0f, c.plane + 1 < L.nz ? 1.0f : 0.0f};
+      if (role == 0) {
+        const float2 ne = tiled_cell(a.p, ring[s1], ring[s0], ring[s2], cB, c.pe, jr + 2, c.par,
+                                     w, false);
+        a.eout[(size_t)cB * cplane + ((size_t)c.plane * L.ny + j) * half + (c.i >> 1)] = ne;
+      } else {
+        const float2 ne = tiled_cell(a.p, ring[s3], ring[s2], ring[s4], cA, c.pe, jr + 2, c.par,
+                                     w, true);
+        if (role == 1 && jr >= 0 && jr < kTY && c.plane >= z0 && c.plane < z1)
+          a.eout[(size_t)cA * cplane + ((size_t)c.plane * L.ny + j) * half + (c.i >> 1)] = ne;
+      }
+    } else if (ok && c.zero) {
+      ring[s3].e[cA][jr + 2][c.pe] = make_float2(0.0f, 0.0f);
+    }
+    // the next step's copy refills a slot this step may have written:
+    // order the shared writes before it
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    if (__syncthreads_or(!ok)) {
+      aborted = true;
+      break;
+    }
+  }
+  if (aborted && tid == 0) {
+    atomicExch(a.err, 1);
+    // let the copies already issued land before the block's shared memory
+    // is released (each wait is bounded)
+    for (int q = max(0, issued - kRing); q < issued; ++q)
+      mbar_wait(&bar[q % kRing], (q / kRing) & 1);
+  }
+}
+
+// ---------------------------------------------------------------- host
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    cudaDriverEntryPointQueryResult q;
+    void* p = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+      return nullptr;
+    fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  }
+  return fn;
+}
+
+// A tensor map of 4-byte words: rank dims (innermost first), byte strides
+// of dims 1 .. rank-1, the box; out-of-range words read as zeros.
+sfx_status encode(CUtensorMap* m, void* base, int rank, const cuuint64_t* dims,
+                  const cuuint64_t* strides, const cuuint32_t* box) {
+  auto fn = encode_fn();
+  if (!fn) return SFX_ERR_CUDA;
+  const cuuint32_t es[4] = {1, 1, 1, 1};
+  const CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, (cuuint32_t)rank, base, dims, strides,
+                        box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                        CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? SFX_OK : SFX_ERR_CUDA;
+}
+
+// 3D grids whose packed rows (nx/2 words of 4 bytes) are whole 16-byte units
+bool tiled_sweep_eligible(const Level& L) {
+  return L.geom == SFX_CART3D && L.nx % 8 == 0;
+}
+
+sfx_status tiled_sweep_prepare(sfx_ctx* c) {
+  F32Scratch& S = c->f32;
+  if (S.tiled_ready) return SFX_OK;
+  const Level& L = c->lev[0].lv;
+  if (!tiled_sweep_eligible(L) || !S.e2b || !S.Hm[0]) return SFX_ERR_ARG;
+  static_assert(sizeof(CUtensorMap) == sizeof(S.tmaps[0]), "tensor map storage");
+  const cuuint64_t half = (cuuint64_t)(L.nx / 2), ny = (cuuint64_t)L.ny, nz = (cuuint64_t)L.nz;
+  sfx_status st;
+  // corrections: float2 words [colour][nz][ny][half] as 4-byte words
+  {
+    const cuuint64_t dims[4] = {2 * half, ny, nz, 2};
+    const cuuint64_t str[3] = {8 * half, 8 * half * ny, 8 * half * ny * nz};
+    const cuuint32_t box[4] = {2 * kEX, kEY, 1, 1};   // one colour
+    float2* bufs[2] = {S.e2, S.e2b};
+    for (int b = 0; b < 2; ++b)
+      if ((st = encode(reinterpret_cast<CUtensorMap*>(S.tmaps[b]), bufs[b], 4, dims, str, box)) !=
+          SFX_OK)
+        return st;
+  }
+  {
+    // (r_f, r_F, u, v): float4 words [colour][nz][ny][half] as 4-byte words
+    const cuuint64_t dims[4] = {4 * half, ny, nz, 2};
+    const cuuint64_t str[3] = {16 * half, 16 * half * ny, 16 * half * ny * nz};
+    const cuuint32_t box[4] = {4 * kRX, kRY, 1, 2};
+    if ((st = encode(reinterpret_cast<CUtensorMap*>(S.tmaps[2]), S.rc, 4, dims, str, box)) != SFX_OK)
+      return st;
+  }
+  {
+    // minus-side face drifts, half2 words colour-packed like the corrections
+    const cuuint64_t dims[4] = {half, ny, nz, 2};
+    const cuuint64_t str[3] = {4 * half, 4 * half * ny, 4 * half * ny * nz};
+    const cuuint32_t box[4] = {kGX, kFY, 1, 2};
+    for (int d = 0; d < 3; ++d)
+      if ((st = encode(reinterpret_cast<CUtensorMap*>(S.tmaps[3 + d]), S.Hm[d], 4, dims, str,
+                       box)) != SFX_OK)
+        return st;
+  }
+  SFX_CUDA(cudaFuncSetAttribute(k_corr2_tiled, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)kSmemBytes));
+  S.tiled_ready = true;
+  return SFX_OK;
+}
+
+sfx_status tiled_sweep(sfx_ctx* c, const Nw32& p, int in_buf, const int* done,
+                       cudaStream_t s) {
+  F32Scratch& S = c->f32;
+  const Level& L = p.L;
+  const int zc = std::max(1, S.tiled_zchunk);
+  TiledArgs a{p, in_buf == 0 ? S.e2b : S.e2, 1, zc, S.flag + 3, done};
+  const dim3 grd((unsigned)((L.nx + kTX - 1) / kTX), (unsigned)((L.ny + kTY - 1) / kTY),
+                 (unsigned)((L.nz + zc - 1) / zc));
+  const CUtensorMap* tm = reinterpret_cast<const CUtensorMap*>(S.tmaps);
+  prof_before(c, K_SMOOTH_TILED, s);
+  k_corr2_tiled<<<grd, kThreads, kSmemBytes, s>>>(tm[in_buf], tm[2], tm[3], tm[4], tm[5], a);
+  prof_after(c, K_SMOOTH_TILED, s);
+  SFX_LAUNCH_CHECK();
+  return SFX_OK;
+}
+
+}  // namespace
+}  // namespace sfx

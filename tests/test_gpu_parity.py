@@ -804,3 +804,39 @@ def test_sweep_planes_per_thread_bitwise(sfx, shape):
         torch.cuda.synchronize()
         outs.append((f.cpu().numpy().copy(), F.cpu().numpy().copy()))
     assert np.array_equal(outs[0][0], outs[1][0]) and np.array_equal(outs[0][1], outs[1][1])
+
+
+@pytest.mark.parametrize("shape,zchunk", [((37, 19, 136), 32), ((37, 19, 136), 4),
+                                          ((9, 8, 64), 32), ((24, 24, 24), 5)])
+def test_tiled_sweep_bitwise(sfx, shape, zchunk):
+    """The tiled sweep (one launch per red-black sweep, z-planes staged in
+    shared memory by tensor copies) gives the colour launches' bits: x tiles
+    with a ragged last tile (136 = 2 x 64 + 8), rows and planes that do not
+    fill the last tile or z-chunk, chunks of 4 and 5 planes (many chunk
+    seams); it runs 4 instead of 7 sweep launches per Newton iteration."""
+    import torch
+    nz, ny, nx = shape
+    g, Cf = _sphere(nx, ny, nz, 0.3)
+    ux, uy, uz = W.uniform_faces(g, (0.3, -0.2, 0.25))
+    p = W.Params(ka=2.0, kd=0.5, Df=2e-3, DF=5e-3, eps=0.75 * g.h)
+    _, phi, delta = oracle.phase_field_build(g, Cf, 24, W.redist_dtau(g), p.eps)
+    outs, launches = [], []
+    for tiled in (0, 1):
+        ctx = _ctx(sfx, g, 1)
+        ctx.sfx_set_tuning(sfx._lib.SFX_TUNE_TILED_SWEEP, tiled)
+        ctx.sfx_set_tuning(sfx._lib.SFX_TUNE_TILED_ZCHUNK, zchunk)
+        f, F = _pairs(ctx, 0.3 * delta), _pairs(ctx, 1.0 - Cf)
+        u = [dev(v, torch.float32) for v in (ux, uy, uz)]
+        ctx.sfx_profile(True)
+        for _ in range(3):
+            assert ctx.sfx_surfactant_step(p, dev(phi), f, F, 0.2 * g.h, *u,
+                                           opts=sfx.default_opts(tol=1e-10)).converged
+        torch.cuda.synchronize()
+        pr = ctx.sfx_profile_read()
+        launches.append((pr["smooth_fine"][0], pr["smooth_tiled"][0]))
+        ctx.sfx_profile(False)
+        outs.append((f.cpu().numpy().copy(), F.cpu().numpy().copy()))
+    assert np.array_equal(outs[0][0], outs[1][0]) and np.array_equal(outs[0][1], outs[1][1])
+    (colour, none), (last_black, tiled) = launches
+    assert none == 0 and tiled == 3 * last_black and (tiled + last_black) * 7 == colour * 4, \
+        launches
