@@ -111,6 +111,9 @@ def parse():
                          "(SFX_TUNE_TILED_SWEEP)")
     ap.add_argument("--tiled-zchunk", type=int, default=32,
                     help="z-planes per block of the tiled sweep (SFX_TUNE_TILED_ZCHUNK)")
+    ap.add_argument("--fast-resid", type=int, default=2,
+                    help="FP32: Newton iterations per solve with FP32 residuals "
+                         "(SFX_TUNE_F32_FAST_RESID; 0 = pair residuals only)")
     ap.add_argument("--predict", action="store_true",
                     help="FP32: start each Newton solve from x* plus the last increment "
                          "(SFX_TUNE_PREDICT 1; no gain on the 3D workload)")
@@ -453,6 +456,7 @@ def run_gpu(a, case, rank, world, local_rank):
         ctx.sfx_set_tuning(sfx._lib.SFX_TUNE_SWEEP_PLANES, a.sweep_planes)
         ctx.sfx_set_tuning(sfx._lib.SFX_TUNE_TILED_SWEEP, a.tiled)
         ctx.sfx_set_tuning(sfx._lib.SFX_TUNE_TILED_ZCHUNK, a.tiled_zchunk)
+        ctx.sfx_set_tuning(sfx._lib.SFX_TUNE_F32_FAST_RESID, a.fast_resid)
     stats = []
 
     def step():
@@ -637,6 +641,10 @@ def run_gpu(a, case, rank, world, local_rank):
                    "newton_start": "x* + last increment" if a.predict else "x*",
                    "sweeps": "tiled (whole sweep per launch, zchunk %d)" % a.tiled_zchunk
                              if (a.tiled and prec == sfx.SFX_F32) else "one launch per colour",
+                   "residuals": ("FP32 for up to %d Newton iterations per step (while the "
+                                 "relative residual is above 1e-3), then pair arithmetic"
+                                 % a.fast_resid) if (a.fast_resid and prec == sfx.SFX_F32)
+                                else "pair arithmetic",
                    "l2": "inputs larger than L2 (state + coefficients %.2f GB)" % (
                        g.ncell * 8 * 20 / 1e9),
                    "parallelism": "replicas%d" % world,

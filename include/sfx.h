@@ -363,6 +363,16 @@ typedef enum {
                                SFX_ERR_TIMEOUT. */
   SFX_TUNE_TILED_ZCHUNK = 7, /* z-planes per block of the tiled sweep, 4 ..
                                4096 (default 32). */
+  SFX_TUNE_F32_FAST_RESID = 8, /* SFX_F32 Newton solver: at most this many
+                               iterations per solve (0 .. 16, default 2)
+                               evaluate the residuals in FP32 instead of
+                               pair arithmetic (about 1e-7 of the scale
+                               instead of 1e-14), switching to the pair
+                               pass once both relative residuals are below
+                               1e-3; only a pair residual can pass the
+                               tolerance test, so the converged state is
+                               the same fixed point; 0 = pair residuals
+                               only. */
   SFX_TUNE_PREDICT = 3      /* SFX_F32 Newton solver: 1 (default) = start
                                the iteration from x* plus the previous
                                step's implicit increment x - x* when the

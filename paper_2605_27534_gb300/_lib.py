@@ -36,6 +36,7 @@ SFX_TUNE_F32_REDIST = 4
 SFX_TUNE_SWEEP_PLANES = 5
 SFX_TUNE_TILED_SWEEP = 6
 SFX_TUNE_TILED_ZCHUNK = 7
+SFX_TUNE_F32_FAST_RESID = 8
 KERNEL_KINDS = ["smooth_fine", "smooth_coarse", "restrict", "prolong", "setup", "residual",
                 "advect", "totals", "forces", "phase", "other", "smooth_tiled"]
 

@@ -188,12 +188,12 @@ sfx_status sfx_ctx_create(const sfx_grid* grid, int precision, sfx_ctx** out) {
   if (st == SFX_OK) st = dalloc(c, &c->chi_tmp, n);
   c->n_partial_blocks = kTotalsBlocks;
   if (st == SFX_OK) st = dalloc(c, &c->partials, (size_t)2 * 8 * c->n_partial_blocks);
-  if (st == SFX_OK) st = dalloc(c, &c->d_norms, 8);
+  if (st == SFX_OK) st = dalloc(c, &c->d_norms, 16);
   if (st == SFX_OK) st = dalloc(c, &c->d_sums, 8);
   if (st == SFX_OK && precision == SFX_F32) st = f32_ensure_scratch(c);
   if (st == SFX_OK) {
     c->d_flag = (int*)(c->d_norms + 7);
-    cudaError_t e = cudaMallocHost(&c->h_norms, 8 * sizeof(unsigned long long));
+    cudaError_t e = cudaMallocHost(&c->h_norms, 16 * sizeof(unsigned long long));
     if (e == cudaSuccess) e = cudaMallocHost(&c->h_sums, 8 * sizeof(double));
     if (e != cudaSuccess) st = cuda_fail(e);
   }
@@ -385,6 +385,10 @@ sfx_status sfx_set_tuning(sfx_ctx* c, int key, int value) {
   }
   if (key == SFX_TUNE_TILED_SWEEP && (value == 0 || value == 1)) {
     c->f32.tiled = value == 1;
+    return SFX_OK;
+  }
+  if (key == SFX_TUNE_F32_FAST_RESID && value >= 0 && value <= 16) {
+    c->f32.fast_resid = value;
     return SFX_OK;
   }
   if (key == SFX_TUNE_TILED_ZCHUNK && value >= 4 && value <= 4096) {

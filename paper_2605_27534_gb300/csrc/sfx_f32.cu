@@ -302,6 +302,30 @@ __global__ void k_corr32(Corr32 p, const float* __restrict__ Bx, const float* __
 // the coupled one does not.
 // Evaluate both residuals (pairs), the 2x2 exchange Jacobian and the
 // norms at every cell of the current state.
+// `done`: the solve converged at an earlier iteration; `mode` (may be
+// null): the residual kind chosen on the device for this iteration (zero:
+// the FP32 pass, nonzero: the pair pass); a launch whose kind `want` is not
+// chosen returns at once.
+__device__ __forceinline__ bool resid_skip(const int* done, const int* mode, int want) {
+  return (done && *done) || (mode && (*mode != 0) != (want != 0));
+}
+
+// Warp maxima of the four norms, then one atomic per block and norm.
+__device__ __forceinline__ void resid_norms(const float* m, unsigned int* norms) {
+  __shared__ float wm[4][8];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const float v = warp_max(m[q]);
+    if ((threadIdx.x & 31) == 0) wm[q][threadIdx.x >> 5] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < 4) {
+    float v = 0.0f;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) v = fmaxf(v, wm[threadIdx.x][w]);
+    atomicMax(&norms[threadIdx.x], fbits(v));
+  }
+}
+
 template <int G>
 __global__ void __launch_bounds__(256, 5)
 k_resid2_32(Nw32 p, const float* __restrict__ phi, const float2* __restrict__ B2x,
@@ -310,8 +334,8 @@ k_resid2_32(Nw32 p, const float* __restrict__ phi, const float2* __restrict__ B2
             const float2* __restrict__ Fin, const float2* __restrict__ fst,
             const float2* __restrict__ Fst, float4* __restrict__ rc,
             unsigned int* norms, float2* __restrict__ e2,
-            const int* __restrict__ done) {
-  if (done && *done) return;   // converged at an earlier iteration
+            const int* __restrict__ done, const int* __restrict__ mode) {
+  if (resid_skip(done, mode, 1)) return;
   const Level& L = p.L;
   float m[4] = {0.0f, 0.0f, 0.0f, 0.0f};
   const float2* B2[3] = {B2x, B2y, B2z};
@@ -323,21 +347,30 @@ k_resid2_32(Nw32 p, const float* __restrict__ phi, const float2* __restrict__ B2
     if (i < L.nx)
       resid2_cell<G>(p, i, j, k, r * (ix)L.nx + (ix)i, phi, B2, fin, Fin, fst, Fst, rc, m, e2);
   }
-  if (norms) {
-    // warp maxima, then one atomic per block and norm
-    __shared__ float wm[4][8];
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const float v = warp_max(m[q]);
-      if ((threadIdx.x & 31) == 0) wm[q][threadIdx.x >> 5] = v;
-    }
-    __syncthreads();
-    if (threadIdx.x < 4) {
-      float v = 0.0f;
-      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) v = fmaxf(v, wm[threadIdx.x][w]);
-      atomicMax(&norms[threadIdx.x], fbits(v));
-    }
+  if (norms) resid_norms(m, norms);
+}
+
+// The FP32 residual pass (resid32_cell), same launch shape and outputs.
+template <int G>
+__global__ void __launch_bounds__(256, 5)
+k_resid32_fast(Nw32 p, const float* __restrict__ phi, const float2* __restrict__ B2x,
+               const float2* __restrict__ B2y, const float2* __restrict__ B2z,
+               const float2* __restrict__ fin, const float2* __restrict__ Fin,
+               const float2* __restrict__ fst, const float2* __restrict__ Fst,
+               float4* __restrict__ rc, unsigned int* norms, float2* __restrict__ e2,
+               const int* __restrict__ done, const int* __restrict__ mode) {
+  if (resid_skip(done, mode, 0)) return;
+  const Level& L = p.L;
+  float m[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+  const float2* B2[3] = {B2x, B2y, B2z};
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const ix rows = (ix)L.ny * (ix)L.nz;
+  for (ix r = blockIdx.y; r < rows; r += gridDim.y) {
+    const int j = (int)(r % (ix)L.ny), k = (int)(r / (ix)L.ny);
+    if (i < L.nx)
+      resid32_cell<G>(p, i, j, k, r * (ix)L.nx + (ix)i, phi, B2, fin, Fin, fst, Fst, rc, m, e2);
   }
+  if (norms) resid_norms(m, norms);
 }
 
 // One colour of the coupled red-black Gauss-Seidel on the correction.
@@ -406,20 +439,22 @@ k_corr2_32(Nw32 p, const __half2* __restrict__ Hx, const __half2* __restrict__ H
 // bound allows and spills.
 struct NewtonKernels {
   decltype(&k_resid2_32<kGeomRuntime>) resid;
+  decltype(&k_resid32_fast<kGeomRuntime>) fast;
   decltype(&k_corr2_32<SFX_CART3D, 1>) corr;
   int kp;   // planes per thread of the correction sweep
 };
 template <int G>
 NewtonKernels newton_kernels_of() {
-  return NewtonKernels{&k_resid2_32<G>, &k_corr2_32<G, 1>, 1};
+  return NewtonKernels{&k_resid2_32<G>, &k_resid32_fast<G>, &k_corr2_32<G, 1>, 1};
 }
 NewtonKernels newton_kernels(int geom, int kp) {
   switch (geom) {
     case SFX_AXISYM: return newton_kernels_of<SFX_AXISYM>();
     case SFX_PLANAR2D: return newton_kernels_of<SFX_PLANAR2D>();
     default:
-      if (kp == 2) return NewtonKernels{&k_resid2_32<kGeomRuntime>, &k_corr2_32<SFX_CART3D, 2>, 2};
-      return NewtonKernels{&k_resid2_32<kGeomRuntime>, &k_corr2_32<SFX_CART3D, 1>, 1};
+      return NewtonKernels{&k_resid2_32<kGeomRuntime>, &k_resid32_fast<SFX_CART3D>,
+                           kp == 2 ? &k_corr2_32<SFX_CART3D, 2> : &k_corr2_32<SFX_CART3D, 1>,
+                           kp == 2 ? 2 : 1};
   }
 }
 
@@ -1215,8 +1250,14 @@ sfx_status solve_dc32(sfx_ctx* c, const Nl32& pf, const Nl32& pF, const float* p
 // and flag[1] records the iteration.
 // A tiled sweep of the previous iteration that gave up waiting for its
 // staged planes (flag[3]) marks the norms with kTimeoutBits instead.
+// Residual kinds: flag[4] = 0 while the FP32 pass evaluates the residuals,
+// nonzero once the pair pass does; only a pair residual passes the test.  The
+// solve switches to the pair pass after `fast_max` FP32 iterations
+// (counted in flag[5]) or once both relative residuals are below
+// kFastSwitch; nrm[4] records the kind each iteration's norms came from.
 constexpr unsigned int kTimeoutBits = 0xffffffffu;
-__global__ void k_flag32(unsigned int* __restrict__ nrm, float tol, int it,
+constexpr float kFastSwitch = 1e-3f;
+__global__ void k_flag32(unsigned int* __restrict__ nrm, float tol, int it, int fast_max,
                          int* __restrict__ flag) {
   if (threadIdx.x != 0 || flag[0]) return;
   if (flag[3]) {
@@ -1225,9 +1266,15 @@ __global__ void k_flag32(unsigned int* __restrict__ nrm, float tol, int it,
   }
   const float rf = __uint_as_float(nrm[0]), bf = __uint_as_float(nrm[1]);
   const float rF = __uint_as_float(nrm[2]), bF = __uint_as_float(nrm[3]);
-  if (rf <= tol * bf && rF <= tol * bF) {
-    flag[0] = 1;
-    flag[1] = it;
+  const bool pair = flag[4] != 0;
+  nrm[4] = pair ? 1u : 0u;
+  if (pair) {
+    if (rf <= tol * bf && rF <= tol * bF) {
+      flag[0] = 1;
+      flag[1] = it;
+    }
+  } else if (++flag[5] >= fast_max || (rf <= kFastSwitch * bf && rF <= kFastSwitch * bF)) {
+    flag[4] = 1;
   }
 }
 
@@ -1327,13 +1374,16 @@ sfx_status solve_newton32(sfx_ctx* c, const Nw32& p, const float* phi, float* co
   // with two planes per thread the grid covers the lower half of the planes
   dim3 blk(128), grd((unsigned)(((L.nx + 1) / 2 + 127) / 128), (unsigned)L.ny,
                      (unsigned)((L.nz + nk.kp - 1) / nk.kp));
-  unsigned int* dn = (unsigned int*)c->d_norms;        // two 4-slot norm buffers
-  unsigned int* hn = (unsigned int*)c->h_norms;
+  unsigned int* dn = (unsigned int*)(c->d_norms + 8);  // two 8-slot norm buffers
+  unsigned int* hn = (unsigned int*)(c->h_norms + 8);
   int* flag = c->f32.flag;
   const RowGrid rg = row_grid(L, c->sm_count);
   const __half2* Hz = L.ndim() == 3 ? c->f32.H2[2] : nullptr;
   const float2* B2[3] = {c->f32.B2[0], c->f32.B2[1], L.ndim() == 3 ? c->f32.B2[2] : nullptr};
-  SFX_CUDA(cudaMemsetAsync(flag, 0, 4 * sizeof(int), s));
+  // flag[4] = 1: pair residuals from the first iteration (no FP32 passes)
+  const int fast_max = c->f32.fast_resid;
+  SFX_CUDA(cudaMemsetAsync(flag, 0, 8 * sizeof(int), s));
+  if (fast_max <= 0) SFX_CUDA(cudaMemsetAsync(flag + 4, 1, sizeof(int), s));
   // sweeps 1 .. S-1 (black, then red) as tiled launches where the grid
   // allows, the last black colour as a colour launch that adds the
   // corrections to the state
@@ -1353,15 +1403,18 @@ sfx_status solve_newton32(sfx_ctx* c, const Nw32& p, const float* phi, float* co
   *conv = false;
   int it = 0, done_it = 0;
   for (it = 1; it <= o->max_cycles; ++it) {
-    unsigned int* nbuf = dn + 4 * (it & 1);
-    SFX_CUDA(cudaMemsetAsync(nbuf, 0, 4 * sizeof(unsigned int), s));
+    unsigned int* nbuf = dn + 8 * (it & 1);
+    SFX_CUDA(cudaMemsetAsync(nbuf, 0, 8 * sizeof(unsigned int), s));
     // from_star: the first iterate is x* itself, read from (f*, F*); the
     // first state update writes x* + e into (f, F), so no copy precedes it
     const bool star = from_star && it == 1;
     const float2* fsrc = star ? fs : fc;
     const float2* Fsrc = star ? Fs : Fc;
+    // the FP32 or the pair residual pass, as chosen on the device
+    SFX_KERNEL(c, K_RESIDUAL, nk.fast, rg.grid, rg.block, s, p, phi, B2[0], B2[1], B2[2], fsrc,
+               Fsrc, fs, Fs, c->f32.rc, nbuf, c->f32.e2, flag, flag + 4);
     SFX_KERNEL(c, K_RESIDUAL, nk.resid, rg.grid, rg.block, s, p, phi, B2[0], B2[1], B2[2], fsrc,
-               Fsrc, fs, Fs, c->f32.rc, nbuf, c->f32.e2, flag);
+               Fsrc, fs, Fs, c->f32.rc, nbuf, c->f32.e2, flag, flag + 4);
     if (it == 1 && predicted) {
       // keep the predicted start only if its residual is already small;
       // otherwise restart from x* (both launches return at once when kept)
@@ -1369,11 +1422,13 @@ sfx_status solve_newton32(sfx_ctx* c, const Nw32& p, const float* phi, float* co
       const float rho = c->f32.predict_rho;
       SFX_KERNEL(c, K_OTHER, k_pred_check32, 1, 32, s, nbuf, rho, ok);
       SFX_KERNEL(c, K_SETUP, k_restore32, nb, 256, s, n, ok, fs, Fs, fc, Fc);
+      SFX_KERNEL(c, K_RESIDUAL, nk.fast, rg.grid, rg.block, s, p, phi, B2[0], B2[1], B2[2],
+                 fc, Fc, fs, Fs, c->f32.rc, nbuf, c->f32.e2, ok, flag + 4);
       SFX_KERNEL(c, K_RESIDUAL, nk.resid, rg.grid, rg.block, s, p, phi, B2[0], B2[1], B2[2],
-                 fc, Fc, fs, Fs, c->f32.rc, nbuf, c->f32.e2, ok);
+                 fc, Fc, fs, Fs, c->f32.rc, nbuf, c->f32.e2, ok, flag + 4);
     }
-    SFX_KERNEL(c, K_OTHER, k_flag32, 1, 32, s, nbuf, tolf, it, flag);
-    SFX_CUDA(cudaMemcpyAsync(hn + 4 * (it & 1), nbuf, 4 * sizeof(unsigned int),
+    SFX_KERNEL(c, K_OTHER, k_flag32, 1, 32, s, nbuf, tolf, it, fast_max, flag);
+    SFX_CUDA(cudaMemcpyAsync(hn + 8 * (it & 1), nbuf, 8 * sizeof(unsigned int),
                              cudaMemcpyDeviceToHost, s));
     SFX_CUDA(cudaEventRecord(c->f32.ev[it & 1], s));
     if (mgl >= 2) {
@@ -1416,11 +1471,12 @@ sfx_status solve_newton32(sfx_ctx* c, const Nw32& p, const float* phi, float* co
     const int prev = it - 1;
     if (prev >= 1) {
       SFX_CUDA(cudaEventSynchronize(c->f32.ev[prev & 1]));
-      if (hn[4 * (prev & 1) + 1] == kTimeoutBits) return SFX_ERR_TIMEOUT;
-      memcpy(nrm, hn + 4 * (prev & 1), 4 * sizeof(float));
+      const unsigned int* hb = hn + 8 * (prev & 1);
+      if (hb[1] == kTimeoutBits) return SFX_ERR_TIMEOUT;
+      memcpy(nrm, hb, 4 * sizeof(float));
       for (int q = 0; q < 4; ++q)
         if (!std::isfinite(nrm[q])) return SFX_ERR_NONFINITE;
-      if (nrm[0] <= tolf * nrm[1] && nrm[2] <= tolf * nrm[3]) {   // as k_flag32 decides
+      if (hb[4] == 1u && nrm[0] <= tolf * nrm[1] && nrm[2] <= tolf * nrm[3]) {   // as k_flag32
         *conv = true;
         done_it = prev;
         break;
@@ -1436,16 +1492,17 @@ sfx_status solve_newton32(sfx_ctx* c, const Nw32& p, const float* phi, float* co
     // the last iteration's residuals
     SFX_CUDA(cudaStreamSynchronize(s));
     const int last = std::min(it, o->max_cycles);
-    if (hn[4 * (last & 1) + 1] == kTimeoutBits) return SFX_ERR_TIMEOUT;
+    const unsigned int* hb = hn + 8 * (last & 1);
+    if (hb[1] == kTimeoutBits) return SFX_ERR_TIMEOUT;
     if (tiled) {
       int err = 0;
       SFX_CUDA(cudaMemcpy(&err, flag + 3, sizeof(int), cudaMemcpyDeviceToHost));
       if (err) return SFX_ERR_TIMEOUT;
     }
-    memcpy(nrm, hn + 4 * (last & 1), 4 * sizeof(float));
+    memcpy(nrm, hb, 4 * sizeof(float));
     for (int q = 0; q < 4; ++q)
       if (!std::isfinite(nrm[q])) return SFX_ERR_NONFINITE;
-    if (nrm[0] <= tolf * nrm[1] && nrm[2] <= tolf * nrm[3]) *conv = true;
+    if (hb[4] == 1u && nrm[0] <= tolf * nrm[1] && nrm[2] <= tolf * nrm[3]) *conv = true;
     done_it = last;
   }
   *iters = done_it;
@@ -1723,7 +1780,7 @@ sfx_status f32_ensure_scratch(sfx_ctx* c) {
   if ((st = get(n * sizeof(float), (void**)&c->f32.phi32)) != SFX_OK) return st;
   if ((st = get(n * sizeof(float), (void**)&c->f32.inc_f)) != SFX_OK) return st;
   if ((st = get(n * sizeof(float), (void**)&c->f32.inc_F)) != SFX_OK) return st;
-  if ((st = get(4 * sizeof(int), (void**)&c->f32.flag)) != SFX_OK) return st;
+  if ((st = get(8 * sizeof(int), (void**)&c->f32.flag)) != SFX_OK) return st;
   if ((st = get(n * sizeof(float2), (void**)&c->f32.falt)) != SFX_OK) return st;
   if ((st = get(n * sizeof(float2), (void**)&c->f32.Falt)) != SFX_OK) return st;
   // the Newton work arrays are colour-packed: 2 planes of ny nz ceil(nx/2)

@@ -499,6 +499,61 @@ __device__ __forceinline__ void resid2_cell(const Nw32& p, int i, int j, int k, 
   if (!(fabsf(rf) <= 3.0e38f) || !(fabsf(rF) <= 3.0e38f)) m[0] = m[2] = __int_as_float(0x7f800000);
 }
 
+// resid2_cell in FP32 arithmetic on the leading floats of the pairs (the
+// same outputs: residuals, u, v, the first red half-sweep and the norms;
+// residuals within ~1e-7 of the scale m[1], m[3]).  The Newton iterations
+// far from convergence use it: their corrections need residuals only to a
+// few digits, and the iterations that decide convergence evaluate the pair
+// residual.
+template <int G>
+__device__ __forceinline__ void resid32_cell(const Nw32& p, int i, int j, int k, ix c,
+                                             const float* __restrict__ phi,
+                                             const float2* const* B2,
+                                             const float2* __restrict__ fin,
+                                             const float2* __restrict__ Fin,
+                                             const float2* __restrict__ fst,
+                                             const float2* __restrict__ Fst,
+                                             float4* __restrict__ rc, float* m,
+                                             float2* __restrict__ e2) {
+  const Level& L = p.L;
+  bool has[6];
+  ix nbi[6];
+  gather6<G>(L, i, j, k, c, has, nbi);
+  float Bf[6], BF[6], nf[6], nF[6], df_, dF_;
+  faces6f2(L, B2[0], B2[1], B2[2], i, j, k, has, Bf, BF);
+#pragma unroll
+  for (int q = 0; q < 6; ++q) {
+    nf[q] = has[q] ? fin[nbi[q]].x : 0.0f;
+    nF[q] = has[q] ? Fin[nbi[q]].x : 0.0f;
+  }
+  const float fc = fin[c].x, Fc = Fin[c].x;
+  const float flf = flux_lin<G>(L, p.invh, p.Dfh, p.literal, i, fc, nf, has, Bf, df_);
+  const float flF = flux_lin<G>(L, p.invh, p.DFh, p.literal, i, Fc, nF, has, BF, dF_);
+  const PhiPair ph = unfold(phi[c]);
+  const float c1 = __fdividef(p.ka, ph.p + p.eta);
+  const float finf = __fmul_rn(__fmul_rn(__fmul_rn(p.ginf, ph.p), ph.q), p.inv_eps);
+  const float u = __fmul_rn(c1, Fc), v = __fmul_rn(c1, __fsub_rn(finf, fc));
+  const float qx = __fmaf_rn(v, Fc, -__fmul_rn(p.kd, fc));   // c1 F (f_inf - f) - r_d f
+  const float fs = fst[c].x, Fs = Fst[c].x;
+  const float rf = __fadd_rn(__fmaf_rn(__fsub_rn(fs, fc), p.inv_dt, flf), qx);
+  const float rF = __fsub_rn(__fmaf_rn(__fsub_rn(Fs, Fc), p.inv_dt, flF), qx);
+  const RBIdx rb = rb_index(L, i, j, k);
+  const ix own = (ix)((i + j + k) & 1) * rb.plane + rb.pos;
+  rc[own] = make_float4(rf, rF, u, v);
+  if (e2 && ((i + j + k) & 1) == 0) {
+    const Jac2 J = jac2(p, u, v);
+    const float a = __fadd_rn(J.ff, df_), e = __fadd_rn(J.FF, dF_);
+    const float inv = __fdividef(1.0f, __fmaf_rn(a, e, -__fmul_rn(J.fF, J.Ff)));
+    e2[own] = make_float2(__fmul_rn(__fmaf_rn(e, rf, __fmul_rn(J.fF, rF)), inv),
+                          __fmul_rn(__fmaf_rn(J.Ff, rf, __fmul_rn(a, rF)), inv));
+  }
+  m[0] = fmaxf(m[0], fabsf(rf));
+  m[1] = fmaxf(m[1], fabsf(__fmaf_rn(fs, p.inv_dt, __fmul_rn(u, finf))));
+  m[2] = fmaxf(m[2], fabsf(rF));
+  m[3] = fmaxf(m[3], fabsf(__fmaf_rn(Fs, p.inv_dt, __fmul_rn(p.kd, fc))));
+  if (!(fabsf(rf) <= 3.0e38f) || !(fabsf(rF) <= 3.0e38f)) m[0] = m[2] = __int_as_float(0x7f800000);
+}
+
 // One cell of the coupled red-black Gauss-Seidel on the correction; with
 // fst != NULL (the last black colour of an iteration) the corrections of
 // this cell and of its red pair partner are added to the state.  The sweeps

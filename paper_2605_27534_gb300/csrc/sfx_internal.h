@@ -76,7 +76,9 @@ struct F32Scratch {
   const double* drift_phi = nullptr;
   float* phi32 = nullptr;           // folded float copy of phi
   int* flag = nullptr;              // convergence flag, iteration, prediction kept,
-                                    // a tiled sweep that gave up waiting
+                                    // a tiled sweep that gave up waiting, residual
+                                    // kind (0 FP32, else pair), FP32 passes so far
+  int fast_resid = 2;               // FP32 residual passes at most per Newton solve
   bool predict = true;              // start Newton from x* + last increment
   bool redist32 = false;            // redistance in FP32 (else FP64)
   int sweep_planes = 2;             // 3D correction sweep: planes per thread (1 or 2)
@@ -159,7 +161,9 @@ struct sfx_ctx {
   // reductions
   double* partials = nullptr;        // block partial sums (s, c) pairs
   int n_partial_blocks = 0;
-  unsigned long long* d_norms = nullptr;  // 8 slots (device)
+  unsigned long long* d_norms = nullptr;  // 16 slots (device): 0..7 the FP64 solves and the
+                                          // FP32 sweeps (7: d_flag), 8..15 the FP32 Newton
+                                          // solve's two norm buffers
   unsigned long long* h_norms = nullptr;  // pinned mirror
   double* d_sums = nullptr;          // compensated totals (device)
   double* h_sums = nullptr;          // pinned mirror

@@ -105,7 +105,8 @@ def test_batch_matches_oracle_per_instance(sfx):
 
 def test_batch_bitwise_equals_single_grid_steps(sfx):
     """Fixed budget (no instance meets tol = 1e-30): the batched kernels run
-    the single-grid SFX_F32 arithmetic cell for cell."""
+    the single-grid SFX_F32 arithmetic cell for cell (with pair residuals at
+    every iteration, as the batch evaluates them)."""
     import torch
     inst = _instances(seed=5)
     B = _Batch(sfx, inst)
@@ -120,6 +121,7 @@ def test_batch_bitwise_equals_single_grid_steps(sfx):
     o = sfx.default_opts(tol=1e-30, max_cycles=4, nu1=2, nu2=0)
     for k, (c, phi, f0) in enumerate(inst):
         ctx = sfx.Context.for_grid(c.grid, sfx.SFX_F32)
+        ctx.sfx_set_tuning(sfx._lib.SFX_TUNE_F32_FAST_RESID, 0)
         f, F = sfx.sfx_df_pack(dev(f0)), sfx.sfx_df_pack(dev(c.F0))
         phid = dev(phi)
         u = [dev(c.ux, torch.float32), dev(c.uy, torch.float32), None]
@@ -267,7 +269,8 @@ def test_planar_kinetics_sweep_matches_oracle_and_conserves(sfx):
 
 def test_planar_batch_bitwise_equals_single_grid_steps(sfx):
     """Fixed budget: planar batched kernels run the single-grid SFX_F32
-    arithmetic cell for cell, as the axisymmetric ones do."""
+    arithmetic cell for cell, as the axisymmetric ones do (pair residuals
+    at every iteration)."""
     import torch
     inst = _flat_instances(seed=21)
     B = _Batch(sfx, inst, flow=False, geom=sfx.SFX_PLANAR2D)
@@ -278,6 +281,7 @@ def test_planar_batch_bitwise_equals_single_grid_steps(sfx):
     o = sfx.default_opts(tol=1e-30, max_cycles=4, nu1=2, nu2=0)
     for k, (c, phi, f0) in enumerate(inst):
         ctx = sfx.Context.for_grid(c.grid, sfx.SFX_F32)
+        ctx.sfx_set_tuning(sfx._lib.SFX_TUNE_F32_FAST_RESID, 0)
         f, F = sfx.sfx_df_pack(dev(f0)), sfx.sfx_df_pack(dev(c.F0))
         for _ in range(2):
             ctx.sfx_surfactant_step(c.params, dev(phi), f, F, c.dt, opts=o,

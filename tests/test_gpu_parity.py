@@ -840,3 +840,35 @@ def test_tiled_sweep_bitwise(sfx, shape, zchunk):
     (colour, none), (last_black, tiled) = launches
     assert none == 0 and tiled == 3 * last_black and (tiled + last_black) * 7 == colour * 4, \
         launches
+
+
+@pytest.mark.parametrize("fast", [1, 2, 4])
+def test_fp32_residual_iterations_reach_the_same_fixed_point(sfx, fast):
+    """Newton iterations with FP32 residuals early in each solve (at most
+    `fast` of them, until the relative residual falls below 1e-3) end on the
+    pair residual's fixed point: the state matches the pair-only solve to
+    far below the FP32 tolerance, each solve converges on a pair residual,
+    and no solve needs more than one extra iteration."""
+    import torch
+    nz, ny, nx = 24, 20, 32
+    g, Cf = _sphere(nx, ny, nz, 0.3)
+    ux, uy, uz = W.uniform_faces(g, (0.3, -0.2, 0.25))
+    p = W.Params(ka=2.0, kd=0.5, Df=2e-3, DF=5e-3, eps=0.75 * g.h)
+    _, phi, delta = oracle.phase_field_build(g, Cf, 24, W.redist_dtau(g), p.eps)
+    outs, its = [], []
+    for mode in (0, fast):
+        ctx = _ctx(sfx, g, 1)
+        ctx.sfx_set_tuning(sfx._lib.SFX_TUNE_F32_FAST_RESID, mode)
+        f, F = _pairs(ctx, 0.3 * delta), _pairs(ctx, 1.0 - Cf)
+        u = [dev(v, torch.float32) for v in (ux, uy, uz)]
+        n = []
+        for _ in range(3):
+            st = ctx.sfx_surfactant_step(p, dev(phi), f, F, 0.2 * g.h, *u,
+                                         opts=sfx.default_opts(tol=1e-10))
+            assert st.converged
+            n.append(st.picard)
+        its.append(n)
+        outs.append((host(ctx.sfx_df_unpack(f)), host(ctx.sfx_df_unpack(F))))
+    for a, b in zip(outs[0], outs[1]):
+        assert np.abs(a - b).max() / np.abs(a).max() < 1e-8
+    assert all(m <= k + 1 for k, m in zip(its[0], its[1])), its
