@@ -439,7 +439,7 @@ k_corr2_32(Nw32 p, const __half2* __restrict__ Hx, const __half2* __restrict__ H
 // bound allows and spills.
 struct NewtonKernels {
   decltype(&k_resid2_32<kGeomRuntime>) resid;
-  decltype(&k_resid32_fast<kGeomRuntime>) fast;
+  decltype(&k_resid32_fast<SFX_CART3D>) fast;
   decltype(&k_corr2_32<SFX_CART3D, 1>) corr;
   int kp;   // planes per thread of the correction sweep
 };

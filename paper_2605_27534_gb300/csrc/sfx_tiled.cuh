@@ -50,7 +50,8 @@ constexpr int kFPad = 2 * kFY * kGX + 16;  // half2 entries per face array, to 1
 #endif
 constexpr int kInFlight = SFX_TILED_INFLIGHT;   // planes staged ahead of the newest one in use
 constexpr int kRing = 5 + kInFlight;      // a step uses planes t - 1 .. t + 3
-constexpr int kThreads = 32 * (2 * kTY + 3);  // B rows, A rows with the ring rows, ring columns
+// warps: B rows, A rows with the ring rows, the ring columns, the producer
+constexpr int kBWarps = kTY, kAWarps = kTY + 3, kThreads = 32 * (kBWarps + kAWarps + 1);
 
 struct TileSlot {
   float2 e[2][kEY][kEX];     // corrections (e_f, e_F): old B values (staged), new A values
@@ -64,7 +65,9 @@ static_assert(kFPad * sizeof(__half2) % 128 == 0, "face array padding");
 constexpr unsigned kSlotBytes = (unsigned)(sizeof(float2) * kEY * kEX +
                                            sizeof(float4) * 2 * kRY * kRX +
                                            3 * sizeof(__half2) * 2 * kFY * kGX);
-constexpr size_t kSmemBytes = kRing * sizeof(TileSlot) + kRing * sizeof(unsigned long long) + 16;
+// the slots, then three barrier rings (planes staged, A planes done, slots
+// free) and the abort flag
+constexpr size_t kSmemBytes = kRing * sizeof(TileSlot) + 3 * kRing * sizeof(unsigned long long) + 16;
 
 __device__ __forceinline__ unsigned smem_u32(const void* p) {
   return (unsigned)__cvta_generic_to_shared(p);
@@ -78,6 +81,10 @@ __device__ __forceinline__ void mbar_expect_tx(unsigned long long* b, unsigned b
           smem_u32(b)),
       "r"(bytes)
       : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(unsigned long long* b) {
+  asm volatile("{\n .reg .b64 st;\n mbarrier.arrive.shared::cta.b64 st, [%0];\n}" ::"r"(smem_u32(b))
+               : "memory");
 }
 __device__ __forceinline__ bool mbar_try_wait(unsigned long long* b, unsigned parity) {
   unsigned ok;
@@ -111,10 +118,12 @@ __device__ __forceinline__ void tma_load_4d(void* dst, const CUtensorMap* m, int
       "r"(smem_u32(bar))
       : "memory");
 }
+// A (black) is updated on the tile and its ring, B (red) on the tile
+constexpr int cA = 1, cB = 0;
+
 struct TiledArgs {
   Nw32 p;
   float2* eout;       // corrections written (colour-packed, the layout of the input)
-  int first_color;    // A: updated on the tile and its ring; B = 1 - A on the tile
   int zchunk;         // planes per block
   int* err;           // set to 1 when a staging wait gave up
   const int* done;    // the solve converged at an earlier iteration
@@ -184,6 +193,22 @@ __device__ __forceinline__ void stage_plane(const TiledMaps& tm, TileSlot& S,
   tma_load_4d(&S.f[2][0], tm.fz, ox / 2 - 4, oy - 1, m, 0, bar);
 }
 
+// Warp-specialised pipeline, no block barrier in the loop.  Plane m is
+// staged plane q = m - z0 + 2 (planes z0 - 2 .. z1 + 1), in slot q % kRing,
+// the u-th use of that slot (u = q / kRing; phase parity u & 1) for each of
+// its three barriers:
+//   full:  the slot's copies landed (the producer's expect_tx);
+//   adone: the A warps finished plane m (one arrival per A warp);
+//   empty: the B warps finished with the slot (one arrival per B warp).
+// Producer (last warp, one lane): stage plane q once the slot's previous
+// plane is released.  A warps: A on planes z0 - 1 .. z1 in order, each
+// after its planes m - 1 .. m + 1 landed.  B warps: B on planes z0 .. z1 - 1
+// in order, each after A finished plane t + 1 (so A finished t - 1 .. t
+// too); B(t) is the last reader of plane t - 1 (A read it for A(t) and
+// A(t - 1), both finished before A(t + 1)), so it then releases that slot.
+// The A warps run ahead by up to kRing - 3 planes.  Every wait gives up
+// after one second: the block then stops, records the error and lets the
+// copies it issued land before it exits.
 __global__ void __launch_bounds__(kThreads, 1)
 k_corr2_tiled(const __grid_constant__ CUtensorMap tm_e, const __grid_constant__ CUtensorMap tm_r,
               const __grid_constant__ CUtensorMap tm_fx, const __grid_constant__ CUtensorMap tm_fy,
@@ -191,135 +216,145 @@ k_corr2_tiled(const __grid_constant__ CUtensorMap tm_e, const __grid_constant__ 
   if (a.done && *a.done) return;   // converged at an earlier iteration
   extern __shared__ __align__(128) unsigned char smem[];
   TileSlot* ring = reinterpret_cast<TileSlot*>(smem);
-  unsigned long long* bar = reinterpret_cast<unsigned long long*>(smem + kRing * sizeof(TileSlot));
+  unsigned long long* full = reinterpret_cast<unsigned long long*>(smem + kRing * sizeof(TileSlot));
+  unsigned long long* adone = full + kRing;
+  unsigned long long* empty = adone + kRing;
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(empty + kRing);
   const TiledMaps tm{&tm_e, &tm_r, &tm_fx, &tm_fy, &tm_fz};
   const Level& L = a.p.L;
   const int ox = blockIdx.x * kTX, oy = blockIdx.y * kTY;
   const int z0 = blockIdx.z * a.zchunk, z1 = min(z0 + a.zchunk, L.nz);
-  // staged planes z0 - 2 .. z1 + 1, plane m at index q = m - z0 + 2 in
-  // slot q % kRing (use q / kRing of that slot); planes outside the grid
-  // and the parts of a box outside it read as zeros
   const int nq = (z1 - z0) + 4;
-  const int tid = threadIdx.x;
-  const int cA = a.first_color, cB = 1 - cA;
-  int issued = 0;   // planes staged so far (thread 0)
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   if (tid == 0) {
-    for (int sl = 0; sl < kRing; ++sl) mbar_init(&bar[sl], 1);
+    for (int sl = 0; sl < kRing; ++sl) {
+      mbar_init(&full[sl], 1);
+      mbar_init(&adone[sl], kAWarps);
+      mbar_init(&empty[sl], kBWarps);
+    }
+    *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   __syncthreads();
-  if (tid == 0)
-    for (; issued < min(nq, kInFlight + 2); ++issued)
-      stage_plane(tm, ring[issued % kRing], &bar[issued % kRing], ox, oy, z0 - 2 + issued, cB);
-  // roles: warps 0 .. kTY-1 update B on tile row w; warps kTY .. 2kTY+1
-  // update A on rows -1 .. kTY (the ring rows included); lanes 0 .. kTY-1
-  // of the last warp update the A cell of their row on the ring column
-  // (x = ox - 1 or ox + kTX, whichever has colour A)
-  const int warp = tid >> 5, lane = tid & 31;
-  int role, jr;
-  if (warp < kTY) {
-    role = 0;
-    jr = warp;
-  } else if (warp < 2 * kTY + 2) {
-    role = 1;
-    jr = warp - kTY - 1;
-  } else {
-    role = lane < kTY ? 2 : 3;
-    jr = lane;
-  }
-  const int j = oy + jr;
-  const bool row_in = j >= 0 && j < L.ny;
+  auto give_up = [&]() {
+    *abort_flag = 1;
+    atomicExch(a.err, 1);
+  };
   const unsigned half = (unsigned)(L.nx >> 1);
   const size_t cplane = (size_t)L.ny * L.nz * half;
-  // walls of this thread's cells: y fixed by the row, x by the parity of
-  // the cell in the row (rows of roles 0 and 1: i = ox + 2 lane + par;
-  // role 2: i = ox - 1 (par 1) or ox + kTX (par 0))
+
+  if (warp == kBWarps + kAWarps) {
+    // ---- producer
+    if (lane != 0) return;
+    int q = 0;
+    for (; q < nq; ++q) {
+      if (*abort_flag) break;
+      const int sl = q % kRing;
+      if (q >= kRing && !mbar_wait(&empty[sl], ((q - kRing) / kRing) & 1)) {
+        give_up();
+        break;
+      }
+      stage_plane(tm, ring[sl], &full[sl], ox, oy, z0 - 2 + q, cB);
+    }
+    if (*abort_flag) {
+      // let the issued copies land before the block's shared memory goes
+      for (int r = max(0, q - kRing); r < q; ++r) mbar_wait(&full[r % kRing], (r / kRing) & 1);
+    }
+    return;
+  }
+
+  const size_t pstride = (size_t)L.ny * half;   // one plane of one colour
+  if (warp >= kBWarps) {
+    // ---- A warps: rows -1 .. kTY (warps kBWarps .. kBWarps + kTY + 1) and
+    // the ring columns (last A warp, lanes 0 .. kTY - 1: the A cell of the
+    // row at x = ox - 1 or ox + kTX, whichever has colour A)
+    const bool cols = warp == kBWarps + kAWarps - 1;
+    const int jr = cols ? lane : warp - kBWarps - 1;
+    const int j = oy + jr;
+    const bool active = !cols || lane < kTY;
+    const bool row_in = active && j >= 0 && j < L.ny;
+    const float wym = j > 0 ? 1.0f : 0.0f, wyp = j + 1 < L.ny ? 1.0f : 0.0f;
+    // x of the cell for par = 0 and 1 (rows: ox + 2 lane + par; columns:
+    // ox + kTX (even) or ox - 1 (odd)), its walls and packed position
+    const int i0 = cols ? ox + kTX : ox + 2 * lane, i1 = cols ? ox - 1 : ox + 2 * lane + 1;
+    const bool in0 = row_in && i0 < L.nx, in1 = row_in && i1 >= 0 && i1 < L.nx;
+    const float wxm0 = i0 > 0 ? 1.0f : 0.0f, wxp0 = i0 + 1 < L.nx ? 1.0f : 0.0f;
+    const float wxm1 = i1 > 0 ? 1.0f : 0.0f, wxp1 = i1 + 1 < L.nx ? 1.0f : 0.0f;
+    const int pe0 = cols ? kPX + 2 : lane + 2, pe1 = cols ? 1 : lane + 2;
+    // rows store their tile cells: packed position ox/2 + lane of plane m
+    const bool stores = !cols && jr >= 0 && jr < kTY && j < L.ny;
+    float2* out = stores ? a.eout + (size_t)cA * cplane + (size_t)j * half + (ox >> 1) + lane
+                         : a.eout;
+    for (int q = 0; q < 2; ++q)
+      if (!mbar_wait(&full[q], 0)) give_up();
+    // plane z0 - 2 has no A cells but takes the first phase of its slot's
+    // barrier, like every staged plane
+    if (lane == 0) mbar_arrive(&adone[0]);
+    for (int m = z0 - 1; m <= z1; ++m) {
+      if (*abort_flag) break;
+      const int qm = m - z0 + 2, qp = qm + 1;
+      if (!mbar_wait(&full[qp % kRing], (qp / kRing) & 1)) {
+        give_up();
+        break;
+      }
+      if (active) {
+        // colour A at (x, j, m): rows par = (j + m + cA) & 1; columns par = 1
+        // when x = ox - 1 has colour A
+        const int par = cols ? ((ox - 1 + j + m + cA) & 1) ^ 1 : (j + m + cA) & 1;
+        const int pe = par ? pe1 : pe0;
+        TileSlot& S0 = ring[qm % kRing];
+        if ((par ? in1 : in0) && m >= 0 && m < L.nz) {
+          const float w[6] = {par ? wxm1 : wxm0, par ? wxp1 : wxp0, wym, wyp,
+                              m > 0 ? 1.0f : 0.0f, m + 1 < L.nz ? 1.0f : 0.0f};
+          const float2 ne = tiled_cell(a.p, S0, ring[(qm + kRing - 1) % kRing],
+                                       ring[qp % kRing], cA, pe, jr + 2, par, w, true);
+          if (stores && m >= z0 && m < z1) out[(size_t)m * pstride] = ne;
+        } else {
+          S0.e[cA][jr + 2][pe] = make_float2(0.0f, 0.0f);   // the neighbour of a wall
+        }
+      }
+      // the slot is refilled by tensor copies later: order these shared
+      // writes before them, then signal the plane done
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&adone[qm % kRing]);
+    }
+    return;
+  }
+
+  // ---- B warps: tile row jr = warp, cell x = ox + 2 lane + par (nx is a
+  // multiple of 8: both parities are in or out together)
+  const int jr = warp, j = oy + jr;
+  const bool in = j < L.ny && ox + 2 * lane < L.nx;
   const float wym = j > 0 ? 1.0f : 0.0f, wyp = j + 1 < L.ny ? 1.0f : 0.0f;
-  const int i0 = role == 2 ? ox + kTX : ox + 2 * lane, i1 = role == 2 ? ox - 1 : ox + 2 * lane + 1;
+  const int i0 = ox + 2 * lane, i1 = i0 + 1;
   const float wxm0 = i0 > 0 ? 1.0f : 0.0f, wxp0 = i0 + 1 < L.nx ? 1.0f : 0.0f;
   const float wxm1 = i1 > 0 ? 1.0f : 0.0f, wxp1 = i1 + 1 < L.nx ? 1.0f : 0.0f;
-  // this thread's cell at step st: B on plane t = z0 - 3 + st (role 0) or
-  // A on plane t + 2 (roles 1, 2); upd: update it; zero: an A position
-  // outside the grid, which holds zero (the neighbour of a wall)
-  struct Cell {
-    int plane, i, par, pe;
-    bool upd, zero;
-  };
-  auto cell_at = [&](int st) {
-    Cell c{0, 0, 0, 0, false, false};
-    const int t = z0 - 3 + st;
-    if (role == 0) {
-      c.plane = t;
-      c.par = (j + t + cB) & 1;
-      c.i = ox + 2 * lane + c.par;
-      c.pe = lane + 2;
-      c.upd = row_in && t >= z0 && t < z1 && c.i < L.nx;
-    } else if (role <= 2) {
-      const int m = t + 2;
-      c.plane = m;
-      if (role == 1) {
-        c.par = (j + m + cA) & 1;
-        c.i = ox + 2 * lane + c.par;
-        c.pe = lane + 2;
-      } else {
-        c.par = ((ox - 1 + j + m) & 1) == cA ? 1 : 0;   // x = ox - 1 is odd
-        c.i = c.par ? ox - 1 : ox + kTX;
-        c.pe = c.par ? 1 : kPX + 2;
-      }
-      const bool in_chunk = m >= z0 - 1 && m <= z1;   // the B cells' neighbour planes
-      c.upd = in_chunk && row_in && m >= 0 && m < L.nz && c.i >= 0 && c.i < L.nx;
-      c.zero = in_chunk && !c.upd;
-    }
-    return c;
-  };
-  bool ok = true;
-  for (int q = 0; q < min(nq, 2); ++q) ok = mbar_wait(&bar[q % kRing], (q / kRing) & 1) && ok;
-  const int nsteps = (z1 - z0) + 3;
-  bool aborted = false;
-  for (int st = 0; st < nsteps; ++st) {
-    // stage plane st + kInFlight + 2 into the slot that plane st - 3 left
-    // (last read in step st - 1)
-    if (tid == 0 && issued < nq) {
-      stage_plane(tm, ring[issued % kRing], &bar[issued % kRing], ox, oy, z0 - 2 + issued, cB);
-      ++issued;
-    }
-    const Cell c = cell_at(st);
-    const int qn = st + 2;   // the newest plane this step reads
-    if (qn < nq) ok = mbar_wait(&bar[qn % kRing], (qn / kRing) & 1) && ok;
-    // slots of planes t - 1 .. t + 3 (staged indices st - 2 .. st + 2)
-    const int s2 = st % kRing;
-    const int s1 = s2 == 0 ? kRing - 1 : s2 - 1, s0 = s1 == 0 ? kRing - 1 : s1 - 1;
-    const int s3 = s2 == kRing - 1 ? 0 : s2 + 1, s4 = s3 == kRing - 1 ? 0 : s3 + 1;
-    if (ok && c.upd) {
-      const float w[6] = {c.par ? wxm1 : wxm0, c.par ? wxp1 : wxp0, wym, wyp,
-                          c.plane > 0 ? 1.0f : 0.0f, c.plane + 1 < L.nz ? 1.0f : 0.0f};
-      if (role == 0) {
-        const float2 ne = tiled_cell(a.p, ring[s1], ring[s0], ring[s2], cB, c.pe, jr + 2, c.par,
-                                     w, false);
-        a.eout[(size_t)cB * cplane + ((size_t)c.plane * L.ny + j) * half + (c.i >> 1)] = ne;
-      } else {
-        const float2 ne = tiled_cell(a.p, ring[s3], ring[s2], ring[s4], cA, c.pe, jr + 2, c.par,
-                                     w, true);
-        if (role == 1 && jr >= 0 && jr < kTY && c.plane >= z0 && c.plane < z1)
-          a.eout[(size_t)cA * cplane + ((size_t)c.plane * L.ny + j) * half + (c.i >> 1)] = ne;
-      }
-    } else if (ok && c.zero) {
-      ring[s3].e[cA][jr + 2][c.pe] = make_float2(0.0f, 0.0f);
-    }
-    // the next step's copy refills a slot this step may have written:
-    // order the shared writes before it
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    if (__syncthreads_or(!ok)) {
-      aborted = true;
+  float2* out = in ? a.eout + (size_t)cB * cplane + (size_t)j * half + (ox >> 1) + lane : a.eout;
+  for (int t = z0; t < z1; ++t) {
+    if (*abort_flag) break;
+    const int qt = t - z0 + 2, qp = qt + 1;
+    // A finished plane t + 1 (and so t - 1 .. t); the planes' copies landed
+    if (!mbar_wait(&adone[qp % kRing], (qp / kRing) & 1) ||
+        !mbar_wait(&full[qp % kRing], (qp / kRing) & 1)) {
+      give_up();
       break;
     }
-  }
-  if (aborted && tid == 0) {
-    atomicExch(a.err, 1);
-    // let the copies already issued land before the block's shared memory
-    // is released (each wait is bounded)
-    for (int q = max(0, issued - kRing); q < issued; ++q)
-      mbar_wait(&bar[q % kRing], (q / kRing) & 1);
+    if (in) {
+      const int par = (j + t + cB) & 1;
+      const float w[6] = {par ? wxm1 : wxm0, par ? wxp1 : wxp0, wym, wyp, t > 0 ? 1.0f : 0.0f,
+                          t + 1 < L.nz ? 1.0f : 0.0f};
+      out[(size_t)t * pstride] = tiled_cell(a.p, ring[qt % kRing], ring[(qt - 1) % kRing],
+                                            ring[qp % kRing], cB, lane + 2, jr + 2, par, w,
+                                            false);
+    }
+    // the last reads of plane t - 1 (and, at the first plane, of z0 - 2,
+    // which only the A warps read)
+    __syncwarp();
+    if (lane == 0) {
+      mbar_arrive(&empty[(qt - 1) % kRing]);
+      if (t == z0) mbar_arrive(&empty[0]);
+    }
   }
 }
 
@@ -404,7 +439,7 @@ sfx_status tiled_sweep(sfx_ctx* c, const Nw32& p, int in_buf, const int* done,
   F32Scratch& S = c->f32;
   const Level& L = p.L;
   const int zc = std::max(1, S.tiled_zchunk);
-  TiledArgs a{p, in_buf == 0 ? S.e2b : S.e2, 1, zc, S.flag + 3, done};
+  TiledArgs a{p, in_buf == 0 ? S.e2b : S.e2, zc, S.flag + 3, done};
   const dim3 grd((unsigned)((L.nx + kTX - 1) / kTX), (unsigned)((L.ny + kTY - 1) / kTY),
                  (unsigned)((L.nz + zc - 1) / zc));
   const CUtensorMap* tm = reinterpret_cast<const CUtensorMap*>(S.tmaps);
