@@ -27,6 +27,7 @@
 #include <cudaTypedefs.h>
 
 #include <algorithm>
+#include <type_traits>
 
 #include "sfx_df.cuh"
 #include "sfx_f32_dev.cuh"
@@ -207,8 +208,9 @@ __device__ __forceinline__ void stage_plane(const TiledMaps& tm, TileSlot& S,
 // too); B(t) is the last reader of plane t - 1 (A read it for A(t) and
 // A(t - 1), both finished before A(t + 1)), so it then releases that slot.
 // The A warps run ahead by up to kRing - 3 planes.  Every wait gives up
-// after one second: the block then stops, records the error and lets the
-// copies it issued land before it exits.
+// after one second: that warp stops and records the error, the waits of
+// the others then give up in turn, and the producer lets the copies it
+// issued land before it exits.
 __global__ void __launch_bounds__(kThreads, 1)
 k_corr2_tiled(const __grid_constant__ CUtensorMap tm_e, const __grid_constant__ CUtensorMap tm_r,
               const __grid_constant__ CUtensorMap tm_fx, const __grid_constant__ CUtensorMap tm_fy,
@@ -267,58 +269,63 @@ k_corr2_tiled(const __grid_constant__ CUtensorMap tm_e, const __grid_constant__ 
   if (warp >= kBWarps) {
     // ---- A warps: rows -1 .. kTY (warps kBWarps .. kBWarps + kTY + 1) and
     // the ring columns (last A warp, lanes 0 .. kTY - 1: the A cell of the
-    // row at x = ox - 1 or ox + kTX, whichever has colour A)
-    const bool cols = warp == kBWarps + kAWarps - 1;
-    const int jr = cols ? lane : warp - kBWarps - 1;
-    const int j = oy + jr;
-    const bool active = !cols || lane < kTY;
-    const bool row_in = active && j >= 0 && j < L.ny;
-    const float wym = j > 0 ? 1.0f : 0.0f, wyp = j + 1 < L.ny ? 1.0f : 0.0f;
-    // x of the cell for par = 0 and 1 (rows: ox + 2 lane + par; columns:
-    // ox + kTX (even) or ox - 1 (odd)), its walls and packed position
-    const int i0 = cols ? ox + kTX : ox + 2 * lane, i1 = cols ? ox - 1 : ox + 2 * lane + 1;
-    const bool in0 = row_in && i0 < L.nx, in1 = row_in && i1 >= 0 && i1 < L.nx;
-    const float wxm0 = i0 > 0 ? 1.0f : 0.0f, wxp0 = i0 + 1 < L.nx ? 1.0f : 0.0f;
-    const float wxm1 = i1 > 0 ? 1.0f : 0.0f, wxp1 = i1 + 1 < L.nx ? 1.0f : 0.0f;
-    const int pe0 = cols ? kPX + 2 : lane + 2, pe1 = cols ? 1 : lane + 2;
-    // rows store their tile cells: packed position ox/2 + lane of plane m
-    const bool stores = !cols && jr >= 0 && jr < kTY && j < L.ny;
-    float2* out = stores ? a.eout + (size_t)cA * cplane + (size_t)j * half + (ox >> 1) + lane
-                         : a.eout;
-    for (int q = 0; q < 2; ++q)
-      if (!mbar_wait(&full[q], 0)) give_up();
-    // plane z0 - 2 has no A cells but takes the first phase of its slot's
-    // barrier, like every staged plane
-    if (lane == 0) mbar_arrive(&adone[0]);
-    for (int m = z0 - 1; m <= z1; ++m) {
-      if (*abort_flag) break;
-      const int qm = m - z0 + 2, qp = qm + 1;
-      if (!mbar_wait(&full[qp % kRing], (qp / kRing) & 1)) {
-        give_up();
-        break;
-      }
-      if (active) {
-        // colour A at (x, j, m): rows par = (j + m + cA) & 1; columns par = 1
-        // when x = ox - 1 has colour A
-        const int par = cols ? ((ox - 1 + j + m + cA) & 1) ^ 1 : (j + m + cA) & 1;
-        const int pe = par ? pe1 : pe0;
-        TileSlot& S0 = ring[qm % kRing];
-        if ((par ? in1 : in0) && m >= 0 && m < L.nz) {
-          const float w[6] = {par ? wxm1 : wxm0, par ? wxp1 : wxp0, wym, wyp,
-                              m > 0 ? 1.0f : 0.0f, m + 1 < L.nz ? 1.0f : 0.0f};
-          const float2 ne = tiled_cell(a.p, S0, ring[(qm + kRing - 1) % kRing],
-                                       ring[qp % kRing], cA, pe, jr + 2, par, w, true);
-          if (stores && m >= z0 && m < z1) out[(size_t)m * pstride] = ne;
-        } else {
-          S0.e[cA][jr + 2][pe] = make_float2(0.0f, 0.0f);   // the neighbour of a wall
+    // row at x = ox - 1 or ox + kTX, whichever has colour A); one loop body
+    // per kind (COLS a compile-time constant)
+    auto a_loop = [&](auto cols_tag) {
+      constexpr bool COLS = decltype(cols_tag)::value;
+      const int jr = COLS ? lane : warp - kBWarps - 1;
+      const int j = oy + jr;
+      const bool active = !COLS || lane < kTY;
+      const bool row_in = active && j >= 0 && j < L.ny;
+      const float wym = j > 0 ? 1.0f : 0.0f, wyp = j + 1 < L.ny ? 1.0f : 0.0f;
+      // x of the cell for par = 0 and 1 (rows: ox + 2 lane + par; columns:
+      // ox + kTX (even) or ox - 1 (odd)), its walls and packed position
+      const int i0 = COLS ? ox + kTX : ox + 2 * lane, i1 = COLS ? ox - 1 : ox + 2 * lane + 1;
+      const bool in0 = row_in && i0 < L.nx, in1 = row_in && i1 >= 0 && i1 < L.nx;
+      const float wxm0 = i0 > 0 ? 1.0f : 0.0f, wxp0 = i0 + 1 < L.nx ? 1.0f : 0.0f;
+      const float wxm1 = i1 > 0 ? 1.0f : 0.0f, wxp1 = i1 + 1 < L.nx ? 1.0f : 0.0f;
+      // rows store their tile cells: packed position ox/2 + lane of plane m
+      const bool stores = !COLS && jr >= 0 && jr < kTY && j < L.ny;
+      float2* out = stores ? a.eout + (size_t)cA * cplane + (size_t)j * half + (ox >> 1) + lane
+                           : a.eout;
+      for (int q = 0; q < 2; ++q)
+        if (!mbar_wait(&full[q], 0)) give_up();
+      // plane z0 - 2 has no A cells but takes the first phase of its slot's
+      // barrier, like every staged plane
+      if (lane == 0) mbar_arrive(&adone[0]);
+      for (int m = z0 - 1; m <= z1; ++m) {
+        const int qm = m - z0 + 2, qp = qm + 1;
+        if (!mbar_wait(&full[qp % kRing], (qp / kRing) & 1)) {
+          give_up();
+          break;
         }
+        if (active) {
+          // colour A at (x, j, m): rows par = (j + m + cA) & 1; columns
+          // par = 1 when x = ox - 1 has colour A
+          const int par = COLS ? ((ox - 1 + j + m + cA) & 1) ^ 1 : (j + m + cA) & 1;
+          const int pe = COLS ? (par ? 1 : kPX + 2) : lane + 2;
+          TileSlot& S0 = ring[qm % kRing];
+          if ((par ? in1 : in0) && m >= 0 && m < L.nz) {
+            const float w[6] = {par ? wxm1 : wxm0, par ? wxp1 : wxp0, wym, wyp,
+                                m > 0 ? 1.0f : 0.0f, m + 1 < L.nz ? 1.0f : 0.0f};
+            const float2 ne = tiled_cell(a.p, S0, ring[(qm + kRing - 1) % kRing],
+                                         ring[qp % kRing], cA, pe, jr + 2, par, w, true);
+            if (stores && m >= z0 && m < z1) out[(size_t)m * pstride] = ne;
+          } else {
+            S0.e[cA][jr + 2][pe] = make_float2(0.0f, 0.0f);   // the neighbour of a wall
+          }
+        }
+        // the slot is refilled by tensor copies later: order these shared
+        // writes before them, then signal the plane done
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&adone[qm % kRing]);
       }
-      // the slot is refilled by tensor copies later: order these shared
-      // writes before them, then signal the plane done
-      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      __syncwarp();
-      if (lane == 0) mbar_arrive(&adone[qm % kRing]);
-    }
+    };
+    if (warp == kBWarps + kAWarps - 1)
+      a_loop(std::true_type{});
+    else
+      a_loop(std::false_type{});
     return;
   }
 
@@ -332,7 +339,6 @@ k_corr2_tiled(const __grid_constant__ CUtensorMap tm_e, const __grid_constant__ 
   const float wxm1 = i1 > 0 ? 1.0f : 0.0f, wxp1 = i1 + 1 < L.nx ? 1.0f : 0.0f;
   float2* out = in ? a.eout + (size_t)cB * cplane + (size_t)j * half + (ox >> 1) + lane : a.eout;
   for (int t = z0; t < z1; ++t) {
-    if (*abort_flag) break;
     const int qt = t - z0 + 2, qp = qt + 1;
     // A finished plane t + 1 (and so t - 1 .. t); the planes' copies landed
     if (!mbar_wait(&adone[qp % kRing], (qp / kRing) & 1) ||
