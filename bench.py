@@ -109,8 +109,9 @@ def parse():
     ap.add_argument("--tiled", type=int, default=1, choices=[0, 1],
                     help="FP32 3D: whole red-black sweeps as tiled launches "
                          "(SFX_TUNE_TILED_SWEEP)")
-    ap.add_argument("--tiled-zchunk", type=int, default=32,
-                    help="z-planes per block of the tiled sweep (SFX_TUNE_TILED_ZCHUNK)")
+    ap.add_argument("--tiled-zchunk", type=int, default=0,
+                    help="z-planes per block of the tiled sweep (SFX_TUNE_TILED_ZCHUNK; "
+                         "0 = chosen from the grid)")
     ap.add_argument("--fast-resid", type=int, default=2,
                     help="FP32: Newton iterations per solve with FP32 residuals "
                          "(SFX_TUNE_F32_FAST_RESID; 0 = pair residuals only)")
@@ -639,7 +640,8 @@ def run_gpu(a, case, rank, world, local_rank):
                                "dt=%g, tol=%g" % (case.name, g.nx, case.dt, a.tol),
                    "cells": g.ncell, "precision": a.precision,
                    "newton_start": "x* + last increment" if a.predict else "x*",
-                   "sweeps": "tiled (whole sweep per launch, zchunk %d)" % a.tiled_zchunk
+                   "sweeps": "tiled (whole sweep per launch, zchunk %s)" % (
+                             a.tiled_zchunk or "auto")
                              if (a.tiled and prec == sfx.SFX_F32) else "one launch per colour",
                    "residuals": ("FP32 for up to %d Newton iterations per step (while the "
                                  "relative residual is above 1e-3), then pair arithmetic"

@@ -362,7 +362,9 @@ typedef enum {
                                gives up (after 1 s) ends the step with
                                SFX_ERR_TIMEOUT. */
   SFX_TUNE_TILED_ZCHUNK = 7, /* z-planes per block of the tiled sweep, 4 ..
-                               4096 (default 32). */
+                               4096, or 0 (default): chosen from the grid
+                               and the SM count to fill the last wave of
+                               blocks (37 at 256^3 on 152 SMs). */
   SFX_TUNE_F32_FAST_RESID = 8, /* SFX_F32 Newton solver: at most this many
                                iterations per solve (0 .. 16, default 2)
                                evaluate the residuals in FP32 instead of

@@ -391,7 +391,7 @@ sfx_status sfx_set_tuning(sfx_ctx* c, int key, int value) {
     c->f32.fast_resid = value;
     return SFX_OK;
   }
-  if (key == SFX_TUNE_TILED_ZCHUNK && value >= 4 && value <= 4096) {
+  if (key == SFX_TUNE_TILED_ZCHUNK && (value == 0 || (value >= 4 && value <= 4096))) {
     c->f32.tiled_zchunk = value;
     return SFX_OK;
   }

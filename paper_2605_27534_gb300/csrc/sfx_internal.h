@@ -102,7 +102,7 @@ struct F32Scratch {
   // e2, e2b, rc and the three face arrays
   bool tiled = true;                    // use it where eligible (SFX_TUNE_TILED_SWEEP)
   bool tiled_ready = false;
-  int tiled_zchunk = 32;                // planes per block
+  int tiled_zchunk = 0;                 // planes per block (0: chosen from the grid)
   float2* e2b = nullptr;
   __half2* Hm[3] = {};
   alignas(64) unsigned char tmaps[6][128] = {};

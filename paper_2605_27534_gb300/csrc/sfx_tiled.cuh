@@ -440,11 +440,32 @@ sfx_status tiled_sweep_prepare(sfx_ctx* c) {
   return SFX_OK;
 }
 
+// Planes per block: one block per SM at a time, so the launch takes
+// ceil(blocks / SMs) waves of blocks whose time grows with their planes
+// plus the chunk's overhead (two extra A planes and the pipeline fill,
+// about three planes); the chunk length in [4, 64] that minimises
+// waves x (planes + 3).
+int tiled_zchunk_auto(const Level& L, int sms) {
+  const long long tiles = (long long)((L.nx + kTX - 1) / kTX) * ((L.ny + kTY - 1) / kTY);
+  int best = 32;
+  long long best_cost = -1;
+  for (int zc = 4; zc <= 64; ++zc) {
+    const long long chunks = (L.nz + zc - 1) / zc;
+    const long long waves = (tiles * chunks + sms - 1) / sms;
+    const long long cost = waves * (zc + 3);
+    if (best_cost < 0 || cost < best_cost) {
+      best = zc;
+      best_cost = cost;
+    }
+  }
+  return std::min(best, std::max(L.nz, 1));
+}
+
 sfx_status tiled_sweep(sfx_ctx* c, const Nw32& p, int in_buf, const int* done,
                        cudaStream_t s) {
   F32Scratch& S = c->f32;
   const Level& L = p.L;
-  const int zc = std::max(1, S.tiled_zchunk);
+  const int zc = S.tiled_zchunk > 0 ? S.tiled_zchunk : tiled_zchunk_auto(L, c->sm_count);
   TiledArgs a{p, in_buf == 0 ? S.e2b : S.e2, zc, S.flag + 3, done};
   const dim3 grd((unsigned)((L.nx + kTX - 1) / kTX), (unsigned)((L.ny + kTY - 1) / kTY),
                  (unsigned)((L.nz + zc - 1) / zc));
