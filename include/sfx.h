@@ -535,6 +535,7 @@ typedef enum {
   SFX_K_PHASE,            /* redistancing and phase field */
   SFX_K_OTHER,
   SFX_K_SMOOTH_TILED,     /* tiled red-black sweep (both colours), fine level */
+  SFX_K_RESID_FAST,       /* FP32 residual passes of the FP32 Newton solve */
   SFX_K_COUNT
 } sfx_kernel_kind;
 
@@ -547,6 +548,13 @@ sfx_status sfx_profile(sfx_ctx* ctx, int on);
    the recorded events.  Any output pointer may be NULL. */
 sfx_status sfx_profile_read(sfx_ctx* ctx, int kind, long long* launches,
                             double* total_ms, long long* timed);
+/* Of the launches of `kind` since the last sfx_profile(ctx, 1), those that
+   did work, where the library can tell: the residual passes of the FP32
+   Newton solve (SFX_K_RESIDUAL, SFX_K_RESID_FAST), of which each iteration
+   launches both kinds and one returns at once, counted from the residual
+   kind recorded with the iteration's norms (iterations whose norms the
+   solve read); -1 for the other kinds.  SFX_ERR_ARG on a bad kind. */
+sfx_status sfx_profile_work(sfx_ctx* ctx, int kind, long long* working);
 
 #ifdef __cplusplus
 }

@@ -191,6 +191,17 @@ class Context:
             out[name] = (n.value, ms.value, nt.value)
         return out
 
+    def sfx_profile_work(self):
+        """{kind: launches that did work} for the kinds the library counts
+        (the FP32 Newton solve's residual passes)."""
+        out = {}
+        for k, name in enumerate(_lib.KERNEL_KINDS):
+            w = C.c_longlong(0)
+            _check(lib().sfx_profile_work(self._h, k, C.byref(w)), "sfx_profile_work")
+            if w.value >= 0:
+                out[name] = w.value
+        return out
+
     # ------------------------------------------------------------ adjoint
     def sfx_f_from_gamma(self, gamma, phi, eps, out=None):
         """f = Gamma delta_phi (double tensors); also maps dL/df to dL/dGamma."""

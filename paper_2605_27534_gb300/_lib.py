@@ -26,7 +26,7 @@ EXPORTS = [
     "sfx_batch_layout", "sfx_batch_set_schedule", "sfx_batch_step", "sfx_batch_stats",
     "sfx_batch_autotune", "sfx_batch_work", "sfx_f_from_gamma", "sfx_marangoni_loss",
     "sfx_adjoint_apply", "sfx_adjoint_step", "sfx_vof_advect", "sfx_capillary_force", "sfx_acdi_step", "sfx_batch_reuse_phi",
-    "sfx_phase_field_from_chi",
+    "sfx_phase_field_from_chi", "sfx_profile_work",
 ]
 SFX_TUNE_FUSED_SWEEP = 0
 SFX_TUNE_F32_SOLVER = 1
@@ -38,7 +38,8 @@ SFX_TUNE_TILED_SWEEP = 6
 SFX_TUNE_TILED_ZCHUNK = 7
 SFX_TUNE_F32_FAST_RESID = 8
 KERNEL_KINDS = ["smooth_fine", "smooth_coarse", "restrict", "prolong", "setup", "residual",
-                "advect", "totals", "forces", "phase", "other", "smooth_tiled"]
+                "advect", "totals", "forces", "phase", "other", "smooth_tiled",
+                "residual_fp32"]
 
 
 class Grid(C.Structure):
@@ -119,6 +120,8 @@ def load(path: str = SO_PATH):
     L.sfx_profile_read.restype = C.c_int
     L.sfx_profile_read.argtypes = [vp, C.c_int, C.POINTER(C.c_longlong), C.POINTER(C.c_double),
                                    C.POINTER(C.c_longlong)]
+    L.sfx_profile_work.restype = C.c_int
+    L.sfx_profile_work.argtypes = [vp, C.c_int, C.POINTER(C.c_longlong)]
     L.sfx_df_pack.restype = C.c_int
     L.sfx_df_pack.argtypes = [vp, vp, C.c_size_t, vp]
     L.sfx_df_unpack.restype = C.c_int

@@ -421,9 +421,16 @@ sfx_status sfx_profile(sfx_ctx* c, int on) {
   if (!c) return SFX_ERR_ARG;
   if (on) {
     for (int k = 0; k < K_COUNT; ++k) c->prof.launches[k] = 0;
+    c->prof.work[0] = c->prof.work[1] = 0;
     c->prof.used = 0;
   }
   c->prof.on = on != 0;
+  return SFX_OK;
+}
+
+sfx_status sfx_profile_work(sfx_ctx* c, int kind, long long* working) {
+  if (!c || kind < 0 || kind >= K_COUNT || !working) return SFX_ERR_ARG;
+  *working = kind == K_RESID_FAST ? c->prof.work[0] : (kind == K_RESIDUAL ? c->prof.work[1] : -1);
   return SFX_OK;
 }
 

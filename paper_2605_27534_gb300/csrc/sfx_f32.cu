@@ -1411,7 +1411,7 @@ sfx_status solve_newton32(sfx_ctx* c, const Nw32& p, const float* phi, float* co
     const float2* fsrc = star ? fs : fc;
     const float2* Fsrc = star ? Fs : Fc;
     // the FP32 or the pair residual pass, as chosen on the device
-    SFX_KERNEL(c, K_RESIDUAL, nk.fast, rg.grid, rg.block, s, p, phi, B2[0], B2[1], B2[2], fsrc,
+    SFX_KERNEL(c, K_RESID_FAST, nk.fast, rg.grid, rg.block, s, p, phi, B2[0], B2[1], B2[2], fsrc,
                Fsrc, fs, Fs, c->f32.rc, nbuf, c->f32.e2, flag, flag + 4);
     SFX_KERNEL(c, K_RESIDUAL, nk.resid, rg.grid, rg.block, s, p, phi, B2[0], B2[1], B2[2], fsrc,
                Fsrc, fs, Fs, c->f32.rc, nbuf, c->f32.e2, flag, flag + 4);
@@ -1422,7 +1422,7 @@ sfx_status solve_newton32(sfx_ctx* c, const Nw32& p, const float* phi, float* co
       const float rho = c->f32.predict_rho;
       SFX_KERNEL(c, K_OTHER, k_pred_check32, 1, 32, s, nbuf, rho, ok);
       SFX_KERNEL(c, K_SETUP, k_restore32, nb, 256, s, n, ok, fs, Fs, fc, Fc);
-      SFX_KERNEL(c, K_RESIDUAL, nk.fast, rg.grid, rg.block, s, p, phi, B2[0], B2[1], B2[2],
+      SFX_KERNEL(c, K_RESID_FAST, nk.fast, rg.grid, rg.block, s, p, phi, B2[0], B2[1], B2[2],
                  fc, Fc, fs, Fs, c->f32.rc, nbuf, c->f32.e2, ok, flag + 4);
       SFX_KERNEL(c, K_RESIDUAL, nk.resid, rg.grid, rg.block, s, p, phi, B2[0], B2[1], B2[2],
                  fc, Fc, fs, Fs, c->f32.rc, nbuf, c->f32.e2, ok, flag + 4);
@@ -1473,6 +1473,7 @@ sfx_status solve_newton32(sfx_ctx* c, const Nw32& p, const float* phi, float* co
       SFX_CUDA(cudaEventSynchronize(c->f32.ev[prev & 1]));
       const unsigned int* hb = hn + 8 * (prev & 1);
       if (hb[1] == kTimeoutBits) return SFX_ERR_TIMEOUT;
+      ++c->prof.work[hb[4] == 1u ? 1 : 0];   // the residual kind of iteration prev
       memcpy(nrm, hb, 4 * sizeof(float));
       for (int q = 0; q < 4; ++q)
         if (!std::isfinite(nrm[q])) return SFX_ERR_NONFINITE;
@@ -1494,6 +1495,7 @@ sfx_status solve_newton32(sfx_ctx* c, const Nw32& p, const float* phi, float* co
     const int last = std::min(it, o->max_cycles);
     const unsigned int* hb = hn + 8 * (last & 1);
     if (hb[1] == kTimeoutBits) return SFX_ERR_TIMEOUT;
+    ++c->prof.work[hb[4] == 1u ? 1 : 0];   // the residual kind of the last iteration
     if (tiled) {
       int err = 0;
       SFX_CUDA(cudaMemcpy(&err, flag + 3, sizeof(int), cudaMemcpyDeviceToHost));

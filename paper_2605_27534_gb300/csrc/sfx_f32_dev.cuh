@@ -68,6 +68,8 @@ struct Nl32 {
   int literal;
 };
 
+#include "sfx_corr3.cuh"
+
 // Area weight of a face relative to h^(d-1) (planar, 3D: 1) or to pi h^2
 // (axisymmetric: 2 i for the radial face at r = i h, 2 i + 1 for the axial
 // faces of column i); the cell volume over the same unit times h is w_c h.
@@ -126,12 +128,6 @@ __device__ __forceinline__ void drift_face(float sL, float sR, float nL, float n
   bf = 0.5f * ((-Df * 2.0f * hL * inv_eps) * nL + (-Df * 2.0f * hR * inv_eps) * nR);
   bF = 0.5f * ((-DF * uL.q * inv_eps) * nL + (-DF * uR.q * inv_eps) * nR);
 }
-
-struct Nw32 {
-  Level L;
-  float invh, Dfh, DFh, inv_dt, ka, kd, ginf, inv_eps, eta;
-  int literal;
-};
 
 // Cell and face indices of the FP32 kernels are 32-bit: an SFX_F32 context
 // refuses grids whose cells or faces reach 2^31 (sfx_ctx_create).
@@ -418,19 +414,6 @@ __device__ __forceinline__ void face32v2(const Adv32& A, const float2* __restric
 // half-sweep of the correction is done here: it starts from zero
 // corrections, so a red cell (i + j + k even) only needs its own 2x2 block,
 // e = M_c^-1 r_c.
-// Kinetic part of the pointwise 2x2 Jacobian of the App. C exchange at one
-// cell, from u = c1 F and v = c1 (f_inf - f) (c1 = r_a/(phi + eta)):
-//   [ff  -fF] = [1/dt + r_d + u    -v      ]
-//   [-Ff  FF]   [-(u + r_d)        1/dt + v]
-// (the flux operators add their diagonal weights to ff and FF).
-struct Jac2 {
-  float ff, fF, Ff, FF;
-};
-__device__ __forceinline__ Jac2 jac2(const Nw32& p, float u, float v) {
-  return Jac2{__fadd_rn(__fadd_rn(p.inv_dt, p.kd), u), v, __fadd_rn(u, p.kd),
-              __fadd_rn(p.inv_dt, v)};
-}
-
 template <int G>
 __device__ __forceinline__ void resid2_cell(const Nw32& p, int i, int j, int k, ix c,
                                             const float* __restrict__ phi,
@@ -624,60 +607,6 @@ __device__ __forceinline__ float2 corr2_block(const Nw32& p, float4 q4, float ef
   const float inv = __fdividef(1.0f, det);
   return make_float2(__fmaf_rn(__fmaf_rn(e, rhof, __fmul_rn(bb, rhoF)), inv, efc),
                      __fmaf_rn(__fmaf_rn(d, rhof, __fmul_rn(a, rhoF)), inv, eFc));
-}
-
-// The 3D sweeps' flux of one field's correction in neighbour-coefficient
-// form (the same linear operator as flux_lin, fewer instructions: no
-// selects).  A face with drift B between cells L and R carries
-//   G = D (e_R - e_L)/h + B e_up = (alpha e_R - beta e_L)/h,
-//   alpha = D + max(B, 0), beta = D - min(B, 0)      (upwind on -B),
-//   alpha = D + min(B, 0), beta = D - max(B, 0)      (literal: on +B),
-// each from t = D +- |B|/2 and +-B/2 (exact halves) in FMA instructions.
-// For a cell the plus faces' neighbours enter with alpha and the cell with
-// beta, the minus faces' the other way round: the flux is
-// (nbs - dg e_c)/h with nbs = sum of the neighbours' terms and dg the sum
-// over open faces (w = 1) of the cell's terms.  A closed face's neighbour
-// value is zero, so it adds nothing to nbs.  hs = +1/2 (upwind on -B) or
-// -1/2 (literal).
-__device__ __forceinline__ void nb3(float Doh, float hs, const float* en, const float* w,
-                                    const float* B, float& nbs, float& dg) {
-  float s = 0.0f, d = 0.0f;
-#pragma unroll
-  for (int q = 0; q < 6; ++q) {
-    const float t = __fmaf_rn(hs, fabsf(B[q]), Doh);
-    const float al = __fmaf_rn(0.5f, B[q], t), be = __fmaf_rn(-0.5f, B[q], t);
-    s = __fmaf_rn((q & 1) ? al : be, en[q], s);
-    d = __fmaf_rn(w[q], (q & 1) ? be : al, d);
-  }
-  nbs = s;
-  dg = d;
-}
-
-// The block Gauss-Seidel update of one 3D cell in the neighbour-coefficient
-// form: the new correction solves the 2x2 system M e = r + (neighbour sums)
-// directly (M = the exchange Jacobian plus the flux diagonals), so the
-// cell's own old value does not enter.  nbf, nbF, dgf, dgF already over h.
-__device__ __forceinline__ float2 corr2_block_nb(const Nw32& p, float4 q4, float nbf, float nbF,
-                                                 float dgf, float dgF) {
-  const Jac2 J = jac2(p, q4.z, q4.w);
-  const float a = __fadd_rn(J.ff, dgf), bb = J.fF, d = J.Ff, e = __fadd_rn(J.FF, dgF);
-  const float sf = __fadd_rn(q4.x, nbf), sF = __fadd_rn(q4.y, nbF);
-  const float inv = __fdividef(1.0f, __fmaf_rn(a, e, -__fmul_rn(bb, d)));
-  return make_float2(__fmul_rn(__fmaf_rn(e, sf, __fmul_rn(bb, sF)), inv),
-                     __fmul_rn(__fmaf_rn(d, sf, __fmul_rn(a, sF)), inv));
-}
-
-// One 3D correction cell from its gathered inputs (both sweeps of 3D
-// grids, the colour launch and the tiled one, so they agree bit for bit).
-__device__ __forceinline__ float2 corr3_cell(const Nw32& p, const float* enf, const float* enF,
-                                            const float* w, const float* Bf, const float* BF,
-                                            float4 q4) {
-  const float hs = p.literal ? -0.5f : 0.5f;
-  float nbf, nbF, dgf, dgF;
-  nb3(p.Dfh, hs, enf, w, Bf, nbf, dgf);
-  nb3(p.DFh, hs, enF, w, BF, nbF, dgF);
-  return corr2_block_nb(p, q4, __fmul_rn(nbf, p.invh), __fmul_rn(nbF, p.invh),
-                        __fmul_rn(dgf, p.invh), __fmul_rn(dgF, p.invh));
 }
 
 template <int G>

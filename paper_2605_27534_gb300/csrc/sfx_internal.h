@@ -34,7 +34,7 @@ struct LevelData {
 // on the launching stream) per context; values match sfx_kernel_kind.
 enum Kind {
   K_SMOOTH_FINE = 0, K_SMOOTH_COARSE, K_RESTRICT, K_PROLONG, K_SETUP, K_RESIDUAL, K_ADVECT,
-  K_TOTALS, K_FORCES, K_PHASE, K_OTHER, K_SMOOTH_TILED, K_COUNT
+  K_TOTALS, K_FORCES, K_PHASE, K_OTHER, K_SMOOTH_TILED, K_RESID_FAST, K_COUNT
 };
 
 // One coarse level of the FP32 multigrid for the coupled Newton correction
@@ -140,6 +140,7 @@ struct AdjScratch {
 struct Prof {
   bool on = false;
   long long launches[K_COUNT] = {};
+  long long work[2] = {};        // residual passes that did work: FP32, pair
   std::vector<cudaEvent_t> ev;   // event pairs (start, end)
   std::vector<int> kind;         // kind of each recorded pair
   size_t used = 0;
