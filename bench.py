@@ -46,12 +46,11 @@ NOMINAL_HBM_GBS = 7900.0   # GB300 HBM3e nominal bandwidth (context beside the m
 # withdrawn (None) as soon as those sources differ from the captured ones.
 NCU_TRAFFIC = {
     ("smooth_tiled", "f32", 3): {
-        "bytes_per_cell": (234.61e6 + 40.95e6) / 192 ** 3,
-        "sources": ["sfx_tiled.cuh", "sfx_f32_dev.cuh", "sfx_f32.cu", "sfx_df.cuh",
-                    "sfx_common.cuh"],
-        "sha256_16": "2bb5896041f3ea92",
-        "capture": "profiles/corr2_tiled_hr3d192_f32.md (192^3, one launch), scaled by the "
-                   "cell count",
+        "bytes_per_cell": (238.20e6 + 42.57e6) / 192 ** 3,
+        "sources": ["sfx_tiled.cuh", "sfx_corr3.cuh"],
+        "sha256_16": "20e35e2630e1d952",
+        "capture": "profiles/corr2_tiled_hr3d192_f32.md (192^3 with the 256^3 z-chunk of 37 "
+                   "planes, one launch), scaled by the cell count",
     },
 }
 
