@@ -365,6 +365,12 @@ typedef enum {
                                4096, or 0 (default): chosen from the grid
                                and the SM count to fill the last wave of
                                blocks (37 at 256^3 on 152 SMs). */
+  SFX_TUNE_ADVECT_STAGED = 9, /* SFX_F32, 3D: 1 (default) = the BCG step of
+                               f and F from z-planes staged in shared
+                               memory (values rounded once, neighbours past
+                               a wall clamped in the staging); 0 = the
+                               tiles that gather from global memory.
+                               Bitwise equal. */
   SFX_TUNE_F32_FAST_RESID = 8, /* SFX_F32 Newton solver: at most this many
                                iterations per solve (0 .. 16, default 2)
                                evaluate the residuals in FP32 instead of

@@ -387,6 +387,10 @@ sfx_status sfx_set_tuning(sfx_ctx* c, int key, int value) {
     c->f32.tiled = value == 1;
     return SFX_OK;
   }
+  if (key == SFX_TUNE_ADVECT_STAGED && (value == 0 || value == 1)) {
+    c->f32.adv_staged = value == 1;
+    return SFX_OK;
+  }
   if (key == SFX_TUNE_F32_FAST_RESID && value >= 0 && value <= 16) {
     c->f32.fast_resid = value;
     return SFX_OK;

@@ -35,6 +35,7 @@
 #include "sfx_f32_dev.cuh"
 #include "sfx_internal.h"
 #include "sfx_tiled.cuh"
+#include "sfx_advect3.cuh"
 
 namespace sfx {
 namespace {
@@ -779,15 +780,6 @@ __device__ __forceinline__ float4 face_flux2(const Adv32& A, const float2* __res
   return make_float4(a.x, a.y, b.x, b.y);
 }
 
-__device__ __forceinline__ void acc_face(float2& S1, float2& S2, float4 q, bool plus) {
-  if (plus) {
-    S1 = df_add2(S1, make_float2(q.x, q.y));
-    S2 = df_add2(S2, make_float2(q.z, q.w));
-  } else {
-    S1 = df_sub2(S1, make_float2(q.x, q.y));
-    S2 = df_sub2(S2, make_float2(q.z, q.w));
-  }
-}
 
 __global__ void __launch_bounds__(kAdvX* kAdvY)
     k_advect2t_32(Adv32 A, const float2* __restrict__ f, const float2* __restrict__ F,
@@ -1557,8 +1549,16 @@ sfx_status step_f32(sfx_ctx* c, const sfx_params* pr, const double* phi_in, cons
     const dim3 ag((unsigned)((L.nx + kAdvX - 2) / (kAdvX - 1)),
                   (unsigned)((L.ny + kAdvY - 2) / (kAdvY - 1)),
                   L.geom == SFX_CART3D ? (unsigned)((L.nz + kAdvZ - 1) / kAdvZ) : 1u);
-    SFX_KERNEL(c, K_ADVECT, k_advect2t_32, ag, kAdvX * kAdvY, s, A, f, F, (float)pr->bc_f,
-               (float)pr->bc_F, fs, Fs);
+    if (L.geom == SFX_CART3D && c->f32.adv_staged) {
+      const dim3 a3((unsigned)((L.nx + kA3X - 2) / (kA3X - 1)),
+                    (unsigned)((L.ny + kA3Y - 2) / (kA3Y - 1)),
+                    (unsigned)((L.nz + kA3Z - 1) / kA3Z));
+      SFX_KERNEL(c, K_ADVECT, k_advect3s_32, a3, kA3X * kA3Y, s, A, f, F, (float)pr->bc_f,
+                 (float)pr->bc_F, fs, Fs);
+    } else {
+      SFX_KERNEL(c, K_ADVECT, k_advect2t_32, ag, kAdvX * kAdvY, s, A, f, F, (float)pr->bc_f,
+                 (float)pr->bc_F, fs, Fs);
+    }
     SFX_LAUNCH_CHECK();
   } else {
     SFX_CUDA(cudaMemcpyAsync(fs, f, n * sizeof(float2), cudaMemcpyDeviceToDevice, s));

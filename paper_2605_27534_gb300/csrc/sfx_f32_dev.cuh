@@ -376,6 +376,36 @@ __device__ __forceinline__ ix fidx32(const Level& L, int d, int i, int j, int k)
   return ((ix)k * fy + (ix)j) * fx + (ix)i;
 }
 
+// The BCG face value of both fields (Sec. 3.1) from the upwind cell's
+// values a: a + cfl x (MC-limited slope along d) minus the transverse
+// upwind differences times the mean transverse velocity.  nb(t, s) gives
+// both fields' values of the upwind cell's neighbour at offset s along t
+// (the cell itself past a wall), vb(t) the mean velocity of its two faces
+// along t.  Every rounding is spelled out, so that each kernel that
+// fetches the operands its own way (global memory, shared-memory tiles)
+// computes the same bits.
+template <class Nb, class Vb>
+__device__ __forceinline__ void bcg_face2(float2 a, float u, float dt, float invh, int d, int nd,
+                                          Nb nb, Vb vb, float& v1, float& v2) {
+  const float cfl = __fmul_rn(0.5f, __fmaf_rn(-__fmul_rn(u, dt), invh, u > 0.0f ? 1.0f : -1.0f));
+  const float2 m = nb(d, -1), pl = nb(d, +1);
+  v1 = __fmaf_rn(cfl, mc32(m.x, a.x, pl.x), a.x);
+  v2 = __fmaf_rn(cfl, mc32(m.y, a.y, pl.y), a.y);
+  const float hdt = __fmul_rn(0.5f, dt);
+#pragma unroll
+  for (int t = 0; t < 3; ++t) {
+    if (t >= nd || t == d) continue;
+    const float vbar = vb(t);
+    const bool up = vbar > 0.0f;
+    const float2 n = nb(t, up ? -1 : +1);
+    const float d1 = up ? __fsub_rn(a.x, n.x) : __fsub_rn(n.x, a.x);
+    const float d2 = up ? __fsub_rn(a.y, n.y) : __fsub_rn(n.y, a.y);
+    const float s = __fmul_rn(hdt, vbar);
+    v1 = __fmaf_rn(-__fmul_rn(s, d1), invh, v1);
+    v2 = __fmaf_rn(-__fmul_rn(s, d2), invh, v2);
+  }
+}
+
 __device__ __forceinline__ void face32v2(const Adv32& A, const float2* __restrict__ x1,
                                          const float2* __restrict__ x2, float bc1, float bc2,
                                          int d, const int* f, float u, float& v1, float& v2) {
@@ -390,22 +420,21 @@ __device__ __forceinline__ void face32v2(const Adv32& A, const float2* __restric
     return;
   }
   const ix U = cidx32(L, uc[0], uc[1], uc[2]);
-  const float a1 = df_val(x1[U]), a2 = df_val(x2[U]);
-  const float cfl = 0.5f * ((u > 0.0f ? 1.0f : -1.0f) - u * A.dt * A.invh);
-  v1 = a1 + cfl * mc32(vnb32(L, x1, uc, U, d, -1), a1, vnb32(L, x1, uc, U, d, +1));
-  v2 = a2 + cfl * mc32(vnb32(L, x2, uc, U, d, -1), a2, vnb32(L, x2, uc, U, d, +1));
-  for (int t = 0; t < L.ndim(); ++t) {
-    if (t == d) continue;
-    int ap[3] = {uc[0], uc[1], uc[2]};
-    ap[t] += 1;
-    const float vbar = 0.5f * (A.u[t][fidx32(L, t, uc[0], uc[1], uc[2])] +
-                               A.u[t][fidx32(L, t, ap[0], ap[1], ap[2])]);
-    const bool up = vbar > 0.0f;
-    const float d1 = up ? a1 - vnb32(L, x1, uc, U, t, -1) : vnb32(L, x1, uc, U, t, +1) - a1;
-    const float d2 = up ? a2 - vnb32(L, x2, uc, U, t, -1) : vnb32(L, x2, uc, U, t, +1) - a2;
-    v1 -= 0.5f * A.dt * vbar * d1 * A.invh;
-    v2 -= 0.5f * A.dt * vbar * d2 * A.invh;
-  }
+  const float2 a = make_float2(df_val(x1[U]), df_val(x2[U]));
+  const int c0 = uc[0], c1 = uc[1], c2 = uc[2];
+  auto nb = [&](int t, int sgn) {
+    const int pos = (t == 0 ? c0 : (t == 1 ? c1 : c2)) + sgn;
+    if (pos < 0 || pos >= L.extent(t)) return a;
+    const ix stride = t == 0 ? 1u : (t == 1 ? (ix)L.nx : (ix)L.nx * (ix)L.ny);
+    const ix V = sgn > 0 ? U + stride : U - stride;
+    return make_float2(df_val(x1[V]), df_val(x2[V]));
+  };
+  auto vb = [&](int t) {
+    return __fmul_rn(0.5f, __fadd_rn(A.u[t][fidx32(L, t, c0, c1, c2)],
+                                     A.u[t][fidx32(L, t, c0 + (t == 0), c1 + (t == 1),
+                                                   c2 + (t == 2))]));
+  };
+  bcg_face2(a, u, A.dt, A.invh, d, L.ndim(), nb, vb, v1, v2);
 }
 
 // Both residuals (pairs) of App. C at cell c of the current state, the
@@ -692,6 +721,18 @@ __device__ __forceinline__ float2 advect_cell(const Adv32& A, const float2* __re
   float2 inc = df_mul_f(df_mul_f(S, -A.dt), A.invh);
   if (L.geom == SFX_AXISYM) inc = df_div_f(inc, wz_face(L.geom, idx[0]));
   return df_add2(x[c], inc);
+}
+
+// A face's weighted pair fluxes (both fields) added to (plus face) or
+// subtracted from (minus face) a cell's sums.
+__device__ __forceinline__ void acc_face(float2& S1, float2& S2, float4 q, bool plus) {
+  if (plus) {
+    S1 = df_add2(S1, make_float2(q.x, q.y));
+    S2 = df_add2(S2, make_float2(q.z, q.w));
+  } else {
+    S1 = df_sub2(S1, make_float2(q.x, q.y));
+    S2 = df_sub2(S2, make_float2(q.z, q.w));
+  }
 }
 
 // advect_cell for two fields sharing the face geometry (bitwise the same

@@ -79,6 +79,7 @@ struct F32Scratch {
                                     // a tiled sweep that gave up waiting, residual
                                     // kind (0 FP32, else pair), FP32 passes so far
   int fast_resid = 2;               // FP32 residual passes at most per Newton solve
+  bool adv_staged = true;           // 3D advection from shared-memory planes
   bool predict = true;              // start Newton from x* + last increment
   bool redist32 = false;            // redistance in FP32 (else FP64)
   int sweep_planes = 2;             // 3D correction sweep: planes per thread (1 or 2)

@@ -872,3 +872,30 @@ def test_fp32_residual_iterations_reach_the_same_fixed_point(sfx, fast):
     for a, b in zip(outs[0], outs[1]):
         assert np.abs(a - b).max() / np.abs(a).max() < 1e-8
     assert all(m <= k + 1 for k, m in zip(its[0], its[1])), its
+
+
+@pytest.mark.parametrize("shape", [(24, 24, 24), (19, 17, 70), (5, 9, 33)])
+def test_staged_advection_bitwise(sfx, shape):
+    """The 3D BCG step from shared-memory planes (values rounded once,
+    neighbours past a wall clamped in the staging) gives the bits of the
+    tiles that gather from global memory: ragged x tiles (70 = 2 x 31 + 8,
+    33 = 31 + 2), rows and planes that do not fill a tile or z-chunk, and
+    inflow values on the walls."""
+    import torch
+    nz, ny, nx = shape
+    g, Cf = _sphere(nx, ny, nz, 0.3)
+    ux, uy, uz = W.uniform_faces(g, (0.3, -0.2, 0.25))
+    p = W.Params(ka=2.0, kd=0.5, Df=2e-3, DF=5e-3, eps=0.75 * g.h, bc_f=0.1, bc_F=1.0)
+    _, phi, delta = oracle.phase_field_build(g, Cf, 24, W.redist_dtau(g), p.eps)
+    outs = []
+    for staged in (0, 1):
+        ctx = _ctx(sfx, g, 1)
+        ctx.sfx_set_tuning(sfx._lib.SFX_TUNE_ADVECT_STAGED, staged)
+        f, F = _pairs(ctx, 0.3 * delta), _pairs(ctx, 1.0 - Cf)
+        u = [dev(v, torch.float32) for v in (ux, uy, uz)]
+        for _ in range(2):
+            assert ctx.sfx_surfactant_step(p, dev(phi), f, F, 0.2 * g.h, *u,
+                                           opts=sfx.default_opts(tol=1e-10)).converged
+        torch.cuda.synchronize()
+        outs.append((f.cpu().numpy().copy(), F.cpu().numpy().copy()))
+    assert np.array_equal(outs[0][0], outs[1][0]) and np.array_equal(outs[0][1], outs[1][1])
