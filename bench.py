@@ -178,7 +178,7 @@ def algorithmic_bytes(kind, grid, wbytes, sweeps=3, tiled=False):
         # arrays (4 B each), write both corrections (8 B); the staged rings
         # (halo) are re-reads, not counted
         return (4.0 + 16.0 + 4.0 * d + 8.0) * N
-    if kind in ("residual", "residual_fp32") and wbytes == 4:
+    if kind in ("residual", "residual_fp32", "residual_incr") and wbytes == 4:
         # k_resid2_32: f, F, f*, F* (pairs), phi, 2 d float faces; writes the
         # residuals and exchange Jacobian (float4) and the red half of both
         # corrections
@@ -207,7 +207,7 @@ def method_bytes(kind, grid, s):
         return (5.0 if s == 4 else 2.5) * s * N
     if kind == "smooth_tiled":
         return 10.0 * s * N         # a whole sweep of both fields
-    if kind in ("residual", "residual_fp32"):
+    if kind in ("residual", "residual_fp32", "residual_incr"):
         return (10.0 if s == 4 else 5.0) * s * N
     if kind == "advect":
         return (4.0 + d) * s * N
@@ -645,8 +645,9 @@ def run_gpu(a, case, rank, world, local_rank):
                              a.tiled_zchunk or "auto")
                              if (a.tiled and prec == sfx.SFX_F32) else "one launch per colour",
                    "residuals": ("FP32 for up to %d Newton iterations per step (while the "
-                                 "relative residual is above 1e-3), then pair arithmetic"
-                                 % a.fast_resid) if (a.fast_resid and prec == sfx.SFX_F32)
+                                 "relative residual is above 1e-3), then one pair pass, then "
+                                 "incremental FP32 from it" % a.fast_resid)
+                                if (a.fast_resid and prec == sfx.SFX_F32)
                                 else "pair arithmetic",
                    "l2": "inputs larger than L2 (state + coefficients %.2f GB)" % (
                        g.ncell * 8 * 20 / 1e9),

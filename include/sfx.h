@@ -365,6 +365,17 @@ typedef enum {
                                4096, or 0 (default): chosen from the grid
                                and the SM count to fill the last wave of
                                blocks (37 at 256^3 on 152 SMs). */
+  SFX_TUNE_F32_INCR_RESID = 10, /* SFX_F32 Newton solver on the tiled path:
+                               1 (default) = after a pair residual pass
+                               whose relative residuals are below 1e5 tol,
+                               the residuals of the next iterates are formed
+                               in FP32 from the previous ones and the
+                               correction just added (linear terms and a
+                               product of the correction, rounded to ~1e-6
+                               of the pair residual, so the chain stays
+                               below a tenth of the tolerance); 0 = a pair
+                               pass at every iteration after the FP32
+                               ones. */
   SFX_TUNE_ADVECT_STAGED = 9, /* SFX_F32, 3D: 1 (default) = the BCG step of
                                f and F from z-planes staged in shared
                                memory (values rounded once, neighbours past
@@ -542,6 +553,7 @@ typedef enum {
   SFX_K_OTHER,
   SFX_K_SMOOTH_TILED,     /* tiled red-black sweep (both colours), fine level */
   SFX_K_RESID_FAST,       /* FP32 residual passes of the FP32 Newton solve */
+  SFX_K_RESID_INCR,       /* incremental FP32 residual passes of that solve */
   SFX_K_COUNT
 } sfx_kernel_kind;
 
@@ -556,8 +568,9 @@ sfx_status sfx_profile_read(sfx_ctx* ctx, int kind, long long* launches,
                             double* total_ms, long long* timed);
 /* Of the launches of `kind` since the last sfx_profile(ctx, 1), those that
    did work, where the library can tell: the residual passes of the FP32
-   Newton solve (SFX_K_RESIDUAL, SFX_K_RESID_FAST), of which each iteration
-   launches both kinds and one returns at once, counted from the residual
+   Newton solve (SFX_K_RESIDUAL, SFX_K_RESID_FAST, SFX_K_RESID_INCR), of
+   which each iteration launches every kind and all but one return at once,
+   counted from the residual
    kind recorded with the iteration's norms (iterations whose norms the
    solve read); -1 for the other kinds.  SFX_ERR_ARG on a bad kind. */
 sfx_status sfx_profile_work(sfx_ctx* ctx, int kind, long long* working);

@@ -387,6 +387,10 @@ sfx_status sfx_set_tuning(sfx_ctx* c, int key, int value) {
     c->f32.tiled = value == 1;
     return SFX_OK;
   }
+  if (key == SFX_TUNE_F32_INCR_RESID && (value == 0 || value == 1)) {
+    c->f32.incr_resid = value == 1;
+    return SFX_OK;
+  }
   if (key == SFX_TUNE_ADVECT_STAGED && (value == 0 || value == 1)) {
     c->f32.adv_staged = value == 1;
     return SFX_OK;
@@ -425,7 +429,7 @@ sfx_status sfx_profile(sfx_ctx* c, int on) {
   if (!c) return SFX_ERR_ARG;
   if (on) {
     for (int k = 0; k < K_COUNT; ++k) c->prof.launches[k] = 0;
-    c->prof.work[0] = c->prof.work[1] = 0;
+    c->prof.work[0] = c->prof.work[1] = c->prof.work[2] = 0;
     c->prof.used = 0;
   }
   c->prof.on = on != 0;
@@ -434,7 +438,9 @@ sfx_status sfx_profile(sfx_ctx* c, int on) {
 
 sfx_status sfx_profile_work(sfx_ctx* c, int kind, long long* working) {
   if (!c || kind < 0 || kind >= K_COUNT || !working) return SFX_ERR_ARG;
-  *working = kind == K_RESID_FAST ? c->prof.work[0] : (kind == K_RESIDUAL ? c->prof.work[1] : -1);
+  *working = kind == K_RESID_FAST ? c->prof.work[0]
+             : kind == K_RESIDUAL ? c->prof.work[1]
+             : kind == K_RESID_INCR ? c->prof.work[2] : -1;
   return SFX_OK;
 }
 

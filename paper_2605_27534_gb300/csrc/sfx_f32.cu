@@ -304,11 +304,11 @@ __global__ void k_corr32(Corr32 p, const float* __restrict__ Bx, const float* __
 // Evaluate both residuals (pairs), the 2x2 exchange Jacobian and the
 // norms at every cell of the current state.
 // `done`: the solve converged at an earlier iteration; `mode` (may be
-// null): the residual kind chosen on the device for this iteration (zero:
-// the FP32 pass, nonzero: the pair pass); a launch whose kind `want` is not
-// chosen returns at once.
+// null): the residual kind chosen on the device for this iteration (0 the
+// FP32 pass, 1 the pair pass, 2 the incremental FP32 pass); a launch whose
+// kind `want` is not chosen returns at once.
 __device__ __forceinline__ bool resid_skip(const int* done, const int* mode, int want) {
-  return (done && *done) || (mode && (*mode != 0) != (want != 0));
+  return (done && *done) || (mode && *mode != want);
 }
 
 // Warp maxima of the four norms, then one atomic per block and norm.
@@ -370,6 +370,33 @@ k_resid32_fast(Nw32 p, const float* __restrict__ phi, const float2* __restrict__
     const int j = (int)(r % (ix)L.ny), k = (int)(r / (ix)L.ny);
     if (i < L.nx)
       resid32_cell<G>(p, i, j, k, r * (ix)L.nx + (ix)i, phi, B2, fin, Fin, fst, Fst, rc, m, e2);
+  }
+  if (norms) resid_norms(m, norms);
+}
+
+// The incremental FP32 residual pass (resid32_incr_cell): the residuals of
+// the current state from the previous iteration's (rc) and the correction
+// it added (E); same launch shape and other outputs.
+template <int G>
+__global__ void __launch_bounds__(256, 4)
+k_resid32_incr(Nw32 p, const float* __restrict__ phi, const float2* __restrict__ B2x,
+               const float2* __restrict__ B2y, const float2* __restrict__ B2z,
+               const float2* __restrict__ fin, const float2* __restrict__ Fin,
+               const float2* __restrict__ fst, const float2* __restrict__ Fst,
+               const float2* __restrict__ E, float4* __restrict__ rc, unsigned int* norms,
+               float2* __restrict__ e2, const int* __restrict__ done,
+               const int* __restrict__ mode) {
+  if (resid_skip(done, mode, 2)) return;
+  const Level& L = p.L;
+  float m[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+  const float2* B2[3] = {B2x, B2y, B2z};
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const ix rows = (ix)L.ny * (ix)L.nz;
+  for (ix r = blockIdx.y; r < rows; r += gridDim.y) {
+    const int j = (int)(r % (ix)L.ny), k = (int)(r / (ix)L.ny);
+    if (i < L.nx)
+      resid32_incr_cell<G>(p, i, j, k, r * (ix)L.nx + (ix)i, phi, B2, fin, Fin, fst, Fst, E, rc,
+                           m, e2);
   }
   if (norms) resid_norms(m, norms);
 }
@@ -441,12 +468,14 @@ k_corr2_32(Nw32 p, const __half2* __restrict__ Hx, const __half2* __restrict__ H
 struct NewtonKernels {
   decltype(&k_resid2_32<kGeomRuntime>) resid;
   decltype(&k_resid32_fast<SFX_CART3D>) fast;
+  decltype(&k_resid32_incr<SFX_CART3D>) incr;
   decltype(&k_corr2_32<SFX_CART3D, 1>) corr;
   int kp;   // planes per thread of the correction sweep
 };
 template <int G>
 NewtonKernels newton_kernels_of() {
-  return NewtonKernels{&k_resid2_32<G>, &k_resid32_fast<G>, &k_corr2_32<G, 1>, 1};
+  return NewtonKernels{&k_resid2_32<G>, &k_resid32_fast<G>, &k_resid32_incr<G>,
+                       &k_corr2_32<G, 1>, 1};
 }
 NewtonKernels newton_kernels(int geom, int kp) {
   switch (geom) {
@@ -454,6 +483,7 @@ NewtonKernels newton_kernels(int geom, int kp) {
     case SFX_PLANAR2D: return newton_kernels_of<SFX_PLANAR2D>();
     default:
       return NewtonKernels{&k_resid2_32<kGeomRuntime>, &k_resid32_fast<SFX_CART3D>,
+                           &k_resid32_incr<SFX_CART3D>,
                            kp == 2 ? &k_corr2_32<SFX_CART3D, 2> : &k_corr2_32<SFX_CART3D, 1>,
                            kp == 2 ? 2 : 1};
   }
@@ -1242,15 +1272,22 @@ sfx_status solve_dc32(sfx_ctx* c, const Nl32& pf, const Nl32& pF, const float* p
 // and flag[1] records the iteration.
 // A tiled sweep of the previous iteration that gave up waiting for its
 // staged planes (flag[3]) marks the norms with kTimeoutBits instead.
-// Residual kinds: flag[4] = 0 while the FP32 pass evaluates the residuals,
-// nonzero once the pair pass does; only a pair residual passes the test.  The
-// solve switches to the pair pass after `fast_max` FP32 iterations
+// Residual kinds (flag[4]): 0 while the FP32 pass evaluates the residuals,
+// 1 once the pair pass does, 2 when the incremental pass follows a pair
+// pass (incr_ok: the solve keeps the previous correction).  The solve
+// switches from FP32 to the pair pass after `fast_max` FP32 iterations
 // (counted in flag[5]) or once both relative residuals are below
-// kFastSwitch; nrm[4] records the kind each iteration's norms came from.
+// kFastSwitch; from the pair to the incremental pass once both relative
+// pair residuals are below kIncrFactor x tol: an incremental chain rounds
+// to about 16 float epsilons (16 x 6e-8) of the pair residual it starts
+// from, which then stays below a tenth of the tolerance.  Only a pair or an
+// incremental residual passes the test; nrm[4] records the kind each
+// iteration's norms came from.
 constexpr unsigned int kTimeoutBits = 0xffffffffu;
 constexpr float kFastSwitch = 1e-3f;
+constexpr float kIncrFactor = 1e5f;
 __global__ void k_flag32(unsigned int* __restrict__ nrm, float tol, int it, int fast_max,
-                         int* __restrict__ flag) {
+                         int incr_ok, int* __restrict__ flag) {
   if (threadIdx.x != 0 || flag[0]) return;
   if (flag[3]) {
     nrm[1] = nrm[3] = kTimeoutBits;
@@ -1258,16 +1295,23 @@ __global__ void k_flag32(unsigned int* __restrict__ nrm, float tol, int it, int 
   }
   const float rf = __uint_as_float(nrm[0]), bf = __uint_as_float(nrm[1]);
   const float rF = __uint_as_float(nrm[2]), bF = __uint_as_float(nrm[3]);
-  const bool pair = flag[4] != 0;
-  nrm[4] = pair ? 1u : 0u;
-  if (pair) {
+  const int kind = flag[4];
+  nrm[4] = (unsigned int)kind;
+  if (kind >= 1) {
     if (rf <= tol * bf && rF <= tol * bF) {
       flag[0] = 1;
       flag[1] = it;
+    } else if (kind == 1 && incr_ok && rf <= kIncrFactor * tol * bf &&
+               rF <= kIncrFactor * tol * bF) {
+      flag[4] = 2;
     }
   } else if (++flag[5] >= fast_max || (rf <= kFastSwitch * bf && rF <= kFastSwitch * bF)) {
     flag[4] = 1;
   }
+}
+
+__global__ void k_set32(int* __restrict__ p, int v) {
+  if (threadIdx.x == 0) *p = v;
 }
 
 // A predicted start whose first relative residual exceeds `rho` (or is not
@@ -1372,10 +1416,6 @@ sfx_status solve_newton32(sfx_ctx* c, const Nw32& p, const float* phi, float* co
   const RowGrid rg = row_grid(L, c->sm_count);
   const __half2* Hz = L.ndim() == 3 ? c->f32.H2[2] : nullptr;
   const float2* B2[3] = {c->f32.B2[0], c->f32.B2[1], L.ndim() == 3 ? c->f32.B2[2] : nullptr};
-  // flag[4] = 1: pair residuals from the first iteration (no FP32 passes)
-  const int fast_max = c->f32.fast_resid;
-  SFX_CUDA(cudaMemsetAsync(flag, 0, 8 * sizeof(int), s));
-  if (fast_max <= 0) SFX_CUDA(cudaMemsetAsync(flag + 4, 1, sizeof(int), s));
   // sweeps 1 .. S-1 (black, then red) as tiled launches where the grid
   // allows, the last black colour as a colour launch that adds the
   // corrections to the state
@@ -1384,6 +1424,17 @@ sfx_status solve_newton32(sfx_ctx* c, const Nw32& p, const float* phi, float* co
     const sfx_status ts = tiled_sweep_prepare(c);
     if (ts != SFX_OK) return ts;
   }
+  // the incremental residual needs the previous correction kept: on the
+  // tiled path the two correction buffers alternate, the residual pass of
+  // an iteration writing the first red half-sweep into the buffer that the
+  // previous iteration's correction is not in
+  const int incr_ok = tiled && c->f32.incr_resid ? 1 : 0;
+  float2* ebuf[2] = {c->f32.e2, tiled ? c->f32.e2b : c->f32.e2};
+  int efin = 1;   // buffer of the last correction added to the state
+  // flag[4] = 1: pair residuals from the first iteration (no FP32 passes)
+  const int fast_max = c->f32.fast_resid;
+  SFX_CUDA(cudaMemsetAsync(flag, 0, 8 * sizeof(int), s));
+  if (fast_max <= 0) SFX_KERNEL(c, K_OTHER, k_set32, 1, 32, s, flag + 4, 1);
   // Each iteration: the residual pass (which also does the first red
   // half-sweep of the correction, from zero), a device-side convergence
   // test, then the rest of the red-black sweeps, the last black one adding
@@ -1403,10 +1454,15 @@ sfx_status solve_newton32(sfx_ctx* c, const Nw32& p, const float* phi, float* co
     const float2* fsrc = star ? fs : fc;
     const float2* Fsrc = star ? Fs : Fc;
     // the FP32 or the pair residual pass, as chosen on the device
+    const int etgt = tiled ? 1 - efin : 0;
+    float2* e2t = ebuf[etgt];
     SFX_KERNEL(c, K_RESID_FAST, nk.fast, rg.grid, rg.block, s, p, phi, B2[0], B2[1], B2[2], fsrc,
-               Fsrc, fs, Fs, c->f32.rc, nbuf, c->f32.e2, flag, flag + 4);
+               Fsrc, fs, Fs, c->f32.rc, nbuf, e2t, flag, flag + 4);
     SFX_KERNEL(c, K_RESIDUAL, nk.resid, rg.grid, rg.block, s, p, phi, B2[0], B2[1], B2[2], fsrc,
-               Fsrc, fs, Fs, c->f32.rc, nbuf, c->f32.e2, flag, flag + 4);
+               Fsrc, fs, Fs, c->f32.rc, nbuf, e2t, flag, flag + 4);
+    if (incr_ok && it > 1)
+      SFX_KERNEL(c, K_RESID_INCR, nk.incr, rg.grid, rg.block, s, p, phi, B2[0], B2[1], B2[2],
+                 fsrc, Fsrc, fs, Fs, ebuf[efin], c->f32.rc, nbuf, e2t, flag, flag + 4);
     if (it == 1 && predicted) {
       // keep the predicted start only if its residual is already small;
       // otherwise restart from x* (both launches return at once when kept)
@@ -1415,11 +1471,11 @@ sfx_status solve_newton32(sfx_ctx* c, const Nw32& p, const float* phi, float* co
       SFX_KERNEL(c, K_OTHER, k_pred_check32, 1, 32, s, nbuf, rho, ok);
       SFX_KERNEL(c, K_SETUP, k_restore32, nb, 256, s, n, ok, fs, Fs, fc, Fc);
       SFX_KERNEL(c, K_RESID_FAST, nk.fast, rg.grid, rg.block, s, p, phi, B2[0], B2[1], B2[2],
-                 fc, Fc, fs, Fs, c->f32.rc, nbuf, c->f32.e2, ok, flag + 4);
+                 fc, Fc, fs, Fs, c->f32.rc, nbuf, e2t, ok, flag + 4);
       SFX_KERNEL(c, K_RESIDUAL, nk.resid, rg.grid, rg.block, s, p, phi, B2[0], B2[1], B2[2],
-                 fc, Fc, fs, Fs, c->f32.rc, nbuf, c->f32.e2, ok, flag + 4);
+                 fc, Fc, fs, Fs, c->f32.rc, nbuf, e2t, ok, flag + 4);
     }
-    SFX_KERNEL(c, K_OTHER, k_flag32, 1, 32, s, nbuf, tolf, it, fast_max, flag);
+    SFX_KERNEL(c, K_OTHER, k_flag32, 1, 32, s, nbuf, tolf, it, fast_max, incr_ok, flag);
     SFX_CUDA(cudaMemcpyAsync(hn + 8 * (it & 1), nbuf, 8 * sizeof(unsigned int),
                              cudaMemcpyDeviceToHost, s));
     SFX_CUDA(cudaEventRecord(c->f32.ev[it & 1], s));
@@ -1443,13 +1499,14 @@ sfx_status solve_newton32(sfx_ctx* c, const Nw32& p, const float* phi, float* co
                      fsrc, Fsrc, flag);
         }
     } else if (tiled) {
-      int in = 0;   // the residual pass wrote the first red half-sweep into e2
+      int in = etgt;   // the residual pass wrote the first red half-sweep there
       for (int q = 0; q + 1 < sweeps; ++q, in ^= 1) {
         const sfx_status ts = tiled_sweep(c, p, in, flag, s);
         if (ts != SFX_OK) return ts;
       }
       SFX_KERNEL(c, K_SMOOTH_FINE, nk.corr, grd, blk, s, p, c->f32.H2[0], c->f32.H2[1], Hz,
-                 c->f32.rc, in == 0 ? c->f32.e2 : c->f32.e2b, 1, 0, fc, Fc, fsrc, Fsrc, flag);
+                 c->f32.rc, ebuf[in], 1, 0, fc, Fc, fsrc, Fsrc, flag);
+      efin = in;
     } else {
       for (int q = 0; q < sweeps; ++q)
         for (int color = (q == 0 ? 1 : 0); color < 2; ++color) {
@@ -1465,11 +1522,11 @@ sfx_status solve_newton32(sfx_ctx* c, const Nw32& p, const float* phi, float* co
       SFX_CUDA(cudaEventSynchronize(c->f32.ev[prev & 1]));
       const unsigned int* hb = hn + 8 * (prev & 1);
       if (hb[1] == kTimeoutBits) return SFX_ERR_TIMEOUT;
-      ++c->prof.work[hb[4] == 1u ? 1 : 0];   // the residual kind of iteration prev
+      ++c->prof.work[hb[4] <= 2u ? hb[4] : 0];   // the residual kind of iteration prev
       memcpy(nrm, hb, 4 * sizeof(float));
       for (int q = 0; q < 4; ++q)
         if (!std::isfinite(nrm[q])) return SFX_ERR_NONFINITE;
-      if (hb[4] == 1u && nrm[0] <= tolf * nrm[1] && nrm[2] <= tolf * nrm[3]) {   // as k_flag32
+      if (hb[4] >= 1u && nrm[0] <= tolf * nrm[1] && nrm[2] <= tolf * nrm[3]) {   // as k_flag32
         *conv = true;
         done_it = prev;
         break;
@@ -1487,7 +1544,7 @@ sfx_status solve_newton32(sfx_ctx* c, const Nw32& p, const float* phi, float* co
     const int last = std::min(it, o->max_cycles);
     const unsigned int* hb = hn + 8 * (last & 1);
     if (hb[1] == kTimeoutBits) return SFX_ERR_TIMEOUT;
-    ++c->prof.work[hb[4] == 1u ? 1 : 0];   // the residual kind of the last iteration
+    ++c->prof.work[hb[4] <= 2u ? hb[4] : 0];   // the residual kind of the last iteration
     if (tiled) {
       int err = 0;
       SFX_CUDA(cudaMemcpy(&err, flag + 3, sizeof(int), cudaMemcpyDeviceToHost));
@@ -1496,7 +1553,7 @@ sfx_status solve_newton32(sfx_ctx* c, const Nw32& p, const float* phi, float* co
     memcpy(nrm, hb, 4 * sizeof(float));
     for (int q = 0; q < 4; ++q)
       if (!std::isfinite(nrm[q])) return SFX_ERR_NONFINITE;
-    if (hb[4] == 1u && nrm[0] <= tolf * nrm[1] && nrm[2] <= tolf * nrm[3]) *conv = true;
+    if (hb[4] >= 1u && nrm[0] <= tolf * nrm[1] && nrm[2] <= tolf * nrm[3]) *conv = true;
     done_it = last;
   }
   *iters = done_it;

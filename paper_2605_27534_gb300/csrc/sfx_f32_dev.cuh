@@ -566,6 +566,82 @@ __device__ __forceinline__ void resid32_cell(const Nw32& p, int i, int j, int k,
   if (!(fabsf(rf) <= 3.0e38f) || !(fabsf(rF) <= 3.0e38f)) m[0] = m[2] = __int_as_float(0x7f800000);
 }
 
+// The residuals of the state x + e from those of x (rc) and the correction
+// e just added to it (E, both colours, colour-packed), in FP32: the
+// App. C residual changes by
+//   r_f: -e_f/dt + flux_f(e_f) + dq,   r_F: -e_F/dt + flux_F(e_F) - dq,
+//   dq = c1 (e_F (f_inf - f) - F e_f - e_F e_f) - r_d e_f   (f, F before
+//      the update) = c1 (e_F (f_inf - f' + e_f) - F' e_f) - r_d e_f with
+//      f' = f + e_f, F' = F + e_F,
+// linear terms and a product of the correction, all of the size of the
+// old residual, so FP32 rounding stays ~1e-7 of it: after a pair residual
+// pass this keeps the pair pass's accuracy.  fin, Fin hold x + e.  The
+// other outputs are those of resid2_cell.
+template <int G>
+__device__ __forceinline__ void resid32_incr_cell(const Nw32& p, int i, int j, int k, ix c,
+                                                  const float* __restrict__ phi,
+                                                  const float2* const* B2,
+                                                  const float2* __restrict__ fin,
+                                                  const float2* __restrict__ Fin,
+                                                  const float2* __restrict__ fst,
+                                                  const float2* __restrict__ Fst,
+                                                  const float2* __restrict__ E,
+                                                  float4* __restrict__ rc, float* m,
+                                                  float2* __restrict__ e2) {
+  const Level& L = p.L;
+  bool has[6];
+  ix nbi[6];
+  gather6<G>(L, i, j, k, c, has, nbi);
+  // the correction of this cell and of its neighbours (the other colour)
+  const RBIdx rb = rb_index(L, i, j, k);
+  const int col = (i + j + k) & 1;
+  const ix own = (ix)col * rb.plane + rb.pos, oth = (ix)(1 - col) * rb.plane + rb.pos;
+  const ix sz = (ix)L.ny * rb.half;
+  nbi[0] = oth - 1 + (i & 1);
+  nbi[1] = oth + (i & 1);
+  nbi[2] = oth - rb.half;
+  nbi[3] = oth + rb.half;
+  nbi[4] = oth - sz;
+  nbi[5] = oth + sz;
+  float Bf[6], BF[6], ef[6], eF[6], df_, dF_;
+  faces6f2(L, B2[0], B2[1], B2[2], i, j, k, has, Bf, BF);
+#pragma unroll
+  for (int q = 0; q < 6; ++q) {
+    const float2 v = has[q] ? E[nbi[q]] : make_float2(0.0f, 0.0f);
+    ef[q] = v.x;
+    eF[q] = v.y;
+  }
+  const float2 ec = E[own];
+  const float4 r0 = rc[own];
+  const float flf = flux_lin<G>(L, p.invh, p.Dfh, p.literal, i, ec.x, ef, has, Bf, df_);
+  const float flF = flux_lin<G>(L, p.invh, p.DFh, p.literal, i, ec.y, eF, has, BF, dF_);
+  const PhiPair ph = unfold(phi[c]);
+  const float c1 = __fdividef(p.ka, ph.p + p.eta);
+  const float finf = __fmul_rn(__fmul_rn(__fmul_rn(p.ginf, ph.p), ph.q), p.inv_eps);
+  const float fc = fin[c].x, Fc = Fin[c].x;   // x + e
+  // dq from the updated values: c1 (e_F (f_inf - fc + e_f) - Fc e_f) - r_d e_f
+  const float dq = __fmaf_rn(
+      c1, __fmaf_rn(ec.y, __fadd_rn(__fsub_rn(finf, fc), ec.x), -__fmul_rn(Fc, ec.x)),
+      -__fmul_rn(p.kd, ec.x));
+  const float rf = __fadd_rn(__fadd_rn(__fmaf_rn(-ec.x, p.inv_dt, r0.x), flf), dq);
+  const float rF = __fsub_rn(__fadd_rn(__fmaf_rn(-ec.y, p.inv_dt, r0.y), flF), dq);
+  const float u = __fmul_rn(c1, Fc), v = __fmul_rn(c1, __fsub_rn(finf, fc));
+  rc[own] = make_float4(rf, rF, u, v);
+  if (col == 0) {
+    const Jac2 J = jac2(p, u, v);
+    const float a = __fadd_rn(J.ff, df_), e = __fadd_rn(J.FF, dF_);
+    const float inv = __fdividef(1.0f, __fmaf_rn(a, e, -__fmul_rn(J.fF, J.Ff)));
+    e2[own] = make_float2(__fmul_rn(__fmaf_rn(e, rf, __fmul_rn(J.fF, rF)), inv),
+                          __fmul_rn(__fmaf_rn(J.Ff, rf, __fmul_rn(a, rF)), inv));
+  }
+  const float fs = fst[c].x, Fs = Fst[c].x;
+  m[0] = fmaxf(m[0], fabsf(rf));
+  m[1] = fmaxf(m[1], fabsf(__fmaf_rn(fs, p.inv_dt, __fmul_rn(u, finf))));
+  m[2] = fmaxf(m[2], fabsf(rF));
+  m[3] = fmaxf(m[3], fabsf(__fmaf_rn(Fs, p.inv_dt, __fmul_rn(p.kd, fc))));
+  if (!(fabsf(rf) <= 3.0e38f) || !(fabsf(rF) <= 3.0e38f)) m[0] = m[2] = __int_as_float(0x7f800000);
+}
+
 // One cell of the coupled red-black Gauss-Seidel on the correction; with
 // fst != NULL (the last black colour of an iteration) the corrections of
 // this cell and of its red pair partner are added to the state.  The sweeps

@@ -34,7 +34,7 @@ struct LevelData {
 // on the launching stream) per context; values match sfx_kernel_kind.
 enum Kind {
   K_SMOOTH_FINE = 0, K_SMOOTH_COARSE, K_RESTRICT, K_PROLONG, K_SETUP, K_RESIDUAL, K_ADVECT,
-  K_TOTALS, K_FORCES, K_PHASE, K_OTHER, K_SMOOTH_TILED, K_RESID_FAST, K_COUNT
+  K_TOTALS, K_FORCES, K_PHASE, K_OTHER, K_SMOOTH_TILED, K_RESID_FAST, K_RESID_INCR, K_COUNT
 };
 
 // One coarse level of the FP32 multigrid for the coupled Newton correction
@@ -80,6 +80,7 @@ struct F32Scratch {
                                     // kind (0 FP32, else pair), FP32 passes so far
   int fast_resid = 2;               // FP32 residual passes at most per Newton solve
   bool adv_staged = true;           // 3D advection from shared-memory planes
+  bool incr_resid = true;           // incremental FP32 residuals after a pair pass (tiled path)
   bool predict = true;              // start Newton from x* + last increment
   bool redist32 = false;            // redistance in FP32 (else FP64)
   int sweep_planes = 2;             // 3D correction sweep: planes per thread (1 or 2)
@@ -141,7 +142,7 @@ struct AdjScratch {
 struct Prof {
   bool on = false;
   long long launches[K_COUNT] = {};
-  long long work[2] = {};        // residual passes that did work: FP32, pair
+  long long work[3] = {};        // residual passes that did work: FP32, pair, incremental
   std::vector<cudaEvent_t> ev;   // event pairs (start, end)
   std::vector<int> kind;         // kind of each recorded pair
   size_t used = 0;

@@ -825,6 +825,8 @@ def test_tiled_sweep_bitwise(sfx, shape, zchunk):
         ctx = _ctx(sfx, g, 1)
         ctx.sfx_set_tuning(sfx._lib.SFX_TUNE_TILED_SWEEP, tiled)
         ctx.sfx_set_tuning(sfx._lib.SFX_TUNE_TILED_ZCHUNK, zchunk)
+        # (the colour-launch path evaluates no incremental residuals)
+        ctx.sfx_set_tuning(sfx._lib.SFX_TUNE_F32_INCR_RESID, 0)
         f, F = _pairs(ctx, 0.3 * delta), _pairs(ctx, 1.0 - Cf)
         u = [dev(v, torch.float32) for v in (ux, uy, uz)]
         ctx.sfx_profile(True)
@@ -899,3 +901,40 @@ def test_staged_advection_bitwise(sfx, shape):
         torch.cuda.synchronize()
         outs.append((f.cpu().numpy().copy(), F.cpu().numpy().copy()))
     assert np.array_equal(outs[0][0], outs[1][0]) and np.array_equal(outs[0][1], outs[1][1])
+
+
+@pytest.mark.parametrize("shape", [(24, 24, 32), (20, 16, 64)])
+def test_incremental_residuals_reach_the_same_fixed_point(sfx, shape):
+    """After the pair residual pass, residuals formed in FP32 from the
+    previous residual and the correction just added (the tiled path) end on
+    the pair-only fixed point: the state matches the pair-only solve far
+    below the FP32 tolerance, each solve converges, no solve needs more than
+    one extra iteration, and the passes were counted as incremental."""
+    import torch
+    nz, ny, nx = shape
+    g, Cf = _sphere(nx, ny, nz, 0.3)
+    ux, uy, uz = W.uniform_faces(g, (0.3, -0.2, 0.25))
+    p = W.Params(ka=2.0, kd=0.5, Df=2e-3, DF=5e-3, eps=0.75 * g.h)
+    _, phi, delta = oracle.phase_field_build(g, Cf, 24, W.redist_dtau(g), p.eps)
+    outs, its, work = [], [], []
+    for incr in (0, 1):
+        ctx = _ctx(sfx, g, 1)
+        ctx.sfx_set_tuning(sfx._lib.SFX_TUNE_F32_INCR_RESID, incr)
+        f, F = _pairs(ctx, 0.3 * delta), _pairs(ctx, 1.0 - Cf)
+        u = [dev(v, torch.float32) for v in (ux, uy, uz)]
+        ctx.sfx_profile(True)
+        n = []
+        for _ in range(3):
+            st = ctx.sfx_surfactant_step(p, dev(phi), f, F, 0.2 * g.h, *u,
+                                         opts=sfx.default_opts(tol=1e-10))
+            assert st.converged and st.res_f <= 1e-10 and st.res_F <= 1e-10
+            n.append(st.picard)
+        torch.cuda.synchronize()
+        work.append(ctx.sfx_profile_work())
+        ctx.sfx_profile(False)
+        its.append(n)
+        outs.append((host(ctx.sfx_df_unpack(f)), host(ctx.sfx_df_unpack(F))))
+    for a, b in zip(outs[0], outs[1]):
+        assert np.abs(a - b).max() / np.abs(a).max() < 1e-8
+    assert all(m <= k + 1 for k, m in zip(its[0], its[1])), its
+    assert work[0]["residual_incr"] == 0 and work[1]["residual_incr"] > 0, work
