@@ -1041,6 +1041,7 @@ def run_gpu_batch(a, rank, world, local_rank, steps=None, summary=False):
     ncell = sum(nr * nz for nr, nz in sizes)
     B = sfx.Batch(inst)
     B.sfx_batch_reuse_phi(True)        # the interfaces are static
+    B.sfx_batch_set_tuning(sfx._lib.SFX_TUNE_F32_FAST_RESID, a.fast_resid)
     ones = torch.ones(ncell, dtype=torch.float64, device=dev)
     f = sfx.sfx_df_pack(torch.zeros_like(ones))
     F = sfx.sfx_df_pack(ones)
@@ -1083,11 +1084,11 @@ def run_gpu_batch(a, rank, world, local_rank, steps=None, summary=False):
             "peak_source": "%s (MEASURED_PEAKS.json hbm_gbs)" % peak_src}
     iters_mean = float(np.mean(np.array(rp) / steps))
     conv = all(st["converged"])
-    sched = {"block": block, "sweeps": sweeps, "iteration_budget": budget}
-    # init, advect, copy (phi static: no fold or drifts); per iteration
-    # residual, flags and the 2 sweeps - 1 colour sweeps; totals and final
-    # the iteration loop runs as long as an instance is active: residual,
-    # flags, 2 sweeps - 1 colour sweeps and the loop test per iteration
+    sched = {"block": block, "sweeps": sweeps, "iteration_budget": budget,
+             "fp32_residual_passes": a.fast_resid}
+    # init, advect, copy (phi static: no fold or drifts); then, as long as
+    # an instance is active, per iteration the residual, the flags, the
+    # 2 sweeps - 1 colour sweeps and the loop test; totals and final
     launches_per_step = 3 + max(st["iters"]) * (2 + 2 * sweeps) + 2
     if summary:
         return {"value": value, "unit": UNIT, "ms_per_step": ms / steps, "steps": steps,

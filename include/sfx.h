@@ -498,6 +498,12 @@ sfx_status sfx_batch_layout(const sfx_batch* b, size_t* n_cells, size_t* n_rface
    256, 3, 8.  An instance that has not converged within the budget keeps
    its last iterate and is reported by sfx_batch_stats. */
 sfx_status sfx_batch_set_schedule(sfx_batch* b, int block, int sweeps, int max_iters);
+/* Solver tuning of a batch, keys as sfx_set_tuning: only
+   SFX_TUNE_F32_FAST_RESID (0 .. 16, default 2) is taken; each instance
+   counts its own FP32 residual passes and switches to pair residuals on
+   its own (the same rule as the single-grid solve).  SFX_ERR_ARG for
+   another key or a value out of range. */
+sfx_status sfx_batch_set_tuning(sfx_batch* b, int key, int value);
 /* One step of every instance.  phi: phase field (double, packed cells);
    ur, uz: face velocities (float, packed radial / axial faces), both NULL
    for no advection; f, F: double-float pairs (packed cells), updated in

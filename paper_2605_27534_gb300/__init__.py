@@ -302,6 +302,10 @@ class Batch:
         _check(lib().sfx_batch_set_schedule(self._h, int(block), int(sweeps), int(max_iters)),
                "sfx_batch_set_schedule")
 
+    def sfx_batch_set_tuning(self, key, value):
+        """Batch solver tuning (SFX_TUNE_F32_FAST_RESID only)."""
+        _check(lib().sfx_batch_set_tuning(self._h, int(key), int(value)), "sfx_batch_set_tuning")
+
     def sfx_batch_reuse_phi(self, on=True):
         """Static phi: fold and drift faces outside the step graph."""
         _check(lib().sfx_batch_reuse_phi(self._h, 1 if on else 0), "sfx_batch_reuse_phi")

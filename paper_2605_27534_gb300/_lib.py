@@ -23,7 +23,8 @@ EXPORTS = [
     "sfx_mg_solve", "sfx_surfactant_step", "sfx_totals", "sfx_marangoni_force", "sfx_cfl_dt",
     "sfx_profile", "sfx_profile_read", "sfx_totals_noalloc", "sfx_df_pack", "sfx_df_unpack",
     "sfx_set_tuning", "sfx_batch_create", "sfx_batch_create_geom", "sfx_batch_destroy",
-    "sfx_batch_layout", "sfx_batch_set_schedule", "sfx_batch_step", "sfx_batch_stats",
+    "sfx_batch_layout", "sfx_batch_set_schedule", "sfx_batch_set_tuning", "sfx_batch_step",
+    "sfx_batch_stats",
     "sfx_batch_autotune", "sfx_batch_work", "sfx_f_from_gamma", "sfx_marangoni_loss",
     "sfx_adjoint_apply", "sfx_adjoint_step", "sfx_vof_advect", "sfx_capillary_force", "sfx_acdi_step", "sfx_batch_reuse_phi",
     "sfx_phase_field_from_chi", "sfx_profile_work",
@@ -145,6 +146,8 @@ def load(path: str = SO_PATH):
     L.sfx_batch_layout.argtypes = [vp, szp, szp, szp, szp, szp, szp]
     L.sfx_batch_set_schedule.restype = C.c_int
     L.sfx_batch_set_schedule.argtypes = [vp, C.c_int, C.c_int, C.c_int]
+    L.sfx_batch_set_tuning.restype = C.c_int
+    L.sfx_batch_set_tuning.argtypes = [vp, C.c_int, C.c_int]
     L.sfx_batch_step.restype = C.c_int
     L.sfx_batch_step.argtypes = [vp, vp, vp, vp, vp, vp, dp, vp]
     L.sfx_batch_stats.restype = C.c_int

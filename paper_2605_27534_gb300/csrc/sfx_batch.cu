@@ -54,6 +54,7 @@ struct BPtr {
   float4* rc;             // r_f, r_F, u = c1 F, v = c1 (f_inf - f) per cell (colour-packed)
   float2* e2;             // Newton corrections (e_f, e_F), colour-packed
   unsigned int* norms;    // 4 per instance
+  int* rkind;             // 2 per instance: residual kind (0 FP32, 1 pair), FP32 passes so far
   int* active;
   int* iters;
   float* rres;            // 2 per instance: last relative residuals
@@ -124,12 +125,14 @@ __global__ void k_b_copy(const BInst* __restrict__ I, int n, const int* __restri
   else { P.fs[g] = P.f[g]; P.Fs[g] = P.F[g]; }
 }
 
-__global__ void k_b_init(int n, BPtr P) {
+__global__ void k_b_init(int n, BPtr P, int fast) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i == 0) *P.loop = 0;
   if (i >= n) return;
   P.active[i] = 1;
   P.iters[i] = 0;
+  P.rkind[2 * i] = fast > 0 ? 0 : 1;
+  P.rkind[2 * i + 1] = 0;
   for (int q = 0; q < 4; ++q) P.norms[4 * i + q] = 0u;
 }
 
@@ -147,8 +150,14 @@ __global__ void k_b_resid(const BInst* __restrict__ I, int n, const int* __restr
     const int i = (int)((ix)c % (ix)L.nx), j = (int)((ix)c / (ix)L.nx);
     const float2* B2[3] = {P.B2[0] + B.rfoff, P.B2[1] + B.zfoff, nullptr};
     const size_t o = B.coff, w = B.poff;
-    resid2_cell<G>(B.p, i, j, 0, c, P.phi32 + o, B2, P.f + o, P.F + o, P.fs + o, P.Fs + o,
-                P.rc + w, m, P.e2 + w);
+    // the FP32 residual for the instance's first iterations (the kind is
+    // the same for every block of an instance)
+    if (P.rkind[2 * inst] == 0)
+      resid32_cell<G>(B.p, i, j, 0, c, P.phi32 + o, B2, P.f + o, P.F + o, P.fs + o, P.Fs + o,
+                      P.rc + w, m, P.e2 + w);
+    else
+      resid2_cell<G>(B.p, i, j, 0, c, P.phi32 + o, B2, P.f + o, P.F + o, P.fs + o, P.Fs + o,
+                     P.rc + w, m, P.e2 + w);
   }
   // block maxima; the flags kernel combines the blocks of each instance
   __shared__ float wm[4][16];
@@ -167,7 +176,7 @@ __global__ void k_b_resid(const BInst* __restrict__ I, int n, const int* __restr
 
 // convergence test of the current iteration: one block per instance still
 // active combines the residual maxima of the instance's blocks
-__global__ void k_b_flags(int n, const int* __restrict__ pre, BPtr P, float tol) {
+__global__ void k_b_flags(int n, const int* __restrict__ pre, BPtr P, float tol, int fast) {
   const int i = blockIdx.x;
   if (i >= n || !P.active[i]) return;
   const int it = *P.loop + 1;
@@ -191,8 +200,16 @@ __global__ void k_b_flags(int n, const int* __restrict__ pre, BPtr P, float tol)
   P.rres[2 * i + 1] = rF / fmaxf(bF, 1e-30f);
   P.iters[i] = it;
   P.work[2 * i] += 1;
-  if (rf <= tol * bf && rF <= tol * bF) P.active[i] = 0;   // converged: stop here
-  else P.work[2 * i + 1] += 1;                             // the sweeps run
+  if (P.rkind[2 * i] != 0 && rf <= tol * bf && rF <= tol * bF) {
+    P.active[i] = 0;   // converged on a pair residual: stop here
+    return;
+  }
+  P.work[2 * i + 1] += 1;   // the sweeps run
+  // after `fast` FP32 passes, or once the residuals are small, the pair
+  // residual (as the single-grid solve switches)
+  if (P.rkind[2 * i] == 0 && (++P.rkind[2 * i + 1] >= fast ||
+                              (rf <= kFastResidSwitch * bf && rF <= kFastResidSwitch * bF)))
+    P.rkind[2 * i] = 1;
 }
 
 // end of an iteration: count it, and let the step's loop run again while
@@ -331,7 +348,7 @@ struct sfx_batch {
   // graph cache
   cudaGraphExec_t exec = nullptr;
   const void* key[5] = {};
-  int key_sched[5] = {};
+  int key_sched[6] = {};
   bool reuse_phi = false;         // phi static: fold and drifts outside the graph
   const void* drift_phi = nullptr;
   double key_tol = 0;
@@ -339,6 +356,7 @@ struct sfx_batch {
   cudaStream_t cap_body = nullptr;   // captures the body of the iteration loop
   // last schedule
   int sweeps = 3, max_it = 8;
+  int fast = 2;                   // FP32 residual passes at most per instance and step
   std::vector<int> h_iters;
 };
 
@@ -383,7 +401,7 @@ sfx_status build_prefix(sfx_batch* b) {
 sfx_status enqueue_step(sfx_batch* b, bool advect, float tol, cudaStream_t s) {
   const int n = b->n, bs = b->block;
   BPtr& P = b->P;
-  k_b_init<<<(n + 127) / 128, 128, 0, s>>>(n, P);
+  k_b_init<<<(n + 127) / 128, 128, 0, s>>>(n, P, b->fast);
   if (!b->reuse_phi) {
     k_b_fold<<<b->nb_cell, bs, 0, s>>>(b->dI, n, b->pre_cell, P);
     k_b_drift<<<b->nb_rf, bs, 0, s>>>(b->dI, n, b->pre_rf, 0, P);
@@ -420,7 +438,7 @@ sfx_status enqueue_step(sfx_batch* b, bool advect, float tol, cudaStream_t s) {
   auto resid = axi ? &k_b_resid<SFX_AXISYM> : &k_b_resid<SFX_PLANAR2D>;
   auto corr = axi ? &k_b_corr<SFX_AXISYM> : &k_b_corr<SFX_PLANAR2D>;
   resid<<<b->nb_cell, bs, 0, sb>>>(b->dI, n, b->pre_cell, P);
-  k_b_flags<<<n, 256, 0, sb>>>(n, b->pre_cell, P, tol);
+  k_b_flags<<<n, 256, 0, sb>>>(n, b->pre_cell, P, tol, b->fast);
   // the residual pass did the first red half-sweep
   for (int q = 0; q < b->sweeps; ++q)
     for (int color = (q == 0 ? 1 : 0); color < 2; ++color)
@@ -443,10 +461,11 @@ sfx_status enqueue_step(sfx_batch* b, bool advect, float tol, cudaStream_t s) {
 sfx_status ensure_graph(sfx_batch* b, const void* phi, const void* ur, const void* uz, void* f,
                         void* F, float tol) {
   const void* k[5] = {phi, ur, uz, f, F};
-  const int sched[5] = {b->block, b->sweeps, b->max_it, ur != nullptr, b->reuse_phi ? 1 : 0};
+  const int sched[6] = {b->block, b->sweeps, b->max_it, ur != nullptr, b->reuse_phi ? 1 : 0,
+                        b->fast};
   bool same = b->exec != nullptr && tol == b->key_tol;
   for (int i = 0; i < 5 && same; ++i) same = k[i] == b->key[i];
-  for (int i = 0; i < 5 && same; ++i) same = sched[i] == b->key_sched[i];
+  for (int i = 0; i < 6 && same; ++i) same = sched[i] == b->key_sched[i];
   if (same) return SFX_OK;
   if (b->exec) {
     cudaGraphExecDestroy(b->exec);
@@ -471,7 +490,7 @@ sfx_status ensure_graph(sfx_batch* b, const void* phi, const void* ur, const voi
   cudaGraphDestroy(g);
   SFX_CUDA(e);
   for (int i = 0; i < 5; ++i) b->key[i] = k[i];
-  for (int i = 0; i < 5; ++i) b->key_sched[i] = sched[i];
+  for (int i = 0; i < 6; ++i) b->key_sched[i] = sched[i];
   b->key_tol = tol;
   return SFX_OK;
 }
@@ -550,6 +569,7 @@ sfx_status sfx_batch_create_geom(const sfx_batch_instance* inst, int n, int geom
   if (st == SFX_OK) st = balloc(b, &P.rc, b->npack);
   if (st == SFX_OK) st = balloc(b, &P.e2, b->npack);
   if (st == SFX_OK) st = balloc(b, &P.norms, 4 * (size_t)n);
+  if (st == SFX_OK) st = balloc(b, &P.rkind, 2 * (size_t)n);
   if (st == SFX_OK) st = balloc(b, &P.active, (size_t)n);
   if (st == SFX_OK) st = balloc(b, &P.iters, (size_t)n);
   if (st == SFX_OK) st = balloc(b, &P.loop, (size_t)1);
@@ -599,6 +619,15 @@ sfx_status sfx_batch_layout(const sfx_batch* b, size_t* n_cells, size_t* n_rface
     if (zface_off) zface_off[i] = b->zfoff[i];
   }
   return SFX_OK;
+}
+
+sfx_status sfx_batch_set_tuning(sfx_batch* b, int key, int value) {
+  if (!b) return SFX_ERR_ARG;
+  if (key == SFX_TUNE_F32_FAST_RESID && value >= 0 && value <= 16) {
+    b->fast = value;
+    return SFX_OK;
+  }
+  return SFX_ERR_ARG;
 }
 
 sfx_status sfx_batch_set_schedule(sfx_batch* b, int block, int sweeps, int max_iters) {

@@ -1284,7 +1284,7 @@ sfx_status solve_dc32(sfx_ctx* c, const Nl32& pf, const Nl32& pF, const float* p
 // incremental residual passes the test; nrm[4] records the kind each
 // iteration's norms came from.
 constexpr unsigned int kTimeoutBits = 0xffffffffu;
-constexpr float kFastSwitch = 1e-3f;
+constexpr float kFastSwitch = kFastResidSwitch;
 constexpr float kIncrFactor = 1e5f;
 __global__ void k_flag32(unsigned int* __restrict__ nrm, float tol, int it, int fast_max,
                          int incr_ok, int* __restrict__ flag) {

@@ -19,6 +19,11 @@ namespace sfx {
 constexpr int kTotalsBlocks = 152 * 4;
 constexpr int kTotalsThreads = 256;
 
+// FP32 Newton solves (single-grid and batched) evaluate the residuals in
+// FP32 until both relative residuals are below this, or for a set number
+// of iterations, then in pair arithmetic.
+constexpr float kFastResidSwitch = 1e-3f;
+
 // Device arrays of one multigrid level.  Level 0 (the fine grid) works on
 // the caller's field; its coefficient arrays live here too.
 struct LevelData {

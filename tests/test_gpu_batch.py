@@ -103,14 +103,17 @@ def test_batch_matches_oracle_per_instance(sfx):
             assert abs(m - (V * x).sum()) <= 1e-13 * max(np.abs(V * x).sum(), 1e-300)
 
 
-def test_batch_bitwise_equals_single_grid_steps(sfx):
+@pytest.mark.parametrize("fast", [0, 2])
+def test_batch_bitwise_equals_single_grid_steps(sfx, fast):
     """Fixed budget (no instance meets tol = 1e-30): the batched kernels run
-    the single-grid SFX_F32 arithmetic cell for cell (with pair residuals at
-    every iteration, as the batch evaluates them)."""
+    the single-grid SFX_F32 arithmetic cell for cell, with the same number
+    of FP32 residual passes (`fast`) before the pair residuals on both
+    sides."""
     import torch
     inst = _instances(seed=5)
     B = _Batch(sfx, inst)
     B.b.sfx_batch_set_schedule(128, 2, 4)
+    B.b.sfx_batch_set_tuning(sfx._lib.SFX_TUNE_F32_FAST_RESID, fast)
     for _ in range(2):
         B.step(1e-30)
     st = B.b.sfx_batch_stats()
@@ -121,7 +124,7 @@ def test_batch_bitwise_equals_single_grid_steps(sfx):
     o = sfx.default_opts(tol=1e-30, max_cycles=4, nu1=2, nu2=0)
     for k, (c, phi, f0) in enumerate(inst):
         ctx = sfx.Context.for_grid(c.grid, sfx.SFX_F32)
-        ctx.sfx_set_tuning(sfx._lib.SFX_TUNE_F32_FAST_RESID, 0)
+        ctx.sfx_set_tuning(sfx._lib.SFX_TUNE_F32_FAST_RESID, fast)
         f, F = sfx.sfx_df_pack(dev(f0)), sfx.sfx_df_pack(dev(c.F0))
         phid = dev(phi)
         u = [dev(c.ux, torch.float32), dev(c.uy, torch.float32), None]
@@ -163,6 +166,35 @@ def test_batch_early_exit_and_closed_box_mass(sfx):
     # the converged one
     rp, sg = B.b.sfx_batch_work()
     assert list(rp) == list(its) and list(sg) == list(its - 5)
+
+
+def test_batch_fp32_residuals_reach_the_same_fixed_point(sfx):
+    """Each instance's first Newton iterations on FP32 residuals (at most
+    two, per instance) end on the pair residual's fixed point: every
+    instance converges on a pair residual, the states match the pair-only
+    batch to far below the FP32 tolerance, and no instance needs more than
+    one extra iteration per step."""
+    import torch
+    inst = _instances(seed=9)
+    outs, its = [], []
+    for fast in (0, 2):
+        B = _Batch(sfx, inst)
+        B.b.sfx_batch_set_schedule(256, 3, 60)
+        B.b.sfx_batch_set_tuning(sfx._lib.SFX_TUNE_F32_FAST_RESID, fast)
+        n = []
+        for _ in range(3):
+            B.step(1e-10)
+            st = B.b.sfx_batch_stats()
+            assert all(st["converged"])
+            assert max(st["res_f"]) <= 1e-10 and max(st["res_F"]) <= 1e-10
+            n.append(np.array(st["iters"]))
+        torch.cuda.synchronize()
+        its.append(n)
+        outs.append((host(sfx.sfx_df_unpack(B.f)), host(sfx.sfx_df_unpack(B.F))))
+    for a, b in zip(outs[0], outs[1]):
+        assert np.abs(a - b).max() / np.abs(a).max() < 1e-8
+    for k, m in zip(its[0], its[1]):
+        assert np.all(m <= k + 1), (k, m)
 
 
 def test_graph_cache_follows_pointers(sfx):
@@ -223,6 +255,10 @@ def test_batch_rejects_bad_arguments(sfx):
     with pytest.raises(sfx.SfxError):
         B.b.sfx_batch_set_schedule(100, 3, 8)
     with pytest.raises(sfx.SfxError):
+        B.b.sfx_batch_set_tuning(sfx._lib.SFX_TUNE_F32_FAST_RESID, 17)
+    with pytest.raises(sfx.SfxError):
+        B.b.sfx_batch_set_tuning(sfx._lib.SFX_TUNE_TILED_SWEEP, 1)
+    with pytest.raises(sfx.SfxError):
         B.b.sfx_batch_step(B.phi, B.f, B.F, 1e-10, ur=B.ur, uz=None)
     with pytest.raises(sfx.SfxError):
         B.b.sfx_batch_step(B.phi, B.f, B.f, 1e-10)
@@ -267,21 +303,23 @@ def test_planar_kinetics_sweep_matches_oracle_and_conserves(sfx):
         assert abs(st["mass_f"][k] - c.grid.h ** 2 * fg.sum()) <= 1e-12 * M0, k
 
 
-def test_planar_batch_bitwise_equals_single_grid_steps(sfx):
+@pytest.mark.parametrize("fast", [0, 2])
+def test_planar_batch_bitwise_equals_single_grid_steps(sfx, fast):
     """Fixed budget: planar batched kernels run the single-grid SFX_F32
-    arithmetic cell for cell, as the axisymmetric ones do (pair residuals
-    at every iteration)."""
+    arithmetic cell for cell, as the axisymmetric ones do (the same number
+    of FP32 residual passes on both sides)."""
     import torch
     inst = _flat_instances(seed=21)
     B = _Batch(sfx, inst, flow=False, geom=sfx.SFX_PLANAR2D)
     B.b.sfx_batch_set_schedule(128, 2, 4)
+    B.b.sfx_batch_set_tuning(sfx._lib.SFX_TUNE_F32_FAST_RESID, fast)
     for _ in range(2):
         B.step(1e-30)
     fb, Fb = B.f.cpu().numpy(), B.F.cpu().numpy()
     o = sfx.default_opts(tol=1e-30, max_cycles=4, nu1=2, nu2=0)
     for k, (c, phi, f0) in enumerate(inst):
         ctx = sfx.Context.for_grid(c.grid, sfx.SFX_F32)
-        ctx.sfx_set_tuning(sfx._lib.SFX_TUNE_F32_FAST_RESID, 0)
+        ctx.sfx_set_tuning(sfx._lib.SFX_TUNE_F32_FAST_RESID, fast)
         f, F = sfx.sfx_df_pack(dev(f0)), sfx.sfx_df_pack(dev(c.F0))
         for _ in range(2):
             ctx.sfx_surfactant_step(c.params, dev(phi), f, F, c.dt, opts=o,
