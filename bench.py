@@ -114,6 +114,9 @@ def parse():
     ap.add_argument("--fast-resid", type=int, default=2,
                     help="FP32: Newton iterations per solve with FP32 residuals "
                          "(SFX_TUNE_F32_FAST_RESID; 0 = pair residuals only)")
+    ap.add_argument("--incr-resid", type=int, default=1, choices=[0, 1],
+                    help="FP32 3D tiled: incremental FP32 residuals after a small pair "
+                         "residual (SFX_TUNE_F32_INCR_RESID)")
     ap.add_argument("--predict", action="store_true",
                     help="FP32: start each Newton solve from x* plus the last increment "
                          "(SFX_TUNE_PREDICT 1; no gain on the 3D workload)")
@@ -146,6 +149,19 @@ def job_rate(units_per_rank, world, ms):
     """Whole-job throughput: the units all ranks processed over the slowest
     rank's time."""
     return units_per_rank * world / (ms * 1e-3)
+
+
+def residual_schedule(a, f32):
+    """The residual passes of a Newton solve, as the bench configures them."""
+    if not f32:
+        return "pair arithmetic"
+    incr = a.incr_resid and a.tiled
+    if not a.fast_resid:
+        return "pair passes" + (", incremental FP32 from a small one" if incr else "")
+    return ("FP32 for up to %d Newton iterations per step (while the relative residual is "
+            "above 1e-3), then %s" % (
+                a.fast_resid, "one pair pass, then incremental FP32 from it" if incr
+                else "pair passes"))
 
 
 def algorithmic_bytes(kind, grid, wbytes, sweeps=3, tiled=False):
@@ -457,6 +473,7 @@ def run_gpu(a, case, rank, world, local_rank):
         ctx.sfx_set_tuning(sfx._lib.SFX_TUNE_TILED_SWEEP, a.tiled)
         ctx.sfx_set_tuning(sfx._lib.SFX_TUNE_TILED_ZCHUNK, a.tiled_zchunk)
         ctx.sfx_set_tuning(sfx._lib.SFX_TUNE_F32_FAST_RESID, a.fast_resid)
+        ctx.sfx_set_tuning(sfx._lib.SFX_TUNE_F32_INCR_RESID, a.incr_resid)
     stats = []
 
     def step():
@@ -645,11 +662,7 @@ def run_gpu(a, case, rank, world, local_rank):
                    "sweeps": "tiled (whole sweep per launch, zchunk %s)" % (
                              a.tiled_zchunk or "auto")
                              if (a.tiled and prec == sfx.SFX_F32) else "one launch per colour",
-                   "residuals": ("FP32 for up to %d Newton iterations per step (while the "
-                                 "relative residual is above 1e-3), then one pair pass, then "
-                                 "incremental FP32 from it" % a.fast_resid)
-                                if (a.fast_resid and prec == sfx.SFX_F32)
-                                else "pair arithmetic",
+                   "residuals": residual_schedule(a, prec == sfx.SFX_F32),
                    "l2": "inputs larger than L2 (state + coefficients %.2f GB)" % (
                        g.ncell * 8 * 20 / 1e9),
                    "parallelism": "replicas%d" % world,
