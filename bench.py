@@ -100,8 +100,11 @@ def parse():
     ap.add_argument("--tol", type=float, default=1e-10)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--sweeps", type=int, default=4,
+    ap.add_argument("--sweeps", type=int, default=3,
                     help="FP32: red-black correction sweeps per Newton iteration")
+    ap.add_argument("--vortex-sweeps", type=int, default=4,
+                    help="FP32: correction sweeps per Newton iteration of the 2D vortex "
+                         "workload (no over-relaxation in 2D)")
     ap.add_argument("--sweep-planes", type=int, default=2, choices=[1, 2],
                     help="FP32 3D: z-planes per thread of the correction sweep "
                          "(SFX_TUNE_SWEEP_PLANES)")
@@ -111,12 +114,16 @@ def parse():
     ap.add_argument("--tiled-zchunk", type=int, default=0,
                     help="z-planes per block of the tiled sweep (SFX_TUNE_TILED_ZCHUNK; "
                          "0 = chosen from the grid)")
-    ap.add_argument("--fast-resid", type=int, default=2,
+    ap.add_argument("--fast-resid", type=int, default=1,
                     help="FP32: Newton iterations per solve with FP32 residuals "
                          "(SFX_TUNE_F32_FAST_RESID; 0 = pair residuals only)")
     ap.add_argument("--incr-resid", type=int, default=1, choices=[0, 1],
                     help="FP32 3D tiled: incremental FP32 residuals after a small pair "
                          "residual (SFX_TUNE_F32_INCR_RESID)")
+    ap.add_argument("--sor", type=int, default=1,
+                    help="FP32 3D: over-relaxed red updates (SFX_TUNE_F32_SOR: 1 = omega "
+                         "from the diffusion numbers, 0 = Gauss-Seidel, 1001..1999 = omega_F "
+                         "in 1/1000)")
     ap.add_argument("--predict", action="store_true",
                     help="FP32: start each Newton solve from x* plus the last increment "
                          "(SFX_TUNE_PREDICT 1; no gain on the 3D workload)")
@@ -474,6 +481,7 @@ def run_gpu(a, case, rank, world, local_rank):
         ctx.sfx_set_tuning(sfx._lib.SFX_TUNE_TILED_ZCHUNK, a.tiled_zchunk)
         ctx.sfx_set_tuning(sfx._lib.SFX_TUNE_F32_FAST_RESID, a.fast_resid)
         ctx.sfx_set_tuning(sfx._lib.SFX_TUNE_F32_INCR_RESID, a.incr_resid)
+        ctx.sfx_set_tuning(sfx._lib.SFX_TUNE_F32_SOR, a.sor)
     stats = []
 
     def step():
@@ -663,6 +671,12 @@ def run_gpu(a, case, rank, world, local_rank):
                              a.tiled_zchunk or "auto")
                              if (a.tiled and prec == sfx.SFX_F32) else "one launch per colour",
                    "residuals": residual_schedule(a, prec == sfx.SFX_F32),
+                   "relaxation": ("%d red-black sweeps per Newton iteration, red updates "
+                                  "over-relaxed (%s)" % (a.sweeps, "omega from the Jacobi-"
+                                  "radius bound" if a.sor == 1 else "omega_F = %.3f" % (
+                                      a.sor / 1000.0)) if a.sor else
+                                  "%d red-black Gauss-Seidel sweeps per Newton iteration" %
+                                  a.sweeps) if prec == sfx.SFX_F32 else None,
                    "l2": "inputs larger than L2 (state + coefficients %.2f GB)" % (
                        g.ncell * 8 * 20 / 1e9),
                    "parallelism": "replicas%d" % world,
@@ -858,7 +872,7 @@ def vortex_run(a, dev, steps, prec, warmup=3, rebuild_every=1):
     force = torch.empty((2,) + g.shape, dtype=vt, device=dev)
     opts = sfx.default_opts(tol=a.tol, max_cycles=200)
     if f32:
-        opts.nu1, opts.nu2 = a.sweeps, 0
+        opts.nu1, opts.nu2 = a.vortex_sweeps, 0
     pic = []
 
     def step(n):

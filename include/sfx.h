@@ -376,6 +376,20 @@ typedef enum {
                                below a tenth of the tolerance); 0 = a pair
                                pass at every iteration after the FP32
                                ones. */
+  SFX_TUNE_F32_SOR = 11,    /* SFX_F32 Newton solver, 3D, relaxation
+                               without multigrid: 1 (default) = every red
+                               update after the first is over-relaxed,
+                               e <- e + omega (e_GS - e), per field with
+                               omega = 2/(2 - rho^2), rho = s/(1 + s),
+                               s = dt (6 D/h^2 + 2 sqrt(3) D/(eps h)) (a
+                               row-sum bound on the Jacobi radius with the
+                               drift bounded by D/eps per face; the
+                               minimax factor of black-then-red sweeps is
+                               rho^2/(2 - rho^2) per sweep instead of
+                               rho^2); 1001 .. 1999 = omega of F set to
+                               value/1000 (f as for 1); 0 = Gauss-Seidel.
+                               The converged state is the same fixed
+                               point. */
   SFX_TUNE_ADVECT_STAGED = 9, /* SFX_F32, 3D: 1 (default) = the BCG step of
                                f and F from z-planes staged in shared
                                memory (values rounded once, neighbours past

@@ -40,6 +40,7 @@ SFX_TUNE_TILED_ZCHUNK = 7
 SFX_TUNE_F32_FAST_RESID = 8
 SFX_TUNE_ADVECT_STAGED = 9
 SFX_TUNE_F32_INCR_RESID = 10
+SFX_TUNE_F32_SOR = 11
 KERNEL_KINDS = ["smooth_fine", "smooth_coarse", "restrict", "prolong", "setup", "residual",
                 "advect", "totals", "forces", "phase", "other", "smooth_tiled",
                 "residual_fp32", "residual_incr"]

@@ -391,6 +391,10 @@ sfx_status sfx_set_tuning(sfx_ctx* c, int key, int value) {
     c->f32.incr_resid = value == 1;
     return SFX_OK;
   }
+  if (key == SFX_TUNE_F32_SOR && (value == 0 || value == 1 || (value > 1000 && value < 2000))) {
+    c->f32.sor = value;
+    return SFX_OK;
+  }
   if (key == SFX_TUNE_ADVECT_STAGED && (value == 0 || value == 1)) {
     c->f32.adv_staged = value == 1;
     return SFX_OK;

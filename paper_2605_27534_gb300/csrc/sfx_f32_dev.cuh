@@ -657,6 +657,7 @@ struct Corr2In {
   float4 q4;
   ix c, own, oth;
   int i;
+  bool red;   // a red update after the first (over-relaxed in 3D)
 };
 
 template <int G>
@@ -692,6 +693,7 @@ __device__ __forceinline__ void corr2_load(const Nw32& p, int i, int j, int k,
     in.enF[q] = v.y;
   }
   in.ec = first ? make_float2(0.0f, 0.0f) : e2[in.own];
+  in.red = color == 0 && !first;
   faces6x2(L, H[0], H[1], H[2], i, j, k, in.has, in.Bf, in.BF);
   in.q4 = rc[in.own];
 }
@@ -726,6 +728,11 @@ __device__ __forceinline__ void corr2_apply(const Nw32& p, const Corr2In& in,
 #pragma unroll
     for (int q = 0; q < 6; ++q) w[q] = in.has[q] ? 1.0f : 0.0f;
     ne = corr3_cell(p, in.enf, in.enF, w, in.Bf, in.BF, in.q4);
+    // the old value is read here, not with the other loads: black launches
+    // (the state update among them) never read it, and keeping it live
+    // across the cell's arithmetic costs the two-plane kernel its overlap
+    // of loads (at its register bound)
+    if (in.red) ne = relax_red(p, ne, e2[in.own]);
   } else {
     float dgf, dgF;
     const float flf = flux_lin<G>(L, p.invh, p.Dfh, p.literal, in.i, efc, in.enf, in.has, in.Bf,

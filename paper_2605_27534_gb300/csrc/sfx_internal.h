@@ -86,6 +86,9 @@ struct F32Scratch {
   int fast_resid = 2;               // FP32 residual passes at most per Newton solve
   bool adv_staged = true;           // 3D advection from shared-memory planes
   bool incr_resid = true;           // incremental FP32 residuals after a pair pass (tiled path)
+  int sor = 1;                      // 3D relaxation: 0 Gauss-Seidel, 1 over-relaxed red
+                                    // updates (omega from the diffusion numbers),
+                                    // 1001 .. 1999 omega_F = sor / 1000
   bool predict = true;              // start Newton from x* + last increment
   bool redist32 = false;            // redistance in FP32 (else FP64)
   int sweep_planes = 2;             // 3D correction sweep: planes per thread (1 or 2)

@@ -172,7 +172,8 @@ __device__ __forceinline__ float2 tiled_cell(const Nw32& p, TileSlot& S0, const 
   }
   const float2 ne = corr3_cell(p, enf, enF, w, Bf, BF, q4);
   if (keep) S0.e[col][ye][pe] = ne;
-  return ne;
+  // colour B (red) is staged: its old value is at hand for over-relaxation
+  return col == cB ? relax_red(p, ne, S0.e[col][ye][pe]) : ne;
 }
 
 // The five copies of one plane into its slot, completing on the slot's

@@ -813,7 +813,8 @@ def test_tiled_sweep_bitwise(sfx, shape, zchunk):
     shared memory by tensor copies) gives the colour launches' bits: x tiles
     with a ragged last tile (136 = 2 x 64 + 8), rows and planes that do not
     fill the last tile or z-chunk, chunks of 4 and 5 planes (many chunk
-    seams); it runs 4 instead of 7 sweep launches per Newton iteration."""
+    seams); it runs 4 instead of 7 sweep launches per Newton iteration.  The
+    red updates are over-relaxed (the default) in both."""
     import torch
     nz, ny, nx = shape
     g, Cf = _sphere(nx, ny, nz, 0.3)
@@ -874,6 +875,40 @@ def test_fp32_residual_iterations_reach_the_same_fixed_point(sfx, fast):
     for a, b in zip(outs[0], outs[1]):
         assert np.abs(a - b).max() / np.abs(a).max() < 1e-8
     assert all(m <= k + 1 for k, m in zip(its[0], its[1])), its
+
+
+@pytest.mark.parametrize("tiled", [0, 1])
+def test_over_relaxed_sweeps_reach_the_same_fixed_point(sfx, tiled):
+    """Red updates over-relaxed (omega from the Jacobi-radius bound, and a
+    fixed omega_F = 1.15) end on the Gauss-Seidel solve's fixed point: the
+    state matches to far below the FP32 tolerance and each solve converges,
+    with no more iterations than Gauss-Seidel at one sweep fewer per
+    iteration; colour launches (tiled = 0) and tiled sweeps alike."""
+    import torch
+    nz, ny, nx = 24, 20, 32
+    g, Cf = _sphere(nx, ny, nz, 0.3)
+    ux, uy, uz = W.uniform_faces(g, (0.3, -0.2, 0.25))
+    p = W.Params(ka=2.0, kd=0.5, Df=2e-3, DF=5e-2, eps=0.75 * g.h)
+    _, phi, delta = oracle.phase_field_build(g, Cf, 24, W.redist_dtau(g), p.eps)
+    outs, its = [], []
+    for sor, sweeps in ((0, 4), (1, 3), (1150, 3)):
+        ctx = _ctx(sfx, g, 1)
+        ctx.sfx_set_tuning(sfx._lib.SFX_TUNE_TILED_SWEEP, tiled)
+        ctx.sfx_set_tuning(sfx._lib.SFX_TUNE_F32_SOR, sor)
+        f, F = _pairs(ctx, 0.3 * delta), _pairs(ctx, 1.0 - Cf)
+        u = [dev(v, torch.float32) for v in (ux, uy, uz)]
+        o = sfx.default_opts(tol=1e-10, nu1=sweeps, nu2=0)
+        n = []
+        for _ in range(3):
+            st = ctx.sfx_surfactant_step(p, dev(phi), f, F, 0.2 * g.h, *u, opts=o)
+            assert st.converged
+            n.append(st.picard)
+        its.append(n)
+        outs.append((host(ctx.sfx_df_unpack(f)), host(ctx.sfx_df_unpack(F))))
+    for k in (1, 2):
+        for a, b in zip(outs[0], outs[k]):
+            assert np.abs(a - b).max() / np.abs(a).max() < 1e-8
+        assert all(m <= q + 1 for q, m in zip(its[0], its[k])), its
 
 
 @pytest.mark.parametrize("shape", [(24, 24, 24), (19, 17, 70), (5, 9, 33)])
