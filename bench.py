@@ -46,9 +46,9 @@ NOMINAL_HBM_GBS = 7900.0   # GB300 HBM3e nominal bandwidth (context beside the m
 # withdrawn (None) as soon as those sources differ from the captured ones.
 NCU_TRAFFIC = {
     ("smooth_tiled", "f32", 3): {
-        "bytes_per_cell": (238.20e6 + 42.57e6) / 192 ** 3,
+        "bytes_per_cell": (238.06e6 + 42.11e6) / 192 ** 3,
         "sources": ["sfx_tiled.cuh", "sfx_corr3.cuh"],
-        "sha256_16": "20e35e2630e1d952",
+        "sha256_16": "4add95b5e93d9bd4",
         "capture": "profiles/corr2_tiled_hr3d192_f32.md (192^3 with the 256^3 z-chunk of 37 "
                    "planes, one launch), scaled by the cell count",
     },

@@ -303,30 +303,6 @@ __global__ void k_corr32(Corr32 p, const float* __restrict__ Bx, const float* __
 // the coupled one does not.
 // Evaluate both residuals (pairs), the 2x2 exchange Jacobian and the
 // norms at every cell of the current state.
-// `done`: the solve converged at an earlier iteration; `mode` (may be
-// null): the residual kind chosen on the device for this iteration (0 the
-// FP32 pass, 1 the pair pass, 2 the incremental FP32 pass); a launch whose
-// kind `want` is not chosen returns at once.
-__device__ __forceinline__ bool resid_skip(const int* done, const int* mode, int want) {
-  return (done && *done) || (mode && *mode != want);
-}
-
-// Warp maxima of the four norms, then one atomic per block and norm.
-__device__ __forceinline__ void resid_norms(const float* m, unsigned int* norms) {
-  __shared__ float wm[4][8];
-#pragma unroll
-  for (int q = 0; q < 4; ++q) {
-    const float v = warp_max(m[q]);
-    if ((threadIdx.x & 31) == 0) wm[q][threadIdx.x >> 5] = v;
-  }
-  __syncthreads();
-  if (threadIdx.x < 4) {
-    float v = 0.0f;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) v = fmaxf(v, wm[threadIdx.x][w]);
-    atomicMax(&norms[threadIdx.x], fbits(v));
-  }
-}
-
 template <int G>
 __global__ void __launch_bounds__(256, 5)
 k_resid2_32(Nw32 p, const float* __restrict__ phi, const float2* __restrict__ B2x,
@@ -614,16 +590,6 @@ struct ZSmem {
   ZCoef cf[ZNC];
 };
 
-__device__ __forceinline__ void cp_async4(void* dst, const void* src) {
-  unsigned d = (unsigned)__cvta_generic_to_shared(dst);
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(src) : "memory");
-}
-__device__ __forceinline__ void cp_async8(void* dst, const void* src) {
-  unsigned d = (unsigned)__cvta_generic_to_shared(dst);
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(src) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
 
 template <int FIELD>
 __global__ void __launch_bounds__(256) k_nlrb32_z(Nl32 p, const float* __restrict__ phi,
@@ -1429,6 +1395,11 @@ sfx_status solve_newton32(sfx_ctx* c, const Nw32& p, const float* phi, float* co
   // an iteration writing the first red half-sweep into the buffer that the
   // previous iteration's correction is not in
   const int incr_ok = tiled && c->f32.incr_resid ? 1 : 0;
+  auto pair_pass = [&](const float2* fa, const float2* Fa, unsigned int* nb, float2* et,
+                       const int* dn) {
+    SFX_KERNEL(c, K_RESIDUAL, nk.resid, rg.grid, rg.block, s, p, phi, B2[0], B2[1], B2[2], fa, Fa,
+               fs, Fs, c->f32.rc, nb, et, dn, flag + 4);
+  };
   float2* ebuf[2] = {c->f32.e2, tiled ? c->f32.e2b : c->f32.e2};
   int efin = 1;   // buffer of the last correction added to the state
   // flag[4] = 1: pair residuals from the first iteration (no FP32 passes)
@@ -1458,8 +1429,7 @@ sfx_status solve_newton32(sfx_ctx* c, const Nw32& p, const float* phi, float* co
     float2* e2t = ebuf[etgt];
     SFX_KERNEL(c, K_RESID_FAST, nk.fast, rg.grid, rg.block, s, p, phi, B2[0], B2[1], B2[2], fsrc,
                Fsrc, fs, Fs, c->f32.rc, nbuf, e2t, flag, flag + 4);
-    SFX_KERNEL(c, K_RESIDUAL, nk.resid, rg.grid, rg.block, s, p, phi, B2[0], B2[1], B2[2], fsrc,
-               Fsrc, fs, Fs, c->f32.rc, nbuf, e2t, flag, flag + 4);
+    pair_pass(fsrc, Fsrc, nbuf, e2t, flag);
     if (incr_ok && it > 1)
       SFX_KERNEL(c, K_RESID_INCR, nk.incr, rg.grid, rg.block, s, p, phi, B2[0], B2[1], B2[2],
                  fsrc, Fsrc, fs, Fs, ebuf[efin], c->f32.rc, nbuf, e2t, flag, flag + 4);
@@ -1472,8 +1442,7 @@ sfx_status solve_newton32(sfx_ctx* c, const Nw32& p, const float* phi, float* co
       SFX_KERNEL(c, K_SETUP, k_restore32, nb, 256, s, n, ok, fs, Fs, fc, Fc);
       SFX_KERNEL(c, K_RESID_FAST, nk.fast, rg.grid, rg.block, s, p, phi, B2[0], B2[1], B2[2],
                  fc, Fc, fs, Fs, c->f32.rc, nbuf, e2t, ok, flag + 4);
-      SFX_KERNEL(c, K_RESIDUAL, nk.resid, rg.grid, rg.block, s, p, phi, B2[0], B2[1], B2[2],
-                 fc, Fc, fs, Fs, c->f32.rc, nbuf, e2t, ok, flag + 4);
+      pair_pass(fc, Fc, nbuf, e2t, ok);
     }
     SFX_KERNEL(c, K_OTHER, k_flag32, 1, 32, s, nbuf, tolf, it, fast_max, incr_ok, flag);
     SFX_CUDA(cudaMemcpyAsync(hn + 8 * (it & 1), nbuf, 8 * sizeof(unsigned int),

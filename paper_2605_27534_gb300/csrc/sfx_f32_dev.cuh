@@ -13,6 +13,19 @@ namespace {
 
 __device__ __forceinline__ unsigned int fbits(float v) { return __float_as_uint(v); }
 
+// Asynchronous copies from global into shared memory (cp.async), their
+// group commit and the wait for every committed group.
+__device__ __forceinline__ void cp_async4(void* dst, const void* src) {
+  unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async8(void* dst, const void* src) {
+  unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
 // ------------------------------------------------------------ drifts
 // Folded float copy of phi: phi where phi <= 1/2, phi - 1 elsewhere.
 __device__ __forceinline__ float fold_phi(double p) {
@@ -437,6 +450,38 @@ __device__ __forceinline__ void face32v2(const Adv32& A, const float2* __restric
   bcg_face2(a, u, A.dt, A.invh, d, L.ndim(), nb, vb, v1, v2);
 }
 
+__device__ __forceinline__ void resid2_tail(const Nw32& p, int i, int j, int k, ix c,
+                                            const float* __restrict__ phi, float2 fc, float2 Fc,
+                                            float2 flf, float2 flF, float df_, float dF_,
+                                            const float2* __restrict__ fst,
+                                            const float2* __restrict__ Fst,
+                                            float4* __restrict__ rc, float* m,
+                                            float2* __restrict__ e2);
+
+// `done`: the solve converged at an earlier iteration; `mode` (may be
+// null): the residual kind chosen on the device for this iteration (0 the
+// FP32 pass, 1 the pair pass, 2 the incremental FP32 pass); a launch whose
+// kind `want` is not chosen returns at once.
+__device__ __forceinline__ bool resid_skip(const int* done, const int* mode, int want) {
+  return (done && *done) || (mode && *mode != want);
+}
+
+// Warp maxima of the four norms, then one atomic per block and norm.
+__device__ __forceinline__ void resid_norms(const float* m, unsigned int* norms) {
+  __shared__ float wm[4][8];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const float v = warp_max(m[q]);
+    if ((threadIdx.x & 31) == 0) wm[q][threadIdx.x >> 5] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < 4) {
+    float v = 0.0f;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) v = fmaxf(v, wm[threadIdx.x][w]);
+    atomicMax(&norms[threadIdx.x], fbits(v));
+  }
+}
+
 // Both residuals (pairs) of App. C at cell c of the current state, the
 // kinetic diagonals and couplings of the linearised system, and the running
 // maxima m = {|r_f|, |b_f|, |r_F|, |b_F|}.  With e2 != NULL the first red
@@ -467,6 +512,21 @@ __device__ __forceinline__ void resid2_cell(const Nw32& p, int i, int j, int k, 
 #pragma unroll
   for (int q = 0; q < 6; ++q) nb[q] = has[q] ? Fin[nbi[q]] : make_float2(0.0f, 0.0f);
   const float2 flF = flux_pair<G>(L, p.invh, p.DFh, p.literal, i, Fc, nb, has, BF, dF_);
+  resid2_tail(p, i, j, k, c, phi, fc, Fc, flf, flF, df_, dF_, fst, Fst, rc, m, e2);
+}
+
+// The rest of the pair residual of one cell from its pair fluxes flf, flF
+// (already over h) and their diagonal weights df_, dF_: the exchange, both
+// residuals, u and v, the first red half-sweep and the norms (the outputs
+// of resid2_cell).
+__device__ __forceinline__ void resid2_tail(const Nw32& p, int i, int j, int k, ix c,
+                                            const float* __restrict__ phi, float2 fc, float2 Fc,
+                                            float2 flf, float2 flF, float df_, float dF_,
+                                            const float2* __restrict__ fst,
+                                            const float2* __restrict__ Fst,
+                                            float4* __restrict__ rc, float* m,
+                                            float2* __restrict__ e2) {
+  const Level& L = p.L;
   // exchange q = c1 F (f_inf - f) - r_d f, one evaluation for both equations
   const PhiPair ph = unfold(phi[c]);
   const float c1 = __fdividef(p.ka, ph.p + p.eta);
