@@ -48,7 +48,7 @@ NCU_TRAFFIC = {
     ("smooth_tiled", "f32", 3): {
         "bytes_per_cell": (238.06e6 + 42.11e6) / 192 ** 3,
         "sources": ["sfx_tiled.cuh", "sfx_corr3.cuh"],
-        "sha256_16": "4add95b5e93d9bd4",
+        "sha256_16": "3ba10fa2bf2a58fa",
         "capture": "profiles/corr2_tiled_hr3d192_f32.md (192^3 with the 256^3 z-chunk of 37 "
                    "planes, one launch), scaled by the cell count",
     },
@@ -117,6 +117,8 @@ def parse():
     ap.add_argument("--fast-resid", type=int, default=1,
                     help="FP32: Newton iterations per solve with FP32 residuals "
                          "(SFX_TUNE_F32_FAST_RESID; 0 = pair residuals only)")
+    ap.add_argument("--batch-fast-resid", type=int, default=2,
+                    help="batched workload: FP32 residual passes per instance and step")
     ap.add_argument("--incr-resid", type=int, default=1, choices=[0, 1],
                     help="FP32 3D tiled: incremental FP32 residuals after a small pair "
                          "residual (SFX_TUNE_F32_INCR_RESID)")
@@ -856,6 +858,7 @@ def vortex_run(a, dev, steps, prec, warmup=3, rebuild_every=1):
     ctx = sfx.Context.for_grid(g, prec)
     if f32:   # the phase field is rebuilt every step: FP32 redistancing (fused 2D kernel)
         ctx.sfx_set_tuning(sfx._lib.SFX_TUNE_F32_REDIST, 1)
+        ctx.sfx_set_tuning(sfx._lib.SFX_TUNE_F32_SOR, a.sor)
     u0h = W.single_vortex_faces(512, g.h, 0.0, T)
     umax0 = max(float(np.abs(x).max()) for x in u0h)
     u0 = [torch.from_numpy(x).to(dev, vt) for x in u0h]
@@ -1068,7 +1071,8 @@ def run_gpu_batch(a, rank, world, local_rank, steps=None, summary=False):
     ncell = sum(nr * nz for nr, nz in sizes)
     B = sfx.Batch(inst)
     B.sfx_batch_reuse_phi(True)        # the interfaces are static
-    B.sfx_batch_set_tuning(sfx._lib.SFX_TUNE_F32_FAST_RESID, a.fast_resid)
+    B.sfx_batch_set_tuning(sfx._lib.SFX_TUNE_F32_FAST_RESID, a.batch_fast_resid)
+    B.sfx_batch_set_tuning(sfx._lib.SFX_TUNE_F32_SOR, a.sor)
     ones = torch.ones(ncell, dtype=torch.float64, device=dev)
     f = sfx.sfx_df_pack(torch.zeros_like(ones))
     F = sfx.sfx_df_pack(ones)
@@ -1112,7 +1116,7 @@ def run_gpu_batch(a, rank, world, local_rank, steps=None, summary=False):
     iters_mean = float(np.mean(np.array(rp) / steps))
     conv = all(st["converged"])
     sched = {"block": block, "sweeps": sweeps, "iteration_budget": budget,
-             "fp32_residual_passes": a.fast_resid}
+             "fp32_residual_passes": a.batch_fast_resid, "sor": a.sor}
     # init, advect, copy (phi static: no fold or drifts); then, as long as
     # an instance is active, per iteration the residual, the flags, the
     # 2 sweeps - 1 colour sweeps and the loop test; totals and final

@@ -376,20 +376,21 @@ typedef enum {
                                below a tenth of the tolerance); 0 = a pair
                                pass at every iteration after the FP32
                                ones. */
-  SFX_TUNE_F32_SOR = 11,    /* SFX_F32 Newton solver, 3D, relaxation
-                               without multigrid: 1 (default) = every red
-                               update after the first is over-relaxed,
+  SFX_TUNE_F32_SOR = 11,    /* SFX_F32 Newton solver, relaxation without
+                               multigrid (also a batch's, through
+                               sfx_batch_set_tuning): 1 (default) = every
+                               red update after the first is over-relaxed,
                                e <- e + omega (e_GS - e), per field with
                                omega = 2/(2 - rho^2), rho = s/(1 + s),
-                               s = dt (6 D/h^2 + 2 sqrt(3) D/(eps h)) (a
-                               row-sum bound on the Jacobi radius with the
-                               drift bounded by D/eps per face; the
-                               minimax factor of black-then-red sweeps is
-                               rho^2/(2 - rho^2) per sweep instead of
-                               rho^2); 1001 .. 1999 = omega of F set to
-                               value/1000 (f as for 1); 0 = Gauss-Seidel.
-                               The converged state is the same fixed
-                               point. */
+                               s = dt (2 d D/h^2 + 2 sqrt(d) D/(eps h)) on
+                               a d-dimensional grid (a row-sum bound on the
+                               Jacobi radius with the drift bounded by
+                               D/eps per face; the minimax factor of
+                               black-then-red sweeps is rho^2/(2 - rho^2)
+                               per sweep instead of rho^2); 1001 .. 1999 =
+                               omega of F set to value/1000 (f as for 1);
+                               0 = Gauss-Seidel.  The converged state is
+                               the same fixed point. */
   SFX_TUNE_ADVECT_STAGED = 9, /* SFX_F32, 3D: 1 (default) = the BCG step of
                                f and F from z-planes staged in shared
                                memory (values rounded once, neighbours past
@@ -512,11 +513,12 @@ sfx_status sfx_batch_layout(const sfx_batch* b, size_t* n_cells, size_t* n_rface
    256, 3, 8.  An instance that has not converged within the budget keeps
    its last iterate and is reported by sfx_batch_stats. */
 sfx_status sfx_batch_set_schedule(sfx_batch* b, int block, int sweeps, int max_iters);
-/* Solver tuning of a batch, keys as sfx_set_tuning: only
-   SFX_TUNE_F32_FAST_RESID (0 .. 16, default 2) is taken; each instance
-   counts its own FP32 residual passes and switches to pair residuals on
-   its own (the same rule as the single-grid solve).  SFX_ERR_ARG for
-   another key or a value out of range. */
+/* Solver tuning of a batch, keys and values as sfx_set_tuning:
+   SFX_TUNE_F32_FAST_RESID (0 .. 16, default 2; each instance counts its
+   own FP32 residual passes and switches to pair residuals on its own, the
+   rule of the single-grid solve) and SFX_TUNE_F32_SOR (default 1; omega
+   per instance from its parameters, as a single-grid context computes it).
+   SFX_ERR_ARG for another key or a value out of range. */
 sfx_status sfx_batch_set_tuning(sfx_batch* b, int key, int value);
 /* One step of every instance.  phi: phase field (double, packed cells);
    ur, uz: face velocities (float, packed radial / axial faces), both NULL

@@ -357,6 +357,7 @@ struct sfx_batch {
   // last schedule
   int sweeps = 3, max_it = 8;
   int fast = 2;                   // FP32 residual passes at most per instance and step
+  int sor = 1;                    // over-relaxed red updates (as SFX_TUNE_F32_SOR)
   std::vector<int> h_iters;
 };
 
@@ -495,6 +496,15 @@ sfx_status ensure_graph(sfx_batch* b, const void* phi, const void* ur, const voi
   return SFX_OK;
 }
 
+// The over-relaxation of an instance's red updates, as the single-grid
+// solve sets it for the same parameters (sor: SFX_TUNE_F32_SOR).
+void set_omega(BInst& B, const sfx_batch_instance& q, int sor) {
+  B.p.om_f = B.p.om_F = 1.0f;
+  if (sor == 0) return;
+  B.p.om_f = sor_omega(q.params.Df, q.dt, q.h, q.params.eps, 2);
+  B.p.om_F = sor > 1000 ? (float)(sor * 1e-3) : sor_omega(q.params.DF, q.dt, q.h, q.params.eps, 2);
+}
+
 bool inst_ok(const sfx_batch_instance& q) {
   return q.nr >= 1 && q.nz >= 1 && q.h > 0.0 && q.dt > 0.0 && q.params.eps > 0.0 &&
          q.params.gamma_inf > 0.0 && q.params.ka >= 0.0 && q.params.kd >= 0.0 &&
@@ -528,6 +538,7 @@ sfx_status sfx_batch_create_geom(const sfx_batch_instance* inst, int n, int geom
                (float)(1.0 / q.dt), (float)q.params.ka, (float)q.params.kd,
                (float)q.params.gamma_inf, (float)(1.0 / q.params.eps), (float)q.params.eta,
                q.params.literal_upwind};
+    set_omega(B, q, 1);
     B.dt = (float)q.dt;
     B.bc_f = (float)q.params.bc_f;
     B.bc_F = (float)q.params.bc_F;
@@ -625,6 +636,12 @@ sfx_status sfx_batch_set_tuning(sfx_batch* b, int key, int value) {
   if (!b) return SFX_ERR_ARG;
   if (key == SFX_TUNE_F32_FAST_RESID && value >= 0 && value <= 16) {
     b->fast = value;
+    return SFX_OK;
+  }
+  if (key == SFX_TUNE_F32_SOR && (value == 0 || value == 1 || (value > 1000 && value < 2000))) {
+    b->sor = value;
+    for (int i = 0; i < b->n; ++i) set_omega(b->hI[i], b->hinst[i], value);
+    SFX_CUDA(cudaMemcpy(b->dI, b->hI.data(), b->n * sizeof(BInst), cudaMemcpyHostToDevice));
     return SFX_OK;
   }
   return SFX_ERR_ARG;

@@ -8,7 +8,7 @@ struct Nw32 {
   Level L;
   float invh, Dfh, DFh, inv_dt, ka, kd, ginf, inv_eps, eta;
   int literal;
-  // over-relaxation of the red updates after the first (3D relaxation
+  // over-relaxation of the red updates after the first (relaxation
   // sweeps): e <- e + omega (e_GS - e) per field; 1 = Gauss-Seidel
   float om_f = 1.0f, om_F = 1.0f;
 };

@@ -1632,21 +1632,11 @@ sfx_status step_f32(sfx_ctx* c, const sfx_params* pr, const double* phi_in, cons
       if (mgl >= 2) {
         st = mg32_prepare(c, mgl, s);
         if (st != SFX_OK) return st;
-      } else if (L.geom == SFX_CART3D && c->f32.sor != 0) {
-        // over-relaxed red updates, omega from a bound on each field's
-        // Jacobi radius: a cell's neighbour weights sum to at most
-        // dt (6 D/h^2 + sum of |B|/h over its six faces) against a diagonal
-        // of 1 + the same sum (the exchange terms only add to it), and the
-        // drift of a face is at most D |n_d|/eps (Sec. 2.3, |n| <= 1), so
-        // the six faces add at most 2 sqrt(3) D/eps
-        auto omega = [&](double D) {
-          const double sd = dt * (6.0 * D / (L.h * L.h) + 2.0 * std::sqrt(3.0) * D /
-                                                              (pr->eps * L.h));
-          const double rho = sd / (1.0 + sd);
-          return (float)(2.0 / (2.0 - rho * rho));
-        };
-        pw.om_f = omega(pr->Df);
-        pw.om_F = c->f32.sor > 1000 ? (float)(c->f32.sor * 1e-3) : omega(pr->DF);
+      } else if (c->f32.sor != 0) {
+        // over-relaxed red updates (relaxation without multigrid)
+        pw.om_f = sor_omega(pr->Df, dt, L.h, pr->eps, L.ndim());
+        pw.om_F = c->f32.sor > 1000 ? (float)(c->f32.sor * 1e-3)
+                                    : sor_omega(pr->DF, dt, L.h, pr->eps, L.ndim());
       }
       const Mg32Coef kc{(float)pr->Df, (float)pr->DF, pf.inv_dt, pf.kd, pr->literal_upwind};
       st = solve_newton32(c, pw, phi, Bf, BF, fc, fo, Fc, Fo, fs, Fs, o, predict, from_star, mgl,

@@ -717,7 +717,7 @@ struct Corr2In {
   float4 q4;
   ix c, own, oth;
   int i;
-  bool red;   // a red update after the first (over-relaxed in 3D)
+  bool red;   // a red update after the first (over-relaxed)
 };
 
 template <int G>
@@ -800,6 +800,7 @@ __device__ __forceinline__ void corr2_apply(const Nw32& p, const Corr2In& in,
     const float flF = flux_lin<G>(L, p.invh, p.DFh, p.literal, in.i, eFc, in.enF, in.has, in.BF,
                                   dgF);
     ne = corr2_block(p, in.q4, efc, eFc, flf, flF, dgf, dgF);
+    if (in.red) ne = relax_red(p, ne, in.ec);
   }
   const float nf = ne.x, nF = ne.y;
   e2[in.own] = make_float2(nf, nF);

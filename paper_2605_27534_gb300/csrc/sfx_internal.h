@@ -3,6 +3,7 @@
 #pragma once
 
 #include <cuda_fp16.h>
+#include <cmath>
 #include <cuda_runtime.h>
 
 #include <string>
@@ -23,6 +24,22 @@ constexpr int kTotalsThreads = 256;
 // FP32 until both relative residuals are below this, or for a set number
 // of iterations, then in pair arithmetic.
 constexpr float kFastResidSwitch = 1e-3f;
+
+// Over-relaxation factor of the red updates of the FP32 Newton correction
+// (relaxation without multigrid) for a field of diffusivity D on a grid of
+// nd dimensions: black-then-red sweeps multiply a mode of Jacobi
+// eigenvalue mu by 1 - omega (1 - mu^2) per sweep, whose largest value over
+// mu^2 in [0, rho^2] is smallest at omega = 2/(2 - rho^2).  rho is bounded
+// by a cell's neighbour weights over its diagonal, s/(1 + s) with
+// s = dt (2 nd D/h^2 + sum over the faces of |B|/h), and the drift of a
+// face is at most D |n_d|/eps (Sec. 2.3, |n| <= 1): the faces add at most
+// 2 sqrt(nd) D/eps.  Single-grid and batched solves take it from here, so
+// that they agree bit for bit.
+inline float sor_omega(double D, double dt, double h, double eps, int nd) {
+  const double sd = dt * (2.0 * nd * D / (h * h) + 2.0 * std::sqrt((double)nd) * D / (eps * h));
+  const double rho = sd / (1.0 + sd);
+  return (float)(2.0 / (2.0 - rho * rho));
+}
 
 // Device arrays of one multigrid level.  Level 0 (the fine grid) works on
 // the caller's field; its coefficient arrays live here too.
@@ -86,7 +103,7 @@ struct F32Scratch {
   int fast_resid = 2;               // FP32 residual passes at most per Newton solve
   bool adv_staged = true;           // 3D advection from shared-memory planes
   bool incr_resid = true;           // incremental FP32 residuals after a pair pass (tiled path)
-  int sor = 1;                      // 3D relaxation: 0 Gauss-Seidel, 1 over-relaxed red
+  int sor = 1;                      // relaxation: 0 Gauss-Seidel, 1 over-relaxed red
                                     // updates (omega from the diffusion numbers),
                                     // 1001 .. 1999 omega_F = sor / 1000
   bool predict = true;              // start Newton from x* + last increment
