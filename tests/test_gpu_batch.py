@@ -197,6 +197,32 @@ def test_batch_fp32_residuals_reach_the_same_fixed_point(sfx):
         assert np.all(m <= k + 1), (k, m)
 
 
+def test_batch_over_relaxation_reaches_the_same_fixed_point(sfx):
+    """Over-relaxed red updates (omega per instance from its parameters)
+    end on the Gauss-Seidel batch's fixed point: every instance converges,
+    the states match far below the FP32 tolerance, and the batch needs no
+    more iterations in total."""
+    import torch
+    inst = _instances(seed=11)
+    outs, its = [], []
+    for sor in (0, 1):
+        B = _Batch(sfx, inst)
+        B.b.sfx_batch_set_schedule(256, 2, 60)
+        B.b.sfx_batch_set_tuning(sfx._lib.SFX_TUNE_F32_SOR, sor)
+        n = 0
+        for _ in range(3):
+            B.step(1e-10)
+            st = B.b.sfx_batch_stats()
+            assert all(st["converged"])
+            n += sum(st["iters"])
+        torch.cuda.synchronize()
+        its.append(n)
+        outs.append((host(sfx.sfx_df_unpack(B.f)), host(sfx.sfx_df_unpack(B.F))))
+    for a, b in zip(outs[0], outs[1]):
+        assert np.abs(a - b).max() / np.abs(a).max() < 1e-8
+    assert its[1] <= its[0], its
+
+
 def test_graph_cache_follows_pointers(sfx):
     """A step on other buffers recaptures the graph; results are bitwise
     those of stepping one buffer twice."""
@@ -258,6 +284,8 @@ def test_batch_rejects_bad_arguments(sfx):
         B.b.sfx_batch_set_tuning(sfx._lib.SFX_TUNE_F32_FAST_RESID, 17)
     with pytest.raises(sfx.SfxError):
         B.b.sfx_batch_set_tuning(sfx._lib.SFX_TUNE_TILED_SWEEP, 1)
+    with pytest.raises(sfx.SfxError):
+        B.b.sfx_batch_set_tuning(sfx._lib.SFX_TUNE_F32_SOR, 2000)
     with pytest.raises(sfx.SfxError):
         B.b.sfx_batch_step(B.phi, B.f, B.F, 1e-10, ur=B.ur, uz=None)
     with pytest.raises(sfx.SfxError):
