@@ -203,14 +203,39 @@ def algorithmic_bytes(kind, grid, wbytes, sweeps=3, tiled=False):
         # arrays (4 B each), write both corrections (8 B); the staged rings
         # (halo) are re-reads, not counted
         return (4.0 + 16.0 + 4.0 * d + 8.0) * N
-    if kind in ("residual", "residual_fp32", "residual_incr") and wbytes == 4:
+    if kind in ("residual", "residual_fp32") and wbytes == 4:
         # k_resid2_32: f, F, f*, F* (pairs), phi, 2 d float faces; writes the
         # residuals and exchange Jacobian (float4) and the red half of both
         # corrections
         return (16.0 + 16.0 + 4.0 + 8.0 * d + 16.0 + 4.0) * N
+    if kind == "residual_incr" and wbytes == 4:
+        # k_resid32_incr: the last correction (both colours, 8 B), phi, 2 d
+        # float faces, the float4 read and written, the red half of both
+        # corrections; neither the state nor x*
+        return (8.0 + 4.0 + 8.0 * d + 32.0 + 4.0) * N
     if kind == "advect":
         return 16.0 * N + wbytes * d * N
     return None
+
+
+# FP32 operations (each add, multiply or fused multiply-add counted once) of
+# the App. C pair residual at an interior 3D cell, counted from the
+# formulation: per field six faces of 22 (the neighbour into the diffusion
+# sum 8, its face weight 1, the upwind drift product 3 and its accumulation
+# 8, the diagonal weight 2) and 32 for the centre term and the scalings;
+# then 44 for the exchange, 70 for both residuals, 7 for u, v and the
+# residuals' rounding, 7.5 for the red half-sweep (half the cells) and 13
+# for the norms.
+PAIR_RESID_OPS_3D = 2 * (6 * 22 + 32) + 44 + 70 + 7 + 7.5 + 13
+
+
+def alu_peak_tops(dev, clocks):
+    """FP32 operations per second of the GPU at the sampled maximum SM clock:
+    SMs x 128 FP32 lanes x clock (an FMA one operation), in T/s."""
+    import torch
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    mhz = (clocks or {}).get("sm_max_mhz") or 2070.0
+    return sms * 128 * mhz * 1e6 / 1e12, sms, mhz
 
 
 def method_bytes(kind, grid, s):
@@ -589,6 +614,23 @@ def run_gpu(a, case, rank, world, local_rank):
             roof["design_bytes_per_launch"] = ab
             roof["design_bytes_achieved"] = ab / avg_s / 1e9
             roof["design_bytes_frac"] = ab / avg_s / 1e9 / peaks["hbm_gbs"]
+        if kind == "residual" and prec == sfx.SFX_F32 and g.ndim == 3:
+            # the pair residual is bound by its arithmetic (ncu: 73 % issue,
+            # 36 % of DRAM): its roofline is the FP32 pipe, its HBM fraction
+            # kept beside it
+            pk, sms, mhz = alu_peak_tops(dev, clocks)
+            ops = PAIR_RESID_OPS_3D * g.ncell
+            hbm = {k: roof[k] for k in ("achieved", "peak", "unit", "frac")}
+            roof.update({"bound": "alu", "achieved": ops / avg_s / 1e12, "peak": pk,
+                         "unit": "TFLOP/s", "frac": ops / avg_s / 1e12 / pk,
+                         "algorithmic_ops_per_launch": ops,
+                         "algorithmic_ops_note": "%.1f FP32 operations per cell of the pair "
+                                                 "residual's formulation (an FMA one "
+                                                 "operation, as in the peak)"
+                                                 % PAIR_RESID_OPS_3D,
+                         "peak_source": "%d SMs x 128 FP32 lanes x %.0f MHz (sampled maximum "
+                                        "SM clock)" % (sms, mhz),
+                         "hbm": hbm})
     launches = int(sum(v[0] for v in prof.values()))
     breakdown = {}
     step_method, step_design = 0.0, 0.0

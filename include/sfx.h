@@ -373,7 +373,10 @@ typedef enum {
                                correction just added (linear terms and a
                                product of the correction, rounded to ~1e-6
                                of the pair residual, so the chain stays
-                               below a tenth of the tolerance); 0 = a pair
+                               below a tenth of the tolerance; the relative
+                               test keeps the scales |b| of the pair pass,
+                               since the chain reads neither the state nor
+                               x*); 0 = a pair
                                pass at every iteration after the FP32
                                ones. */
   SFX_TUNE_F32_SOR = 11,    /* SFX_F32 Newton solver, relaxation without

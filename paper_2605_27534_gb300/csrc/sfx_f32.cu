@@ -357,8 +357,6 @@ template <int G>
 __global__ void __launch_bounds__(256, 4)
 k_resid32_incr(Nw32 p, const float* __restrict__ phi, const float2* __restrict__ B2x,
                const float2* __restrict__ B2y, const float2* __restrict__ B2z,
-               const float2* __restrict__ fin, const float2* __restrict__ Fin,
-               const float2* __restrict__ fst, const float2* __restrict__ Fst,
                const float2* __restrict__ E, float4* __restrict__ rc, unsigned int* norms,
                float2* __restrict__ e2, const int* __restrict__ done,
                const int* __restrict__ mode) {
@@ -371,8 +369,7 @@ k_resid32_incr(Nw32 p, const float* __restrict__ phi, const float2* __restrict__
   for (ix r = blockIdx.y; r < rows; r += gridDim.y) {
     const int j = (int)(r % (ix)L.ny), k = (int)(r / (ix)L.ny);
     if (i < L.nx)
-      resid32_incr_cell<G>(p, i, j, k, r * (ix)L.nx + (ix)i, phi, B2, fin, Fin, fst, Fst, E, rc,
-                           m, e2);
+      resid32_incr_cell<G>(p, i, j, k, r * (ix)L.nx + (ix)i, phi, B2, E, rc, m, e2);
   }
   if (norms) resid_norms(m, norms);
 }
@@ -1252,12 +1249,18 @@ sfx_status solve_dc32(sfx_ctx* c, const Nl32& pf, const Nl32& pF, const float* p
 constexpr unsigned int kTimeoutBits = 0xffffffffu;
 constexpr float kFastSwitch = kFastResidSwitch;
 constexpr float kIncrFactor = 1e5f;
-__global__ void k_flag32(unsigned int* __restrict__ nrm, float tol, int it, int fast_max,
-                         int incr_ok, int* __restrict__ flag) {
+__global__ void k_flag32(unsigned int* __restrict__ nrm, const unsigned int* __restrict__ prev,
+                         float tol, int it, int fast_max, int incr_ok, int* __restrict__ flag) {
   if (threadIdx.x != 0 || flag[0]) return;
   if (flag[3]) {
     nrm[1] = nrm[3] = kTimeoutBits;
     return;
+  }
+  // an incremental pass reads neither the state nor x*: its scales are
+  // those of the iteration before, back to the pair pass the chain began at
+  if (flag[4] == 2) {
+    nrm[1] = prev[1];
+    nrm[3] = prev[3];
   }
   const float rf = __uint_as_float(nrm[0]), bf = __uint_as_float(nrm[1]);
   const float rF = __uint_as_float(nrm[2]), bF = __uint_as_float(nrm[3]);
@@ -1432,7 +1435,7 @@ sfx_status solve_newton32(sfx_ctx* c, const Nw32& p, const float* phi, float* co
     pair_pass(fsrc, Fsrc, nbuf, e2t, flag);
     if (incr_ok && it > 1)
       SFX_KERNEL(c, K_RESID_INCR, nk.incr, rg.grid, rg.block, s, p, phi, B2[0], B2[1], B2[2],
-                 fsrc, Fsrc, fs, Fs, ebuf[efin], c->f32.rc, nbuf, e2t, flag, flag + 4);
+                 ebuf[efin], c->f32.rc, nbuf, e2t, flag, flag + 4);
     if (it == 1 && predicted) {
       // keep the predicted start only if its residual is already small;
       // otherwise restart from x* (both launches return at once when kept)
@@ -1444,7 +1447,8 @@ sfx_status solve_newton32(sfx_ctx* c, const Nw32& p, const float* phi, float* co
                  fc, Fc, fs, Fs, c->f32.rc, nbuf, e2t, ok, flag + 4);
       pair_pass(fc, Fc, nbuf, e2t, ok);
     }
-    SFX_KERNEL(c, K_OTHER, k_flag32, 1, 32, s, nbuf, tolf, it, fast_max, incr_ok, flag);
+    SFX_KERNEL(c, K_OTHER, k_flag32, 1, 32, s, nbuf, dn + 8 * ((it - 1) & 1), tolf, it, fast_max,
+               incr_ok, flag);
     SFX_CUDA(cudaMemcpyAsync(hn + 8 * (it & 1), nbuf, 8 * sizeof(unsigned int),
                              cudaMemcpyDeviceToHost, s));
     SFX_CUDA(cudaEventRecord(c->f32.ev[it & 1], s));

@@ -630,21 +630,20 @@ __device__ __forceinline__ void resid32_cell(const Nw32& p, int i, int j, int k,
 // e just added to it (E, both colours, colour-packed), in FP32: the
 // App. C residual changes by
 //   r_f: -e_f/dt + flux_f(e_f) + dq,   r_F: -e_F/dt + flux_F(e_F) - dq,
-//   dq = c1 (e_F (f_inf - f) - F e_f - e_F e_f) - r_d e_f   (f, F before
-//      the update) = c1 (e_F (f_inf - f' + e_f) - F' e_f) - r_d e_f with
-//      f' = f + e_f, F' = F + e_F,
-// linear terms and a product of the correction, all of the size of the
-// old residual, so FP32 rounding stays ~1e-7 of it: after a pair residual
-// pass this keeps the pair pass's accuracy.  fin, Fin hold x + e.  The
-// other outputs are those of resid2_cell.
+//   dq = c1 (e_F (f_inf - f) - F e_f - e_F e_f) - r_d e_f
+//      = e_F v - u e_f - c1 e_F e_f - r_d e_f
+// with u = c1 F and v = c1 (f_inf - f) of x (rc's third and fourth
+// entries), which become u + c1 e_F and v - c1 e_f for x + e: linear terms
+// and a product of the correction, all of the size of the old residual,
+// so FP32 rounding stays ~1e-7 of it, and after a pair residual pass this
+// keeps the pair pass's accuracy.  Neither the state nor x* is read: the
+// norms' scales m[1], m[3] are left at zero and the convergence test takes
+// those of the pass the chain started from.  The other outputs are those
+// of resid2_cell.
 template <int G>
 __device__ __forceinline__ void resid32_incr_cell(const Nw32& p, int i, int j, int k, ix c,
                                                   const float* __restrict__ phi,
                                                   const float2* const* B2,
-                                                  const float2* __restrict__ fin,
-                                                  const float2* __restrict__ Fin,
-                                                  const float2* __restrict__ fst,
-                                                  const float2* __restrict__ Fst,
                                                   const float2* __restrict__ E,
                                                   float4* __restrict__ rc, float* m,
                                                   float2* __restrict__ e2) {
@@ -677,15 +676,13 @@ __device__ __forceinline__ void resid32_incr_cell(const Nw32& p, int i, int j, i
   const float flF = flux_lin<G>(L, p.invh, p.DFh, p.literal, i, ec.y, eF, has, BF, dF_);
   const PhiPair ph = unfold(phi[c]);
   const float c1 = __fdividef(p.ka, ph.p + p.eta);
-  const float finf = __fmul_rn(__fmul_rn(__fmul_rn(p.ginf, ph.p), ph.q), p.inv_eps);
-  const float fc = fin[c].x, Fc = Fin[c].x;   // x + e
-  // dq from the updated values: c1 (e_F (f_inf - fc + e_f) - Fc e_f) - r_d e_f
-  const float dq = __fmaf_rn(
-      c1, __fmaf_rn(ec.y, __fadd_rn(__fsub_rn(finf, fc), ec.x), -__fmul_rn(Fc, ec.x)),
-      -__fmul_rn(p.kd, ec.x));
+  // dq = e_F v - u e_f - c1 e_F e_f - r_d e_f with x's u, v
+  const float ce = __fmul_rn(c1, ec.x);
+  const float dq = __fmaf_rn(ec.y, __fsub_rn(r0.w, ce),
+                             -__fmul_rn(__fadd_rn(r0.z, p.kd), ec.x));
   const float rf = __fadd_rn(__fadd_rn(__fmaf_rn(-ec.x, p.inv_dt, r0.x), flf), dq);
   const float rF = __fsub_rn(__fadd_rn(__fmaf_rn(-ec.y, p.inv_dt, r0.y), flF), dq);
-  const float u = __fmul_rn(c1, Fc), v = __fmul_rn(c1, __fsub_rn(finf, fc));
+  const float u = __fmaf_rn(c1, ec.y, r0.z), v = __fsub_rn(r0.w, ce);
   rc[own] = make_float4(rf, rF, u, v);
   if (col == 0) {
     const Jac2 J = jac2(p, u, v);
@@ -694,11 +691,8 @@ __device__ __forceinline__ void resid32_incr_cell(const Nw32& p, int i, int j, i
     e2[own] = make_float2(__fmul_rn(__fmaf_rn(e, rf, __fmul_rn(J.fF, rF)), inv),
                           __fmul_rn(__fmaf_rn(J.Ff, rf, __fmul_rn(a, rF)), inv));
   }
-  const float fs = fst[c].x, Fs = Fst[c].x;
   m[0] = fmaxf(m[0], fabsf(rf));
-  m[1] = fmaxf(m[1], fabsf(__fmaf_rn(fs, p.inv_dt, __fmul_rn(u, finf))));
   m[2] = fmaxf(m[2], fabsf(rF));
-  m[3] = fmaxf(m[3], fabsf(__fmaf_rn(Fs, p.inv_dt, __fmul_rn(p.kd, fc))));
   if (!(fabsf(rf) <= 3.0e38f) || !(fabsf(rF) <= 3.0e38f)) m[0] = m[2] = __int_as_float(0x7f800000);
 }
 
