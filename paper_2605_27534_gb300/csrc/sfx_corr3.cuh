@@ -26,9 +26,10 @@ __device__ __forceinline__ Jac2 jac2(const Nw32& p, float u, float v) {
               __fadd_rn(p.inv_dt, v)};
 }
 
-// The 3D sweeps' flux of one field's correction in neighbour-coefficient
+// The 3D sweeps' flux of both fields' corrections in neighbour-coefficient
 // form (the same linear operator as flux_lin, fewer instructions: no
-// selects).  A face with drift B between cells L and R carries
+// selects), one lane per field (x f, y F).  A face with drift B between
+// cells L and R carries
 //   G = D (e_R - e_L)/h + B e_up = (alpha e_R - beta e_L)/h,
 //   alpha = D + max(B, 0), beta = D - min(B, 0)      (upwind on -B),
 //   alpha = D + min(B, 0), beta = D - max(B, 0)      (literal: on +B),
@@ -39,15 +40,15 @@ __device__ __forceinline__ Jac2 jac2(const Nw32& p, float u, float v) {
 // over open faces (w = 1) of the cell's terms.  A closed face's neighbour
 // value is zero, so it adds nothing to nbs.  hs = +1/2 (upwind on -B) or
 // -1/2 (literal).
-__device__ __forceinline__ void nb3(float Doh, float hs, const float* en, const float* w,
-                                    const float* B, float& nbs, float& dg) {
-  float s = 0.0f, d = 0.0f;
+__device__ __forceinline__ void nb3(float2 Doh, float hs, const float2* en, const float* w,
+                                    const float2* B, float2& nbs, float2& dg) {
+  float2 s = v_bc(0.0f), d = v_bc(0.0f);
 #pragma unroll
   for (int q = 0; q < 6; ++q) {
-    const float t = __fmaf_rn(hs, fabsf(B[q]), Doh);
-    const float al = __fmaf_rn(0.5f, B[q], t), be = __fmaf_rn(-0.5f, B[q], t);
-    s = __fmaf_rn((q & 1) ? al : be, en[q], s);
-    d = __fmaf_rn(w[q], (q & 1) ? be : al, d);
+    const float2 t = v_fma(v_bc(hs), make_float2(fabsf(B[q].x), fabsf(B[q].y)), Doh);
+    const float2 al = v_fma(v_bc(0.5f), B[q], t), be = v_fma(v_bc(-0.5f), B[q], t);
+    s = v_fma((q & 1) ? al : be, en[q], s);
+    d = v_fma(v_bc(w[q]), (q & 1) ? be : al, d);
   }
   nbs = s;
   dg = d;
@@ -56,15 +57,15 @@ __device__ __forceinline__ void nb3(float Doh, float hs, const float* en, const 
 // The block Gauss-Seidel update of one 3D cell in the neighbour-coefficient
 // form: the new correction solves the 2x2 system M e = r + (neighbour sums)
 // directly (M = the exchange Jacobian plus the flux diagonals), so the
-// cell's own old value does not enter.  nbf, nbF, dgf, dgF already over h.
-__device__ __forceinline__ float2 corr2_block_nb(const Nw32& p, float4 q4, float nbf, float nbF,
-                                                 float dgf, float dgF) {
+// cell's own old value does not enter.  nb, dg (f, F) already over h.
+__device__ __forceinline__ float2 corr2_block_nb(const Nw32& p, float4 q4, float2 nb, float2 dg) {
   const Jac2 J = jac2(p, q4.z, q4.w);
-  const float a = __fadd_rn(J.ff, dgf), bb = J.fF, d = J.Ff, e = __fadd_rn(J.FF, dgF);
-  const float sf = __fadd_rn(q4.x, nbf), sF = __fadd_rn(q4.y, nbF);
+  const float2 ae = v_add(make_float2(J.ff, J.FF), dg);   // (a, e)
+  const float a = ae.x, bb = J.fF, d = J.Ff, e = ae.y;
+  const float2 sv = v_add(make_float2(q4.x, q4.y), nb);   // (sf, sF)
   const float inv = __fdividef(1.0f, __fmaf_rn(a, e, -__fmul_rn(bb, d)));
-  return make_float2(__fmul_rn(__fmaf_rn(e, sf, __fmul_rn(bb, sF)), inv),
-                     __fmul_rn(__fmaf_rn(d, sf, __fmul_rn(a, sF)), inv));
+  return v_mul(v_fma(make_float2(e, d), v_bc(sv.x), v_mul(make_float2(bb, a), v_bc(sv.y))),
+               v_bc(inv));
 }
 
 // A red update over-relaxed from the cell's old value.  With black then
@@ -79,14 +80,11 @@ __device__ __forceinline__ float2 relax_red(const Nw32& p, float2 gs, float2 old
 
 // One 3D correction cell from its gathered inputs (both sweeps of 3D
 // grids, the colour launch and the tiled one, so they agree bit for bit).
-__device__ __forceinline__ float2 corr3_cell(const Nw32& p, const float* enf, const float* enF,
-                                            const float* w, const float* Bf, const float* BF,
-                                            float4 q4) {
+__device__ __forceinline__ float2 corr3_cell(const Nw32& p, const float2* en, const float* w,
+                                            const float2* B, float4 q4) {
   const float hs = p.literal ? -0.5f : 0.5f;
-  float nbf, nbF, dgf, dgF;
-  nb3(p.Dfh, hs, enf, w, Bf, nbf, dgf);
-  nb3(p.DFh, hs, enF, w, BF, nbF, dgF);
-  return corr2_block_nb(p, q4, __fmul_rn(nbf, p.invh), __fmul_rn(nbF, p.invh),
-                        __fmul_rn(dgf, p.invh), __fmul_rn(dgF, p.invh));
+  float2 nb, dg;
+  nb3(make_float2(p.Dfh, p.DFh), hs, en, w, B, nb, dg);
+  return corr2_block_nb(p, q4, v_mul(nb, v_bc(p.invh)), v_mul(dg, v_bc(p.invh)));
 }
 

@@ -304,7 +304,7 @@ __global__ void k_corr32(Corr32 p, const float* __restrict__ Bx, const float* __
 // Evaluate both residuals (pairs), the 2x2 exchange Jacobian and the
 // norms at every cell of the current state.
 template <int G>
-__global__ void __launch_bounds__(256, 5)
+__global__ void __launch_bounds__(256, 4)
 k_resid2_32(Nw32 p, const float* __restrict__ phi, const float2* __restrict__ B2x,
             const float2* __restrict__ B2y, const float2* __restrict__ B2z,
             const float2* __restrict__ fin,
@@ -439,7 +439,7 @@ k_corr2_32(Nw32 p, const __half2* __restrict__ Hx, const __half2* __restrict__ H
 // at run time: specialised it needs more registers than its occupancy
 // bound allows and spills.
 struct NewtonKernels {
-  decltype(&k_resid2_32<kGeomRuntime>) resid;
+  decltype(&k_resid2_32<SFX_CART3D>) resid;
   decltype(&k_resid32_fast<SFX_CART3D>) fast;
   decltype(&k_resid32_incr<SFX_CART3D>) incr;
   decltype(&k_corr2_32<SFX_CART3D, 1>) corr;
@@ -455,7 +455,7 @@ NewtonKernels newton_kernels(int geom, int kp) {
     case SFX_AXISYM: return newton_kernels_of<SFX_AXISYM>();
     case SFX_PLANAR2D: return newton_kernels_of<SFX_PLANAR2D>();
     default:
-      return NewtonKernels{&k_resid2_32<kGeomRuntime>, &k_resid32_fast<SFX_CART3D>,
+      return NewtonKernels{&k_resid2_32<SFX_CART3D>, &k_resid32_fast<SFX_CART3D>,
                            &k_resid32_incr<SFX_CART3D>,
                            kp == 2 ? &k_corr2_32<SFX_CART3D, 2> : &k_corr2_32<SFX_CART3D, 1>,
                            kp == 2 ? 2 : 1};

@@ -26,6 +26,64 @@ __device__ __forceinline__ void cp_async8(void* dst, const void* src) {
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
 
+// ------------------------------------------------------------ two lanes
+// Both fields at once: lane x for f, lane y for F.  The packed FP32
+// instructions round each lane exactly as the scalar ones do, so every
+// lane computes the bits of the scalar expression it replaces.
+__device__ __forceinline__ float2 v_add(float2 a, float2 b) { return __fadd2_rn(a, b); }
+// a - b as a + b (-1): the product is exact, so the one rounding is a - b's
+__device__ __forceinline__ float2 v_sub(float2 a, float2 b) {
+  return __ffma2_rn(b, make_float2(-1.0f, -1.0f), a);
+}
+__device__ __forceinline__ float2 v_mul(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 v_fma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 v_bc(float a) { return make_float2(a, a); }
+
+// A pair per lane: (hi.x, lo.x) of f, (hi.y, lo.y) of F.
+struct P2 {
+  float2 hi, lo;
+};
+__device__ __forceinline__ P2 p2_of(float2 f, float2 F) {
+  return P2{make_float2(f.x, F.x), make_float2(f.y, F.y)};
+}
+__device__ __forceinline__ float2 p2_f(const P2& a) { return make_float2(a.hi.x, a.lo.x); }
+__device__ __forceinline__ float2 p2_F(const P2& a) { return make_float2(a.hi.y, a.lo.y); }
+
+// acc_add and acc_sub per lane
+__device__ __forceinline__ void v_acc_add(P2& s, const P2& x) {
+  const float2 t = v_add(s.hi, x.hi);
+  const float2 bb = v_sub(t, s.hi);
+  const float2 e = v_add(v_sub(s.hi, v_sub(t, bb)), v_sub(x.hi, bb));
+  s.hi = t;
+  s.lo = v_add(s.lo, v_add(e, x.lo));
+}
+__device__ __forceinline__ void v_acc_sub(P2& s, const P2& x) {
+  // the two-sum of s.hi and -x.hi: -x.hi - bb rounds to -(x.hi + bb)
+  const float2 t = v_sub(s.hi, x.hi);
+  const float2 bb = v_sub(t, s.hi);
+  const float2 e = v_sub(v_sub(s.hi, v_sub(t, bb)), v_add(x.hi, bb));
+  s.hi = t;
+  s.lo = v_add(s.lo, v_sub(e, x.lo));
+}
+// acc_get per lane
+__device__ __forceinline__ P2 v_acc_get(const P2& s) {
+  const float2 t = v_add(s.hi, s.lo);
+  return P2{t, v_sub(s.lo, v_sub(t, s.hi))};
+}
+// lp_mul per lane
+__device__ __forceinline__ P2 v_lp_mul(const P2& a, float2 b) {
+  const float2 p = v_mul(a.hi, b);
+  return P2{p, v_fma(a.lo, b, v_fma(a.hi, b, make_float2(-p.x, -p.y)))};
+}
+// lp_sub per lane
+__device__ __forceinline__ P2 v_lp_sub(const P2& a, const P2& b) {
+  const float2 t = v_sub(a.hi, b.hi);
+  const float2 bb = v_sub(t, a.hi);
+  const float2 e = v_sub(v_sub(a.hi, v_sub(t, bb)), v_add(b.hi, bb));
+  return P2{t, v_add(e, v_sub(a.lo, b.lo))};
+}
+
+
 // ------------------------------------------------------------ drifts
 // Folded float copy of phi: phi where phi <= 1/2, phi - 1 elsewhere.
 __device__ __forceinline__ float fold_phi(double p) {
@@ -227,6 +285,21 @@ __device__ __forceinline__ void faces6f2(const Level& L, const float2* Bx, const
   }
 }
 
+// faces6f2 with each face's (B_f, B_F) kept together (one lane per field).
+__device__ __forceinline__ void faces6v(const Level& L, const float2* Bx, const float2* By,
+                                        const float2* Bz, int i, int j, int k, const bool* has,
+                                        float2* B) {
+  const ix c = cidx32(L, i, j, k);
+  const ix fx = c + (ix)k * (ix)L.ny + (ix)j, fy = c + (ix)k * (ix)L.nx;
+  const float2 z = make_float2(0.0f, 0.0f);
+  B[0] = has[0] ? Bx[fx] : z;
+  B[1] = has[1] ? Bx[fx + 1] : z;
+  B[2] = has[2] ? By[fy] : z;
+  B[3] = has[3] ? By[fy + L.nx] : z;
+  B[4] = has[4] ? Bz[c] : z;
+  B[5] = has[5] ? Bz[c + (ix)L.nx * (ix)L.ny] : z;
+}
+
 // faces6 for both fields at once from the packed (B_f, B_F) half2 faces.
 __device__ __forceinline__ void faces6x2(const Level& L, const __half2* Hx, const __half2* Hy,
                                          const __half2* Hz, int i, int j, int k, const bool* has,
@@ -295,6 +368,56 @@ __device__ __forceinline__ float2 flux_pair(const Level& L, float invh, float Do
   return flux;
 }
 
+// flux_pair of both fields at once (lane x f with Doh.x and drifts B[q].x,
+// lane y F), the same operations per lane: flux_pair's bits.
+template <int G>
+__device__ __forceinline__ P2 flux_pair2(const Level& L, float invh, float2 Doh, int literal,
+                                         int i, const P2& ac, const P2* nb, const bool* has,
+                                         const float2* B, float2& dflux) {
+  const bool axi = geom_of<G>(L) == SFX_AXISYM;
+  P2 D{v_bc(0.0f), v_bc(0.0f)}, T{v_bc(0.0f), v_bc(0.0f)};
+  float W = 0.0f;
+  float2 dg = v_bc(0.0f);
+#pragma unroll
+  for (int q = 0; q < 6; ++q) {
+    if (!has[q]) continue;
+    const bool plus = q & 1;
+    const bool upf = literal ? (B[q].x > 0.0f) : (B[q].x < 0.0f);
+    const bool upF = literal ? (B[q].y > 0.0f) : (B[q].y < 0.0f);
+    float w = 1.0f;
+    const int g = geom_of<G>(L);
+    if (axi) w = q < 2 ? wr_face(g, i + (plus ? 1 : 0)) : (q < 4 ? wz_face(g, i) : 1.0f);
+    v_acc_add(D, axi ? v_lp_mul(nb[q], v_bc(w)) : nb[q]);
+    W = __fadd_rn(W, w);
+    // upwind value per lane: the left cell when up; this cell is left on
+    // plus faces
+    const bool cf = plus == upf, cF = plus == upF;
+    const P2 aup{make_float2(cf ? ac.hi.x : nb[q].hi.x, cF ? ac.hi.y : nb[q].hi.y),
+                 make_float2(cf ? ac.lo.x : nb[q].lo.x, cF ? ac.lo.y : nb[q].lo.y)};
+    P2 u = v_lp_mul(aup, B[q]);
+    if (axi) u = v_lp_mul(u, v_bc(w));
+    if (plus) {
+      v_acc_add(T, u);
+      dg = v_fma(v_bc(w), v_sub(Doh, make_float2(upf ? B[q].x : 0.0f, upF ? B[q].y : 0.0f)), dg);
+    } else {
+      v_acc_sub(T, u);
+      dg = v_fma(v_bc(w), v_add(Doh, make_float2(upf ? 0.0f : B[q].x, upF ? 0.0f : B[q].y)), dg);
+    }
+  }
+  v_acc_sub(D, v_lp_mul(ac, v_bc(W)));
+  v_acc_add(T, v_lp_mul(v_acc_get(D), Doh));
+  P2 flux = v_lp_mul(v_acc_get(T), v_bc(invh));
+  dflux = v_mul(dg, v_bc(invh));
+  if (axi) {
+    const float wc = wz_face(geom_of<G>(L), i);
+    const float2 a = df_div_f(ef_fast_two_sum(flux.hi.x, flux.lo.x), wc);
+    const float2 b = df_div_f(ef_fast_two_sum(flux.hi.y, flux.lo.y), wc);
+    flux = p2_of(a, b);
+    dflux = make_float2(__fdividef(dflux.x, wc), __fdividef(dflux.y, wc));
+  }
+  return flux;
+}
+
 // linear flux of a correction field (FP32) and its diagonal weight
 template <int G>
 __device__ __forceinline__ float flux_lin(const Level& L, float invh, float Doh, int literal,
@@ -322,6 +445,38 @@ __device__ __forceinline__ float flux_lin(const Level& L, float invh, float Doh,
   const float s = invh / wz_face(geom_of<G>(L), i);
   dflux = __fmul_rn(dg, s);
   return __fmul_rn(S, s);
+}
+
+// flux_lin of both fields at once (lane x f with Doh.x, drifts B[q].x and
+// corrections en[q].x; lane y F), the same operations per lane.
+template <int G>
+__device__ __forceinline__ float2 flux_lin2(const Level& L, float invh, float2 Doh, int literal,
+                                            int i, float2 ec, const float2* en, const bool* has,
+                                            const float2* B, float2& dflux) {
+  float2 S = v_bc(0.0f), dg = v_bc(0.0f);
+#pragma unroll
+  for (int q = 0; q < 6; ++q) {
+    if (!has[q]) continue;
+    const bool plus = q & 1;
+    const bool upf = literal ? (B[q].x > 0.0f) : (B[q].x < 0.0f);
+    const bool upF = literal ? (B[q].y > 0.0f) : (B[q].y < 0.0f);
+    float w = 1.0f;
+    const int g = geom_of<G>(L);
+    if (g == SFX_AXISYM) w = q < 2 ? wr_face(g, i + (plus ? 1 : 0)) : (q < 4 ? wz_face(g, i) : 1.0f);
+    const float2 eL = plus ? ec : en[q], eR = plus ? en[q] : ec;
+    const float2 up = make_float2(upf ? eL.x : eR.x, upF ? eL.y : eR.y);
+    const float2 fq = v_fma(Doh, v_sub(eR, eL), v_mul(B[q], up));
+    if (plus) {
+      S = v_fma(v_bc(w), fq, S);
+      dg = v_fma(v_bc(w), v_sub(Doh, make_float2(upf ? B[q].x : 0.0f, upF ? B[q].y : 0.0f)), dg);
+    } else {
+      S = v_fma(v_bc(-w), fq, S);
+      dg = v_fma(v_bc(w), v_add(Doh, make_float2(upf ? 0.0f : B[q].x, upF ? 0.0f : B[q].y)), dg);
+    }
+  }
+  const float s = invh / wz_face(geom_of<G>(L), i);
+  dflux = v_mul(dg, v_bc(s));
+  return v_mul(S, v_bc(s));
 }
 
 __device__ __forceinline__ float mc32(float xm, float x0, float xp) {
@@ -451,8 +606,8 @@ __device__ __forceinline__ void face32v2(const Adv32& A, const float2* __restric
 }
 
 __device__ __forceinline__ void resid2_tail(const Nw32& p, int i, int j, int k, ix c,
-                                            const float* __restrict__ phi, float2 fc, float2 Fc,
-                                            float2 flf, float2 flF, float df_, float dF_,
+                                            const float* __restrict__ phi, const P2& ac,
+                                            const P2& fl, float2 dfl,
                                             const float2* __restrict__ fst,
                                             const float2* __restrict__ Fst,
                                             float4* __restrict__ rc, float* m,
@@ -502,31 +657,34 @@ __device__ __forceinline__ void resid2_cell(const Nw32& p, int i, int j, int k, 
   bool has[6];
   ix nbi[6];
   gather6<G>(L, i, j, k, c, has, nbi);
-  float2 nb[6];
-  const float2 fc = fin[c], Fc = Fin[c];
-  float Bf[6], BF[6], df_, dF_;
-  faces6f2(L, B2[0], B2[1], B2[2], i, j, k, has, Bf, BF);
+  // both fields' pairs, one lane per field
+  P2 nb[6];
+  const P2 ac = p2_of(fin[c], Fin[c]);
+  float2 B[6], dfl;
+  faces6v(L, B2[0], B2[1], B2[2], i, j, k, has, B);
 #pragma unroll
-  for (int q = 0; q < 6; ++q) nb[q] = has[q] ? fin[nbi[q]] : make_float2(0.0f, 0.0f);
-  const float2 flf = flux_pair<G>(L, p.invh, p.Dfh, p.literal, i, fc, nb, has, Bf, df_);
-#pragma unroll
-  for (int q = 0; q < 6; ++q) nb[q] = has[q] ? Fin[nbi[q]] : make_float2(0.0f, 0.0f);
-  const float2 flF = flux_pair<G>(L, p.invh, p.DFh, p.literal, i, Fc, nb, has, BF, dF_);
-  resid2_tail(p, i, j, k, c, phi, fc, Fc, flf, flF, df_, dF_, fst, Fst, rc, m, e2);
+  for (int q = 0; q < 6; ++q) {
+    const float2 z = make_float2(0.0f, 0.0f);
+    nb[q] = p2_of(has[q] ? fin[nbi[q]] : z, has[q] ? Fin[nbi[q]] : z);
+  }
+  const P2 fl = flux_pair2<G>(L, p.invh, make_float2(p.Dfh, p.DFh), p.literal, i, ac, nb, has,
+                              B, dfl);
+  resid2_tail(p, i, j, k, c, phi, ac, fl, dfl, fst, Fst, rc, m, e2);
 }
 
-// The rest of the pair residual of one cell from its pair fluxes flf, flF
-// (already over h) and their diagonal weights df_, dF_: the exchange, both
-// residuals, u and v, the first red half-sweep and the norms (the outputs
-// of resid2_cell).
+// The rest of the pair residual of one cell from the cell's pairs ac and
+// its pair fluxes fl (already over h, lane x f, lane y F) with their
+// diagonal weights dfl: the exchange, both residuals, u and v, the first
+// red half-sweep and the norms (the outputs of resid2_cell).
 __device__ __forceinline__ void resid2_tail(const Nw32& p, int i, int j, int k, ix c,
-                                            const float* __restrict__ phi, float2 fc, float2 Fc,
-                                            float2 flf, float2 flF, float df_, float dF_,
+                                            const float* __restrict__ phi, const P2& ac,
+                                            const P2& fl, float2 dfl,
                                             const float2* __restrict__ fst,
                                             const float2* __restrict__ Fst,
                                             float4* __restrict__ rc, float* m,
                                             float2* __restrict__ e2) {
   const Level& L = p.L;
+  const float2 fc = p2_f(ac), Fc = p2_F(ac);
   // exchange q = c1 F (f_inf - f) - r_d f, one evaluation for both equations
   const PhiPair ph = unfold(phi[c]);
   const float c1 = __fdividef(p.ka, ph.p + p.eta);
@@ -541,14 +699,13 @@ __device__ __forceinline__ void resid2_tail(const Nw32& p, int i, int j, int k, 
   acc_sub(q, des);
   const float2 qq = acc_get(q);
   const float2 fs = fst[c], Fs = Fst[c];
-  Acc Rf{0.0f, 0.0f}, RF{0.0f, 0.0f};
-  acc_add(Rf, lp_mul(lp_sub(fs, fc), p.inv_dt));
-  acc_add(Rf, flf);
-  acc_add(Rf, qq);
-  acc_add(RF, lp_mul(lp_sub(Fs, Fc), p.inv_dt));
-  acc_add(RF, flF);
-  acc_sub(RF, qq);
-  const float rf = __fadd_rn(Rf.hi, Rf.lo), rF = __fadd_rn(RF.hi, RF.lo);
+  // both residuals, one lane each: (x* - x)/dt + flux, then +q (f), -q (F)
+  P2 R{v_bc(0.0f), v_bc(0.0f)};
+  v_acc_add(R, v_lp_mul(v_lp_sub(p2_of(fs, Fs), ac), v_bc(p.inv_dt)));
+  v_acc_add(R, fl);
+  v_acc_add(R, P2{make_float2(qq.x, -qq.x), make_float2(qq.y, -qq.y)});
+  const float2 rr = v_add(R.hi, R.lo);
+  const float rf = rr.x, rF = rr.y;
   const float Fv = __fadd_rn(Fc.x, Fc.y), fv = __fadd_rn(fc.x, fc.y);
   // the linearised exchange: u = c1 F and v = c1 (f_inf - f) fix the 2x2
   // block (Jac2); stored with the residuals as one float4 per cell
@@ -559,7 +716,7 @@ __device__ __forceinline__ void resid2_tail(const Nw32& p, int i, int j, int k, 
   if (e2 && ((i + j + k) & 1) == 0) {
     // [a -b; -d e] [x; y] = [r_f; r_F], diagonals with the flux weights
     const Jac2 J = jac2(p, u, v);
-    const float a = __fadd_rn(J.ff, df_), e = __fadd_rn(J.FF, dF_);
+    const float a = __fadd_rn(J.ff, dfl.x), e = __fadd_rn(J.FF, dfl.y);
     const float inv = __fdividef(1.0f, __fmaf_rn(a, e, -__fmul_rn(J.fF, J.Ff)));
     e2[own] = make_float2(__fmul_rn(__fmaf_rn(e, rf, __fmul_rn(J.fF, rF)), inv),
                           __fmul_rn(__fmaf_rn(J.Ff, rf, __fmul_rn(a, rF)), inv));
@@ -591,16 +748,15 @@ __device__ __forceinline__ void resid32_cell(const Nw32& p, int i, int j, int k,
   bool has[6];
   ix nbi[6];
   gather6<G>(L, i, j, k, c, has, nbi);
-  float Bf[6], BF[6], nf[6], nF[6], df_, dF_;
-  faces6f2(L, B2[0], B2[1], B2[2], i, j, k, has, Bf, BF);
+  float2 B[6], nv[6], dfl;
+  faces6v(L, B2[0], B2[1], B2[2], i, j, k, has, B);
 #pragma unroll
-  for (int q = 0; q < 6; ++q) {
-    nf[q] = has[q] ? fin[nbi[q]].x : 0.0f;
-    nF[q] = has[q] ? Fin[nbi[q]].x : 0.0f;
-  }
+  for (int q = 0; q < 6; ++q)
+    nv[q] = has[q] ? make_float2(fin[nbi[q]].x, Fin[nbi[q]].x) : make_float2(0.0f, 0.0f);
   const float fc = fin[c].x, Fc = Fin[c].x;
-  const float flf = flux_lin<G>(L, p.invh, p.Dfh, p.literal, i, fc, nf, has, Bf, df_);
-  const float flF = flux_lin<G>(L, p.invh, p.DFh, p.literal, i, Fc, nF, has, BF, dF_);
+  const float2 fl = flux_lin2<G>(L, p.invh, make_float2(p.Dfh, p.DFh), p.literal, i,
+                                 make_float2(fc, Fc), nv, has, B, dfl);
+  const float flf = fl.x, flF = fl.y, df_ = dfl.x, dF_ = dfl.y;
   const PhiPair ph = unfold(phi[c]);
   const float c1 = __fdividef(p.ka, ph.p + p.eta);
   const float finf = __fmul_rn(__fmul_rn(__fmul_rn(p.ginf, ph.p), ph.q), p.inv_eps);
@@ -662,18 +818,15 @@ __device__ __forceinline__ void resid32_incr_cell(const Nw32& p, int i, int j, i
   nbi[3] = oth + rb.half;
   nbi[4] = oth - sz;
   nbi[5] = oth + sz;
-  float Bf[6], BF[6], ef[6], eF[6], df_, dF_;
-  faces6f2(L, B2[0], B2[1], B2[2], i, j, k, has, Bf, BF);
+  float2 B[6], ev[6], dfl;
+  faces6v(L, B2[0], B2[1], B2[2], i, j, k, has, B);
 #pragma unroll
-  for (int q = 0; q < 6; ++q) {
-    const float2 v = has[q] ? E[nbi[q]] : make_float2(0.0f, 0.0f);
-    ef[q] = v.x;
-    eF[q] = v.y;
-  }
+  for (int q = 0; q < 6; ++q) ev[q] = has[q] ? E[nbi[q]] : make_float2(0.0f, 0.0f);
   const float2 ec = E[own];
   const float4 r0 = rc[own];
-  const float flf = flux_lin<G>(L, p.invh, p.Dfh, p.literal, i, ec.x, ef, has, Bf, df_);
-  const float flF = flux_lin<G>(L, p.invh, p.DFh, p.literal, i, ec.y, eF, has, BF, dF_);
+  const float2 fl = flux_lin2<G>(L, p.invh, make_float2(p.Dfh, p.DFh), p.literal, i, ec, ev, has,
+                                 B, dfl);
+  const float flf = fl.x, flF = fl.y, df_ = dfl.x, dF_ = dfl.y;
   const PhiPair ph = unfold(phi[c]);
   const float c1 = __fdividef(p.ka, ph.p + p.eta);
   // dq = e_F v - u e_f - c1 e_F e_f - r_d e_f with x's u, v
@@ -781,7 +934,13 @@ __device__ __forceinline__ void corr2_apply(const Nw32& p, const Corr2In& in,
     float w[6];
 #pragma unroll
     for (int q = 0; q < 6; ++q) w[q] = in.has[q] ? 1.0f : 0.0f;
-    ne = corr3_cell(p, in.enf, in.enF, w, in.Bf, in.BF, in.q4);
+    float2 en[6], B[6];
+#pragma unroll
+    for (int q = 0; q < 6; ++q) {
+      en[q] = make_float2(in.enf[q], in.enF[q]);
+      B[q] = make_float2(in.Bf[q], in.BF[q]);
+    }
+    ne = corr3_cell(p, en, w, B, in.q4);
     // the old value is read here, not with the other loads: black launches
     // (the state update among them) never read it, and keeping it live
     // across the cell's arithmetic costs the two-plane kernel its overlap

@@ -161,16 +161,10 @@ __device__ __forceinline__ float2 tiled_cell(const Nw32& p, TileSlot& S0, const 
   hf[4] = S0.f[2][own];
   hf[5] = Sp.f[2][oth];
   const float4 q4 = S0.r[col][ye - 1][pe - 1];
-  float enf[6], enF[6], Bf[6], BF[6];
+  float2 B[6];
 #pragma unroll
-  for (int q = 0; q < 6; ++q) {
-    enf[q] = nb[q].x;
-    enF[q] = nb[q].y;
-    const float2 b = __half22float2(hf[q]);
-    Bf[q] = b.x;
-    BF[q] = b.y;
-  }
-  const float2 ne = corr3_cell(p, enf, enF, w, Bf, BF, q4);
+  for (int q = 0; q < 6; ++q) B[q] = __half22float2(hf[q]);
+  const float2 ne = corr3_cell(p, nb, w, B, q4);
   if (keep) S0.e[col][ye][pe] = ne;
   // colour B (red) is staged: its old value is at hand for over-relaxation
   return col == cB ? relax_red(p, ne, S0.e[col][ye][pe]) : ne;
