@@ -46,9 +46,9 @@ NOMINAL_HBM_GBS = 7900.0   # GB300 HBM3e nominal bandwidth (context beside the m
 # withdrawn (None) as soon as those sources differ from the captured ones.
 NCU_TRAFFIC = {
     ("smooth_tiled", "f32", 3): {
-        "bytes_per_cell": (238.06e6 + 42.11e6) / 192 ** 3,
+        "bytes_per_cell": (238.25e6 + 42.65e6) / 192 ** 3,
         "sources": ["sfx_tiled.cuh", "sfx_corr3.cuh"],
-        "sha256_16": "3ba10fa2bf2a58fa",
+        "sha256_16": "bfcde9800814a5bc",
         "capture": "profiles/corr2_tiled_hr3d192_f32.md (192^3 with the 256^3 z-chunk of 37 "
                    "planes, one launch), scaled by the cell count",
     },

@@ -322,54 +322,12 @@ __device__ __forceinline__ void faces6x2(const Level& L, const __half2* Hx, cons
   }
 }
 
-// (1/V) sum +-A G of one field around cell i as an unnormalised pair, and
+// (1/V) sum +-A G of both fields around cell i (lane x f with Doh.x and
+// drifts B[q].x, lane y F) as an unnormalised pair, and
 // the derivative of that sum in the cell value (negated: diagonal weight).
 // The diffusive part is gathered as Doh (sum_q w_q a_q - W a_c), W = sum_q
 // w_q, one pair product instead of one per face; the drift part as
 // sum_q +-w_q B_q a_up(q).
-template <int G>
-__device__ __forceinline__ float2 flux_pair(const Level& L, float invh, float Doh, int literal,
-                                            int i, float2 ac, const float2* nb, const bool* has,
-                                            const float* B, float& dflux) {
-  const bool axi = geom_of<G>(L) == SFX_AXISYM;
-  Acc D{0.0f, 0.0f}, T{0.0f, 0.0f};
-  float W = 0.0f, dg = 0.0f;
-#pragma unroll
-  for (int q = 0; q < 6; ++q) {
-    if (!has[q]) continue;
-    const bool plus = q & 1;
-    const bool upL = literal ? (B[q] > 0.0f) : (B[q] < 0.0f);
-    float w = 1.0f;
-    const int g = geom_of<G>(L);
-    if (axi) w = q < 2 ? wr_face(g, i + (plus ? 1 : 0)) : (q < 4 ? wz_face(g, i) : 1.0f);
-    acc_add(D, axi ? lp_mul(nb[q], w) : nb[q]);
-    W = __fadd_rn(W, w);
-    // upwind value: the left cell when upL; this cell is left on plus faces
-    const float2 aup = (plus == upL) ? ac : nb[q];
-    float2 u = lp_mul(aup, B[q]);
-    if (axi) u = lp_mul(u, w);   // B w in float would round the drift itself
-    if (plus) {
-      acc_add(T, u);
-      dg = __fmaf_rn(w, __fsub_rn(Doh, upL ? B[q] : 0.0f), dg);
-    } else {
-      acc_sub(T, u);
-      dg = __fmaf_rn(w, __fadd_rn(Doh, upL ? 0.0f : B[q]), dg);
-    }
-  }
-  acc_sub(D, lp_mul(ac, W));
-  acc_add(T, lp_mul(acc_get(D), Doh));
-  float2 flux = lp_mul(acc_get(T), invh);
-  dflux = __fmul_rn(dg, invh);
-  if (axi) {
-    const float wc = wz_face(geom_of<G>(L), i);
-    flux = df_div_f(ef_fast_two_sum(flux.x, flux.y), wc);
-    dflux = __fdividef(dflux, wc);
-  }
-  return flux;
-}
-
-// flux_pair of both fields at once (lane x f with Doh.x and drifts B[q].x,
-// lane y F), the same operations per lane: flux_pair's bits.
 template <int G>
 __device__ __forceinline__ P2 flux_pair2(const Level& L, float invh, float2 Doh, int literal,
                                          int i, const P2& ac, const P2* nb, const bool* has,
