@@ -1078,6 +1078,27 @@ __device__ __forceinline__ void force32_cell(const Level& L, const double* __res
   for (int d = 0; d < nd; ++d) force[(ix)d * n + c] = dm * (gs[d] - nn[d] * ndg);
 }
 
+// The rows r = k ny + j that a block of a row-walking kernel visits
+// (blockIdx.y, then every gridDim.y-th), their (j, k) advanced by additions
+// instead of a division per row.
+struct RowWalk {
+  int j, k, dj, dk, ny;
+  __device__ __forceinline__ RowWalk(int ny_) : ny(ny_) {
+    j = (int)(blockIdx.y % (unsigned)ny_);
+    k = (int)(blockIdx.y / (unsigned)ny_);
+    dj = (int)(gridDim.y % (unsigned)ny_);
+    dk = (int)(gridDim.y / (unsigned)ny_);
+  }
+  __device__ __forceinline__ void next() {
+    j += dj;
+    k += dk;
+    if (j >= ny) {
+      j -= ny;
+      ++k;
+    }
+  }
+};
+
 // blocks over (x chunk, rows); each block walks rows r = k ny + j
 __global__ void k_force32(Level L, const double* __restrict__ phi, const float* __restrict__ C,
                           const float* __restrict__ dsig, int dm_mode, float inv_eps,
@@ -1085,8 +1106,9 @@ __global__ void k_force32(Level L, const double* __restrict__ phi, const float* 
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= L.nx) return;
   const ix rows = (ix)L.ny * (ix)L.nz, n = rows * (ix)L.nx;
-  for (ix r = blockIdx.y; r < rows; r += gridDim.y) {
-    const int j = (int)(r % (ix)L.ny), k = (int)(r / (ix)L.ny);
+  RowWalk w(L.ny);
+  for (ix r = blockIdx.y; r < rows; r += gridDim.y, w.next()) {
+    const int j = w.j, k = w.k;
     force32_cell(L, phi, C, dsig, dm_mode, inv_eps, i, j, k, r * (ix)L.nx + (ix)i, n, force);
   }
 }
