@@ -435,9 +435,7 @@ k_corr2_32(Nw32 p, const __half2* __restrict__ Hx, const __half2* __restrict__ H
 }
 
 // The Newton kernels of one geometry (the branches on the geometry in the
-// cell functions fold at compile time).  The 3D residual keeps the branch
-// at run time: specialised it needs more registers than its occupancy
-// bound allows and spills.
+// cell functions fold at compile time).
 struct NewtonKernels {
   decltype(&k_resid2_32<SFX_CART3D>) resid;
   decltype(&k_resid32_fast<SFX_CART3D>) fast;
