@@ -911,6 +911,40 @@ def test_over_relaxed_sweeps_reach_the_same_fixed_point(sfx, tiled):
         assert all(m <= q + 1 for q, m in zip(its[0], its[k])), its
 
 
+@pytest.mark.parametrize("geom", ["planar", "axi"])
+def test_over_relaxed_sweeps_reach_the_same_fixed_point_2d(sfx, geom):
+    """The over-relaxed red updates on planar and axisymmetric grids (omega
+    from the Jacobi-radius bound, D dt/h^2 ~ 0.5 for F): the same fixed
+    point as Gauss-Seidel to far below the FP32 tolerance, every solve
+    converged, and no more Newton iterations over three steps."""
+    import torch
+    if geom == "planar":
+        g, Cf = _planar_circle(96, 80)
+    else:
+        g, Cf = _axi_sphere(48, 96)
+    ux, uy = W.uniform_faces(g, (0.3, -0.2))[:2] if geom == "planar" else (None, None)
+    p = W.Params(ka=2.0, kd=0.5, Df=2e-3, DF=5e-2, eps=0.75 * g.h)
+    _, phi, delta = oracle.phase_field_build(g, Cf, 24, W.redist_dtau(g), p.eps)
+    dt = 0.5 * g.h * g.h / p.DF
+    outs, its = [], []
+    for sor in (0, 1):
+        ctx = _ctx(sfx, g, 1)
+        ctx.sfx_set_tuning(sfx._lib.SFX_TUNE_F32_SOR, sor)
+        f, F = _pairs(ctx, 0.3 * delta), _pairs(ctx, 1.0 - Cf)
+        u = [dev(v, torch.float32) if v is not None else None for v in (ux, uy)] + [None]
+        n = 0
+        for _ in range(3):
+            st = ctx.sfx_surfactant_step(p, dev(phi), f, F, dt, *u,
+                                         opts=sfx.default_opts(tol=1e-10, mg_levels=1))
+            assert st.converged
+            n += st.picard
+        its.append(n)
+        outs.append((host(ctx.sfx_df_unpack(f)), host(ctx.sfx_df_unpack(F))))
+    for a, b in zip(outs[0], outs[1]):
+        assert np.abs(a - b).max() / np.abs(a).max() < 1e-8
+    assert its[1] <= its[0], its
+
+
 @pytest.mark.parametrize("shape", [(24, 24, 24), (19, 17, 70), (5, 9, 33)])
 def test_staged_advection_bitwise(sfx, shape):
     """The 3D BCG step from shared-memory planes (values rounded once,
