@@ -1497,8 +1497,11 @@ sfx_status solve_newton32(sfx_ctx* c, const Nw32& p, const float* phi, float* co
         const sfx_status ts = tiled_sweep(c, p, in, flag, s);
         if (ts != SFX_OK) return ts;
       }
-      SFX_KERNEL(c, K_SMOOTH_FINE, nk.corr, grd, blk, s, p, c->f32.H2[0], c->f32.H2[1], Hz,
-                 c->f32.rc, ebuf[in], 1, 0, fc, Fc, fsrc, Fsrc, flag);
+      // the last black colour, which adds the corrections to the state: one
+      // plane per thread (0.191 vs 0.207 ms at 256^3 with two)
+      const dim3 grd1(grd.x, grd.y, (unsigned)L.nz);
+      SFX_KERNEL(c, K_SMOOTH_FINE, (k_corr2_32<SFX_CART3D, 1>), grd1, blk, s, p, c->f32.H2[0],
+                 c->f32.H2[1], Hz, c->f32.rc, ebuf[in], 1, 0, fc, Fc, fsrc, Fsrc, flag);
       efin = in;
     } else {
       for (int q = 0; q < sweeps; ++q)
