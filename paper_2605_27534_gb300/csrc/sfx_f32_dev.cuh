@@ -867,18 +867,21 @@ __device__ __forceinline__ void corr2_load(const Nw32& p, int i, int j, int k,
 // its flux sums (flf, flF), their diagonal weights (dgf, dgF) and its
 // (r_f, r_F, u, v).  Every rounding is spelled out, so that each kernel
 // that inlines it computes the same bits.
-__device__ __forceinline__ float2 corr2_block(const Nw32& p, float4 q4, float efc, float eFc,
-                                              float flf, float flF, float dgf, float dgF) {
+__device__ __forceinline__ float2 corr2_block(const Nw32& p, float4 q4, float2 ec, float2 fl,
+                                              float2 dg) {
   const Jac2 J = jac2(p, q4.z, q4.w);
-  // residuals of the correction equation at this cell
-  const float rhof = __fmaf_rn(J.fF, eFc, __fmaf_rn(-J.ff, efc, __fadd_rn(q4.x, flf)));
-  const float rhoF = __fmaf_rn(J.Ff, efc, __fmaf_rn(-J.FF, eFc, __fadd_rn(q4.y, flF)));
+  // residuals of the correction equation at this cell, one lane per field:
+  // r + flux - diag e + coupling e_other
+  const float2 rho = v_fma(make_float2(J.fF, J.Ff), make_float2(ec.y, ec.x),
+                           v_fma(make_float2(-J.ff, -J.FF), ec,
+                                 v_add(make_float2(q4.x, q4.y), fl)));
   // 2x2 block solve: [a  -b; -d  e] [x; y] = [rhof; rhoF]
-  const float a = __fadd_rn(J.ff, dgf), bb = J.fF, d = J.Ff, e = __fadd_rn(J.FF, dgF);
+  const float2 ae = v_add(make_float2(J.ff, J.FF), dg);
+  const float a = ae.x, bb = J.fF, d = J.Ff, e = ae.y;
   const float det = __fmaf_rn(a, e, -__fmul_rn(bb, d));
   const float inv = __fdividef(1.0f, det);
-  return make_float2(__fmaf_rn(__fmaf_rn(e, rhof, __fmul_rn(bb, rhoF)), inv, efc),
-                     __fmaf_rn(__fmaf_rn(d, rhof, __fmul_rn(a, rhoF)), inv, eFc));
+  return v_fma(v_fma(make_float2(e, d), v_bc(rho.x), v_mul(make_float2(bb, a), v_bc(rho.y))),
+               v_bc(inv), ec);
 }
 
 template <int G>
@@ -905,12 +908,16 @@ __device__ __forceinline__ void corr2_apply(const Nw32& p, const Corr2In& in,
     // of loads (at its register bound)
     if (in.red) ne = relax_red(p, ne, e2[in.own]);
   } else {
-    float dgf, dgF;
-    const float flf = flux_lin<G>(L, p.invh, p.Dfh, p.literal, in.i, efc, in.enf, in.has, in.Bf,
-                                  dgf);
-    const float flF = flux_lin<G>(L, p.invh, p.DFh, p.literal, in.i, eFc, in.enF, in.has, in.BF,
-                                  dgF);
-    ne = corr2_block(p, in.q4, efc, eFc, flf, flF, dgf, dgF);
+    // both fields in two lanes
+    float2 en[6], B[6], dg;
+#pragma unroll
+    for (int q = 0; q < 6; ++q) {
+      en[q] = make_float2(in.enf[q], in.enF[q]);
+      B[q] = make_float2(in.Bf[q], in.BF[q]);
+    }
+    const float2 fl = flux_lin2<G>(L, p.invh, make_float2(p.Dfh, p.DFh), p.literal, in.i,
+                                   make_float2(efc, eFc), en, in.has, B, dg);
+    ne = corr2_block(p, in.q4, make_float2(efc, eFc), fl, dg);
     if (in.red) ne = relax_red(p, ne, in.ec);
   }
   const float nf = ne.x, nF = ne.y;
