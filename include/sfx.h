@@ -347,9 +347,12 @@ typedef enum {
                                the step then moves by 5e-5.  0 (default) =
                                FP64 redistancing as in SFX_F64 contexts. */
   SFX_TUNE_SWEEP_PLANES = 5, /* SFX_F32, 3D: z-planes each thread of the
-                               Newton correction sweep updates, 1 or 2
-                               (default: two independent cells' loads in
-                               flight per thread; 5 % faster at 256^3).
+                               Newton correction's colour launches updates,
+                               1 or 2 (default: two independent cells'
+                               loads in flight per thread; 5 % faster at
+                               256^3).  With tiled sweeps the one colour
+                               launch left, which adds the corrections to
+                               the state, always takes one (8 % faster).
                                Bitwise equal. */
   SFX_TUNE_TILED_SWEEP = 6, /* SFX_F32 Newton solver, 3D grids with nx a
                                multiple of 4, relaxation without the V-cycle
