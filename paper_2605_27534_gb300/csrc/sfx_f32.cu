@@ -840,8 +840,12 @@ __global__ void __launch_bounds__(kAdvX* kAdvY)
 // Per-thread double-float accumulation of w_i (hi + lo) with w_i the cell
 // volume over its constant factor (1, or 2i+1 on rings); FP64 only across
 // threads.
-__global__ void k_total32_partials(Level L, const float2* __restrict__ x, int fi,
+__global__ void k_total32_partials(Level L, const float2* __restrict__ x0,
+                                   const float2* __restrict__ x1, int f0,
                                    double* __restrict__ partials) {
+  // blockIdx.y picks the field: both fields' blocks in flight together
+  const float2* __restrict__ x = blockIdx.y ? x1 : x0;
+  const int fi = f0 + (int)blockIdx.y;
   const size_t n = L.ncell();
   // four independent pair accumulators: four loads in flight per thread
   float2 acc[4] = {make_float2(0.0f, 0.0f), make_float2(0.0f, 0.0f), make_float2(0.0f, 0.0f),
@@ -1775,9 +1779,11 @@ sfx_status advect32(sfx_ctx* c, const float* ux, const float* uy, const float* u
 sfx_status totals32(sfx_ctx* c, const void* const* fields, int nf, double* out, cudaStream_t s) {
   const Level& L = c->lev[0].lv;
   const int nblk = c->n_partial_blocks;
-  for (int i = 0; i < nf; ++i)
-    SFX_KERNEL(c, K_TOTALS, k_total32_partials, nblk, 256, s, L, (const float2*)fields[i], i,
-               c->partials);
+  for (int i = 0; i < nf; i += 2) {
+    const int m = std::min(2, nf - i);
+    SFX_KERNEL(c, K_TOTALS, k_total32_partials, dim3((unsigned)nblk, (unsigned)m), 256, s, L,
+               (const float2*)fields[i], (const float2*)fields[i + m - 1], i, c->partials);
+  }
   double h = L.h;
   double scale = L.geom == SFX_PLANAR2D ? h * h : (L.geom == SFX_CART3D ? h * h * h : kPi * h * h * h);
   SFX_KERNEL(c, K_TOTALS, k_total32_final, nf, 256, s, c->partials, nblk, scale, c->d_sums);
