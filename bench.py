@@ -648,7 +648,8 @@ def run_gpu(a, case, rank, world, local_rank):
         else:
             nw_m = nw
         if m is not None and nw > 0:
-            e["method_gbs"] = round(m / (v[1] * 1e-3 / nw) / 1e9, 1)
+            # the method's bytes are per pass (totals and forces: per step)
+            e["method_gbs"] = round(m * nw_m / (v[1] * 1e-3) / 1e9, 1)
             e["method_frac"] = round(e["method_gbs"] / peaks["hbm_gbs"], 3)
             step_method += m * nw_m
         if b is not None and nw > 0:
