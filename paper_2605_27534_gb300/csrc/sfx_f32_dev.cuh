@@ -83,7 +83,6 @@ __device__ __forceinline__ P2 v_lp_sub(const P2& a, const P2& b) {
   return P2{t, v_add(e, v_sub(a.lo, b.lo))};
 }
 
-
 // ------------------------------------------------------------ drifts
 // Folded float copy of phi: phi where phi <= 1/2, phi - 1 elsewhere.
 __device__ __forceinline__ float fold_phi(double p) {
